@@ -1,0 +1,294 @@
+"""Benchmark of the CTA hot path on GB300 (one JSON line on stdout).
+
+Workload (one "step"): one CTA solve (Alg. 1.1, H = A Aᵀ, ping-pong t-cycling
+up to t = 5, true residual every 40 steps) from x = 0 toward the 1e-8 relative
+residual target on the 2D convection-diffusion 5-point stencil on a 1000 x 1000
+grid (n = 1e6, 4,996,000 nonzeros, CSR, FP64, b = A·1), capped at
+ITERS_PER_STEP F_t applications. The system needs far more iterations than
+the cap to reach 1e-8 (kappa(AAᵀ) ~ 1e11), so every step runs the full cap and
+the metric is the F_t iteration rate; the residual reached is reported.
+
+value      : F_t iterations per second over the K timed steps (device events),
+             inputs resident in HBM, L2 flushed between steps.
+e2e        : same metric through the one-shot C ABI call with host buffers
+             (pinned): A and b copied in, plan built (device transpose), solve,
+             x and the residual history copied out, all inside the timed region.
+roofline   : the iteration's products (CSR SpMV with A and Aᵀ), timed one by one
+             with CUDA events inside a profiled solve of the same workload;
+             algorithmic bytes per product = 12 nnz + 4 (rows+1) + 8 cols + 8 rows.
+cpu_baseline: the FP64 numpy oracle on the same workload, a bounded sample of
+             CPU_SAMPLE_ITERS iterations.
+
+--impl reference times the oracle itself (the CPU statement of the method) on
+the same config, each step a bounded sample of REF_ITERS_PER_STEP iterations.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GRID = 1000
+ITERS_PER_STEP = 1000
+TOL = 1e-8
+CPU_SAMPLE_ITERS = 40
+REF_ITERS_PER_STEP = 4
+METRIC = "TA/CTA iterations/sec and time-to-1e-8 rel. residual; achieved HBM GB/s vs peak"
+UNIT = "CTA iterations/s"
+WORKLOAD = "cta_fp64_convdiff_5pt_1000x1000"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_record():
+    """dram bytes per launch of the SpMV from a committed ncu capture, if the kernel
+    source is unchanged since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "spmv_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2304_12168_gb300", "csrc", "kernels.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec.get("kernels_cu_sha256"):
+            return None
+        return float(rec["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 7:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def problem():
+    import gen
+    return gen.convdiff_stencil(GRID)
+
+
+def cpu_baseline(p, iters):
+    import oracle
+    A = oracle.make_operator(p)
+    t0 = time.perf_counter()
+    r = oracle.cta_solve(A, p.b, tol=TOL, tol_normal=0.0, max_iter=iters)
+    dt = time.perf_counter() - t0
+    return r.iters / dt, dt, r
+
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores, on this workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p = problem()
+    for _ in range(args.warmup):
+        cpu_baseline(p, REF_ITERS_PER_STEP)
+    times = []
+    for _ in range(args.steps):
+        _, dt, r = cpu_baseline(p, REF_ITERS_PER_STEP)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * REF_ITERS_PER_STEP / total
+    sample = f"first {REF_ITERS_PER_STEP} F_t steps of the solve per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": f"{GRID}x{GRID}", "n": p.n, "nnz": p.nnz,
+                       "iters_per_step": REF_ITERS_PER_STEP, "tol": TOL},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tacta", choices=["tacta", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import paper_2304_12168_gb300 as tacta
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    tacta.load_library()
+
+    p = problem()
+    A = tacta.CSR(torch.from_numpy(p.rowptr).to(dev), torch.from_numpy(p.colidx).to(dev),
+                  torch.from_numpy(p.vals).to(dev), (p.m, p.n))
+    b = torch.from_numpy(p.b).to(dev)
+    plan = tacta.Plan(A)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    opts = dict(tol=TOL, tol_normal=0.0, max_iter=ITERS_PER_STEP)
+
+    for _ in range(args.warmup):
+        plan.cta(b, **opts)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: K steps, device events, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    iters = []
+    launches = 0
+    infos = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            x, hist, info = plan.cta(b, **opts)
+            ev[i][1].record(stream)
+            iters.append(info["iters"])
+            launches += info["launches"]
+            infos.append(info)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * sum(iters) / (total_ms * 1e-3)
+    clocks = clk.summary()
+    last = infos[-1]
+
+    # ---------------- roofline: the products of the iteration, each timed with events
+    _, _, prof = plan.cta(b, profile=1, **opts)
+    spmv_us = 1e3 * prof["spmv_ms"] / prof["spmv_count"]
+    spmv_bytes = prof["spmv_bytes"] / prof["spmv_count"]
+    achieved = spmv_bytes / (spmv_us * 1e-6) / 1e9
+    peak, peak_kind = peaks()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_record(),
+                "kernel": "spmv_scalar<CsrAcc, EPI_NORM> (A and Aᵀ products of the F_t chain)",
+                "launches_timed": prof["spmv_count"], "avg_launch_us": spmv_us,
+                "bytes_per_launch": spmv_bytes, "peak_kind": peak_kind,
+                "fp64_fma_per_launch": (p.nnz + p.m),
+                "fp64_fma_frac_of_nominal": (p.nnz + p.m) / (spmv_us * 1e-6) / 0.629e12}
+
+    # ---------------- e2e: one-shot C ABI call with pinned host buffers
+    hA = tacta.CSR(torch.from_numpy(p.rowptr).pin_memory(), torch.from_numpy(p.colidx).pin_memory(),
+                   torch.from_numpy(p.vals).pin_memory(), (p.m, p.n))
+    hb = torch.from_numpy(p.b).pin_memory()
+    e2e_steps = min(args.steps, 5)
+    tacta.cta_solve(hA, hb, hist_cap=ITERS_PER_STEP + 1, **opts)       # warm
+    e2e_iters, t0 = 0, time.perf_counter()
+    for _ in range(e2e_steps):
+        xh, hh, ih = tacta.cta_solve(hA, hb, hist_cap=ITERS_PER_STEP + 1, **opts)
+        e2e_iters += ih["iters"]
+    e2e_s = time.perf_counter() - t0
+    h2d = 4 * (p.m + 1) + 12 * p.nnz + 8 * p.m
+    d2h = 8 * p.n + 8 * (ITERS_PER_STEP + 1)
+    e2e = {"value": world * e2e_iters / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+           "includes": "H2D of A and b, plan build (device CSR transpose), solve, D2H of x and history"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": f"{GRID}x{GRID}", "n": p.n, "nnz": p.nnz,
+                       "iters_per_step": ITERS_PER_STEP, "t_cycle": "ping-pong 1..5", "R": 40,
+                       "tol": TOL, "l2": "flushed between steps (256 MiB write); working set "
+                       "~0.23 GB > 129 MB L2", "parallelism": f"replicas x{world}"},
+            "rel_res_after_step": last["rel_res"], "time_to_tol_s": None,
+            "matvecs_per_s": world * sum(i["matvecs"] for i in infos) / (total_ms * 1e-3),
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, r = cpu_baseline(p, CPU_SAMPLE_ITERS)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {CPU_SAMPLE_ITERS} F_t steps of the same solve "
+                                          f"({dt:.1f} s, numpy FP64, single thread)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * tacta.h -- C ABI of the GB300 (sm_103a) Triangle Algorithm / Centering
+ * Triangle Algorithm solvers (Lau & Kalantari, arXiv:2304.12168).
+ *
+ * The library computes approximate and minimum-norm solutions of A x = b and
+ * of the normal equation AᵀA x = Aᵀb for an m x n real matrix A of any shape
+ * and rank, stored dense row-major or CSR, in FP64 on one GPU.
+ *
+ * Entry points (all return a tacta_status; none aborts or prints):
+ *   cta_solve  -- Algorithm 1.1 (CTA, H = A Aᵀ, Sec. 3.2) with the t-cycling
+ *                 of Sec. 5.1: iterates of F_t (Eqs. F_t, eqcoeff, CTAGEN7,
+ *                 CTAGEN7A).
+ *   ta_solve   -- Algorithm 2.2 (TA with growing rho, Sec. 4.3): pivot from
+ *                 Thm. prop0TA (Eqs. vr, eqlem2), step from Prop. prop1TA
+ *                 (Eq. alph).
+ *   ta_minnorm -- the hybrid of Sec. 5.2: CTA to tol_cta, then Algorithm 2.5
+ *                 (bisection on rho, Sec. 4.4, lower bound of Cor. cor1) on
+ *                 (A, b) when CTA's x solves A x = b, else on (AᵀA, Aᵀb)
+ *                 applied through products with A and Aᵀ.
+ * Plans (tacta_plan_*) hold the device copy of A and its transpose, so that
+ * several right-hand sides reuse one setup.
+ *
+ * Conventions
+ *   - Every array is caller-owned. The library copies A into its own device
+ *     storage (plus Aᵀ) at plan creation; the caller's A may be freed after
+ *     tacta_plan_create returns (one-shot calls keep nothing).
+ *   - on_device = 1: every pointer argument of the call (A's arrays, b, x0,
+ *     x_out, hist) is a CUDA device pointer of the current device;
+ *     on_device = 0: all are host pointers and the library does the copies.
+ *   - All GPU work is enqueued on opt->stream (a cudaStream_t; NULL = the
+ *     legacy default stream). Every call synchronises that stream before it
+ *     returns, so outputs are ready on return.
+ *   - Tolerances are relative: the residual test is ||b - A x|| <= tol ||b||,
+ *     the normal-equation test ||Aᵀ(b - A x)|| <= tol_normal ||Aᵀ b||.
+ *   - Validation: sizes and options are checked on the host before any GPU
+ *     work (m, n >= 1 and < 2^31; dense m*n <= 2^40; 0 <= nnz < 2^31; tol
+ *     finite and > 0; t_max in 1..8; max_iter >= 0). The CSR structure
+ *     (rowptr[0] = 0, non-decreasing, rowptr[m] = nnz, 0 <= colidx < n) is
+ *     checked by a kernel right after A is copied to the device, before any
+ *     kernel indexes with it; a violation returns TACTA_ERR_INVALID.
+ *   - MAXITER, BREAKDOWN and WITNESS still fill x_out and info.
+ *   - Errors (negative status) leave x_out unspecified; tacta_last_error()
+ *     gives a message for the calling thread.
+ */
+#ifndef TACTA_H
+#define TACTA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TACTA_OK = 0,            /* a stopping test of the algorithm was met          */
+    TACTA_MAXITER = 1,       /* iteration cap reached first                        */
+    TACTA_BREAKDOWN = 2,     /* step undefined: Hankel rank 0 or ||v - b'|| = 0    */
+    TACTA_WITNESS = 3,       /* Alg. 2.1 witness (only from internal trips)        */
+    TACTA_ERR_INVALID = -1,  /* bad argument (message in tacta_last_error)         */
+    TACTA_ERR_NONFINITE = -2,/* NaN / Inf appeared in a reduction                  */
+    TACTA_ERR_CUDA = -3,     /* a CUDA runtime call failed                         */
+    TACTA_ERR_OOM = -4,      /* device allocation failed                           */
+    TACTA_ERR_TIMEOUT = -5   /* a bounded device wait gave up                      */
+} tacta_status;
+
+/* why the iteration ended (tacta_info.reason) */
+enum {
+    TACTA_REASON_NONE = 0,
+    TACTA_REASON_RESIDUAL = 1,   /* ||b - A x|| <= tol ||b|| (true residual)               */
+    TACTA_REASON_NORMAL = 2,     /* ||Aᵀ r|| <= tol_normal ||Aᵀ b||: normal equation solved */
+    TACTA_REASON_MAXITER = 3,
+    TACTA_REASON_BREAKDOWN = 4,
+    TACTA_REASON_WITNESS = 5,
+    TACTA_REASON_GAP = 6,        /* Alg. 2.5: rho_upper - rho_lower <= tol ||x_eps||        */
+    TACTA_REASON_ZERO_RHS = 7,   /* b = 0: x = 0                                            */
+    TACTA_REASON_NONFINITE = 8
+};
+
+enum { TACTA_DENSE = 0, TACTA_CSR = 1 };
+
+/* t-cycling (Sec. 5.1): ping-pong 1,2,..,t_max,..,2,1,2,..; sawtooth 1..t_max,1..; fixed t_max */
+enum { TACTA_CYCLE_PINGPONG = 0, TACTA_CYCLE_SAWTOOTH = 1, TACTA_CYCLE_FIXED = 2 };
+
+typedef struct {
+    int64_t m, n;            /* rows, columns                                        */
+    int64_t nnz;             /* CSR: stored entries (= rowptr[m]); dense: ignored     */
+    int32_t format;          /* TACTA_DENSE (row-major m x n) or TACTA_CSR            */
+    int32_t on_device;       /* 1: device pointers (all arrays of the call); 0: host  */
+    const double* vals;      /* dense: m*n values, row-major; CSR: nnz values         */
+    const int32_t* rowptr;   /* CSR: m+1 offsets                                      */
+    const int32_t* colidx;   /* CSR: nnz column indices                               */
+} tacta_matrix;
+
+typedef struct {
+    double tol;              /* relative residual tolerance (> 0)                              */
+    double tol_normal;       /* relative normal-equation tolerance; < 0: same as tol;
+                                0: stop only when Aᵀ r is exactly 0                            */
+    double tol_cta;          /* ta_minnorm: tolerance of the CTA phase; <= 0: same as tol     */
+    double pivot_tol;        /* truncation threshold of the scaled Hankel Cholesky; <= 0: 1e-12 */
+    int32_t max_iter;        /* iteration cap (CTA: F_t steps; TA: loop trips)                 */
+    int32_t t_max;           /* largest CTA order (1..8; the paper cycles up to 5)             */
+    int32_t cycle;           /* TACTA_CYCLE_*                                                   */
+    int32_t recompute_every; /* R: true residual b - A x every R iterations; 0: never          */
+    int32_t use_graph;       /* 1: replay the iteration body as a captured CUDA graph          */
+    int32_t poll_every;      /* host checks the device stop flag every this many iterations    */
+    int32_t profile;         /* 1: time every product of the iteration with CUDA events on the
+                                stream (forces use_graph = 0); results in tacta_info.spmv_*    */
+    void* stream;            /* cudaStream_t (NULL: legacy default stream)                      */
+} tacta_options;
+
+typedef struct {
+    int32_t status;          /* same as the return value                               */
+    int32_t reason;          /* TACTA_REASON_*                                         */
+    int32_t iters;           /* CTA: F_t steps; TA: loop trips (all trips for minnorm) */
+    int32_t matvecs;         /* products with A or Aᵀ made by the iteration            */
+    double rel_res;          /* true ||b - A x|| / ||b|| at exit                       */
+    double rel_normal_res;   /* true ||Aᵀ(b - A x)|| / ||Aᵀ b|| at exit                */
+    double rho;              /* TA: final rho; minnorm: rho_upper                      */
+    double rho_lower;        /* minnorm: the lower bound rho_lower (Cor. cor1)         */
+    int32_t trips;           /* minnorm: bisection trips                               */
+    int32_t cta_iters;       /* minnorm: CTA iterations of the first phase             */
+    int32_t normal_system;   /* minnorm: 1 when TA ran on (AᵀA, Aᵀb)                    */
+    int32_t hist_len;        /* entries written to hist                                */
+    int64_t launches;        /* GPU kernels launched by the call                        */
+    int32_t spmv_count;      /* profile = 1: products timed (iteration chain only)      */
+    int32_t spmv_pad;
+    double spmv_ms;          /* profile = 1: summed device time of those products       */
+    double spmv_bytes;       /* profile = 1: their algorithmic bytes (values, indices,
+                                row offsets, input vector once, output vector once)     */
+} tacta_info;
+
+/* Fill *opt with the defaults: tol 1e-10, tol_normal -1, tol_cta 0, pivot_tol 1e-12,
+   max_iter 1000, t_max 5, ping-pong cycle, R = 40, use_graph 1, poll_every 64, profile 0,
+   NULL stream. */
+void tacta_default_options(tacta_options* opt);
+
+/*
+ * cta_solve -- Algorithm 1.1 (CTA) with H = A Aᵀ.
+ *   A       matrix (see tacta_matrix); b: m values; x0: n values or NULL (start at 0;
+ *           from 0 the iterates stay in range(Aᵀ), Thm. thmone (4));
+ *   opt     options (NULL: defaults); x_out: n values (written);
+ *   hist    relative residual after each F_t step, hist[0] at the start
+ *           (min(iters+1, hist_cap) values; NULL or hist_cap = 0: not written);
+ *   info    outcome (may be NULL).
+ */
+tacta_status cta_solve(const tacta_matrix* A, const double* b, const double* x0,
+                       const tacta_options* opt, double* x_out, double* hist,
+                       int32_t hist_cap, tacta_info* info);
+
+/* ta_solve -- Algorithm 2.2 (TA, rho = 0 grown on witnesses). Arguments as cta_solve;
+   x0 (optional) is a warm start: b' = A x0 and rho = ||x0||. hist holds ||b - b'|| / ||b||. */
+tacta_status ta_solve(const tacta_matrix* A, const double* b, const double* x0,
+                      const tacta_options* opt, double* x_out, double* hist,
+                      int32_t hist_cap, tacta_info* info);
+
+/* ta_minnorm -- approximate minimum-norm solution (Def. minnormapp): CTA to tol_cta from 0,
+   then Algorithm 2.5 at tol. x0 is ignored. hist holds the CTA phase's history.
+   info->rho = rho_upper (>= ||x_out||), info->rho_lower = rho_lower (< ||x_*||). */
+tacta_status ta_minnorm(const tacta_matrix* A, const double* b, const double* x0,
+                        const tacta_options* opt, double* x_out, double* hist,
+                        int32_t hist_cap, tacta_info* info);
+
+/* Plans: device copy of A (+ Aᵀ, built on the GPU) and solver workspace, on the device
+   that is current at creation. The plan must be used from that device only.
+   Plan solves take the same arguments as the one-shot calls minus A; their vector
+   pointers follow A's on_device flag given at creation. */
+typedef struct tacta_plan_s* tacta_plan;
+
+tacta_status tacta_plan_create(const tacta_matrix* A, const tacta_options* opt, tacta_plan* plan);
+tacta_status tacta_plan_cta(tacta_plan plan, const double* b, const double* x0,
+                            const tacta_options* opt, double* x_out, double* hist,
+                            int32_t hist_cap, tacta_info* info);
+tacta_status tacta_plan_ta(tacta_plan plan, const double* b, const double* x0,
+                           const tacta_options* opt, double* x_out, double* hist,
+                           int32_t hist_cap, tacta_info* info);
+tacta_status tacta_plan_minnorm(tacta_plan plan, const double* b, const double* x0,
+                                const tacta_options* opt, double* x_out, double* hist,
+                                int32_t hist_cap, tacta_info* info);
+void tacta_plan_destroy(tacta_plan plan);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char* tacta_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int32_t tacta_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TACTA_H */

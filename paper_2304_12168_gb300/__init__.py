@@ -1,0 +1,291 @@
+"""GB300-native TA / CTA linear-system solvers (Lau & Kalantari, arXiv:2304.12168).
+
+Thin ctypes binding of ``libtacta.so`` (declared in ``include/tacta.h``). The
+functions here only marshal arguments: every step of the solvers runs in the
+library's CUDA kernels. There is no CPU fallback; if the library is missing,
+every call raises.
+
+Matrices are passed as
+  * a 2-D float64 array / tensor (dense, row-major), or
+  * ``CSR(rowptr, colidx, vals, shape)`` (int32, int32, float64), or
+  * any object with ``fmt`` ("dense"/"csr"), ``m``, ``n`` and the arrays
+    ``dense`` or ``rowptr``/``colidx``/``vals``.
+Arrays may be numpy arrays / CPU tensors (host: the library copies them) or
+CUDA tensors (device: all arrays of one call must then be CUDA tensors on the
+current device; work runs on torch's current stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtacta.so")
+
+# ---------------------------------------------------------------- C structs (include/tacta.h)
+
+TACTA_DENSE, TACTA_CSR = 0, 1
+CYCLE_PINGPONG, CYCLE_SAWTOOTH, CYCLE_FIXED = 0, 1, 2
+STATUS = {0: "OK", 1: "MAXITER", 2: "BREAKDOWN", 3: "WITNESS", -1: "ERR_INVALID",
+          -2: "ERR_NONFINITE", -3: "ERR_CUDA", -4: "ERR_OOM", -5: "ERR_TIMEOUT"}
+REASON = {0: "NONE", 1: "RESIDUAL", 2: "NORMAL", 3: "MAXITER", 4: "BREAKDOWN", 5: "WITNESS",
+          6: "GAP", 7: "ZERO_RHS", 8: "NONFINITE"}
+
+
+class tacta_matrix(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("format", ctypes.c_int32), ("on_device", ctypes.c_int32),
+                ("vals", ctypes.c_void_p), ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p)]
+
+
+class tacta_options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("tol_normal", ctypes.c_double),
+                ("tol_cta", ctypes.c_double), ("pivot_tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("t_max", ctypes.c_int32), ("cycle", ctypes.c_int32),
+                ("recompute_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("poll_every", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class tacta_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reason", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("matvecs", ctypes.c_int32), ("rel_res", ctypes.c_double),
+                ("rel_normal_res", ctypes.c_double), ("rho", ctypes.c_double),
+                ("rho_lower", ctypes.c_double), ("trips", ctypes.c_int32),
+                ("cta_iters", ctypes.c_int32), ("normal_system", ctypes.c_int32),
+                ("hist_len", ctypes.c_int32), ("launches", ctypes.c_int64),
+                ("spmv_count", ctypes.c_int32), ("spmv_pad", ctypes.c_int32),
+                ("spmv_ms", ctypes.c_double), ("spmv_bytes", ctypes.c_double)]
+
+
+EXPORTS = ["tacta_default_options", "cta_solve", "ta_solve", "ta_minnorm", "tacta_plan_create",
+           "tacta_plan_cta", "tacta_plan_ta", "tacta_plan_minnorm", "tacta_plan_destroy",
+           "tacta_last_error", "tacta_version"]
+
+_lib_handle = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libtacta.so (raises if it has not been built)."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2304_12168_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, dp = ctypes.c_void_p, ctypes.c_void_p
+    solve_args = [P(tacta_matrix), dp, dp, P(tacta_options), dp, dp, ctypes.c_int32, P(tacta_info)]
+    plan_args = [vp, dp, dp, P(tacta_options), dp, dp, ctypes.c_int32, P(tacta_info)]
+    lib.tacta_default_options.argtypes = [P(tacta_options)]
+    lib.tacta_default_options.restype = None
+    for name in ("cta_solve", "ta_solve", "ta_minnorm"):
+        getattr(lib, name).argtypes = solve_args
+        getattr(lib, name).restype = ctypes.c_int32
+    for name in ("tacta_plan_cta", "tacta_plan_ta", "tacta_plan_minnorm"):
+        getattr(lib, name).argtypes = plan_args
+        getattr(lib, name).restype = ctypes.c_int32
+    lib.tacta_plan_create.argtypes = [P(tacta_matrix), P(tacta_options), P(vp)]
+    lib.tacta_plan_create.restype = ctypes.c_int32
+    lib.tacta_plan_destroy.argtypes = [vp]
+    lib.tacta_plan_destroy.restype = None
+    lib.tacta_last_error.argtypes = []
+    lib.tacta_last_error.restype = ctypes.c_char_p
+    lib.tacta_version.argtypes = []
+    lib.tacta_version.restype = ctypes.c_int32
+    _lib_handle = lib
+    return lib
+
+
+# ---------------------------------------------------------------- argument marshalling
+
+@dataclass
+class CSR:
+    rowptr: object
+    colidx: object
+    vals: object
+    shape: tuple
+
+
+def _is_cuda(a) -> bool:
+    return getattr(a, "is_cuda", False)
+
+
+def _ptr(a, dtype) -> tuple[int, bool, object]:
+    """(address, on_device, keep-alive) of a contiguous array of `dtype`."""
+    if a is None:
+        return 0, False, None
+    if hasattr(a, "data_ptr"):       # torch tensor
+        import torch
+        tdt = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        if a.dtype != tdt or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {tdt} tensor, got {a.dtype}")
+        return a.data_ptr(), bool(a.is_cuda), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, False, arr
+
+
+def _matrix(A):
+    """tacta_matrix + keep-alive list from a dense array, CSR, or problem-like object."""
+    keep = []
+    if isinstance(A, CSR) or getattr(A, "fmt", None) == "csr":
+        if isinstance(A, CSR):
+            rp, ci, va, (m, n) = A.rowptr, A.colidx, A.vals, A.shape
+        else:
+            rp, ci, va, m, n = A.rowptr, A.colidx, A.vals, A.m, A.n
+        pr, d1, k1 = _ptr(rp, np.int32)
+        pc, d2, k2 = _ptr(ci, np.int32)
+        pv, d3, k3 = _ptr(va, np.float64)
+        if not (d1 == d2 == d3):
+            raise ValueError("CSR arrays must all be on the host or all on the device")
+        nnz = int(k3.numel() if hasattr(k3, "numel") else k3.size)
+        keep += [k1, k2, k3]
+        return tacta_matrix(int(m), int(n), nnz, TACTA_CSR, int(d1), pv, pr, pc), d1, keep
+    D = A.dense if getattr(A, "fmt", None) == "dense" else A
+    if len(D.shape) != 2:
+        raise ValueError("dense A must be 2-D")
+    m, n = int(D.shape[0]), int(D.shape[1])
+    pv, dv, kv = _ptr(D, np.float64)
+    keep.append(kv)
+    return tacta_matrix(m, n, m * n, TACTA_DENSE, int(dv), pv, 0, 0), dv, keep
+
+
+def _stream_ptr(on_device: bool):
+    if not on_device:
+        return None
+    import torch
+    return torch.cuda.current_stream().cuda_stream or None
+
+
+def make_options(on_device=False, **kw) -> tacta_options:
+    o = tacta_options()
+    load_library().tacta_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k!r}")
+        setattr(o, k, v)
+    if "stream" not in kw:
+        o.stream = _stream_ptr(on_device)
+    return o
+
+
+def _vec_out(n, on_device, like):
+    if on_device:
+        import torch
+        return torch.empty(n, dtype=torch.float64, device=like.device)
+    return np.empty(n, dtype=np.float64)
+
+
+def _info_dict(st: int, info: tacta_info) -> dict:
+    d = {f: getattr(info, f) for f, _ in tacta_info._fields_}
+    d["status_name"] = STATUS.get(st, str(st))
+    d["reason_name"] = REASON.get(info.reason, str(info.reason))
+    return d
+
+
+class TactaError(RuntimeError):
+    pass
+
+
+def _check(st: int):
+    if st < 0:
+        msg = load_library().tacta_last_error().decode()
+        raise TactaError(f"{STATUS.get(st, st)}: {msg}")
+
+
+def _solve(name, A, b, x0=None, hist_cap=None, **opts):
+    lib = load_library()
+    M, on_dev, keep = _matrix(A)
+    pb, db_, kb = _ptr(b, np.float64)
+    px, dx, kx = _ptr(x0, np.float64)
+    if db_ != bool(on_dev) or (x0 is not None and dx != bool(on_dev)):
+        raise ValueError("A, b and x0 must all be on the host or all on the device")
+    o = make_options(on_dev, **opts)
+    if hist_cap is None:
+        hist_cap = int(o.max_iter) + 1
+    x = _vec_out(int(M.n), on_dev, kb)
+    hist = _vec_out(max(hist_cap, 1), on_dev, kb)
+    info = tacta_info()
+    st = getattr(lib, name)(ctypes.byref(M), pb, px or None, ctypes.byref(o),
+                            _ptr(x, np.float64)[0], _ptr(hist, np.float64)[0], int(hist_cap),
+                            ctypes.byref(info))
+    _check(st)
+    del keep, kb, kx
+    return x, hist[: info.hist_len], _info_dict(st, info)
+
+
+def cta_solve(A, b, x0=None, hist_cap=None, **opts):
+    """Algorithm 1.1 (CTA, H = A Aᵀ) -> (x, residual history, info dict)."""
+    return _solve("cta_solve", A, b, x0, hist_cap, **opts)
+
+
+def ta_solve(A, b, x0=None, hist_cap=None, **opts):
+    """Algorithm 2.2 (TA) -> (x, residual history, info dict)."""
+    return _solve("ta_solve", A, b, x0, hist_cap, **opts)
+
+
+def ta_minnorm(A, b, hist_cap=None, **opts):
+    """Hybrid CTA -> Algorithm 2.5 minimum-norm solve -> (x, CTA history, info dict)."""
+    return _solve("ta_minnorm", A, b, None, hist_cap, **opts)
+
+
+class Plan:
+    """A on the GPU (plus Aᵀ) reused across right-hand sides (tacta_plan_*)."""
+
+    def __init__(self, A, **opts):
+        lib = load_library()
+        M, self.on_device, keep = _matrix(A)
+        self.m, self.n = int(M.m), int(M.n)
+        o = make_options(self.on_device, **opts)
+        h = ctypes.c_void_p()
+        st = lib.tacta_plan_create(ctypes.byref(M), ctypes.byref(o), ctypes.byref(h))
+        _check(st)
+        self._h = h
+        del keep
+
+    def _call(self, fn, b, x0, hist_cap, opts):
+        lib = load_library()
+        pb, db_, kb = _ptr(b, np.float64)
+        px, _, kx = _ptr(x0, np.float64)
+        if db_ != bool(self.on_device):
+            raise ValueError("b must be on the same side as the plan's matrix")
+        o = make_options(self.on_device, **opts)
+        if hist_cap is None:
+            hist_cap = int(o.max_iter) + 1
+        x = _vec_out(self.n, self.on_device, kb)
+        hist = _vec_out(max(hist_cap, 1), self.on_device, kb)
+        info = tacta_info()
+        st = getattr(lib, fn)(self._h, pb, px or None, ctypes.byref(o), _ptr(x, np.float64)[0],
+                              _ptr(hist, np.float64)[0], int(hist_cap), ctypes.byref(info))
+        _check(st)
+        del kb, kx
+        return x, hist[: info.hist_len], _info_dict(st, info)
+
+    def cta(self, b, x0=None, hist_cap=None, **opts):
+        return self._call("tacta_plan_cta", b, x0, hist_cap, opts)
+
+    def ta(self, b, x0=None, hist_cap=None, **opts):
+        return self._call("tacta_plan_ta", b, x0, hist_cap, opts)
+
+    def minnorm(self, b, hist_cap=None, **opts):
+        return self._call("tacta_plan_minnorm", b, None, hist_cap, opts)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().tacta_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ = ["cta_solve", "ta_solve", "ta_minnorm", "Plan", "CSR", "load_library", "make_options",
+           "TactaError", "EXPORTS", "LIB_PATH"]

@@ -1,0 +1,70 @@
+"""Builds libtacta.so in-tree with nvcc for sm_103a (GB300).
+
+The translation units are compiled in parallel into ``_build/`` and linked
+into ``paper_2304_12168_gb300/libtacta.so`` (static CUDA runtime). A unit is
+rebuilt when it or any header under ``csrc/`` / ``include/`` is newer than its
+object file.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libtacta.so")
+SOURCES = ["kernels.cu", "transpose.cu", "tacta.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+                "-I" + os.path.join(ROOT, "include")]
+
+
+def nvcc() -> str:
+    exe = os.environ.get("NVCC") or shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(exe):
+        raise RuntimeError(f"nvcc not found (looked for {exe})")
+    return exe
+
+
+def _headers_mtime() -> float:
+    t = 0.0
+    for d in (CSRC, os.path.join(ROOT, "include")):
+        for f in os.listdir(d):
+            if f.endswith((".h", ".cuh")):
+                t = max(t, os.path.getmtime(os.path.join(d, f)))
+    return t
+
+
+def _compile(src: str, force: bool, hdr: float, extra) -> str:
+    s = os.path.join(CSRC, src)
+    o = os.path.join(BUILD, src.replace(".cu", ".o"))
+    if not force and os.path.exists(o) and os.path.getmtime(o) >= max(os.path.getmtime(s), hdr):
+        return o
+    cmd = [nvcc()] + FLAGS + list(extra) + ["-c", s, "-o", o]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {src}:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    return o
+
+
+def build(force: bool = False, extra_flags=()) -> str:
+    """Compile and link libtacta.so; returns its path."""
+    os.makedirs(BUILD, exist_ok=True)
+    hdr = _headers_mtime()
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        objs = list(ex.map(lambda s: _compile(s, force, hdr, extra_flags), SOURCES))
+    newest = max(os.path.getmtime(o) for o in objs)
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", LIB] + objs
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True))

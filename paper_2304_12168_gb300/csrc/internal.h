@@ -1,0 +1,152 @@
+// Internal declarations shared by the translation units of libtacta.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/tacta.h"
+
+namespace tacta {
+
+constexpr int kTMax = 8;            // largest CTA order supported
+constexpr int kBlock = 256;         // threads per block of every streaming kernel
+
+// ---------------------------------------------------------------- control block
+// One per plan, in device memory. Written only by single-thread "finisher"
+// code (the last block of a reducing kernel) or by one-thread kernels, read
+// by every kernel at entry. Kernel boundaries order all accesses.
+struct Ctl {
+    int32_t status;        // 0 while running, else a TACTA_REASON_* stop reason
+    int32_t k;             // completed iterations (of the current TA trip)
+    int32_t need_true;     // the next gated residual kernel must run
+    int32_t is_true;       // the carried residual equals b - A x
+    int32_t pivot;         // TA: this iteration takes a pivot step
+    int32_t rank;          // CTA: rank of the last auxiliary solve
+    int32_t max_iter;
+    int32_t R;             // true-residual period (0: never)
+    int32_t hist_cap;
+    int32_t hist_len;
+    int32_t grow_rho;      // TA: 1 = Alg. 2.2 (rho grows), 0 = Alg. 2.1 (witness stops)
+    uint32_t counter;      // last-block-done ticket
+    int32_t matvecs;       // products with A or Aᵀ made by the iteration (setup included)
+    int32_t pad_;
+    double bn2;            // ||b||²  (b = rhs of the operator in use)
+    double mtbn2;          // ||Mᵀ b||²
+    double tol2, tol_n2, pivot_tol;
+    double res_thr, nrm_thr;
+    double rn2;            // ||r||² (CTA) or ||d||² with d = b - b' (TA)
+    double db;             // TA: dᵀ b
+    double cn2;            // TA: ||c||²
+    double s;              // TA: rho / ||c||
+    double ta_alpha;       // TA: step
+    double rho;            // TA: radius
+    double phi[2 * kTMax + 2];
+    double alpha[kTMax];
+    double red[4];         // scratch results of setup reductions
+};
+
+// ---------------------------------------------------------------- reductions
+enum Finisher : int {
+    FIN_NONE = 0,
+    FIN_STORE = 1,        // red[0..1] -> ctl->red[idx], ctl->red[idx+1]
+    FIN_PHI = 2,          // r0 -> phi[idx]
+    FIN_CTA_STEP = 3,     // r0 -> phi[2t]; normal test; auxiliary solve -> alpha
+    FIN_CTA_UPDATE = 4,   // r0 = ||r||²: k++, history, R-gate, loop-top tests
+    FIN_TRUE_RES = 5,     // r0 = ||r||² (r1 = rᵀb): is_true, history, loop-top tests
+    FIN_TA_C = 6,         // r0 = ||c||²: normal test, pivot test, rho growth / witness
+    FIN_TA_V = 7,         // r0 = dᵀ(v - b'), r1 = ||v - b'||²: alpha
+    FIN_TA_UPDATE = 8,    // r0 = ||d||², r1 = dᵀb: k++, history, R-gate, loop-top tests
+    FIN_SETUP_B = 9,      // r0 = ||b||²
+    FIN_SETUP_MTB = 10,   // r0 = ||Mᵀb||²: thresholds
+    FIN_TRIP_START = 11,  // r0 = ||d||², r1 = dᵀb at the start of a TA trip: loop-top tests
+    FIN_SETUP_RHO = 12    // r0 = ||x0||²: rho = ||x0|| (TA warm start)
+};
+
+struct FinArgs {
+    int kind;
+    int idx;              // FIN_PHI / FIN_STORE slot, FIN_CTA_STEP: t
+    double* hist;         // device history buffer (capacity ctl->hist_cap)
+};
+
+// Epilogues of the matrix-vector kernels: y = A x, then per row
+enum Epilogue : int {
+    EPI_NONE = 0,      // y = A x
+    EPI_NORM = 1,      // y = A x;          red0 += y²
+    EPI_RESID = 2,     // y = b - A x;      red0 += y², red1 += y b
+    EPI_TAPIVOT = 3    // y = s (A x) = v;  w = v - b + d (= v - b'); red0 += d w, red1 += w²
+};
+
+struct EpiArgs {
+    const double* b;   // EPI_RESID / EPI_TAPIVOT: right-hand side
+    const double* d;   // EPI_TAPIVOT: d = b - b'
+};
+
+// Gate: which device flag must be set for the kernel to run (all kernels
+// also return immediately when ctl->status != 0).
+enum Gate : int { GATE_ALWAYS = 0, GATE_NEED_TRUE = 1, GATE_PIVOT = 2,
+                  GATE_FORCE = 3 /* runs even after a stop (exit diagnostics) */ };
+
+// ---------------------------------------------------------------- device matrix
+struct SpmvCfg {
+    int kind;      // 0 scalar (thread per row), 1 warp per row
+    int grid;      // blocks
+};
+
+struct DevCSR {          // CSR operand in device memory (rows x cols)
+    int64_t rows = 0, cols = 0, nnz = 0;
+    int32_t* rowptr = nullptr;
+    int32_t* colidx = nullptr;
+    double* vals = nullptr;
+    SpmvCfg cfg{};
+};
+
+struct DevDense {        // dense row-major operand in device memory
+    int64_t rows = 0, cols = 0;
+    double* vals = nullptr;
+    SpmvCfg cfg{};
+};
+
+struct DevOperand {      // A or Aᵀ
+    int format = TACTA_CSR;
+    DevCSR csr;
+    DevDense dense;
+    int64_t rows() const { return format == TACTA_CSR ? csr.rows : dense.rows; }
+    int64_t cols() const { return format == TACTA_CSR ? csr.cols : dense.cols; }
+    int64_t nnz() const { return format == TACTA_CSR ? csr.nnz : dense.rows * dense.cols; }
+};
+
+// ---------------------------------------------------------------- kernel launchers
+struct LaunchCtx {
+    cudaStream_t stream;
+    Ctl* ctl;
+    double* partials;     // >= 2 * max grid doubles
+    int max_grid;         // blocks of reducing kernels (fixed per plan)
+    int64_t* launches;    // counter of launched kernels
+};
+
+cudaError_t launch_spmv(const LaunchCtx& L, const DevOperand& A, const double* x, double* y,
+                        int epi, EpiArgs e, FinArgs f, int gate);
+cudaError_t launch_cta_update(const LaunchCtx& L, int t, int64_t m, int64_t n,
+                              double* x, double* r, double* const* z, double* const* u,
+                              FinArgs f);
+cudaError_t launch_ta_update(const LaunchCtx& L, int64_t m, int64_t n, double* x, double* d,
+                             const double* b, const double* v, const double* c, FinArgs f);
+cudaError_t launch_reduce_vec(const LaunchCtx& L, int64_t len, const double* a, const double* b,
+                              FinArgs f, int gate);
+cudaError_t launch_ctl_init(const LaunchCtx& L, const Ctl& host_init);
+cudaError_t launch_copy_gated(const LaunchCtx& L, double* dst, const double* src, int64_t len, int gate);
+cudaError_t launch_fill(const LaunchCtx& L, double* dst, double v, int64_t len);
+
+// plan-time helpers (transpose.cu)
+cudaError_t csr_validate(cudaStream_t s, const int32_t* rowptr, const int32_t* colidx, int64_t m,
+                         int64_t n, int64_t nnz, int* flag_dev, int* flag_host);
+cudaError_t csr_transpose(cudaStream_t s, const DevCSR& A, DevCSR& T);
+cudaError_t dense_transpose(cudaStream_t s, const double* A, int64_t rows, int64_t cols, double* T);
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+const char* get_error();
+
+}  // namespace tacta

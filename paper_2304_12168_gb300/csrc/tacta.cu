@@ -1,0 +1,897 @@
+// Host side of libtacta: plans, the CTA / TA / minimum-norm drivers and the C ABI.
+//
+// The drivers enqueue the per-iteration kernels of kernels.cu on the caller's
+// stream. All decisions of the algorithms (stop tests, pivot test, rho growth,
+// the auxiliary solve) are taken on the device by finisher code, so the host
+// never waits inside an iteration: it enqueues blocks of iterations (replayed
+// as a captured CUDA graph by default) and reads a 4-byte stop flag once per
+// block, one block behind, so the GPU always has queued work.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace tacta {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+const char* get_error() { return g_err.c_str(); }
+
+#define CUDA_TRY(expr)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));                  \
+            return e_ == cudaErrorMemoryAllocation ? TACTA_ERR_OOM : TACTA_ERR_CUDA;        \
+        }                                                                                   \
+    } while (0)
+
+// ------------------------------------------------------------------ kernels local to the driver
+__global__ void ctl_set_trip(Ctl* c, double rho, int max_iter) {
+    c->rho = rho;
+    c->max_iter = max_iter;
+    c->status = 0;
+    c->k = 0;
+    c->pivot = 0;
+    c->need_true = 0;
+    c->is_true = 1;
+    c->grow_rho = 0;
+    c->hist_cap = 0;
+}
+
+// ------------------------------------------------------------------ plan
+struct Plan {
+    int device = 0;
+    int on_device = 0;
+    int64_t m = 0, n = 0;
+    DevOperand A, At;
+    int sms = 0, grid = 0;
+    Ctl* ctl = nullptr;          // device control block
+    Ctl* stage = nullptr;        // pinned host staging / read-back of the control block
+    int32_t* poll = nullptr;     // pinned host, 2 polled status words
+    int* flag_dev = nullptr;
+    int* flag_host = nullptr;    // pinned
+    double* partials = nullptr;
+    double *b = nullptr, *x = nullptr, *r = nullptr, *tmp_m = nullptr, *tmp_n = nullptr;
+    double* z[kTMax] = {};
+    double* u[kTMax] = {};
+    double *d = nullptr, *c = nullptr, *v = nullptr, *bt = nullptr;
+    double *xbest = nullptr, *wx = nullptr, *wd = nullptr;
+    double* hist = nullptr;
+    int64_t hist_alloc = 0;
+    cudaStream_t cap = nullptr;  // private stream used only for graph capture
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    // cached graphs of one block of iterations
+    cudaGraphExec_t g_cta = nullptr;
+    int g_cta_key = -1;
+    int64_t g_cta_launches = 0;
+    int g_cta_iters = 0;
+    cudaGraphExec_t g_ta[2] = {nullptr, nullptr};
+    int64_t g_ta_launches[2] = {0, 0};
+    int g_ta_iters[2] = {0, 0};
+    // opt-in profiling of the iteration's products (events around each launch)
+    bool profiling = false;
+    std::vector<cudaEvent_t> pev;
+    size_t pev_used = 0;
+    double prof_bytes = 0.0;
+};
+
+// algorithmic bytes of one product: stored values and indices, row offsets,
+// the input vector read once and the output vector written once
+static double spmv_bytes(const DevOperand& A) {
+    const double R = (double)A.rows(), C = (double)A.cols();
+    if (A.format == TACTA_CSR) return 12.0 * (double)A.csr.nnz + 4.0 * (R + 1.0) + 8.0 * C + 8.0 * R;
+    return 8.0 * R * C + 8.0 * C + 8.0 * R;
+}
+
+// a product of the iteration chain; timed with a pair of events when profiling
+static cudaError_t chain_spmv(Plan* p, const LaunchCtx& L, const DevOperand& A, const double* x, double* y,
+                              int epi, EpiArgs e, FinArgs f, int gate) {
+    if (!p->profiling) return launch_spmv(L, A, x, y, epi, e, f, gate);
+    while (p->pev.size() < p->pev_used + 2) {
+        cudaEvent_t ev;
+        cudaError_t err = cudaEventCreate(&ev);
+        if (err != cudaSuccess) return err;
+        p->pev.push_back(ev);
+    }
+    cudaError_t err = cudaEventRecord(p->pev[p->pev_used], L.stream);
+    if (err != cudaSuccess) return err;
+    if ((err = launch_spmv(L, A, x, y, epi, e, f, gate)) != cudaSuccess) return err;
+    if ((err = cudaEventRecord(p->pev[p->pev_used + 1], L.stream)) != cudaSuccess) return err;
+    p->pev_used += 2;
+    p->prof_bytes += spmv_bytes(A);
+    return cudaSuccess;
+}
+
+static void prof_begin(Plan* p, int profile) {
+    p->profiling = profile != 0;
+    p->pev_used = 0;
+    p->prof_bytes = 0.0;
+}
+
+static void prof_end(Plan* p, tacta_info* info) {
+    if (!info) return;
+    if (!p->profiling) return;
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < p->pev_used; i += 2) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p->pev[i], p->pev[i + 1]) == cudaSuccess) ms += t;
+    }
+    info->spmv_count = (int32_t)(p->pev_used / 2);
+    info->spmv_ms = ms;
+    info->spmv_bytes = p->prof_bytes;
+    p->profiling = false;
+}
+
+static void free_graphs(Plan* p) {
+    if (p->g_cta) cudaGraphExecDestroy(p->g_cta);
+    p->g_cta = nullptr;
+    p->g_cta_key = -1;
+    for (int i = 0; i < 2; ++i) {
+        if (p->g_ta[i]) cudaGraphExecDestroy(p->g_ta[i]);
+        p->g_ta[i] = nullptr;
+    }
+}
+
+static void plan_free(Plan* p) {
+    if (!p) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    free_graphs(p);
+    auto F = [](void* q) { if (q) cudaFree(q); };
+    F(p->A.csr.rowptr); F(p->A.csr.colidx); F(p->A.csr.vals); F(p->A.dense.vals);
+    F(p->At.csr.rowptr); F(p->At.csr.colidx); F(p->At.csr.vals); F(p->At.dense.vals);
+    F(p->ctl); F(p->partials); F(p->flag_dev);
+    F(p->b); F(p->x); F(p->r); F(p->tmp_m); F(p->tmp_n);
+    for (int i = 0; i < kTMax; ++i) { F(p->z[i]); F(p->u[i]); }
+    F(p->d); F(p->c); F(p->v); F(p->bt); F(p->xbest); F(p->wx); F(p->wd); F(p->hist);
+    if (p->stage) cudaFreeHost(p->stage);
+    if (p->poll) cudaFreeHost(p->poll);
+    if (p->flag_host) cudaFreeHost(p->flag_host);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    for (int i = 0; i < 2; ++i) if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    for (cudaEvent_t e : p->pev) cudaEventDestroy(e);
+    cudaSetDevice(cur);
+    delete p;
+}
+
+static int choose_kind_csr(int64_t rows, int64_t nnz) {
+    // thread per row keeps every FP64 lane busy on short rows; long rows go warp per row
+    const double avg = rows > 0 ? (double)nnz / (double)rows : 0.0;
+    return avg >= 64.0 ? 1 : 0;
+}
+
+static tacta_status validate_opts(const tacta_options& o) {
+    if (!(std::isfinite(o.tol) && o.tol > 0.0)) { set_error("tol must be finite and > 0"); return TACTA_ERR_INVALID; }
+    if (!std::isfinite(o.tol_normal)) { set_error("tol_normal must be finite"); return TACTA_ERR_INVALID; }
+    if (o.t_max < 1 || o.t_max > kTMax) { set_error("t_max must be in 1..8"); return TACTA_ERR_INVALID; }
+    if (o.max_iter < 0) { set_error("max_iter must be >= 0"); return TACTA_ERR_INVALID; }
+    if (o.recompute_every < 0) { set_error("recompute_every must be >= 0"); return TACTA_ERR_INVALID; }
+    if (o.cycle < 0 || o.cycle > 2) { set_error("unknown cycle"); return TACTA_ERR_INVALID; }
+    return TACTA_OK;
+}
+
+static tacta_status plan_create(const tacta_matrix* M, const tacta_options* opt, Plan** out) {
+    *out = nullptr;
+    if (!M) { set_error("A is NULL"); return TACTA_ERR_INVALID; }
+    if (M->m < 1 || M->n < 1) { set_error("A must have m >= 1 and n >= 1"); return TACTA_ERR_INVALID; }
+    if (M->m >= (1LL << 31) || M->n >= (1LL << 31)) { set_error("m and n must be < 2^31"); return TACTA_ERR_INVALID; }
+    if (M->format != TACTA_DENSE && M->format != TACTA_CSR) { set_error("unknown format"); return TACTA_ERR_INVALID; }
+    if (!M->vals && (M->format == TACTA_DENSE || M->nnz > 0)) { set_error("A.vals is NULL"); return TACTA_ERR_INVALID; }
+    if (M->format == TACTA_DENSE && M->m * M->n > (1LL << 40)) { set_error("dense A too large"); return TACTA_ERR_INVALID; }
+    if (M->format == TACTA_CSR) {
+        if (!M->rowptr || (M->nnz > 0 && !M->colidx)) { set_error("CSR arrays missing"); return TACTA_ERR_INVALID; }
+        if (M->nnz < 0 || M->nnz >= (1LL << 31)) { set_error("nnz must be in [0, 2^31)"); return TACTA_ERR_INVALID; }
+    }
+    Plan* p = new Plan();
+    p->on_device = M->on_device ? 1 : 0;
+    p->m = M->m;
+    p->n = M->n;
+    cudaStream_t s = opt && opt->stream ? (cudaStream_t)opt->stream : (cudaStream_t)0;
+    auto fail = [&](tacta_status st) { plan_free(p); return st; };
+#define PTRY(expr)                                                                        \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));                \
+            return fail(e_ == cudaErrorMemoryAllocation ? TACTA_ERR_OOM : TACTA_ERR_CUDA); \
+        }                                                                                 \
+    } while (0)
+    PTRY(cudaGetDevice(&p->device));
+    PTRY(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device));
+    p->grid = p->sms * 8;
+    PTRY(cudaMallocHost(&p->flag_host, sizeof(int)));
+    PTRY(cudaMalloc(&p->flag_dev, sizeof(int)));
+    const int64_t m = p->m, n = p->n;
+    if (M->format == TACTA_CSR) {
+        const int64_t nnz = M->nnz;
+        DevCSR& a = p->A.csr;
+        p->A.format = p->At.format = TACTA_CSR;
+        a.rows = m; a.cols = n; a.nnz = nnz;
+        PTRY(cudaMalloc(&a.rowptr, sizeof(int32_t) * (m + 1)));
+        PTRY(cudaMalloc(&a.colidx, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+        PTRY(cudaMalloc(&a.vals, sizeof(double) * std::max<int64_t>(nnz, 1)));
+        PTRY(cudaMemcpyAsync(a.rowptr, M->rowptr, sizeof(int32_t) * (m + 1), cudaMemcpyDefault, s));
+        if (nnz > 0) {
+            PTRY(cudaMemcpyAsync(a.colidx, M->colidx, sizeof(int32_t) * nnz, cudaMemcpyDefault, s));
+            PTRY(cudaMemcpyAsync(a.vals, M->vals, sizeof(double) * nnz, cudaMemcpyDefault, s));
+        }
+        PTRY(csr_validate(s, a.rowptr, a.colidx, m, n, nnz, p->flag_dev, p->flag_host));
+        if (*p->flag_host) {
+            const int f = *p->flag_host;
+            std::string msg = "invalid CSR structure:";
+            if (f & 1) msg += " rowptr[0] != 0;";
+            if (f & 2) msg += " rowptr decreases;";
+            if (f & 4) msg += " rowptr[m] != nnz;";
+            if (f & 8) msg += " column index out of range;";
+            set_error(msg);
+            return fail(TACTA_ERR_INVALID);
+        }
+        PTRY(csr_transpose(s, a, p->At.csr));
+        a.cfg.kind = choose_kind_csr(m, nnz);
+        p->At.csr.cfg.kind = choose_kind_csr(n, nnz);
+    } else {
+        p->A.format = p->At.format = TACTA_DENSE;
+        DevDense& a = p->A.dense;
+        DevDense& t = p->At.dense;
+        a.rows = m; a.cols = n; t.rows = n; t.cols = m;
+        PTRY(cudaMalloc(&a.vals, sizeof(double) * m * n));
+        PTRY(cudaMalloc(&t.vals, sizeof(double) * m * n));
+        PTRY(cudaMemcpyAsync(a.vals, M->vals, sizeof(double) * m * n, cudaMemcpyDefault, s));
+        PTRY(dense_transpose(s, a.vals, m, n, t.vals));
+        a.cfg.kind = n >= 64 ? 1 : 0;
+        t.cfg.kind = m >= 64 ? 1 : 0;
+    }
+    const int64_t mn = std::max(m, n);
+    PTRY(cudaMalloc(&p->ctl, sizeof(Ctl)));
+    PTRY(cudaMemsetAsync(p->ctl, 0, sizeof(Ctl), s));
+    PTRY(cudaMallocHost(&p->stage, sizeof(Ctl)));
+    PTRY(cudaMallocHost(&p->poll, 2 * sizeof(int32_t)));
+    PTRY(cudaMalloc(&p->partials, sizeof(double) * 2 * p->grid));
+    PTRY(cudaMalloc(&p->b, sizeof(double) * m));
+    PTRY(cudaMalloc(&p->x, sizeof(double) * n));
+    PTRY(cudaMalloc(&p->r, sizeof(double) * m));
+    PTRY(cudaMalloc(&p->tmp_m, sizeof(double) * m));
+    PTRY(cudaMalloc(&p->tmp_n, sizeof(double) * n));
+    PTRY(cudaMalloc(&p->d, sizeof(double) * mn));
+    PTRY(cudaMalloc(&p->c, sizeof(double) * n));
+    PTRY(cudaMalloc(&p->v, sizeof(double) * mn));
+    PTRY(cudaMalloc(&p->bt, sizeof(double) * n));
+    PTRY(cudaMalloc(&p->xbest, sizeof(double) * n));
+    PTRY(cudaMalloc(&p->wx, sizeof(double) * n));
+    PTRY(cudaMalloc(&p->wd, sizeof(double) * mn));
+    PTRY(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) PTRY(cudaEventCreateWithFlags(&p->ev[i], cudaEventDisableTiming));
+    PTRY(cudaStreamSynchronize(s));
+#undef PTRY
+    *out = p;
+    return TACTA_OK;
+}
+
+static tacta_status ensure_chain(Plan* p, int t_max) {
+    for (int i = 0; i < t_max; ++i) {
+        if (!p->z[i]) {
+            free_graphs(p);
+            CUDA_TRY(cudaMalloc(&p->z[i], sizeof(double) * p->n));
+            CUDA_TRY(cudaMalloc(&p->u[i], sizeof(double) * p->m));
+        }
+    }
+    return TACTA_OK;
+}
+
+static tacta_status ensure_hist(Plan* p, int64_t cap) {
+    if (cap <= p->hist_alloc) return TACTA_OK;
+    free_graphs(p);  // graphs hold the history pointer
+    if (p->hist) cudaFree(p->hist);
+    p->hist = nullptr;
+    p->hist_alloc = 0;
+    CUDA_TRY(cudaMalloc(&p->hist, sizeof(double) * cap));
+    p->hist_alloc = cap;
+    return TACTA_OK;
+}
+
+// ------------------------------------------------------------------ options
+
+struct Opts {
+    tacta_options o;
+    cudaStream_t s;
+};
+
+static Opts resolve(const tacta_options* opt) {
+    Opts r;
+    tacta_default_options(&r.o);
+    if (opt) r.o = *opt;
+    if (r.o.tol_normal < 0.0) r.o.tol_normal = r.o.tol;
+    if (!(r.o.tol_cta > 0.0)) r.o.tol_cta = r.o.tol;
+    if (!(r.o.pivot_tol > 0.0)) r.o.pivot_tol = 1e-12;
+    if (r.o.poll_every < 1) r.o.poll_every = 64;
+    r.s = (cudaStream_t)r.o.stream;
+    return r;
+}
+
+static int schedule(int64_t k, int t_max, int cycle) {
+    if (cycle == TACTA_CYCLE_FIXED || t_max == 1) return t_max;
+    if (cycle == TACTA_CYCLE_SAWTOOTH) return 1 + (int)(k % t_max);
+    const int period = 2 * t_max - 2;
+    const int j = (int)(k % period);
+    return j < t_max ? j + 1 : 2 * t_max - 1 - j;
+}
+
+static int schedule_period(int t_max, int cycle) {
+    if (cycle == TACTA_CYCLE_FIXED || t_max == 1) return 1;
+    if (cycle == TACTA_CYCLE_SAWTOOTH) return t_max;
+    return 2 * t_max - 2;
+}
+
+// ------------------------------------------------------------------ iteration bodies
+
+static cudaError_t enqueue_cta_iter(Plan* p, const LaunchCtx& L, int t) {
+    cudaError_t e;
+    const double* uprev = p->r;
+    EpiArgs none{nullptr, nullptr};
+    for (int i = 0; i < t; ++i) {
+        if ((e = chain_spmv(p, L, p->At, uprev, p->z[i], EPI_NORM, none, FinArgs{FIN_PHI, 2 * i + 1, nullptr},
+                            GATE_ALWAYS)) != cudaSuccess) return e;
+        FinArgs f = (i == t - 1) ? FinArgs{FIN_CTA_STEP, t, nullptr} : FinArgs{FIN_PHI, 2 * i + 2, nullptr};
+        if ((e = chain_spmv(p, L, p->A, p->z[i], p->u[i], EPI_NORM, none, f, GATE_ALWAYS)) != cudaSuccess) return e;
+        uprev = p->u[i];
+    }
+    if ((e = launch_cta_update(L, t, p->m, p->n, p->x, p->r, p->z, p->u,
+                               FinArgs{FIN_CTA_UPDATE, 0, p->hist})) != cudaSuccess) return e;
+    return launch_spmv(L, p->A, p->x, p->r, EPI_RESID, EpiArgs{p->b, nullptr},
+                       FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE);
+}
+
+// operator of TA: M = A (normal = 0) or M = AᵀA (normal = 1), rhs = b or Aᵀb
+static cudaError_t apply_M(Plan* p, const LaunchCtx& L, int normal, const double* in, double* out,
+                           int epi, EpiArgs e, FinArgs f, int gate) {
+    if (!normal) return launch_spmv(L, p->A, in, out, epi, e, f, gate);
+    cudaError_t err = launch_spmv(L, p->A, in, p->tmp_m, EPI_NONE, EpiArgs{nullptr, nullptr},
+                                  FinArgs{FIN_NONE, 0, nullptr}, gate);
+    if (err != cudaSuccess) return err;
+    return launch_spmv(L, p->At, p->tmp_m, out, epi, e, f, gate);
+}
+static cudaError_t apply_Mt(Plan* p, const LaunchCtx& L, int normal, const double* in, double* out,
+                            int epi, EpiArgs e, FinArgs f, int gate) {
+    if (!normal) return launch_spmv(L, p->At, in, out, epi, e, f, gate);
+    return apply_M(p, L, 1, in, out, epi, e, f, gate);   // AᵀA is symmetric
+}
+
+static cudaError_t enqueue_ta_iter(Plan* p, const LaunchCtx& L, int normal, double* hist) {
+    cudaError_t e;
+    const double* rhs = normal ? p->bt : p->b;
+    const int64_t mm = normal ? p->n : p->m;
+    EpiArgs none{nullptr, nullptr};
+    // c = Mᵀ (b - b'), ||c||², pivot test (Eq. eqlem2) / rho growth
+    if (!normal) {
+        if ((e = chain_spmv(p, L, p->At, p->d, p->c, EPI_NORM, none, FinArgs{FIN_TA_C, 0, nullptr},
+                            GATE_ALWAYS)) != cudaSuccess) return e;
+    } else if ((e = apply_Mt(p, L, normal, p->d, p->c, EPI_NORM, none, FinArgs{FIN_TA_C, 0, nullptr},
+                             GATE_ALWAYS)) != cudaSuccess) return e;
+    // v = rho M c / ||c|| (Eq. vr) with the dots of Eq. alph
+    if ((e = apply_M(p, L, normal, p->c, p->v, EPI_TAPIVOT, EpiArgs{rhs, p->d},
+                     FinArgs{FIN_TA_V, 0, nullptr}, GATE_PIVOT)) != cudaSuccess) return e;
+    if ((e = launch_ta_update(L, mm, p->n, p->x, p->d, rhs, p->v, p->c,
+                              FinArgs{FIN_TA_UPDATE, 0, hist})) != cudaSuccess) return e;
+    return apply_M(p, L, normal, p->x, p->d, EPI_RESID, EpiArgs{rhs, nullptr},
+                   FinArgs{FIN_TRUE_RES, 0, hist}, GATE_NEED_TRUE);
+}
+
+// ------------------------------------------------------------------ iteration loop with polling
+
+struct LoopResult { int64_t launches = 0; };
+
+// Runs iterations until the device stop flag is set or max_iter iterations were enqueued.
+// body(L, k) enqueues iteration k; graph holds a captured block of `gper` iterations (optional).
+template <class Body>
+static tacta_status run_loop(Plan* p, const Opts& O, int64_t max_iter, int period, bool use_graph,
+                             cudaGraphExec_t* graph, int64_t* graph_launches, int* graph_iters,
+                             Body body, int64_t* launches) {
+    LaunchCtx L{O.s, p->ctl, p->partials, p->grid, launches};
+    if (max_iter <= 0) return TACTA_OK;
+    const int64_t poll = std::max<int64_t>(O.o.poll_every, 1);
+    if (use_graph && *graph == nullptr) {
+        // capture ceil(poll / period) periods of iterations on the private stream
+        const int reps = (int)std::max<int64_t>(1, (poll + period - 1) / period);
+        const int iters = reps * period;
+        int64_t cnt = 0;
+        LaunchCtx C{p->cap, p->ctl, p->partials, p->grid, &cnt};
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < iters && e == cudaSuccess; ++k) e = body(C, (int64_t)k);
+        cudaError_t e2 = cudaStreamEndCapture(p->cap, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            set_error(std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+            return TACTA_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            *graph = nullptr;
+            set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
+            return TACTA_ERR_CUDA;
+        }
+        *graph_launches = cnt;
+        *graph_iters = iters;
+    }
+    int64_t k = 0;
+    int chunk = 0;
+    bool stopped = false;
+    while (k < max_iter && !stopped) {
+        if (use_graph) {
+            CUDA_TRY(cudaGraphLaunch(*graph, O.s));
+            *launches += *graph_launches;
+            k += *graph_iters;
+        } else {
+            const int64_t todo = std::min<int64_t>(poll, max_iter - k);
+            for (int64_t j = 0; j < todo; ++j) CUDA_TRY(body(L, k + j));
+            k += todo;
+        }
+        const int slot = chunk & 1;
+        CUDA_TRY(cudaMemcpyAsync(&p->poll[slot], &p->ctl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, O.s));
+        CUDA_TRY(cudaEventRecord(p->ev[slot], O.s));
+        if (chunk > 0) {
+            CUDA_TRY(cudaEventSynchronize(p->ev[slot ^ 1]));
+            if (p->poll[slot ^ 1] != 0) stopped = true;
+        }
+        ++chunk;
+    }
+    return TACTA_OK;
+}
+
+// ------------------------------------------------------------------ shared bits
+
+static tacta_status read_ctl(Plan* p, cudaStream_t s) {
+    CUDA_TRY(cudaMemcpyAsync(p->stage, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return TACTA_OK;
+}
+
+static tacta_status write_ctl(Plan* p, cudaStream_t s, const Ctl& h) {
+    // the staging buffer is reused: wait for earlier users of the stream first
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *p->stage = h;
+    CUDA_TRY(cudaMemcpyAsync(p->ctl, p->stage, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    return TACTA_OK;
+}
+
+static tacta_status status_of(int reason) {
+    switch (reason) {
+    case TACTA_REASON_RESIDUAL:
+    case TACTA_REASON_NORMAL:
+    case TACTA_REASON_GAP:
+    case TACTA_REASON_ZERO_RHS: return TACTA_OK;
+    case TACTA_REASON_MAXITER: return TACTA_MAXITER;
+    case TACTA_REASON_BREAKDOWN: return TACTA_BREAKDOWN;
+    case TACTA_REASON_WITNESS: return TACTA_WITNESS;
+    case TACTA_REASON_NONFINITE: return TACTA_ERR_NONFINITE;
+    default: return TACTA_MAXITER;
+    }
+}
+
+// true ||b - A x||² and ||Aᵀ(b - A x)||² at exit, into ctl->red[0], ctl->red[2]
+static tacta_status exit_residuals(Plan* p, const Opts& O, const double* x, int64_t* launches) {
+    LaunchCtx L{O.s, p->ctl, p->partials, p->grid, launches};
+    CUDA_TRY(launch_spmv(L, p->A, x, p->tmp_m, EPI_RESID, EpiArgs{p->b, nullptr},
+                         FinArgs{FIN_STORE, 0, nullptr}, GATE_FORCE));
+    CUDA_TRY(launch_spmv(L, p->At, p->tmp_m, p->tmp_n, EPI_NORM, EpiArgs{nullptr, nullptr},
+                         FinArgs{FIN_STORE, 2, nullptr}, GATE_FORCE));
+    return TACTA_OK;
+}
+
+static Ctl base_ctl(const Opts& O, int64_t hist_cap) {
+    Ctl h;
+    std::memset(&h, 0, sizeof(h));
+    h.max_iter = O.o.max_iter;
+    h.R = O.o.recompute_every;
+    h.hist_cap = (int32_t)hist_cap;
+    h.tol2 = O.o.tol * O.o.tol;
+    h.tol_n2 = O.o.tol_normal * O.o.tol_normal;
+    h.pivot_tol = O.o.pivot_tol;
+    return h;
+}
+
+struct VecIO {   // caller vectors
+    const double* b;
+    const double* x0;
+    double* x_out;
+    double* hist;
+    int32_t hist_cap;
+};
+
+static tacta_status load_b(Plan* p, const Opts& O, const VecIO& io) {
+    if (!io.b) { set_error("b is NULL"); return TACTA_ERR_INVALID; }
+    if (!io.x_out) { set_error("x_out is NULL"); return TACTA_ERR_INVALID; }
+    CUDA_TRY(cudaMemcpyAsync(p->b, io.b, sizeof(double) * p->m, cudaMemcpyDefault, O.s));
+    return TACTA_OK;
+}
+
+static tacta_status store_out(Plan* p, const Opts& O, const VecIO& io, const double* x, int hist_len) {
+    CUDA_TRY(cudaMemcpyAsync(io.x_out, x, sizeof(double) * p->n, cudaMemcpyDefault, O.s));
+    if (io.hist && io.hist_cap > 0 && hist_len > 0) {
+        const int64_t h = std::min<int64_t>(hist_len, io.hist_cap);
+        CUDA_TRY(cudaMemcpyAsync(io.hist, p->hist, sizeof(double) * h, cudaMemcpyDefault, O.s));
+    }
+    CUDA_TRY(cudaStreamSynchronize(O.s));
+    return TACTA_OK;
+}
+
+// ------------------------------------------------------------------ CTA (Alg. 1.1)
+
+// Runs CTA from x0 (or 0) on the plan's b; leaves x in p->x and the final control block in p->stage.
+static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t hist_cap, int64_t* launches) {
+    tacta_status st;
+    if ((st = ensure_chain(p, O.o.t_max)) != TACTA_OK) return st;
+    if ((st = ensure_hist(p, std::max<int64_t>(hist_cap, 1))) != TACTA_OK) return st;
+    LaunchCtx L{O.s, p->ctl, p->partials, p->grid, launches};
+    Ctl h = base_ctl(O, hist_cap);
+    h.need_true = x0 ? 1 : 0;
+    if ((st = write_ctl(p, O.s, h)) != TACTA_OK) return st;
+    EpiArgs none{nullptr, nullptr};
+    CUDA_TRY(launch_reduce_vec(L, p->m, p->b, nullptr, FinArgs{FIN_SETUP_B, 0, nullptr}, GATE_ALWAYS));
+    CUDA_TRY(launch_spmv(L, p->At, p->b, p->tmp_n, EPI_NORM, none, FinArgs{FIN_SETUP_MTB, 0, nullptr}, GATE_ALWAYS));
+    if (x0) {
+        CUDA_TRY(cudaMemcpyAsync(p->x, x0, sizeof(double) * p->n, cudaMemcpyDefault, O.s));
+        CUDA_TRY(launch_spmv(L, p->A, p->x, p->r, EPI_RESID, EpiArgs{p->b, nullptr},
+                             FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE));
+    } else {
+        CUDA_TRY(cudaMemsetAsync(p->x, 0, sizeof(double) * p->n, O.s));
+        CUDA_TRY(cudaMemcpyAsync(p->r, p->b, sizeof(double) * p->m, cudaMemcpyDeviceToDevice, O.s));
+        CUDA_TRY(launch_reduce_vec(L, p->m, p->r, nullptr, FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_ALWAYS));
+    }
+    const int t_max = O.o.t_max, cycle = O.o.cycle;
+    const int period = schedule_period(t_max, cycle);
+    const int key = t_max * 4 + cycle;
+    if (p->g_cta && p->g_cta_key != key) {
+        cudaGraphExecDestroy(p->g_cta);
+        p->g_cta = nullptr;
+    }
+    p->g_cta_key = key;
+    auto body = [&](const LaunchCtx& LL, int64_t k) {
+        return enqueue_cta_iter(p, LL, schedule(k, t_max, cycle));
+    };
+    st = run_loop(p, O, O.o.max_iter, period, O.o.use_graph != 0, &p->g_cta, &p->g_cta_launches,
+                  &p->g_cta_iters, body, launches);
+    if (st != TACTA_OK) return st;
+    CUDA_TRY(cudaGetLastError());
+    return TACTA_OK;
+}
+
+static void fill_info(tacta_info* info, const Ctl& c, tacta_status st, int64_t launches) {
+    if (!info) return;
+    std::memset(info, 0, sizeof(*info));
+    info->status = st;
+    info->reason = c.status;
+    info->iters = c.k;
+    info->matvecs = c.matvecs;
+    info->rel_res = c.bn2 > 0 ? std::sqrt(c.red[0] / c.bn2) : 0.0;
+    info->rel_normal_res = c.mtbn2 > 0 ? std::sqrt(c.red[2] / c.mtbn2) : 0.0;
+    info->rho = c.rho;
+    info->hist_len = c.hist_len;
+    info->launches = launches;
+}
+
+static tacta_status plan_cta(Plan* p, const VecIO& io, const tacta_options* opt, tacta_info* info) {
+    Opts O = resolve(opt);
+    tacta_status st;
+    if ((st = validate_opts(O.o)) != TACTA_OK) return st;
+    CUDA_TRY(cudaSetDevice(p->device));
+    if ((st = load_b(p, O, io)) != TACTA_OK) return st;
+    int64_t launches = 0;
+    const int64_t hist_cap = io.hist && io.hist_cap > 0 ? std::min<int64_t>(io.hist_cap, (int64_t)O.o.max_iter + 1) : 0;
+    if (O.o.profile) O.o.use_graph = 0;
+    prof_begin(p, O.o.profile);
+    if ((st = cta_core(p, O, io.x0, hist_cap, &launches)) != TACTA_OK) { p->profiling = false; return st; }
+    if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
+    if (p->stage->status == TACTA_REASON_ZERO_RHS) CUDA_TRY(cudaMemsetAsync(p->x, 0, sizeof(double) * p->n, O.s));
+    if ((st = exit_residuals(p, O, p->x, &launches)) != TACTA_OK) return st;
+    if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
+    Ctl c = *p->stage;
+    if ((st = store_out(p, O, io, p->x, c.hist_len)) != TACTA_OK) return st;
+    const tacta_status out = status_of(c.status);
+    if (out == TACTA_ERR_NONFINITE) set_error("non-finite value in a reduction");
+    fill_info(info, c, out, launches);
+    prof_end(p, info);
+    p->profiling = false;
+    if (info && c.status == TACTA_REASON_ZERO_RHS) { info->rel_res = 0.0; info->rel_normal_res = 0.0; }
+    return out;
+}
+
+// ------------------------------------------------------------------ TA (Alg. 2.2 / 2.1)
+
+// Starts TA on M (normal: AᵀA with rhs Aᵀb) from (x, d) already in p->x / p->d.
+static tacta_status ta_setup(Plan* p, const Opts& O, int normal, const double* x0, int64_t hist_cap,
+                             int64_t* launches) {
+    LaunchCtx L{O.s, p->ctl, p->partials, p->grid, launches};
+    const double* rhs = normal ? p->bt : p->b;
+    const int64_t mm = normal ? p->n : p->m;
+    EpiArgs none{nullptr, nullptr};
+    CUDA_TRY(launch_reduce_vec(L, mm, rhs, nullptr, FinArgs{FIN_SETUP_B, 0, nullptr}, GATE_ALWAYS));
+    CUDA_TRY(apply_Mt(p, L, normal, rhs, p->tmp_n, EPI_NORM, none, FinArgs{FIN_SETUP_MTB, 0, nullptr}, GATE_ALWAYS));
+    if (x0) {
+        CUDA_TRY(cudaMemcpyAsync(p->x, x0, sizeof(double) * p->n, cudaMemcpyDefault, O.s));
+        CUDA_TRY(launch_reduce_vec(L, p->n, p->x, nullptr, FinArgs{FIN_SETUP_RHO, 0, nullptr}, GATE_ALWAYS));
+        CUDA_TRY(apply_M(p, L, normal, p->x, p->d, EPI_RESID, EpiArgs{rhs, nullptr},
+                         FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE));
+    } else {
+        CUDA_TRY(cudaMemsetAsync(p->x, 0, sizeof(double) * p->n, O.s));
+        CUDA_TRY(cudaMemcpyAsync(p->d, rhs, sizeof(double) * mm, cudaMemcpyDeviceToDevice, O.s));
+        CUDA_TRY(launch_reduce_vec(L, mm, p->d, rhs, FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_ALWAYS));
+    }
+    (void)hist_cap;
+    return TACTA_OK;
+}
+
+// TA iterations; the history pointer is always the plan's buffer (trips of Alg. 2.5 run with
+// hist_cap = 0 in the control block, so they write no history and share the cached graph).
+static tacta_status ta_iterate(Plan* p, const Opts& O, int normal, int64_t max_iter, int64_t* launches) {
+    auto body = [&](const LaunchCtx& LL, int64_t) { return enqueue_ta_iter(p, LL, normal, p->hist); };
+    return run_loop(p, O, max_iter, 1, O.o.use_graph != 0, &p->g_ta[normal], &p->g_ta_launches[normal],
+                    &p->g_ta_iters[normal], body, launches);
+}
+
+static tacta_status plan_ta(Plan* p, const VecIO& io, const tacta_options* opt, tacta_info* info) {
+    Opts O = resolve(opt);
+    tacta_status st;
+    if ((st = validate_opts(O.o)) != TACTA_OK) return st;
+    CUDA_TRY(cudaSetDevice(p->device));
+    if ((st = load_b(p, O, io)) != TACTA_OK) return st;
+    int64_t launches = 0;
+    const int64_t hist_cap = io.hist && io.hist_cap > 0 ? std::min<int64_t>(io.hist_cap, (int64_t)O.o.max_iter + 1) : 0;
+    if ((st = ensure_hist(p, std::max<int64_t>(hist_cap, 1))) != TACTA_OK) return st;
+    Ctl h = base_ctl(O, hist_cap);
+    h.grow_rho = 1;
+    h.need_true = io.x0 ? 1 : 0;
+    if ((st = write_ctl(p, O.s, h)) != TACTA_OK) return st;
+    if ((st = ta_setup(p, O, 0, io.x0, hist_cap, &launches)) != TACTA_OK) return st;
+    if (O.o.profile) O.o.use_graph = 0;
+    prof_begin(p, O.o.profile);
+    if ((st = ta_iterate(p, O, 0, O.o.max_iter, &launches)) != TACTA_OK) { p->profiling = false; return st; }
+    if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
+    if (p->stage->status == TACTA_REASON_ZERO_RHS) CUDA_TRY(cudaMemsetAsync(p->x, 0, sizeof(double) * p->n, O.s));
+    if ((st = exit_residuals(p, O, p->x, &launches)) != TACTA_OK) return st;
+    if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
+    Ctl c = *p->stage;
+    if ((st = store_out(p, O, io, p->x, c.hist_len)) != TACTA_OK) return st;
+    const tacta_status out = status_of(c.status);
+    if (out == TACTA_ERR_NONFINITE) set_error("non-finite value in a reduction");
+    fill_info(info, c, out, launches);
+    prof_end(p, info);
+    p->profiling = false;
+    if (info && c.status == TACTA_REASON_ZERO_RHS) { info->rel_res = 0.0; info->rel_normal_res = 0.0; }
+    return out;
+}
+
+// ------------------------------------------------------------------ hybrid minimum norm (Sec. 5.2, Alg. 2.5)
+
+static tacta_status plan_minnorm(Plan* p, const VecIO& io, const tacta_options* opt, tacta_info* info) {
+    Opts O = resolve(opt);
+    tacta_status st;
+    if ((st = validate_opts(O.o)) != TACTA_OK) return st;
+    CUDA_TRY(cudaSetDevice(p->device));
+    if ((st = load_b(p, O, io)) != TACTA_OK) return st;
+    int64_t launches = 0;
+    LaunchCtx L{O.s, p->ctl, p->partials, p->grid, &launches};
+    // phase 1: CTA to tol_cta from x = 0
+    Opts Oc = O;
+    Oc.o.tol = O.o.tol_cta;
+    const int64_t hist_cap = io.hist && io.hist_cap > 0 ? std::min<int64_t>(io.hist_cap, (int64_t)O.o.max_iter + 1) : 0;
+    if ((st = cta_core(p, Oc, nullptr, hist_cap, &launches)) != TACTA_OK) return st;
+    if ((st = exit_residuals(p, O, p->x, &launches)) != TACTA_OK) return st;
+    if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
+    const Ctl c1 = *p->stage;
+    tacta_info out_info;
+    std::memset(&out_info, 0, sizeof(out_info));
+    out_info.cta_iters = c1.k;
+    out_info.hist_len = c1.hist_len;
+    const double bn2_orig = c1.bn2, atbn2_orig = c1.mtbn2;
+    if (c1.status == TACTA_REASON_ZERO_RHS) {
+        CUDA_TRY(cudaMemsetAsync(p->x, 0, sizeof(double) * p->n, O.s));
+        if ((st = store_out(p, O, io, p->x, c1.hist_len)) != TACTA_OK) return st;
+        out_info.status = TACTA_OK;
+        out_info.reason = TACTA_REASON_ZERO_RHS;
+        out_info.launches = launches;
+        if (info) *info = out_info;
+        return TACTA_OK;
+    }
+    if (status_of(c1.status) != TACTA_OK) {   // CTA did not reach tol_cta
+        if ((st = store_out(p, O, io, p->x, c1.hist_len)) != TACTA_OK) return st;
+        const tacta_status s1 = status_of(c1.status);
+        fill_info(info, c1, s1, launches);
+        if (info) { info->cta_iters = c1.k; info->iters = 0; info->rho = 0.0; info->matvecs = 0; }
+        return s1;
+    }
+    const double rel_res = std::sqrt(c1.red[0] / c1.bn2);
+    const int normal = rel_res <= O.o.tol_cta ? 0 : 1;
+    // phase 2: Algorithm 2.5 on (A, b) or (AᵀA, Aᵀb)
+    EpiArgs none{nullptr, nullptr};
+    if (normal)
+        CUDA_TRY(launch_spmv(L, p->At, p->b, p->bt, EPI_NONE, none, FinArgs{FIN_NONE, 0, nullptr}, GATE_FORCE));
+    CUDA_TRY(cudaMemcpyAsync(p->xbest, p->x, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
+    Ctl h = base_ctl(O, 0);
+    if ((st = write_ctl(p, O.s, h)) != TACTA_OK) return st;
+    CUDA_TRY(launch_reduce_vec(L, p->n, p->x, nullptr, FinArgs{FIN_STORE, 0, nullptr}, GATE_ALWAYS));
+    if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
+    double rho_hi = std::sqrt(p->stage->red[0]);
+    double rho_lo = 0.0;
+    const double gap = O.o.tol * rho_hi;
+    // thresholds of the operator in use (||rhs||², ||Mᵀ rhs||²)
+    const double* rhs = normal ? p->bt : p->b;
+    const int64_t mm = normal ? p->n : p->m;
+    CUDA_TRY(launch_reduce_vec(L, mm, rhs, nullptr, FinArgs{FIN_SETUP_B, 0, nullptr}, GATE_ALWAYS));
+    CUDA_TRY(apply_Mt(p, L, normal, rhs, p->tmp_n, EPI_NORM, none, FinArgs{FIN_SETUP_MTB, 0, nullptr}, GATE_ALWAYS));
+    bool have_witness = false;
+    int64_t used = 0;
+    int trips = 0;
+    int final_reason = TACTA_REASON_GAP;
+    while (rho_hi - rho_lo > gap) {
+        if (used >= O.o.max_iter) { final_reason = TACTA_REASON_MAXITER; break; }
+        const double rho = 0.5 * (rho_hi + rho_lo);
+        ctl_set_trip<<<1, 1, 0, O.s>>>(p->ctl, rho, (int)(O.o.max_iter - used));
+        ++launches;
+        CUDA_TRY(cudaGetLastError());
+        if (have_witness) {
+            CUDA_TRY(cudaMemcpyAsync(p->x, p->wx, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
+            CUDA_TRY(cudaMemcpyAsync(p->d, p->wd, sizeof(double) * mm, cudaMemcpyDeviceToDevice, O.s));
+        } else {
+            CUDA_TRY(cudaMemsetAsync(p->x, 0, sizeof(double) * p->n, O.s));
+            CUDA_TRY(cudaMemcpyAsync(p->d, rhs, sizeof(double) * mm, cudaMemcpyDeviceToDevice, O.s));
+        }
+        CUDA_TRY(launch_reduce_vec(L, mm, p->d, rhs, FinArgs{FIN_TRIP_START, 0, nullptr}, GATE_FORCE));
+        if ((st = ta_iterate(p, O, normal, O.o.max_iter - used, &launches)) != TACTA_OK) return st;
+        if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
+        const Ctl c = *p->stage;
+        used += c.k;
+        ++trips;
+        if (c.status == TACTA_REASON_RESIDUAL) {
+            rho_hi = rho;
+            CUDA_TRY(cudaMemcpyAsync(p->xbest, p->x, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
+        } else if (c.status == TACTA_REASON_WITNESS) {
+            rho_lo = c.db / std::sqrt(c.cn2);
+            have_witness = true;
+            CUDA_TRY(cudaMemcpyAsync(p->wx, p->x, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
+            CUDA_TRY(cudaMemcpyAsync(p->wd, p->d, sizeof(double) * mm, cudaMemcpyDeviceToDevice, O.s));
+        } else if (c.status == TACTA_REASON_NORMAL) {
+            CUDA_TRY(cudaMemcpyAsync(p->xbest, p->x, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
+            final_reason = TACTA_REASON_NORMAL;
+            break;
+        } else {
+            final_reason = c.status;
+            break;
+        }
+    }
+    // residuals of the original system at x_best
+    if ((st = exit_residuals(p, O, p->xbest, &launches)) != TACTA_OK) return st;
+    if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
+    const Ctl c = *p->stage;
+    if ((st = store_out(p, O, io, p->xbest, 0)) != TACTA_OK) return st;
+    if (io.hist && io.hist_cap > 0 && c1.hist_len > 0) {
+        // the CTA phase history was overwritten only if hist was reused: it was not (trips pass NULL)
+        CUDA_TRY(cudaMemcpyAsync(io.hist, p->hist, sizeof(double) * std::min<int64_t>(c1.hist_len, io.hist_cap),
+                                 cudaMemcpyDefault, O.s));
+        CUDA_TRY(cudaStreamSynchronize(O.s));
+    }
+    const tacta_status out = status_of(final_reason);
+    if (out == TACTA_ERR_NONFINITE) set_error("non-finite value in a reduction");
+    out_info.status = out;
+    out_info.reason = final_reason;
+    out_info.iters = (int32_t)used;
+    out_info.rel_res = std::sqrt(c.red[0] / bn2_orig);
+    out_info.rel_normal_res = atbn2_orig > 0 ? std::sqrt(c.red[2] / atbn2_orig) : 0.0;
+    out_info.rho = rho_hi;
+    out_info.rho_lower = rho_lo;
+    out_info.trips = trips;
+    out_info.normal_system = normal;
+    out_info.launches = launches;
+    if (info) *info = out_info;
+    return out;
+}
+
+}  // namespace tacta
+
+// ==================================================================== C ABI
+using namespace tacta;
+
+struct tacta_plan_s { Plan* p; };
+
+extern "C" {
+
+void tacta_default_options(tacta_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-10;
+    o->tol_normal = -1.0;
+    o->tol_cta = 0.0;
+    o->pivot_tol = 1e-12;
+    o->max_iter = 1000;
+    o->t_max = 5;
+    o->cycle = TACTA_CYCLE_PINGPONG;
+    o->recompute_every = 40;
+    o->use_graph = 1;
+    o->poll_every = 64;
+    o->profile = 0;
+    o->stream = nullptr;
+}
+
+const char* tacta_last_error(void) { return get_error(); }
+
+int32_t tacta_version(void) { return 10000; }
+
+tacta_status tacta_plan_create(const tacta_matrix* A, const tacta_options* opt, tacta_plan* plan) {
+    set_error("");
+    if (!plan) { set_error("plan is NULL"); return TACTA_ERR_INVALID; }
+    *plan = nullptr;
+    Plan* p = nullptr;
+    tacta_status st = plan_create(A, opt, &p);
+    if (st != TACTA_OK) return st;
+    *plan = new tacta_plan_s{p};
+    return TACTA_OK;
+}
+
+void tacta_plan_destroy(tacta_plan plan) {
+    if (!plan) return;
+    plan_free(plan->p);
+    delete plan;
+}
+
+static tacta_status plan_call(int algo, tacta_plan plan, const double* b, const double* x0,
+                              const tacta_options* opt, double* x_out, double* hist, int32_t hist_cap,
+                              tacta_info* info) {
+    set_error("");
+    if (!plan || !plan->p) { set_error("plan is NULL"); return TACTA_ERR_INVALID; }
+    if (hist_cap < 0) { set_error("hist_cap must be >= 0"); return TACTA_ERR_INVALID; }
+    VecIO io{b, x0, x_out, hist, hist_cap};
+    if (algo == 0) return plan_cta(plan->p, io, opt, info);
+    if (algo == 1) return plan_ta(plan->p, io, opt, info);
+    return plan_minnorm(plan->p, io, opt, info);
+}
+
+tacta_status tacta_plan_cta(tacta_plan plan, const double* b, const double* x0, const tacta_options* opt,
+                            double* x_out, double* hist, int32_t hist_cap, tacta_info* info) {
+    return plan_call(0, plan, b, x0, opt, x_out, hist, hist_cap, info);
+}
+tacta_status tacta_plan_ta(tacta_plan plan, const double* b, const double* x0, const tacta_options* opt,
+                           double* x_out, double* hist, int32_t hist_cap, tacta_info* info) {
+    return plan_call(1, plan, b, x0, opt, x_out, hist, hist_cap, info);
+}
+tacta_status tacta_plan_minnorm(tacta_plan plan, const double* b, const double* x0, const tacta_options* opt,
+                                double* x_out, double* hist, int32_t hist_cap, tacta_info* info) {
+    return plan_call(2, plan, b, x0, opt, x_out, hist, hist_cap, info);
+}
+
+static tacta_status one_shot(int algo, const tacta_matrix* A, const double* b, const double* x0,
+                             const tacta_options* opt, double* x_out, double* hist, int32_t hist_cap,
+                             tacta_info* info) {
+    tacta_plan plan = nullptr;
+    tacta_status st = tacta_plan_create(A, opt, &plan);
+    if (st != TACTA_OK) return st;
+    st = plan_call(algo, plan, b, x0, opt, x_out, hist, hist_cap, info);
+    std::string keep = get_error();
+    tacta_plan_destroy(plan);
+    set_error(keep);
+    return st;
+}
+
+tacta_status cta_solve(const tacta_matrix* A, const double* b, const double* x0, const tacta_options* opt,
+                       double* x_out, double* hist, int32_t hist_cap, tacta_info* info) {
+    return one_shot(0, A, b, x0, opt, x_out, hist, hist_cap, info);
+}
+tacta_status ta_solve(const tacta_matrix* A, const double* b, const double* x0, const tacta_options* opt,
+                      double* x_out, double* hist, int32_t hist_cap, tacta_info* info) {
+    return one_shot(1, A, b, x0, opt, x_out, hist, hist_cap, info);
+}
+tacta_status ta_minnorm(const tacta_matrix* A, const double* b, const double* x0, const tacta_options* opt,
+                        double* x_out, double* hist, int32_t hist_cap, tacta_info* info) {
+    return one_shot(2, A, b, x0, opt, x_out, hist, hist_cap, info);
+}
+
+}  // extern "C"
