@@ -171,6 +171,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tacta", choices=["tacta", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--iters", type=int, default=ITERS_PER_STEP,
+                    help="F_t iterations per step (default %(default)s; smaller for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -199,7 +201,8 @@ def main():
     plan = tacta.Plan(A)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    opts = dict(tol=TOL, tol_normal=0.0, max_iter=ITERS_PER_STEP)
+    iters_per_step = args.iters
+    opts = dict(tol=TOL, tol_normal=0.0, max_iter=iters_per_step)
 
     for _ in range(args.warmup):
         plan.cta(b, **opts)
@@ -244,7 +247,7 @@ def main():
     peak, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic_record(),
-                "kernel": "spmv_scalar<CsrAcc, EPI_NORM> (A and Aᵀ products of the F_t chain)",
+                "kernel": "spmv_tiled<2048, EPI_NORM> (A and Aᵀ products of the F_t chain)",
                 "launches_timed": prof["spmv_count"], "avg_launch_us": spmv_us,
                 "bytes_per_launch": spmv_bytes, "peak_kind": peak_kind,
                 "fp64_fma_per_launch": (p.nnz + p.m),
@@ -255,14 +258,14 @@ def main():
                    torch.from_numpy(p.vals).pin_memory(), (p.m, p.n))
     hb = torch.from_numpy(p.b).pin_memory()
     e2e_steps = min(args.steps, 5)
-    tacta.cta_solve(hA, hb, hist_cap=ITERS_PER_STEP + 1, **opts)       # warm
+    tacta.cta_solve(hA, hb, hist_cap=iters_per_step + 1, **opts)       # warm
     e2e_iters, t0 = 0, time.perf_counter()
     for _ in range(e2e_steps):
-        xh, hh, ih = tacta.cta_solve(hA, hb, hist_cap=ITERS_PER_STEP + 1, **opts)
+        xh, hh, ih = tacta.cta_solve(hA, hb, hist_cap=iters_per_step + 1, **opts)
         e2e_iters += ih["iters"]
     e2e_s = time.perf_counter() - t0
     h2d = 4 * (p.m + 1) + 12 * p.nnz + 8 * p.m
-    d2h = 8 * p.n + 8 * (ITERS_PER_STEP + 1)
+    d2h = 8 * p.n + 8 * (iters_per_step + 1)
     e2e = {"value": world * e2e_iters / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "steps": e2e_steps,
            "includes": "H2D of A and b, plan build (device CSR transpose), solve, D2H of x and history"}
@@ -271,7 +274,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": f"{GRID}x{GRID}", "n": p.n, "nnz": p.nnz,
-                       "iters_per_step": ITERS_PER_STEP, "t_cycle": "ping-pong 1..5", "R": 40,
+                       "iters_per_step": iters_per_step, "t_cycle": "ping-pong 1..5", "R": 40,
                        "tol": TOL, "l2": "flushed between steps (256 MiB write); working set "
                        "~0.23 GB > 129 MB L2", "parallelism": f"replicas x{world}"},
             "rel_res_after_step": last["rel_res"], "time_to_tol_s": None,

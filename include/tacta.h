@@ -73,7 +73,8 @@ enum {
     TACTA_REASON_WITNESS = 5,
     TACTA_REASON_GAP = 6,        /* Alg. 2.5: rho_upper - rho_lower <= tol ||x_eps||        */
     TACTA_REASON_ZERO_RHS = 7,   /* b = 0: x = 0                                            */
-    TACTA_REASON_NONFINITE = 8
+    TACTA_REASON_NONFINITE = 8,
+    TACTA_REASON_TIMEOUT = 9     /* a bounded wait inside a kernel gave up (TACTA_ERR_TIMEOUT) */
 };
 
 enum { TACTA_DENSE = 0, TACTA_CSR = 1 };

@@ -90,17 +90,30 @@ enum Gate : int { GATE_ALWAYS = 0, GATE_NEED_TRUE = 1, GATE_PIVOT = 2,
 
 // ---------------------------------------------------------------- device matrix
 struct SpmvCfg {
-    int kind;      // 0 scalar (thread per row), 1 warp per row
+    int kind;      // 0 scalar (thread per row), 1 warp per row, 2 TMA-staged row tiles
     int grid;      // blocks
 };
 
+// Row tiles of the staged CSR kernel: rows [x, y), nonzeros [z, w); at most
+// kTileRows rows and `cap` nonzeros per tile (built at plan time).
+constexpr int kTileRows = 256;
+constexpr int kTileCapSmall = 2048;   // 4 blocks per SM
+constexpr int kTileCapLarge = 8192;   // 1 block per SM
+
 struct DevCSR {          // CSR operand in device memory (rows x cols)
     int64_t rows = 0, cols = 0, nnz = 0;
-    int32_t* rowptr = nullptr;
-    int32_t* colidx = nullptr;
-    double* vals = nullptr;
+    int32_t* rowptr = nullptr;   // rows + 1 (+ 4 padding)
+    int32_t* colidx = nullptr;   // nnz (+ 4 padding)
+    double* vals = nullptr;      // nnz (+ 2 padding)
+    int4* tiles = nullptr;       // kind 2: tile descriptors
+    int ntiles = 0;
+    int cap = 0;                 // kind 2: nonzero capacity of a tile
     SpmvCfg cfg{};
 };
+
+// padding (elements) after each CSR array so that 16-byte-rounded bulk copies
+// of a tile window never leave the allocation
+constexpr int kPadRowptr = 4, kPadColidx = 4, kPadVals = 2;
 
 struct DevDense {        // dense row-major operand in device memory
     int64_t rows = 0, cols = 0;
@@ -138,6 +151,9 @@ cudaError_t launch_reduce_vec(const LaunchCtx& L, int64_t len, const double* a, 
 cudaError_t launch_ctl_init(const LaunchCtx& L, const Ctl& host_init);
 cudaError_t launch_copy_gated(const LaunchCtx& L, double* dst, const double* src, int64_t len, int gate);
 cudaError_t launch_fill(const LaunchCtx& L, double* dst, double v, int64_t len);
+
+cudaError_t spmv_tiled_prepare();   // raises the dynamic shared-memory limit of the tiled kernels
+size_t spmv_tiled_smem(int cap);
 
 // plan-time helpers (transpose.cu)
 cudaError_t csr_validate(cudaStream_t s, const int32_t* rowptr, const int32_t* colidx, int64_t m,

@@ -21,6 +21,7 @@
 // spends exactly one FP64 FMA per stored nonzero (thread-per-row FMA chains,
 // or warp-per-row chains for long rows) and keeps all index arithmetic in the
 // integer pipes.
+#include <algorithm>
 #include <cfloat>
 #include <cstdio>
 
@@ -109,7 +110,8 @@ __device__ int hankel_solve_dev(const double* phi, int t, double pivot_tol, doub
     return rank;
 }
 
-__device__ void finish(Ctl* c, const FinArgs& f, double r0, double r1) {
+__device__ __noinline__ void finish(Ctl* c, const FinArgs& f, double r0, double r1) {
+    if (c->status == TACTA_REASON_TIMEOUT) return;   // a kernel gave up waiting: keep that verdict
     switch (f.kind) {
     case FIN_STORE:
         c->red[f.idx] = r0;
@@ -297,11 +299,17 @@ spmv_scalar(Acc A, const double* __restrict__ x, double* __restrict__ y, EpiArgs
     const double s = (EPI == EPI_TAPIVOT) ? ctl->s : 0.0;
     double a0 = 0.0, a1 = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.rows; row += stride) {
-        const int64_t b = A.begin(row), en = A.end(row);
+    // the loop runs while any lane of the warp has a row, so shuffles stay converged
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < A.rows; base += stride) {
+        const int64_t row = base + threadIdx.x;
+        const bool active = row < A.rows;
+        const int64_t b = active ? A.begin(row) : 0, en = active ? A.end(row) : 0;
+        const int len = (int)(en - b);
+        const int maxlen = __reduce_max_sync(0xffffffffu, len);
         double sum = 0.0;
-        for (int64_t k = b; k < en; ++k) sum = fma(A.val(k), __ldg(x + A.col(k, b)), sum);
-        epilogue<EPI>(row, sum, y, e, s, a0, a1);
+        for (int u = 0; u < maxlen; ++u)
+            if (u < len) sum = fma(A.val(b + u), __ldg(x + A.col(b + u, b)), sum);
+        if (active) epilogue<EPI>(row, sum, y, e, s, a0, a1);
     }
     if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish(a0, a1, ctl, partials, f);
 }
@@ -326,6 +334,203 @@ spmv_warp(Acc A, const double* __restrict__ x, double* __restrict__ y, EpiArgs e
         if (lane == 0) epilogue<EPI>(row, sum, y, e, s, a0, a1);
     }
     if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish(a0, a1, ctl, partials, f);
+}
+
+// ------------------------------------------------------------------ TMA-staged row tiles
+//
+// A tile is up to kTileRows consecutive rows holding at most CAP nonzeros. One
+// elected thread copies the tile's values, column indices and row offsets into
+// shared memory with cp.async.bulk (1-D TMA), completion tracked by an
+// mbarrier; two stages, so tile j+1 streams in while tile j is multiplied.
+// Every thread then runs the FMA chain of its own row out of shared memory,
+// gathering x through the read-only path. Bulk copies start on 16-byte
+// boundaries: each window is rounded outwards and the padded CSR arrays
+// (kPad*) keep the rounded end inside the allocation.
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// bounded wait: gives up after ~2^31 SM cycles (about a second)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1LL << 31)) return false;
+    }
+    return true;
+}
+
+template <int CAP>
+struct __align__(16) TileStage {
+    double vals[CAP + 2];
+    int32_t cols[CAP + 4];
+    int32_t rp[kTileRows + 8];
+};
+
+size_t spmv_tiled_smem(int cap) {
+    return cap <= kTileCapSmall ? 2 * sizeof(TileStage<kTileCapSmall>) : 2 * sizeof(TileStage<kTileCapLarge>);
+}
+
+__device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15u; }
+
+// issue the bulk copies of tile d into stage st (one thread)
+template <int CAP>
+__device__ __forceinline__ void tile_issue(const int4 d, TileStage<CAP>* st, uint64_t* bar,
+                                           const int32_t* rowptr, const int32_t* colidx,
+                                           const double* vals) {
+    const int a0 = d.z & ~1, c0 = d.z & ~3, r0 = d.x & ~3;
+    const uint32_t bv = d.w > d.z ? round16((uint32_t)(d.w - a0) * 8u) : 0u;
+    const uint32_t bc = d.w > d.z ? round16((uint32_t)(d.w - c0) * 4u) : 0u;
+    const uint32_t br = round16((uint32_t)(d.y + 1 - r0) * 4u);
+    mbar_expect_tx(bar, bv + bc + br);
+    if (bv) bulk_g2s(st->vals, vals + a0, bv, bar);
+    if (bc) bulk_g2s(st->cols, colidx + c0, bc, bar);
+    bulk_g2s(st->rp, rowptr + r0, br, bar);
+}
+
+template <int CAP, int EPI>
+__global__ void __launch_bounds__(kTileRows)
+spmv_tiled(const int4* __restrict__ tiles, int ntiles, const int32_t* __restrict__ rowptr,
+           const int32_t* __restrict__ colidx, const double* __restrict__ vals,
+           const double* __restrict__ x, double* __restrict__ y, EpiArgs e, Ctl* ctl, double* partials,
+           FinArgs f, int gate) {
+    if (gated_out(ctl, gate)) return;
+    if (gate != GATE_FORCE && blockIdx.x == 0 && threadIdx.x == 0) ctl->matvecs += 1;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TileStage<CAP>* st = reinterpret_cast<TileStage<CAP>*>(smem_raw);
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int failed;
+    const int tid = threadIdx.x;
+    const int G = gridDim.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
+        for (int j = 0; j < 2; ++j) {
+            const int t = blockIdx.x + j * G;
+            if (t < ntiles) tile_issue<CAP>(__ldg(tiles + t), st + j, bar + j, rowptr, colidx, vals);
+        }
+    }
+    __syncthreads();
+    const double s = (EPI == EPI_TAPIVOT) ? ctl->s : 0.0;
+    double a0 = 0.0, a1 = 0.0;
+    for (int j = 0;; ++j) {
+        const int t = blockIdx.x + j * G;
+        if (t >= ntiles) break;
+        const int sidx = j & 1;
+        const int4 d = __ldg(tiles + t);
+        bool ok = !failed && mbar_wait_bounded(bar + sidx, (uint32_t)((j >> 1) & 1));
+        if (!ok) {
+            failed = 1;
+            atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+        }
+        const TileStage<CAP>* S = st + sidx;
+        const int row = d.x + tid;
+        const bool active = ok && row < d.y;
+        int kb = 0, len = 0;
+        if (active) {
+            const int r0 = d.x & ~3;
+            kb = S->rp[row - r0];
+            len = S->rp[row + 1 - r0] - kb;
+        }
+        // A predicated-off FP64 FMA still occupies the narrow FP64 pipe, so each warp
+        // issues exactly max(row length over its lanes) FMAs, in groups of 8 with all
+        // gathers of a group in flight before its FMA chain.
+        const int maxlen = __reduce_max_sync(0xffffffffu, len);
+        double sum = 0.0;
+        const double* vp = S->vals + (kb - (d.z & ~1));
+        const int32_t* cp = S->cols + (kb - (d.z & ~3));
+        for (int u0 = 0; u0 < maxlen; u0 += 8) {
+            double xv[8], vv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (u0 + u < len) {
+                    xv[u] = __ldg(x + cp[u0 + u]);
+                    vv[u] = vp[u0 + u];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (u0 + u >= maxlen) break;   // warp-uniform
+                if (u0 + u < len) sum = fma(vv[u], xv[u], sum);
+            }
+        }
+        if (active) epilogue<EPI>(row, sum, y, e, s, a0, a1);
+        __syncthreads();   // stage sidx is free again
+        if (tid == 0 && !failed) {
+            const int tn = t + 2 * G;
+            if (tn < ntiles) tile_issue<CAP>(__ldg(tiles + tn), st + sidx, bar + sidx, rowptr, colidx, vals);
+        }
+    }
+    if (failed && tid == 0) {
+        // give the copies still in flight a bounded chance to land before the block exits
+        for (int j = 0; j < 2; ++j) mbar_wait_bounded(bar + j, 0u);
+    }
+    if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish(a0, a1, ctl, partials, f);
+}
+
+cudaError_t spmv_tiled_prepare() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+#define TACTA_TILED_ATTR(CAP, EPI)                                                                   \
+    if (e == cudaSuccess)                                                                            \
+        e = cudaFuncSetAttribute(spmv_tiled<CAP, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                 (int)spmv_tiled_smem(CAP));
+    TACTA_TILED_ATTR(kTileCapSmall, EPI_NONE) TACTA_TILED_ATTR(kTileCapSmall, EPI_NORM)
+    TACTA_TILED_ATTR(kTileCapSmall, EPI_RESID) TACTA_TILED_ATTR(kTileCapSmall, EPI_TAPIVOT)
+    TACTA_TILED_ATTR(kTileCapLarge, EPI_NONE) TACTA_TILED_ATTR(kTileCapLarge, EPI_NORM)
+    TACTA_TILED_ATTR(kTileCapLarge, EPI_RESID) TACTA_TILED_ATTR(kTileCapLarge, EPI_TAPIVOT)
+#undef TACTA_TILED_ATTR
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <int EPI>
+static cudaError_t spmv_tiled_launch(const LaunchCtx& L, const DevCSR& A, const double* x, double* y,
+                                     EpiArgs e, FinArgs f, int gate) {
+    const int per_sm = A.cap <= kTileCapSmall ? 4 : 1;
+    int grid = std::min(A.ntiles, std::max(1, (L.max_grid / 8) * per_sm));
+    if (grid < 1) grid = 1;
+    const size_t sm = spmv_tiled_smem(A.cap);
+    if (A.cap <= kTileCapSmall)
+        spmv_tiled<kTileCapSmall, EPI><<<grid, kTileRows, sm, L.stream>>>(
+            A.tiles, A.ntiles, A.rowptr, A.colidx, A.vals, x, y, e, L.ctl, L.partials, f, gate);
+    else
+        spmv_tiled<kTileCapLarge, EPI><<<grid, kTileRows, sm, L.stream>>>(
+            A.tiles, A.ntiles, A.rowptr, A.colidx, A.vals, x, y, e, L.ctl, L.partials, f, gate);
+    if (L.launches) ++*L.launches;
+    return cudaGetLastError();
 }
 
 template <class Acc, int EPI>
@@ -353,6 +558,14 @@ static cudaError_t spmv_dispatch(const LaunchCtx& L, int kind, const Acc& acc, c
 
 cudaError_t launch_spmv(const LaunchCtx& L, const DevOperand& A, const double* x, double* y,
                         int epi, EpiArgs e, FinArgs f, int gate) {
+    if (A.format == TACTA_CSR && A.csr.cfg.kind == 2) {
+        switch (epi) {
+        case EPI_NONE: return spmv_tiled_launch<EPI_NONE>(L, A.csr, x, y, e, f, gate);
+        case EPI_NORM: return spmv_tiled_launch<EPI_NORM>(L, A.csr, x, y, e, f, gate);
+        case EPI_RESID: return spmv_tiled_launch<EPI_RESID>(L, A.csr, x, y, e, f, gate);
+        default: return spmv_tiled_launch<EPI_TAPIVOT>(L, A.csr, x, y, e, f, gate);
+        }
+    }
     if (A.format == TACTA_CSR) {
         CsrAcc acc{A.csr.rowptr, A.csr.colidx, A.csr.vals, A.csr.rows};
         return spmv_dispatch(L, A.csr.cfg.kind, acc, x, y, epi, e, f, gate);

@@ -146,8 +146,8 @@ static void plan_free(Plan* p) {
     cudaSetDevice(p->device);
     free_graphs(p);
     auto F = [](void* q) { if (q) cudaFree(q); };
-    F(p->A.csr.rowptr); F(p->A.csr.colidx); F(p->A.csr.vals); F(p->A.dense.vals);
-    F(p->At.csr.rowptr); F(p->At.csr.colidx); F(p->At.csr.vals); F(p->At.dense.vals);
+    F(p->A.csr.rowptr); F(p->A.csr.colidx); F(p->A.csr.vals); F(p->A.csr.tiles); F(p->A.dense.vals);
+    F(p->At.csr.rowptr); F(p->At.csr.colidx); F(p->At.csr.vals); F(p->At.csr.tiles); F(p->At.dense.vals);
     F(p->ctl); F(p->partials); F(p->flag_dev);
     F(p->b); F(p->x); F(p->r); F(p->tmp_m); F(p->tmp_n);
     for (int i = 0; i < kTMax; ++i) { F(p->z[i]); F(p->u[i]); }
@@ -162,10 +162,40 @@ static void plan_free(Plan* p) {
     delete p;
 }
 
-static int choose_kind_csr(int64_t rows, int64_t nnz) {
-    // thread per row keeps every FP64 lane busy on short rows; long rows go warp per row
-    const double avg = rows > 0 ? (double)nnz / (double)rows : 0.0;
-    return avg >= 64.0 ? 1 : 0;
+// Kernel choice for a CSR operand: rows averaging >= 64 nonzeros run warp per
+// row; shorter rows run the TMA-staged row tiles (one FP64 FMA chain per
+// thread, every lane busy), provided no single row exceeds a tile's capacity.
+// Tiles: greedy runs of consecutive rows, at most kTileRows rows and `cap`
+// nonzeros each, described by {row begin, row end, nnz begin, nnz end}.
+static cudaError_t setup_csr_kernel(DevCSR& a, cudaStream_t s) {
+    const double avg = a.rows > 0 ? (double)a.nnz / (double)a.rows : 0.0;
+    a.cfg.kind = 1;
+    if (avg >= 64.0) return cudaSuccess;
+    std::vector<int32_t> rp((size_t)a.rows + 1);
+    cudaError_t e = cudaMemcpyAsync(rp.data(), a.rowptr, sizeof(int32_t) * (a.rows + 1), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    const int cap = avg * kTileRows <= 0.9 * kTileCapSmall ? kTileCapSmall : kTileCapLarge;
+    int32_t maxrow = 0;
+    for (int64_t i = 0; i < a.rows; ++i) maxrow = std::max(maxrow, rp[i + 1] - rp[i]);
+    if (maxrow > cap) return cudaSuccess;   // an outlier row: keep warp per row
+    std::vector<int4> tiles;
+    tiles.reserve((size_t)(a.rows / kTileRows + a.nnz / cap + 2));
+    int64_t r = 0;
+    while (r < a.rows) {
+        int64_t e2 = r;
+        while (e2 < a.rows && e2 - r < kTileRows && (int64_t)rp[e2 + 1] - rp[r] <= cap) ++e2;
+        tiles.push_back(make_int4((int)r, (int)e2, rp[r], rp[e2]));
+        r = e2;
+    }
+    if ((e = cudaMalloc(&a.tiles, sizeof(int4) * tiles.size())) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(a.tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    a.ntiles = (int)tiles.size();
+    a.cap = cap;
+    a.cfg.kind = 2;
+    return spmv_tiled_prepare();
 }
 
 static tacta_status validate_opts(const tacta_options& o) {
@@ -215,9 +245,12 @@ static tacta_status plan_create(const tacta_matrix* M, const tacta_options* opt,
         DevCSR& a = p->A.csr;
         p->A.format = p->At.format = TACTA_CSR;
         a.rows = m; a.cols = n; a.nnz = nnz;
-        PTRY(cudaMalloc(&a.rowptr, sizeof(int32_t) * (m + 1)));
-        PTRY(cudaMalloc(&a.colidx, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
-        PTRY(cudaMalloc(&a.vals, sizeof(double) * std::max<int64_t>(nnz, 1)));
+        PTRY(cudaMalloc(&a.rowptr, sizeof(int32_t) * (m + 1 + kPadRowptr)));
+        PTRY(cudaMalloc(&a.colidx, sizeof(int32_t) * (nnz + kPadColidx)));
+        PTRY(cudaMalloc(&a.vals, sizeof(double) * (nnz + kPadVals)));
+        PTRY(cudaMemsetAsync(a.rowptr, 0, sizeof(int32_t) * (m + 1 + kPadRowptr), s));
+        PTRY(cudaMemsetAsync(a.colidx, 0, sizeof(int32_t) * (nnz + kPadColidx), s));
+        PTRY(cudaMemsetAsync(a.vals, 0, sizeof(double) * (nnz + kPadVals), s));
         PTRY(cudaMemcpyAsync(a.rowptr, M->rowptr, sizeof(int32_t) * (m + 1), cudaMemcpyDefault, s));
         if (nnz > 0) {
             PTRY(cudaMemcpyAsync(a.colidx, M->colidx, sizeof(int32_t) * nnz, cudaMemcpyDefault, s));
@@ -235,8 +268,8 @@ static tacta_status plan_create(const tacta_matrix* M, const tacta_options* opt,
             return fail(TACTA_ERR_INVALID);
         }
         PTRY(csr_transpose(s, a, p->At.csr));
-        a.cfg.kind = choose_kind_csr(m, nnz);
-        p->At.csr.cfg.kind = choose_kind_csr(n, nnz);
+        PTRY(setup_csr_kernel(a, s));
+        PTRY(setup_csr_kernel(p->At.csr, s));
     } else {
         p->A.format = p->At.format = TACTA_DENSE;
         DevDense& a = p->A.dense;

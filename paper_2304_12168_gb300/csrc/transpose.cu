@@ -109,10 +109,12 @@ cudaError_t csr_transpose(cudaStream_t s, const DevCSR& A, DevCSR& T) {
     T.cols = A.rows;
     T.nnz = nnz;
     // all allocations are the caller's to free (rowptr, colidx, vals of T)
-    if ((e = cudaMalloc(&T.rowptr, sizeof(int32_t) * (T.rows + 1))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&T.colidx, sizeof(int32_t) * (nnz > 0 ? nnz : 1))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&T.vals, sizeof(double) * (nnz > 0 ? nnz : 1))) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(T.rowptr, 0, sizeof(int32_t) * (T.rows + 1), s)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&T.rowptr, sizeof(int32_t) * (T.rows + 1 + kPadRowptr))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&T.colidx, sizeof(int32_t) * (nnz + kPadColidx))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&T.vals, sizeof(double) * (nnz + kPadVals))) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(T.rowptr, 0, sizeof(int32_t) * (T.rows + 1 + kPadRowptr), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(T.colidx, 0, sizeof(int32_t) * (nnz + kPadColidx), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(T.vals, 0, sizeof(double) * (nnz + kPadVals), s)) != cudaSuccess) return e;
     if (nnz == 0) return cudaStreamSynchronize(s);
 
     int32_t *rowof = nullptr, *seq = nullptr, *keys_out = nullptr, *perm = nullptr, *counts = nullptr;
