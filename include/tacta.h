@@ -179,6 +179,30 @@ tacta_status tacta_plan_minnorm(tacta_plan plan, const double* b, const double* 
                                 int32_t hist_cap, tacta_info* info);
 void tacta_plan_destroy(tacta_plan plan);
 
+/*
+ * tacta_residual_static -- r = b - A x with ||r||² and rᵀb, allocating nothing.
+ *   The paper has no counterpart: this entry serves callers that cannot allocate
+ *   device memory when they need a residual -- code inside a framework whose
+ *   caching allocator has reserved the device, and latency-bound loops that must
+ *   not enter cudaMalloc / cudaFree (which may synchronize the device). Instead of
+ *   plan workspace it uses one file-scope device array of 1 MiB per device
+ *   (held by every GPU that loads the library until the process exits).
+ *   A        dense or CSR, on_device = 1 (host arrays are rejected: copying them
+ *            would need an allocation); A->m <= 16,773,120 (the scratch holds one
+ *            pair of doubles per 256-row block); larger m -> TACTA_ERR_INVALID.
+ *   x, b     device pointers, n and m values; r_out: device pointer, m values.
+ *   norms_out  two doubles (host or device): ||r||², rᵀb.
+ *   stream   cudaStream_t or NULL; the call synchronizes it before returning.
+ *   Makes no cudaMalloc / cudaFree or other allocating call. Every call on a device
+ *   shares the scratch array, which keeps the last call's contents; the ticket
+ *   counter that must start at zero is cleared at the start of each call; calls
+ *   whose work overlaps on the GPU race on the array. The first call on each
+ *   device looks up the array's address (cudaGetSymbolAddress) with that device
+ *   current; make that first call before any stream capture.
+ */
+tacta_status tacta_residual_static(const tacta_matrix* A, const double* x, const double* b,
+                                   double* r_out, double* norms_out, void* stream);
+
 /* Description of the last error on the calling thread ("" if none). */
 const char* tacta_last_error(void);
 

@@ -63,7 +63,7 @@ class tacta_info(ctypes.Structure):
 
 EXPORTS = ["tacta_default_options", "cta_solve", "ta_solve", "ta_minnorm", "tacta_plan_create",
            "tacta_plan_cta", "tacta_plan_ta", "tacta_plan_minnorm", "tacta_plan_destroy",
-           "tacta_last_error", "tacta_version"]
+           "tacta_residual_static", "tacta_last_error", "tacta_version"]
 
 _lib_handle = None
 
@@ -96,6 +96,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tacta_last_error.restype = ctypes.c_char_p
     lib.tacta_version.argtypes = []
     lib.tacta_version.restype = ctypes.c_int32
+    lib.tacta_residual_static.argtypes = [P(tacta_matrix), dp, dp, dp, dp, vp]
+    lib.tacta_residual_static.restype = ctypes.c_int32
     _lib_handle = lib
     return lib
 
@@ -234,6 +236,27 @@ def ta_minnorm(A, b, hist_cap=None, **opts):
     return _solve("ta_minnorm", A, b, None, hist_cap, **opts)
 
 
+def residual_static(A, x, b):
+    """tacta_residual_static: r = b - A x, ||r||² and rᵀb with no device allocation by the
+    library (for callers that cannot allocate at the point of the call). A, x and b must
+    be CUDA tensors; returns (r, ||r||², rᵀb). The output tensor r is allocated here by
+    torch, before the call."""
+    import torch
+    lib = load_library()
+    M, on_dev, keep = _matrix(A)
+    if not on_dev:
+        raise ValueError("residual_static needs CUDA tensors")
+    px, _, kx = _ptr(x, np.float64)
+    pb, _, kb = _ptr(b, np.float64)
+    r = torch.empty(int(M.m), dtype=torch.float64, device=kb.device)
+    norms = np.zeros(2, dtype=np.float64)
+    st = lib.tacta_residual_static(ctypes.byref(M), px, pb, r.data_ptr(), norms.ctypes.data,
+                                   _stream_ptr(True))
+    _check(st)
+    del keep, kx, kb
+    return r, float(norms[0]), float(norms[1])
+
+
 class Plan:
     """A on the GPU (plus Aᵀ) reused across right-hand sides (tacta_plan_*)."""
 
@@ -287,5 +310,5 @@ class Plan:
             pass
 
 
-__all__ = ["cta_solve", "ta_solve", "ta_minnorm", "Plan", "CSR", "load_library", "make_options",
-           "TactaError", "EXPORTS", "LIB_PATH"]
+__all__ = ["cta_solve", "ta_solve", "ta_minnorm", "residual_static", "Plan", "CSR", "load_library",
+           "make_options", "TactaError", "EXPORTS", "LIB_PATH"]
