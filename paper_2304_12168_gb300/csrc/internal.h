@@ -75,12 +75,14 @@ enum Epilogue : int {
     EPI_NONE = 0,      // y = A x
     EPI_NORM = 1,      // y = A x;          red0 += y²
     EPI_RESID = 2,     // y = b - A x;      red0 += y², red1 += y b
-    EPI_TAPIVOT = 3    // y = s (A x) = v;  w = v - b + d (= v - b'); red0 += d w, red1 += w²
+    EPI_TAPIVOT = 3,   // y = s (A x) = v;  w = v - b + d (= v - b'); red0 += d w, red1 += w²
+    EPI_RESID_F32 = 4  // FP64 product, v = b - A x; yf = (float) v; red0 += v², red1 += v b
 };
 
 struct EpiArgs {
-    const double* b;   // EPI_RESID / EPI_TAPIVOT: right-hand side
+    const double* b;   // EPI_RESID / EPI_TAPIVOT / EPI_RESID_F32: right-hand side
     const double* d;   // EPI_TAPIVOT: d = b - b'
+    float* yf;         // EPI_RESID_F32: FP32 copy of the residual
 };
 
 // Gate: which device flag must be set for the kernel to run (all kernels
@@ -108,8 +110,16 @@ struct DevCSR {          // CSR operand in device memory (rows x cols)
     int4* tiles = nullptr;       // kind 2: tile descriptors
     int ntiles = 0;
     int cap = 0;                 // kind 2: nonzero capacity of a tile
+    int2* xwin = nullptr;        // kind 3: per tile {first column, last column} of its x window
     SpmvCfg cfg{};
 };
+
+// Banded operands (every tile's columns span at most kXSpan entries of x) also
+// stage the tile's x window in shared memory: kind 3.
+constexpr int kXSpan = 2560;
+// every plan vector that can be a product's input carries this many doubles of
+// padding, so 16-byte-rounded x-window copies stay inside the allocation
+constexpr int kPadVec = 2;
 
 // padding (elements) after each CSR array so that 16-byte-rounded bulk copies
 // of a tile window never leave the allocation
@@ -129,6 +139,15 @@ struct DevOperand {      // A or Aᵀ
     int64_t cols() const { return format == TACTA_CSR ? csr.cols : dense.cols; }
     int64_t nnz() const { return format == TACTA_CSR ? csr.nnz : dense.rows * dense.cols; }
 };
+
+// FP32 copy of a CSR operand for the mixed-precision path: values in FP32, the
+// structure (rowptr, colidx, tiles, x windows) shared with the FP64 operand.
+struct DevCSR32 {
+    const DevCSR* base = nullptr;
+    float* vals = nullptr;       // nnz (+ 4 padding)
+};
+constexpr int kPadVals32 = 4;
+constexpr int kPadVec32 = 4;     // FP32 vectors read by products carry 4 floats of padding
 
 // ---------------------------------------------------------------- kernel launchers
 struct LaunchCtx {
@@ -151,6 +170,15 @@ cudaError_t launch_reduce_vec(const LaunchCtx& L, int64_t len, const double* a, 
 cudaError_t launch_ctl_init(const LaunchCtx& L, const Ctl& host_init);
 cudaError_t launch_copy_gated(const LaunchCtx& L, double* dst, const double* src, int64_t len, int gate);
 cudaError_t launch_fill(const LaunchCtx& L, double* dst, double v, int64_t len);
+
+// mixed precision (FP32 chain, FP64 refinement)
+cudaError_t launch_spmv32(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y, int epi,
+                          FinArgs f, int gate);
+cudaError_t launch_cta_update32(const LaunchCtx& L, int t, int64_t m, int64_t n, float* dx, float* r,
+                                float* const* z, float* const* u, FinArgs f);
+cudaError_t launch_fold_correction(const LaunchCtx& L, int64_t n, double* x, float* dx, int gate);
+cudaError_t convert_to_f32(cudaStream_t s, const double* src, float* dst, int64_t len);
+cudaError_t spmv32_prepare();
 
 cudaError_t spmv_tiled_prepare();   // raises the dynamic shared-memory limit of the tiled kernels
 size_t spmv_tiled_smem(int cap);

@@ -202,20 +202,35 @@ __device__ __noinline__ void finish(Ctl* c, const FinArgs& f, double r0, double 
     }
 }
 
-// Block-level reduction of (a0, a1), partial per block, last block sums all
-// partials in fixed order and runs the finisher.
+// Sum of one value over a block of kBlock threads, result valid in warp 0.
+// An FP64 warp-instruction costs the same on GB300 whatever the number of
+// active lanes, so the values go through shared memory and warp 0 alone adds
+// them (7 + 5 FP64 warp-instructions, instead of a shuffle tree in every warp).
+__device__ __forceinline__ double block_sum_warp0(double v, double* sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = sh[threadIdx.x];
+#pragma unroll
+        for (int i = 1; i < kBlock / 32; ++i) s += sh[threadIdx.x + 32 * i];
+        s = warp_sum(s);
+    }
+    __syncthreads();
+    return s;
+}
+
+// Block-level reduction of NRED values (a0 and, if NRED = 2, a1), one partial
+// per block; the last block to finish (atomic ticket, no waiting) sums the
+// partials in block order and runs the finisher. Requires blockDim = kBlock.
+template <int NRED = 2>
 __device__ void reduce_and_finish(double a0, double a1, Ctl* ctl, double* partials,
                                   const FinArgs& f) {
-    __shared__ double sh0[kBlock / 32], sh1[kBlock / 32];
+    __shared__ double sh[kBlock];
     __shared__ int am_last;
-    a0 = warp_sum(a0);
-    a1 = warp_sum(a1);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) { sh0[w] = a0; sh1[w] = a1; }
-    __syncthreads();
+    const double s0 = block_sum_warp0(a0, sh);
+    const double s1 = NRED > 1 ? block_sum_warp0(a1, sh) : 0.0;
     if (threadIdx.x == 0) {
-        double s0 = 0.0, s1 = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { s0 += sh0[i]; s1 += sh1[i]; }
         partials[2 * blockIdx.x] = s0;
         partials[2 * blockIdx.x + 1] = s1;
         __threadfence();
@@ -225,23 +240,23 @@ __device__ void reduce_and_finish(double a0, double a1, Ctl* ctl, double* partia
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    double s0 = 0.0, s1 = 0.0;
+    double t0 = 0.0, t1 = 0.0;
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-        s0 += __ldcg(&partials[2 * i]);
-        s1 += __ldcg(&partials[2 * i + 1]);
+        t0 += __ldcg(&partials[2 * i]);
+        if (NRED > 1) t1 += __ldcg(&partials[2 * i + 1]);
     }
-    s0 = warp_sum(s0);
-    s1 = warp_sum(s1);
-    __syncthreads();
-    if (l == 0) { sh0[w] = s0; sh1[w] = s1; }
-    __syncthreads();
+    t0 = block_sum_warp0(t0, sh);
+    if (NRED > 1) t1 = block_sum_warp0(t1, sh);
     if (threadIdx.x == 0) {
-        double t0 = 0.0, t1 = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { t0 += sh0[i]; t1 += sh1[i]; }
         ctl->counter = 0;
         finish(ctl, f, t0, t1);
     }
 }
+
+template <int EPI>
+struct EpiRed {
+    static constexpr int value = (EPI == EPI_RESID || EPI == EPI_TAPIVOT || EPI == EPI_RESID_F32) ? 2 : 1;
+};
 
 // ------------------------------------------------------------------ operand access
 
@@ -279,13 +294,19 @@ __device__ __forceinline__ void epilogue(int64_t row, double sum, double* __rest
         y[row] = v;
         a0 = fma(v, v, a0);
         a1 = fma(v, bv, a1);
-    } else {  // EPI_TAPIVOT: v = s (A c); w = v - b' = v - b + d
+    } else if (EPI == EPI_TAPIVOT) {  // v = s (A c); w = v - b' = v - b + d
         const double v = s * sum;
         const double dv = __ldg(e.d + row);
         const double w = (v - __ldg(e.b + row)) + dv;
         y[row] = v;
         a0 = fma(dv, w, a0);
         a1 = fma(w, w, a1);
+    } else {  // EPI_RESID_F32: FP64 residual, stored in FP32 for the mixed-precision chain
+        const double bv = __ldg(e.b + row);
+        const double v = bv - sum;
+        e.yf[row] = (float)v;
+        a0 = fma(v, v, a0);
+        a1 = fma(v, bv, a1);
     }
 }
 
@@ -311,7 +332,7 @@ spmv_scalar(Acc A, const double* __restrict__ x, double* __restrict__ y, EpiArgs
             if (u < len) sum = fma(A.val(b + u), __ldg(x + A.col(b + u, b)), sum);
         if (active) epilogue<EPI>(row, sum, y, e, s, a0, a1);
     }
-    if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish(a0, a1, ctl, partials, f);
+    if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish<EpiRed<EPI>::value>(a0, a1, ctl, partials, f);
 }
 
 // Warp per row: lanes stride over the row, shuffle-sum at the end (long rows).
@@ -333,7 +354,7 @@ spmv_warp(Acc A, const double* __restrict__ x, double* __restrict__ y, EpiArgs e
         sum = warp_sum(sum);
         if (lane == 0) epilogue<EPI>(row, sum, y, e, s, a0, a1);
     }
-    if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish(a0, a1, ctl, partials, f);
+    if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish<EpiRed<EPI>::value>(a0, a1, ctl, partials, f);
 }
 
 // ------------------------------------------------------------------ TMA-staged row tiles
@@ -417,6 +438,55 @@ __device__ __forceinline__ void tile_issue(const int4 d, TileStage<CAP>* st, uin
     bulk_g2s(st->rp, rowptr + r0, br, bar);
 }
 
+// Registers a thread carries for one row of a tile: the row's first entries of x
+// (gathered ahead of use) and where the row's values sit in its stage.
+constexpr int kAhead = 6;
+struct RowRegs {
+    double xv[kAhead];
+    int kb;        // first value of the row, relative to the stage's value window
+    int cb;        // same for the column window
+    int len;
+    int maxlen;    // max len over the warp (warp-uniform FMA trip count)
+    bool active;
+};
+
+template <int CAP>
+__device__ __forceinline__ void row_fetch(const TileStage<CAP>* S, const int4 d, int tid, bool ok,
+                                          const double* __restrict__ x, RowRegs& R) {
+    const int row = d.x + tid;
+    R.active = ok && row < d.y;
+    R.len = 0;
+    R.kb = 0;
+    R.cb = 0;
+    if (R.active) {
+        const int r0 = d.x & ~3;
+        const int k0 = S->rp[row - r0];
+        R.len = S->rp[row + 1 - r0] - k0;
+        R.kb = k0 - (d.z & ~1);
+        R.cb = k0 - (d.z & ~3);
+    }
+    R.maxlen = __reduce_max_sync(0xffffffffu, R.len);
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u)
+        if (u < R.len) R.xv[u] = __ldg(x + S->cols[R.cb + u]);
+}
+
+template <int CAP>
+__device__ __forceinline__ double row_dot(const TileStage<CAP>* S, const RowRegs& R,
+                                          const double* __restrict__ x) {
+    // a predicated-off FP64 FMA still costs a full warp slot on GB300: the trip
+    // count is the warp-uniform maximum row length
+    double sum = 0.0;
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+        if (u >= R.maxlen) break;
+        if (u < R.len) sum = fma(S->vals[R.kb + u], R.xv[u], sum);
+    }
+    for (int u = kAhead; u < R.maxlen; ++u)
+        if (u < R.len) sum = fma(S->vals[R.kb + u], __ldg(x + S->cols[R.cb + u]), sum);
+    return sum;
+}
+
 template <int CAP, int EPI>
 __global__ void __launch_bounds__(kTileRows)
 spmv_tiled(const int4* __restrict__ tiles, int ntiles, const int32_t* __restrict__ rowptr,
@@ -444,17 +514,124 @@ spmv_tiled(const int4* __restrict__ tiles, int ntiles, const int32_t* __restrict
     __syncthreads();
     const double s = (EPI == EPI_TAPIVOT) ? ctl->s : 0.0;
     double a0 = 0.0, a1 = 0.0;
+    // Software pipeline over this block's tiles j = 0, 1, ...: tile j+1's x values
+    // are gathered (loads in flight) before tile j's FMA chains run on the values
+    // gathered one step earlier; tile j+2's bulk copy is issued once every thread
+    // is done with tile j's stage.
+    RowRegs cur;
+    int4 dcur = make_int4(0, 0, 0, 0);
+    if (blockIdx.x < ntiles) {
+        dcur = __ldg(tiles + blockIdx.x);
+        bool ok = mbar_wait_bounded(bar + 0, 0u);
+        if (!ok) { failed = 1; atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT); }
+        row_fetch<CAP>(st + 0, dcur, tid, ok, x, cur);
+    }
+    for (int j = 0;; ++j) {
+        const int t = blockIdx.x + j * G;
+        if (t >= ntiles) break;
+        const int sidx = j & 1;
+        RowRegs nxt;
+        int4 dnxt = make_int4(0, 0, 0, 0);
+        const int tn = t + G;
+        if (tn < ntiles) {
+            dnxt = __ldg(tiles + tn);
+            bool ok = !failed && mbar_wait_bounded(bar + (sidx ^ 1), (uint32_t)(((j + 1) >> 1) & 1));
+            if (!ok) { failed = 1; atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT); }
+            row_fetch<CAP>(st + (sidx ^ 1), dnxt, tid, ok, x, nxt);
+        }
+        const double sum = row_dot<CAP>(st + sidx, cur, x);
+        if (cur.active) epilogue<EPI>(dcur.x + tid, sum, y, e, s, a0, a1);
+        __syncthreads();   // stage sidx is free again
+        if (tid == 0 && !failed) {
+            const int t2 = t + 2 * G;
+            if (t2 < ntiles) tile_issue<CAP>(__ldg(tiles + t2), st + sidx, bar + sidx, rowptr, colidx, vals);
+        }
+        cur = nxt;
+        dcur = dnxt;
+    }
+    if (failed && tid == 0) {
+        // give the copies still in flight a bounded chance to land before the block exits
+        for (int j = 0; j < 2; ++j) mbar_wait_bounded(bar + j, 0u);
+    }
+    if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish<EpiRed<EPI>::value>(a0, a1, ctl, partials, f);
+}
+
+// ------------------------------------------------------------------ banded variant: x window staged too
+//
+// When every tile's columns fall in a window of at most kXSpan entries of x
+// (banded operands such as stencils), the bulk copies also bring that window
+// of x into shared memory, so each row's FMA chain reads values, indices and
+// x from shared memory and the narrow FP64 pipe is not left waiting on global
+// gathers.
+
+template <int CAP>
+struct __align__(16) TileStageX {
+    double vals[CAP + 2];
+    int32_t cols[CAP + 4];
+    int32_t rp[kTileRows + 8];
+    double xs[kXSpan + 2];
+};
+
+size_t spmv_tiled_x_smem() { return 2 * sizeof(TileStageX<kTileCapSmall>); }
+
+template <int CAP>
+__device__ __forceinline__ void tile_issue_x(const int4 d, const int2 w, TileStageX<CAP>* st,
+                                             uint64_t* bar, const int32_t* rowptr,
+                                             const int32_t* colidx, const double* vals,
+                                             const double* x) {
+    const int a0 = d.z & ~1, c0 = d.z & ~3, r0 = d.x & ~3, x0 = w.x & ~1;
+    const uint32_t bv = d.w > d.z ? round16((uint32_t)(d.w - a0) * 8u) : 0u;
+    const uint32_t bc = d.w > d.z ? round16((uint32_t)(d.w - c0) * 4u) : 0u;
+    const uint32_t br = round16((uint32_t)(d.y + 1 - r0) * 4u);
+    const uint32_t bx = d.w > d.z ? round16((uint32_t)(w.y + 1 - x0) * 8u) : 0u;
+    mbar_expect_tx(bar, bv + bc + br + bx);
+    if (bv) bulk_g2s(st->vals, vals + a0, bv, bar);
+    if (bc) bulk_g2s(st->cols, colidx + c0, bc, bar);
+    bulk_g2s(st->rp, rowptr + r0, br, bar);
+    if (bx) bulk_g2s(st->xs, x + x0, bx, bar);
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kTileRows)
+spmv_tiled_x(const int4* __restrict__ tiles, const int2* __restrict__ xwin, int ntiles,
+             const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+             const double* __restrict__ vals, const double* __restrict__ x, double* __restrict__ y,
+             EpiArgs e, Ctl* ctl, double* partials, FinArgs f, int gate) {
+    constexpr int CAP = kTileCapSmall;
+    if (gated_out(ctl, gate)) return;
+    if (gate != GATE_FORCE && blockIdx.x == 0 && threadIdx.x == 0) ctl->matvecs += 1;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TileStageX<CAP>* st = reinterpret_cast<TileStageX<CAP>*>(smem_raw);
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int failed;
+    const int tid = threadIdx.x;
+    const int G = gridDim.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
+        for (int j = 0; j < 2; ++j) {
+            const int t = blockIdx.x + j * G;
+            if (t < ntiles)
+                tile_issue_x<CAP>(__ldg(tiles + t), __ldg(xwin + t), st + j, bar + j, rowptr, colidx, vals, x);
+        }
+    }
+    __syncthreads();
+    const double s = (EPI == EPI_TAPIVOT) ? ctl->s : 0.0;
+    double a0 = 0.0, a1 = 0.0;
     for (int j = 0;; ++j) {
         const int t = blockIdx.x + j * G;
         if (t >= ntiles) break;
         const int sidx = j & 1;
         const int4 d = __ldg(tiles + t);
-        bool ok = !failed && mbar_wait_bounded(bar + sidx, (uint32_t)((j >> 1) & 1));
+        const int xw0 = __ldg(&xwin[t].x) & ~1;
+        const bool ok = !failed && mbar_wait_bounded(bar + sidx, (uint32_t)((j >> 1) & 1));
         if (!ok) {
             failed = 1;
             atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
         }
-        const TileStage<CAP>* S = st + sidx;
+        const TileStageX<CAP>* S = st + sidx;
         const int row = d.x + tid;
         const bool active = ok && row < d.y;
         int kb = 0, len = 0;
@@ -463,40 +640,36 @@ spmv_tiled(const int4* __restrict__ tiles, int ntiles, const int32_t* __restrict
             kb = S->rp[row - r0];
             len = S->rp[row + 1 - r0] - kb;
         }
-        // A predicated-off FP64 FMA still occupies the narrow FP64 pipe, so each warp
-        // issues exactly max(row length over its lanes) FMAs, in groups of 8 with all
-        // gathers of a group in flight before its FMA chain.
+        // trip count = warp-uniform max row length (a masked FP64 FMA costs a full slot)
         const int maxlen = __reduce_max_sync(0xffffffffu, len);
+        const int vb = kb - (d.z & ~1), cb = kb - (d.z & ~3);
         double sum = 0.0;
-        const double* vp = S->vals + (kb - (d.z & ~1));
-        const int32_t* cp = S->cols + (kb - (d.z & ~3));
-        for (int u0 = 0; u0 < maxlen; u0 += 8) {
-            double xv[8], vv[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (u0 + u < len) {
-                    xv[u] = __ldg(x + cp[u0 + u]);
-                    vv[u] = vp[u0 + u];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (u0 + u >= maxlen) break;   // warp-uniform
-                if (u0 + u < len) sum = fma(vv[u], xv[u], sum);
-            }
-        }
+        for (int u = 0; u < maxlen; ++u)
+            if (u < len) sum = fma(S->vals[vb + u], S->xs[S->cols[cb + u] - xw0], sum);
         if (active) epilogue<EPI>(row, sum, y, e, s, a0, a1);
         __syncthreads();   // stage sidx is free again
         if (tid == 0 && !failed) {
-            const int tn = t + 2 * G;
-            if (tn < ntiles) tile_issue<CAP>(__ldg(tiles + tn), st + sidx, bar + sidx, rowptr, colidx, vals);
+            const int t2 = t + 2 * G;
+            if (t2 < ntiles)
+                tile_issue_x<CAP>(__ldg(tiles + t2), __ldg(xwin + t2), st + sidx, bar + sidx, rowptr,
+                                  colidx, vals, x);
         }
     }
     if (failed && tid == 0) {
-        // give the copies still in flight a bounded chance to land before the block exits
         for (int j = 0; j < 2; ++j) mbar_wait_bounded(bar + j, 0u);
     }
-    if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish(a0, a1, ctl, partials, f);
+    if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish<EpiRed<EPI>::value>(a0, a1, ctl, partials, f);
+}
+
+template <int EPI>
+static cudaError_t spmv_tiled_x_launch(const LaunchCtx& L, const DevCSR& A, const double* x, double* y,
+                                       EpiArgs e, FinArgs f, int gate) {
+    // two 46 KB stages per block: two blocks per SM
+    int grid = std::min(A.ntiles, std::max(1, (L.max_grid / 8) * 2));
+    spmv_tiled_x<EPI><<<grid, kTileRows, spmv_tiled_x_smem(), L.stream>>>(
+        A.tiles, A.xwin, A.ntiles, A.rowptr, A.colidx, A.vals, x, y, e, L.ctl, L.partials, f, gate);
+    if (L.launches) ++*L.launches;
+    return cudaGetLastError();
 }
 
 cudaError_t spmv_tiled_prepare() {
@@ -511,7 +684,15 @@ cudaError_t spmv_tiled_prepare() {
     TACTA_TILED_ATTR(kTileCapSmall, EPI_RESID) TACTA_TILED_ATTR(kTileCapSmall, EPI_TAPIVOT)
     TACTA_TILED_ATTR(kTileCapLarge, EPI_NONE) TACTA_TILED_ATTR(kTileCapLarge, EPI_NORM)
     TACTA_TILED_ATTR(kTileCapLarge, EPI_RESID) TACTA_TILED_ATTR(kTileCapLarge, EPI_TAPIVOT)
+    TACTA_TILED_ATTR(kTileCapSmall, EPI_RESID_F32) TACTA_TILED_ATTR(kTileCapLarge, EPI_RESID_F32)
 #undef TACTA_TILED_ATTR
+#define TACTA_TILED_X_ATTR(EPI)                                                                      \
+    if (e == cudaSuccess)                                                                            \
+        e = cudaFuncSetAttribute(spmv_tiled_x<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                 (int)spmv_tiled_x_smem());
+    TACTA_TILED_X_ATTR(EPI_NONE) TACTA_TILED_X_ATTR(EPI_NORM) TACTA_TILED_X_ATTR(EPI_RESID)
+    TACTA_TILED_X_ATTR(EPI_TAPIVOT) TACTA_TILED_X_ATTR(EPI_RESID_F32)
+#undef TACTA_TILED_X_ATTR
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -552,17 +733,28 @@ static cudaError_t spmv_dispatch(const LaunchCtx& L, int kind, const Acc& acc, c
     case EPI_NONE: return spmv_dispatch_epi<Acc, EPI_NONE>(L, kind, acc, x, y, e, f, gate);
     case EPI_NORM: return spmv_dispatch_epi<Acc, EPI_NORM>(L, kind, acc, x, y, e, f, gate);
     case EPI_RESID: return spmv_dispatch_epi<Acc, EPI_RESID>(L, kind, acc, x, y, e, f, gate);
+    case EPI_RESID_F32: return spmv_dispatch_epi<Acc, EPI_RESID_F32>(L, kind, acc, x, y, e, f, gate);
     default: return spmv_dispatch_epi<Acc, EPI_TAPIVOT>(L, kind, acc, x, y, e, f, gate);
     }
 }
 
 cudaError_t launch_spmv(const LaunchCtx& L, const DevOperand& A, const double* x, double* y,
                         int epi, EpiArgs e, FinArgs f, int gate) {
+    if (A.format == TACTA_CSR && A.csr.cfg.kind == 3) {
+        switch (epi) {
+        case EPI_NONE: return spmv_tiled_x_launch<EPI_NONE>(L, A.csr, x, y, e, f, gate);
+        case EPI_NORM: return spmv_tiled_x_launch<EPI_NORM>(L, A.csr, x, y, e, f, gate);
+        case EPI_RESID: return spmv_tiled_x_launch<EPI_RESID>(L, A.csr, x, y, e, f, gate);
+        case EPI_RESID_F32: return spmv_tiled_x_launch<EPI_RESID_F32>(L, A.csr, x, y, e, f, gate);
+        default: return spmv_tiled_x_launch<EPI_TAPIVOT>(L, A.csr, x, y, e, f, gate);
+        }
+    }
     if (A.format == TACTA_CSR && A.csr.cfg.kind == 2) {
         switch (epi) {
         case EPI_NONE: return spmv_tiled_launch<EPI_NONE>(L, A.csr, x, y, e, f, gate);
         case EPI_NORM: return spmv_tiled_launch<EPI_NORM>(L, A.csr, x, y, e, f, gate);
         case EPI_RESID: return spmv_tiled_launch<EPI_RESID>(L, A.csr, x, y, e, f, gate);
+        case EPI_RESID_F32: return spmv_tiled_launch<EPI_RESID_F32>(L, A.csr, x, y, e, f, gate);
         default: return spmv_tiled_launch<EPI_TAPIVOT>(L, A.csr, x, y, e, f, gate);
         }
     }
@@ -577,6 +769,7 @@ cudaError_t launch_spmv(const LaunchCtx& L, const DevOperand& A, const double* x
 // ------------------------------------------------------------------ vector kernels
 
 struct VecPtrs { double* p[kTMax]; };
+struct F32Ptrs { float* p[kTMax]; };
 
 // CTA update (Eqs. CTAGEN7, CTAGEN7A): x += sum alpha_i z_i, r -= sum alpha_i u_i, ||r||².
 template <int T>
@@ -605,7 +798,7 @@ cta_update(int64_t m, int64_t n, double* __restrict__ x, double* __restrict__ r,
             a0 = fma(v, v, a0);
         }
     }
-    reduce_and_finish(a0, 0.0, ctl, partials, f);
+    reduce_and_finish<1>(a0, 0.0, ctl, partials, f);
 }
 
 // TA update (Alg. 2.2): d = (1-alpha) d + alpha (b - v)  [d = b - b'],
@@ -664,6 +857,276 @@ __global__ void copy_gated(double* __restrict__ dst, const double* __restrict__ 
 __global__ void fill_kernel(double* __restrict__ dst, double v, int64_t len) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) dst[i] = v;
+}
+
+// ------------------------------------------------------------------ mixed precision: FP32 chain
+//
+// The matrix values and the chain vectors z_i, u_i, r are FP32 (half the bytes,
+// and FP32 FMAs run at ~60x the FP64 rate on GB300). Products accumulate in
+// FP32; each thread's share of a moment (sum of y² over its rows) is kept in
+// FP32 and the block / grid sums are FP64. The auxiliary solve, the stop tests
+// and every scalar stay FP64 in the finishers; the true residual b - A x is
+// computed by the FP64 product (refinement) every R steps and at stop checks.
+
+template <int CAP, bool XW>
+struct __align__(16) TileStage32 {
+    float vals[CAP + 4];
+    int32_t cols[CAP + 4];
+    int32_t rp[kTileRows + 8];
+    float xs[XW ? kXSpan + 4 : 4];
+};
+
+template <int CAP, bool XW>
+size_t spmv32_smem() { return 2 * sizeof(TileStage32<CAP, XW>); }
+
+template <int CAP, bool XW>
+__device__ __forceinline__ void tile_issue32(const int4 d, const int2 w, TileStage32<CAP, XW>* st,
+                                             uint64_t* bar, const int32_t* rowptr,
+                                             const int32_t* colidx, const float* vals, const float* x) {
+    const int a0 = d.z & ~3, c0 = d.z & ~3, r0 = d.x & ~3;
+    const uint32_t bv = d.w > d.z ? round16((uint32_t)(d.w - a0) * 4u) : 0u;
+    const uint32_t bc = d.w > d.z ? round16((uint32_t)(d.w - c0) * 4u) : 0u;
+    const uint32_t br = round16((uint32_t)(d.y + 1 - r0) * 4u);
+    uint32_t bx = 0;
+    int x0 = 0;
+    if (XW && d.w > d.z) {
+        x0 = w.x & ~3;
+        bx = round16((uint32_t)(w.y + 1 - x0) * 4u);
+    }
+    mbar_expect_tx(bar, bv + bc + br + bx);
+    if (bv) bulk_g2s(st->vals, vals + a0, bv, bar);
+    if (bc) bulk_g2s(st->cols, colidx + c0, bc, bar);
+    bulk_g2s(st->rp, rowptr + r0, br, bar);
+    if (bx) bulk_g2s(st->xs, x + x0, bx, bar);
+}
+
+template <int CAP, bool XW, int EPI>
+__global__ void __launch_bounds__(kTileRows)
+spmv32_tiled(const int4* __restrict__ tiles, const int2* __restrict__ xwin, int ntiles,
+             const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+             const float* __restrict__ vals, const float* __restrict__ x, float* __restrict__ y,
+             Ctl* ctl, double* partials, FinArgs f, int gate) {
+    if (gated_out(ctl, gate)) return;
+    if (gate != GATE_FORCE && blockIdx.x == 0 && threadIdx.x == 0) ctl->matvecs += 1;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TileStage32<CAP, XW>* st = reinterpret_cast<TileStage32<CAP, XW>*>(smem_raw);
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int failed;
+    const int tid = threadIdx.x;
+    const int G = gridDim.x;
+    const int2 nowin = make_int2(0, 0);
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
+        for (int j = 0; j < 2; ++j) {
+            const int t = blockIdx.x + j * G;
+            if (t < ntiles)
+                tile_issue32<CAP, XW>(__ldg(tiles + t), XW ? __ldg(xwin + t) : nowin, st + j, bar + j,
+                                      rowptr, colidx, vals, x);
+        }
+    }
+    __syncthreads();
+    float acc = 0.0f;
+    for (int j = 0;; ++j) {
+        const int t = blockIdx.x + j * G;
+        if (t >= ntiles) break;
+        const int sidx = j & 1;
+        const int4 d = __ldg(tiles + t);
+        const int xw0 = XW ? (__ldg(&xwin[t].x) & ~3) : 0;
+        const bool ok = !failed && mbar_wait_bounded(bar + sidx, (uint32_t)((j >> 1) & 1));
+        if (!ok) {
+            failed = 1;
+            atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+        }
+        const TileStage32<CAP, XW>* S = st + sidx;
+        const int row = d.x + tid;
+        const bool active = ok && row < d.y;
+        int kb = 0, len = 0;
+        if (active) {
+            const int r0 = d.x & ~3;
+            kb = S->rp[row - r0];
+            len = S->rp[row + 1 - r0] - kb;
+        }
+        const int vb = kb - (d.z & ~3);
+        float sum = 0.0f;
+        for (int u = 0; u < len; ++u) {
+            const int c = S->cols[vb + u];
+            const float xv = XW ? S->xs[c - xw0] : __ldg(x + c);
+            sum = fmaf(S->vals[vb + u], xv, sum);
+        }
+        if (active) {
+            y[row] = sum;
+            if (EPI == EPI_NORM) acc = fmaf(sum, sum, acc);
+        }
+        __syncthreads();
+        if (tid == 0 && !failed) {
+            const int t2 = t + 2 * G;
+            if (t2 < ntiles)
+                tile_issue32<CAP, XW>(__ldg(tiles + t2), XW ? __ldg(xwin + t2) : nowin, st + sidx,
+                                      bar + sidx, rowptr, colidx, vals, x);
+        }
+    }
+    if (failed && tid == 0) {
+        for (int j = 0; j < 2; ++j) mbar_wait_bounded(bar + j, 0u);
+    }
+    if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish<1>((double)acc, 0.0, ctl, partials, f);
+}
+
+// warp per row for long FP32 rows
+template <int EPI>
+__global__ void __launch_bounds__(kBlock)
+spmv32_warp(int64_t rows, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+            const float* __restrict__ vals, const float* __restrict__ x, float* __restrict__ y,
+            Ctl* ctl, double* partials, FinArgs f, int gate) {
+    if (gated_out(ctl, gate)) return;
+    if (gate != GATE_FORCE && blockIdx.x == 0 && threadIdx.x == 0) ctl->matvecs += 1;
+    float acc = 0.0f;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += warps) {
+        const int64_t b = __ldg(rowptr + row), en = __ldg(rowptr + row + 1);
+        float sum = 0.0f;
+        for (int64_t k = b + lane; k < en; k += 32) sum = fmaf(__ldg(vals + k), __ldg(x + __ldg(colidx + k)), sum);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+        if (lane == 0) {
+            y[row] = sum;
+            if (EPI == EPI_NORM) acc = fmaf(sum, sum, acc);
+        }
+    }
+    if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish<1>((double)acc, 0.0, ctl, partials, f);
+}
+
+template <int CAP, bool XW, int EPI>
+static cudaError_t spmv32_tiled_launch(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y,
+                                       FinArgs f, int gate) {
+    const DevCSR& a = *A.base;
+    const size_t sm = spmv32_smem<CAP, XW>();
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(6, (220u << 10) / (sm + 3072)));
+    const int grid = std::min(a.ntiles, std::max(1, (L.max_grid / 8) * per_sm));
+    spmv32_tiled<CAP, XW, EPI><<<grid, kTileRows, sm, L.stream>>>(a.tiles, a.xwin, a.ntiles, a.rowptr,
+                                                                   a.colidx, A.vals, x, y, L.ctl,
+                                                                   L.partials, f, gate);
+    if (L.launches) ++*L.launches;
+    return cudaGetLastError();
+}
+
+template <int EPI>
+static cudaError_t spmv32_epi(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y, FinArgs f,
+                              int gate) {
+    const DevCSR& a = *A.base;
+    if (a.cfg.kind == 3) return spmv32_tiled_launch<kTileCapSmall, true, EPI>(L, A, x, y, f, gate);
+    if (a.cfg.kind == 2) {
+        if (a.cap <= kTileCapSmall) return spmv32_tiled_launch<kTileCapSmall, false, EPI>(L, A, x, y, f, gate);
+        return spmv32_tiled_launch<kTileCapLarge, false, EPI>(L, A, x, y, f, gate);
+    }
+    spmv32_warp<EPI><<<L.max_grid, kBlock, 0, L.stream>>>(a.rows, a.rowptr, a.colidx, A.vals, x, y, L.ctl,
+                                                          L.partials, f, gate);
+    if (L.launches) ++*L.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv32(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y, int epi,
+                          FinArgs f, int gate) {
+    return epi == EPI_NORM ? spmv32_epi<EPI_NORM>(L, A, x, y, f, gate) : spmv32_epi<EPI_NONE>(L, A, x, y, f, gate);
+}
+
+cudaError_t spmv32_prepare() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+#define TACTA_S32_ATTR(CAP, XW, EPI)                                                                        \
+    if (e == cudaSuccess)                                                                                   \
+        e = cudaFuncSetAttribute(spmv32_tiled<CAP, XW, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                 (int)spmv32_smem<CAP, XW>());
+    TACTA_S32_ATTR(kTileCapSmall, true, EPI_NORM) TACTA_S32_ATTR(kTileCapSmall, true, EPI_NONE)
+    TACTA_S32_ATTR(kTileCapSmall, false, EPI_NORM) TACTA_S32_ATTR(kTileCapSmall, false, EPI_NONE)
+    TACTA_S32_ATTR(kTileCapLarge, false, EPI_NORM) TACTA_S32_ATTR(kTileCapLarge, false, EPI_NONE)
+#undef TACTA_S32_ATTR
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+// CTA update in FP32: dx += sum alpha_i z_i (the correction to the FP64 x since the
+// last refinement), r -= sum alpha_i u_i; ||r||² per thread in FP32, reduced in FP64.
+template <int T>
+__global__ void __launch_bounds__(kBlock)
+cta_update32(int64_t m, int64_t n, float* __restrict__ dx, float* __restrict__ r, F32Ptrs z, F32Ptrs u,
+             Ctl* ctl, double* partials, FinArgs f) {
+    if (ctl->status != 0) return;
+    float al[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) al[j] = (float)ctl->alpha[j];
+    float acc = 0.0f;
+    const int64_t len = m > n ? m : n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
+        if (i < n) {
+            float v = dx[i];
+#pragma unroll
+            for (int j = 0; j < T; ++j) v = fmaf(al[j], __ldg(z.p[j] + i), v);
+            dx[i] = v;
+        }
+        if (i < m) {
+            float v = r[i];
+#pragma unroll
+            for (int j = 0; j < T; ++j) v = fmaf(-al[j], __ldg(u.p[j] + i), v);
+            r[i] = v;
+            acc = fmaf(v, v, acc);
+        }
+    }
+    reduce_and_finish<1>((double)acc, 0.0, ctl, partials, f);
+}
+
+// x += (double) dx, dx = 0: the FP32 correction folded into the FP64 iterate
+__global__ void fold_correction(int64_t n, double* __restrict__ x, float* __restrict__ dx, const Ctl* ctl,
+                                int gate) {
+    if (gated_out(ctl, gate)) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        x[i] += (double)dx[i];
+        dx[i] = 0.0f;
+    }
+}
+
+__global__ void d2f_kernel(const double* __restrict__ src, float* __restrict__ dst, int64_t len) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) dst[i] = (float)src[i];
+}
+
+cudaError_t launch_cta_update32(const LaunchCtx& L, int t, int64_t m, int64_t n, float* dx, float* r,
+                                float* const* z, float* const* u, FinArgs f) {
+    F32Ptrs zp{}, up{};
+    for (int j = 0; j < t; ++j) { zp.p[j] = z[j]; up.p[j] = u[j]; }
+    const int g = L.max_grid;
+    switch (t) {
+    case 1: cta_update32<1><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
+    case 2: cta_update32<2><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
+    case 3: cta_update32<3><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
+    case 4: cta_update32<4><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
+    case 5: cta_update32<5><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
+    case 6: cta_update32<6><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
+    case 7: cta_update32<7><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
+    default: cta_update32<8><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
+    }
+    if (L.launches) ++*L.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold_correction(const LaunchCtx& L, int64_t n, double* x, float* dx, int gate) {
+    fold_correction<<<L.max_grid, kBlock, 0, L.stream>>>(n, x, dx, L.ctl, gate);
+    if (L.launches) ++*L.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t convert_to_f32(cudaStream_t s, const double* src, float* dst, int64_t len) {
+    int64_t blocks = (len + kBlock - 1) / kBlock;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 65536) blocks = 65536;
+    d2f_kernel<<<(unsigned)blocks, kBlock, 0, s>>>(src, dst, len);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ launchers

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -75,6 +76,16 @@ struct Plan {
     cudaGraphExec_t g_ta[2] = {nullptr, nullptr};
     int64_t g_ta_launches[2] = {0, 0};
     int g_ta_iters[2] = {0, 0};
+    // mixed precision: FP32 values of A / Aᵀ (structure shared), FP32 chain vectors
+    DevCSR32 A32, At32;
+    float* z32[kTMax] = {};
+    float* u32[kTMax] = {};
+    float* r32 = nullptr;
+    float* dx32 = nullptr;
+    cudaGraphExec_t g_cta32 = nullptr;
+    int g_cta32_key = -1;
+    int64_t g_cta32_launches = 0;
+    int g_cta32_iters = 0;
     // opt-in profiling of the iteration's products (events around each launch)
     bool profiling = false;
     std::vector<cudaEvent_t> pev;
@@ -133,6 +144,9 @@ static void free_graphs(Plan* p) {
     if (p->g_cta) cudaGraphExecDestroy(p->g_cta);
     p->g_cta = nullptr;
     p->g_cta_key = -1;
+    if (p->g_cta32) cudaGraphExecDestroy(p->g_cta32);
+    p->g_cta32 = nullptr;
+    p->g_cta32_key = -1;
     for (int i = 0; i < 2; ++i) {
         if (p->g_ta[i]) cudaGraphExecDestroy(p->g_ta[i]);
         p->g_ta[i] = nullptr;
@@ -146,12 +160,16 @@ static void plan_free(Plan* p) {
     cudaSetDevice(p->device);
     free_graphs(p);
     auto F = [](void* q) { if (q) cudaFree(q); };
-    F(p->A.csr.rowptr); F(p->A.csr.colidx); F(p->A.csr.vals); F(p->A.csr.tiles); F(p->A.dense.vals);
-    F(p->At.csr.rowptr); F(p->At.csr.colidx); F(p->At.csr.vals); F(p->At.csr.tiles); F(p->At.dense.vals);
+    F(p->A.csr.rowptr); F(p->A.csr.colidx); F(p->A.csr.vals); F(p->A.csr.tiles); F(p->A.csr.xwin);
+    F(p->A.dense.vals);
+    F(p->At.csr.rowptr); F(p->At.csr.colidx); F(p->At.csr.vals); F(p->At.csr.tiles); F(p->At.csr.xwin);
+    F(p->At.dense.vals);
     F(p->ctl); F(p->partials); F(p->flag_dev);
     F(p->b); F(p->x); F(p->r); F(p->tmp_m); F(p->tmp_n);
     for (int i = 0; i < kTMax; ++i) { F(p->z[i]); F(p->u[i]); }
     F(p->d); F(p->c); F(p->v); F(p->bt); F(p->xbest); F(p->wx); F(p->wd); F(p->hist);
+    F(p->A32.vals); F(p->At32.vals); F(p->r32); F(p->dx32);
+    for (int i = 0; i < kTMax; ++i) { F(p->z32[i]); F(p->u32[i]); }
     if (p->stage) cudaFreeHost(p->stage);
     if (p->poll) cudaFreeHost(p->poll);
     if (p->flag_host) cudaFreeHost(p->flag_host);
@@ -195,6 +213,29 @@ static cudaError_t setup_csr_kernel(DevCSR& a, cudaStream_t s) {
     a.ntiles = (int)tiles.size();
     a.cap = cap;
     a.cfg.kind = 2;
+    // banded? every tile's columns within a window of kXSpan entries of x (aligned start)
+    if (cap == kTileCapSmall && a.nnz > 0) {
+        std::vector<int32_t> ci((size_t)a.nnz);
+        if ((e = cudaMemcpyAsync(ci.data(), a.colidx, sizeof(int32_t) * a.nnz, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        std::vector<int2> win(tiles.size());
+        bool banded = true;
+        for (size_t t = 0; t < tiles.size() && banded; ++t) {
+            int lo = INT32_MAX, hi = -1;
+            for (int k = tiles[t].z; k < tiles[t].w; ++k) { lo = std::min(lo, ci[k]); hi = std::max(hi, ci[k]); }
+            if (hi < 0) { lo = 0; hi = 0; }
+            win[t] = make_int2(lo, hi);
+            if (hi - (lo & ~1) + 1 > kXSpan) banded = false;
+        }
+        if (banded) {
+            if ((e = cudaMalloc(&a.xwin, sizeof(int2) * win.size())) != cudaSuccess) return e;
+            if ((e = cudaMemcpyAsync(a.xwin, win.data(), sizeof(int2) * win.size(), cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess) return e;
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+            a.cfg.kind = 3;
+        }
+    }
     return spmv_tiled_prepare();
 }
 
@@ -205,6 +246,10 @@ static tacta_status validate_opts(const tacta_options& o) {
     if (o.max_iter < 0) { set_error("max_iter must be >= 0"); return TACTA_ERR_INVALID; }
     if (o.recompute_every < 0) { set_error("recompute_every must be >= 0"); return TACTA_ERR_INVALID; }
     if (o.cycle < 0 || o.cycle > 2) { set_error("unknown cycle"); return TACTA_ERR_INVALID; }
+    if (o.precision != TACTA_PRECISION_FP64 && o.precision != TACTA_PRECISION_MIXED) {
+        set_error("unknown precision");
+        return TACTA_ERR_INVALID;
+    }
     return TACTA_OK;
 }
 
@@ -288,18 +333,24 @@ static tacta_status plan_create(const tacta_matrix* M, const tacta_options* opt,
     PTRY(cudaMallocHost(&p->stage, sizeof(Ctl)));
     PTRY(cudaMallocHost(&p->poll, 2 * sizeof(int32_t)));
     PTRY(cudaMalloc(&p->partials, sizeof(double) * 2 * p->grid));
-    PTRY(cudaMalloc(&p->b, sizeof(double) * m));
-    PTRY(cudaMalloc(&p->x, sizeof(double) * n));
-    PTRY(cudaMalloc(&p->r, sizeof(double) * m));
-    PTRY(cudaMalloc(&p->tmp_m, sizeof(double) * m));
-    PTRY(cudaMalloc(&p->tmp_n, sizeof(double) * n));
-    PTRY(cudaMalloc(&p->d, sizeof(double) * mn));
-    PTRY(cudaMalloc(&p->c, sizeof(double) * n));
-    PTRY(cudaMalloc(&p->v, sizeof(double) * mn));
-    PTRY(cudaMalloc(&p->bt, sizeof(double) * n));
-    PTRY(cudaMalloc(&p->xbest, sizeof(double) * n));
-    PTRY(cudaMalloc(&p->wx, sizeof(double) * n));
-    PTRY(cudaMalloc(&p->wd, sizeof(double) * mn));
+    // every vector that a product may read carries kPadVec doubles of zeroed padding
+    auto vec = [&](double** ptr, int64_t len) {
+        cudaError_t e2 = cudaMalloc(ptr, sizeof(double) * (len + kPadVec));
+        if (e2 == cudaSuccess) e2 = cudaMemsetAsync(*ptr, 0, sizeof(double) * (len + kPadVec), s);
+        return e2;
+    };
+    PTRY(vec(&p->b, m));
+    PTRY(vec(&p->x, n));
+    PTRY(vec(&p->r, m));
+    PTRY(vec(&p->tmp_m, m));
+    PTRY(vec(&p->tmp_n, n));
+    PTRY(vec(&p->d, mn));
+    PTRY(vec(&p->c, n));
+    PTRY(vec(&p->v, mn));
+    PTRY(vec(&p->bt, n));
+    PTRY(vec(&p->xbest, n));
+    PTRY(vec(&p->wx, n));
+    PTRY(vec(&p->wd, mn));
     PTRY(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     for (int i = 0; i < 2; ++i) PTRY(cudaEventCreateWithFlags(&p->ev[i], cudaEventDisableTiming));
     PTRY(cudaStreamSynchronize(s));
@@ -312,8 +363,10 @@ static tacta_status ensure_chain(Plan* p, int t_max) {
     for (int i = 0; i < t_max; ++i) {
         if (!p->z[i]) {
             free_graphs(p);
-            CUDA_TRY(cudaMalloc(&p->z[i], sizeof(double) * p->n));
-            CUDA_TRY(cudaMalloc(&p->u[i], sizeof(double) * p->m));
+            CUDA_TRY(cudaMalloc(&p->z[i], sizeof(double) * (p->n + kPadVec)));
+            CUDA_TRY(cudaMalloc(&p->u[i], sizeof(double) * (p->m + kPadVec)));
+            CUDA_TRY(cudaMemset(p->z[i], 0, sizeof(double) * (p->n + kPadVec)));
+            CUDA_TRY(cudaMemset(p->u[i], 0, sizeof(double) * (p->m + kPadVec)));
         }
     }
     return TACTA_OK;
@@ -330,6 +383,61 @@ static tacta_status ensure_hist(Plan* p, int64_t cap) {
     return TACTA_OK;
 }
 
+// FP32 copies and vectors of the mixed-precision path (made on first use)
+static tacta_status ensure_mixed(Plan* p, int t_max, cudaStream_t s) {
+    if (p->A.format != TACTA_CSR) {
+        set_error("mixed precision needs A in CSR format");
+        return TACTA_ERR_INVALID;
+    }
+    auto f32 = [&](float** ptr, int64_t len) {
+        cudaError_t e = cudaMalloc(ptr, sizeof(float) * (len + kPadVec32));
+        if (e == cudaSuccess) e = cudaMemsetAsync(*ptr, 0, sizeof(float) * (len + kPadVec32), s);
+        return e;
+    };
+    if (!p->A32.vals) {
+        free_graphs(p);
+        for (DevCSR32* a : {&p->A32, &p->At32}) {
+            const DevCSR& base = (a == &p->A32) ? p->A.csr : p->At.csr;
+            a->base = &base;
+            CUDA_TRY(cudaMalloc(&a->vals, sizeof(float) * (base.nnz + kPadVals32)));
+            CUDA_TRY(cudaMemsetAsync(a->vals, 0, sizeof(float) * (base.nnz + kPadVals32), s));
+            if (base.nnz > 0) CUDA_TRY(convert_to_f32(s, base.vals, a->vals, base.nnz));
+        }
+        CUDA_TRY(f32(&p->r32, p->m));
+        CUDA_TRY(f32(&p->dx32, p->n));
+        CUDA_TRY(spmv32_prepare());
+    }
+    for (int i = 0; i < t_max; ++i) {
+        if (!p->z32[i]) {
+            free_graphs(p);
+            CUDA_TRY(f32(&p->z32[i], p->n));
+            CUDA_TRY(f32(&p->u32[i], p->m));
+        }
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return TACTA_OK;
+}
+
+// One F_t step, mixed precision: FP32 chain and update, then (gated on the device)
+// the refinement: fold the FP32 correction into the FP64 x and recompute the true
+// residual b - A x with the FP64 product, stored back into the FP32 residual.
+static cudaError_t enqueue_cta32_iter(Plan* p, const LaunchCtx& L, int t) {
+    cudaError_t e;
+    const float* uprev = p->r32;
+    for (int i = 0; i < t; ++i) {
+        if ((e = launch_spmv32(L, p->At32, uprev, p->z32[i], EPI_NORM, FinArgs{FIN_PHI, 2 * i + 1, nullptr},
+                               GATE_ALWAYS)) != cudaSuccess) return e;
+        FinArgs f = (i == t - 1) ? FinArgs{FIN_CTA_STEP, t, nullptr} : FinArgs{FIN_PHI, 2 * i + 2, nullptr};
+        if ((e = launch_spmv32(L, p->A32, p->z32[i], p->u32[i], EPI_NORM, f, GATE_ALWAYS)) != cudaSuccess) return e;
+        uprev = p->u32[i];
+    }
+    if ((e = launch_cta_update32(L, t, p->m, p->n, p->dx32, p->r32, p->z32, p->u32,
+                                 FinArgs{FIN_CTA_UPDATE, 0, p->hist})) != cudaSuccess) return e;
+    if ((e = launch_fold_correction(L, p->n, p->x, p->dx32, GATE_NEED_TRUE)) != cudaSuccess) return e;
+    return launch_spmv(L, p->A, p->x, p->tmp_m, EPI_RESID_F32, EpiArgs{p->b, nullptr, p->r32},
+                       FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE);
+}
+
 // ------------------------------------------------------------------ options
 
 struct Opts {
@@ -343,7 +451,7 @@ static Opts resolve(const tacta_options* opt) {
     if (opt) r.o = *opt;
     if (r.o.tol_normal < 0.0) r.o.tol_normal = r.o.tol;
     if (!(r.o.tol_cta > 0.0)) r.o.tol_cta = r.o.tol;
-    if (!(r.o.pivot_tol > 0.0)) r.o.pivot_tol = 1e-12;
+    if (!(r.o.pivot_tol > 0.0)) r.o.pivot_tol = r.o.precision == TACTA_PRECISION_MIXED ? 1e-6 : 1e-12;
     if (r.o.poll_every < 1) r.o.poll_every = 64;
     r.s = (cudaStream_t)r.o.stream;
     return r;
@@ -368,7 +476,7 @@ static int schedule_period(int t_max, int cycle) {
 static cudaError_t enqueue_cta_iter(Plan* p, const LaunchCtx& L, int t) {
     cudaError_t e;
     const double* uprev = p->r;
-    EpiArgs none{nullptr, nullptr};
+    EpiArgs none{nullptr, nullptr, nullptr};
     for (int i = 0; i < t; ++i) {
         if ((e = chain_spmv(p, L, p->At, uprev, p->z[i], EPI_NORM, none, FinArgs{FIN_PHI, 2 * i + 1, nullptr},
                             GATE_ALWAYS)) != cudaSuccess) return e;
@@ -378,7 +486,7 @@ static cudaError_t enqueue_cta_iter(Plan* p, const LaunchCtx& L, int t) {
     }
     if ((e = launch_cta_update(L, t, p->m, p->n, p->x, p->r, p->z, p->u,
                                FinArgs{FIN_CTA_UPDATE, 0, p->hist})) != cudaSuccess) return e;
-    return launch_spmv(L, p->A, p->x, p->r, EPI_RESID, EpiArgs{p->b, nullptr},
+    return launch_spmv(L, p->A, p->x, p->r, EPI_RESID, EpiArgs{p->b, nullptr, nullptr},
                        FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE);
 }
 
@@ -386,7 +494,7 @@ static cudaError_t enqueue_cta_iter(Plan* p, const LaunchCtx& L, int t) {
 static cudaError_t apply_M(Plan* p, const LaunchCtx& L, int normal, const double* in, double* out,
                            int epi, EpiArgs e, FinArgs f, int gate) {
     if (!normal) return launch_spmv(L, p->A, in, out, epi, e, f, gate);
-    cudaError_t err = launch_spmv(L, p->A, in, p->tmp_m, EPI_NONE, EpiArgs{nullptr, nullptr},
+    cudaError_t err = launch_spmv(L, p->A, in, p->tmp_m, EPI_NONE, EpiArgs{nullptr, nullptr, nullptr},
                                   FinArgs{FIN_NONE, 0, nullptr}, gate);
     if (err != cudaSuccess) return err;
     return launch_spmv(L, p->At, p->tmp_m, out, epi, e, f, gate);
@@ -401,7 +509,7 @@ static cudaError_t enqueue_ta_iter(Plan* p, const LaunchCtx& L, int normal, doub
     cudaError_t e;
     const double* rhs = normal ? p->bt : p->b;
     const int64_t mm = normal ? p->n : p->m;
-    EpiArgs none{nullptr, nullptr};
+    EpiArgs none{nullptr, nullptr, nullptr};
     // c = Mᵀ (b - b'), ||c||², pivot test (Eq. eqlem2) / rho growth
     if (!normal) {
         if ((e = chain_spmv(p, L, p->At, p->d, p->c, EPI_NORM, none, FinArgs{FIN_TA_C, 0, nullptr},
@@ -409,11 +517,11 @@ static cudaError_t enqueue_ta_iter(Plan* p, const LaunchCtx& L, int normal, doub
     } else if ((e = apply_Mt(p, L, normal, p->d, p->c, EPI_NORM, none, FinArgs{FIN_TA_C, 0, nullptr},
                              GATE_ALWAYS)) != cudaSuccess) return e;
     // v = rho M c / ||c|| (Eq. vr) with the dots of Eq. alph
-    if ((e = apply_M(p, L, normal, p->c, p->v, EPI_TAPIVOT, EpiArgs{rhs, p->d},
+    if ((e = apply_M(p, L, normal, p->c, p->v, EPI_TAPIVOT, EpiArgs{rhs, p->d, nullptr},
                      FinArgs{FIN_TA_V, 0, nullptr}, GATE_PIVOT)) != cudaSuccess) return e;
     if ((e = launch_ta_update(L, mm, p->n, p->x, p->d, rhs, p->v, p->c,
                               FinArgs{FIN_TA_UPDATE, 0, hist})) != cudaSuccess) return e;
-    return apply_M(p, L, normal, p->x, p->d, EPI_RESID, EpiArgs{rhs, nullptr},
+    return apply_M(p, L, normal, p->x, p->d, EPI_RESID, EpiArgs{rhs, nullptr, nullptr},
                    FinArgs{FIN_TRUE_RES, 0, hist}, GATE_NEED_TRUE);
 }
 
@@ -514,9 +622,9 @@ static tacta_status status_of(int reason) {
 // true ||b - A x||² and ||Aᵀ(b - A x)||² at exit, into ctl->red[0], ctl->red[2]
 static tacta_status exit_residuals(Plan* p, const Opts& O, const double* x, int64_t* launches) {
     LaunchCtx L{O.s, p->ctl, p->partials, p->grid, launches};
-    CUDA_TRY(launch_spmv(L, p->A, x, p->tmp_m, EPI_RESID, EpiArgs{p->b, nullptr},
+    CUDA_TRY(launch_spmv(L, p->A, x, p->tmp_m, EPI_RESID, EpiArgs{p->b, nullptr, nullptr},
                          FinArgs{FIN_STORE, 0, nullptr}, GATE_FORCE));
-    CUDA_TRY(launch_spmv(L, p->At, p->tmp_m, p->tmp_n, EPI_NORM, EpiArgs{nullptr, nullptr},
+    CUDA_TRY(launch_spmv(L, p->At, p->tmp_m, p->tmp_n, EPI_NORM, EpiArgs{nullptr, nullptr, nullptr},
                          FinArgs{FIN_STORE, 2, nullptr}, GATE_FORCE));
     return TACTA_OK;
 }
@@ -563,18 +671,26 @@ static tacta_status store_out(Plan* p, const Opts& O, const VecIO& io, const dou
 // Runs CTA from x0 (or 0) on the plan's b; leaves x in p->x and the final control block in p->stage.
 static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t hist_cap, int64_t* launches) {
     tacta_status st;
-    if ((st = ensure_chain(p, O.o.t_max)) != TACTA_OK) return st;
+    const bool mixed = O.o.precision == TACTA_PRECISION_MIXED;
+    if (mixed && (st = ensure_mixed(p, O.o.t_max, O.s)) != TACTA_OK) return st;
+    if (!mixed && (st = ensure_chain(p, O.o.t_max)) != TACTA_OK) return st;
     if ((st = ensure_hist(p, std::max<int64_t>(hist_cap, 1))) != TACTA_OK) return st;
     LaunchCtx L{O.s, p->ctl, p->partials, p->grid, launches};
     Ctl h = base_ctl(O, hist_cap);
-    h.need_true = x0 ? 1 : 0;
+    h.need_true = (x0 || mixed) ? 1 : 0;
     if ((st = write_ctl(p, O.s, h)) != TACTA_OK) return st;
-    EpiArgs none{nullptr, nullptr};
+    EpiArgs none{nullptr, nullptr, nullptr};
     CUDA_TRY(launch_reduce_vec(L, p->m, p->b, nullptr, FinArgs{FIN_SETUP_B, 0, nullptr}, GATE_ALWAYS));
     CUDA_TRY(launch_spmv(L, p->At, p->b, p->tmp_n, EPI_NORM, none, FinArgs{FIN_SETUP_MTB, 0, nullptr}, GATE_ALWAYS));
-    if (x0) {
+    if (mixed) {
+        if (x0) CUDA_TRY(cudaMemcpyAsync(p->x, x0, sizeof(double) * p->n, cudaMemcpyDefault, O.s));
+        else CUDA_TRY(cudaMemsetAsync(p->x, 0, sizeof(double) * p->n, O.s));
+        CUDA_TRY(cudaMemsetAsync(p->dx32, 0, sizeof(float) * p->n, O.s));
+        CUDA_TRY(launch_spmv(L, p->A, p->x, p->tmp_m, EPI_RESID_F32, EpiArgs{p->b, nullptr, p->r32},
+                             FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE));
+    } else if (x0) {
         CUDA_TRY(cudaMemcpyAsync(p->x, x0, sizeof(double) * p->n, cudaMemcpyDefault, O.s));
-        CUDA_TRY(launch_spmv(L, p->A, p->x, p->r, EPI_RESID, EpiArgs{p->b, nullptr},
+        CUDA_TRY(launch_spmv(L, p->A, p->x, p->r, EPI_RESID, EpiArgs{p->b, nullptr, nullptr},
                              FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE));
     } else {
         CUDA_TRY(cudaMemsetAsync(p->x, 0, sizeof(double) * p->n, O.s));
@@ -584,17 +700,22 @@ static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t h
     const int t_max = O.o.t_max, cycle = O.o.cycle;
     const int period = schedule_period(t_max, cycle);
     const int key = t_max * 4 + cycle;
-    if (p->g_cta && p->g_cta_key != key) {
-        cudaGraphExecDestroy(p->g_cta);
-        p->g_cta = nullptr;
+    cudaGraphExec_t* g = mixed ? &p->g_cta32 : &p->g_cta;
+    int* gkey = mixed ? &p->g_cta32_key : &p->g_cta_key;
+    if (*g && *gkey != key) {
+        cudaGraphExecDestroy(*g);
+        *g = nullptr;
     }
-    p->g_cta_key = key;
+    *gkey = key;
     auto body = [&](const LaunchCtx& LL, int64_t k) {
-        return enqueue_cta_iter(p, LL, schedule(k, t_max, cycle));
+        const int t = schedule(k, t_max, cycle);
+        return mixed ? enqueue_cta32_iter(p, LL, t) : enqueue_cta_iter(p, LL, t);
     };
-    st = run_loop(p, O, O.o.max_iter, period, O.o.use_graph != 0, &p->g_cta, &p->g_cta_launches,
-                  &p->g_cta_iters, body, launches);
+    st = run_loop(p, O, O.o.max_iter, period, O.o.use_graph != 0, g,
+                  mixed ? &p->g_cta32_launches : &p->g_cta_launches,
+                  mixed ? &p->g_cta32_iters : &p->g_cta_iters, body, launches);
     if (st != TACTA_OK) return st;
+    if (mixed) CUDA_TRY(launch_fold_correction(L, p->n, p->x, p->dx32, GATE_FORCE));
     CUDA_TRY(cudaGetLastError());
     return TACTA_OK;
 }
@@ -647,13 +768,13 @@ static tacta_status ta_setup(Plan* p, const Opts& O, int normal, const double* x
     LaunchCtx L{O.s, p->ctl, p->partials, p->grid, launches};
     const double* rhs = normal ? p->bt : p->b;
     const int64_t mm = normal ? p->n : p->m;
-    EpiArgs none{nullptr, nullptr};
+    EpiArgs none{nullptr, nullptr, nullptr};
     CUDA_TRY(launch_reduce_vec(L, mm, rhs, nullptr, FinArgs{FIN_SETUP_B, 0, nullptr}, GATE_ALWAYS));
     CUDA_TRY(apply_Mt(p, L, normal, rhs, p->tmp_n, EPI_NORM, none, FinArgs{FIN_SETUP_MTB, 0, nullptr}, GATE_ALWAYS));
     if (x0) {
         CUDA_TRY(cudaMemcpyAsync(p->x, x0, sizeof(double) * p->n, cudaMemcpyDefault, O.s));
         CUDA_TRY(launch_reduce_vec(L, p->n, p->x, nullptr, FinArgs{FIN_SETUP_RHO, 0, nullptr}, GATE_ALWAYS));
-        CUDA_TRY(apply_M(p, L, normal, p->x, p->d, EPI_RESID, EpiArgs{rhs, nullptr},
+        CUDA_TRY(apply_M(p, L, normal, p->x, p->d, EPI_RESID, EpiArgs{rhs, nullptr, nullptr},
                          FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE));
     } else {
         CUDA_TRY(cudaMemsetAsync(p->x, 0, sizeof(double) * p->n, O.s));
@@ -746,7 +867,7 @@ static tacta_status plan_minnorm(Plan* p, const VecIO& io, const tacta_options* 
     const double rel_res = std::sqrt(c1.red[0] / c1.bn2);
     const int normal = rel_res <= O.o.tol_cta ? 0 : 1;
     // phase 2: Algorithm 2.5 on (A, b) or (AᵀA, Aᵀb)
-    EpiArgs none{nullptr, nullptr};
+    EpiArgs none{nullptr, nullptr, nullptr};
     if (normal)
         CUDA_TRY(launch_spmv(L, p->At, p->b, p->bt, EPI_NONE, none, FinArgs{FIN_NONE, 0, nullptr}, GATE_FORCE));
     CUDA_TRY(cudaMemcpyAsync(p->xbest, p->x, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
@@ -852,6 +973,7 @@ void tacta_default_options(tacta_options* o) {
     o->use_graph = 1;
     o->poll_every = 64;
     o->profile = 0;
+    o->precision = TACTA_PRECISION_FP64;
     o->stream = nullptr;
 }
 
