@@ -127,6 +127,93 @@ def problem():
     return gen.convdiff_stencil(GRID)
 
 
+def aggregate(dist, device, local_ms: float, local_units: int):
+    """Whole-job figures over ranks: the slowest rank's time and the sum of the
+    units (F_t iterations) all ranks processed. With one process, the local values."""
+    if dist is None:
+        return local_ms, local_units
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
+def timed_solve(plan, b, stream, **kw):
+    """One plan CTA solve timed with CUDA events on the launching stream (ms, x, info)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    x, _, info = plan.cta(b, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), x, info
+
+
+def extra_workloads(tacta, dev, stream, plan_stencil, b_stencil, steps):
+    """The other configurations, each timed with device events (inputs resident):
+    the mixed-precision rate on the benchmark stencil, time to 1e-8 on the LP-like
+    rectangular system (FP64 and mixed), and the Clement rate."""
+    import gen
+    import numpy as np
+    import torch
+    out = {}
+    opts = dict(tol=TOL, tol_normal=0.0, max_iter=ITERS_PER_STEP, precision=tacta.PRECISION_MIXED)
+    for _ in range(2):
+        plan_stencil.cta(b_stencil, **opts)
+    ms, its = 0.0, 0
+    for _ in range(steps):
+        t, _, info = timed_solve(plan_stencil, b_stencil, stream, **opts)
+        ms += t
+        its += info["iters"]
+    out["cta_mixed_convdiff_1000x1000"] = {
+        "value": its / (ms * 1e-3), "unit": UNIT, "steps": steps, "iters_per_step": ITERS_PER_STEP,
+        "dtype": "f32 chain (values, vectors, products), f64 moments reduction, centering solve, "
+                 "stop tests and residual refinement every 40 steps"}
+    # LP-like rectangular min-norm system, 10,000 x 1,000,000, 31.6M nonzeros: time to 1e-8
+    p = gen.lp_rect()
+    A = tacta.CSR(torch.from_numpy(p.rowptr).to(dev), torch.from_numpy(p.colidx).to(dev),
+                  torch.from_numpy(p.vals).to(dev), (p.m, p.n))
+    b = torch.from_numpy(p.b).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = tacta.Plan(A)
+    plan_s = time.perf_counter() - t0
+    res = {"workload": "lp_rect_10000x1000000 (30 nnz per column, 500 duplicated scaled rows)",
+           "nnz": p.nnz, "plan_build_s": plan_s, "tol": TOL}
+    xs = {}
+    for name, prec in (("fp64", tacta.PRECISION_FP64), ("mixed", tacta.PRECISION_MIXED)):
+        kw = dict(tol=TOL, tol_normal=0.0, max_iter=5000, precision=prec)
+        plan.cta(b, **kw)                                   # warm (graph capture, FP32 copies)
+        best = None
+        for _ in range(3):
+            t, x, info = timed_solve(plan, b, stream, **kw)
+            best = t if best is None else min(best, t)
+        xs[name] = x.double()
+        res[name] = {"time_to_tol_ms": best, "iters": info["iters"], "rel_res": info["rel_res"],
+                     "reason": info["reason_name"]}
+    res["mixed_vs_fp64_rel_x_diff"] = float(torch.linalg.norm(xs["mixed"] - xs["fp64"]) /
+                                            torch.linalg.norm(xs["fp64"]))
+    res["speedup_mixed_over_fp64"] = res["fp64"]["time_to_tol_ms"] / res["mixed"]["time_to_tol_ms"]
+    out["time_to_1e-8_lp_rect"] = res
+    plan.close()
+    # Clement n = 100001 (singular, b in range): F_t rate over a fixed budget
+    q = gen.clement(100001)
+    Aq = tacta.CSR(torch.from_numpy(q.rowptr).to(dev), torch.from_numpy(q.colidx).to(dev),
+                   torch.from_numpy(q.vals).to(dev), (q.m, q.n))
+    bq = torch.from_numpy(q.b).to(dev)
+    plan = tacta.Plan(Aq)
+    kw = dict(tol=TOL, tol_normal=0.0, max_iter=20000)
+    plan.cta(bq, **kw)
+    t, x, info = timed_solve(plan, bq, stream, **kw)
+    out["cta_fp64_clement_100001"] = {"value": info["iters"] / (t * 1e-3), "unit": UNIT,
+                                      "iters": info["iters"], "rel_res": info["rel_res"]}
+    plan.close()
+    return out
+
+
 def cpu_baseline(p, iters):
     import oracle
     A = oracle.make_operator(p)
@@ -171,6 +258,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tacta", choices=["tacta", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
     ap.add_argument("--iters", type=int, default=ITERS_PER_STEP,
                     help="F_t iterations per step (default %(default)s; smaller for profiler runs)")
     args = ap.parse_args()
@@ -230,12 +318,8 @@ def main():
     if dist:
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * sum(iters) / (total_ms * 1e-3)
+    total_ms, all_iters = aggregate(dist, dev, sum(step_ms), sum(iters))
+    value = all_iters / (total_ms * 1e-3)
     clocks = clk.summary()
     last = infos[-1]
 
@@ -280,6 +364,8 @@ def main():
             "rel_res_after_step": last["rel_res"], "time_to_tol_s": None,
             "matvecs_per_s": world * sum(i["matvecs"] for i in infos) / (total_ms * 1e-3),
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    if rank == 0 and not args.no_extra:
+        line["extra"] = extra_workloads(tacta, dev, stream, plan, b, min(args.steps, 5))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, r = cpu_baseline(p, CPU_SAMPLE_ITERS)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -74,7 +74,8 @@ enum {
     TACTA_REASON_GAP = 6,        /* Alg. 2.5: rho_upper - rho_lower <= tol ||x_eps||        */
     TACTA_REASON_ZERO_RHS = 7,   /* b = 0: x = 0                                            */
     TACTA_REASON_NONFINITE = 8,
-    TACTA_REASON_TIMEOUT = 9     /* a bounded wait inside a kernel gave up (TACTA_ERR_TIMEOUT) */
+    TACTA_REASON_TIMEOUT = 9,    /* a bounded wait inside a kernel gave up (TACTA_ERR_TIMEOUT) */
+    TACTA_REASON_RHO_BOUND = 10  /* ta_solve: rho passed opt->rho_max                          */
 };
 
 enum { TACTA_DENSE = 0, TACTA_CSR = 1 };
@@ -106,8 +107,18 @@ typedef struct {
     int32_t poll_every;      /* host checks the device stop flag every this many iterations    */
     int32_t profile;         /* 1: time every product of the iteration with CUDA events on the
                                 stream (forces use_graph = 0); results in tacta_info.spmv_*    */
+    int32_t precision;       /* TACTA_PRECISION_FP64 (default) or TACTA_PRECISION_MIXED (CSR,
+                                cta_solve / plan_cta / minnorm's CTA phase): FP32 chain products
+                                and updates, FP64 centering solve, stop tests and refinement
+                                b - A x every recompute_every steps; pivot_tol <= 0 then means 1e-6 */
+    int32_t nonneg;          /* ta_solve only: 1 = TA for LP feasibility A x = b, x >= 0 (Sec. 6):
+                                c is replaced by max(c, 0); WITNESS when ||max(c,0)|| <=
+                                tol_normal ||Aᵀb|| while (b - b')ᵀb > 0 (Farkas certificate)   */
+    double rho_max;          /* ta_solve: stop (reason RHO_BOUND) once rho exceeds this; <= 0: none */
     void* stream;            /* cudaStream_t (NULL: legacy default stream)                      */
 } tacta_options;
+
+enum { TACTA_PRECISION_FP64 = 0, TACTA_PRECISION_MIXED = 1 };
 
 typedef struct {
     int32_t status;          /* same as the return value                               */
@@ -132,7 +143,7 @@ typedef struct {
 
 /* Fill *opt with the defaults: tol 1e-10, tol_normal -1, tol_cta 0, pivot_tol 1e-12,
    max_iter 1000, t_max 5, ping-pong cycle, R = 40, use_graph 1, poll_every 64, profile 0,
-   NULL stream. */
+   precision FP64, nonneg 0, rho_max 0 (none), NULL stream. */
 void tacta_default_options(tacta_options* opt);
 
 /*
@@ -178,6 +189,24 @@ tacta_status tacta_plan_minnorm(tacta_plan plan, const double* b, const double* 
                                 const tacta_options* opt, double* x_out, double* hist,
                                 int32_t hist_cap, tacta_info* info);
 void tacta_plan_destroy(tacta_plan plan);
+
+/* tacta_plan_transpose -- a new plan for Aᵀ built from the device copy held by `plan`
+   (used by adjoint solves: the backward of a solve with A solves with Aᵀ). The new plan's
+   vector pointers follow the same on_device flag. */
+tacta_status tacta_plan_transpose(tacta_plan plan, const tacta_options* opt, tacta_plan* out);
+
+/* tacta_plan_matvec -- y = A x (transpose = 0) or y = Aᵀ x (transpose = 1) with the plan's
+   product kernels; x and y follow the plan's on_device flag (lengths n / m, or m / n). */
+tacta_status tacta_plan_matvec(tacta_plan plan, int32_t transpose, const double* x, double* y,
+                               const tacta_options* opt);
+
+/* tacta_plan_outer -- out[k] += alpha * u[row(k)] * v[col(k)] for every stored entry k of A
+   (CSR: in the caller's nonzero order; dense: row-major m*n). With u = -lambda, v = x it
+   forms the gradient dL/dA of x = A^{-1} b on A's pattern (Sec. 3 solves made
+   differentiable; the paper has no counterpart). u: m values, v: n values, out: the
+   caller's value array layout; all follow the plan's on_device flag. */
+tacta_status tacta_plan_outer(tacta_plan plan, double alpha, const double* u, const double* v,
+                              double* out, const tacta_options* opt);
 
 /*
  * tacta_residual_static -- r = b - A x with ||r||² and rᵀb, allocating nothing.

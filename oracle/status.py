@@ -25,3 +25,4 @@ class Reason(IntEnum):
     GAP = 6         # Alg. 2.5: rho_upper - rho_lower <= gap tolerance
     ZERO_RHS = 7    # b = 0: x = 0 is the minimum-norm solution
     NONFINITE = 8
+    RHO_BOUND = 10  # TA with x >= 0 (Sec. 6): rho passed its termination bound

@@ -60,9 +60,18 @@ class TAResult:
 
 
 def _ta_loop(M, b, x, bp, rho, grow_rho, tol, tol_normal, max_iter, recompute_every, mtb_n2,
-             observer=None):
+             observer=None, nonneg=False, rho_max=math.inf):
     """The TA while-loop shared by Alg. 2.1 (grow_rho=False: a failed pivot
-    test is a witness, STOP) and Alg. 2.2 (grow_rho=True: rho grows)."""
+    test is a witness, STOP) and Alg. 2.2 (grow_rho=True: rho grows).
+
+    nonneg=True is the LP-feasibility form of Sec. 6: c is replaced by
+    c_+ = max(c, 0) (Eq. vrend2: the maximiser of c_+ᵀx over {Ax in E_{A,rho}, x >= 0}
+    is rho c_+/||c_+||), so every iterate stays x' >= 0. Reading where the section is
+    silent: when c_+ = 0 the maximiser is x = 0 (v = 0), still a strict pivot if
+    (b-b')ᵀb <= 0; if ||c_+|| <= tol_normal ||Aᵀb|| and (b-b')ᵀb > 0 then d = b - b'
+    certifies infeasibility up to that tolerance (Farkas: Aᵀd <= 0, bᵀd > 0) and the
+    loop stops with WITNESS. The normal-equation stop does not apply; rho growing past
+    rho_max (the section's termination bound) ends the loop with RHO_BOUND."""
     bn2 = float(b @ b)
     res_thr = tol * tol * bn2
     nrm_thr = tol_normal * tol_normal * mtb_n2
@@ -91,19 +100,28 @@ def _ta_loop(M, b, x, bp, rho, grow_rho, tol, tol_normal, max_iter, recompute_ev
             status, reason = Status.MAXITER, Reason.MAXITER
             break
         c = M.rmatvec(d)
+        if nonneg:
+            c = np.maximum(c, 0.0)
         cn2 = float(c @ c)
         db = float(d @ b)
         if not (math.isfinite(cn2) and math.isfinite(db)):
             status, reason = Status.NONFINITE, Reason.NONFINITE
             break
         cn = math.sqrt(cn2)
-        if cn2 <= nrm_thr:
+        if nonneg:
+            # c_+ = 0 and (b-b')ᵀb > 0: d = b - b' has Aᵀd <= 0 and bᵀd > 0, a Farkas
+            # certificate that A x = b, x >= 0 has no solution (a witness for every rho)
+            if cn2 <= nrm_thr and db > 0.0:
+                status, reason = Status.WITNESS, Reason.WITNESS
+                break
+        elif cn2 <= nrm_thr:
             status, reason = Status.OK, Reason.NORMAL
             break
         alpha = None
         if rho * cn >= db:
-            # strict pivot v = rho A c / ||c|| (Thm. prop0TA) and step (Prop. prop1TA)
-            s = rho / cn
+            # strict pivot v = rho A c / ||c|| (Thm. prop0TA) and step (Prop. prop1TA);
+            # with c_+ = 0 the maximiser over {||x|| <= rho, x >= 0} is x = 0, so v = 0
+            s = rho / cn if cn > 0.0 else 0.0
             v = s * M.matvec(c)
             w = v - bp
             num = float(d @ w)
@@ -116,6 +134,9 @@ def _ta_loop(M, b, x, bp, rho, grow_rho, tol, tol_normal, max_iter, recompute_ev
             x = (1.0 - alpha) * x + (alpha * s) * c
         elif grow_rho:
             rho = max(2.0 * rho, db / cn)          # Alg. 2.2 else-branch
+            if rho > rho_max:
+                status, reason = Status.OK, Reason.RHO_BOUND
+                break
         else:
             status, reason = Status.WITNESS, Reason.WITNESS   # Alg. 2.1 STOP
             break
@@ -142,11 +163,12 @@ def _finish(M, b, x, bp, status, reason, k, matvecs, rho, hist, db, cn, mtb_n2):
 
 
 def ta_solve(M, b, x0=None, tol=1e-10, tol_normal=None, max_iter=1000,
-             recompute_every=40, observer=None) -> TAResult:
+             recompute_every=40, observer=None, nonneg=False, rho_max=math.inf) -> TAResult:
     """Algorithm 2.2: rho = 0, x' = 0, b' = 0 (or the warm start x0).
 
     ``observer(k, x, b', rho, alpha)`` is called after every iteration
-    (alpha is None on a rho-growth iteration).
+    (alpha is None on a rho-growth iteration). ``nonneg`` / ``rho_max``: the
+    LP-feasibility form of Sec. 6 (see _ta_loop); a warm start must then be >= 0.
     """
     if tol_normal is None:
         tol_normal = tol
@@ -166,7 +188,8 @@ def ta_solve(M, b, x0=None, tol=1e-10, tol_normal=None, max_iter=1000,
         bp = M.matvec(x)
         rho = float(np.linalg.norm(x))
     x, bp, rho, st, rs, k, hist, db, cn = _ta_loop(M, b, x, bp, rho, True, tol, tol_normal,
-                                                   max_iter, recompute_every, mtb_n2, observer)
+                                                   max_iter, recompute_every, mtb_n2, observer,
+                                                   nonneg, rho_max)
     return _finish(M, b, x, bp, st, rs, k, M.nmatvec - start, rho, hist, db, cn, mtb_n2)
 
 

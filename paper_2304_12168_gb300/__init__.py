@@ -29,10 +29,11 @@ LIB_PATH = os.path.join(_HERE, "libtacta.so")
 
 TACTA_DENSE, TACTA_CSR = 0, 1
 CYCLE_PINGPONG, CYCLE_SAWTOOTH, CYCLE_FIXED = 0, 1, 2
+PRECISION_FP64, PRECISION_MIXED = 0, 1
 STATUS = {0: "OK", 1: "MAXITER", 2: "BREAKDOWN", 3: "WITNESS", -1: "ERR_INVALID",
           -2: "ERR_NONFINITE", -3: "ERR_CUDA", -4: "ERR_OOM", -5: "ERR_TIMEOUT"}
 REASON = {0: "NONE", 1: "RESIDUAL", 2: "NORMAL", 3: "MAXITER", 4: "BREAKDOWN", 5: "WITNESS",
-          6: "GAP", 7: "ZERO_RHS", 8: "NONFINITE"}
+          6: "GAP", 7: "ZERO_RHS", 8: "NONFINITE", 9: "TIMEOUT", 10: "RHO_BOUND"}
 
 
 class tacta_matrix(ctypes.Structure):
@@ -47,7 +48,8 @@ class tacta_options(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("t_max", ctypes.c_int32), ("cycle", ctypes.c_int32),
                 ("recompute_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("poll_every", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("precision", ctypes.c_int32), ("nonneg", ctypes.c_int32),
+                ("rho_max", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
 
 class tacta_info(ctypes.Structure):
@@ -63,6 +65,7 @@ class tacta_info(ctypes.Structure):
 
 EXPORTS = ["tacta_default_options", "cta_solve", "ta_solve", "ta_minnorm", "tacta_plan_create",
            "tacta_plan_cta", "tacta_plan_ta", "tacta_plan_minnorm", "tacta_plan_destroy",
+           "tacta_plan_transpose", "tacta_plan_matvec", "tacta_plan_outer",
            "tacta_residual_static", "tacta_last_error", "tacta_version"]
 
 _lib_handle = None
@@ -98,6 +101,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tacta_version.restype = ctypes.c_int32
     lib.tacta_residual_static.argtypes = [P(tacta_matrix), dp, dp, dp, dp, vp]
     lib.tacta_residual_static.restype = ctypes.c_int32
+    lib.tacta_plan_transpose.argtypes = [vp, P(tacta_options), P(vp)]
+    lib.tacta_plan_transpose.restype = ctypes.c_int32
+    lib.tacta_plan_matvec.argtypes = [vp, ctypes.c_int32, dp, dp, P(tacta_options)]
+    lib.tacta_plan_matvec.restype = ctypes.c_int32
+    lib.tacta_plan_outer.argtypes = [vp, ctypes.c_double, dp, dp, dp, P(tacta_options)]
+    lib.tacta_plan_outer.restype = ctypes.c_int32
     _lib_handle = lib
     return lib
 
@@ -297,6 +306,36 @@ class Plan:
 
     def minnorm(self, b, hist_cap=None, **opts):
         return self._call("tacta_plan_minnorm", b, None, hist_cap, opts)
+
+    def transpose(self, **opts):
+        """tacta_plan_transpose: a plan for Aᵀ from this plan's device copy."""
+        lib = load_library()
+        o = make_options(self.on_device, **opts)
+        h = ctypes.c_void_p()
+        _check(lib.tacta_plan_transpose(self._h, ctypes.byref(o), ctypes.byref(h)))
+        q = Plan.__new__(Plan)
+        q._h, q.on_device, q.m, q.n = h, self.on_device, self.n, self.m
+        return q
+
+    def matvec(self, x, transpose=False, **opts):
+        """tacta_plan_matvec: A x, or Aᵀ x with transpose=True."""
+        lib = load_library()
+        px, _, kx = _ptr(x, np.float64)
+        y = _vec_out(self.n if transpose else self.m, self.on_device, kx)
+        o = make_options(self.on_device, **opts)
+        _check(lib.tacta_plan_matvec(self._h, int(bool(transpose)), px, _ptr(y, np.float64)[0],
+                                     ctypes.byref(o)))
+        return y
+
+    def outer(self, alpha, u, v, out, **opts):
+        """tacta_plan_outer: out[k] += alpha u[row(k)] v[col(k)] over A's stored entries."""
+        lib = load_library()
+        pu, _, ku = _ptr(u, np.float64)
+        pv, _, kv = _ptr(v, np.float64)
+        po, _, ko = _ptr(out, np.float64)
+        o = make_options(self.on_device, **opts)
+        _check(lib.tacta_plan_outer(self._h, float(alpha), pu, pv, po, ctypes.byref(o)))
+        return out
 
     def close(self):
         if getattr(self, "_h", None):

@@ -29,6 +29,7 @@ struct Ctl {
     int32_t hist_cap;
     int32_t hist_len;
     int32_t grow_rho;      // TA: 1 = Alg. 2.2 (rho grows), 0 = Alg. 2.1 (witness stops)
+    int32_t nonneg;        // TA for LP feasibility (Sec. 6): c replaced by max(c, 0)
     uint32_t counter;      // last-block-done ticket
     int32_t matvecs;       // products with A or Aᵀ made by the iteration (setup included)
     int32_t pad_;
@@ -42,6 +43,8 @@ struct Ctl {
     double s;              // TA: rho / ||c||
     double ta_alpha;       // TA: step
     double rho;            // TA: radius
+    double rho_max;        // TA: termination bound on rho (infinity: none)
+    double cs2;            // chain scale²: the chain's moments are cs2^k phi_k (1 on the FP64 path)
     double phi[2 * kTMax + 2];
     double alpha[kTMax];
     double red[4];         // scratch results of setup reductions
@@ -76,7 +79,8 @@ enum Epilogue : int {
     EPI_NORM = 1,      // y = A x;          red0 += y²
     EPI_RESID = 2,     // y = b - A x;      red0 += y², red1 += y b
     EPI_TAPIVOT = 3,   // y = s (A x) = v;  w = v - b + d (= v - b'); red0 += d w, red1 += w²
-    EPI_RESID_F32 = 4  // FP64 product, v = b - A x; yf = (float) v; red0 += v², red1 += v b
+    EPI_RESID_F32 = 4, // FP64 product, v = b - A x; yf = (float) v; red0 += v², red1 += v b
+    EPI_NORM_POS = 5   // y = max(A x, 0);  red0 += y²  (c_+ of TA for LP feasibility)
 };
 
 struct EpiArgs {
@@ -172,10 +176,13 @@ cudaError_t launch_copy_gated(const LaunchCtx& L, double* dst, const double* src
 cudaError_t launch_fill(const LaunchCtx& L, double* dst, double v, int64_t len);
 
 // mixed precision (FP32 chain, FP64 refinement)
-cudaError_t launch_spmv32(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y, int epi,
-                          FinArgs f, int gate);
+cudaError_t launch_spmv32(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y, float scale,
+                          int epi, FinArgs f, int gate);
 cudaError_t launch_cta_update32(const LaunchCtx& L, int t, int64_t m, int64_t n, float* dx, float* r,
-                                float* const* z, float* const* u, FinArgs f);
+                                float* const* z, float* const* u, float xscale, FinArgs f);
+cudaError_t abs_row_sum_max(cudaStream_t s, const DevCSR& A, double* dev_out, double* host_out);
+cudaError_t launch_outer_on_pattern(cudaStream_t s, int grid, const DevOperand& A, double alpha, const double* u,
+                                    const double* v, double* out);
 cudaError_t launch_fold_correction(const LaunchCtx& L, int64_t n, double* x, float* dx, int gate);
 cudaError_t convert_to_f32(cudaStream_t s, const double* src, float* dst, int64_t len);
 cudaError_t spmv32_prepare();

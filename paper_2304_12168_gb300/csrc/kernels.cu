@@ -41,6 +41,7 @@ __device__ __forceinline__ bool gated_out(const Ctl* c, int gate) {
 
 __device__ __forceinline__ bool finite(double v) { return v == v && fabs(v) <= DBL_MAX; }
 
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -125,7 +126,7 @@ __device__ __noinline__ void finish(Ctl* c, const FinArgs& f, double r0, double 
         c->phi[2 * t] = r0;
         for (int i = 1; i <= 2 * t; ++i)
             if (!finite(c->phi[i])) { c->status = TACTA_REASON_NONFINITE; return; }
-        if (c->phi[1] <= c->nrm_thr) { c->status = TACTA_REASON_NORMAL; return; }
+        if (c->phi[1] <= __dmul_rn(c->nrm_thr, c->cs2)) { c->status = TACTA_REASON_NORMAL; return; }
         c->rank = hankel_solve_dev(c->phi, t, c->pivot_tol, c->alpha);
         if (c->rank == 0) c->status = TACTA_REASON_BREAKDOWN;
         break;
@@ -159,15 +160,25 @@ __device__ __noinline__ void finish(Ctl* c, const FinArgs& f, double r0, double 
     case FIN_TA_C: {
         c->cn2 = r0;
         if (!finite(r0) || !finite(c->db)) { c->status = TACTA_REASON_NONFINITE; return; }
-        if (r0 <= c->nrm_thr) { c->status = TACTA_REASON_NORMAL; return; }
+        if (c->nonneg) {
+            // c_+ ~ 0 with (b - b')ᵀb > 0: Farkas certificate of infeasibility (Sec. 6 reading)
+            if (r0 <= c->nrm_thr && c->db > 0.0) { c->status = TACTA_REASON_WITNESS; return; }
+        } else if (r0 <= c->nrm_thr) {
+            c->status = TACTA_REASON_NORMAL;
+            return;
+        }
         const double cn = __dsqrt_rn(r0);
         if (__dmul_rn(c->rho, cn) >= c->db) {            // strict pivot (Eq. eqlem2)
             c->pivot = 1;
-            c->s = __ddiv_rn(c->rho, cn);
+            c->s = cn > 0.0 ? __ddiv_rn(c->rho, cn) : 0.0;   // c_+ = 0: the pivot is v = 0
         } else {
             c->pivot = 0;
-            if (c->grow_rho) c->rho = fmax(__dmul_rn(2.0, c->rho), __ddiv_rn(c->db, cn));
-            else c->status = TACTA_REASON_WITNESS;      // Alg. 2.1 STOP
+            if (c->grow_rho) {
+                c->rho = fmax(__dmul_rn(2.0, c->rho), __ddiv_rn(c->db, cn));
+                if (c->rho > c->rho_max) c->status = TACTA_REASON_RHO_BOUND;
+            } else {
+                c->status = TACTA_REASON_WITNESS;      // Alg. 2.1 STOP
+            }
         }
         break;
     }
@@ -288,6 +299,10 @@ __device__ __forceinline__ void epilogue(int64_t row, double sum, double* __rest
     } else if (EPI == EPI_NORM) {
         y[row] = sum;
         a0 = fma(sum, sum, a0);
+    } else if (EPI == EPI_NORM_POS) {
+        const double v = sum > 0.0 ? sum : 0.0;
+        y[row] = v;
+        a0 = fma(v, v, a0);
     } else if (EPI == EPI_RESID) {
         const double bv = __ldg(e.b + row);
         const double v = bv - sum;
@@ -685,13 +700,14 @@ cudaError_t spmv_tiled_prepare() {
     TACTA_TILED_ATTR(kTileCapLarge, EPI_NONE) TACTA_TILED_ATTR(kTileCapLarge, EPI_NORM)
     TACTA_TILED_ATTR(kTileCapLarge, EPI_RESID) TACTA_TILED_ATTR(kTileCapLarge, EPI_TAPIVOT)
     TACTA_TILED_ATTR(kTileCapSmall, EPI_RESID_F32) TACTA_TILED_ATTR(kTileCapLarge, EPI_RESID_F32)
+    TACTA_TILED_ATTR(kTileCapSmall, EPI_NORM_POS) TACTA_TILED_ATTR(kTileCapLarge, EPI_NORM_POS)
 #undef TACTA_TILED_ATTR
 #define TACTA_TILED_X_ATTR(EPI)                                                                      \
     if (e == cudaSuccess)                                                                            \
         e = cudaFuncSetAttribute(spmv_tiled_x<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                  (int)spmv_tiled_x_smem());
     TACTA_TILED_X_ATTR(EPI_NONE) TACTA_TILED_X_ATTR(EPI_NORM) TACTA_TILED_X_ATTR(EPI_RESID)
-    TACTA_TILED_X_ATTR(EPI_TAPIVOT) TACTA_TILED_X_ATTR(EPI_RESID_F32)
+    TACTA_TILED_X_ATTR(EPI_TAPIVOT) TACTA_TILED_X_ATTR(EPI_RESID_F32) TACTA_TILED_X_ATTR(EPI_NORM_POS)
 #undef TACTA_TILED_X_ATTR
     if (e == cudaSuccess) done = true;
     return e;
@@ -734,6 +750,7 @@ static cudaError_t spmv_dispatch(const LaunchCtx& L, int kind, const Acc& acc, c
     case EPI_NORM: return spmv_dispatch_epi<Acc, EPI_NORM>(L, kind, acc, x, y, e, f, gate);
     case EPI_RESID: return spmv_dispatch_epi<Acc, EPI_RESID>(L, kind, acc, x, y, e, f, gate);
     case EPI_RESID_F32: return spmv_dispatch_epi<Acc, EPI_RESID_F32>(L, kind, acc, x, y, e, f, gate);
+    case EPI_NORM_POS: return spmv_dispatch_epi<Acc, EPI_NORM_POS>(L, kind, acc, x, y, e, f, gate);
     default: return spmv_dispatch_epi<Acc, EPI_TAPIVOT>(L, kind, acc, x, y, e, f, gate);
     }
 }
@@ -746,6 +763,7 @@ cudaError_t launch_spmv(const LaunchCtx& L, const DevOperand& A, const double* x
         case EPI_NORM: return spmv_tiled_x_launch<EPI_NORM>(L, A.csr, x, y, e, f, gate);
         case EPI_RESID: return spmv_tiled_x_launch<EPI_RESID>(L, A.csr, x, y, e, f, gate);
         case EPI_RESID_F32: return spmv_tiled_x_launch<EPI_RESID_F32>(L, A.csr, x, y, e, f, gate);
+        case EPI_NORM_POS: return spmv_tiled_x_launch<EPI_NORM_POS>(L, A.csr, x, y, e, f, gate);
         default: return spmv_tiled_x_launch<EPI_TAPIVOT>(L, A.csr, x, y, e, f, gate);
         }
     }
@@ -755,6 +773,7 @@ cudaError_t launch_spmv(const LaunchCtx& L, const DevOperand& A, const double* x
         case EPI_NORM: return spmv_tiled_launch<EPI_NORM>(L, A.csr, x, y, e, f, gate);
         case EPI_RESID: return spmv_tiled_launch<EPI_RESID>(L, A.csr, x, y, e, f, gate);
         case EPI_RESID_F32: return spmv_tiled_launch<EPI_RESID_F32>(L, A.csr, x, y, e, f, gate);
+        case EPI_NORM_POS: return spmv_tiled_launch<EPI_NORM_POS>(L, A.csr, x, y, e, f, gate);
         default: return spmv_tiled_launch<EPI_TAPIVOT>(L, A.csr, x, y, e, f, gate);
         }
     }
@@ -905,7 +924,7 @@ __global__ void __launch_bounds__(kTileRows)
 spmv32_tiled(const int4* __restrict__ tiles, const int2* __restrict__ xwin, int ntiles,
              const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
              const float* __restrict__ vals, const float* __restrict__ x, float* __restrict__ y,
-             Ctl* ctl, double* partials, FinArgs f, int gate) {
+             float scale, Ctl* ctl, double* partials, FinArgs f, int gate) {
     if (gated_out(ctl, gate)) return;
     if (gate != GATE_FORCE && blockIdx.x == 0 && threadIdx.x == 0) ctl->matvecs += 1;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -957,6 +976,7 @@ spmv32_tiled(const int4* __restrict__ tiles, const int2* __restrict__ xwin, int 
             sum = fmaf(S->vals[vb + u], xv, sum);
         }
         if (active) {
+            sum *= scale;   // a power of two: exact
             y[row] = sum;
             if (EPI == EPI_NORM) acc = fmaf(sum, sum, acc);
         }
@@ -979,7 +999,7 @@ template <int EPI>
 __global__ void __launch_bounds__(kBlock)
 spmv32_warp(int64_t rows, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
             const float* __restrict__ vals, const float* __restrict__ x, float* __restrict__ y,
-            Ctl* ctl, double* partials, FinArgs f, int gate) {
+            float scale, Ctl* ctl, double* partials, FinArgs f, int gate) {
     if (gated_out(ctl, gate)) return;
     if (gate != GATE_FORCE && blockIdx.x == 0 && threadIdx.x == 0) ctl->matvecs += 1;
     float acc = 0.0f;
@@ -992,6 +1012,7 @@ spmv32_warp(int64_t rows, const int32_t* __restrict__ rowptr, const int32_t* __r
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
         if (lane == 0) {
+            sum *= scale;
             y[row] = sum;
             if (EPI == EPI_NORM) acc = fmaf(sum, sum, acc);
         }
@@ -1001,36 +1022,62 @@ spmv32_warp(int64_t rows, const int32_t* __restrict__ rowptr, const int32_t* __r
 
 template <int CAP, bool XW, int EPI>
 static cudaError_t spmv32_tiled_launch(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y,
-                                       FinArgs f, int gate) {
+                                       float scale, FinArgs f, int gate) {
     const DevCSR& a = *A.base;
     const size_t sm = spmv32_smem<CAP, XW>();
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(6, (220u << 10) / (sm + 3072)));
     const int grid = std::min(a.ntiles, std::max(1, (L.max_grid / 8) * per_sm));
     spmv32_tiled<CAP, XW, EPI><<<grid, kTileRows, sm, L.stream>>>(a.tiles, a.xwin, a.ntiles, a.rowptr,
-                                                                   a.colidx, A.vals, x, y, L.ctl,
+                                                                   a.colidx, A.vals, x, y, scale, L.ctl,
                                                                    L.partials, f, gate);
     if (L.launches) ++*L.launches;
     return cudaGetLastError();
 }
 
 template <int EPI>
-static cudaError_t spmv32_epi(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y, FinArgs f,
-                              int gate) {
+static cudaError_t spmv32_epi(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y, float scale,
+                              FinArgs f, int gate) {
     const DevCSR& a = *A.base;
-    if (a.cfg.kind == 3) return spmv32_tiled_launch<kTileCapSmall, true, EPI>(L, A, x, y, f, gate);
+    if (a.cfg.kind == 3) return spmv32_tiled_launch<kTileCapSmall, true, EPI>(L, A, x, y, scale, f, gate);
     if (a.cfg.kind == 2) {
-        if (a.cap <= kTileCapSmall) return spmv32_tiled_launch<kTileCapSmall, false, EPI>(L, A, x, y, f, gate);
-        return spmv32_tiled_launch<kTileCapLarge, false, EPI>(L, A, x, y, f, gate);
+        if (a.cap <= kTileCapSmall)
+            return spmv32_tiled_launch<kTileCapSmall, false, EPI>(L, A, x, y, scale, f, gate);
+        return spmv32_tiled_launch<kTileCapLarge, false, EPI>(L, A, x, y, scale, f, gate);
     }
-    spmv32_warp<EPI><<<L.max_grid, kBlock, 0, L.stream>>>(a.rows, a.rowptr, a.colidx, A.vals, x, y, L.ctl,
-                                                          L.partials, f, gate);
+    spmv32_warp<EPI><<<L.max_grid, kBlock, 0, L.stream>>>(a.rows, a.rowptr, a.colidx, A.vals, x, y, scale,
+                                                          L.ctl, L.partials, f, gate);
     if (L.launches) ++*L.launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_spmv32(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y, int epi,
-                          FinArgs f, int gate) {
-    return epi == EPI_NORM ? spmv32_epi<EPI_NORM>(L, A, x, y, f, gate) : spmv32_epi<EPI_NONE>(L, A, x, y, f, gate);
+cudaError_t launch_spmv32(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y, float scale,
+                          int epi, FinArgs f, int gate) {
+    return epi == EPI_NORM ? spmv32_epi<EPI_NORM>(L, A, x, y, scale, f, gate)
+                           : spmv32_epi<EPI_NONE>(L, A, x, y, scale, f, gate);
+}
+
+// max_i sum_k |A_ik| (the infinity norm), for the chain scale of the mixed path
+__global__ void abs_row_sum_max_kernel(int64_t rows, const int32_t* __restrict__ rowptr,
+                                       const double* __restrict__ vals, unsigned long long* out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double best = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
+        double s = 0.0;
+        for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) s += fabs(vals[k]);
+        best = fmax(best, s);
+    }
+    // non-negative doubles order like their bit patterns
+    atomicMax(out, (unsigned long long)__double_as_longlong(best));
+}
+
+cudaError_t abs_row_sum_max(cudaStream_t s, const DevCSR& A, double* dev_out, double* host_out) {
+    cudaError_t e = cudaMemsetAsync(dev_out, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    abs_row_sum_max_kernel<<<1024, kBlock, 0, s>>>(A.rows, A.rowptr, A.vals,
+                                                   reinterpret_cast<unsigned long long*>(dev_out));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(host_out, dev_out, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
 }
 
 cudaError_t spmv32_prepare() {
@@ -1054,11 +1101,17 @@ cudaError_t spmv32_prepare() {
 template <int T>
 __global__ void __launch_bounds__(kBlock)
 cta_update32(int64_t m, int64_t n, float* __restrict__ dx, float* __restrict__ r, F32Ptrs z, F32Ptrs u,
-             Ctl* ctl, double* partials, FinArgs f) {
+             float xscale, Ctl* ctl, double* partials, FinArgs f) {
     if (ctl->status != 0) return;
-    float al[T];
+    // the chain vectors are scaled (z_i by s^(2i-1), u_i by s^(2i), s = xscale a power of
+    // two), so the solve on the scaled moments gives beta with x += s sum beta_i z_i,
+    // r -= sum beta_i u_i
+    float al[T], ax[T];
 #pragma unroll
-    for (int j = 0; j < T; ++j) al[j] = (float)ctl->alpha[j];
+    for (int j = 0; j < T; ++j) {
+        al[j] = (float)ctl->alpha[j];
+        ax[j] = (float)(ctl->alpha[j] * (double)xscale);
+    }
     float acc = 0.0f;
     const int64_t len = m > n ? m : n;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1066,7 +1119,7 @@ cta_update32(int64_t m, int64_t n, float* __restrict__ dx, float* __restrict__ r
         if (i < n) {
             float v = dx[i];
 #pragma unroll
-            for (int j = 0; j < T; ++j) v = fmaf(al[j], __ldg(z.p[j] + i), v);
+            for (int j = 0; j < T; ++j) v = fmaf(ax[j], __ldg(z.p[j] + i), v);
             dx[i] = v;
         }
         if (i < m) {
@@ -1097,19 +1150,19 @@ __global__ void d2f_kernel(const double* __restrict__ src, float* __restrict__ d
 }
 
 cudaError_t launch_cta_update32(const LaunchCtx& L, int t, int64_t m, int64_t n, float* dx, float* r,
-                                float* const* z, float* const* u, FinArgs f) {
+                                float* const* z, float* const* u, float xscale, FinArgs f) {
     F32Ptrs zp{}, up{};
     for (int j = 0; j < t; ++j) { zp.p[j] = z[j]; up.p[j] = u[j]; }
     const int g = L.max_grid;
     switch (t) {
-    case 1: cta_update32<1><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
-    case 2: cta_update32<2><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
-    case 3: cta_update32<3><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
-    case 4: cta_update32<4><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
-    case 5: cta_update32<5><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
-    case 6: cta_update32<6><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
-    case 7: cta_update32<7><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
-    default: cta_update32<8><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, L.ctl, L.partials, f); break;
+    case 1: cta_update32<1><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, xscale, L.ctl, L.partials, f); break;
+    case 2: cta_update32<2><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, xscale, L.ctl, L.partials, f); break;
+    case 3: cta_update32<3><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, xscale, L.ctl, L.partials, f); break;
+    case 4: cta_update32<4><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, xscale, L.ctl, L.partials, f); break;
+    case 5: cta_update32<5><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, xscale, L.ctl, L.partials, f); break;
+    case 6: cta_update32<6><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, xscale, L.ctl, L.partials, f); break;
+    case 7: cta_update32<7><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, xscale, L.ctl, L.partials, f); break;
+    default: cta_update32<8><<<g, kBlock, 0, L.stream>>>(m, n, dx, r, zp, up, xscale, L.ctl, L.partials, f); break;
     }
     if (L.launches) ++*L.launches;
     return cudaGetLastError();
@@ -1126,6 +1179,41 @@ cudaError_t convert_to_f32(cudaStream_t s, const double* src, float* dst, int64_
     if (blocks < 1) blocks = 1;
     if (blocks > 65536) blocks = 65536;
     d2f_kernel<<<(unsigned)blocks, kBlock, 0, s>>>(src, dst, len);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ pattern outer product
+// out[k] += alpha u[row(k)] v[col(k)] over the stored entries of A (CSR: nonzero order;
+// dense: row-major) -- the gradient dL/dA of a linear solve restricted to A's pattern.
+__global__ void __launch_bounds__(kBlock)
+outer_on_pattern_csr(int64_t rows, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                     double alpha, const double* __restrict__ u, const double* __restrict__ v,
+                     double* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+        const double au = alpha * u[r];
+        for (int64_t k = rowptr[r] + lane; k < rowptr[r + 1]; k += 32) out[k] = fma(au, v[colidx[k]], out[k]);
+    }
+}
+
+__global__ void __launch_bounds__(kBlock)
+outer_on_pattern_dense(int64_t rows, int64_t cols, double alpha, const double* __restrict__ u,
+                       const double* __restrict__ v, double* __restrict__ out) {
+    const int64_t total = rows * cols;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += stride) {
+        const int64_t r = k / cols, c = k - r * cols;
+        out[k] = fma(alpha * u[r], v[c], out[k]);
+    }
+}
+
+cudaError_t launch_outer_on_pattern(cudaStream_t s, int grid, const DevOperand& A, double alpha, const double* u,
+                                    const double* v, double* out) {
+    if (A.format == TACTA_CSR)
+        outer_on_pattern_csr<<<grid, kBlock, 0, s>>>(A.csr.rows, A.csr.rowptr, A.csr.colidx, alpha, u, v, out);
+    else
+        outer_on_pattern_dense<<<grid, kBlock, 0, s>>>(A.dense.rows, A.dense.cols, alpha, u, v, out);
     return cudaGetLastError();
 }
 

@@ -73,15 +73,16 @@ struct Plan {
     int g_cta_key = -1;
     int64_t g_cta_launches = 0;
     int g_cta_iters = 0;
-    cudaGraphExec_t g_ta[2] = {nullptr, nullptr};
-    int64_t g_ta_launches[2] = {0, 0};
-    int g_ta_iters[2] = {0, 0};
+    cudaGraphExec_t g_ta[3] = {nullptr, nullptr, nullptr};   // plain, normal system, LP (c_+)
+    int64_t g_ta_launches[3] = {0, 0, 0};
+    int g_ta_iters[3] = {0, 0, 0};
     // mixed precision: FP32 values of A / Aᵀ (structure shared), FP32 chain vectors
     DevCSR32 A32, At32;
     float* z32[kTMax] = {};
     float* u32[kTMax] = {};
     float* r32 = nullptr;
     float* dx32 = nullptr;
+    float chain_scale = 1.0f;    // 1/sigma, sigma a power of two >= sqrt(||A||_1 ||A||_inf) >= ||A||_2
     cudaGraphExec_t g_cta32 = nullptr;
     int g_cta32_key = -1;
     int64_t g_cta32_launches = 0;
@@ -147,7 +148,7 @@ static void free_graphs(Plan* p) {
     if (p->g_cta32) cudaGraphExecDestroy(p->g_cta32);
     p->g_cta32 = nullptr;
     p->g_cta32_key = -1;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 3; ++i) {
         if (p->g_ta[i]) cudaGraphExecDestroy(p->g_ta[i]);
         p->g_ta[i] = nullptr;
     }
@@ -406,6 +407,18 @@ static tacta_status ensure_mixed(Plan* p, int t_max, cudaStream_t s) {
         CUDA_TRY(f32(&p->r32, p->m));
         CUDA_TRY(f32(&p->dx32, p->n));
         CUDA_TRY(spmv32_prepare());
+        // chain scale: products are multiplied by 1/sigma so the FP32 chain vectors stay
+        // within range (H^i r grows like ||A||^(2i)); sigma is a power of two (exact)
+        double ninf = 0.0, n1 = 0.0;
+        CUDA_TRY(abs_row_sum_max(s, p->A.csr, p->partials, &p->stage->red[0]));
+        ninf = p->stage->red[0];
+        CUDA_TRY(abs_row_sum_max(s, p->At.csr, p->partials, &p->stage->red[0]));
+        n1 = p->stage->red[0];
+        const double bound = std::sqrt(ninf * n1);
+        int e2 = 0;
+        if (bound > 0.0 && std::isfinite(bound)) e2 = (int)std::ceil(std::log2(bound));
+        e2 = std::max(-120, std::min(120, e2));
+        p->chain_scale = std::ldexp(1.0f, -e2);
     }
     for (int i = 0; i < t_max; ++i) {
         if (!p->z32[i]) {
@@ -421,17 +434,36 @@ static tacta_status ensure_mixed(Plan* p, int t_max, cudaStream_t s) {
 // One F_t step, mixed precision: FP32 chain and update, then (gated on the device)
 // the refinement: fold the FP32 correction into the FP64 x and recompute the true
 // residual b - A x with the FP64 product, stored back into the FP32 residual.
+static cudaError_t chain_spmv32(Plan* p, const LaunchCtx& L, const DevCSR32& A, const float* x, float* y,
+                                FinArgs f) {
+    if (!p->profiling) return launch_spmv32(L, A, x, y, p->chain_scale, EPI_NORM, f, GATE_ALWAYS);
+    while (p->pev.size() < p->pev_used + 2) {
+        cudaEvent_t ev;
+        cudaError_t err = cudaEventCreate(&ev);
+        if (err != cudaSuccess) return err;
+        p->pev.push_back(ev);
+    }
+    cudaError_t err = cudaEventRecord(p->pev[p->pev_used], L.stream);
+    if (err != cudaSuccess) return err;
+    if ((err = launch_spmv32(L, A, x, y, p->chain_scale, EPI_NORM, f, GATE_ALWAYS)) != cudaSuccess) return err;
+    if ((err = cudaEventRecord(p->pev[p->pev_used + 1], L.stream)) != cudaSuccess) return err;
+    p->pev_used += 2;
+    const DevCSR& a = *A.base;
+    p->prof_bytes += 8.0 * (double)a.nnz + 4.0 * (double)(a.rows + 1) + 4.0 * (double)a.cols + 4.0 * (double)a.rows;
+    return cudaSuccess;
+}
+
 static cudaError_t enqueue_cta32_iter(Plan* p, const LaunchCtx& L, int t) {
     cudaError_t e;
     const float* uprev = p->r32;
     for (int i = 0; i < t; ++i) {
-        if ((e = launch_spmv32(L, p->At32, uprev, p->z32[i], EPI_NORM, FinArgs{FIN_PHI, 2 * i + 1, nullptr},
-                               GATE_ALWAYS)) != cudaSuccess) return e;
+        if ((e = chain_spmv32(p, L, p->At32, uprev, p->z32[i], FinArgs{FIN_PHI, 2 * i + 1, nullptr})) != cudaSuccess)
+            return e;
         FinArgs f = (i == t - 1) ? FinArgs{FIN_CTA_STEP, t, nullptr} : FinArgs{FIN_PHI, 2 * i + 2, nullptr};
-        if ((e = launch_spmv32(L, p->A32, p->z32[i], p->u32[i], EPI_NORM, f, GATE_ALWAYS)) != cudaSuccess) return e;
+        if ((e = chain_spmv32(p, L, p->A32, p->z32[i], p->u32[i], f)) != cudaSuccess) return e;
         uprev = p->u32[i];
     }
-    if ((e = launch_cta_update32(L, t, p->m, p->n, p->dx32, p->r32, p->z32, p->u32,
+    if ((e = launch_cta_update32(L, t, p->m, p->n, p->dx32, p->r32, p->z32, p->u32, p->chain_scale,
                                  FinArgs{FIN_CTA_UPDATE, 0, p->hist})) != cudaSuccess) return e;
     if ((e = launch_fold_correction(L, p->n, p->x, p->dx32, GATE_NEED_TRUE)) != cudaSuccess) return e;
     return launch_spmv(L, p->A, p->x, p->tmp_m, EPI_RESID_F32, EpiArgs{p->b, nullptr, p->r32},
@@ -505,15 +537,15 @@ static cudaError_t apply_Mt(Plan* p, const LaunchCtx& L, int normal, const doubl
     return apply_M(p, L, 1, in, out, epi, e, f, gate);   // AᵀA is symmetric
 }
 
-static cudaError_t enqueue_ta_iter(Plan* p, const LaunchCtx& L, int normal, double* hist) {
+static cudaError_t enqueue_ta_iter(Plan* p, const LaunchCtx& L, int normal, int nonneg, double* hist) {
     cudaError_t e;
     const double* rhs = normal ? p->bt : p->b;
     const int64_t mm = normal ? p->n : p->m;
     EpiArgs none{nullptr, nullptr, nullptr};
-    // c = Mᵀ (b - b'), ||c||², pivot test (Eq. eqlem2) / rho growth
+    // c = Mᵀ (b - b') (c_+ = max(c, 0) for LP feasibility), ||c||², pivot test (Eq. eqlem2) / rho growth
     if (!normal) {
-        if ((e = chain_spmv(p, L, p->At, p->d, p->c, EPI_NORM, none, FinArgs{FIN_TA_C, 0, nullptr},
-                            GATE_ALWAYS)) != cudaSuccess) return e;
+        if ((e = chain_spmv(p, L, p->At, p->d, p->c, nonneg ? EPI_NORM_POS : EPI_NORM, none,
+                            FinArgs{FIN_TA_C, 0, nullptr}, GATE_ALWAYS)) != cudaSuccess) return e;
     } else if ((e = apply_Mt(p, L, normal, p->d, p->c, EPI_NORM, none, FinArgs{FIN_TA_C, 0, nullptr},
                              GATE_ALWAYS)) != cudaSuccess) return e;
     // v = rho M c / ||c|| (Eq. vr) with the dots of Eq. alph
@@ -610,7 +642,9 @@ static tacta_status status_of(int reason) {
     case TACTA_REASON_RESIDUAL:
     case TACTA_REASON_NORMAL:
     case TACTA_REASON_GAP:
-    case TACTA_REASON_ZERO_RHS: return TACTA_OK;
+    case TACTA_REASON_ZERO_RHS:
+    case TACTA_REASON_RHO_BOUND: return TACTA_OK;
+    case TACTA_REASON_TIMEOUT: return TACTA_ERR_TIMEOUT;
     case TACTA_REASON_MAXITER: return TACTA_MAXITER;
     case TACTA_REASON_BREAKDOWN: return TACTA_BREAKDOWN;
     case TACTA_REASON_WITNESS: return TACTA_WITNESS;
@@ -636,6 +670,8 @@ static Ctl base_ctl(const Opts& O, int64_t hist_cap) {
     h.R = O.o.recompute_every;
     h.hist_cap = (int32_t)hist_cap;
     h.tol2 = O.o.tol * O.o.tol;
+    h.cs2 = 1.0;
+    h.rho_max = O.o.rho_max > 0.0 ? O.o.rho_max : INFINITY;
     h.tol_n2 = O.o.tol_normal * O.o.tol_normal;
     h.pivot_tol = O.o.pivot_tol;
     return h;
@@ -678,6 +714,7 @@ static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t h
     LaunchCtx L{O.s, p->ctl, p->partials, p->grid, launches};
     Ctl h = base_ctl(O, hist_cap);
     h.need_true = (x0 || mixed) ? 1 : 0;
+    if (mixed) h.cs2 = (double)p->chain_scale * (double)p->chain_scale;
     if ((st = write_ctl(p, O.s, h)) != TACTA_OK) return st;
     EpiArgs none{nullptr, nullptr, nullptr};
     CUDA_TRY(launch_reduce_vec(L, p->m, p->b, nullptr, FinArgs{FIN_SETUP_B, 0, nullptr}, GATE_ALWAYS));
@@ -788,9 +825,11 @@ static tacta_status ta_setup(Plan* p, const Opts& O, int normal, const double* x
 // TA iterations; the history pointer is always the plan's buffer (trips of Alg. 2.5 run with
 // hist_cap = 0 in the control block, so they write no history and share the cached graph).
 static tacta_status ta_iterate(Plan* p, const Opts& O, int normal, int64_t max_iter, int64_t* launches) {
-    auto body = [&](const LaunchCtx& LL, int64_t) { return enqueue_ta_iter(p, LL, normal, p->hist); };
-    return run_loop(p, O, max_iter, 1, O.o.use_graph != 0, &p->g_ta[normal], &p->g_ta_launches[normal],
-                    &p->g_ta_iters[normal], body, launches);
+    const int nonneg = (!normal && O.o.nonneg) ? 1 : 0;
+    const int slot = nonneg ? 2 : normal;
+    auto body = [&](const LaunchCtx& LL, int64_t) { return enqueue_ta_iter(p, LL, normal, nonneg, p->hist); };
+    return run_loop(p, O, max_iter, 1, O.o.use_graph != 0, &p->g_ta[slot], &p->g_ta_launches[slot],
+                    &p->g_ta_iters[slot], body, launches);
 }
 
 static tacta_status plan_ta(Plan* p, const VecIO& io, const tacta_options* opt, tacta_info* info) {
@@ -804,6 +843,7 @@ static tacta_status plan_ta(Plan* p, const VecIO& io, const tacta_options* opt, 
     if ((st = ensure_hist(p, std::max<int64_t>(hist_cap, 1))) != TACTA_OK) return st;
     Ctl h = base_ctl(O, hist_cap);
     h.grow_rho = 1;
+    h.nonneg = O.o.nonneg ? 1 : 0;
     h.need_true = io.x0 ? 1 : 0;
     if ((st = write_ctl(p, O.s, h)) != TACTA_OK) return st;
     if ((st = ta_setup(p, O, 0, io.x0, hist_cap, &launches)) != TACTA_OK) return st;
@@ -818,6 +858,7 @@ static tacta_status plan_ta(Plan* p, const VecIO& io, const tacta_options* opt, 
     if ((st = store_out(p, O, io, p->x, c.hist_len)) != TACTA_OK) return st;
     const tacta_status out = status_of(c.status);
     if (out == TACTA_ERR_NONFINITE) set_error("non-finite value in a reduction");
+    if (out == TACTA_ERR_TIMEOUT) set_error("a bounded wait inside a kernel gave up");
     fill_info(info, c, out, launches);
     prof_end(p, info);
     p->profiling = false;
@@ -974,6 +1015,8 @@ void tacta_default_options(tacta_options* o) {
     o->poll_every = 64;
     o->profile = 0;
     o->precision = TACTA_PRECISION_FP64;
+    o->nonneg = 0;
+    o->rho_max = 0.0;
     o->stream = nullptr;
 }
 
@@ -1021,6 +1064,86 @@ tacta_status tacta_plan_ta(tacta_plan plan, const double* b, const double* x0, c
 tacta_status tacta_plan_minnorm(tacta_plan plan, const double* b, const double* x0, const tacta_options* opt,
                                 double* x_out, double* hist, int32_t hist_cap, tacta_info* info) {
     return plan_call(2, plan, b, x0, opt, x_out, hist, hist_cap, info);
+}
+
+tacta_status tacta_plan_transpose(tacta_plan plan, const tacta_options* opt, tacta_plan* out) {
+    set_error("");
+    if (!plan || !plan->p || !out) { set_error("NULL argument"); return TACTA_ERR_INVALID; }
+    Plan* p = plan->p;
+    CUDA_TRY(cudaSetDevice(p->device));
+    tacta_matrix M;
+    std::memset(&M, 0, sizeof(M));
+    M.m = p->n;
+    M.n = p->m;
+    M.on_device = 1;
+    if (p->At.format == TACTA_CSR) {
+        M.format = TACTA_CSR;
+        M.nnz = p->At.csr.nnz;
+        M.vals = p->At.csr.vals;
+        M.rowptr = p->At.csr.rowptr;
+        M.colidx = p->At.csr.colidx;
+    } else {
+        M.format = TACTA_DENSE;
+        M.vals = p->At.dense.vals;
+    }
+    Plan* q = nullptr;
+    tacta_status st = plan_create(&M, opt, &q);
+    if (st != TACTA_OK) return st;
+    q->on_device = p->on_device;
+    *out = new tacta_plan_s{q};
+    return TACTA_OK;
+}
+
+tacta_status tacta_plan_matvec(tacta_plan plan, int32_t transpose, const double* x, double* y,
+                               const tacta_options* opt) {
+    set_error("");
+    if (!plan || !plan->p || !x || !y) { set_error("NULL argument"); return TACTA_ERR_INVALID; }
+    Plan* p = plan->p;
+    Opts O = resolve(opt);
+    CUDA_TRY(cudaSetDevice(p->device));
+    const DevOperand& A = transpose ? p->At : p->A;
+    const int64_t in_len = A.cols(), out_len = A.rows();
+    // the input goes through a padded plan buffer: the staged kernels read 16-byte-rounded windows
+    double* xin = transpose ? p->tmp_m : p->tmp_n;
+    double* yout = transpose ? p->tmp_n : p->tmp_m;
+    CUDA_TRY(cudaMemcpyAsync(xin, x, sizeof(double) * in_len, cudaMemcpyDefault, O.s));
+    int64_t launches = 0;
+    LaunchCtx L{O.s, p->ctl, p->partials, p->grid, &launches};
+    CUDA_TRY(launch_spmv(L, A, xin, yout, EPI_NONE, EpiArgs{nullptr, nullptr, nullptr},
+                         FinArgs{FIN_NONE, 0, nullptr}, GATE_FORCE));
+    CUDA_TRY(cudaMemcpyAsync(y, yout, sizeof(double) * out_len, cudaMemcpyDefault, O.s));
+    CUDA_TRY(cudaStreamSynchronize(O.s));
+    return TACTA_OK;
+}
+
+tacta_status tacta_plan_outer(tacta_plan plan, double alpha, const double* u, const double* v, double* out,
+                              const tacta_options* opt) {
+    set_error("");
+    if (!plan || !plan->p || !u || !v || !out) { set_error("NULL argument"); return TACTA_ERR_INVALID; }
+    Plan* p = plan->p;
+    Opts O = resolve(opt);
+    CUDA_TRY(cudaSetDevice(p->device));
+    const int64_t len = p->A.nnz();
+    // stage through plan buffers when the caller's arrays are on the host
+    const double* du = u;
+    const double* dv = v;
+    double* dout = out;
+    double* hold = nullptr;
+    if (!p->on_device) {
+        CUDA_TRY(cudaMemcpyAsync(p->tmp_m, u, sizeof(double) * p->m, cudaMemcpyHostToDevice, O.s));
+        CUDA_TRY(cudaMemcpyAsync(p->tmp_n, v, sizeof(double) * p->n, cudaMemcpyHostToDevice, O.s));
+        CUDA_TRY(cudaMalloc(&hold, sizeof(double) * std::max<int64_t>(len, 1)));
+        CUDA_TRY(cudaMemcpyAsync(hold, out, sizeof(double) * len, cudaMemcpyHostToDevice, O.s));
+        du = p->tmp_m;
+        dv = p->tmp_n;
+        dout = hold;
+    }
+    cudaError_t e = launch_outer_on_pattern(O.s, p->grid, p->A, alpha, du, dv, dout);
+    if (e == cudaSuccess && hold) e = cudaMemcpyAsync(out, hold, sizeof(double) * len, cudaMemcpyDeviceToHost, O.s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(O.s);
+    if (hold) cudaFree(hold);
+    CUDA_TRY(e);
+    return TACTA_OK;
 }
 
 static tacta_status one_shot(int algo, const tacta_matrix* A, const double* b, const double* x0,

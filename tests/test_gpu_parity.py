@@ -28,7 +28,8 @@ RES_TOL = 1e-10
 
 REASON = {int(Reason.RESIDUAL): "RESIDUAL", int(Reason.NORMAL): "NORMAL",
           int(Reason.MAXITER): "MAXITER", int(Reason.ZERO_RHS): "ZERO_RHS",
-          int(Reason.GAP): "GAP", int(Reason.BREAKDOWN): "BREAKDOWN"}
+          int(Reason.GAP): "GAP", int(Reason.BREAKDOWN): "BREAKDOWN",
+          int(Reason.WITNESS): "WITNESS", int(Reason.RHO_BOUND): "RHO_BOUND"}
 
 
 @pytest.fixture(scope="module")
@@ -421,3 +422,59 @@ def test_nonfinite_input_reports_error(tacta):
     b[3] = float("nan")
     with pytest.raises(tacta.TactaError, match="NONFINITE"):
         tacta.cta_solve(A, b, tol=1e-10)
+
+
+# ------------------------------------------------------------------ TA for LP feasibility (Sec. 6)
+
+def test_ta_lp_identity_golden(tacta):
+    """A = I, b = (3, -4): the c_+ iteration ends at the orthant projection (3, 0) with a
+    Farkas certificate of infeasibility (golden fixture, hand-derived)."""
+    import json
+    import os
+    import torch
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "ta_lp_identity.json")))
+    A = torch.tensor(g["A"], dtype=torch.float64, device="cuda:0")
+    b = torch.tensor(g["b"], dtype=torch.float64, device="cuda:0")
+    x, _, info = tacta.ta_solve(A, b, tol=1e-14, tol_normal=1e-14, max_iter=10, nonneg=1)
+    assert info["status_name"] == "WITNESS" and info["iters"] == g["iters"]
+    np.testing.assert_allclose(x.cpu().numpy(), g["x_final"], rtol=1e-14, atol=1e-14)
+
+
+def _lp_problem(seed, fmt):
+    rng = np.random.default_rng(seed)
+    D = rng.uniform(0.0, 1.0, (30, 80))
+    D[rng.uniform(size=D.shape) < 0.6] = 0.0
+    b = D @ rng.uniform(0.0, 1.0, 80)
+    p = gen.Problem(f"lp{seed}", 30, 80, "dense", np.ascontiguousarray(D), b=b)
+    return p.as_csr() if fmt == "csr" else p
+
+
+@pytest.mark.parametrize("fmt", ["dense", "csr"])
+def test_ta_lp_trajectory_and_feasible_solve(tacta, fmt):
+    import torch
+    p = _lp_problem(21, fmt)
+    A, b = dev(p)
+    Ao = oracle.make_operator(p)
+    x, hist, info = tacta.ta_solve(A, b, tol=1e-30, tol_normal=0.0, max_iter=25, nonneg=1)
+    ref = oracle.ta_solve(Ao, p.b, tol=1e-30, tol_normal=0.0, max_iter=25, nonneg=True)
+    assert info["iters"] == ref.iters == 25
+    assert relerr(x.cpu().numpy(), ref.x) <= X_TOL
+    assert info["rho"] == pytest.approx(ref.rho, rel=1e-12)
+    x, hist, info = tacta.ta_solve(A, b, tol=1e-6, tol_normal=0.0, max_iter=200000, nonneg=1)
+    xg = x.cpu().numpy()
+    assert info["reason_name"] == "RESIDUAL" and info["rel_res"] <= 1e-6
+    assert xg.min() >= 0.0
+    D = p.to_dense()
+    assert np.linalg.norm(D @ xg - p.b) <= 1e-6 * np.linalg.norm(p.b) * (1 + 1e-9)
+
+
+def test_ta_lp_rho_bound(tacta):
+    import torch
+    D = np.array([[1.0, 1.0], [1.0, 1.001]])
+    A = torch.from_numpy(D).to("cuda:0")
+    b = torch.tensor([1.0, -1.0], dtype=torch.float64, device="cuda:0")
+    x, _, info = tacta.ta_solve(A, b, tol=1e-9, tol_normal=1e-12, max_iter=100000, nonneg=1, rho_max=1e6)
+    ref = oracle.ta_solve(oracle.Operator(2, 2, "dense", dense=D), np.array([1.0, -1.0]), tol=1e-9,
+                          tol_normal=1e-12, max_iter=100000, nonneg=True, rho_max=1e6)
+    assert info["reason_name"] == REASON.get(int(ref.reason), ref.reason.name)
+    assert x.cpu().numpy().min() >= 0.0

@@ -98,3 +98,13 @@ def test_mutation_hankel_rhs_off_by_one(monkeypatch):
     monkeypatch.setattr(ocx, "hankel_solve", ns["hankel_solve"])
     monkeypatch.setattr(oracle, "hankel_solve", ns["hankel_solve"])
     _fails(pins.test_hankel_golden_closed_forms)
+
+
+def test_mutation_lp_uses_c_instead_of_c_plus(monkeypatch):
+    """Sec. 6: the LP form must replace c by c_+; keeping c breaks x' >= 0 and the golden."""
+    import inspect
+    src = inspect.getsource(otx._ta_loop).replace("c = np.maximum(c, 0.0)", "c = c")
+    ns = dict(otx.__dict__)
+    exec(compile(src, "<mutant>", "exec"), ns)
+    monkeypatch.setattr(otx, "_ta_loop", ns["_ta_loop"])
+    _fails(pins.test_ta_lp_identity_golden)

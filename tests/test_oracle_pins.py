@@ -524,3 +524,41 @@ def test_ta_minnorm_hybrid_consistent():
     xs = minnorm(D, b)
     assert res.rho_lower <= np.linalg.norm(xs) * (1 + 1e-12)
     assert np.linalg.norm(res.x - xs) <= 1e-3 * np.linalg.norm(xs)
+
+
+# --------------------------------------------------------------------------- TA for LP feasibility (Sec. 6)
+
+def test_ta_lp_identity_golden():
+    g = golden("ta_lp_identity.json")
+    rhos = []
+    res = oracle.ta_solve(op_dense(g["A"]), np.array(g["b"]), tol=1e-14, tol_normal=1e-14, max_iter=10,
+                          nonneg=True, observer=lambda k, x, bp, rho, a: rhos.append(rho))
+    assert rhos[0] == pytest.approx(g["rho_after_1"], rel=1e-15)
+    assert res.iters == g["iters"] and res.reason == Reason.WITNESS     # Farkas: b_2 < 0
+    np.testing.assert_allclose(res.x, g["x_final"], rtol=1e-14, atol=1e-14)
+
+
+def test_ta_lp_feasible_keeps_nonnegative_iterates():
+    """Sec. 6: with b = A x_+ for some x_+ >= 0 the c_+ iteration finds x >= 0 with
+    ||Ax - b|| <= tol ||b||; every iterate is a convex combination of nonnegative
+    vectors, so x' >= 0 throughout."""
+    rng = np.random.default_rng(21)
+    D = rng.uniform(0.0, 1.0, (8, 20))
+    xp = rng.uniform(0.0, 1.0, 20)
+    b = D @ xp
+    neg = []
+    res = oracle.ta_solve(op_dense(D), b, tol=1e-6, tol_normal=0.0, max_iter=200000, nonneg=True,
+                          observer=lambda k, x, bp, rho, a: neg.append(x.min()))
+    assert res.reason == Reason.RESIDUAL and res.rel_res <= 1e-6 * (1 + 1e-9)
+    assert min(neg) >= 0.0 and res.x.min() >= 0.0
+
+
+def test_ta_lp_infeasible_hits_rho_bound():
+    """b with no nonnegative preimage: c_+ keeps an ascent direction along which rho grows
+    without the residual closing; the termination bound on rho ends the test."""
+    D = np.array([[1.0, 1.0], [1.0, 1.0 + 1e-3]])
+    b = np.array([1.0, -1.0])                   # x = A^{-1} b has mixed signs
+    res = oracle.ta_solve(op_dense(D), b, tol=1e-9, tol_normal=1e-12, max_iter=100000, nonneg=True,
+                          rho_max=1e6)
+    assert res.reason in (Reason.RHO_BOUND, Reason.WITNESS)
+    assert res.x.min() >= 0.0 and res.rel_res > 1e-3
