@@ -121,6 +121,7 @@ struct DevCSR {          // CSR operand in device memory (rows x cols)
 // Banded operands (every tile's columns span at most kXSpan entries of x) also
 // stage the tile's x window in shared memory: kind 3.
 constexpr int kXSpan = 2560;
+constexpr int kXCapCompactPlan = 1280, kXSpanCompactPlan = 2304;   // compact x-window instance
 // every plan vector that can be a product's input carries this many doubles of
 // padding, so 16-byte-rounded x-window copies stay inside the allocation
 constexpr int kPadVec = 2;

@@ -579,18 +579,24 @@ spmv_tiled(const int4* __restrict__ tiles, int ntiles, const int32_t* __restrict
 // x from shared memory and the narrow FP64 pipe is not left waiting on global
 // gathers.
 
-template <int CAP>
+template <int CAP, int XS>
 struct __align__(16) TileStageX {
     double vals[CAP + 2];
     int32_t cols[CAP + 4];
     int32_t rp[kTileRows + 8];
-    double xs[kXSpan + 2];
+    double xs[XS + 2];
 };
 
-size_t spmv_tiled_x_smem() { return 2 * sizeof(TileStageX<kTileCapSmall>); }
+// two instances: a compact one (three blocks per SM) for tiles of <= 1280 nonzeros whose
+// x windows span <= 2304 entries (e.g. 5-point stencils up to 1000 columns of bandwidth),
+// and the general one (two blocks per SM)
+constexpr int kXCapCompact = kXCapCompactPlan, kXSpanCompact = kXSpanCompactPlan;
 
-template <int CAP>
-__device__ __forceinline__ void tile_issue_x(const int4 d, const int2 w, TileStageX<CAP>* st,
+template <int CAP, int XS>
+size_t spmv_tiled_x_smem() { return 2 * sizeof(TileStageX<CAP, XS>); }
+
+template <int CAP, int XS>
+__device__ __forceinline__ void tile_issue_x(const int4 d, const int2 w, TileStageX<CAP, XS>* st,
                                              uint64_t* bar, const int32_t* rowptr,
                                              const int32_t* colidx, const double* vals,
                                              const double* x) {
@@ -606,17 +612,16 @@ __device__ __forceinline__ void tile_issue_x(const int4 d, const int2 w, TileSta
     if (bx) bulk_g2s(st->xs, x + x0, bx, bar);
 }
 
-template <int EPI>
+template <int CAP, int XS, int EPI>
 __global__ void __launch_bounds__(kTileRows)
 spmv_tiled_x(const int4* __restrict__ tiles, const int2* __restrict__ xwin, int ntiles,
              const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
              const double* __restrict__ vals, const double* __restrict__ x, double* __restrict__ y,
              EpiArgs e, Ctl* ctl, double* partials, FinArgs f, int gate) {
-    constexpr int CAP = kTileCapSmall;
     if (gated_out(ctl, gate)) return;
     if (gate != GATE_FORCE && blockIdx.x == 0 && threadIdx.x == 0) ctl->matvecs += 1;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    TileStageX<CAP>* st = reinterpret_cast<TileStageX<CAP>*>(smem_raw);
+    TileStageX<CAP, XS>* st = reinterpret_cast<TileStageX<CAP, XS>*>(smem_raw);
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int failed;
     const int tid = threadIdx.x;
@@ -629,7 +634,7 @@ spmv_tiled_x(const int4* __restrict__ tiles, const int2* __restrict__ xwin, int 
         for (int j = 0; j < 2; ++j) {
             const int t = blockIdx.x + j * G;
             if (t < ntiles)
-                tile_issue_x<CAP>(__ldg(tiles + t), __ldg(xwin + t), st + j, bar + j, rowptr, colidx, vals, x);
+                tile_issue_x<CAP, XS>(__ldg(tiles + t), __ldg(xwin + t), st + j, bar + j, rowptr, colidx, vals, x);
         }
     }
     __syncthreads();
@@ -646,7 +651,7 @@ spmv_tiled_x(const int4* __restrict__ tiles, const int2* __restrict__ xwin, int 
             failed = 1;
             atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
         }
-        const TileStageX<CAP>* S = st + sidx;
+        const TileStageX<CAP, XS>* S = st + sidx;
         const int row = d.x + tid;
         const bool active = ok && row < d.y;
         int kb = 0, len = 0;
@@ -666,8 +671,8 @@ spmv_tiled_x(const int4* __restrict__ tiles, const int2* __restrict__ xwin, int 
         if (tid == 0 && !failed) {
             const int t2 = t + 2 * G;
             if (t2 < ntiles)
-                tile_issue_x<CAP>(__ldg(tiles + t2), __ldg(xwin + t2), st + sidx, bar + sidx, rowptr,
-                                  colidx, vals, x);
+                tile_issue_x<CAP, XS>(__ldg(tiles + t2), __ldg(xwin + t2), st + sidx, bar + sidx, rowptr,
+                                      colidx, vals, x);
         }
     }
     if (failed && tid == 0) {
@@ -679,10 +684,18 @@ spmv_tiled_x(const int4* __restrict__ tiles, const int2* __restrict__ xwin, int 
 template <int EPI>
 static cudaError_t spmv_tiled_x_launch(const LaunchCtx& L, const DevCSR& A, const double* x, double* y,
                                        EpiArgs e, FinArgs f, int gate) {
-    // two 46 KB stages per block: two blocks per SM
-    int grid = std::min(A.ntiles, std::max(1, (L.max_grid / 8) * 2));
-    spmv_tiled_x<EPI><<<grid, kTileRows, spmv_tiled_x_smem(), L.stream>>>(
-        A.tiles, A.xwin, A.ntiles, A.rowptr, A.colidx, A.vals, x, y, e, L.ctl, L.partials, f, gate);
+    const int sms = L.max_grid / 8;
+    if (A.cap == kXCapCompact) {   // two 36 KB stages per block: three blocks per SM
+        const int grid = std::min(A.ntiles, std::max(1, sms * 3));
+        spmv_tiled_x<kXCapCompact, kXSpanCompact, EPI>
+            <<<grid, kTileRows, spmv_tiled_x_smem<kXCapCompact, kXSpanCompact>(), L.stream>>>(
+                A.tiles, A.xwin, A.ntiles, A.rowptr, A.colidx, A.vals, x, y, e, L.ctl, L.partials, f, gate);
+    } else {                       // two 46 KB stages per block: two blocks per SM
+        const int grid = std::min(A.ntiles, std::max(1, sms * 2));
+        spmv_tiled_x<kTileCapSmall, kXSpan, EPI>
+            <<<grid, kTileRows, spmv_tiled_x_smem<kTileCapSmall, kXSpan>(), L.stream>>>(
+                A.tiles, A.xwin, A.ntiles, A.rowptr, A.colidx, A.vals, x, y, e, L.ctl, L.partials, f, gate);
+    }
     if (L.launches) ++*L.launches;
     return cudaGetLastError();
 }
@@ -702,10 +715,15 @@ cudaError_t spmv_tiled_prepare() {
     TACTA_TILED_ATTR(kTileCapSmall, EPI_RESID_F32) TACTA_TILED_ATTR(kTileCapLarge, EPI_RESID_F32)
     TACTA_TILED_ATTR(kTileCapSmall, EPI_NORM_POS) TACTA_TILED_ATTR(kTileCapLarge, EPI_NORM_POS)
 #undef TACTA_TILED_ATTR
-#define TACTA_TILED_X_ATTR(EPI)                                                                      \
-    if (e == cudaSuccess)                                                                            \
-        e = cudaFuncSetAttribute(spmv_tiled_x<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                 (int)spmv_tiled_x_smem());
+#define TACTA_TILED_X_ATTR(EPI)                                                                          \
+    if (e == cudaSuccess)                                                                                \
+        e = cudaFuncSetAttribute(spmv_tiled_x<kTileCapSmall, kXSpan, EPI>,                               \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
+                                 (int)spmv_tiled_x_smem<kTileCapSmall, kXSpan>());                       \
+    if (e == cudaSuccess)                                                                                \
+        e = cudaFuncSetAttribute(spmv_tiled_x<kXCapCompact, kXSpanCompact, EPI>,                         \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,                            \
+                                 (int)spmv_tiled_x_smem<kXCapCompact, kXSpanCompact>());
     TACTA_TILED_X_ATTR(EPI_NONE) TACTA_TILED_X_ATTR(EPI_NORM) TACTA_TILED_X_ATTR(EPI_RESID)
     TACTA_TILED_X_ATTR(EPI_TAPIVOT) TACTA_TILED_X_ATTR(EPI_RESID_F32) TACTA_TILED_X_ATTR(EPI_NORM_POS)
 #undef TACTA_TILED_X_ATTR

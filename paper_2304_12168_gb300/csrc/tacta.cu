@@ -230,6 +230,13 @@ static cudaError_t setup_csr_kernel(DevCSR& a, cudaStream_t s) {
             if (hi - (lo & ~1) + 1 > kXSpan) banded = false;
         }
         if (banded) {
+            // the compact instance (three blocks per SM) when every tile fits it
+            int32_t max_nnz = 0, max_span = 0;
+            for (size_t t = 0; t < tiles.size(); ++t) {
+                max_nnz = std::max(max_nnz, tiles[t].w - tiles[t].z);
+                max_span = std::max(max_span, win[t].y - (win[t].x & ~1) + 1);
+            }
+            if (max_nnz <= kXCapCompactPlan && max_span <= kXSpanCompactPlan) a.cap = kXCapCompactPlan;
             if ((e = cudaMalloc(&a.xwin, sizeof(int2) * win.size())) != cudaSuccess) return e;
             if ((e = cudaMemcpyAsync(a.xwin, win.data(), sizeof(int2) * win.size(), cudaMemcpyHostToDevice, s)) !=
                 cudaSuccess) return e;
