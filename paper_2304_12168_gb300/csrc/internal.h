@@ -45,6 +45,8 @@ struct Ctl {
     double rho;            // TA: radius
     double rho_max;        // TA: termination bound on rho (infinity: none)
     double cs2;            // chain scale²: the chain's moments are cs2^k phi_k (1 on the FP64 path)
+    double ref_eta2;       // mixed CTA: refine once ||r||² <= ref_eta2 * ||r||² at the last refinement (0: off)
+    double ref_thr;        // that threshold, set by each true residual
     double phi[2 * kTMax + 2];
     double alpha[kTMax];
     double red[4];         // scratch results of setup reductions
@@ -115,6 +117,9 @@ struct DevCSR {          // CSR operand in device memory (rows x cols)
     int ntiles = 0;
     int cap = 0;                 // kind 2: nonzero capacity of a tile
     int2* xwin = nullptr;        // kind 3: per tile {first column, last column} of its x window
+    // kind 3 operands whose tiles draw on at most kRunMax short runs of x also carry:
+    uint16_t* lcol = nullptr;    // per nonzero: its column's slot in the tile's staged runs (nnz + kPadLcol)
+    int2* runs = nullptr;        // per tile kRunMax {first column (even), length (even; 0 = unused)}
     SpmvCfg cfg{};
 };
 
@@ -122,6 +127,16 @@ struct DevCSR {          // CSR operand in device memory (rows x cols)
 // stage the tile's x window in shared memory: kind 3.
 constexpr int kXSpan = 2560;
 constexpr int kXCapCompactPlan = 1280, kXSpanCompactPlan = 2304;   // compact x-window instance
+// Run-staged operands: a tile's distinct columns form at most kRunMax runs (a gap of
+// more than kRunGap columns starts a new run) of kRunXs entries of x in total, and the
+// tile holds at most kRunCap nonzeros. Only those runs of x are staged, and column
+// indices shrink to 16-bit slots in them.
+constexpr int kRunCap = 1280, kRunXs = 896, kRunMax = 4, kRunGap = 16;
+constexpr int kPadLcol = 8;
+// Mixed-precision CTA refines (FP64 residual, fold of the FP32 correction) as soon as
+// the FP32 inner iteration has reduced the residual by kRefineEta over the last
+// refinement; the FP32 chain cannot resolve much more than that.
+constexpr double kRefineEta2 = 1e-6;
 // every plan vector that can be a product's input carries this many doubles of
 // padding, so 16-byte-rounded x-window copies stay inside the allocation
 constexpr int kPadVec = 2;

@@ -161,9 +161,9 @@ static void plan_free(Plan* p) {
     cudaSetDevice(p->device);
     free_graphs(p);
     auto F = [](void* q) { if (q) cudaFree(q); };
-    F(p->A.csr.rowptr); F(p->A.csr.colidx); F(p->A.csr.vals); F(p->A.csr.tiles); F(p->A.csr.xwin);
+    F(p->A.csr.rowptr); F(p->A.csr.colidx); F(p->A.csr.vals); F(p->A.csr.tiles); F(p->A.csr.xwin); F(p->A.csr.runs); F(p->A.csr.lcol);
     F(p->A.dense.vals);
-    F(p->At.csr.rowptr); F(p->At.csr.colidx); F(p->At.csr.vals); F(p->At.csr.tiles); F(p->At.csr.xwin);
+    F(p->At.csr.rowptr); F(p->At.csr.colidx); F(p->At.csr.vals); F(p->At.csr.tiles); F(p->At.csr.xwin); F(p->At.csr.runs); F(p->At.csr.lcol);
     F(p->At.dense.vals);
     F(p->ctl); F(p->partials); F(p->flag_dev);
     F(p->b); F(p->x); F(p->r); F(p->tmp_m); F(p->tmp_n);
@@ -186,6 +186,51 @@ static void plan_free(Plan* p) {
 // thread, every lane busy), provided no single row exceeds a tile's capacity.
 // Tiles: greedy runs of consecutive rows, at most kTileRows rows and `cap`
 // nonzeros each, described by {row begin, row end, nnz begin, nnz end}.
+// Runs of x for the run-staged product: per tile, the distinct columns (inside the
+// tile's window win[t]) split where the gap exceeds kRunGap; each run starts on an even
+// column and has an even length (16-byte bulk copies), and lcol maps every nonzero to
+// its slot in the runs laid end to end. False when a tile needs more than kRunMax runs
+// or kRunXs staged entries.
+static bool build_runs(const std::vector<int4>& tiles, const std::vector<int2>& win,
+                       const std::vector<int32_t>& ci, std::vector<int2>& runs, std::vector<uint16_t>& lcol) {
+    runs.assign(tiles.size() * kRunMax, make_int2(0, 0));
+    lcol.assign(ci.size() + kPadLcol, 0);
+    std::vector<uint8_t> used(kXSpan + 2);
+    for (size_t t = 0; t < tiles.size(); ++t) {
+        const int z = tiles[t].z, w = tiles[t].w;
+        if (w == z) continue;
+        const int lo = win[t].x, span = win[t].y - win[t].x + 1;
+        std::fill(used.begin(), used.begin() + span, 0);
+        for (int k = z; k < w; ++k) used[ci[k] - lo] = 1;
+        int2* rt = &runs[t * kRunMax];
+        int nrun = 0, total = 0, first = -1, last = -1;
+        auto close_run = [&]() {
+            if (nrun == kRunMax) return false;
+            const int c0 = (lo + first) & ~1;
+            const int len = (lo + last + 1 - c0 + 1) & ~1;
+            rt[nrun++] = make_int2(c0, len);
+            total += len;
+            return total <= kRunXs;
+        };
+        for (int c = 0; c < span; ++c) {
+            if (!used[c]) continue;
+            if (first >= 0 && c - last > kRunGap) {
+                if (!close_run()) return false;
+                first = -1;
+            }
+            if (first < 0) first = c;
+            last = c;
+        }
+        if (!close_run()) return false;
+        for (int k = z; k < w; ++k) {
+            int off = 0, r = 0;
+            while (ci[k] >= rt[r].x + rt[r].y) off += rt[r++].y;
+            lcol[k] = (uint16_t)(off + ci[k] - rt[r].x);
+        }
+    }
+    return true;
+}
+
 static cudaError_t setup_csr_kernel(DevCSR& a, cudaStream_t s) {
     const double avg = a.rows > 0 ? (double)a.nnz / (double)a.rows : 0.0;
     a.cfg.kind = 1;
@@ -242,6 +287,17 @@ static cudaError_t setup_csr_kernel(DevCSR& a, cudaStream_t s) {
                 cudaSuccess) return e;
             if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
             a.cfg.kind = 3;
+            std::vector<int2> runs;
+            std::vector<uint16_t> lcol;
+            if (max_nnz <= kRunCap && build_runs(tiles, win, ci, runs, lcol)) {
+                if ((e = cudaMalloc(&a.runs, sizeof(int2) * runs.size())) != cudaSuccess) return e;
+                if ((e = cudaMalloc(&a.lcol, sizeof(uint16_t) * lcol.size())) != cudaSuccess) return e;
+                if ((e = cudaMemcpyAsync(a.runs, runs.data(), sizeof(int2) * runs.size(), cudaMemcpyHostToDevice,
+                                         s)) != cudaSuccess) return e;
+                if ((e = cudaMemcpyAsync(a.lcol, lcol.data(), sizeof(uint16_t) * lcol.size(), cudaMemcpyHostToDevice,
+                                         s)) != cudaSuccess) return e;
+                if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+            }
         }
     }
     return spmv_tiled_prepare();
@@ -721,7 +777,10 @@ static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t h
     LaunchCtx L{O.s, p->ctl, p->partials, p->grid, launches};
     Ctl h = base_ctl(O, hist_cap);
     h.need_true = (x0 || mixed) ? 1 : 0;
-    if (mixed) h.cs2 = (double)p->chain_scale * (double)p->chain_scale;
+    if (mixed) {
+        h.cs2 = (double)p->chain_scale * (double)p->chain_scale;
+        h.ref_eta2 = kRefineEta2;
+    }
     if ((st = write_ctl(p, O.s, h)) != TACTA_OK) return st;
     EpiArgs none{nullptr, nullptr, nullptr};
     CUDA_TRY(launch_reduce_vec(L, p->m, p->b, nullptr, FinArgs{FIN_SETUP_B, 0, nullptr}, GATE_ALWAYS));

@@ -141,3 +141,37 @@ def test_min_norm_2000x8000_gradient(tacta):
     Lm = _loss(cta_solve_autograd(A.detach(), bt.detach() - h * torch.tensor(v, device="cuda:0"), **opts), xtt)
     fd = (Lp - Lm).item() / (2 * h)
     assert fd == pytest.approx(float(bt.grad.cpu().numpy() @ v), rel=1e-5)
+
+
+def test_stencil_256_forward_and_adjoint_trajectories(tacta):
+    """The 256 x 256 stencil (n = 65,536) of the differentiable workload. CTA needs far more
+    than a test's worth of iterations to converge there, so the forward and the adjoint
+    solve run eight steps each and are compared with the oracle's eight-step trajectories
+    on A and Aᵀ; the pattern gradient must equal -lambda[row] x[col] exactly."""
+    import torch
+    import paper_2304_12168_gb300 as t
+    from paper_2304_12168_gb300.autograd import cta_solve_autograd
+    p = gen.convdiff_stencil(256)
+    d = "cuda:0"
+    opts = dict(tol=1e-30, tol_normal=0.0, max_iter=8)
+    vals = torch.tensor(p.vals, device=d, requires_grad=True)
+    A = t.CSR(torch.from_numpy(p.rowptr).to(d), torch.from_numpy(p.colidx).to(d), vals, (p.m, p.n))
+    bt = torch.tensor(p.b, device=d, requires_grad=True)
+    xt = np.random.default_rng(4).standard_normal(p.n)
+    x = cta_solve_autograd(A, bt, **opts)
+    _loss(x, torch.tensor(xt, device=d)).backward()
+    import oracle
+    S = p.scipy()
+    Ao = oracle.make_operator(p)
+    ref = oracle.cta_solve(Ao, p.b, **opts)
+    xs = x.detach().cpu().numpy()
+    assert np.linalg.norm(xs - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+    ST = S.T.tocsr()
+    pt = gen.Problem(name="stencil_T", m=p.n, n=p.m, fmt="csr", rowptr=ST.indptr.astype(np.int32),
+                     colidx=ST.indices.astype(np.int32), vals=ST.data.astype(np.float64),
+                     b=2 * (xs - xt))
+    lam_ref = oracle.cta_solve(oracle.make_operator(pt), pt.b, **opts).x
+    lam = bt.grad.cpu().numpy()
+    assert np.linalg.norm(lam - lam_ref) <= 1e-9 * np.linalg.norm(lam_ref)
+    rows = np.repeat(np.arange(p.m), np.diff(p.rowptr))
+    np.testing.assert_array_equal(vals.grad.cpu().numpy(), -lam[rows] * xs[p.colidx])
