@@ -129,11 +129,19 @@ def test_cta_single_step_from_oracle_states(tacta, t):
         x, hist, info = tacta.cta_solve(A, b, torch.from_numpy(xk).to("cuda:0"), tol=1e-30,
                                         tol_normal=0.0, max_iter=1, t_max=t, cycle=2)
         ref = oracle.cta_solve(Ao, p.b, xk, tol=1e-30, tol_normal=0.0, max_iter=1, t_max=t, cycle=2)
+        # the order-t auxiliary solve amplifies rounding late in the trajectory: the
+        # moments summed in another order differ by ~sqrt(n) u relative, so the oracle's
+        # own spread under a perturbation of x_k of that size bounds what any summation
+        # order can reproduce
+        eps = np.sqrt(p.n) * 2.0 ** -53
+        xp = xk * (1 + eps * np.random.default_rng(k + t).standard_normal(p.n))
+        refp = oracle.cta_solve(Ao, p.b, xp, tol=1e-30, tol_normal=0.0, max_iter=1, t_max=t, cycle=2)
+        spread = np.linalg.norm((refp.x - xp) - (ref.x - xk))
         # x'' - x' loses digits to cancellation once the step is small next to x':
-        # judge the step to 1e-9 of itself plus rounding of ||x'||
+        # judge the step to 1e-9 of itself (or the spread) plus rounding of ||x'||
         step_o = ref.x - xk
         dx = np.linalg.norm(x.cpu().numpy() - ref.x)
-        assert dx <= X_TOL * np.linalg.norm(step_o) + 1e-14 * np.linalg.norm(xk), (k, dx)
+        assert dx <= max(X_TOL * np.linalg.norm(step_o), 10 * spread) + 1e-14 * np.linalg.norm(xk), (k, dx, spread)
         assert hist.cpu().numpy()[1] == pytest.approx(ref.hist[1], rel=1e-9)
 
 
