@@ -211,7 +211,62 @@ def extra_workloads(tacta, dev, stream, plan_stencil, b_stencil, steps):
     out["cta_fp64_clement_100001"] = {"value": info["iters"] / (t * 1e-3), "unit": UNIT,
                                       "iters": info["iters"], "rel_res": info["rel_res"]}
     plan.close()
+    out["batched_dense_4096"] = batched_workload(tacta, dev, stream)
     return out
+
+
+def batched_workload(tacta, dev, stream):
+    """4096 uneven dense systems (m in [32, 512], n in [m/2, 2m], 10% rank m/2) to 1e-8:
+    one persistent launch per storage precision (autotuned launch shape), against the
+    single-system FP64 path (Plan per system) timed on an evenly spaced sample."""
+    import gen
+    import numpy as np
+    import torch
+    B0 = gen.dense_batch(4096, seed=7)
+    b = torch.from_numpy(B0.packed_b()).to(dev)
+    mats = [torch.from_numpy(a).to(dev) for a in B0.mats]
+    kw = dict(tol=TOL, tol_normal=0.0, max_iter=20000)
+    res = {"workload": "4096 dense systems, m ~ U[32,512], n ~ U[m/2,2m], 10% rank m/2, b = A x*",
+           "entries": int(sum(a.size for a in B0.mats)), "tol": TOL, "max_iter_per_system": 20000}
+    for name, st in (("fp64", tacta.BATCH_FP64), ("fp32", tacta.BATCH_FP32), ("bf16", tacta.BATCH_BF16)):
+        B = tacta.Batch(mats, storage=st)
+        cfg, _ = B.tune(b, tol=TOL, tol_normal=0.0, max_iter=100)
+        B.cta(b, **kw)                                       # warm (graph capture)
+        t, (x, iters, rel, reason) = timed(lambda: B.cta(b, **kw), stream)
+        conv = reason == 1
+        res[name] = {"time_ms": t, "converged": int(conv.sum()), "maxiter": int((reason == 3).sum()),
+                     "system_iters": int(iters.sum()), "system_iters_per_s": float(iters.sum() / (t * 1e-3)),
+                     "max_rel_res_converged": float(rel[conv].max()) if conv.any() else None,
+                     "config": tacta.Batch.configs()[cfg]}
+        B.close()
+    # single-system FP64 path on a sample, extrapolated to the batch
+    idx = np.linspace(0, B0.count - 1, 24).astype(int)
+    tot, its = 0.0, 0
+    for s_ in idx:
+        plan = tacta.Plan(mats[s_])
+        plan.cta(torch.from_numpy(B0.bs[s_]).to(dev), **kw)
+        t, (x, _, info) = timed(lambda: plan.cta(torch.from_numpy(B0.bs[s_]).to(dev), **kw), stream)
+        tot += t
+        its += info["iters"]
+        plan.close()
+    res["plan_fp64_per_system_sample"] = {"systems": len(idx), "mean_ms": tot / len(idx),
+                                          "extrapolated_batch_ms": tot / len(idx) * B0.count,
+                                          "system_iters_per_s": its / (tot * 1e-3)}
+    for name in ("fp64", "fp32", "bf16"):
+        res[name]["speedup_over_plan_fp64"] = res["plan_fp64_per_system_sample"]["extrapolated_batch_ms"] / \
+            res[name]["time_ms"]
+    return res
+
+
+def timed(fn, stream):
+    import torch
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record(stream)
+    r = fn()
+    e.record(stream)
+    torch.cuda.synchronize()
+    return s.elapsed_time(e), r
 
 
 def cpu_baseline(p, iters):

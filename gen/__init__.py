@@ -17,7 +17,9 @@ Shapes and structure follow the paper's workloads:
   * the Clement tridiagonal matrix (Sec. 5.1, Clement tables),
   * an LP-like rectangular m << n sparse matrix with duplicated scaled rows
     (stand-in for the lpnetlib set of Sec. 5.2, which is not available here),
-  * small ragged / empty-row CSR matrices for edge cases.
+  * small ragged / empty-row CSR matrices for edge cases,
+  * batches of uneven dense systems (m in [32, 512], n in [m/2, 2m], 10% of rank
+    m/2) for the batched solver.
 """
 from __future__ import annotations
 
@@ -28,7 +30,7 @@ import scipy.sparse as sp
 
 __all__ = [
     "Problem", "dense_gaussian", "dense_low_rank", "convdiff_stencil",
-    "clement", "lp_rect", "random_csr", "diag_matrix",
+    "clement", "lp_rect", "random_csr", "diag_matrix", "DenseBatch", "dense_batch",
 ]
 
 
@@ -214,3 +216,43 @@ def diag_matrix(d: np.ndarray, x_known=None) -> Problem:
     A = sp.diags(d, 0, shape=(n, n), format="csr")
     A.eliminate_zeros()
     return _from_scipy(f"diag_{n}", A, np.ones(n) if x_known is None else x_known)
+
+
+@dataclass
+class DenseBatch:
+    """Independent dense systems A_s x = b_s, b_s = A_s x*_s (consistent)."""
+    mats: list                     # A_s, (m_s, n_s) float64 C order
+    bs: list                       # b_s
+    xstar: list                    # x*_s
+    low_rank: np.ndarray           # bool per system: A_s = U V^T of rank m_s / 2
+
+    @property
+    def count(self) -> int:
+        return len(self.mats)
+
+    def packed_b(self) -> np.ndarray:
+        return np.concatenate(self.bs) if self.bs else np.zeros(0)
+
+
+def dense_batch(count: int = 4096, m_range=(32, 512), low_rank_frac: float = 0.1,
+                seed: int = 7) -> DenseBatch:
+    """Uneven dense systems: m uniform in m_range, n uniform in [ceil(m/2), 2m], entries
+    N(0,1); a fraction low_rank_frac is U V^T of rank floor(m/2) (U, V Gaussian, scaled to
+    unit-variance entries); b = A x* with x* ~ N(0,1)."""
+    rng = np.random.default_rng(seed)
+    mats, bs, xs = [], [], []
+    lr = np.zeros(count, dtype=bool)
+    for s in range(count):
+        m = int(rng.integers(m_range[0], m_range[1] + 1))
+        n = int(rng.integers((m + 1) // 2, 2 * m + 1))
+        if rng.random() < low_rank_frac:
+            r = max(1, m // 2)
+            A = (rng.standard_normal((m, r)) @ rng.standard_normal((r, n))) / np.sqrt(r)
+            lr[s] = True
+        else:
+            A = rng.standard_normal((m, n))
+        x = rng.standard_normal(n)
+        mats.append(np.ascontiguousarray(A))
+        xs.append(x)
+        bs.append(A @ x)
+    return DenseBatch(mats=mats, bs=bs, xstar=xs, low_rank=lr)

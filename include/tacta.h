@@ -232,6 +232,68 @@ tacta_status tacta_plan_outer(tacta_plan plan, double alpha, const double* u, co
 tacta_status tacta_residual_static(const tacta_matrix* A, const double* x, const double* b,
                                    double* r_out, double* norms_out, void* stream);
 
+/*
+ * Batched dense systems -- tacta_batch_*
+ *   Many independent systems A_s x_s = b_s (s = 0 .. count-1), A_s dense m_s x n_s,
+ *   each solved by CTA (Alg. 1.1 with H = A_s A_sᵀ and the t-cycling of Sec. 5.1)
+ *   from x_s = 0, so that x_s stays in range(A_sᵀ) (Thm. thmone (4)) and a consistent
+ *   rank-deficient system yields the minimum-norm solution. All systems run in one
+ *   persistent kernel launch (replayed as a CUDA graph when opt->use_graph is set):
+ *   each thread block takes the next unsolved system from a queue, largest first.
+ *   The paper treats one system at a time; batching is this library's extension.
+ *
+ *   Storage of the copy of A_s that the chain z_i = Aᵀ u_{i-1}, u_i = A z_i reads:
+ *     TACTA_BATCH_FP64 -- FP64 chain; the iteration follows the FP64 path exactly.
+ *     TACTA_BATCH_FP32 -- FP32 values and chain (FP32 accumulation).
+ *     TACTA_BATCH_BF16 -- BF16 values widened to FP32 (FP32 accumulation).
+ *   In every mode the moments, the auxiliary solve (Eq. eqcoeff) and the stop
+ *   tests are FP64, and the residual b - A x is recomputed in FP64 from an FP64
+ *   copy of A_s: every recompute_every steps, whenever the carried residual passes
+ *   the tolerance (a pass counts only on the recomputed residual), and -- FP32 and
+ *   BF16 -- once the carried residual has fallen by 1e-3 since the last recompute,
+ *   where the FP32 correction is folded into the FP64 x (iterative refinement).
+ *   A low-precision copy perturbs A_s by up to its unit roundoff (2^-24 FP32,
+ *   2^-9 BF16): refinement still drives the FP64 residual to tol while
+ *   cond(A_s) times that roundoff stays below one, and the solution's component
+ *   outside range(A_sᵀ) is of that relative size.
+ *
+ *   Layout: the systems are packed back to back in system order -- A_s row-major
+ *   at element sum_{j<s} m_j n_j of vals, b_s at sum_{j<s} m_j of b, x_s at
+ *   sum_{j<s} n_j of x. 1 <= m_s, n_s <= 4096; the chain's vectors of the largest
+ *   system must fit a block's shared memory ((t_max + 1)(m_max + n_max) values),
+ *   else tacta_batch_cta returns TACTA_ERR_INVALID.
+ */
+typedef struct tacta_batch_s* tacta_batch;
+enum { TACTA_BATCH_FP64 = 0, TACTA_BATCH_FP32 = 1, TACTA_BATCH_BF16 = 2 };
+
+/* tacta_batch_create -- copy the count systems' matrices (vals, FP64, host or device per
+   on_device; m and n are host arrays) to the device, with the storage copy and each
+   system's chain scale. Uses opt->stream only. The caller's arrays may be freed after. */
+tacta_status tacta_batch_create(int32_t count, const int32_t* m, const int32_t* n, const double* vals,
+                                int32_t on_device, int32_t storage, const tacta_options* opt,
+                                tacta_batch* out);
+
+/* tacta_batch_cta -- solve every system. b: sum m_s values, x: sum n_s values (host or
+   device, any: copies go through cudaMemcpyDefault). iters, rel_res (the recomputed FP64
+   ||b_s - A_s x_s|| / ||b_s||) and reason (TACTA_REASON_*) receive count values each and
+   may be NULL. Options used: tol, tol_normal, pivot_tol (0: 1e-12 FP64, 1e-6 otherwise),
+   max_iter (per system), t_max, cycle, recompute_every, use_graph, stream. */
+tacta_status tacta_batch_cta(tacta_batch batch, const double* b, double* x, int32_t* iters,
+                             double* rel_res, int32_t* reason, const tacta_options* opt);
+
+/* Launch configurations: threads per block and resident blocks per SM. The autotuner
+   times every configuration that fits on (batch, b) with the given options, keeps the
+   fastest for later solves and returns its index and time; set_config picks one
+   (-1: the default). */
+int32_t tacta_batch_num_configs(void);
+tacta_status tacta_batch_config_shape(int32_t config, int32_t* threads, int32_t* blocks_per_sm);
+tacta_status tacta_batch_tune(tacta_batch batch, const double* b, const tacta_options* opt,
+                              int32_t* best_config, double* best_ms);
+tacta_status tacta_batch_set_config(tacta_batch batch, int32_t config);
+void tacta_batch_destroy(tacta_batch batch);
+/* message of the last failed tacta_batch_* call on the calling thread */
+const char* tacta_batch_last_error(void);
+
 /* Description of the last error on the calling thread ("" if none). */
 const char* tacta_last_error(void);
 

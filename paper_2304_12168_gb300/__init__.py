@@ -66,7 +66,10 @@ class tacta_info(ctypes.Structure):
 EXPORTS = ["tacta_default_options", "cta_solve", "ta_solve", "ta_minnorm", "tacta_plan_create",
            "tacta_plan_cta", "tacta_plan_ta", "tacta_plan_minnorm", "tacta_plan_destroy",
            "tacta_plan_transpose", "tacta_plan_matvec", "tacta_plan_outer",
-           "tacta_residual_static", "tacta_last_error", "tacta_version"]
+           "tacta_residual_static", "tacta_last_error", "tacta_version",
+           "tacta_batch_create", "tacta_batch_cta", "tacta_batch_destroy", "tacta_batch_tune",
+           "tacta_batch_set_config", "tacta_batch_num_configs", "tacta_batch_config_shape",
+           "tacta_batch_last_error"]
 
 _lib_handle = None
 
@@ -107,6 +110,24 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tacta_plan_matvec.restype = ctypes.c_int32
     lib.tacta_plan_outer.argtypes = [vp, ctypes.c_double, dp, dp, dp, P(tacta_options)]
     lib.tacta_plan_outer.restype = ctypes.c_int32
+    i32p = P(ctypes.c_int32)
+    lib.tacta_batch_create.argtypes = [ctypes.c_int32, i32p, i32p, dp, ctypes.c_int32, ctypes.c_int32,
+                                       P(tacta_options), P(vp)]
+    lib.tacta_batch_create.restype = ctypes.c_int32
+    lib.tacta_batch_cta.argtypes = [vp, dp, dp, vp, vp, vp, P(tacta_options)]
+    lib.tacta_batch_cta.restype = ctypes.c_int32
+    lib.tacta_batch_destroy.argtypes = [vp]
+    lib.tacta_batch_destroy.restype = None
+    lib.tacta_batch_tune.argtypes = [vp, dp, P(tacta_options), i32p, P(ctypes.c_double)]
+    lib.tacta_batch_tune.restype = ctypes.c_int32
+    lib.tacta_batch_set_config.argtypes = [vp, ctypes.c_int32]
+    lib.tacta_batch_set_config.restype = ctypes.c_int32
+    lib.tacta_batch_num_configs.argtypes = []
+    lib.tacta_batch_num_configs.restype = ctypes.c_int32
+    lib.tacta_batch_config_shape.argtypes = [ctypes.c_int32, i32p, i32p]
+    lib.tacta_batch_config_shape.restype = ctypes.c_int32
+    lib.tacta_batch_last_error.argtypes = []
+    lib.tacta_batch_last_error.restype = ctypes.c_char_p
     _lib_handle = lib
     return lib
 
@@ -349,5 +370,100 @@ class Plan:
             pass
 
 
-__all__ = ["cta_solve", "ta_solve", "ta_minnorm", "residual_static", "Plan", "CSR", "load_library",
-           "make_options", "TactaError", "EXPORTS", "LIB_PATH"]
+BATCH_FP64, BATCH_FP32, BATCH_BF16 = 0, 1, 2
+
+
+def _check_batch(st: int):
+    if st < 0:
+        msg = load_library().tacta_batch_last_error().decode()
+        raise TactaError(f"{STATUS.get(st, st)}: {msg}")
+
+
+class Batch:
+    """Many independent dense systems solved by CTA in one persistent launch (tacta_batch_*).
+
+    mats: a list of 2-D float64 arrays (numpy or torch, all on the host or all on one
+    CUDA device). storage: BATCH_FP64, BATCH_FP32 or BATCH_BF16.
+    """
+
+    def __init__(self, mats, storage=BATCH_FP32, **opts):
+        lib = load_library()
+        self.m = np.array([int(a.shape[0]) for a in mats], dtype=np.int32)
+        self.n = np.array([int(a.shape[1]) for a in mats], dtype=np.int32)
+        self.count = len(mats)
+        self.on_device = bool(mats) and _is_cuda(mats[0])
+        if self.on_device:
+            import torch
+            flat = torch.cat([a.reshape(-1) for a in mats]) if mats else None
+        else:
+            flat = np.concatenate([np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in mats]) \
+                if mats else np.zeros(1)
+        pv, _, keep = _ptr(flat, np.float64)
+        o = make_options(self.on_device, **opts)
+        h = ctypes.c_void_p()
+        _check_batch(lib.tacta_batch_create(self.count, self.m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                            self.n.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), pv,
+                                            int(self.on_device), int(storage), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.b_offsets = np.concatenate([[0], np.cumsum(self.m, dtype=np.int64)])
+        self.x_offsets = np.concatenate([[0], np.cumsum(self.n, dtype=np.int64)])
+        del keep
+
+    def cta(self, b, **opts):
+        """Solve all systems; b packed (sum m values). Returns (x packed, iters, rel_res, reason)."""
+        lib = load_library()
+        pb, db_, kb = _ptr(b, np.float64)
+        o = make_options(db_, **opts)
+        x = _vec_out(int(self.x_offsets[-1]), db_, kb)
+        iters = np.zeros(self.count, dtype=np.int32)
+        rel = np.zeros(self.count, dtype=np.float64)
+        reason = np.zeros(self.count, dtype=np.int32)
+        _check_batch(lib.tacta_batch_cta(self._h, pb, _ptr(x, np.float64)[0], iters.ctypes.data,
+                                         rel.ctypes.data, reason.ctypes.data, ctypes.byref(o)))
+        del kb
+        return x, iters, rel, reason
+
+    def tune(self, b, **opts):
+        """Autotune the launch configuration on (self, b); returns (config, ms)."""
+        lib = load_library()
+        pb, db_, kb = _ptr(b, np.float64)
+        o = make_options(db_, **opts)
+        cfg = ctypes.c_int32()
+        ms = ctypes.c_double()
+        _check_batch(lib.tacta_batch_tune(self._h, pb, ctypes.byref(o), ctypes.byref(cfg), ctypes.byref(ms)))
+        del kb
+        return int(cfg.value), float(ms.value)
+
+    def set_config(self, config: int):
+        _check_batch(load_library().tacta_batch_set_config(self._h, int(config)))
+
+    @staticmethod
+    def configs():
+        """[(threads per block, blocks per SM)] of the launch configurations."""
+        lib = load_library()
+        out = []
+        for c in range(lib.tacta_batch_num_configs()):
+            t, p = ctypes.c_int32(), ctypes.c_int32()
+            _check_batch(lib.tacta_batch_config_shape(c, ctypes.byref(t), ctypes.byref(p)))
+            out.append((t.value, p.value))
+        return out
+
+    def split(self, v, which="x"):
+        """Per-system views of a packed vector."""
+        off = self.x_offsets if which == "x" else self.b_offsets
+        return [v[int(off[i]):int(off[i + 1])] for i in range(self.count)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().tacta_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ = ["cta_solve", "ta_solve", "ta_minnorm", "residual_static", "Plan", "CSR", "Batch", "load_library",
+           "make_options", "TactaError", "EXPORTS", "LIB_PATH", "BATCH_FP64", "BATCH_FP32", "BATCH_BF16"]

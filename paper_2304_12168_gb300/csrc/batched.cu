@@ -1,0 +1,816 @@
+// Batched dense CTA: many independent systems A_s x_s = b_s in one persistent launch.
+//
+// Each block takes the next unsolved system from a queue (largest first) and runs
+// CTA (Alg. 1.1 with H = A_s A_sᵀ, Eqs. CTAGEN7/CTAGEN7A, auxiliary equation
+// Eq. eqcoeff) on it to its own stop, then takes the next one. The chain
+// z_i = Aᵀ u_{i-1}, u_i = A z_i runs in the storage precision's arithmetic (FP64,
+// or FP32 for FP32 and BF16 copies of A) on a copy of A_s staged in shared memory
+// when it fits (read through L2 otherwise); the moments, the centering solve and
+// every stop test are FP64. With an FP32 chain the correction dx accumulates in
+// FP32 and is folded into the FP64 x at each refinement, where the residual
+// b - A x is recomputed in FP64 from the FP64 A_s: every R steps, once the inner
+// solve has reduced the residual by kRefineEta, and whenever the recursive
+// residual passes the tolerance (verify-on-pass). The chain is scaled by a power of
+// two s >= ||A_s||_2 (z_i by s^-(2i-1), u_i by s^-2i): the scaled auxiliary system
+// gives beta_j = s^(2j) alpha_j, and x += s^-1 sum beta_j z_j, r -= sum beta_j u_j
+// (exact in binary arithmetic).
+//
+// The paper solves one system at a time; batching is this library's extension.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "hankel.cuh"
+#include "internal.h"
+
+namespace tacta {
+namespace {
+
+// ------------------------------------------------------------------ storage types
+
+template <class TA> struct Elem;
+template <> struct Elem<double> { using TC = double; static constexpr int V = 2; };
+template <> struct Elem<float> { using TC = float; static constexpr int V = 4; };
+template <> struct Elem<__nv_bfloat16> { using TC = float; static constexpr int V = 8; };
+
+// V consecutive elements from a 16-byte aligned address, widened to the chain type
+__device__ __forceinline__ void load16(const double* p, double (&o)[2]) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x;
+    o[1] = v.y;
+}
+__device__ __forceinline__ void load16(const float* p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load16(const __nv_bfloat16* p, float (&o)[8]) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {   // bf16 -> fp32 is a 16-bit shift (exact)
+        o[2 * i] = __uint_as_float(w[i] << 16);
+        o[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+}
+
+__device__ __forceinline__ bool finite_d(double v) { return fabs(v) <= DBL_MAX; }
+
+template <class TA> __device__ __forceinline__ TA to_store(double v);
+template <> __device__ __forceinline__ double to_store<double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_store<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+
+struct SysDesc {
+    int32_t m, n, ld;      // rows, columns, padded row length of the low-precision copy
+    int32_t pad_;
+    int64_t a_lo;          // offset (elements) of A_s in the low-precision copy
+    int64_t a64;           // offset of A_s in the FP64 copy (row-major m x n)
+    int64_t b_off, x_off;  // offsets of b_s and x_s
+    double s, inv_s;       // chain scale (power of two) and its inverse
+};
+
+struct BatchParams {
+    double tol2, tol_n2, pivot_tol, eta2;
+    int32_t max_iter, R, t_max, cycle;
+    int32_t m_cap, n_cap;  // vector capacities (n_cap a multiple of 8)
+    int64_t a_cap;         // elements of A a block can stage in shared memory
+};
+
+struct BatchOut {
+    int32_t* iters;
+    int32_t* reason;
+    double* rel_res;
+};
+
+__device__ __forceinline__ int schedule_dev(int k, int t_max, int cycle) {
+    if (cycle == TACTA_CYCLE_FIXED || t_max == 1) return t_max;
+    if (cycle == TACTA_CYCLE_SAWTOOTH) return 1 + k % t_max;
+    const int period = 2 * t_max - 2;
+    const int j = k % period;
+    return j < t_max ? j + 1 : 2 * t_max - 1 - j;
+}
+
+// block-wide sums of two FP64 values; every thread gets the result
+template <int NT>
+__device__ __forceinline__ double2 block_sum2(double a, double b, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();                       // red is free (previous readers are done)
+    if (lane == 0) { red[2 * w] = a; red[2 * w + 1] = b; }
+    __syncthreads();
+    double2 r = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) { r.x += red[2 * i]; r.y += red[2 * i + 1]; }
+    return r;
+}
+
+// out = (Aᵀ u) * scale, out and the squares' sum in the chain type / FP64
+template <class TA, int NT>
+__device__ double prod_t(const TA* A, int m, int n, int ld, const typename Elem<TA>::TC* u,
+                         typename Elem<TA>::TC* out, typename Elem<TA>::TC* part, double scale) {
+    using TC = typename Elem<TA>::TC;
+    constexpr int V = Elem<TA>::V;
+    const int CG = (n + V - 1) / V;
+    const int RG = CG >= NT ? 1 : NT / CG;
+    const TC sc = (TC)scale;
+    double sq = 0.0;
+    for (int w = threadIdx.x; w < CG * RG; w += NT) {
+        const int cg = w % CG, rg = w / CG;
+        TC acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0;
+        for (int i = rg; i < m; i += RG) {
+            TC a[V];
+            load16(A + (int64_t)i * ld + cg * V, a);
+            const TC ui = u[i];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = fma(a[v], ui, acc[v]);
+        }
+        if (RG == 1) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const int c = cg * V + v;
+                if (c < n) {
+                    const TC z = acc[v] * sc;
+                    out[c] = z;
+                    sq = fma((double)z, (double)z, sq);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) part[rg * CG * V + cg * V + v] = acc[v];
+        }
+    }
+    if (RG > 1) {
+        __syncthreads();
+        for (int c = threadIdx.x; c < n; c += NT) {
+            TC acc = 0;
+            for (int rg = 0; rg < RG; ++rg) acc += part[rg * CG * V + c];
+            const TC z = acc * sc;
+            out[c] = z;
+            sq = fma((double)z, (double)z, sq);
+        }
+    }
+    return sq;
+}
+
+// out = (A z) * scale: LPR lanes per row (a power of two >= the row's vectors, <= 32)
+template <class TA, int NT>
+__device__ double prod_n(const TA* A, int m, int n, int ld, const typename Elem<TA>::TC* z,
+                         typename Elem<TA>::TC* out, double scale) {
+    using TC = typename Elem<TA>::TC;
+    constexpr int V = Elem<TA>::V;
+    const int CG = (n + V - 1) / V;
+    int lpr = 1;
+    while (lpr < CG && lpr < 32) lpr <<= 1;
+    const int rpw = 32 / lpr;                       // rows per warp pass
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane / lpr, sl = lane % lpr;
+    const TC sc = (TC)scale;
+    double sq = 0.0;
+    for (int base = warp * rpw; base < m; base += (NT / 32) * rpw) {
+        const int row = base + sub;
+        TC acc = 0;
+        if (row < m) {
+            for (int c = sl; c < CG; c += lpr) {
+                TC a[V];
+                load16(A + (int64_t)row * ld + c * V, a);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc = fma(a[v], z[c * V + v], acc);
+            }
+        }
+        for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (row < m && sl == 0) {
+            const TC y = acc * sc;
+            out[row] = y;
+            sq = fma((double)y, (double)y, sq);
+        }
+    }
+    return sq;
+}
+
+// r = b - A64 x in FP64 (A64 row-major m x n); returns ||r||² and rᵀb
+template <class TC, int NT>
+__device__ double2 residual64(const double* __restrict__ A64, int m, int n, const double* __restrict__ b,
+                              const double* __restrict__ x, TC* r) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double sq = 0.0, rb = 0.0;
+    for (int row = warp; row < m; row += NT / 32) {
+        double acc = 0.0;
+        for (int c = lane; c < n; c += 32) acc = fma(A64[(int64_t)row * n + c], x[c], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            const double v = b[row] - acc;
+            r[row] = (TC)v;
+            sq = fma(v, v, sq);
+            rb = fma(v, b[row], rb);
+        }
+    }
+    return make_double2(sq, rb);
+}
+
+struct Shared {           // block-wide scalars (static shared memory)
+    double red[2 * 16];
+    double phi[2 * kTMax + 2];
+    double beta[kTMax];
+    int32_t sys;
+    int32_t rank;
+    int32_t stop;
+};
+
+template <class TA, int NT>
+__global__ void __launch_bounds__(NT)
+batch_cta(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, int count,
+          const TA* __restrict__ alo, const double* __restrict__ a64, const double* __restrict__ bvec,
+          double* __restrict__ xvec, BatchOut out, int32_t* queue, BatchParams P) {
+    using TC = typename Elem<TA>::TC;
+    __shared__ Shared S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* As = reinterpret_cast<TA*>(smem_raw);
+    TC* vec = reinterpret_cast<TC*>(smem_raw + ((P.a_cap * (int64_t)sizeof(TA) + 15) & ~(int64_t)15));
+    TC* r = vec;                                     // m_cap
+    TC* u = r + P.m_cap;                             // t_max x m_cap
+    TC* z = u + (int64_t)P.t_max * P.m_cap;          // t_max x n_cap
+    TC* dx = z + (int64_t)P.t_max * P.n_cap;         // n_cap
+    TC* part = dx + P.n_cap;                         // NT * V
+    const int tid = threadIdx.x;
+
+    for (;;) {
+        if (tid == 0) S.sys = atomicAdd(queue, 1);
+        __syncthreads();
+        const int q = S.sys;
+        if (q >= count) break;
+        const SysDesc d = sys[order[q]];
+        const int m = d.m, n = d.n, ld = d.ld;
+        const double* b = bvec + d.b_off;
+        double* x = xvec + d.x_off;
+        const double* A64 = a64 + d.a64;
+        // stage A_s in shared memory when it fits (16-byte copies)
+        const TA* A = alo + d.a_lo;
+        const int64_t a_elems = (int64_t)m * ld;
+        if (a_elems <= P.a_cap) {
+            const int64_t nv = a_elems * (int64_t)sizeof(TA) / 16;
+            const uint4* src = reinterpret_cast<const uint4*>(A);
+            uint4* dst = reinterpret_cast<uint4*>(As);
+            for (int64_t i = tid; i < nv; i += NT) dst[i] = __ldg(src + i);
+            A = As;
+        }
+        // x = 0, dx = 0 (with the padding the products read), r = b
+        for (int c = tid; c < n; c += NT) x[c] = 0.0;
+        for (int c = tid; c < P.n_cap; c += NT) dx[c] = 0;
+        for (int i = 0; i < P.t_max; ++i)
+            for (int c = tid; c < P.n_cap; c += NT) z[(int64_t)i * P.n_cap + c] = 0;
+        double bb = 0.0;
+        for (int i = tid; i < m; i += NT) {
+            r[i] = (TC)b[i];
+            bb = fma(b[i], b[i], bb);
+        }
+        const double bn2 = block_sum2<NT>(bb, 0.0, S.red).x;   // also orders the writes above
+        double nrm_thr = 0.0;
+        if (P.tol_n2 > 0.0 && bn2 > 0.0) {
+            const double mt = prod_t<TA, NT>(A, m, n, ld, r, z, part, 1.0);
+            nrm_thr = P.tol_n2 * block_sum2<NT>(mt, 0.0, S.red).x;
+            for (int c = tid; c < n; c += NT) z[c] = 0;
+        }
+        double rn2 = bn2;
+        bool is_true = true, need_true = false;
+        int k = 0, reason = 0;
+        const double res_thr = P.tol2 * bn2;
+        double ref_thr = P.eta2 * bn2;
+        if (bn2 == 0.0) reason = TACTA_REASON_ZERO_RHS;
+        while (reason == 0) {
+            if (!finite_d(rn2)) { reason = TACTA_REASON_NONFINITE; break; }
+            if (rn2 <= res_thr) {
+                if (is_true) { reason = TACTA_REASON_RESIDUAL; break; }
+                need_true = true;
+            }
+            if (need_true) {   // refinement: fold dx into x, FP64 residual
+                for (int c = tid; c < n; c += NT) {
+                    x[c] += (double)dx[c];
+                    dx[c] = 0;
+                }
+                __syncthreads();
+                const double2 rr = residual64<TC, NT>(A64, m, n, b, x, r);
+                rn2 = block_sum2<NT>(rr.x, 0.0, S.red).x;
+                is_true = true;
+                need_true = false;
+                ref_thr = P.eta2 * rn2;
+                continue;
+            }
+            if (k >= P.max_iter) { reason = TACTA_REASON_MAXITER; break; }
+            const int t = schedule_dev(k, P.t_max, P.cycle);
+            // the chain u_0 = r, z_i = Aᵀ u_{i-1} / s, u_i = A z_i / s
+            const TC* uprev = r;
+            for (int i = 1; i <= t; ++i) {
+                TC* zi = z + (int64_t)(i - 1) * P.n_cap;
+                TC* ui = u + (int64_t)(i - 1) * P.m_cap;
+                const double p1 = prod_t<TA, NT>(A, m, n, ld, uprev, zi, part, d.inv_s);
+                __syncthreads();   // zi complete before the product with A reads it
+                const double p2 = prod_n<TA, NT>(A, m, n, ld, zi, ui, d.inv_s);
+                const double2 ph = block_sum2<NT>(p1, p2, S.red);   // also completes ui
+                if (tid == 0) {
+                    S.phi[2 * i - 1] = ph.x;
+                    S.phi[2 * i] = ph.y;
+                }
+                uprev = ui;
+            }
+            if (tid == 0) {
+                int st = 0;
+                for (int i = 1; i <= 2 * t; ++i)
+                    if (!finite_d(S.phi[i])) st = TACTA_REASON_NONFINITE;
+                // normal-equation test on the unscaled phi_1 = s² phi~_1
+                if (st == 0 && S.phi[1] * d.s * d.s <= nrm_thr) st = TACTA_REASON_NORMAL;
+                if (st == 0) {
+                    S.rank = hankel_solve_dev(S.phi, t, P.pivot_tol, S.beta);
+                    if (S.rank == 0) st = TACTA_REASON_BREAKDOWN;
+                }
+                S.stop = st;
+            }
+            __syncthreads();
+            if (S.stop) { reason = S.stop; break; }
+            // dx += s^-1 sum beta_j z_j ; r -= sum beta_j u_j ; ||r||²
+            TC bz[kTMax], bu[kTMax];
+            for (int j = 0; j < t; ++j) {
+                bu[j] = (TC)S.beta[j];
+                bz[j] = (TC)(S.beta[j] * d.inv_s);
+            }
+            for (int c = tid; c < n; c += NT) {
+                TC v = dx[c];
+                for (int j = 0; j < t; ++j) v = fma(bz[j], z[(int64_t)j * P.n_cap + c], v);
+                dx[c] = v;
+            }
+            double sq = 0.0;
+            for (int i = tid; i < m; i += NT) {
+                TC v = r[i];
+                for (int j = 0; j < t; ++j) v = fma(-bu[j], u[(int64_t)j * P.m_cap + i], v);
+                r[i] = v;
+                sq = fma((double)v, (double)v, sq);
+            }
+            rn2 = block_sum2<NT>(sq, 0.0, S.red).x;
+            ++k;
+            is_true = false;
+            if (P.R > 0 && k % P.R == 0) need_true = true;
+            else if (P.eta2 > 0.0 && rn2 <= ref_thr) need_true = true;
+        }
+        // exit: fold the correction and report the true residual
+        double rel = 0.0;
+        if (reason != TACTA_REASON_ZERO_RHS) {
+            for (int c = tid; c < n; c += NT) {
+                x[c] += (double)dx[c];
+                dx[c] = 0;
+            }
+            __syncthreads();
+            const double2 rr = residual64<TC, NT>(A64, m, n, b, x, r);
+            rel = sqrt(block_sum2<NT>(rr.x, 0.0, S.red).x / bn2);
+        }
+        if (tid == 0) {
+            out.iters[order[q]] = k;
+            out.reason[order[q]] = reason;
+            out.rel_res[order[q]] = rel;
+        }
+        __syncthreads();   // the next system may reuse every buffer
+    }
+}
+
+// ------------------------------------------------------------------ setup kernels
+
+// low-precision copy with padded rows; one block per system
+template <class TA>
+__global__ void pack_lo(const SysDesc* __restrict__ sys, const double* __restrict__ a64, TA* __restrict__ alo) {
+    const SysDesc d = sys[blockIdx.x];
+    const int64_t total = (int64_t)d.m * d.ld;
+    for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+        const int i = (int)(e / d.ld), c = (int)(e % d.ld);
+        const double v = c < d.n ? a64[d.a64 + (int64_t)i * d.n + c] : 0.0;
+        alo[d.a_lo + e] = to_store<TA>(v);
+    }
+}
+
+// chain scale: the smallest power of two >= sqrt(||A||_1 ||A||_inf) >= ||A||_2
+__global__ void chain_scale(SysDesc* sys, const double* __restrict__ a64) {
+    SysDesc& d = sys[blockIdx.x];
+    __shared__ double red[2][32];
+    double rmax = 0.0, cmax = 0.0;
+    for (int i = threadIdx.x; i < d.m; i += blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < d.n; ++c) s += fabs(a64[d.a64 + (int64_t)i * d.n + c]);
+        rmax = fmax(rmax, s);
+    }
+    for (int c = threadIdx.x; c < d.n; c += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < d.m; ++i) s += fabs(a64[d.a64 + (int64_t)i * d.n + c]);
+        cmax = fmax(cmax, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = rmax; red[1][threadIdx.x >> 5] = cmax; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { rmax = fmax(rmax, red[0][w]); cmax = fmax(cmax, red[1][w]); }
+        rmax = fmax(rmax, red[0][0]);
+        cmax = fmax(cmax, red[1][0]);
+        const double bound = sqrt(rmax * cmax);
+        int e = 0;
+        if (bound > 0.0 && bound <= DBL_MAX) { (void)frexp(bound, &e); }
+        d.s = ldexp(1.0, e);          // 2^e > bound (frexp: bound = f 2^e, f in [0.5, 1))
+        d.inv_s = ldexp(1.0, -e);
+    }
+}
+
+// ------------------------------------------------------------------ launch configurations
+
+struct Config {
+    int nt;            // threads per block
+    int per_sm;        // resident blocks per SM
+};
+constexpr Config kConfigs[] = {{128, 2}, {256, 1}, {256, 2}, {512, 1}};
+constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
+
+template <class TA>
+size_t vec_bytes(const BatchParams& P, int nt) {
+    using TC = typename Elem<TA>::TC;
+    const int64_t v = (int64_t)P.m_cap * (1 + P.t_max) + (int64_t)P.n_cap * (1 + P.t_max) + (int64_t)nt * Elem<TA>::V;
+    return (size_t)v * sizeof(TC);
+}
+
+// dynamic shared memory a block may ask for (the static Shared block and slack aside)
+constexpr int64_t kBatchSmemMax = 232448 - 2048;
+
+cudaError_t prepare_kernels() {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        auto set = [](const void* f) {
+            if (attr == cudaSuccess)
+                attr = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmemMax);
+        };
+        set((const void*)batch_cta<double, 128>); set((const void*)batch_cta<double, 256>);
+        set((const void*)batch_cta<double, 512>); set((const void*)batch_cta<float, 128>);
+        set((const void*)batch_cta<float, 256>); set((const void*)batch_cta<float, 512>);
+        set((const void*)batch_cta<__nv_bfloat16, 128>); set((const void*)batch_cta<__nv_bfloat16, 256>);
+        set((const void*)batch_cta<__nv_bfloat16, 512>);
+    });
+    return attr;
+}
+
+template <class TA, int NT>
+cudaError_t launch_one(cudaStream_t s, int grid, size_t smem, const SysDesc* sys, const int32_t* order, int count,
+                       const void* alo, const double* a64, const double* b, double* x, BatchOut o, int32_t* queue,
+                       const BatchParams& P) {
+    batch_cta<TA, NT><<<grid, NT, smem, s>>>(sys, order, count, reinterpret_cast<const TA*>(alo), a64, b, x, o,
+                                             queue, P);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace tacta
+
+// ================================================================== C ABI
+
+using namespace tacta;
+
+struct tacta_batch_s {
+    int device = 0, sms = 0;
+    int32_t count = 0;
+    int32_t storage = TACTA_BATCH_FP32;
+    int32_t m_max = 0, n_max = 0;
+    int64_t a64_len = 0, alo_len = 0, b_len = 0, x_len = 0;
+    SysDesc* sys = nullptr;
+    int32_t* order = nullptr;
+    double* a64 = nullptr;
+    void* alo = nullptr;
+    double* b = nullptr;
+    double* x = nullptr;
+    int32_t* iters = nullptr;
+    int32_t* reason = nullptr;
+    double* rel = nullptr;
+    int32_t* queue = nullptr;
+    int config = -1;               // index into kConfigs (-1: default)
+    cudaGraphExec_t graph = nullptr;
+    int graph_key = -1;
+    BatchParams graph_params{};
+};
+
+namespace {
+
+thread_local std::string g_batch_err;
+
+void free_batch(tacta_batch_s* B) {
+    if (!B) return;
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    cudaFree(B->sys); cudaFree(B->order); cudaFree(B->a64); cudaFree(B->alo); cudaFree(B->b); cudaFree(B->x);
+    cudaFree(B->iters); cudaFree(B->reason); cudaFree(B->rel); cudaFree(B->queue);
+    delete B;
+}
+
+size_t elem_size(int storage) {
+    return storage == TACTA_BATCH_FP64 ? 8 : storage == TACTA_BATCH_FP32 ? 4 : 2;
+}
+
+BatchParams make_params(const tacta_batch_s* B, const tacta_options& o, int nt, int per_sm, size_t* smem_out) {
+    BatchParams P{};
+    P.tol2 = o.tol * o.tol;
+    P.tol_n2 = o.tol_normal > 0.0 ? o.tol_normal * o.tol_normal : 0.0;
+    P.pivot_tol = o.pivot_tol > 0.0 ? o.pivot_tol : (B->storage == TACTA_BATCH_FP64 ? 1e-12 : 1e-6);
+    P.eta2 = B->storage == TACTA_BATCH_FP64 ? 0.0 : kRefineEta2;
+    P.max_iter = o.max_iter;
+    P.R = o.recompute_every;
+    P.t_max = o.t_max;
+    P.cycle = o.cycle;
+    P.m_cap = B->m_max;
+    P.n_cap = (B->n_max + 7) & ~7;
+    size_t vb = 0;
+    switch (B->storage) {
+    case TACTA_BATCH_FP64: vb = vec_bytes<double>(P, nt); break;
+    case TACTA_BATCH_FP32: vb = vec_bytes<float>(P, nt); break;
+    default: vb = vec_bytes<__nv_bfloat16>(P, nt); break;
+    }
+    // shared memory per block: what per_sm blocks can share of the SM's 228 KB
+    // (1 KB per block reserved, the static Shared block), the vectors first
+    const int64_t per_block = std::min<int64_t>(kBatchSmemMax, (228 * 1024) / per_sm - 1024 - 2048);
+    const int64_t a_bytes = std::max<int64_t>(0, per_block - (int64_t)vb - 16);
+    P.a_cap = (a_bytes / 16) * 16 / (int64_t)elem_size(B->storage);
+    *smem_out = (size_t)(((P.a_cap * (int64_t)elem_size(B->storage) + 15) & ~15) + (int64_t)vb);
+    return P;
+}
+
+cudaError_t launch_batch(tacta_batch_s* B, cudaStream_t s, const tacta_options& o, int cfg) {
+    const Config C = kConfigs[cfg];
+    size_t smem = 0;
+    BatchParams P = make_params(B, o, C.nt, C.per_sm, &smem);
+    if ((int64_t)smem > kBatchSmemMax) return cudaErrorInvalidConfiguration;
+    const int grid = std::max(1, std::min(B->count, B->sms * C.per_sm));
+    BatchOut out{B->iters, B->reason, B->rel};
+    cudaError_t e = cudaMemsetAsync(B->queue, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+#define TACTA_BATCH_LAUNCH(TA)                                                                                   \
+    switch (C.nt) {                                                                                              \
+    case 128: return launch_one<TA, 128>(s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x,  \
+                                         out, B->queue, P);                                                      \
+    case 256: return launch_one<TA, 256>(s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x,  \
+                                         out, B->queue, P);                                                      \
+    default: return launch_one<TA, 512>(s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x,   \
+                                        out, B->queue, P);                                                       \
+    }
+    switch (B->storage) {
+    case TACTA_BATCH_FP64: TACTA_BATCH_LAUNCH(double)
+    case TACTA_BATCH_FP32: TACTA_BATCH_LAUNCH(float)
+    default: TACTA_BATCH_LAUNCH(__nv_bfloat16)
+    }
+#undef TACTA_BATCH_LAUNCH
+}
+
+bool batch_opts_ok(const tacta_options& o) {
+    if (!(std::isfinite(o.tol) && o.tol > 0.0)) { g_batch_err = "tol must be finite and > 0"; return false; }
+    if (!std::isfinite(o.tol_normal)) { g_batch_err = "tol_normal must be finite"; return false; }
+    if (o.t_max < 1 || o.t_max > kTMax) { g_batch_err = "t_max must be in 1..8"; return false; }
+    if (o.max_iter < 0) { g_batch_err = "max_iter must be >= 0"; return false; }
+    if (o.recompute_every < 0) { g_batch_err = "recompute_every must be >= 0"; return false; }
+    if (o.cycle < 0 || o.cycle > 2) { g_batch_err = "unknown cycle"; return false; }
+    return true;
+}
+
+tacta_options resolve_opts(const tacta_options* opt) {
+    tacta_options o;
+    tacta_default_options(&o);
+    if (opt) o = *opt;
+    if (o.tol_normal < 0.0) o.tol_normal = 0.0;
+    return o;
+}
+
+}  // namespace
+
+#define BTRY(expr)                                                                     \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            g_batch_err = std::string(#expr) + ": " + cudaGetErrorString(e_);          \
+            return e_ == cudaErrorMemoryAllocation ? TACTA_ERR_OOM : TACTA_ERR_CUDA;   \
+        }                                                                              \
+    } while (0)
+
+extern "C" const char* tacta_batch_last_error(void) { return g_batch_err.c_str(); }
+
+extern "C" tacta_status tacta_batch_create(int32_t count, const int32_t* m, const int32_t* n, const double* vals,
+                                           int32_t on_device, int32_t storage, const tacta_options* opt,
+                                           tacta_batch* out) {
+    g_batch_err.clear();
+    if (!out) { g_batch_err = "out is NULL"; return TACTA_ERR_INVALID; }
+    *out = nullptr;
+    if (count < 0) { g_batch_err = "count must be >= 0"; return TACTA_ERR_INVALID; }
+    if (count > 0 && (!m || !n || !vals)) { g_batch_err = "m, n or vals is NULL"; return TACTA_ERR_INVALID; }
+    if (storage != TACTA_BATCH_FP64 && storage != TACTA_BATCH_FP32 && storage != TACTA_BATCH_BF16) {
+        g_batch_err = "unknown storage";
+        return TACTA_ERR_INVALID;
+    }
+    std::vector<SysDesc> d((size_t)count);
+    int64_t a64 = 0, alo = 0, bo = 0, xo = 0;
+    int32_t mmax = 1, nmax = 1;
+    for (int32_t s = 0; s < count; ++s) {
+        if (m[s] < 1 || n[s] < 1 || m[s] > kBatchMaxDim || n[s] > kBatchMaxDim) {
+            g_batch_err = "system " + std::to_string(s) + ": m and n must be in 1.." + std::to_string(kBatchMaxDim);
+            return TACTA_ERR_INVALID;
+        }
+        SysDesc& q = d[(size_t)s];
+        std::memset(&q, 0, sizeof(q));
+        q.m = m[s];
+        q.n = n[s];
+        q.ld = (n[s] + 7) & ~7;
+        q.a64 = a64;
+        q.a_lo = alo;
+        q.b_off = bo;
+        q.x_off = xo;
+        a64 += (int64_t)m[s] * n[s];
+        alo += (int64_t)m[s] * q.ld;
+        bo += m[s];
+        xo += n[s];
+        mmax = std::max(mmax, m[s]);
+        nmax = std::max(nmax, n[s]);
+    }
+    tacta_batch_s* B = new tacta_batch_s();
+    B->count = count;
+    B->storage = storage;
+    B->m_max = mmax;
+    B->n_max = nmax;
+    B->a64_len = a64;
+    B->alo_len = alo;
+    B->b_len = bo;
+    B->x_len = xo;
+    cudaStream_t s = opt && opt->stream ? (cudaStream_t)opt->stream : (cudaStream_t)0;
+    auto fail = [&](cudaError_t e, const char* what) {
+        g_batch_err = std::string(what) + ": " + cudaGetErrorString(e);
+        free_batch(B);
+        return e == cudaErrorMemoryAllocation ? TACTA_ERR_OOM : TACTA_ERR_CUDA;
+    };
+#define BCHK(expr) do { cudaError_t e_ = (expr); if (e_ != cudaSuccess) return fail(e_, #expr); } while (0)
+    BCHK(cudaGetDevice(&B->device));
+    BCHK(cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, B->device));
+    BCHK(prepare_kernels());
+    const size_t es = elem_size(storage);
+    BCHK(cudaMalloc(&B->sys, sizeof(SysDesc) * std::max<int32_t>(count, 1)));
+    BCHK(cudaMalloc(&B->order, sizeof(int32_t) * std::max<int32_t>(count, 1)));
+    BCHK(cudaMalloc(&B->a64, sizeof(double) * std::max<int64_t>(a64, 1)));
+    BCHK(cudaMalloc(&B->alo, es * std::max<int64_t>(alo, 8) + 16));
+    BCHK(cudaMalloc(&B->b, sizeof(double) * std::max<int64_t>(bo, 1)));
+    BCHK(cudaMalloc(&B->x, sizeof(double) * std::max<int64_t>(xo, 1)));
+    BCHK(cudaMalloc(&B->iters, sizeof(int32_t) * std::max<int32_t>(count, 1)));
+    BCHK(cudaMalloc(&B->reason, sizeof(int32_t) * std::max<int32_t>(count, 1)));
+    BCHK(cudaMalloc(&B->rel, sizeof(double) * std::max<int32_t>(count, 1)));
+    BCHK(cudaMalloc(&B->queue, sizeof(int32_t)));
+    if (count > 0) {
+        // largest systems first: the queue's tail is then made of short jobs
+        std::vector<int32_t> ord((size_t)count);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b2) {
+            return (int64_t)d[a].m * d[a].n > (int64_t)d[b2].m * d[b2].n;
+        });
+        BCHK(cudaMemcpyAsync(B->sys, d.data(), sizeof(SysDesc) * count, cudaMemcpyHostToDevice, s));
+        BCHK(cudaMemcpyAsync(B->order, ord.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
+        BCHK(cudaMemcpyAsync(B->a64, vals, sizeof(double) * a64, on_device ? cudaMemcpyDeviceToDevice
+                                                                           : cudaMemcpyHostToDevice, s));
+        chain_scale<<<count, 256, 0, s>>>(B->sys, B->a64);
+        BCHK(cudaGetLastError());
+        switch (storage) {
+        case TACTA_BATCH_FP64: pack_lo<double><<<count, 256, 0, s>>>(B->sys, B->a64, (double*)B->alo); break;
+        case TACTA_BATCH_FP32: pack_lo<float><<<count, 256, 0, s>>>(B->sys, B->a64, (float*)B->alo); break;
+        default: pack_lo<__nv_bfloat16><<<count, 256, 0, s>>>(B->sys, B->a64, (__nv_bfloat16*)B->alo); break;
+        }
+        BCHK(cudaGetLastError());
+        BCHK(cudaStreamSynchronize(s));
+    }
+#undef BCHK
+    *out = B;
+    return TACTA_OK;
+}
+
+extern "C" void tacta_batch_destroy(tacta_batch B) {
+    if (!B) return;
+    cudaSetDevice(B->device);
+    free_batch(B);
+}
+
+extern "C" tacta_status tacta_batch_set_config(tacta_batch B, int32_t config) {
+    g_batch_err.clear();
+    if (!B) { g_batch_err = "NULL batch"; return TACTA_ERR_INVALID; }
+    if (config < -1 || config >= kNumConfigs) { g_batch_err = "unknown config"; return TACTA_ERR_INVALID; }
+    B->config = config;
+    return TACTA_OK;
+}
+
+extern "C" int32_t tacta_batch_num_configs(void) { return kNumConfigs; }
+
+extern "C" tacta_status tacta_batch_config_shape(int32_t config, int32_t* threads, int32_t* blocks_per_sm) {
+    if (config < 0 || config >= kNumConfigs || !threads || !blocks_per_sm) return TACTA_ERR_INVALID;
+    *threads = kConfigs[config].nt;
+    *blocks_per_sm = kConfigs[config].per_sm;
+    return TACTA_OK;
+}
+
+extern "C" tacta_status tacta_batch_cta(tacta_batch B, const double* b, double* x, int32_t* iters,
+                                        double* rel_res, int32_t* reason, const tacta_options* opt) {
+    g_batch_err.clear();
+    if (!B) { g_batch_err = "NULL batch"; return TACTA_ERR_INVALID; }
+    if (B->count > 0 && (!b || !x)) { g_batch_err = "b or x is NULL"; return TACTA_ERR_INVALID; }
+    const tacta_options o = resolve_opts(opt);
+    if (!batch_opts_ok(o)) return TACTA_ERR_INVALID;
+    BTRY(cudaSetDevice(B->device));
+    if (B->count == 0) return TACTA_OK;
+    cudaStream_t s = (cudaStream_t)o.stream;
+    const int cfg = B->config >= 0 ? B->config : 2;
+    {
+        size_t smem = 0;
+        make_params(B, o, kConfigs[cfg].nt, kConfigs[cfg].per_sm, &smem);
+        if ((int64_t)smem > kBatchSmemMax) {
+            g_batch_err = "the largest system's vectors exceed shared memory: lower t_max or solve it with a plan";
+            return TACTA_ERR_INVALID;
+        }
+    }
+    BTRY(cudaMemcpyAsync(B->b, b, sizeof(double) * B->b_len, cudaMemcpyDefault, s));
+    if (o.use_graph) {
+        // the solve is a queue reset and one persistent launch: replay it as a graph
+        size_t smem = 0;
+        const BatchParams P = make_params(B, o, kConfigs[cfg].nt, kConfigs[cfg].per_sm, &smem);
+        if (!B->graph || B->graph_key != cfg || std::memcmp(&P, &B->graph_params, sizeof(P)) != 0) {
+            if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
+            cudaStream_t cs;
+            BTRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t el = launch_batch(B, cs, o, cfg);
+                e = cudaStreamEndCapture(cs, &g);
+                if (el != cudaSuccess) e = el;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&B->graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            BTRY(e);
+            B->graph_key = cfg;
+            B->graph_params = P;
+        }
+        BTRY(cudaGraphLaunch(B->graph, s));
+    } else {
+        BTRY(launch_batch(B, s, o, cfg));
+    }
+    BTRY(cudaMemcpyAsync(x, B->x, sizeof(double) * B->x_len, cudaMemcpyDefault, s));
+    if (iters) BTRY(cudaMemcpyAsync(iters, B->iters, sizeof(int32_t) * B->count, cudaMemcpyDefault, s));
+    if (rel_res) BTRY(cudaMemcpyAsync(rel_res, B->rel, sizeof(double) * B->count, cudaMemcpyDefault, s));
+    if (reason) BTRY(cudaMemcpyAsync(reason, B->reason, sizeof(int32_t) * B->count, cudaMemcpyDefault, s));
+    BTRY(cudaStreamSynchronize(s));
+    return TACTA_OK;
+}
+
+// Autotuner: times every launch configuration on the batch (each solve capped at
+// max_iter of the given options, graphs off), keeps the fastest, and returns it.
+extern "C" tacta_status tacta_batch_tune(tacta_batch B, const double* b, const tacta_options* opt,
+                                         int32_t* best_config, double* best_ms) {
+    g_batch_err.clear();
+    if (!B || !b) { g_batch_err = "NULL argument"; return TACTA_ERR_INVALID; }
+    tacta_options o = resolve_opts(opt);
+    if (!batch_opts_ok(o)) return TACTA_ERR_INVALID;
+    BTRY(cudaSetDevice(B->device));
+    if (B->count == 0) { if (best_config) *best_config = 2; return TACTA_OK; }
+    cudaStream_t s = (cudaStream_t)o.stream;
+    BTRY(cudaMemcpyAsync(B->b, b, sizeof(double) * B->b_len, cudaMemcpyDefault, s));
+    cudaEvent_t e0, e1;
+    BTRY(cudaEventCreate(&e0));
+    BTRY(cudaEventCreate(&e1));
+    int best = -1;
+    float best_t = 0.0f;
+    for (int c = 0; c < kNumConfigs; ++c) {
+        size_t smem = 0;
+        make_params(B, o, kConfigs[c].nt, kConfigs[c].per_sm, &smem);
+        if ((int64_t)smem > kBatchSmemMax) continue;
+        float tc = 0.0f;
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; ++rep) {      // the first run warms caches and loads the module
+            ok = cudaEventRecord(e0, s) == cudaSuccess && launch_batch(B, s, o, c) == cudaSuccess &&
+                 cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                 cudaEventElapsedTime(&tc, e0, e1) == cudaSuccess;
+        }
+        if (ok && (best < 0 || tc < best_t)) { best = c; best_t = tc; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    BTRY(cudaGetLastError());
+    if (best < 0) { g_batch_err = "no launch configuration fits this batch"; return TACTA_ERR_CUDA; }
+    B->config = best;
+    if (best_config) *best_config = best;
+    if (best_ms) *best_ms = best_t;
+    return TACTA_OK;
+}

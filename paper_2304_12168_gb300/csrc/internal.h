@@ -137,6 +137,8 @@ constexpr int kPadLcol = 8;
 // the FP32 inner iteration has reduced the residual by kRefineEta over the last
 // refinement; the FP32 chain cannot resolve much more than that.
 constexpr double kRefineEta2 = 1e-6;
+// batched dense systems: rows and columns of each system at most this
+constexpr int32_t kBatchMaxDim = 4096;
 // every plan vector that can be a product's input carries this many doubles of
 // padding, so 16-byte-rounded x-window copies stay inside the allocation
 constexpr int kPadVec = 2;

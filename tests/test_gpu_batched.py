@@ -1,0 +1,162 @@
+"""Batched dense CTA (one persistent launch over many systems) against the oracle and
+the mathematics (needs a GB300).
+
+FP64 storage follows the FP64 iteration, so fixed-length trajectories must match the
+oracle's per system. FP32 and BF16 storage are checked through what holds at any
+precision: the FP64 residual recomputed on the host reaches the tolerance, and the
+solution is the minimum-norm one (numpy pseudo-inverse) up to the storage's roundoff
+times the system's condition number.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tacta():
+    import torch
+    import paper_2304_12168_gb300 as t
+    t.load_library()
+    torch.cuda.set_device(0)
+    return t
+
+
+def small_batch(seed, count, m_range=(20, 120), aspect=None):
+    """Seeded systems; aspect=(lo, hi) restricts n/m away from 1 (well conditioned)."""
+    rng = np.random.default_rng(seed)
+    mats, bs, lr = [], [], []
+    for s in range(count):
+        m = int(rng.integers(m_range[0], m_range[1] + 1))
+        if aspect is None:
+            n = int(rng.integers((m + 1) // 2, 2 * m + 1))
+        else:
+            f = rng.uniform(*aspect) if rng.random() < 0.5 else 1.0 / rng.uniform(*aspect)
+            n = max(1, int(round(m * f)))
+        low = s % 5 == 3
+        if low:
+            r = max(1, m // 2)
+            A = rng.standard_normal((m, r)) @ rng.standard_normal((r, n)) / np.sqrt(r)
+        else:
+            A = rng.standard_normal((m, n))
+        mats.append(A)
+        bs.append(A @ rng.standard_normal(n))
+        lr.append(low)
+    return mats, bs, np.array(lr)
+
+
+def problem(A, b):
+    return gen.Problem(name="d", m=A.shape[0], n=A.shape[1], fmt="dense",
+                       dense=np.ascontiguousarray(A), b=b)
+
+
+def run(tacta, mats, bs, storage, **opts):
+    B = tacta.Batch(mats, storage=storage)
+    x, iters, rel, reason = B.cta(np.concatenate(bs), **opts)
+    xs = B.split(x)
+    B.close()
+    return xs, iters, rel, reason
+
+
+def test_fp64_fixed_trajectories_match_oracle(tacta):
+    """Four steps (t = 1..4) per system, FP64 storage: x, iteration and product counts of
+    every system against the oracle's run on that system alone."""
+    mats, bs, _ = small_batch(1, 40)
+    opts = dict(tol=1e-30, tol_normal=0.0, max_iter=4)
+    xs, iters, rel, reason = run(tacta, mats, bs, tacta.BATCH_FP64, **opts)
+    for s, (A, b) in enumerate(zip(mats, bs)):
+        ref = oracle.cta_solve(oracle.make_operator(problem(A, b)), b, **opts)
+        assert iters[s] == ref.iters, s
+        assert np.linalg.norm(xs[s] - ref.x) <= 1e-9 * np.linalg.norm(ref.x), s
+        assert rel[s] == pytest.approx(ref.rel_res, rel=1e-9), s
+        assert tacta.REASON[int(reason[s])] == "MAXITER"
+
+
+@pytest.mark.parametrize("storage,tol,xtol", [("BATCH_FP64", 1e-10, 1e-8), ("BATCH_FP32", 1e-8, 1e-6),
+                                              ("BATCH_BF16", 1e-8, 3e-2)])
+def test_to_tolerance_min_norm(tacta, storage, tol, xtol):
+    """Well-conditioned systems (n/m in [1.4, 2] or its inverse; every fifth of rank m/2):
+    the host-recomputed FP64 residual meets tol, the reported one equals it, and x is the
+    minimum-norm solution within cond(A) times xtol: about 100 tol for FP64, and for the
+    low-precision copies 10 times their unit roundoff (2^-24, 2^-9) plus the tolerance."""
+    mats, bs, lr = small_batch(2, 48, aspect=(1.4, 2.0))
+    xs, iters, rel, reason = run(tacta, mats, bs, getattr(tacta, storage), tol=tol, tol_normal=0.0,
+                                 max_iter=20000)
+    for s, (A, b) in enumerate(zip(mats, bs)):
+        assert tacta.REASON[int(reason[s])] == "RESIDUAL", (s, reason[s], rel[s])
+        r = np.linalg.norm(b - A @ xs[s]) / np.linalg.norm(b)
+        assert r <= tol * (1 + 1e-6), (s, r)
+        assert rel[s] == pytest.approx(r, rel=1e-6, abs=1e-14)
+        sv = np.linalg.svd(A, compute_uv=False)
+        sv = sv[sv > 1e-10 * sv[0]]
+        kappa = sv[0] / sv[-1]
+        xmn = np.linalg.pinv(A, rcond=1e-10) @ b
+        err = np.linalg.norm(xs[s] - xmn) / np.linalg.norm(xmn)
+        assert err <= xtol * kappa, (s, kappa, err)
+
+
+def test_edge_cases(tacta):
+    """1 x 1, one row, one column, a zero right-hand side, and max_iter = 0."""
+    rng = np.random.default_rng(3)
+    mats = [np.array([[2.0]]), rng.standard_normal((1, 7)), rng.standard_normal((9, 1)),
+            rng.standard_normal((30, 40))]
+    bs = [np.array([4.0]), rng.standard_normal(1), mats[2] @ np.array([1.5]), np.zeros(30)]
+    xs, iters, rel, reason = run(tacta, mats, bs, tacta.BATCH_FP64, tol=1e-12, tol_normal=0.0, max_iter=1000)
+    assert xs[0][0] == pytest.approx(2.0, rel=1e-14)
+    xmn = np.linalg.pinv(mats[1]) @ bs[1]
+    np.testing.assert_allclose(xs[1], xmn, rtol=1e-10, atol=1e-12)
+    assert xs[2][0] == pytest.approx(1.5, rel=1e-10)
+    assert tacta.REASON[int(reason[3])] == "ZERO_RHS" and np.all(xs[3] == 0.0) and iters[3] == 0
+    xs, iters, rel, reason = run(tacta, mats[:3], bs[:3], tacta.BATCH_FP32, tol=1e-8, tol_normal=0.0, max_iter=0)
+    assert all(tacta.REASON[int(r)] == "MAXITER" for r in reason)
+    assert np.all(iters == 0) and np.allclose(rel, 1.0) and all(np.all(x == 0.0) for x in xs)
+
+
+def test_empty_batch(tacta):
+    B = tacta.Batch([], storage=tacta.BATCH_FP32)
+    x, iters, rel, reason = B.cta(np.zeros(0))
+    assert x.size == 0 and iters.size == 0
+    B.close()
+
+
+def test_graph_replay_and_configs_agree(tacta):
+    """Graph replay and direct launch give identical results; every launch configuration
+    (different block sizes, hence reduction orders) meets the tolerance; the autotuner
+    picks one of them."""
+    mats, bs, _ = small_batch(4, 30, m_range=(32, 200), aspect=(1.4, 2.0))
+    b = np.concatenate(bs)
+    B = tacta.Batch(mats, storage=tacta.BATCH_FP32)
+    opts = dict(tol=1e-8, tol_normal=0.0, max_iter=5000)
+    x1, it1, r1, _ = B.cta(b, use_graph=1, **opts)
+    x2, it2, r2, _ = B.cta(b, use_graph=1, **opts)
+    x3, it3, r3, _ = B.cta(b, use_graph=0, **opts)
+    assert np.array_equal(x1, x2) and np.array_equal(x1, x3) and np.array_equal(it1, it3)
+    for c in range(len(tacta.Batch.configs())):
+        B.set_config(c)
+        _, _, rc, reason = B.cta(b, **opts)
+        assert all(tacta.REASON[int(r)] == "RESIDUAL" for r in reason) and np.all(rc <= 1e-8 * (1 + 1e-6))
+    best, ms = B.tune(b, **opts)
+    assert 0 <= best < len(tacta.Batch.configs()) and ms > 0
+    B.close()
+
+
+def test_full_batch_4096_fp32(tacta):
+    """The full workload: 4096 systems (m in [32, 512], n in [m/2, 2m], 10% rank m/2),
+    FP32 storage, tol 1e-8, at most 20000 steps each. Every system that reports RESIDUAL
+    has a host-recomputed FP64 residual within tol; every system with n/m outside
+    [0.8, 1.25] or of low rank converges."""
+    B0 = gen.dense_batch(4096, seed=7)
+    x, iters, rel, reason = run(tacta, B0.mats, B0.bs, tacta.BATCH_FP32, tol=1e-8, tol_normal=0.0,
+                                max_iter=20000)
+    names = [tacta.REASON[int(r)] for r in reason]
+    for s, (A, b) in enumerate(zip(B0.mats, B0.bs)):
+        m, n = A.shape
+        if names[s] == "RESIDUAL":
+            r = np.linalg.norm(b - A @ x[s]) / np.linalg.norm(b)
+            assert r <= 1e-8 * (1 + 1e-6), (s, r)
+        elif B0.low_rank[s] or n / m >= 1.25 or n / m <= 0.8:
+            raise AssertionError((s, m, n, names[s], rel[s]))
+        assert names[s] in ("RESIDUAL", "MAXITER"), (s, names[s])
