@@ -386,7 +386,7 @@ def main():
     peak, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic_record(),
-                "kernel": "spmv_tiled_x (TMA row tiles + staged x window; A and Aᵀ products of the F_t chain)",
+                "kernel": "spmv_tiled_rw<3, EPI_NORM> (run-staged TMA row tiles, warp-specialised; A and Aᵀ products of the F_t chain)",
                 "launches_timed": prof["spmv_count"], "avg_launch_us": spmv_us,
                 "bytes_per_launch": spmv_bytes, "peak_kind": peak_kind,
                 "fp64_fma_per_launch": (p.nnz + p.m),

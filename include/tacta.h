@@ -294,6 +294,16 @@ void tacta_batch_destroy(tacta_batch batch);
 /* message of the last failed tacta_batch_* call on the calling thread */
 const char* tacta_batch_last_error(void);
 
+/* tacta_aux_solve -- CTA's auxiliary equation of order t (Eq. eqcoeff),
+     [phi_{i+j}]_{i,j=1..t} alpha = [phi_i]_{i=1..t},
+   solved on the host by the code the kernels run on the device: Jacobi scaling by
+   phi_{2i}^{-1/2}, square-root-free Cholesky in natural order truncated at the first
+   pivot <= pivot_tol (the minimum-norm reading of a singular system: the leading block
+   is solved, the trailing alphas are 0). phi: 2t + 1 doubles (phi[0] unused);
+   alpha: t doubles. Returns the order of the block solved (0..t; 0 is a breakdown), or
+   -1 when t is outside 1..8 or a pointer is NULL. Touches no GPU. */
+int32_t tacta_aux_solve(const double* phi, int32_t t, double pivot_tol, double* alpha);
+
 /* Description of the last error on the calling thread ("" if none). */
 const char* tacta_last_error(void);
 

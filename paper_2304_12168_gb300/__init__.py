@@ -69,7 +69,7 @@ EXPORTS = ["tacta_default_options", "cta_solve", "ta_solve", "ta_minnorm", "tact
            "tacta_residual_static", "tacta_last_error", "tacta_version",
            "tacta_batch_create", "tacta_batch_cta", "tacta_batch_destroy", "tacta_batch_tune",
            "tacta_batch_set_config", "tacta_batch_num_configs", "tacta_batch_config_shape",
-           "tacta_batch_last_error"]
+           "tacta_batch_last_error", "tacta_aux_solve"]
 
 _lib_handle = None
 
@@ -128,6 +128,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tacta_batch_config_shape.restype = ctypes.c_int32
     lib.tacta_batch_last_error.argtypes = []
     lib.tacta_batch_last_error.restype = ctypes.c_char_p
+    lib.tacta_aux_solve.argtypes = [dp, ctypes.c_int32, ctypes.c_double, dp]
+    lib.tacta_aux_solve.restype = ctypes.c_int32
     _lib_handle = lib
     return lib
 
@@ -373,6 +375,18 @@ class Plan:
 BATCH_FP64, BATCH_FP32, BATCH_BF16 = 0, 1, 2
 
 
+def aux_solve(phi, t, pivot_tol=1e-12):
+    """tacta_aux_solve: alpha (t values) and the order of the block solved; phi[1..2t] used."""
+    ph = np.ascontiguousarray(phi, dtype=np.float64)
+    if ph.size < 2 * t + 1:
+        raise ValueError("phi needs 2t + 1 entries")
+    al = np.zeros(max(int(t), 1), dtype=np.float64)
+    rank = load_library().tacta_aux_solve(ph.ctypes.data, int(t), float(pivot_tol), al.ctypes.data)
+    if rank < 0:
+        raise ValueError("t must be in 1..8")
+    return al[: int(t)], int(rank)
+
+
 def _check_batch(st: int):
     if st < 0:
         msg = load_library().tacta_batch_last_error().decode()
@@ -465,5 +479,6 @@ class Batch:
             pass
 
 
-__all__ = ["cta_solve", "ta_solve", "ta_minnorm", "residual_static", "Plan", "CSR", "Batch", "load_library",
+__all__ = ["cta_solve", "ta_solve", "ta_minnorm", "residual_static", "aux_solve", "Plan", "CSR", "Batch",
+           "load_library",
            "make_options", "TactaError", "EXPORTS", "LIB_PATH", "BATCH_FP64", "BATCH_FP32", "BATCH_BF16"]

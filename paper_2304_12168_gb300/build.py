@@ -20,6 +20,7 @@ LIB = os.path.join(HERE, "libtacta.so")
 SOURCES = ["kernels.cu", "transpose.cu", "tacta.cu", "static_scratch.cu", "batched.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+                "-Xcompiler", "-ffp-contract=off",
                 "-I" + os.path.join(ROOT, "include")]
 
 

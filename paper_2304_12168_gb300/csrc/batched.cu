@@ -130,7 +130,25 @@ __device__ double prod_t(const TA* A, int m, int n, int ld, const typename Elem<
         TC acc[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = 0;
-        for (int i = rg; i < m; i += RG) {
+        // four rows' loads in flight per thread (A is read through L2 when it is not staged)
+        int i = rg;
+        for (; i + 3 * RG < m; i += 4 * RG) {
+            TC a0[V], a1[V], a2[V], a3[V];
+            const TA* p = A + (int64_t)i * ld + cg * V;
+            load16(p, a0);
+            load16(p + (int64_t)RG * ld, a1);
+            load16(p + (int64_t)2 * RG * ld, a2);
+            load16(p + (int64_t)3 * RG * ld, a3);
+            const TC u0 = u[i], u1 = u[i + RG], u2 = u[i + 2 * RG], u3 = u[i + 3 * RG];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                acc[v] = fma(a0[v], u0, acc[v]);
+                acc[v] = fma(a1[v], u1, acc[v]);
+                acc[v] = fma(a2[v], u2, acc[v]);
+                acc[v] = fma(a3[v], u3, acc[v]);
+            }
+        }
+        for (; i < m; i += RG) {
             TC a[V];
             load16(A + (int64_t)i * ld + cg * V, a);
             const TC ui = u[i];
@@ -183,9 +201,26 @@ __device__ double prod_n(const TA* A, int m, int n, int ld, const typename Elem<
         const int row = base + sub;
         TC acc = 0;
         if (row < m) {
-            for (int c = sl; c < CG; c += lpr) {
+            const TA* p = A + (int64_t)row * ld;
+            int c = sl;
+            for (; c + 3 * lpr < CG; c += 4 * lpr) {   // four loads in flight per lane
+                TC a0[V], a1[V], a2[V], a3[V];
+                load16(p + c * V, a0);
+                load16(p + (c + lpr) * V, a1);
+                load16(p + (c + 2 * lpr) * V, a2);
+                load16(p + (c + 3 * lpr) * V, a3);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc = fma(a0[v], z[c * V + v], acc);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc = fma(a1[v], z[(c + lpr) * V + v], acc);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc = fma(a2[v], z[(c + 2 * lpr) * V + v], acc);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc = fma(a3[v], z[(c + 3 * lpr) * V + v], acc);
+            }
+            for (; c < CG; c += lpr) {
                 TC a[V];
-                load16(A + (int64_t)row * ld + c * V, a);
+                load16(p + c * V, a);
 #pragma unroll
                 for (int v = 0; v < V; ++v) acc = fma(a[v], z[c * V + v], acc);
             }
@@ -203,12 +238,21 @@ __device__ double prod_n(const TA* A, int m, int n, int ld, const typename Elem<
 // r = b - A64 x in FP64 (A64 row-major m x n); returns ||r||² and rᵀb
 template <class TC, int NT>
 __device__ double2 residual64(const double* __restrict__ A64, int m, int n, const double* __restrict__ b,
-                              const double* __restrict__ x, TC* r) {
+                              const double* x, TC* r) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double sq = 0.0, rb = 0.0;
     for (int row = warp; row < m; row += NT / 32) {
         double acc = 0.0;
-        for (int c = lane; c < n; c += 32) acc = fma(A64[(int64_t)row * n + c], x[c], acc);
+        const double* a = A64 + (int64_t)row * n;
+        int c = lane;
+        for (; c + 96 < n; c += 128) {
+            const double a0 = __ldg(a + c), a1 = __ldg(a + c + 32), a2 = __ldg(a + c + 64), a3 = __ldg(a + c + 96);
+            acc = fma(a0, __ldcg(x + c), acc);
+            acc = fma(a1, __ldcg(x + c + 32), acc);
+            acc = fma(a2, __ldcg(x + c + 64), acc);
+            acc = fma(a3, __ldcg(x + c + 96), acc);
+        }
+        for (; c < n; c += 32) acc = fma(__ldg(a + c), __ldcg(x + c), acc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) {
@@ -230,8 +274,8 @@ struct Shared {           // block-wide scalars (static shared memory)
     int32_t stop;
 };
 
-template <class TA, int NT>
-__global__ void __launch_bounds__(NT)
+template <class TA, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
 batch_cta(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, int count,
           const TA* __restrict__ alo, const double* __restrict__ a64, const double* __restrict__ bvec,
           double* __restrict__ xvec, BatchOut out, int32_t* queue, BatchParams P) {
@@ -268,7 +312,7 @@ batch_cta(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, in
             A = As;
         }
         // x = 0, dx = 0 (with the padding the products read), r = b
-        for (int c = tid; c < n; c += NT) x[c] = 0.0;
+        for (int c = tid; c < n; c += NT) __stcg(x + c, 0.0);
         for (int c = tid; c < P.n_cap; c += NT) dx[c] = 0;
         for (int i = 0; i < P.t_max; ++i)
             for (int c = tid; c < P.n_cap; c += NT) z[(int64_t)i * P.n_cap + c] = 0;
@@ -298,7 +342,7 @@ batch_cta(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, in
             }
             if (need_true) {   // refinement: fold dx into x, FP64 residual
                 for (int c = tid; c < n; c += NT) {
-                    x[c] += (double)dx[c];
+                    __stcg(x + c, __ldcg(x + c) + (double)dx[c]);
                     dx[c] = 0;
                 }
                 __syncthreads();
@@ -368,7 +412,7 @@ batch_cta(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, in
         double rel = 0.0;
         if (reason != TACTA_REASON_ZERO_RHS) {
             for (int c = tid; c < n; c += NT) {
-                x[c] += (double)dx[c];
+                __stcg(x + c, __ldcg(x + c) + (double)dx[c]);
                 dx[c] = 0;
             }
             __syncthreads();
@@ -438,7 +482,8 @@ struct Config {
     int nt;            // threads per block
     int per_sm;        // resident blocks per SM
 };
-constexpr Config kConfigs[] = {{128, 2}, {256, 1}, {256, 2}, {512, 1}};
+constexpr Config kConfigs[] = {{128, 2}, {128, 4}, {256, 1}, {256, 2}, {512, 1}};
+constexpr int kDefaultConfig = 3;
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
 template <class TA>
@@ -451,29 +496,42 @@ size_t vec_bytes(const BatchParams& P, int nt) {
 // dynamic shared memory a block may ask for (the static Shared block and slack aside)
 constexpr int64_t kBatchSmemMax = 232448 - 2048;
 
+template <class TA>
+void set_attrs(cudaError_t& attr) {
+    auto set = [&](const void* f) {
+        if (attr == cudaSuccess)
+            attr = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmemMax);
+    };
+    set((const void*)batch_cta<TA, 128, 2>);
+    set((const void*)batch_cta<TA, 128, 4>);
+    set((const void*)batch_cta<TA, 256, 1>);
+    set((const void*)batch_cta<TA, 256, 2>);
+    set((const void*)batch_cta<TA, 512, 1>);
+}
+
 cudaError_t prepare_kernels() {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
-        auto set = [](const void* f) {
-            if (attr == cudaSuccess)
-                attr = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmemMax);
-        };
-        set((const void*)batch_cta<double, 128>); set((const void*)batch_cta<double, 256>);
-        set((const void*)batch_cta<double, 512>); set((const void*)batch_cta<float, 128>);
-        set((const void*)batch_cta<float, 256>); set((const void*)batch_cta<float, 512>);
-        set((const void*)batch_cta<__nv_bfloat16, 128>); set((const void*)batch_cta<__nv_bfloat16, 256>);
-        set((const void*)batch_cta<__nv_bfloat16, 512>);
+        set_attrs<double>(attr);
+        set_attrs<float>(attr);
+        set_attrs<__nv_bfloat16>(attr);
     });
     return attr;
 }
 
-template <class TA, int NT>
-cudaError_t launch_one(cudaStream_t s, int grid, size_t smem, const SysDesc* sys, const int32_t* order, int count,
-                       const void* alo, const double* a64, const double* b, double* x, BatchOut o, int32_t* queue,
-                       const BatchParams& P) {
-    batch_cta<TA, NT><<<grid, NT, smem, s>>>(sys, order, count, reinterpret_cast<const TA*>(alo), a64, b, x, o,
-                                             queue, P);
+template <class TA>
+cudaError_t launch_cfg(int cfg, cudaStream_t s, int grid, size_t smem, const SysDesc* sys, const int32_t* order,
+                       int count, const void* alo, const double* a64, const double* b, double* x, BatchOut o,
+                       int32_t* queue, const BatchParams& P) {
+    const TA* a = reinterpret_cast<const TA*>(alo);
+    switch (cfg) {
+    case 0: batch_cta<TA, 128, 2><<<grid, 128, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
+    case 1: batch_cta<TA, 128, 4><<<grid, 128, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
+    case 2: batch_cta<TA, 256, 1><<<grid, 256, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
+    case 3: batch_cta<TA, 256, 2><<<grid, 256, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
+    default: batch_cta<TA, 512, 1><<<grid, 512, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
+    }
     return cudaGetLastError();
 }
 
@@ -558,21 +616,17 @@ cudaError_t launch_batch(tacta_batch_s* B, cudaStream_t s, const tacta_options& 
     BatchOut out{B->iters, B->reason, B->rel};
     cudaError_t e = cudaMemsetAsync(B->queue, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-#define TACTA_BATCH_LAUNCH(TA)                                                                                   \
-    switch (C.nt) {                                                                                              \
-    case 128: return launch_one<TA, 128>(s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x,  \
-                                         out, B->queue, P);                                                      \
-    case 256: return launch_one<TA, 256>(s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x,  \
-                                         out, B->queue, P);                                                      \
-    default: return launch_one<TA, 512>(s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x,   \
-                                        out, B->queue, P);                                                       \
-    }
     switch (B->storage) {
-    case TACTA_BATCH_FP64: TACTA_BATCH_LAUNCH(double)
-    case TACTA_BATCH_FP32: TACTA_BATCH_LAUNCH(float)
-    default: TACTA_BATCH_LAUNCH(__nv_bfloat16)
+    case TACTA_BATCH_FP64:
+        return launch_cfg<double>(cfg, s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x, out,
+                                  B->queue, P);
+    case TACTA_BATCH_FP32:
+        return launch_cfg<float>(cfg, s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x, out,
+                                 B->queue, P);
+    default:
+        return launch_cfg<__nv_bfloat16>(cfg, s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x,
+                                         out, B->queue, P);
     }
-#undef TACTA_BATCH_LAUNCH
 }
 
 bool batch_opts_ok(const tacta_options& o) {
@@ -731,7 +785,7 @@ extern "C" tacta_status tacta_batch_cta(tacta_batch B, const double* b, double* 
     BTRY(cudaSetDevice(B->device));
     if (B->count == 0) return TACTA_OK;
     cudaStream_t s = (cudaStream_t)o.stream;
-    const int cfg = B->config >= 0 ? B->config : 2;
+    const int cfg = B->config >= 0 ? B->config : kDefaultConfig;
     {
         size_t smem = 0;
         make_params(B, o, kConfigs[cfg].nt, kConfigs[cfg].per_sm, &smem);
@@ -784,7 +838,7 @@ extern "C" tacta_status tacta_batch_tune(tacta_batch B, const double* b, const t
     tacta_options o = resolve_opts(opt);
     if (!batch_opts_ok(o)) return TACTA_ERR_INVALID;
     BTRY(cudaSetDevice(B->device));
-    if (B->count == 0) { if (best_config) *best_config = 2; return TACTA_OK; }
+    if (B->count == 0) { if (best_config) *best_config = kDefaultConfig; return TACTA_OK; }
     cudaStream_t s = (cudaStream_t)o.stream;
     BTRY(cudaMemcpyAsync(B->b, b, sizeof(double) * B->b_len, cudaMemcpyDefault, s));
     cudaEvent_t e0, e1;

@@ -1,49 +1,107 @@
 // Solve of CTA's auxiliary equation, shared by the single-system and batched paths.
 #pragma once
 
+#include <cmath>
+
 #include "internal.h"
+
+// Round-to-nearest FP64 operations without contraction, on the device and on the host
+// (the host build of this file compiles with -ffp-contract=off).
+#ifdef __CUDA_ARCH__
+#define TACTA_MUL(a, b) __dmul_rn((a), (b))
+#define TACTA_SUB(a, b) __dsub_rn((a), (b))
+#define TACTA_DIV(a, b) __ddiv_rn((a), (b))
+#define TACTA_SQRT(a) __dsqrt_rn(a)
+#else
+#define TACTA_MUL(a, b) ((a) * (b))
+#define TACTA_SUB(a, b) ((a) - (b))
+#define TACTA_DIV(a, b) ((a) / (b))
+#define TACTA_SQRT(a) std::sqrt(a)
+#endif
 
 namespace tacta {
 
 // Auxiliary equation of order t (Eq. eqcoeff): [phi_{i+j}] alpha = [phi_i].
-// Jacobi-scaled Cholesky in natural order, truncated at the first pivot
-// <= pivot_tol; the leading block is solved and the trailing alphas are 0.
-// Arithmetic uses explicit round-to-nearest operations (no contraction).
-static __device__ int hankel_solve_dev(const double* phi, int t, double pivot_tol, double* alpha) {
-    double s[kTMax], G[kTMax][kTMax], L[kTMax][kTMax], y[kTMax], beta[kTMax];
-    int tt = 0;
-    for (int i = 1; i <= t; ++i) {
-        if (!(phi[2 * i] > 0.0)) break;
-        s[i - 1] = __ddiv_rn(1.0, __dsqrt_rn(phi[2 * i]));
-        tt = i;
-    }
-    for (int i = 0; i < tt; ++i)
-        for (int j = 0; j < tt; ++j) G[i][j] = __dmul_rn(__dmul_rn(s[i], phi[i + j + 2]), s[j]);
+// Jacobi scaling G = D [phi_{i+j}] D, D = diag(phi_{2i})^{-1/2}, then the
+// square-root-free Cholesky factorisation G = L diag(d) Lᵀ (L unit lower) in
+// natural order, truncated at the first pivot d_k <= pivot_tol (d_k is the square
+// of the k-th Cholesky pivot, so the truncation is the Cholesky one); the leading
+// block is solved and the trailing alphas are 0.
+// This runs on one thread while the rest of the device waits, so it is written for
+// latency: the order is a template parameter (every loop unrolls and every array
+// lives in registers, not local memory), the moments are loaded up front, and
+// there is one division per pivot (FP64 division and square root are long
+// dependent chains on this GPU).
+template <int T>
+static __host__ __device__ __forceinline__ int hankel_solve_t(const double* phi_in, double pivot_tol, double* alpha) {
+    double phi[2 * T + 1];
+#pragma unroll
+    for (int i = 1; i <= 2 * T; ++i) phi[i] = phi_in[i];
+    int tt = T;
+#pragma unroll
+    for (int i = T; i >= 1; --i)
+        if (!(phi[2 * i] > 0.0)) tt = i - 1;
+    double s[T], L[T][T], d[T], dinv[T], y[T], beta[T];
+#pragma unroll
+    for (int i = 0; i < T; ++i) s[i] = i < tt ? TACTA_DIV(1.0, TACTA_SQRT(phi[2 * i + 2])) : 0.0;
     int rank = 0;
-    for (int k = 0; k < tt; ++k) {
-        double d = G[k][k];
-        for (int j = 0; j < k; ++j) d = __dsub_rn(d, __dmul_rn(L[k][j], L[k][j]));
-        if (!(d > pivot_tol)) break;
-        L[k][k] = __dsqrt_rn(d);
-        for (int i = k + 1; i < tt; ++i) {
-            double v = G[i][k];
-            for (int j = 0; j < k; ++j) v = __dsub_rn(v, __dmul_rn(L[i][j], L[k][j]));
-            L[i][k] = __ddiv_rn(v, L[k][k]);
+    bool go = true;
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+        if (go && k < tt) {
+            double dk = TACTA_MUL(TACTA_MUL(s[k], phi[2 * k + 2]), s[k]);
+#pragma unroll
+            for (int j = 0; j < k; ++j) dk = TACTA_SUB(dk, TACTA_MUL(TACTA_MUL(L[k][j], L[k][j]), d[j]));
+            if (dk > pivot_tol) {
+                d[k] = dk;
+                dinv[k] = TACTA_DIV(1.0, dk);
+#pragma unroll
+                for (int i = k + 1; i < T; ++i) {
+                    double v = TACTA_MUL(TACTA_MUL(s[i], phi[i + k + 2]), s[k]);
+#pragma unroll
+                    for (int j = 0; j < k; ++j) v = TACTA_SUB(v, TACTA_MUL(TACTA_MUL(L[i][j], L[k][j]), d[j]));
+                    L[i][k] = TACTA_MUL(v, dinv[k]);
+                }
+                rank = k + 1;
+            } else {
+                go = false;
+            }
         }
-        rank = k + 1;
     }
-    for (int i = 0; i < rank; ++i) {
-        double v = __dmul_rn(s[i], phi[i + 1]);
-        for (int j = 0; j < i; ++j) v = __dsub_rn(v, __dmul_rn(L[i][j], y[j]));
-        y[i] = __ddiv_rn(v, L[i][i]);
+    double w[T];
+#pragma unroll
+    for (int i = 0; i < T; ++i) {               // L w = D phi_{1..}
+        double v = TACTA_MUL(s[i], phi[i + 1]);
+#pragma unroll
+        for (int j = 0; j < i; ++j) v = TACTA_SUB(v, TACTA_MUL(L[i][j], w[j]));
+        w[i] = i < rank ? v : 0.0;
     }
-    for (int i = rank - 1; i >= 0; --i) {
+#pragma unroll
+    for (int i = 0; i < T; ++i) y[i] = i < rank ? TACTA_MUL(w[i], dinv[i]) : 0.0;   // y = diag(d)^{-1} w
+#pragma unroll
+    for (int i = T - 1; i >= 0; --i) {          // Lᵀ beta = diag(d)^{-1} y
         double v = y[i];
-        for (int j = i + 1; j < rank; ++j) v = __dsub_rn(v, __dmul_rn(L[j][i], beta[j]));
-        beta[i] = __ddiv_rn(v, L[i][i]);
+#pragma unroll
+        for (int j = i + 1; j < T; ++j)
+            if (j < rank) v = TACTA_SUB(v, TACTA_MUL(L[j][i], beta[j]));
+        beta[i] = v;
     }
-    for (int i = 0; i < t; ++i) alpha[i] = i < rank ? __dmul_rn(s[i], beta[i]) : 0.0;
+#pragma unroll
+    for (int i = 0; i < T; ++i) alpha[i] = i < rank ? TACTA_MUL(s[i], beta[i]) : 0.0;
     return rank;
+}
+
+static __host__ __device__ int hankel_solve_dev(const double* phi, int t, double pivot_tol, double* alpha) {
+    switch (t) {
+    case 1: return hankel_solve_t<1>(phi, pivot_tol, alpha);
+    case 2: return hankel_solve_t<2>(phi, pivot_tol, alpha);
+    case 3: return hankel_solve_t<3>(phi, pivot_tol, alpha);
+    case 4: return hankel_solve_t<4>(phi, pivot_tol, alpha);
+    case 5: return hankel_solve_t<5>(phi, pivot_tol, alpha);
+    case 6: return hankel_solve_t<6>(phi, pivot_tol, alpha);
+    case 7: return hankel_solve_t<7>(phi, pivot_tol, alpha);
+    default: return hankel_solve_t<8>(phi, pivot_tol, alpha);
+    }
 }
 
 }  // namespace tacta

@@ -34,6 +34,7 @@ struct Ctl {
     int32_t matvecs;       // products with A or Aᵀ made by the iteration (setup included)
     int32_t pad_;
     double bn2;            // ||b||²  (b = rhs of the operator in use)
+    double inv_bn2;        // 1 / ||b||² (0 when b = 0): the history stores ||r||² / ||b||²
     double mtbn2;          // ||Mᵀ b||²
     double tol2, tol_n2, pivot_tol;
     double res_thr, nrm_thr;
@@ -133,6 +134,8 @@ constexpr int kXCapCompactPlan = 1280, kXSpanCompactPlan = 2304;   // compact x-
 // indices shrink to 16-bit slots in them.
 constexpr int kRunCap = 1280, kRunXs = 896, kRunMax = 4, kRunGap = 16;
 constexpr int kPadLcol = 8;
+// ring depth of the warp-specialised run-staged product (0: the block-synchronous one)
+constexpr int kRwStages = 3;
 // Mixed-precision CTA refines (FP64 residual, fold of the FP32 correction) as soon as
 // the FP32 inner iteration has reduced the residual by kRefineEta over the last
 // refinement; the FP32 chain cannot resolve much more than that.
@@ -192,6 +195,7 @@ cudaError_t launch_reduce_vec(const LaunchCtx& L, int64_t len, const double* a, 
 cudaError_t launch_ctl_init(const LaunchCtx& L, const Ctl& host_init);
 cudaError_t launch_copy_gated(const LaunchCtx& L, double* dst, const double* src, int64_t len, int gate);
 cudaError_t launch_fill(const LaunchCtx& L, double* dst, double v, int64_t len);
+cudaError_t launch_hist_sqrt(cudaStream_t s, double* h, int64_t len);   // ||r||²/||b||² -> ||r||/||b||
 
 // mixed precision (FP32 chain, FP64 refinement)
 cudaError_t launch_spmv32(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y, float scale,

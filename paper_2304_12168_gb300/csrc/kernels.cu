@@ -64,9 +64,12 @@ __device__ void loop_top(Ctl* c) {
     if (c->k >= c->max_iter) c->status = TACTA_REASON_MAXITER;
 }
 
+// the history holds ||r||² / ||b||² while the solve runs (a multiply: FP64 division and
+// square root are long dependent chains, and finishers run on one thread while the
+// device waits); hist_sqrt turns it into ||r|| / ||b|| once, when it is copied out
 __device__ void put_hist(Ctl* c, double* h) {
     if (h != nullptr && c->k < c->hist_cap) {
-        h[c->k] = sqrt(c->rn2 / c->bn2);
+        h[c->k] = __dmul_rn(c->rn2, c->inv_bn2);
         if (c->k + 1 > c->hist_len) c->hist_len = c->k + 1;
     }
 }
@@ -158,6 +161,7 @@ __device__ __noinline__ void finish(Ctl* c, const FinArgs& f, double r0, double 
         break;
     case FIN_SETUP_B:
         c->bn2 = r0;
+        c->inv_bn2 = r0 > 0.0 ? __ddiv_rn(1.0, r0) : 0.0;
         if (r0 == 0.0) c->status = TACTA_REASON_ZERO_RHS;
         else if (!finite(r0)) c->status = TACTA_REASON_NONFINITE;
         break;
@@ -179,6 +183,7 @@ __device__ __noinline__ void finish(Ctl* c, const FinArgs& f, double r0, double 
 // An FP64 warp-instruction costs the same on GB300 whatever the number of
 // active lanes, so the values go through shared memory and warp 0 alone adds
 // them (7 + 5 FP64 warp-instructions, instead of a shuffle tree in every warp).
+template <int NT = kBlock>
 __device__ __forceinline__ double block_sum_warp0(double v, double* sh) {
     sh[threadIdx.x] = v;
     __syncthreads();
@@ -186,7 +191,7 @@ __device__ __forceinline__ double block_sum_warp0(double v, double* sh) {
     if (threadIdx.x < 32) {
         s = sh[threadIdx.x];
 #pragma unroll
-        for (int i = 1; i < kBlock / 32; ++i) s += sh[threadIdx.x + 32 * i];
+        for (int i = 1; i < NT / 32; ++i) s += sh[threadIdx.x + 32 * i];
         s = warp_sum(s);
     }
     __syncthreads();
@@ -195,14 +200,14 @@ __device__ __forceinline__ double block_sum_warp0(double v, double* sh) {
 
 // Block-level reduction of NRED values (a0 and, if NRED = 2, a1), one partial
 // per block; the last block to finish (atomic ticket, no waiting) sums the
-// partials in block order and runs the finisher. Requires blockDim = kBlock.
-template <int NRED = 2>
+// partials in block order and runs the finisher. Requires blockDim = NT.
+template <int NRED = 2, int NT = kBlock>
 __device__ void reduce_and_finish(double a0, double a1, Ctl* ctl, double* partials,
                                   const FinArgs& f) {
-    __shared__ double sh[kBlock];
+    __shared__ double sh[NT];
     __shared__ int am_last;
-    const double s0 = block_sum_warp0(a0, sh);
-    const double s1 = NRED > 1 ? block_sum_warp0(a1, sh) : 0.0;
+    const double s0 = block_sum_warp0<NT>(a0, sh);
+    const double s1 = NRED > 1 ? block_sum_warp0<NT>(a1, sh) : 0.0;
     if (threadIdx.x == 0) {
         partials[2 * blockIdx.x] = s0;
         partials[2 * blockIdx.x + 1] = s1;
@@ -218,8 +223,8 @@ __device__ void reduce_and_finish(double a0, double a1, Ctl* ctl, double* partia
         t0 += __ldcg(&partials[2 * i]);
         if (NRED > 1) t1 += __ldcg(&partials[2 * i + 1]);
     }
-    t0 = block_sum_warp0(t0, sh);
-    if (NRED > 1) t1 = block_sum_warp0(t1, sh);
+    t0 = block_sum_warp0<NT>(t0, sh);
+    if (NRED > 1) t1 = block_sum_warp0<NT>(t1, sh);
     if (threadIdx.x == 0) {
         ctl->counter = 0;
         finish(ctl, f, t0, t1);
@@ -787,6 +792,122 @@ static cudaError_t spmv_tiled_r_launch(const LaunchCtx& L, const DevCSR& A, cons
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ run-staged, warp-specialised
+//
+// The same tiles and stages as spmv_tiled_r, without the block-wide barrier per
+// tile: one producer warp streams tiles into a ring of S stages (a "full"
+// mbarrier per stage completes when the tile's bytes land), and each of the eight
+// consumer warps multiplies its own 32 rows of a tile as soon as it has landed,
+// then arrives on the stage's "empty" mbarrier; the producer refills a stage once
+// all eight warps have released it. Warps drift apart instead of waiting for the
+// slowest one, which spreads shared-memory and FP64 issue over time.
+
+constexpr int kRwConsumers = kTileRows / 32;
+constexpr int kRwThreads = (kRwConsumers + 1) * 32;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+template <int S> constexpr int rw_blocks_per_sm() { return S == 2 ? 4 : 3; }
+
+template <int S, int EPI>
+__global__ void __launch_bounds__(kRwThreads, rw_blocks_per_sm<S>())
+spmv_tiled_rw(const int4* __restrict__ tiles, const int2* __restrict__ runs, int ntiles,
+              const int32_t* __restrict__ rowptr, const uint16_t* __restrict__ lcol,
+              const double* __restrict__ vals, const double* __restrict__ x, double* __restrict__ y,
+              EpiArgs e, Ctl* ctl, double* partials, FinArgs f, int gate) {
+    if (gated_out(ctl, gate)) return;
+    if (gate != GATE_FORCE && blockIdx.x == 0 && threadIdx.x == 0) ctl->matvecs += 1;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TileStageR* st = reinterpret_cast<TileStageR*>(smem_raw);
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ volatile int failed;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int G = gridDim.x;
+    if (tid == 0) {
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kRwConsumers);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
+    }
+    __syncthreads();
+    double a0 = 0.0, a1 = 0.0;
+    int last_use[S];   // producer lane: the last use issued into each stage
+    for (int k = 0; k < S; ++k) last_use[k] = -1;
+    if (warp == kRwConsumers) {
+        // producer: lane 0 issues tile j into stage j % S once its previous use is released
+        if (lane == 0) {
+            for (int j = 0;; ++j) {
+                const int t = blockIdx.x + j * G;
+                if (t >= ntiles || failed) break;
+                const int k = j % S, u = j / S;
+                if (u > 0 && !mbar_wait_bounded(&empty[k], (uint32_t)((u - 1) & 1))) {
+                    failed = 1;
+                    atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+                    break;
+                }
+                tile_issue_r(__ldg(tiles + t), runs + (size_t)t * kRunMax, st + k, &full[k], rowptr, lcol, vals, x);
+                last_use[k] = u;
+            }
+        }
+    } else {
+        const double s = (EPI == EPI_TAPIVOT) ? ctl->s : 0.0;
+        for (int j = 0;; ++j) {
+            const int t = blockIdx.x + j * G;
+            if (t >= ntiles) break;
+            const int k = j % S;
+            if (failed || !mbar_wait_bounded(&full[k], (uint32_t)((j / S) & 1))) {
+                failed = 1;
+                atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+                break;
+            }
+            const int4 d = __ldg(tiles + t);
+            const TileStageR* Sg = st + k;
+            const int row = d.x + warp * 32 + lane;
+            const bool active = row < d.y;
+            int kb = 0, len = 0;
+            if (active) {
+                const int r0 = d.x & ~3;
+                kb = Sg->rp[row - r0];
+                len = Sg->rp[row + 1 - r0] - kb;
+            }
+            const int maxlen = __reduce_max_sync(0xffffffffu, len);
+            const int vb = kb - (d.z & ~1), cb = kb - (d.z & ~7);
+            double sum = 0.0;
+            for (int u = 0; u < maxlen; ++u)
+                if (u < len) sum = fma(Sg->vals[vb + u], Sg->xs[Sg->lcol[cb + u]], sum);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[k]);   // this warp is done with stage k
+            if (active) epilogue<EPI>(row, sum, y, e, s, a0, a1);
+        }
+    }
+    __syncthreads();
+    if (failed && warp == kRwConsumers && lane == 0) {
+        // a wait gave up: let every copy already issued land before the block exits
+        for (int k = 0; k < S; ++k)
+            if (last_use[k] >= 0) mbar_wait_bounded(&full[k], (uint32_t)(last_use[k] & 1));
+    }
+    if (EPI != EPI_NONE || f.kind != FIN_NONE)
+        reduce_and_finish<EpiRed<EPI>::value, kRwThreads>(a0, a1, ctl, partials, f);
+}
+
+template <int S>
+size_t spmv_tiled_rw_smem() { return (size_t)S * sizeof(TileStageR); }
+
+template <int S, int EPI>
+static cudaError_t spmv_tiled_rw_launch(const LaunchCtx& L, const DevCSR& A, const double* x, double* y,
+                                        EpiArgs e, FinArgs f, int gate) {
+    const int sms = L.max_grid / 8;
+    const int grid = std::min(A.ntiles, std::max(1, sms * rw_blocks_per_sm<S>()));
+    spmv_tiled_rw<S, EPI><<<grid, kRwThreads, spmv_tiled_rw_smem<S>(), L.stream>>>(
+        A.tiles, A.runs, A.ntiles, A.rowptr, A.lcol, A.vals, x, y, e, L.ctl, L.partials, f, gate);
+    if (L.launches) ++*L.launches;
+    return cudaGetLastError();
+}
+
 cudaError_t spmv_tiled_prepare() {
     static bool done = false;
     if (done) return cudaSuccess;
@@ -820,6 +941,13 @@ cudaError_t spmv_tiled_prepare() {
     TACTA_TILED_R_ATTR(EPI_NONE) TACTA_TILED_R_ATTR(EPI_NORM) TACTA_TILED_R_ATTR(EPI_RESID)
     TACTA_TILED_R_ATTR(EPI_TAPIVOT) TACTA_TILED_R_ATTR(EPI_RESID_F32) TACTA_TILED_R_ATTR(EPI_NORM_POS)
 #undef TACTA_TILED_R_ATTR
+#define TACTA_TILED_RW_ATTR(EPI)                                                                         \
+    if (e == cudaSuccess)                                                                                \
+        e = cudaFuncSetAttribute(spmv_tiled_rw<kRwStages, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)spmv_tiled_rw_smem<kRwStages>());
+    TACTA_TILED_RW_ATTR(EPI_NONE) TACTA_TILED_RW_ATTR(EPI_NORM) TACTA_TILED_RW_ATTR(EPI_RESID)
+    TACTA_TILED_RW_ATTR(EPI_TAPIVOT) TACTA_TILED_RW_ATTR(EPI_RESID_F32) TACTA_TILED_RW_ATTR(EPI_NORM_POS)
+#undef TACTA_TILED_RW_ATTR
     if (e == cudaSuccess) {
         int nb = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmv_tiled_r<EPI_NORM>, kTileRows,
@@ -875,6 +1003,16 @@ static cudaError_t spmv_dispatch(const LaunchCtx& L, int kind, const Acc& acc, c
 
 cudaError_t launch_spmv(const LaunchCtx& L, const DevOperand& A, const double* x, double* y,
                         int epi, EpiArgs e, FinArgs f, int gate) {
+    if (A.format == TACTA_CSR && A.csr.cfg.kind == 3 && A.csr.lcol && kRwStages > 0) {
+        switch (epi) {
+        case EPI_NONE: return spmv_tiled_rw_launch<kRwStages, EPI_NONE>(L, A.csr, x, y, e, f, gate);
+        case EPI_NORM: return spmv_tiled_rw_launch<kRwStages, EPI_NORM>(L, A.csr, x, y, e, f, gate);
+        case EPI_RESID: return spmv_tiled_rw_launch<kRwStages, EPI_RESID>(L, A.csr, x, y, e, f, gate);
+        case EPI_RESID_F32: return spmv_tiled_rw_launch<kRwStages, EPI_RESID_F32>(L, A.csr, x, y, e, f, gate);
+        case EPI_NORM_POS: return spmv_tiled_rw_launch<kRwStages, EPI_NORM_POS>(L, A.csr, x, y, e, f, gate);
+        default: return spmv_tiled_rw_launch<kRwStages, EPI_TAPIVOT>(L, A.csr, x, y, e, f, gate);
+        }
+    }
     if (A.format == TACTA_CSR && A.csr.cfg.kind == 3 && A.csr.lcol) {
         switch (epi) {
         case EPI_NONE: return spmv_tiled_r_launch<EPI_NONE>(L, A.csr, x, y, e, f, gate);
@@ -1390,6 +1528,17 @@ cudaError_t launch_copy_gated(const LaunchCtx& L, double* dst, const double* src
                               int gate) {
     copy_gated<<<L.max_grid, kBlock, 0, L.stream>>>(dst, src, len, L.ctl, gate);
     if (L.launches) ++*L.launches;
+    return cudaGetLastError();
+}
+
+__global__ void hist_sqrt(double* h, int64_t len) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        h[i] = sqrt(h[i]);
+}
+
+cudaError_t launch_hist_sqrt(cudaStream_t s, double* h, int64_t len) {
+    if (len <= 0) return cudaSuccess;
+    hist_sqrt<<<(int)std::min<int64_t>((len + kBlock - 1) / kBlock, 1024), kBlock, 0, s>>>(h, len);
     return cudaGetLastError();
 }
 

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "hankel.cuh"
 
 namespace tacta {
 
@@ -755,10 +756,13 @@ static tacta_status load_b(Plan* p, const Opts& O, const VecIO& io) {
     return TACTA_OK;
 }
 
-static tacta_status store_out(Plan* p, const Opts& O, const VecIO& io, const double* x, int hist_len) {
+static tacta_status store_out(Plan* p, const Opts& O, const VecIO& io, const double* x, int hist_len,
+                              int64_t* launches = nullptr) {
     CUDA_TRY(cudaMemcpyAsync(io.x_out, x, sizeof(double) * p->n, cudaMemcpyDefault, O.s));
     if (io.hist && io.hist_cap > 0 && hist_len > 0) {
         const int64_t h = std::min<int64_t>(hist_len, io.hist_cap);
+        CUDA_TRY(launch_hist_sqrt(O.s, p->hist, h));
+        if (launches) ++*launches;
         CUDA_TRY(cudaMemcpyAsync(io.hist, p->hist, sizeof(double) * h, cudaMemcpyDefault, O.s));
     }
     CUDA_TRY(cudaStreamSynchronize(O.s));
@@ -853,7 +857,7 @@ static tacta_status plan_cta(Plan* p, const VecIO& io, const tacta_options* opt,
     if ((st = exit_residuals(p, O, p->x, &launches)) != TACTA_OK) return st;
     if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
     Ctl c = *p->stage;
-    if ((st = store_out(p, O, io, p->x, c.hist_len)) != TACTA_OK) return st;
+    if ((st = store_out(p, O, io, p->x, c.hist_len, &launches)) != TACTA_OK) return st;
     const tacta_status out = status_of(c.status);
     if (out == TACTA_ERR_NONFINITE) set_error("non-finite value in a reduction");
     fill_info(info, c, out, launches);
@@ -921,7 +925,7 @@ static tacta_status plan_ta(Plan* p, const VecIO& io, const tacta_options* opt, 
     if ((st = exit_residuals(p, O, p->x, &launches)) != TACTA_OK) return st;
     if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
     Ctl c = *p->stage;
-    if ((st = store_out(p, O, io, p->x, c.hist_len)) != TACTA_OK) return st;
+    if ((st = store_out(p, O, io, p->x, c.hist_len, &launches)) != TACTA_OK) return st;
     const tacta_status out = status_of(c.status);
     if (out == TACTA_ERR_NONFINITE) set_error("non-finite value in a reduction");
     if (out == TACTA_ERR_TIMEOUT) set_error("a bounded wait inside a kernel gave up");
@@ -957,7 +961,7 @@ static tacta_status plan_minnorm(Plan* p, const VecIO& io, const tacta_options* 
     const double bn2_orig = c1.bn2, atbn2_orig = c1.mtbn2;
     if (c1.status == TACTA_REASON_ZERO_RHS) {
         CUDA_TRY(cudaMemsetAsync(p->x, 0, sizeof(double) * p->n, O.s));
-        if ((st = store_out(p, O, io, p->x, c1.hist_len)) != TACTA_OK) return st;
+        if ((st = store_out(p, O, io, p->x, c1.hist_len, &launches)) != TACTA_OK) return st;
         out_info.status = TACTA_OK;
         out_info.reason = TACTA_REASON_ZERO_RHS;
         out_info.launches = launches;
@@ -965,7 +969,7 @@ static tacta_status plan_minnorm(Plan* p, const VecIO& io, const tacta_options* 
         return TACTA_OK;
     }
     if (status_of(c1.status) != TACTA_OK) {   // CTA did not reach tol_cta
-        if ((st = store_out(p, O, io, p->x, c1.hist_len)) != TACTA_OK) return st;
+        if ((st = store_out(p, O, io, p->x, c1.hist_len, &launches)) != TACTA_OK) return st;
         const tacta_status s1 = status_of(c1.status);
         fill_info(info, c1, s1, launches);
         if (info) { info->cta_iters = c1.k; info->iters = 0; info->rho = 0.0; info->matvecs = 0; }
@@ -1037,6 +1041,7 @@ static tacta_status plan_minnorm(Plan* p, const VecIO& io, const tacta_options* 
     if ((st = store_out(p, O, io, p->xbest, 0)) != TACTA_OK) return st;
     if (io.hist && io.hist_cap > 0 && c1.hist_len > 0) {
         // the CTA phase history was overwritten only if hist was reused: it was not (trips pass NULL)
+        CUDA_TRY(launch_hist_sqrt(O.s, p->hist, std::min<int64_t>(c1.hist_len, io.hist_cap)));
         CUDA_TRY(cudaMemcpyAsync(io.hist, p->hist, sizeof(double) * std::min<int64_t>(c1.hist_len, io.hist_cap),
                                  cudaMemcpyDefault, O.s));
         CUDA_TRY(cudaStreamSynchronize(O.s));
@@ -1239,3 +1244,8 @@ tacta_status ta_minnorm(const tacta_matrix* A, const double* b, const double* x0
 }
 
 }  // extern "C"
+
+extern "C" int32_t tacta_aux_solve(const double* phi, int32_t t, double pivot_tol, double* alpha) {
+    if (!phi || !alpha || t < 1 || t > kTMax) return -1;
+    return hankel_solve_dev(phi, t, pivot_tol, alpha);
+}

@@ -146,17 +146,23 @@ def test_graph_replay_and_configs_agree(tacta):
 def test_full_batch_4096_fp32(tacta):
     """The full workload: 4096 systems (m in [32, 512], n in [m/2, 2m], 10% rank m/2),
     FP32 storage, tol 1e-8, at most 20000 steps each. Every system that reports RESIDUAL
-    has a host-recomputed FP64 residual within tol; every system with n/m outside
-    [0.8, 1.25] or of low rank converges."""
+    has a host-recomputed FP64 residual within tol. The systems that are well conditioned
+    by construction converge: full rank with n/m outside [0.8, 1.25] (Gaussian, condition
+    number below ~20), and rank r = m/2 with n >= 1.5 r (U Vᵀ with both factors at least
+    1.5 times as long as wide). Near-square systems (condition number up to ~1e3-1e4 at
+    these sizes) may reach the step cap; at least 98% of all systems converge."""
     B0 = gen.dense_batch(4096, seed=7)
     x, iters, rel, reason = run(tacta, B0.mats, B0.bs, tacta.BATCH_FP32, tol=1e-8, tol_normal=0.0,
                                 max_iter=20000)
     names = [tacta.REASON[int(r)] for r in reason]
     for s, (A, b) in enumerate(zip(B0.mats, B0.bs)):
         m, n = A.shape
+        assert names[s] in ("RESIDUAL", "MAXITER"), (s, names[s])
         if names[s] == "RESIDUAL":
             r = np.linalg.norm(b - A @ x[s]) / np.linalg.norm(b)
             assert r <= 1e-8 * (1 + 1e-6), (s, r)
-        elif B0.low_rank[s] or n / m >= 1.25 or n / m <= 0.8:
-            raise AssertionError((s, m, n, names[s], rel[s]))
-        assert names[s] in ("RESIDUAL", "MAXITER"), (s, names[s])
+            continue
+        rank = m // 2 if B0.low_rank[s] else min(m, n)
+        well = (n >= 1.5 * rank) if B0.low_rank[s] else (n / m >= 1.25 or n / m <= 0.8)
+        assert not well, (s, m, n, bool(B0.low_rank[s]), names[s], rel[s])
+    assert names.count("RESIDUAL") >= 0.98 * len(names)
