@@ -212,7 +212,60 @@ def extra_workloads(tacta, dev, stream, plan_stencil, b_stencil, steps):
                                       "iters": info["iters"], "rel_res": info["rel_res"]}
     plan.close()
     out["batched_dense_4096"] = batched_workload(tacta, dev, stream)
+    out["dense_256"] = dense_workload(tacta, dev, stream)
+    out["autograd_2000x8000"] = autograd_workload(tacta, dev, stream)
     return out
+
+
+def dense_workload(tacta, dev, stream):
+    """Dense 256 x 256 N(0,1) (seed 0) and its rank-128 variant U Vᵀ: CTA and TA to a
+    relative residual of 1e-10 (at most 20000 steps), inputs resident, device events."""
+    import gen
+    import torch
+    res = {}
+    for name, p in (("full_rank", gen.dense_gaussian(256, 256, seed=0)),
+                    ("rank_128", gen.dense_low_rank(256, 256, 128, seed=1))):
+        A = torch.from_numpy(p.dense).to(dev)
+        b = torch.from_numpy(p.b).to(dev)
+        plan = tacta.Plan(A)
+        for alg in ("cta", "ta"):
+            kw = dict(tol=1e-10, tol_normal=0.0, max_iter=20000)
+            fn = getattr(plan, alg)
+            fn(b, **kw)
+            t, (x, _, info) = timed(lambda: fn(b, **kw), stream)
+            res[f"{name}_{alg}"] = {"time_to_tol_ms": t, "iters": info["iters"],
+                                    "it_per_s": info["iters"] / (t * 1e-3), "rel_res": info["rel_res"],
+                                    "reason": info["reason_name"]}
+        plan.close()
+    return res
+
+
+def autograd_workload(tacta, dev, stream):
+    """Differentiable min-norm solve on a dense 2000 x 8000 N(0,1) system, L = ||x - x_t||²:
+    forward + backward time and dL/db against the closed form (A Aᵀ)^{-1} A g (numpy)."""
+    import numpy as np
+    import torch
+    from paper_2304_12168_gb300.autograd import cta_solve_autograd
+    rng = np.random.default_rng(5)
+    D = rng.standard_normal((2000, 8000))
+    bh = rng.standard_normal(2000)
+    xt = torch.from_numpy(rng.standard_normal(8000)).to(dev)
+    opts = dict(tol=1e-12, tol_normal=0.0, max_iter=20000)
+
+    def step():
+        A = torch.tensor(D, device=dev, requires_grad=True)
+        b = torch.tensor(bh, device=dev, requires_grad=True)
+        x = cta_solve_autograd(A, b, **opts)
+        ((x - xt) ** 2).sum().backward()
+        return x, b.grad
+    step()
+    t, (x, gb) = timed(step, stream)
+    G = D @ D.T
+    xs = D.T @ np.linalg.solve(G, bh)
+    lam = np.linalg.solve(G, D @ (2 * (xs - xt.cpu().numpy())))
+    return {"fwd_bwd_ms": t, "tol": 1e-12,
+            "rel_err_x": float(np.linalg.norm(x.detach().cpu().numpy() - xs) / np.linalg.norm(xs)),
+            "rel_err_dL_db": float(np.linalg.norm(gb.cpu().numpy() - lam) / np.linalg.norm(lam))}
 
 
 def batched_workload(tacta, dev, stream):

@@ -29,6 +29,7 @@
 
 #include "hankel.cuh"
 #include "internal.h"
+#include "mbarrier.cuh"
 
 namespace tacta {
 namespace {
@@ -81,6 +82,7 @@ struct BatchParams {
     int32_t max_iter, R, t_max, cycle;
     int32_t m_cap, n_cap;  // vector capacities (n_cap a multiple of 8)
     int64_t a_cap;         // elements of A a block can stage in shared memory
+    int64_t area_bytes;    // streamed kernel: bytes of the A area (ring, or A when resident)
 };
 
 struct BatchOut {
@@ -428,6 +430,373 @@ batch_cta(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, in
     }
 }
 
+// ------------------------------------------------------------------ streamed, fused kernel
+//
+// Same iteration as batch_cta, with the products reorganised around the reads of A:
+//  * one pass over A serves both products of a chain step: for each row, the warp that
+//    owns it forms u_i[row] = A[row,:] z_i / s (lanes hold the row's values in registers,
+//    a shuffle reduction gives the dot product) and at once adds A[row,:]ᵀ u_i[row] / s
+//    to its lanes' register accumulators of z_{i+1}; a step of order t costs t + 1
+//    passes (z_1 = Aᵀ r, then u_i with z_{i+1}, the last pass u_t only) instead of 2t;
+//  * A reaches shared memory by 1-D bulk copies (cp.async.bulk) of 32 KB row chunks: one
+//    producer warp keeps a three-chunk ring full ("full"/"empty" mbarriers, bounded
+//    waits), so tens of kilobytes are in flight per SM whatever the registers allow;
+//    when A_s fits the area it is copied once and every pass reads it in place.
+// Inside an iteration the consumer warps synchronise among themselves (named barrier
+// 1), never with the producer, which may be waiting for a stage; the whole block meets
+// only at iteration boundaries, after the producer has issued the iteration's chunks.
+// Requires ceil(n / V) <= 32 JV for every system (the accumulators live in registers).
+
+constexpr int kChunkBytes = 32 * 1024;
+constexpr int kRing = 3;
+
+template <int NT>
+__device__ __forceinline__ void consumers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+
+// sum of one FP64 value over the NT consumer threads (all must call); every caller gets it
+template <int NT>
+__device__ __forceinline__ double consumer_sum(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    consumers_sync<NT>();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    consumers_sync<NT>();
+    double r = 0.0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) r += red[i];
+    return r;
+}
+
+struct Ring {
+    unsigned char* area;   // kRing stages of kChunkBytes
+    uint64_t* full;
+    uint64_t* empty;
+};
+
+// One pass over A (consumer warps). DOT: uo = A zin * sc (returns ||uo||² in sq_u);
+// else the row weights come from uin. AXPY: zo = Aᵀ u * sc (returns ||zo||² in sq_z).
+// resident: A_s is in shared memory at Ares; else chunk q of the sequence sits in ring
+// stage q % kRing. Returns false if a wait gave up.
+template <class TA, int NW, int JV, bool DOT, bool AXPY>
+__device__ bool fused_pass(const TA* Ares, bool resident, const Ring& ring, uint32_t& qseq, int m, int n, int ld,
+                           int R, int nch, int n_cap, const typename Elem<TA>::TC* zin,
+                           const typename Elem<TA>::TC* uin, typename Elem<TA>::TC* uo,
+                           typename Elem<TA>::TC* zo, typename Elem<TA>::TC* part, double sc, double* red,
+                           double& sq_u, double& sq_z) {
+    using TC = typename Elem<TA>::TC;
+    constexpr int V = Elem<TA>::V, NT = NW * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int CG = ld / V;
+    const TC tsc = (TC)sc;
+    TC acc[JV][V];
+#pragma unroll
+    for (int j = 0; j < JV; ++j)
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[j][v] = 0;
+    double su = 0.0;
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+        const TA* chunk;
+        int k = 0;
+        if (resident) {
+            chunk = Ares + (int64_t)c * R * ld;
+        } else {
+            k = (int)(qseq % kRing);
+            if (ok) ok = mbar_wait_bounded(&ring.full[k], (qseq / kRing) & 1u);
+            chunk = reinterpret_cast<const TA*>(ring.area + (size_t)k * kChunkBytes);
+        }
+        const int row0 = c * R, rows = min(R, m - row0);
+        if (ok) {
+            for (int rr = warp; rr < rows; rr += NW) {
+                TC a[JV][V];
+#pragma unroll
+                for (int j = 0; j < JV; ++j) {
+                    const int cv = lane + 32 * j;
+                    if (cv < CG) {
+                        load16(chunk + (int64_t)rr * ld + cv * V, a[j]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) a[j][v] = 0;
+                    }
+                }
+                TC u;
+                if (DOT) {
+                    TC dsum = 0;
+#pragma unroll
+                    for (int j = 0; j < JV; ++j) {
+                        const int cv = lane + 32 * j;
+                        if (cv < CG) {
+#pragma unroll
+                            for (int v = 0; v < V; ++v) dsum = fma(a[j][v], zin[cv * V + v], dsum);
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+                    u = dsum * tsc;
+                    if (lane == 0) {
+                        uo[row0 + rr] = u;
+                        su = fma((double)u, (double)u, su);
+                    }
+                } else {
+                    u = uin[row0 + rr];
+                }
+                if (AXPY) {
+#pragma unroll
+                    for (int j = 0; j < JV; ++j)
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[j][v] = fma(a[j][v], u, acc[j][v]);
+                }
+            }
+        }
+        if (!resident) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ring.empty[k]);   // this warp is done with the stage
+            ++qseq;
+        }
+    }
+    double sz = 0.0;
+    if (AXPY) {
+        // zo = (sum over warps of the accumulators) * sc, in warp order (deterministic)
+#pragma unroll
+        for (int j = 0; j < JV; ++j) {
+            const int cv = lane + 32 * j;
+            if (cv < CG) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) part[(int64_t)warp * n_cap + cv * V + v] = acc[j][v];
+            }
+        }
+        consumers_sync<NT>();
+        for (int col = threadIdx.x; col < n; col += NT) {
+            TC t = 0;
+            for (int w = 0; w < NW; ++w) t += part[(int64_t)w * n_cap + col];
+            t *= tsc;
+            zo[col] = t;
+            sz = fma((double)t, (double)t, sz);
+        }
+    }
+    sq_u = DOT ? consumer_sum<NT>(su, red) : 0.0;
+    sq_z = AXPY ? consumer_sum<NT>(sz, red) : 0.0;
+    return ok;
+}
+
+template <class TA, int NW, int JV>
+__global__ void __launch_bounds__((NW + 1) * 32, 1)
+batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, int count,
+            const TA* __restrict__ alo, const double* __restrict__ a64, const double* __restrict__ bvec,
+            double* __restrict__ xvec, BatchOut out, int32_t* queue, BatchParams P, int32_t* fail_flag) {
+    using TC = typename Elem<TA>::TC;
+    constexpr int NT = NW * 32;              // consumer threads
+    constexpr int NB = NT + 32;              // with the producer warp
+    __shared__ Shared S;
+    __shared__ double cred[NW];
+    __shared__ __align__(8) uint64_t full[kRing], empty[kRing], loaded;
+    __shared__ int fail_s;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TC* vec = reinterpret_cast<TC*>(smem_raw + P.area_bytes);
+    TC* r = vec;                                     // m_cap
+    TC* u = r + P.m_cap;                             // t_max x m_cap
+    TC* z = u + (int64_t)P.t_max * P.m_cap;          // t_max x n_cap
+    TC* dx = z + (int64_t)P.t_max * P.n_cap;         // n_cap
+    TC* part = dx + P.n_cap;                         // NW x n_cap
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool producer = warp == NW;
+    const Ring ring{smem_raw, full, empty};
+    if (tid == 0) {
+        for (int k = 0; k < kRing; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], NW);
+        }
+        mbar_init(&loaded, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fail_s = 0;
+    }
+    __syncthreads();
+    uint32_t qseq = 0, loaded_phase = 0;
+    for (;;) {
+        if (tid == 0) S.sys = atomicAdd(queue, 1);
+        __syncthreads();
+        const int q = S.sys;
+        if (q >= count) break;
+        if (fail_s) {   // this block stops; the system it took is reported as timed out
+            if (tid == 0) out.reason[order[q]] = TACTA_REASON_TIMEOUT;
+            break;
+        }
+        const SysDesc d = sys[order[q]];
+        const int m = d.m, n = d.n, ld = d.ld;
+        const double* b = bvec + d.b_off;
+        double* x = xvec + d.x_off;
+        const double* A64 = a64 + d.a64;
+        const TA* Ag = alo + d.a_lo;
+        const int64_t row_bytes = (int64_t)ld * (int64_t)sizeof(TA);
+        const int R = (int)max((int64_t)1, (int64_t)kChunkBytes / row_bytes);
+        const int nch = (m + R - 1) / R;
+        const bool resident = (int64_t)m * row_bytes <= P.area_bytes;
+        const TA* Ares = reinterpret_cast<const TA*>(smem_raw);
+        if (resident) {   // one copy of A_s into the area
+            if (tid == NT) {
+                const uint32_t bytes = (uint32_t)((int64_t)m * row_bytes);
+                mbar_expect_tx(&loaded, bytes);
+                bulk_g2s(smem_raw, Ag, bytes, &loaded);
+            }
+        }
+        for (int c = tid; c < n; c += NB) __stcg(x + c, 0.0);
+        for (int c = tid; c < P.n_cap; c += NB) dx[c] = 0;
+        for (int i = 0; i < P.t_max; ++i)
+            for (int c = tid; c < P.n_cap; c += NB) z[(int64_t)i * P.n_cap + c] = 0;
+        double bb = 0.0;
+        for (int i = tid; i < m; i += NB) {
+            r[i] = (TC)b[i];
+            bb = fma(b[i], b[i], bb);
+        }
+        if (resident) {
+            if (!mbar_wait_bounded(&loaded, loaded_phase)) fail_s = 1;
+            loaded_phase ^= 1u;
+        }
+        const double bn2 = block_sum2<NB>(bb, 0.0, S.red).x;
+        double nrm_thr = 0.0;
+        if (P.tol_n2 > 0.0 && bn2 > 0.0) {   // ||Aᵀb||² (from global memory, the slow path)
+            const double mt = prod_t<TA, NB>(Ag, m, n, ld, r, z, part, 1.0);
+            nrm_thr = P.tol_n2 * block_sum2<NB>(mt, 0.0, S.red).x;
+            for (int c = tid; c < n; c += NB) z[c] = 0;
+        }
+        double rn2 = bn2;
+        bool is_true = true, need_true = false;
+        int k = 0, reason = 0;
+        const double res_thr = P.tol2 * bn2;
+        double ref_thr = P.eta2 * bn2;
+        if (bn2 == 0.0) reason = TACTA_REASON_ZERO_RHS;
+        __syncthreads();
+        if (fail_s) reason = TACTA_REASON_TIMEOUT;
+        while (reason == 0) {
+            if (!finite_d(rn2)) { reason = TACTA_REASON_NONFINITE; break; }
+            if (rn2 <= res_thr) {
+                if (is_true) { reason = TACTA_REASON_RESIDUAL; break; }
+                need_true = true;
+            }
+            if (need_true) {
+                for (int c = tid; c < n; c += NB) {
+                    __stcg(x + c, __ldcg(x + c) + (double)dx[c]);
+                    dx[c] = 0;
+                }
+                __syncthreads();
+                const double2 rr = residual64<TC, NB>(A64, m, n, b, x, r);
+                rn2 = block_sum2<NB>(rr.x, 0.0, S.red).x;
+                is_true = true;
+                need_true = false;
+                ref_thr = P.eta2 * rn2;
+                continue;
+            }
+            if (k >= P.max_iter) { reason = TACTA_REASON_MAXITER; break; }
+            const int t = schedule_dev(k, P.t_max, P.cycle);
+            if (producer) {
+                if (!resident && lane == 0) {
+                    // the iteration's t + 1 passes, chunk by chunk, into the ring
+                    for (int pass = 0; pass <= t && !fail_s; ++pass) {
+                        for (int c = 0; c < nch; ++c) {
+                            const int kk = (int)(qseq % kRing);
+                            const uint32_t use = qseq / kRing;
+                            if (use > 0 && !mbar_wait_bounded(&empty[kk], (use - 1) & 1u)) {
+                                fail_s = 1;
+                                break;
+                            }
+                            const int row0 = c * R, rows = min(R, m - row0);
+                            const uint32_t bytes = (uint32_t)((int64_t)rows * row_bytes);
+                            mbar_expect_tx(&full[kk], bytes);
+                            bulk_g2s(smem_raw + (size_t)kk * kChunkBytes, Ag + (int64_t)row0 * ld, bytes, &full[kk]);
+                            ++qseq;
+                        }
+                    }
+                }
+                if (!resident) qseq = __shfl_sync(0xffffffffu, qseq, 0);
+            } else {
+                // z_1 = Aᵀ r / s ; then u_i = A z_i / s with z_{i+1} = Aᵀ u_i / s ; u_t alone
+                double pu = 0.0, pz = 0.0;
+                bool ok = fused_pass<TA, NW, JV, false, true>(Ares, resident, ring, qseq, m, n, ld, R, nch, P.n_cap,
+                                                             nullptr, r, nullptr, z, part, d.inv_s, cred, pu, pz);
+                if (tid == 0) S.phi[1] = pz;
+                for (int i = 1; i <= t && ok; ++i) {
+                    TC* zi = z + (int64_t)(i - 1) * P.n_cap;
+                    TC* ui = u + (int64_t)(i - 1) * P.m_cap;
+                    consumers_sync<NT>();   // z_i complete
+                    if (i < t) {
+                        ok = fused_pass<TA, NW, JV, true, true>(Ares, resident, ring, qseq, m, n, ld, R, nch, P.n_cap,
+                                                               zi, nullptr, ui, zi + P.n_cap, part, d.inv_s, cred, pu,
+                                                               pz);
+                        if (tid == 0) { S.phi[2 * i] = pu; S.phi[2 * i + 1] = pz; }
+                    } else {
+                        ok = fused_pass<TA, NW, JV, true, false>(Ares, resident, ring, qseq, m, n, ld, R, nch,
+                                                                P.n_cap, zi, nullptr, ui, nullptr, part, d.inv_s,
+                                                                cred, pu, pz);
+                        if (tid == 0) S.phi[2 * i] = pu;
+                    }
+                }
+                if (!ok) fail_s = 1;
+                if (tid == 0) {
+                    int st = 0;
+                    for (int i = 1; i <= 2 * t; ++i)
+                        if (!finite_d(S.phi[i])) st = TACTA_REASON_NONFINITE;
+                    if (st == 0 && S.phi[1] * d.s * d.s <= nrm_thr) st = TACTA_REASON_NORMAL;
+                    if (st == 0) {
+                        S.rank = hankel_solve_dev(S.phi, t, P.pivot_tol, S.beta);
+                        if (S.rank == 0) st = TACTA_REASON_BREAKDOWN;
+                    }
+                    S.stop = st;
+                }
+            }
+            __syncthreads();
+            if (fail_s) { reason = TACTA_REASON_TIMEOUT; break; }
+            if (S.stop) { reason = S.stop; break; }
+            TC bz[kTMax], bu[kTMax];
+            for (int j = 0; j < t; ++j) {
+                bu[j] = (TC)S.beta[j];
+                bz[j] = (TC)(S.beta[j] * d.inv_s);
+            }
+            for (int c = tid; c < n; c += NB) {
+                TC v = dx[c];
+                for (int j = 0; j < t; ++j) v = fma(bz[j], z[(int64_t)j * P.n_cap + c], v);
+                dx[c] = v;
+            }
+            double sq = 0.0;
+            for (int i = tid; i < m; i += NB) {
+                TC v = r[i];
+                for (int j = 0; j < t; ++j) v = fma(-bu[j], u[(int64_t)j * P.m_cap + i], v);
+                r[i] = v;
+                sq = fma((double)v, (double)v, sq);
+            }
+            rn2 = block_sum2<NB>(sq, 0.0, S.red).x;
+            ++k;
+            is_true = false;
+            if (P.R > 0 && k % P.R == 0) need_true = true;
+            else if (P.eta2 > 0.0 && rn2 <= ref_thr) need_true = true;
+        }
+        double rel = 0.0;
+        if (reason != TACTA_REASON_ZERO_RHS) {
+            for (int c = tid; c < n; c += NB) {
+                __stcg(x + c, __ldcg(x + c) + (double)dx[c]);
+                dx[c] = 0;
+            }
+            __syncthreads();
+            const double2 rr = residual64<TC, NB>(A64, m, n, b, x, r);
+            rel = sqrt(block_sum2<NB>(rr.x, 0.0, S.red).x / bn2);
+        }
+        if (tid == 0) {
+            out.iters[order[q]] = k;
+            out.reason[order[q]] = reason;
+            out.rel_res[order[q]] = rel;
+        }
+        __syncthreads();
+    }
+    if (fail_s && tid == NT) {
+        // a wait gave up: let the chunks still in flight land before the block exits
+        atomicExch(fail_flag, 1);
+        const uint32_t first = qseq > (uint32_t)kRing ? qseq - (uint32_t)kRing : 0u;
+        for (uint32_t qq = first; qq < qseq; ++qq) mbar_wait_bounded(&full[qq % kRing], (qq / kRing) & 1u);
+        mbar_wait_bounded(&loaded, loaded_phase ^ 1u);
+    }
+}
+
 // ------------------------------------------------------------------ setup kernels
 
 // low-precision copy with padded rows; one block per system
@@ -479,11 +848,14 @@ __global__ void chain_scale(SysDesc* sys, const double* __restrict__ a64) {
 // ------------------------------------------------------------------ launch configurations
 
 struct Config {
-    int nt;            // threads per block
+    int nt;            // threads per block (the streamed kernel: consumers, plus one producer warp)
     int per_sm;        // resident blocks per SM
+    bool streamed;     // batch_cta_s (fused passes, bulk-copy ring) instead of batch_cta
 };
-constexpr Config kConfigs[] = {{128, 2}, {128, 4}, {256, 1}, {256, 2}, {512, 1}};
+constexpr Config kConfigs[] = {{128, 2, false}, {128, 4, false}, {256, 1, false}, {256, 2, false}, {512, 1, false},
+                               {256, 1, true}};
 constexpr int kDefaultConfig = 3;
+constexpr int kStreamNW = 8, kStreamJV = 8;
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
 template <class TA>
@@ -502,6 +874,7 @@ void set_attrs(cudaError_t& attr) {
         if (attr == cudaSuccess)
             attr = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmemMax);
     };
+    set((const void*)batch_cta_s<TA, kStreamNW, kStreamJV>);
     set((const void*)batch_cta<TA, 128, 2>);
     set((const void*)batch_cta<TA, 128, 4>);
     set((const void*)batch_cta<TA, 256, 1>);
@@ -523,9 +896,13 @@ cudaError_t prepare_kernels() {
 template <class TA>
 cudaError_t launch_cfg(int cfg, cudaStream_t s, int grid, size_t smem, const SysDesc* sys, const int32_t* order,
                        int count, const void* alo, const double* a64, const double* b, double* x, BatchOut o,
-                       int32_t* queue, const BatchParams& P) {
+                       int32_t* queue, const BatchParams& P, int32_t* fail_flag) {
     const TA* a = reinterpret_cast<const TA*>(alo);
     switch (cfg) {
+    case 5:
+        batch_cta_s<TA, kStreamNW, kStreamJV><<<grid, kStreamNW * 32 + 32, smem, s>>>(sys, order, count, a, a64, b,
+                                                                                    x, o, queue, P, fail_flag);
+        break;
     case 0: batch_cta<TA, 128, 2><<<grid, 128, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
     case 1: batch_cta<TA, 128, 4><<<grid, 128, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
     case 2: batch_cta<TA, 256, 1><<<grid, 256, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
@@ -580,7 +957,12 @@ size_t elem_size(int storage) {
     return storage == TACTA_BATCH_FP64 ? 8 : storage == TACTA_BATCH_FP32 ? 4 : 2;
 }
 
-BatchParams make_params(const tacta_batch_s* B, const tacta_options& o, int nt, int per_sm, size_t* smem_out) {
+template <class TA>
+int chain_size() { return (int)sizeof(typename Elem<TA>::TC); }
+
+// launch parameters of configuration cfg; false when it cannot run this batch
+bool make_params(const tacta_batch_s* B, const tacta_options& o, int cfg, BatchParams* out, size_t* smem_out) {
+    const Config C = kConfigs[cfg];
     BatchParams P{};
     P.tol2 = o.tol * o.tol;
     P.tol_n2 = o.tol_normal > 0.0 ? o.tol_normal * o.tol_normal : 0.0;
@@ -592,40 +974,52 @@ BatchParams make_params(const tacta_batch_s* B, const tacta_options& o, int nt, 
     P.cycle = o.cycle;
     P.m_cap = B->m_max;
     P.n_cap = (B->n_max + 7) & ~7;
-    size_t vb = 0;
-    switch (B->storage) {
-    case TACTA_BATCH_FP64: vb = vec_bytes<double>(P, nt); break;
-    case TACTA_BATCH_FP32: vb = vec_bytes<float>(P, nt); break;
-    default: vb = vec_bytes<__nv_bfloat16>(P, nt); break;
-    }
+    const int V = B->storage == TACTA_BATCH_FP64 ? 2 : B->storage == TACTA_BATCH_FP32 ? 4 : 8;
+    const int tc = B->storage == TACTA_BATCH_FP64 ? 8 : 4;
     // shared memory per block: what per_sm blocks can share of the SM's 228 KB
-    // (1 KB per block reserved, the static Shared block), the vectors first
-    const int64_t per_block = std::min<int64_t>(kBatchSmemMax, (228 * 1024) / per_sm - 1024 - 2048);
-    const int64_t a_bytes = std::max<int64_t>(0, per_block - (int64_t)vb - 16);
-    P.a_cap = (a_bytes / 16) * 16 / (int64_t)elem_size(B->storage);
-    *smem_out = (size_t)(((P.a_cap * (int64_t)elem_size(B->storage) + 15) & ~15) + (int64_t)vb);
-    return P;
+    // (1 KB per block reserved, the static shared block and slack)
+    const int64_t per_block = std::min<int64_t>(kBatchSmemMax, (228 * 1024) / C.per_sm - 1024 - 2048);
+    const int64_t chain = ((int64_t)P.m_cap + P.n_cap) * (1 + P.t_max);
+    if (!C.streamed) {
+        const int64_t vb = (chain + (int64_t)C.nt * V) * tc;
+        const int64_t a_bytes = std::max<int64_t>(0, per_block - vb - 16);
+        P.a_cap = (a_bytes / 16) * 16 / (int64_t)elem_size(B->storage);
+        P.area_bytes = 0;
+        *smem_out = (size_t)(((P.a_cap * (int64_t)elem_size(B->storage) + 15) & ~15) + vb);
+    } else {
+        if (P.n_cap / V > 32 * kStreamJV) return false;          // row slices must fit the registers
+        const int64_t part = std::max<int64_t>((int64_t)kStreamNW * P.n_cap, (int64_t)(C.nt + 32) * V);
+        const int64_t vb = (chain + part) * tc;
+        const int64_t area = ((per_block - vb) / 16) * 16;
+        if (area < (int64_t)kRing * kChunkBytes) return false;
+        P.area_bytes = area;
+        P.a_cap = 0;
+        *smem_out = (size_t)(area + vb);
+    }
+    if ((int64_t)*smem_out > kBatchSmemMax) return false;
+    *out = P;
+    return true;
 }
 
 cudaError_t launch_batch(tacta_batch_s* B, cudaStream_t s, const tacta_options& o, int cfg) {
     const Config C = kConfigs[cfg];
     size_t smem = 0;
-    BatchParams P = make_params(B, o, C.nt, C.per_sm, &smem);
-    if ((int64_t)smem > kBatchSmemMax) return cudaErrorInvalidConfiguration;
+    BatchParams P{};
+    if (!make_params(B, o, cfg, &P, &smem)) return cudaErrorInvalidConfiguration;
     const int grid = std::max(1, std::min(B->count, B->sms * C.per_sm));
     BatchOut out{B->iters, B->reason, B->rel};
-    cudaError_t e = cudaMemsetAsync(B->queue, 0, sizeof(int32_t), s);
+    cudaError_t e = cudaMemsetAsync(B->queue, 0, 2 * sizeof(int32_t), s);   // queue head, timeout flag
     if (e != cudaSuccess) return e;
     switch (B->storage) {
     case TACTA_BATCH_FP64:
         return launch_cfg<double>(cfg, s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x, out,
-                                  B->queue, P);
+                                  B->queue, P, B->queue + 1);
     case TACTA_BATCH_FP32:
         return launch_cfg<float>(cfg, s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x, out,
-                                 B->queue, P);
+                                 B->queue, P, B->queue + 1);
     default:
         return launch_cfg<__nv_bfloat16>(cfg, s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x,
-                                         out, B->queue, P);
+                                         out, B->queue, P, B->queue + 1);
     }
 }
 
@@ -725,7 +1119,7 @@ extern "C" tacta_status tacta_batch_create(int32_t count, const int32_t* m, cons
     BCHK(cudaMalloc(&B->iters, sizeof(int32_t) * std::max<int32_t>(count, 1)));
     BCHK(cudaMalloc(&B->reason, sizeof(int32_t) * std::max<int32_t>(count, 1)));
     BCHK(cudaMalloc(&B->rel, sizeof(double) * std::max<int32_t>(count, 1)));
-    BCHK(cudaMalloc(&B->queue, sizeof(int32_t)));
+    BCHK(cudaMalloc(&B->queue, 2 * sizeof(int32_t)));
     if (count > 0) {
         // largest systems first: the queue's tail is then made of short jobs
         std::vector<int32_t> ord((size_t)count);
@@ -770,7 +1164,7 @@ extern "C" int32_t tacta_batch_num_configs(void) { return kNumConfigs; }
 
 extern "C" tacta_status tacta_batch_config_shape(int32_t config, int32_t* threads, int32_t* blocks_per_sm) {
     if (config < 0 || config >= kNumConfigs || !threads || !blocks_per_sm) return TACTA_ERR_INVALID;
-    *threads = kConfigs[config].nt;
+    *threads = kConfigs[config].nt + (kConfigs[config].streamed ? 32 : 0);
     *blocks_per_sm = kConfigs[config].per_sm;
     return TACTA_OK;
 }
@@ -786,19 +1180,18 @@ extern "C" tacta_status tacta_batch_cta(tacta_batch B, const double* b, double* 
     if (B->count == 0) return TACTA_OK;
     cudaStream_t s = (cudaStream_t)o.stream;
     const int cfg = B->config >= 0 ? B->config : kDefaultConfig;
+    BatchParams P{};
     {
         size_t smem = 0;
-        make_params(B, o, kConfigs[cfg].nt, kConfigs[cfg].per_sm, &smem);
-        if ((int64_t)smem > kBatchSmemMax) {
-            g_batch_err = "the largest system's vectors exceed shared memory: lower t_max or solve it with a plan";
+        if (!make_params(B, o, cfg, &P, &smem)) {
+            g_batch_err = "the largest system does not fit this launch configuration's shared memory: "
+                          "lower t_max, pick another configuration, or solve it with a plan";
             return TACTA_ERR_INVALID;
         }
     }
     BTRY(cudaMemcpyAsync(B->b, b, sizeof(double) * B->b_len, cudaMemcpyDefault, s));
     if (o.use_graph) {
         // the solve is a queue reset and one persistent launch: replay it as a graph
-        size_t smem = 0;
-        const BatchParams P = make_params(B, o, kConfigs[cfg].nt, kConfigs[cfg].per_sm, &smem);
         if (!B->graph || B->graph_key != cfg || std::memcmp(&P, &B->graph_params, sizeof(P)) != 0) {
             if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
             cudaStream_t cs;
@@ -825,7 +1218,13 @@ extern "C" tacta_status tacta_batch_cta(tacta_batch B, const double* b, double* 
     if (iters) BTRY(cudaMemcpyAsync(iters, B->iters, sizeof(int32_t) * B->count, cudaMemcpyDefault, s));
     if (rel_res) BTRY(cudaMemcpyAsync(rel_res, B->rel, sizeof(double) * B->count, cudaMemcpyDefault, s));
     if (reason) BTRY(cudaMemcpyAsync(reason, B->reason, sizeof(int32_t) * B->count, cudaMemcpyDefault, s));
+    int32_t timed_out = 0;
+    BTRY(cudaMemcpyAsync(&timed_out, B->queue + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     BTRY(cudaStreamSynchronize(s));
+    if (timed_out) {
+        g_batch_err = "a wait in the batched kernel gave up (systems reported with reason TIMEOUT)";
+        return TACTA_ERR_TIMEOUT;
+    }
     return TACTA_OK;
 }
 
@@ -848,8 +1247,8 @@ extern "C" tacta_status tacta_batch_tune(tacta_batch B, const double* b, const t
     float best_t = 0.0f;
     for (int c = 0; c < kNumConfigs; ++c) {
         size_t smem = 0;
-        make_params(B, o, kConfigs[c].nt, kConfigs[c].per_sm, &smem);
-        if ((int64_t)smem > kBatchSmemMax) continue;
+        BatchParams P{};
+        if (!make_params(B, o, c, &P, &smem)) continue;
         float tc = 0.0f;
         bool ok = true;
         for (int rep = 0; rep < 2 && ok; ++rep) {      // the first run warms caches and loads the module

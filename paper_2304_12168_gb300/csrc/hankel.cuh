@@ -91,7 +91,7 @@ static __host__ __device__ __forceinline__ int hankel_solve_t(const double* phi_
     return rank;
 }
 
-static __host__ __device__ int hankel_solve_dev(const double* phi, int t, double pivot_tol, double* alpha) {
+static __host__ __device__ __noinline__ int hankel_solve_dev(const double* phi, int t, double pivot_tol, double* alpha) {
     switch (t) {
     case 1: return hankel_solve_t<1>(phi, pivot_tol, alpha);
     case 2: return hankel_solve_t<2>(phi, pivot_tol, alpha);

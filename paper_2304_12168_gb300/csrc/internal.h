@@ -58,7 +58,7 @@ enum Finisher : int {
     FIN_NONE = 0,
     FIN_STORE = 1,        // red[0..1] -> ctl->red[idx], ctl->red[idx+1]
     FIN_PHI = 2,          // r0 -> phi[idx]
-    FIN_CTA_STEP = 3,     // r0 -> phi[2t]; normal test; auxiliary solve -> alpha
+    FIN_UNUSED_3 = 3,
     FIN_CTA_UPDATE = 4,   // r0 = ||r||²: k++, history, R-gate, loop-top tests
     FIN_TRUE_RES = 5,     // r0 = ||r||² (r1 = rᵀb): is_true, history, loop-top tests
     FIN_TA_C = 6,         // r0 = ||c||²: normal test, pivot test, rho growth / witness
@@ -72,7 +72,7 @@ enum Finisher : int {
 
 struct FinArgs {
     int kind;
-    int idx;              // FIN_PHI / FIN_STORE slot, FIN_CTA_STEP: t
+    int idx;              // FIN_PHI / FIN_STORE slot
     double* hist;         // device history buffer (capacity ctl->hist_cap)
 };
 
@@ -195,7 +195,8 @@ cudaError_t launch_reduce_vec(const LaunchCtx& L, int64_t len, const double* a, 
 cudaError_t launch_ctl_init(const LaunchCtx& L, const Ctl& host_init);
 cudaError_t launch_copy_gated(const LaunchCtx& L, double* dst, const double* src, int64_t len, int gate);
 cudaError_t launch_fill(const LaunchCtx& L, double* dst, double v, int64_t len);
-cudaError_t launch_hist_sqrt(cudaStream_t s, double* h, int64_t len);   // ||r||²/||b||² -> ||r||/||b||
+cudaError_t launch_hist_sqrt(cudaStream_t s, double* h, int64_t len);
+cudaError_t launch_cta_aux_step(const LaunchCtx& L, int t);   // CTA step decision + auxiliary solve   // ||r||²/||b||² -> ||r||/||b||
 
 // mixed precision (FP32 chain, FP64 refinement)
 cudaError_t launch_spmv32(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y, float scale,
@@ -217,6 +218,10 @@ cudaError_t csr_validate(cudaStream_t s, const int32_t* rowptr, const int32_t* c
                          int64_t n, int64_t nnz, int* flag_dev, int* flag_host);
 cudaError_t csr_transpose(cudaStream_t s, const DevCSR& A, DevCSR& T);
 cudaError_t dense_transpose(cudaStream_t s, const double* A, int64_t rows, int64_t cols, double* T);
+// run-staged layout of fixed kTileRows-row tiles built on the device (stats: 4 int32 on
+// the device; [0] failure bits, [1] max nonzeros per tile, [2] max window span)
+cudaError_t run_tiles_build(cudaStream_t s, const DevCSR& a, int4* tiles, int2* xwin, int2* runs, uint16_t* lcol,
+                            int32_t* stats);
 
 // ---------------------------------------------------------------- errors
 void set_error(const std::string& msg);

@@ -27,6 +27,7 @@
 
 #include "internal.h"
 #include "hankel.cuh"
+#include "mbarrier.cuh"
 
 namespace tacta {
 
@@ -84,16 +85,6 @@ __device__ __noinline__ void finish(Ctl* c, const FinArgs& f, double r0, double 
     case FIN_PHI:
         c->phi[f.idx] = r0;
         break;
-    case FIN_CTA_STEP: {
-        const int t = f.idx;
-        c->phi[2 * t] = r0;
-        for (int i = 1; i <= 2 * t; ++i)
-            if (!finite(c->phi[i])) { c->status = TACTA_REASON_NONFINITE; return; }
-        if (c->phi[1] <= __dmul_rn(c->nrm_thr, c->cs2)) { c->status = TACTA_REASON_NORMAL; return; }
-        c->rank = hankel_solve_dev(c->phi, t, c->pivot_tol, c->alpha);
-        if (c->rank == 0) c->status = TACTA_REASON_BREAKDOWN;
-        break;
-    }
     case FIN_CTA_UPDATE:
         c->k += 1;
         c->is_true = 0;
@@ -349,48 +340,6 @@ spmv_warp(Acc A, const double* __restrict__ x, double* __restrict__ y, EpiArgs e
 // gathering x through the read-only path. Bulk copies start on 16-byte
 // boundaries: each window is rounded outwards and the padded CSR arrays
 // (kPad*) keep the rounded end inside the allocation.
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// bounded wait: gives up after ~2^31 SM cycles (about a second)
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > (1LL << 31)) return false;
-    }
-    return true;
-}
 
 template <int CAP>
 struct __align__(16) TileStage {
@@ -805,9 +754,6 @@ static cudaError_t spmv_tiled_r_launch(const LaunchCtx& L, const DevCSR& A, cons
 constexpr int kRwConsumers = kTileRows / 32;
 constexpr int kRwThreads = (kRwConsumers + 1) * 32;
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
 
 template <int S> constexpr int rw_blocks_per_sm() { return S == 2 ? 4 : 3; }
 
@@ -1527,6 +1473,26 @@ cudaError_t launch_ctl_init(const LaunchCtx& L, const Ctl& host_init) {
 cudaError_t launch_copy_gated(const LaunchCtx& L, double* dst, const double* src, int64_t len,
                               int gate) {
     copy_gated<<<L.max_grid, kBlock, 0, L.stream>>>(dst, src, len, L.ctl, gate);
+    if (L.launches) ++*L.launches;
+    return cudaGetLastError();
+}
+
+// CTA step decision (Alg. 1.1 with Eq. eqcoeff), one thread, after the chain's last
+// product: finite moments, the normal-equation test, the auxiliary solve -> alpha. It is
+// its own kernel so that the solve's registers (its arrays live in registers) do not
+// count against the occupancy of every product and update kernel, as they would if it
+// ran inside their shared finisher.
+__global__ void cta_aux_step(Ctl* c, int t) {
+    if (threadIdx.x != 0 || c->status != 0) return;
+    for (int i = 1; i <= 2 * t; ++i)
+        if (!finite(c->phi[i])) { c->status = TACTA_REASON_NONFINITE; return; }
+    if (c->phi[1] <= __dmul_rn(c->nrm_thr, c->cs2)) { c->status = TACTA_REASON_NORMAL; return; }
+    c->rank = hankel_solve_dev(c->phi, t, c->pivot_tol, c->alpha);
+    if (c->rank == 0) c->status = TACTA_REASON_BREAKDOWN;
+}
+
+cudaError_t launch_cta_aux_step(const LaunchCtx& L, int t) {
+    cta_aux_step<<<1, 32, 0, L.stream>>>(L.ctl, t);
     if (L.launches) ++*L.launches;
     return cudaGetLastError();
 }

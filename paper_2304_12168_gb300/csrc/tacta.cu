@@ -232,10 +232,45 @@ static bool build_runs(const std::vector<int4>& tiles, const std::vector<int2>& 
     return true;
 }
 
+// Device-built run-staged layout (fixed 256-row tiles): true when every tile fits the
+// run-staged product; otherwise nothing is kept and the host path decides.
+static bool setup_run_tiles_device(DevCSR& a, cudaStream_t s, cudaError_t* err) {
+    const int64_t ntiles = (a.rows + kTileRows - 1) / kTileRows;
+    int32_t* stats = nullptr;
+    int32_t h[4] = {0, 0, 0, 0};
+    auto fail = [&](cudaError_t e) {
+        cudaFree(a.tiles); cudaFree(a.xwin); cudaFree(a.runs); cudaFree(a.lcol); cudaFree(stats);
+        a.tiles = nullptr; a.xwin = nullptr; a.runs = nullptr; a.lcol = nullptr;
+        *err = e;
+        return false;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&a.tiles, sizeof(int4) * ntiles)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&a.xwin, sizeof(int2) * ntiles)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&a.runs, sizeof(int2) * kRunMax * ntiles)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&a.lcol, sizeof(uint16_t) * (a.nnz + kPadLcol))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&stats, sizeof(int32_t) * 4)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemsetAsync(a.lcol, 0, sizeof(uint16_t) * (a.nnz + kPadLcol), s)) != cudaSuccess) return fail(e);
+    if ((e = run_tiles_build(s, a, a.tiles, a.xwin, a.runs, a.lcol, stats)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(h, stats, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e);
+    if (h[0] != 0 || h[1] > kRunCap || h[2] > kXSpan) return fail(cudaSuccess);
+    cudaFree(stats);
+    a.ntiles = (int)ntiles;
+    a.cap = (h[1] <= kXCapCompactPlan && h[2] <= kXSpanCompactPlan) ? kXCapCompactPlan : kTileCapSmall;
+    a.cfg.kind = 3;
+    return true;
+}
+
 static cudaError_t setup_csr_kernel(DevCSR& a, cudaStream_t s) {
     const double avg = a.rows > 0 ? (double)a.nnz / (double)a.rows : 0.0;
     a.cfg.kind = 1;
     if (avg >= 64.0) return cudaSuccess;
+    if (a.nnz > 0 && avg * kTileRows <= (double)kRunCap) {
+        cudaError_t e = cudaSuccess;
+        if (setup_run_tiles_device(a, s, &e)) return spmv_tiled_prepare();
+        if (e != cudaSuccess) return e;
+    }
     std::vector<int32_t> rp((size_t)a.rows + 1);
     cudaError_t e = cudaMemcpyAsync(rp.data(), a.rowptr, sizeof(int32_t) * (a.rows + 1), cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return e;
@@ -523,10 +558,11 @@ static cudaError_t enqueue_cta32_iter(Plan* p, const LaunchCtx& L, int t) {
     for (int i = 0; i < t; ++i) {
         if ((e = chain_spmv32(p, L, p->At32, uprev, p->z32[i], FinArgs{FIN_PHI, 2 * i + 1, nullptr})) != cudaSuccess)
             return e;
-        FinArgs f = (i == t - 1) ? FinArgs{FIN_CTA_STEP, t, nullptr} : FinArgs{FIN_PHI, 2 * i + 2, nullptr};
-        if ((e = chain_spmv32(p, L, p->A32, p->z32[i], p->u32[i], f)) != cudaSuccess) return e;
+        if ((e = chain_spmv32(p, L, p->A32, p->z32[i], p->u32[i], FinArgs{FIN_PHI, 2 * i + 2, nullptr})) !=
+            cudaSuccess) return e;
         uprev = p->u32[i];
     }
+    if ((e = launch_cta_aux_step(L, t)) != cudaSuccess) return e;
     if ((e = launch_cta_update32(L, t, p->m, p->n, p->dx32, p->r32, p->z32, p->u32, p->chain_scale,
                                  FinArgs{FIN_CTA_UPDATE, 0, p->hist})) != cudaSuccess) return e;
     if ((e = launch_fold_correction(L, p->n, p->x, p->dx32, GATE_NEED_TRUE)) != cudaSuccess) return e;
@@ -576,10 +612,11 @@ static cudaError_t enqueue_cta_iter(Plan* p, const LaunchCtx& L, int t) {
     for (int i = 0; i < t; ++i) {
         if ((e = chain_spmv(p, L, p->At, uprev, p->z[i], EPI_NORM, none, FinArgs{FIN_PHI, 2 * i + 1, nullptr},
                             GATE_ALWAYS)) != cudaSuccess) return e;
-        FinArgs f = (i == t - 1) ? FinArgs{FIN_CTA_STEP, t, nullptr} : FinArgs{FIN_PHI, 2 * i + 2, nullptr};
-        if ((e = chain_spmv(p, L, p->A, p->z[i], p->u[i], EPI_NORM, none, f, GATE_ALWAYS)) != cudaSuccess) return e;
+        if ((e = chain_spmv(p, L, p->A, p->z[i], p->u[i], EPI_NORM, none, FinArgs{FIN_PHI, 2 * i + 2, nullptr},
+                            GATE_ALWAYS)) != cudaSuccess) return e;
         uprev = p->u[i];
     }
+    if ((e = launch_cta_aux_step(L, t)) != cudaSuccess) return e;
     if ((e = launch_cta_update(L, t, p->m, p->n, p->x, p->r, p->z, p->u,
                                FinArgs{FIN_CTA_UPDATE, 0, p->hist})) != cudaSuccess) return e;
     return launch_spmv(L, p->A, p->x, p->r, EPI_RESID, EpiArgs{p->b, nullptr, nullptr},

@@ -10,6 +10,8 @@
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
+#include <climits>
+
 #include "internal.h"
 
 namespace tacta {
@@ -88,7 +90,112 @@ inline int blocks_for(int64_t n) {
     return (int)b;
 }
 
+// Run-staged layout of fixed 256-row tiles, one block per tile (plan time). Per
+// tile: row range and nonzero range, the window [lo, hi] of columns, the runs of
+// used columns (a gap of more than kRunGap columns starts a new run; each run starts
+// on an even column and has an even length) and each nonzero's 16-bit slot in the
+// runs laid end to end. stats: [0] failure bits (1: a tile holds more than kRunCap
+// nonzeros, 2: its window spans more than kXSpan columns, 4: more than kRunMax
+// runs, 8: more than kRunXs staged entries), [1] max nonzeros of a tile, [2] max
+// window span.
+__global__ void __launch_bounds__(kTileRows)
+run_tiles(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, int64_t rows, int4* tiles,
+          int2* xwin, int2* runs, uint16_t* lcol, int32_t* stats) {
+    constexpr int kWords = (kXSpan + 31) / 32;
+    __shared__ uint32_t used[kWords];
+    __shared__ int lo_s, hi_s, fail_s, nrun_s;
+    __shared__ int2 rr[kRunMax];
+    const int t = blockIdx.x, tid = threadIdx.x;
+    const int64_t r0 = (int64_t)t * kTileRows, r1 = min(rows, r0 + kTileRows);
+    const int z = rowptr[r0], w = rowptr[r1];
+    if (tid == 0) {
+        lo_s = INT_MAX;
+        hi_s = -1;
+        fail_s = 0;
+        nrun_s = 0;
+        tiles[t] = make_int4((int)r0, (int)r1, z, w);
+    }
+    for (int i = tid; i < kWords; i += blockDim.x) used[i] = 0u;
+    __syncthreads();
+    int lo = INT_MAX, hi = -1;
+    for (int k = z + tid; k < w; k += blockDim.x) {
+        const int c = colidx[k];
+        lo = min(lo, c);
+        hi = max(hi, c);
+    }
+    atomicMin(&lo_s, lo);
+    atomicMax(&hi_s, hi);
+    __syncthreads();
+    const int wlo = hi_s < 0 ? 0 : lo_s, whi = hi_s < 0 ? 0 : hi_s;
+    const int span = whi - (wlo & ~1) + 1;
+    if (tid == 0) {
+        xwin[t] = make_int2(wlo, whi);
+        atomicMax(&stats[1], w - z);
+        atomicMax(&stats[2], span);
+        if (w - z > kRunCap) fail_s |= 1;
+        if (whi - wlo + 1 > kXSpan) fail_s |= 2;
+    }
+    __syncthreads();
+    if (fail_s) {
+        if (tid == 0) atomicOr(&stats[0], fail_s);
+        return;
+    }
+    for (int k = z + tid; k < w; k += blockDim.x) {
+        const int c = colidx[k] - wlo;
+        atomicOr(&used[c >> 5], 1u << (c & 31));
+    }
+    __syncthreads();
+    if (tid == 0 && w > z) {
+        // runs, scanning the window's bitmap in column order
+        int nrun = 0, total = 0, first = -1, last = -1, f = 0;
+        auto close = [&]() {
+            if (nrun == kRunMax) { f |= 4; return; }
+            const int c0 = (wlo + first) & ~1;
+            const int len = (wlo + last + 1 - c0 + 1) & ~1;
+            rr[nrun++] = make_int2(c0, len);
+            total += len;
+            if (total > kRunXs) f |= 8;
+        };
+        const int width = whi - wlo + 1;
+        for (int wd = 0; wd * 32 < width && !f; ++wd) {
+            uint32_t bits = used[wd];
+            while (bits && !f) {
+                const int c = wd * 32 + __ffs(bits) - 1;
+                bits &= bits - 1;
+                if (first >= 0 && c - last > kRunGap) {
+                    close();
+                    first = -1;
+                }
+                if (first < 0) first = c;
+                last = c;
+            }
+        }
+        if (!f) close();
+        nrun_s = nrun;
+        fail_s = f;
+        if (f) atomicOr(&stats[0], f);
+    }
+    __syncthreads();
+    if (fail_s) return;
+    if (tid < kRunMax) runs[(size_t)t * kRunMax + tid] = tid < nrun_s ? rr[tid] : make_int2(0, 0);
+    for (int k = z + tid; k < w; k += blockDim.x) {
+        const int c = colidx[k];
+        int off = 0, r = 0;
+        while (r + 1 < nrun_s && c >= rr[r].x + rr[r].y) off += rr[r++].y;
+        lcol[k] = (uint16_t)(off + c - rr[r].x);
+    }
+}
+
 }  // namespace
+
+cudaError_t run_tiles_build(cudaStream_t s, const DevCSR& a, int4* tiles, int2* xwin, int2* runs, uint16_t* lcol,
+                            int32_t* stats) {
+    const int ntiles = (int)((a.rows + kTileRows - 1) / kTileRows);
+    cudaError_t e = cudaMemsetAsync(stats, 0, sizeof(int32_t) * 4, s);
+    if (e != cudaSuccess || ntiles == 0) return e;
+    run_tiles<<<ntiles, kTileRows, 0, s>>>(a.rowptr, a.colidx, a.rows, tiles, xwin, runs, lcol, stats);
+    return cudaGetLastError();
+}
 
 cudaError_t csr_validate(cudaStream_t s, const int32_t* rowptr, const int32_t* colidx, int64_t m,
                          int64_t n, int64_t nnz, int* flag_dev, int* flag_host) {

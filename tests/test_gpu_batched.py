@@ -53,20 +53,27 @@ def problem(A, b):
                        dense=np.ascontiguousarray(A), b=b)
 
 
-def run(tacta, mats, bs, storage, **opts):
+STREAMED = 5   # launch configuration of the fused-pass kernel with the bulk-copy ring
+
+
+def run(tacta, mats, bs, storage, config=None, **opts):
     B = tacta.Batch(mats, storage=storage)
+    if config is not None:
+        B.set_config(config)
     x, iters, rel, reason = B.cta(np.concatenate(bs), **opts)
     xs = B.split(x)
     B.close()
     return xs, iters, rel, reason
 
 
-def test_fp64_fixed_trajectories_match_oracle(tacta):
+@pytest.mark.parametrize("config", [None, STREAMED])
+def test_fp64_fixed_trajectories_match_oracle(tacta, config):
     """Four steps (t = 1..4) per system, FP64 storage: x, iteration and product counts of
-    every system against the oracle's run on that system alone."""
+    every system against the oracle's run on that system alone; the default kernel and
+    the fused-pass kernel (whose largest systems here stream through the ring)."""
     mats, bs, _ = small_batch(1, 40)
     opts = dict(tol=1e-30, tol_normal=0.0, max_iter=4)
-    xs, iters, rel, reason = run(tacta, mats, bs, tacta.BATCH_FP64, **opts)
+    xs, iters, rel, reason = run(tacta, mats, bs, tacta.BATCH_FP64, config=config, **opts)
     for s, (A, b) in enumerate(zip(mats, bs)):
         ref = oracle.cta_solve(oracle.make_operator(problem(A, b)), b, **opts)
         assert iters[s] == ref.iters, s
@@ -75,16 +82,20 @@ def test_fp64_fixed_trajectories_match_oracle(tacta):
         assert tacta.REASON[int(reason[s])] == "MAXITER"
 
 
+@pytest.mark.parametrize("config", [None, STREAMED])
 @pytest.mark.parametrize("storage,tol,xtol", [("BATCH_FP64", 1e-10, 1e-8), ("BATCH_FP32", 1e-8, 1e-6),
                                               ("BATCH_BF16", 1e-8, 3e-2)])
-def test_to_tolerance_min_norm(tacta, storage, tol, xtol):
+def test_to_tolerance_min_norm(tacta, storage, tol, xtol, config):
     """Well-conditioned systems (n/m in [1.4, 2] or its inverse; every fifth of rank m/2):
     the host-recomputed FP64 residual meets tol, the reported one equals it, and x is the
     minimum-norm solution within cond(A) times xtol: about 100 tol for FP64, and for the
     low-precision copies 10 times their unit roundoff (2^-24, 2^-9) plus the tolerance."""
     mats, bs, lr = small_batch(2, 48, aspect=(1.4, 2.0))
-    xs, iters, rel, reason = run(tacta, mats, bs, getattr(tacta, storage), tol=tol, tol_normal=0.0,
-                                 max_iter=20000)
+    if config == STREAMED:   # add systems larger than the shared-memory area: they stream
+        m2, b2, _ = small_batch(6, 12, m_range=(220, 300), aspect=(1.4, 1.8))
+        mats, bs = mats + m2, bs + b2
+    xs, iters, rel, reason = run(tacta, mats, bs, getattr(tacta, storage), config=config, tol=tol,
+                                 tol_normal=0.0, max_iter=20000)
     for s, (A, b) in enumerate(zip(mats, bs)):
         assert tacta.REASON[int(reason[s])] == "RESIDUAL", (s, reason[s], rel[s])
         r = np.linalg.norm(b - A @ xs[s]) / np.linalg.norm(b)
