@@ -43,8 +43,11 @@ class CTASolveFn(torch.autograd.Function):
         m, n = ctx.shape
         plan = ctx.plan
         opts = dict(ctx.opts)
-        # the adjoint systems are least-squares problems: stop on the normal-equation test too
-        opts.setdefault("tol_normal", opts.get("tol", 1e-10))
+        # the adjoint systems are least-squares problems (Aᵀ lambda = g has no exact solution
+        # unless g is in range(Aᵀ)): their stop is the normal-equation test, at the forward
+        # tolerance unless a positive one was given
+        if not opts.get("tol_normal", 0.0) or opts["tol_normal"] <= 0.0:
+            opts["tol_normal"] = opts.get("tol", 1e-10)
         pt = plan.transpose()
         try:
             lam, _, _ = pt.cta(g.contiguous(), **opts)
