@@ -120,7 +120,7 @@ struct DevCSR {          // CSR operand in device memory (rows x cols)
     int2* xwin = nullptr;        // kind 3: per tile {first column, last column} of its x window
     // kind 3 operands whose tiles draw on at most kRunMax short runs of x also carry:
     uint16_t* lcol = nullptr;    // per nonzero: its column's slot in the tile's staged runs (nnz + kPadLcol)
-    int2* runs = nullptr;        // per tile kRunMax {first column (even), length (even; 0 = unused)}
+    int2* runs = nullptr;        // per tile kRunMax {first column, length} (multiples of 4; length 0 = unused)
     SpmvCfg cfg{};
 };
 
@@ -144,7 +144,7 @@ constexpr double kRefineEta2 = 1e-6;
 constexpr int32_t kBatchMaxDim = 4096;
 // every plan vector that can be a product's input carries this many doubles of
 // padding, so 16-byte-rounded x-window copies stay inside the allocation
-constexpr int kPadVec = 2;
+constexpr int kPadVec = 4;
 
 // padding (elements) after each CSR array so that 16-byte-rounded bulk copies
 // of a tile window never leave the allocation

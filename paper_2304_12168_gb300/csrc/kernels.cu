@@ -625,14 +625,16 @@ static cudaError_t spmv_tiled_x_launch(const LaunchCtx& L, const DevCSR& A, cons
 // runs: 10 bytes per nonzero from HBM instead of 12.
 
 struct __align__(16) TileStageR {
+    int4 desc;                       // the tile's descriptor (written by the producer)
     double vals[kRunCap + 2];
     uint16_t lcol[kRunCap + kPadLcol];
     int32_t rp[kTileRows + 8];
     double xs[kRunXs];
 };
 static_assert(sizeof(TileStageR) % 16 == 0, "stage size keeps 16-byte alignment");
-static_assert(offsetof(TileStageR, lcol) % 16 == 0 && offsetof(TileStageR, rp) % 16 == 0 &&
-              offsetof(TileStageR, xs) % 16 == 0, "bulk-copy destinations are 16-byte aligned");
+static_assert(offsetof(TileStageR, vals) % 16 == 0 && offsetof(TileStageR, lcol) % 16 == 0 &&
+              offsetof(TileStageR, rp) % 16 == 0 && offsetof(TileStageR, xs) % 16 == 0,
+              "bulk-copy destinations are 16-byte aligned");
 constexpr int kRunBlocksPerSM = 5;
 static int g_run_resident = kRunBlocksPerSM;   // blocks per SM the device actually fits
 
@@ -648,7 +650,7 @@ __device__ __forceinline__ void tile_issue_r(const int4 d, const int2* __restric
 #pragma unroll
     for (int k = 0; k < kRunMax; ++k) {
         rr[k] = __ldg(runs + k);
-        bx += (uint32_t)rr[k].y * 8u;       // even lengths: multiples of 16 bytes
+        bx += (uint32_t)rr[k].y * 8u;       // lengths are multiples of 4: 16-byte multiples
     }
     mbar_expect_tx(bar, bv + bc + br + bx);
     if (bv) bulk_g2s(st->vals, vals + a0, bv, bar);
@@ -795,7 +797,9 @@ spmv_tiled_rw(const int4* __restrict__ tiles, const int2* __restrict__ runs, int
                     atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
                     break;
                 }
-                tile_issue_r(__ldg(tiles + t), runs + (size_t)t * kRunMax, st + k, &full[k], rowptr, lcol, vals, x);
+                const int4 d = __ldg(tiles + t);
+                st[k].desc = d;   // visible to the consumers through the stage's mbarrier (release/acquire)
+                tile_issue_r(d, runs + (size_t)t * kRunMax, st + k, &full[k], rowptr, lcol, vals, x);
                 last_use[k] = u;
             }
         }
@@ -810,8 +814,8 @@ spmv_tiled_rw(const int4* __restrict__ tiles, const int2* __restrict__ runs, int
                 atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
                 break;
             }
-            const int4 d = __ldg(tiles + t);
             const TileStageR* Sg = st + k;
+            const int4 d = Sg->desc;
             const int row = d.x + warp * 32 + lane;
             const bool active = row < d.y;
             int kb = 0, len = 0;
@@ -1206,6 +1210,131 @@ spmv32_tiled(const int4* __restrict__ tiles, const int2* __restrict__ xwin, int 
     if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish<1>((double)acc, 0.0, ctl, partials, f);
 }
 
+// FP32 run-staged product, warp-specialised (the mixed-precision chain): the FP64
+// operand's tiles, runs and 16-bit slots with the FP32 copy of the values; runs start
+// and end on multiples of 4 entries, so the FP32 x runs move in 16-byte units too.
+struct __align__(16) TileStageR32 {
+    int4 desc;
+    float vals[kRunCap + 4];
+    uint16_t lcol[kRunCap + kPadLcol];
+    int32_t rp[kTileRows + 8];
+    float xs[kRunXs];
+};
+static_assert(offsetof(TileStageR32, vals) % 16 == 0 && offsetof(TileStageR32, lcol) % 16 == 0 &&
+              offsetof(TileStageR32, rp) % 16 == 0 && offsetof(TileStageR32, xs) % 16 == 0 &&
+              sizeof(TileStageR32) % 16 == 0, "bulk-copy destinations are 16-byte aligned");
+constexpr int kRw32Stages = 4, kRw32BlocksPerSM = 4;
+
+__device__ __forceinline__ void tile_issue_r32(const int4 d, const int2* __restrict__ runs, TileStageR32* st,
+                                               uint64_t* bar, const int32_t* rowptr, const uint16_t* lcol,
+                                               const float* vals, const float* x) {
+    const int a0 = d.z & ~3, c0 = d.z & ~7, r0 = d.x & ~3;
+    const uint32_t bv = d.w > d.z ? round16((uint32_t)(d.w - a0) * 4u) : 0u;
+    const uint32_t bc = d.w > d.z ? round16((uint32_t)(d.w - c0) * 2u) : 0u;
+    const uint32_t br = round16((uint32_t)(d.y + 1 - r0) * 4u);
+    int2 rr[kRunMax];
+    uint32_t bx = 0;
+#pragma unroll
+    for (int k = 0; k < kRunMax; ++k) {
+        rr[k] = __ldg(runs + k);
+        bx += (uint32_t)rr[k].y * 4u;        // lengths are multiples of 4: 16-byte multiples
+    }
+    mbar_expect_tx(bar, bv + bc + br + bx);
+    if (bv) bulk_g2s(st->vals, vals + a0, bv, bar);
+    if (bc) bulk_g2s(st->lcol, lcol + c0, bc, bar);
+    bulk_g2s(st->rp, rowptr + r0, br, bar);
+    int off = 0;
+#pragma unroll
+    for (int k = 0; k < kRunMax; ++k) {
+        if (rr[k].y > 0) bulk_g2s(st->xs + off, x + rr[k].x, (uint32_t)rr[k].y * 4u, bar);
+        off += rr[k].y;
+    }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kRwThreads, kRw32BlocksPerSM)
+spmv32_tiled_rw(const int4* __restrict__ tiles, const int2* __restrict__ runs, int ntiles,
+                const int32_t* __restrict__ rowptr, const uint16_t* __restrict__ lcol,
+                const float* __restrict__ vals, const float* __restrict__ x, float* __restrict__ y, float scale,
+                Ctl* ctl, double* partials, FinArgs f, int gate) {
+    constexpr int S = kRw32Stages;
+    if (gated_out(ctl, gate)) return;
+    if (gate != GATE_FORCE && blockIdx.x == 0 && threadIdx.x == 0) ctl->matvecs += 1;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TileStageR32* st = reinterpret_cast<TileStageR32*>(smem_raw);
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ volatile int failed;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int G = gridDim.x;
+    if (tid == 0) {
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kRwConsumers);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
+    }
+    __syncthreads();
+    int last_use[S];
+    for (int k = 0; k < S; ++k) last_use[k] = -1;
+    float acc = 0.0f;
+    if (warp == kRwConsumers) {
+        if (lane == 0) {
+            for (int j = 0;; ++j) {
+                const int t = blockIdx.x + j * G;
+                if (t >= ntiles || failed) break;
+                const int k = j % S, u = j / S;
+                if (u > 0 && !mbar_wait_bounded(&empty[k], (uint32_t)((u - 1) & 1))) {
+                    failed = 1;
+                    atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+                    break;
+                }
+                const int4 d = __ldg(tiles + t);
+                st[k].desc = d;
+                tile_issue_r32(d, runs + (size_t)t * kRunMax, st + k, &full[k], rowptr, lcol, vals, x);
+                last_use[k] = u;
+            }
+        }
+    } else {
+        for (int j = 0;; ++j) {
+            const int t = blockIdx.x + j * G;
+            if (t >= ntiles) break;
+            const int k = j % S;
+            if (failed || !mbar_wait_bounded(&full[k], (uint32_t)((j / S) & 1))) {
+                failed = 1;
+                atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+                break;
+            }
+            const TileStageR32* Sg = st + k;
+            const int4 d = Sg->desc;
+            const int row = d.x + warp * 32 + lane;
+            const bool active = row < d.y;
+            int kb = 0, len = 0;
+            if (active) {
+                const int r0 = d.x & ~3;
+                kb = Sg->rp[row - r0];
+                len = Sg->rp[row + 1 - r0] - kb;
+            }
+            const int vb = kb - (d.z & ~3), cb = kb - (d.z & ~7);
+            float sum = 0.0f;
+            for (int u = 0; u < len; ++u) sum = fmaf(Sg->vals[vb + u], Sg->xs[Sg->lcol[cb + u]], sum);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[k]);
+            if (active) {
+                sum *= scale;   // a power of two: exact
+                y[row] = sum;
+                if (EPI == EPI_NORM) acc = fmaf(sum, sum, acc);
+            }
+        }
+    }
+    __syncthreads();
+    if (failed && warp == kRwConsumers && lane == 0) {
+        for (int k = 0; k < S; ++k)
+            if (last_use[k] >= 0) mbar_wait_bounded(&full[k], (uint32_t)(last_use[k] & 1));
+    }
+    if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish<1, kRwThreads>((double)acc, 0.0, ctl, partials, f);
+}
+
 // warp per row for long FP32 rows
 template <int EPI>
 __global__ void __launch_bounds__(kBlock)
@@ -1250,6 +1379,21 @@ template <int EPI>
 static cudaError_t spmv32_epi(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y, float scale,
                               FinArgs f, int gate) {
     const DevCSR& a = *A.base;
+    if (a.cfg.kind == 3 && a.lcol) {
+        static bool attr_set = false;
+        constexpr size_t sm = kRw32Stages * sizeof(TileStageR32);
+        if (!attr_set) {
+            const cudaError_t e2 = cudaFuncSetAttribute(spmv32_tiled_rw<EPI>,
+                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e2 != cudaSuccess) return e2;
+            attr_set = true;
+        }
+        const int grid = std::min(a.ntiles, std::max(1, (L.max_grid / 8) * kRw32BlocksPerSM));
+        spmv32_tiled_rw<EPI><<<grid, kRwThreads, sm, L.stream>>>(a.tiles, a.runs, a.ntiles, a.rowptr, a.lcol, A.vals,
+                                                                 x, y, scale, L.ctl, L.partials, f, gate);
+        if (L.launches) ++*L.launches;
+        return cudaGetLastError();
+    }
     if (a.cfg.kind == 3) return spmv32_tiled_launch<kTileCapSmall, true, EPI>(L, A, x, y, scale, f, gate);
     if (a.cfg.kind == 2) {
         if (a.cap <= kTileCapSmall)

@@ -188,8 +188,9 @@ static void plan_free(Plan* p) {
 // Tiles: greedy runs of consecutive rows, at most kTileRows rows and `cap`
 // nonzeros each, described by {row begin, row end, nnz begin, nnz end}.
 // Runs of x for the run-staged product: per tile, the distinct columns (inside the
-// tile's window win[t]) split where the gap exceeds kRunGap; each run starts on an even
-// column and has an even length (16-byte bulk copies), and lcol maps every nonzero to
+// tile's window win[t]) split where the gap exceeds kRunGap; each run starts on a column
+// that is a multiple of 4 and has a length that is a multiple of 4 (16-byte bulk copies of
+// FP64 and of FP32 x), and lcol maps every nonzero to
 // its slot in the runs laid end to end. False when a tile needs more than kRunMax runs
 // or kRunXs staged entries.
 static bool build_runs(const std::vector<int4>& tiles, const std::vector<int2>& win,
@@ -207,8 +208,8 @@ static bool build_runs(const std::vector<int4>& tiles, const std::vector<int2>& 
         int nrun = 0, total = 0, first = -1, last = -1;
         auto close_run = [&]() {
             if (nrun == kRunMax) return false;
-            const int c0 = (lo + first) & ~1;
-            const int len = (lo + last + 1 - c0 + 1) & ~1;
+            const int c0 = (lo + first) & ~3;
+            const int len = (lo + last + 1 - c0 + 3) & ~3;
             rt[nrun++] = make_int2(c0, len);
             total += len;
             return total <= kRunXs;

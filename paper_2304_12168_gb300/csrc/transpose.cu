@@ -93,7 +93,8 @@ inline int blocks_for(int64_t n) {
 // Run-staged layout of fixed 256-row tiles, one block per tile (plan time). Per
 // tile: row range and nonzero range, the window [lo, hi] of columns, the runs of
 // used columns (a gap of more than kRunGap columns starts a new run; each run starts
-// on an even column and has an even length) and each nonzero's 16-bit slot in the
+// on a column that is a multiple of 4 and has a length that is a multiple of 4, so that
+// FP64 and FP32 copies of x both move in 16-byte units) and each nonzero's 16-bit slot in the
 // runs laid end to end. stats: [0] failure bits (1: a tile holds more than kRunCap
 // nonzeros, 2: its window spans more than kXSpan columns, 4: more than kRunMax
 // runs, 8: more than kRunXs staged entries), [1] max nonzeros of a tile, [2] max
@@ -150,8 +151,8 @@ run_tiles(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx
         int nrun = 0, total = 0, first = -1, last = -1, f = 0;
         auto close = [&]() {
             if (nrun == kRunMax) { f |= 4; return; }
-            const int c0 = (wlo + first) & ~1;
-            const int len = (wlo + last + 1 - c0 + 1) & ~1;
+            const int c0 = (wlo + first) & ~3;
+            const int len = (wlo + last + 1 - c0 + 3) & ~3;
             rr[nrun++] = make_int2(c0, len);
             total += len;
             if (total > kRunXs) f |= 8;
