@@ -134,7 +134,7 @@ constexpr int kXCapCompactPlan = 1280, kXSpanCompactPlan = 2304;   // compact x-
 // indices shrink to 16-bit slots in them.
 constexpr int kRunCap = 1280, kRunXs = 896, kRunMax = 4, kRunGap = 16;
 constexpr int kPadLcol = 8;
-// ring depth of the warp-specialised run-staged product (0: the block-synchronous one)
+// ring depth of the warp-specialised run-staged product
 constexpr int kRwStages = 3;
 // Mixed-precision CTA refines (FP64 residual, fold of the FP32 correction) as soon as
 // the FP32 inner iteration has reduced the residual by kRefineEta over the last

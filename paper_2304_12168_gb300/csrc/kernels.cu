@@ -620,9 +620,9 @@ static cudaError_t spmv_tiled_x_launch(const LaunchCtx& L, const DevCSR& A, cons
 //
 // Banded and stencil operands use only a few short runs of x per tile (a 5-point
 // stencil: the rows below, at and above the tile). Staging just those runs instead
-// of the whole window cuts the shared-memory footprint to ~21 KB per stage (five
-// blocks per SM), and each nonzero's column is stored as a 16-bit slot in the staged
-// runs: 10 bytes per nonzero from HBM instead of 12.
+// of the whole window cuts the shared-memory footprint to ~21 KB per stage, and each
+// nonzero's column is stored as a 16-bit slot in the staged runs: 10 bytes per
+// nonzero from HBM instead of 12.
 
 struct __align__(16) TileStageR {
     int4 desc;                       // the tile's descriptor (written by the producer)
@@ -635,8 +635,6 @@ static_assert(sizeof(TileStageR) % 16 == 0, "stage size keeps 16-byte alignment"
 static_assert(offsetof(TileStageR, vals) % 16 == 0 && offsetof(TileStageR, lcol) % 16 == 0 &&
               offsetof(TileStageR, rp) % 16 == 0 && offsetof(TileStageR, xs) % 16 == 0,
               "bulk-copy destinations are 16-byte aligned");
-constexpr int kRunBlocksPerSM = 5;
-static int g_run_resident = kRunBlocksPerSM;   // blocks per SM the device actually fits
 
 __device__ __forceinline__ void tile_issue_r(const int4 d, const int2* __restrict__ runs, TileStageR* st,
                                              uint64_t* bar, const int32_t* rowptr, const uint16_t* lcol,
@@ -664,89 +662,10 @@ __device__ __forceinline__ void tile_issue_r(const int4 d, const int2* __restric
     }
 }
 
-template <int EPI>
-__global__ void __launch_bounds__(kTileRows, kRunBlocksPerSM)
-spmv_tiled_r(const int4* __restrict__ tiles, const int2* __restrict__ runs, int ntiles,
-             const int32_t* __restrict__ rowptr, const uint16_t* __restrict__ lcol,
-             const double* __restrict__ vals, const double* __restrict__ x, double* __restrict__ y,
-             EpiArgs e, Ctl* ctl, double* partials, FinArgs f, int gate) {
-    if (gated_out(ctl, gate)) return;
-    if (gate != GATE_FORCE && blockIdx.x == 0 && threadIdx.x == 0) ctl->matvecs += 1;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    TileStageR* st = reinterpret_cast<TileStageR*>(smem_raw);
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int failed;
-    const int tid = threadIdx.x;
-    const int G = gridDim.x;
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        failed = 0;
-        for (int j = 0; j < 2; ++j) {
-            const int t = blockIdx.x + j * G;
-            if (t < ntiles)
-                tile_issue_r(__ldg(tiles + t), runs + (size_t)t * kRunMax, st + j, bar + j, rowptr, lcol, vals, x);
-        }
-    }
-    __syncthreads();
-    const double s = (EPI == EPI_TAPIVOT) ? ctl->s : 0.0;
-    double a0 = 0.0, a1 = 0.0;
-    for (int j = 0;; ++j) {
-        const int t = blockIdx.x + j * G;
-        if (t >= ntiles) break;
-        const int sidx = j & 1;
-        const int4 d = __ldg(tiles + t);
-        const bool ok = !failed && mbar_wait_bounded(bar + sidx, (uint32_t)((j >> 1) & 1));
-        if (!ok) {
-            failed = 1;
-            atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
-        }
-        const TileStageR* S = st + sidx;
-        const int row = d.x + tid;
-        const bool active = ok && row < d.y;
-        int kb = 0, len = 0;
-        if (active) {
-            const int r0 = d.x & ~3;
-            kb = S->rp[row - r0];
-            len = S->rp[row + 1 - r0] - kb;
-        }
-        // trip count = warp-uniform max row length (a masked FP64 FMA costs a full slot)
-        const int maxlen = __reduce_max_sync(0xffffffffu, len);
-        const int vb = kb - (d.z & ~1), cb = kb - (d.z & ~7);
-        double sum = 0.0;
-        for (int u = 0; u < maxlen; ++u)
-            if (u < len) sum = fma(S->vals[vb + u], S->xs[S->lcol[cb + u]], sum);
-        if (active) epilogue<EPI>(row, sum, y, e, s, a0, a1);
-        __syncthreads();   // stage sidx is free again
-        if (tid == 0 && !failed) {
-            const int t2 = t + 2 * G;
-            if (t2 < ntiles)
-                tile_issue_r(__ldg(tiles + t2), runs + (size_t)t2 * kRunMax, st + sidx, bar + sidx, rowptr,
-                             lcol, vals, x);
-        }
-    }
-    if (failed && tid == 0) {
-        for (int j = 0; j < 2; ++j) mbar_wait_bounded(bar + j, 0u);
-    }
-    if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish<EpiRed<EPI>::value>(a0, a1, ctl, partials, f);
-}
-
-template <int EPI>
-static cudaError_t spmv_tiled_r_launch(const LaunchCtx& L, const DevCSR& A, const double* x, double* y,
-                                       EpiArgs e, FinArgs f, int gate) {
-    const int sms = L.max_grid / 8;
-    const int grid = std::min(A.ntiles, std::max(1, sms * g_run_resident));
-    spmv_tiled_r<EPI><<<grid, kTileRows, 2 * sizeof(TileStageR), L.stream>>>(
-        A.tiles, A.runs, A.ntiles, A.rowptr, A.lcol, A.vals, x, y, e, L.ctl, L.partials, f, gate);
-    if (L.launches) ++*L.launches;
-    return cudaGetLastError();
-}
-
 // ------------------------------------------------------------------ run-staged, warp-specialised
 //
-// The same tiles and stages as spmv_tiled_r, without the block-wide barrier per
-// tile: one producer warp streams tiles into a ring of S stages (a "full"
+// Run-staged tiles without a block-wide barrier per tile: one producer warp
+// streams tiles into a ring of S stages (a "full"
 // mbarrier per stage completes when the tile's bytes land), and each of the eight
 // consumer warps multiplies its own 32 rows of a tile as soon as it has landed,
 // then arrives on the stage's "empty" mbarrier; the producer refills a stage once
@@ -884,13 +803,7 @@ cudaError_t spmv_tiled_prepare() {
                                  (int)spmv_tiled_x_smem<kXCapCompact, kXSpanCompact>());
     TACTA_TILED_X_ATTR(EPI_NONE) TACTA_TILED_X_ATTR(EPI_NORM) TACTA_TILED_X_ATTR(EPI_RESID)
     TACTA_TILED_X_ATTR(EPI_TAPIVOT) TACTA_TILED_X_ATTR(EPI_RESID_F32) TACTA_TILED_X_ATTR(EPI_NORM_POS)
-#define TACTA_TILED_R_ATTR(EPI)                                                                          \
-    if (e == cudaSuccess)                                                                                \
-        e = cudaFuncSetAttribute(spmv_tiled_r<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
-                                 (int)(2 * sizeof(TileStageR)));
-    TACTA_TILED_R_ATTR(EPI_NONE) TACTA_TILED_R_ATTR(EPI_NORM) TACTA_TILED_R_ATTR(EPI_RESID)
-    TACTA_TILED_R_ATTR(EPI_TAPIVOT) TACTA_TILED_R_ATTR(EPI_RESID_F32) TACTA_TILED_R_ATTR(EPI_NORM_POS)
-#undef TACTA_TILED_R_ATTR
+
 #define TACTA_TILED_RW_ATTR(EPI)                                                                         \
     if (e == cudaSuccess)                                                                                \
         e = cudaFuncSetAttribute(spmv_tiled_rw<kRwStages, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
@@ -898,12 +811,7 @@ cudaError_t spmv_tiled_prepare() {
     TACTA_TILED_RW_ATTR(EPI_NONE) TACTA_TILED_RW_ATTR(EPI_NORM) TACTA_TILED_RW_ATTR(EPI_RESID)
     TACTA_TILED_RW_ATTR(EPI_TAPIVOT) TACTA_TILED_RW_ATTR(EPI_RESID_F32) TACTA_TILED_RW_ATTR(EPI_NORM_POS)
 #undef TACTA_TILED_RW_ATTR
-    if (e == cudaSuccess) {
-        int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmv_tiled_r<EPI_NORM>, kTileRows,
-                                                          2 * sizeof(TileStageR));
-        if (e == cudaSuccess) g_run_resident = std::max(1, std::min(nb, kRunBlocksPerSM));
-    }
+
 #undef TACTA_TILED_X_ATTR
     if (e == cudaSuccess) done = true;
     return e;
@@ -953,7 +861,7 @@ static cudaError_t spmv_dispatch(const LaunchCtx& L, int kind, const Acc& acc, c
 
 cudaError_t launch_spmv(const LaunchCtx& L, const DevOperand& A, const double* x, double* y,
                         int epi, EpiArgs e, FinArgs f, int gate) {
-    if (A.format == TACTA_CSR && A.csr.cfg.kind == 3 && A.csr.lcol && kRwStages > 0) {
+    if (A.format == TACTA_CSR && A.csr.cfg.kind == 3 && A.csr.lcol) {
         switch (epi) {
         case EPI_NONE: return spmv_tiled_rw_launch<kRwStages, EPI_NONE>(L, A.csr, x, y, e, f, gate);
         case EPI_NORM: return spmv_tiled_rw_launch<kRwStages, EPI_NORM>(L, A.csr, x, y, e, f, gate);
@@ -961,16 +869,6 @@ cudaError_t launch_spmv(const LaunchCtx& L, const DevOperand& A, const double* x
         case EPI_RESID_F32: return spmv_tiled_rw_launch<kRwStages, EPI_RESID_F32>(L, A.csr, x, y, e, f, gate);
         case EPI_NORM_POS: return spmv_tiled_rw_launch<kRwStages, EPI_NORM_POS>(L, A.csr, x, y, e, f, gate);
         default: return spmv_tiled_rw_launch<kRwStages, EPI_TAPIVOT>(L, A.csr, x, y, e, f, gate);
-        }
-    }
-    if (A.format == TACTA_CSR && A.csr.cfg.kind == 3 && A.csr.lcol) {
-        switch (epi) {
-        case EPI_NONE: return spmv_tiled_r_launch<EPI_NONE>(L, A.csr, x, y, e, f, gate);
-        case EPI_NORM: return spmv_tiled_r_launch<EPI_NORM>(L, A.csr, x, y, e, f, gate);
-        case EPI_RESID: return spmv_tiled_r_launch<EPI_RESID>(L, A.csr, x, y, e, f, gate);
-        case EPI_RESID_F32: return spmv_tiled_r_launch<EPI_RESID_F32>(L, A.csr, x, y, e, f, gate);
-        case EPI_NORM_POS: return spmv_tiled_r_launch<EPI_NORM_POS>(L, A.csr, x, y, e, f, gate);
-        default: return spmv_tiled_r_launch<EPI_TAPIVOT>(L, A.csr, x, y, e, f, gate);
         }
     }
     if (A.format == TACTA_CSR && A.csr.cfg.kind == 3) {
