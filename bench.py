@@ -164,9 +164,10 @@ def timed_solve(plan, b, stream, **kw):
 
 
 def extra_workloads(tacta, dev, stream, plan_stencil, b_stencil, steps):
-    """The other configurations, each timed with device events (inputs resident):
-    the mixed-precision rate on the benchmark stencil, time to 1e-8 on the LP-like
-    rectangular system (FP64 and mixed), and the Clement rate."""
+    """The other configurations, each timed with device events (inputs resident): the
+    mixed-precision CTA rate and the TA rate on the benchmark stencil, time to 1e-8 on the
+    LP-like rectangular system (FP64 and mixed), the Clement rate, the batched dense
+    workload, the dense 256 x 256 systems and the differentiable 2000 x 8000 solve."""
     import gen
     import numpy as np
     import torch
@@ -179,10 +180,26 @@ def extra_workloads(tacta, dev, stream, plan_stencil, b_stencil, steps):
         t, _, info = timed_solve(plan_stencil, b_stencil, stream, **opts)
         ms += t
         its += info["iters"]
+    # TA (Alg. 2.2) on the same stencil: iterations per second over a fixed budget
+    kw = dict(tol=TOL, tol_normal=0.0, max_iter=ITERS_PER_STEP)
+    plan_stencil.ta(b_stencil, **kw)
+    ta_ms, ta_its = 0.0, 0
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, _, info = plan_stencil.ta(b_stencil, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ta_ms += e0.elapsed_time(e1)
+        ta_its += info["iters"]
+    out["ta_fp64_convdiff_1000x1000"] = {"value": ta_its / (ta_ms * 1e-3), "unit": "TA iterations/s",
+                                         "steps": steps, "iters_per_step": ITERS_PER_STEP,
+                                         "rel_res_after_step": info["rel_res"]}
     out["cta_mixed_convdiff_1000x1000"] = {
         "value": its / (ms * 1e-3), "unit": UNIT, "steps": steps, "iters_per_step": ITERS_PER_STEP,
         "dtype": "f32 chain (values, vectors, products), f64 moments reduction, centering solve, "
-                 "stop tests and residual refinement every 40 steps"}
+                 "stop tests, and residual refinement every 40 steps or once the f32 residual fell by 1e-3"}
     # LP-like rectangular min-norm system, 10,000 x 1,000,000, 31.6M nonzeros: time to 1e-8
     p = gen.lp_rect()
     A = tacta.CSR(torch.from_numpy(p.rowptr).to(dev), torch.from_numpy(p.colidx).to(dev),

@@ -75,7 +75,8 @@ enum {
     TACTA_REASON_ZERO_RHS = 7,   /* b = 0: x = 0                                            */
     TACTA_REASON_NONFINITE = 8,
     TACTA_REASON_TIMEOUT = 9,    /* a bounded wait inside a kernel gave up (TACTA_ERR_TIMEOUT) */
-    TACTA_REASON_RHO_BOUND = 10  /* ta_solve: rho passed opt->rho_max                          */
+    TACTA_REASON_RHO_BOUND = 10, /* ta_solve: rho passed opt->rho_max                          */
+    TACTA_REASON_ENHANCED = 11   /* CTA with opt->enhanced: the enhanced stop of Sec. 3.2 held   */
 };
 
 enum { TACTA_DENSE = 0, TACTA_CSR = 1 };
@@ -114,6 +115,14 @@ typedef struct {
     int32_t nonneg;          /* ta_solve only: 1 = TA for LP feasibility A x = b, x >= 0 (Sec. 6):
                                 c is replaced by max(c, 0); WITNESS when ||max(c,0)|| <=
                                 tol_normal ||Aᵀb|| while (b - b')ᵀb > 0 (Farkas certificate)   */
+    int32_t enhanced;        /* CTA, FP64 path: 1 = the enhanced algorithm of Sec. 3.2. At a step of
+                                order t >= 2 it also stops when, for the smallest j <= t-1, the j-th
+                                first-order iterate r_j = F_1^j(r') has r_jᵀ H r_j <= tol_normal²
+                                ||Aᵀb||², and returns x^ = x' + sum_{i<j} alpha_{1,1}(r_i) Aᵀ r_i
+                                (Eq. widehatxB; reason ENHANCED). r_jᵀ H r_j is evaluated from the
+                                step's moments phi_1..phi_{2j+1}, so the test is resolved for
+                                tol_normal down to ~1e-7 (below that its rounding, ~1e-16 phi_1,
+                                reaches the threshold)                                          */
     double rho_max;          /* ta_solve: stop (reason RHO_BOUND) once rho exceeds this; <= 0: none */
     void* stream;            /* cudaStream_t (NULL: legacy default stream)                      */
 } tacta_options;

@@ -145,6 +145,29 @@ def cta_step(A, x, r, t: int, pivot_tol: float = 1e-12):
     return x2, r2, alpha, rank, phi
 
 
+def enhanced_stop(A, x, r, jmax: int, thr: float):
+    """The enhanced stop of Sec. 3.2 from (x', r'): apply the first-order map
+    F_1(r) = r - alpha_{1,1}(r) H r, alpha_{1,1}(r) = rᵀHr / rᵀH²r, j = 1, 2, ... times and
+    return (x^, r_j, j) for the smallest j <= jmax with r_jᵀ H r_j <= thr, where
+    x^ = x' + sum_{i<j} alpha_{1,1}(r_i) Aᵀ r_i (Eq. widehatxB, H = A Aᵀ); None if no j does.
+    """
+    xh = np.array(x, dtype=np.float64)
+    ri = np.array(r, dtype=np.float64)
+    for j in range(1, jmax + 1):
+        w = A.rmatvec(ri)                 # Aᵀ r_{j-1}
+        hr = A.matvec(w)                  # H r_{j-1}
+        den = float(hr @ hr)
+        if not den > 0.0:
+            return None
+        a = float(w @ w) / den            # alpha_{1,1}(r_{j-1})
+        xh = xh + a * w
+        ri = ri - a * hr
+        wj = A.rmatvec(ri)
+        if float(wj @ wj) <= thr:         # r_jᵀ H r_j = ||Aᵀ r_j||²
+            return xh, ri, j
+    return None
+
+
 @dataclass
 class CTAResult:
     x: np.ndarray
@@ -159,7 +182,8 @@ class CTAResult:
 
 
 def cta_solve(A, b, x0=None, tol=1e-10, tol_normal=None, max_iter=1000, t_max=5,
-              cycle=PINGPONG, recompute_every=40, pivot_tol=1e-12, observer=None) -> CTAResult:
+              cycle=PINGPONG, recompute_every=40, pivot_tol=1e-12, observer=None,
+              enhanced=False) -> CTAResult:
     """Algorithm 1.1 (CTA) with H = A Aᵀ and the Sec. 5.1 t-cycling.
 
     Loop (k counts completed F_t steps; hist[k] = ||r_k|| / ||b||):
@@ -168,7 +192,9 @@ def cta_solve(A, b, x0=None, tol=1e-10, tol_normal=None, max_iter=1000, t_max=5,
       2. stop if k = max_iter.
       3. t = t(k); chain z_i, u_i and moments phi_1..phi_2t.
       4. stop if phi_1 = ||Aᵀ r||² <= tol_normal² ||Aᵀ b||² (normal equation
-         solved, Alg. 1.1 second clause).
+         solved, Alg. 1.1 second clause); with ``enhanced`` and t >= 2, the enhanced
+         algorithm of Sec. 3.2 also stops here when a first-order iterate F_1^j(r),
+         j <= t - 1, meets that test, with x = x^ of Eq. widehatxB (counted as a step).
       5. alpha from the auxiliary equation; rank 0 -> breakdown.
       6. x += sum alpha_i z_i, r -= sum alpha_i u_i; k += 1; every R-th k the
          true residual replaces r.
@@ -224,6 +250,16 @@ def cta_solve(A, b, x0=None, tol=1e-10, tol_normal=None, max_iter=1000, t_max=5,
         if phi[1] <= nrm_thr:
             status, reason = Status.OK, Reason.NORMAL
             break
+        if enhanced and t >= 2:
+            hit = enhanced_stop(A, x, r, t - 1, nrm_thr)
+            if hit is not None:
+                x, r, _ = hit
+                k += 1
+                is_true = False
+                rn2 = float(r @ r)
+                hist.append(math.sqrt(rn2 / bn2))
+                status, reason = Status.OK, Reason.ENHANCED
+                break
         alpha, rank = hankel_solve(phi, t, pivot_tol)
         if rank == 0:
             status, reason = Status.BREAKDOWN, Reason.BREAKDOWN

@@ -26,3 +26,4 @@ class Reason(IntEnum):
     ZERO_RHS = 7    # b = 0: x = 0 is the minimum-norm solution
     NONFINITE = 8
     RHO_BOUND = 10  # TA with x >= 0 (Sec. 6): rho passed its termination bound
+    ENHANCED = 11   # enhanced CTA (Sec. 3.2): a first-order iterate met the normal-equation test

@@ -33,7 +33,7 @@ PRECISION_FP64, PRECISION_MIXED = 0, 1
 STATUS = {0: "OK", 1: "MAXITER", 2: "BREAKDOWN", 3: "WITNESS", -1: "ERR_INVALID",
           -2: "ERR_NONFINITE", -3: "ERR_CUDA", -4: "ERR_OOM", -5: "ERR_TIMEOUT"}
 REASON = {0: "NONE", 1: "RESIDUAL", 2: "NORMAL", 3: "MAXITER", 4: "BREAKDOWN", 5: "WITNESS",
-          6: "GAP", 7: "ZERO_RHS", 8: "NONFINITE", 9: "TIMEOUT", 10: "RHO_BOUND"}
+          6: "GAP", 7: "ZERO_RHS", 8: "NONFINITE", 9: "TIMEOUT", 10: "RHO_BOUND", 11: "ENHANCED"}
 
 
 class tacta_matrix(ctypes.Structure):
@@ -48,7 +48,7 @@ class tacta_options(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("t_max", ctypes.c_int32), ("cycle", ctypes.c_int32),
                 ("recompute_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("poll_every", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("nonneg", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("nonneg", ctypes.c_int32), ("enhanced", ctypes.c_int32),
                 ("rho_max", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
 

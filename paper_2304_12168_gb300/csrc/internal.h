@@ -32,6 +32,8 @@ struct Ctl {
     int32_t nonneg;        // TA for LP feasibility (Sec. 6): c replaced by max(c, 0)
     uint32_t counter;      // last-block-done ticket
     int32_t matvecs;       // products with A or Aᵀ made by the iteration (setup included)
+    int32_t enhanced;      // CTA: the enhanced stop of Sec. 3.2 is on
+    int32_t enh_stop;      // CTA: this step applies x^ and ends the solve (reason ENHANCED)
     int32_t pad_;
     double bn2;            // ||b||²  (b = rhs of the operator in use)
     double inv_bn2;        // 1 / ||b||² (0 when b = 0): the history stores ||r||² / ||b||²

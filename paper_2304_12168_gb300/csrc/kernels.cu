@@ -90,6 +90,7 @@ __device__ __noinline__ void finish(Ctl* c, const FinArgs& f, double r0, double 
         c->is_true = 0;
         c->rn2 = r0;
         put_hist(c, f.hist);
+        if (c->enh_stop) { c->status = TACTA_REASON_ENHANCED; break; }
         if (c->R > 0 && c->k % c->R == 0) { c->need_true = 1; break; }
         if (c->ref_eta2 > 0.0 && r0 <= c->ref_thr) { c->need_true = 1; break; }
         loop_top(c);
@@ -1524,11 +1525,48 @@ cudaError_t launch_copy_gated(const LaunchCtx& L, double* dst, const double* src
 // its own kernel so that the solve's registers (its arrays live in registers) do not
 // count against the occupancy of every product and update kernel, as they would if it
 // ran inside their shared finisher.
+// Enhanced stop (Sec. 3.2, Eq. widehatxB): the first-order iterates r_0 = r',
+// r_{i+1} = r_i - a_i H r_i with a_i = r_iᵀH r_i / r_iᵀH² r_i are polynomials in H
+// applied to r' (r_i = sum_k c_k H^k r'), so r_iᵀ H^s r_i = sum_{a,b} c_a c_b phi_{a+b+s}
+// comes from the step's moments. If r_jᵀ H r_j <= thr for the smallest j <= t-1, the
+// step's coefficients become those of x^ = x' + sum_{i<j} a_i Aᵀ r_i
+// = x' + sum_k beta_k z_{k+1} (and r^ = r' - sum_k beta_k u_{k+1} = r_j), so the update
+// kernel applies x^ unchanged. Returns true if it stops there.
+__device__ bool enhanced_stop(Ctl* c, int t) {
+    double cf[kTMax], beta[kTMax];
+    for (int k = 0; k < kTMax; ++k) { cf[k] = 0.0; beta[k] = 0.0; }
+    cf[0] = 1.0;
+    for (int i = 0; i + 1 < t; ++i) {              // from r_i (degree i) to r_{i+1}
+        double s1 = 0.0, s2 = 0.0;
+        for (int a = 0; a <= i; ++a)
+            for (int b = 0; b <= i; ++b) {
+                const double w = __dmul_rn(cf[a], cf[b]);
+                s1 = __fma_rn(w, c->phi[a + b + 1], s1);
+                s2 = __fma_rn(w, c->phi[a + b + 2], s2);
+            }
+        if (!(s2 > 0.0)) return false;
+        const double ai = __ddiv_rn(s1, s2);
+        for (int k = 0; k <= i; ++k) beta[k] = __fma_rn(ai, cf[k], beta[k]);
+        for (int k = i + 1; k >= 1; --k) cf[k] = __fma_rn(-ai, cf[k - 1], cf[k]);
+        double q = 0.0;                              // r_{i+1}ᵀ H r_{i+1}
+        for (int a = 0; a <= i + 1; ++a)
+            for (int b = 0; b <= i + 1; ++b) q = __fma_rn(__dmul_rn(cf[a], cf[b]), c->phi[a + b + 1], q);
+        if (q <= c->nrm_thr) {
+            for (int k = 0; k < t; ++k) c->alpha[k] = beta[k];
+            c->rank = i + 1;
+            c->enh_stop = 1;
+            return true;
+        }
+    }
+    return false;
+}
+
 __global__ void cta_aux_step(Ctl* c, int t) {
     if (threadIdx.x != 0 || c->status != 0) return;
     for (int i = 1; i <= 2 * t; ++i)
         if (!finite(c->phi[i])) { c->status = TACTA_REASON_NONFINITE; return; }
     if (c->phi[1] <= __dmul_rn(c->nrm_thr, c->cs2)) { c->status = TACTA_REASON_NORMAL; return; }
+    if (c->enhanced && t >= 2 && enhanced_stop(c, t)) return;
     c->rank = hankel_solve_dev(c->phi, t, c->pivot_tol, c->alpha);
     if (c->rank == 0) c->status = TACTA_REASON_BREAKDOWN;
 }

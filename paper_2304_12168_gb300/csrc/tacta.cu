@@ -745,7 +745,8 @@ static tacta_status status_of(int reason) {
     case TACTA_REASON_NORMAL:
     case TACTA_REASON_GAP:
     case TACTA_REASON_ZERO_RHS:
-    case TACTA_REASON_RHO_BOUND: return TACTA_OK;
+    case TACTA_REASON_RHO_BOUND:
+    case TACTA_REASON_ENHANCED: return TACTA_OK;
     case TACTA_REASON_TIMEOUT: return TACTA_ERR_TIMEOUT;
     case TACTA_REASON_MAXITER: return TACTA_MAXITER;
     case TACTA_REASON_BREAKDOWN: return TACTA_BREAKDOWN;
@@ -819,6 +820,7 @@ static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t h
     LaunchCtx L{O.s, p->ctl, p->partials, p->grid, launches};
     Ctl h = base_ctl(O, hist_cap);
     h.need_true = (x0 || mixed) ? 1 : 0;
+    h.enhanced = (!mixed && O.o.enhanced) ? 1 : 0;
     if (mixed) {
         h.cs2 = (double)p->chain_scale * (double)p->chain_scale;
         h.ref_eta2 = kRefineEta2;

@@ -562,3 +562,51 @@ def test_ta_lp_infeasible_hits_rho_bound():
                           rho_max=1e6)
     assert res.reason in (Reason.RHO_BOUND, Reason.WITNESS)
     assert res.x.min() >= 0.0 and res.rel_res > 1e-3
+
+
+# ------------------------------------------------------------------ enhanced CTA (Sec. 3.2)
+
+def test_enhanced_stop_closed_form_scaled_orthogonal():
+    """A = 2Q (Q orthogonal): H = 4I, so one first-order step annihilates the residual
+    (alpha_{1,1} = 1/4) and the enhanced algorithm stops at j = 1 with x^ = A^{-1} b."""
+    import oracle.cta as ocx
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((16, 16)))
+    A = 2.0 * Q
+    b = rng.standard_normal(16)
+    p = gen.Problem(name="q", m=16, n=16, fmt="dense", dense=A, b=b)
+    res = ocx.cta_solve(oracle.make_operator(p), b, tol=1e-30, tol_normal=1e-8, max_iter=5, t_max=2,
+                        cycle=ocx.FIXED, enhanced=True)
+    assert res.reason == oracle.Reason.ENHANCED and res.iters == 1
+    np.testing.assert_allclose(res.x, Q.T @ b / 2.0, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_enhanced_stop_is_repeated_first_order_steps(seed):
+    """Wherever the enhanced stop fires, x^ equals j applications of F_1 (the order-1
+    step of the plain iteration, Eq. eqcoeff with t = 1) from the same state, b - A x^ equals
+    the returned residual, the returned residual meets the test, and no smaller j does."""
+    import oracle.cta as ocx
+    rng = np.random.default_rng(seed)
+    m, n = 30, 45
+    A = rng.standard_normal((m, 6)) @ rng.standard_normal((6, n)) + 0.05 * rng.standard_normal((m, n))
+    b = A @ rng.standard_normal(n)
+    p = gen.Problem(name="e", m=m, n=n, fmt="dense", dense=A, b=b)
+    op = oracle.make_operator(p)
+    thr = (1e-3 * np.linalg.norm(A.T @ b)) ** 2
+    hit, k = None, 0
+    x, r = np.zeros(n), b.copy()
+    while hit is None and k < 200:
+        hit = ocx.enhanced_stop(op, x, r, 4, thr)
+        if hit is None:
+            x, r, _, _, _ = ocx.cta_step(op, x, r, 5)
+            k += 1
+    assert hit is not None
+    xh, rh, j = hit
+    xs, rs = x.copy(), r.copy()
+    for _ in range(j):
+        xs, rs, _, _, _ = ocx.cta_step(op, xs, rs, 1)
+    np.testing.assert_allclose(xh, xs, rtol=1e-9, atol=1e-12 * np.linalg.norm(xs))
+    assert np.linalg.norm((b - A @ xh) - rh) <= 1e-9 * np.linalg.norm(b)
+    assert np.linalg.norm(A.T @ rh) ** 2 <= thr
+    assert j == 1 or ocx.enhanced_stop(op, x, r, j - 1, thr) is None
