@@ -98,3 +98,26 @@ def test_ctypes_layouts_match_the_c_header(tmp_path):
         assert int(got[sname]) == ctypes.sizeof(cls), sname
         for f, _ in cls._fields_:
             assert int(got[f"{sname}.{f}"]) == getattr(cls, f).offset, f"{sname}.{f}"
+
+
+def test_batch_arguments_are_rejected_before_gpu_work(lib):
+    """tacta_batch_create / tacta_batch_cta validate on the host before any CUDA call."""
+    i32 = ctypes.c_int32
+    out = ctypes.c_void_p()
+    m = (i32 * 2)(3, 0)
+    n = (i32 * 2)(4, 5)
+    vals = (ctypes.c_double * 32)()
+    st = lib.tacta_batch_create(2, m, n, ctypes.cast(vals, ctypes.c_void_p), 0, 1, None, ctypes.byref(out))
+    assert st == -1 and b"system 1" in lib.tacta_batch_last_error() and not out.value
+    m2 = (i32 * 1)(3)
+    n2 = (i32 * 1)(4)
+    st = lib.tacta_batch_create(1, m2, n2, ctypes.cast(vals, ctypes.c_void_p), 0, 7, None, ctypes.byref(out))
+    assert st == -1 and b"storage" in lib.tacta_batch_last_error()
+    st = lib.tacta_batch_create(-1, None, None, None, 0, 1, None, ctypes.byref(out))
+    assert st == -1 and b"count" in lib.tacta_batch_last_error()
+    st = lib.tacta_batch_cta(None, None, None, None, None, None, None)
+    assert st == -1 and b"NULL" in lib.tacta_batch_last_error()
+    t, p = ctypes.c_int32(), ctypes.c_int32()
+    assert lib.tacta_batch_num_configs() >= 1
+    assert lib.tacta_batch_config_shape(0, ctypes.byref(t), ctypes.byref(p)) == 0 and t.value > 0 and p.value > 0
+    assert lib.tacta_batch_config_shape(99, ctypes.byref(t), ctypes.byref(p)) == -1
