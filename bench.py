@@ -500,7 +500,7 @@ def main():
             "rel_res_after_step": last["rel_res"], "time_to_tol_s": None,
             "matvecs_per_s": world * sum(i["matvecs"] for i in infos) / (total_ms * 1e-3),
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
-    if rank == 0 and not args.no_extra:
+    if rank == 0 and world == 1 and not args.no_extra:   # the other configurations: at N = 1 only
         line["extra"] = extra_workloads(tacta, dev, stream, plan, b, min(args.steps, 5))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, r = cpu_baseline(p, CPU_SAMPLE_ITERS)
