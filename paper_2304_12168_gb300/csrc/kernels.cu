@@ -637,20 +637,53 @@ static_assert(offsetof(TileStageR, vals) % 16 == 0 && offsetof(TileStageR, lcol)
               offsetof(TileStageR, rp) % 16 == 0 && offsetof(TileStageR, xs) % 16 == 0,
               "bulk-copy destinations are 16-byte aligned");
 
-__device__ __forceinline__ void tile_issue_r(const int4 d, const int2* __restrict__ runs, TileStageR* st,
-                                             uint64_t* bar, const int32_t* rowptr, const uint16_t* lcol,
-                                             const double* vals, const double* x) {
+// A tile's descriptor and its kRunMax runs, as the producer warp prefetches them
+struct TileMeta {
+    int4 d;        // {row begin, row end, nnz begin, nnz end}
+    int4 r01, r23; // runs 0..3 as {first, length} pairs
+};
+
+__device__ __forceinline__ int4 shfl_int4(const int4 v, int src) {
+    return make_int4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                     __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+
+// Producer warp: lane i holds the metadata of the block's tile j0 + i, loaded 32 tiles at
+// a time, so that lane 0's copy issue never waits on a global load.
+struct TilePrefetch {
+    TileMeta m{};
+    int j0 = -32;
+    __device__ __forceinline__ TileMeta get(int j, const int4* __restrict__ tiles, const int2* __restrict__ runs,
+                                            int ntiles, int G, int lane) {
+        if (j - j0 >= 32) {
+            j0 = j;
+            const int tl = blockIdx.x + (j0 + lane) * G;
+            if (tl < ntiles) {
+                m.d = __ldg(tiles + tl);
+                const int4* r4 = reinterpret_cast<const int4*>(runs + (size_t)tl * kRunMax);
+                m.r01 = __ldg(r4);
+                m.r23 = __ldg(r4 + 1);
+            }
+        }
+        const int src = j - j0;
+        return TileMeta{shfl_int4(m.d, src), shfl_int4(m.r01, src), shfl_int4(m.r23, src)};
+    }
+};
+static_assert(kRunMax == 4, "TileMeta holds four runs");
+
+__device__ __forceinline__ void tile_issue_r(const TileMeta& tm, TileStageR* st, uint64_t* bar,
+                                             const int32_t* rowptr, const uint16_t* lcol, const double* vals,
+                                             const double* x) {
+    const int4 d = tm.d;
     const int a0 = d.z & ~1, c0 = d.z & ~7, r0 = d.x & ~3;
     const uint32_t bv = d.w > d.z ? round16((uint32_t)(d.w - a0) * 8u) : 0u;
     const uint32_t bc = d.w > d.z ? round16((uint32_t)(d.w - c0) * 2u) : 0u;
     const uint32_t br = round16((uint32_t)(d.y + 1 - r0) * 4u);
-    int2 rr[kRunMax];
+    const int2 rr[kRunMax] = {make_int2(tm.r01.x, tm.r01.y), make_int2(tm.r01.z, tm.r01.w),
+                              make_int2(tm.r23.x, tm.r23.y), make_int2(tm.r23.z, tm.r23.w)};
     uint32_t bx = 0;
 #pragma unroll
-    for (int k = 0; k < kRunMax; ++k) {
-        rr[k] = __ldg(runs + k);
-        bx += (uint32_t)rr[k].y * 8u;       // lengths are multiples of 4: 16-byte multiples
-    }
+    for (int k = 0; k < kRunMax; ++k) bx += (uint32_t)rr[k].y * 8u;   // lengths are multiples of 4
     mbar_expect_tx(bar, bv + bc + br + bx);
     if (bv) bulk_g2s(st->vals, vals + a0, bv, bar);
     if (bc) bulk_g2s(st->lcol, lcol + c0, bc, bar);
@@ -706,22 +739,25 @@ spmv_tiled_rw(const int4* __restrict__ tiles, const int2* __restrict__ runs, int
     int last_use[S];   // producer lane: the last use issued into each stage
     for (int k = 0; k < S; ++k) last_use[k] = -1;
     if (warp == kRwConsumers) {
-        // producer: lane 0 issues tile j into stage j % S once its previous use is released
-        if (lane == 0) {
-            for (int j = 0;; ++j) {
-                const int t = blockIdx.x + j * G;
-                if (t >= ntiles || failed) break;
+        // producer: lane 0 issues tile j into stage j % S once its previous use is released;
+        // the warp's lanes prefetch the tiles' metadata
+        TilePrefetch pf;
+        for (int j = 0;; ++j) {
+            const int t = blockIdx.x + j * G;
+            if (t >= ntiles || failed) break;
+            const TileMeta tm = pf.get(j, tiles, runs, ntiles, G, lane);
+            if (lane == 0) {
                 const int k = j % S, u = j / S;
                 if (u > 0 && !mbar_wait_bounded(&empty[k], (uint32_t)((u - 1) & 1))) {
                     failed = 1;
                     atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
-                    break;
+                } else {
+                    st[k].desc = tm.d;   // visible to the consumers through the stage's mbarrier
+                    tile_issue_r(tm, st + k, &full[k], rowptr, lcol, vals, x);
+                    last_use[k] = u;
                 }
-                const int4 d = __ldg(tiles + t);
-                st[k].desc = d;   // visible to the consumers through the stage's mbarrier (release/acquire)
-                tile_issue_r(d, runs + (size_t)t * kRunMax, st + k, &full[k], rowptr, lcol, vals, x);
-                last_use[k] = u;
             }
+            __syncwarp();
         }
     } else {
         const double s = (EPI == EPI_TAPIVOT) ? ctl->s : 0.0;
@@ -1124,20 +1160,19 @@ static_assert(offsetof(TileStageR32, vals) % 16 == 0 && offsetof(TileStageR32, l
               sizeof(TileStageR32) % 16 == 0, "bulk-copy destinations are 16-byte aligned");
 constexpr int kRw32Stages = 4, kRw32BlocksPerSM = 4;
 
-__device__ __forceinline__ void tile_issue_r32(const int4 d, const int2* __restrict__ runs, TileStageR32* st,
-                                               uint64_t* bar, const int32_t* rowptr, const uint16_t* lcol,
-                                               const float* vals, const float* x) {
+__device__ __forceinline__ void tile_issue_r32(const TileMeta& tm, TileStageR32* st, uint64_t* bar,
+                                               const int32_t* rowptr, const uint16_t* lcol, const float* vals,
+                                               const float* x) {
+    const int4 d = tm.d;
     const int a0 = d.z & ~3, c0 = d.z & ~7, r0 = d.x & ~3;
     const uint32_t bv = d.w > d.z ? round16((uint32_t)(d.w - a0) * 4u) : 0u;
     const uint32_t bc = d.w > d.z ? round16((uint32_t)(d.w - c0) * 2u) : 0u;
     const uint32_t br = round16((uint32_t)(d.y + 1 - r0) * 4u);
-    int2 rr[kRunMax];
+    const int2 rr[kRunMax] = {make_int2(tm.r01.x, tm.r01.y), make_int2(tm.r01.z, tm.r01.w),
+                              make_int2(tm.r23.x, tm.r23.y), make_int2(tm.r23.z, tm.r23.w)};
     uint32_t bx = 0;
 #pragma unroll
-    for (int k = 0; k < kRunMax; ++k) {
-        rr[k] = __ldg(runs + k);
-        bx += (uint32_t)rr[k].y * 4u;        // lengths are multiples of 4: 16-byte multiples
-    }
+    for (int k = 0; k < kRunMax; ++k) bx += (uint32_t)rr[k].y * 4u;   // lengths are multiples of 4
     mbar_expect_tx(bar, bv + bc + br + bx);
     if (bv) bulk_g2s(st->vals, vals + a0, bv, bar);
     if (bc) bulk_g2s(st->lcol, lcol + c0, bc, bar);
@@ -1178,21 +1213,23 @@ spmv32_tiled_rw(const int4* __restrict__ tiles, const int2* __restrict__ runs, i
     for (int k = 0; k < S; ++k) last_use[k] = -1;
     float acc = 0.0f;
     if (warp == kRwConsumers) {
-        if (lane == 0) {
-            for (int j = 0;; ++j) {
-                const int t = blockIdx.x + j * G;
-                if (t >= ntiles || failed) break;
+        TilePrefetch pf;
+        for (int j = 0;; ++j) {
+            const int t = blockIdx.x + j * G;
+            if (t >= ntiles || failed) break;
+            const TileMeta tm = pf.get(j, tiles, runs, ntiles, G, lane);
+            if (lane == 0) {
                 const int k = j % S, u = j / S;
                 if (u > 0 && !mbar_wait_bounded(&empty[k], (uint32_t)((u - 1) & 1))) {
                     failed = 1;
                     atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
-                    break;
+                } else {
+                    st[k].desc = tm.d;
+                    tile_issue_r32(tm, st + k, &full[k], rowptr, lcol, vals, x);
+                    last_use[k] = u;
                 }
-                const int4 d = __ldg(tiles + t);
-                st[k].desc = d;
-                tile_issue_r32(d, runs + (size_t)t * kRunMax, st + k, &full[k], rowptr, lcol, vals, x);
-                last_use[k] = u;
             }
+            __syncwarp();
         }
     } else {
         for (int j = 0;; ++j) {
