@@ -38,6 +38,15 @@ def banded(n, offsets, seed):
     return S
 
 
+def banded_with_empty_rows(n, seed):
+    """Tridiagonal-plus-far-band matrix with every 7th row and a block of 300 rows emptied."""
+    S = banded(n, [-700, -1, 0, 1, 700], seed).tolil()
+    for i in list(range(0, n, 7)) + list(range(10000, 10300)):
+        S.rows[i] = []
+        S.data[i] = []
+    return S.tocsr()
+
+
 def from_scipy(S, seed=0):
     rng = np.random.default_rng(seed + 100)
     S = S.tocsr()
@@ -58,6 +67,11 @@ STRUCTURES = {
     "five_runs": lambda: from_scipy(banded(20000, [-1000, -500, 0, 500, 1000], 1)),
     # four runs of 256 entries: more than a run stage holds -> x-window tiles
     "wide_runs": lambda: from_scipy(banded(20000, [-900, -300, 300, 900], 2)),
+    # rectangular banded (m != n; Aᵀ run-staged too)
+    "rect_banded": lambda: from_scipy(sp.diags([np.random.default_rng(5).standard_normal(20000)] * 3, [0, 700, 1500],
+                                               shape=(20000, 22000), format="csr")),
+    # banded with empty rows inside tiles
+    "holes": lambda: from_scipy(banded_with_empty_rows(30000, 7)),
     # unstructured short rows -> generic tiles
     "random_short": lambda: gen.random_csr(30000, 20000, density=6 / 20000, seed=3),
     # long rows -> warp per row
@@ -92,7 +106,7 @@ def test_products_match_scipy(tacta, name):
     plan.close()
 
 
-@pytest.mark.parametrize("name", ["five_runs", "wide_runs", "stencil_300"])
+@pytest.mark.parametrize("name", ["five_runs", "wide_runs", "stencil_300", "rect_banded", "holes"])
 def test_cta_trajectory_per_variant(tacta, name):
     """Four CTA steps (t = 1..4, 20 products) against the oracle on each banded variant."""
     import torch
