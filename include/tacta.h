@@ -123,6 +123,12 @@ typedef struct {
                                 step's moments phi_1..phi_{2j+1}, so the test is resolved for
                                 tol_normal down to ~1e-7 (below that its rounding, ~1e-16 phi_1,
                                 reaches the threshold)                                          */
+    int32_t fused_chain;     /* CTA on CSR operands whose A and Aᵀ both take the run-staged product
+                                (banded and stencil matrices): 1 (default) = the 2t products
+                                z_i = Aᵀ u_{i-1}, u_i = A z_i of a step (Alg. 1.1) and their moments
+                                run as one cooperative launch, the products separated by grid-wide
+                                barriers; 0 = one launch per product. Same arithmetic per row; the
+                                moments' partial sums are added in a different fixed order      */
     double rho_max;          /* ta_solve: stop (reason RHO_BOUND) once rho exceeds this; <= 0: none */
     void* stream;            /* cudaStream_t (NULL: legacy default stream)                      */
 } tacta_options;
@@ -152,7 +158,7 @@ typedef struct {
 
 /* Fill *opt with the defaults: tol 1e-10, tol_normal -1, tol_cta 0, pivot_tol 1e-12,
    max_iter 1000, t_max 5, ping-pong cycle, R = 40, use_graph 1, poll_every 64, profile 0,
-   precision FP64, nonneg 0, rho_max 0 (none), NULL stream. */
+   precision FP64, nonneg 0, enhanced 0, fused_chain 1, rho_max 0 (none), NULL stream. */
 void tacta_default_options(tacta_options* opt);
 
 /*

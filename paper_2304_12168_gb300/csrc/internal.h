@@ -34,7 +34,7 @@ struct Ctl {
     int32_t matvecs;       // products with A or Aᵀ made by the iteration (setup included)
     int32_t enhanced;      // CTA: the enhanced stop of Sec. 3.2 is on
     int32_t enh_stop;      // CTA: this step applies x^ and ends the solve (reason ENHANCED)
-    int32_t pad_;
+    uint32_t chain_bar;    // fused CTA chain: grid-wide arrivals (reset by the step's auxiliary kernel)
     double bn2;            // ||b||²  (b = rhs of the operator in use)
     double inv_bn2;        // 1 / ||b||² (0 when b = 0): the history stores ||r||² / ||b||²
     double mtbn2;          // ||Mᵀ b||²
@@ -197,8 +197,33 @@ cudaError_t launch_reduce_vec(const LaunchCtx& L, int64_t len, const double* a, 
 cudaError_t launch_ctl_init(const LaunchCtx& L, const Ctl& host_init);
 cudaError_t launch_copy_gated(const LaunchCtx& L, double* dst, const double* src, int64_t len, int gate);
 cudaError_t launch_fill(const LaunchCtx& L, double* dst, double v, int64_t len);
-cudaError_t launch_hist_sqrt(cudaStream_t s, double* h, int64_t len);
-cudaError_t launch_cta_aux_step(const LaunchCtx& L, int t);   // CTA step decision + auxiliary solve   // ||r||²/||b||² -> ||r||/||b||
+cudaError_t launch_hist_sqrt(cudaStream_t s, double* h, int64_t len);   // ||r||²/||b||² -> ||r||/||b||
+// CTA step decision + auxiliary solve; with part != nullptr the moments phi_1..phi_2t are
+// first summed from the fused chain's per-block partials (part[(i - 1) * G + block])
+cudaError_t launch_cta_aux_step(const LaunchCtx& L, int t, const double* part = nullptr, int G = 0);
+
+// The fused CTA chain (chain.cu): both operands run-staged; index 0 is Aᵀ, 1 is A.
+template <typename V>
+struct ChainOps {
+    const int4* tiles[2];
+    const int2* runs[2];
+    const int32_t* rowptr[2];
+    const uint16_t* lcol[2];
+    const V* vals[2];
+    int ntiles[2];
+};
+template <typename V>
+struct ChainVecs {
+    const V* r;          // u_0
+    V* z[kTMax];         // z_i = Aᵀ u_{i-1}
+    V* u[kTMax];         // u_i = A z_i
+};
+// blocks of the cooperative chain launch (all resident), 0 if it cannot run here
+int cta_chain_grid(int sms, int max_tiles, bool fp32);
+cudaError_t launch_cta_chain(const LaunchCtx& L, const ChainOps<double>& ops, const ChainVecs<double>& v, int t,
+                             double* part, int grid);
+cudaError_t launch_cta_chain32(const LaunchCtx& L, const ChainOps<float>& ops, const ChainVecs<float>& v, int t,
+                               float scale, double* part, int grid);
 
 // mixed precision (FP32 chain, FP64 refinement)
 cudaError_t launch_spmv32(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y, float scale,

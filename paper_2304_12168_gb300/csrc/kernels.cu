@@ -28,6 +28,7 @@
 #include "internal.h"
 #include "hankel.cuh"
 #include "mbarrier.cuh"
+#include "rowtiles.cuh"
 
 namespace tacta {
 
@@ -353,8 +354,6 @@ size_t spmv_tiled_smem(int cap) {
     return cap <= kTileCapSmall ? 2 * sizeof(TileStage<kTileCapSmall>) : 2 * sizeof(TileStage<kTileCapLarge>);
 }
 
-__device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15u; }
-
 // issue the bulk copies of tile d into stage st (one thread)
 template <int CAP>
 __device__ __forceinline__ void tile_issue(const int4 d, TileStage<CAP>* st, uint64_t* bar,
@@ -617,85 +616,6 @@ static cudaError_t spmv_tiled_x_launch(const LaunchCtx& L, const DevCSR& A, cons
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ run-staged variant
-//
-// Banded and stencil operands use only a few short runs of x per tile (a 5-point
-// stencil: the rows below, at and above the tile). Staging just those runs instead
-// of the whole window cuts the shared-memory footprint to ~21 KB per stage, and each
-// nonzero's column is stored as a 16-bit slot in the staged runs: 10 bytes per
-// nonzero from HBM instead of 12.
-
-struct __align__(16) TileStageR {
-    int4 desc;                       // the tile's descriptor (written by the producer)
-    double vals[kRunCap + 2];
-    uint16_t lcol[kRunCap + kPadLcol];
-    int32_t rp[kTileRows + 8];
-    double xs[kRunXs];
-};
-static_assert(sizeof(TileStageR) % 16 == 0, "stage size keeps 16-byte alignment");
-static_assert(offsetof(TileStageR, vals) % 16 == 0 && offsetof(TileStageR, lcol) % 16 == 0 &&
-              offsetof(TileStageR, rp) % 16 == 0 && offsetof(TileStageR, xs) % 16 == 0,
-              "bulk-copy destinations are 16-byte aligned");
-
-// A tile's descriptor and its kRunMax runs, as the producer warp prefetches them
-struct TileMeta {
-    int4 d;        // {row begin, row end, nnz begin, nnz end}
-    int4 r01, r23; // runs 0..3 as {first, length} pairs
-};
-
-__device__ __forceinline__ int4 shfl_int4(const int4 v, int src) {
-    return make_int4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
-                     __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
-}
-
-// Producer warp: lane i holds the metadata of the block's tile j0 + i, loaded 32 tiles at
-// a time, so that lane 0's copy issue never waits on a global load.
-struct TilePrefetch {
-    TileMeta m{};
-    int j0 = -32;
-    __device__ __forceinline__ TileMeta get(int j, const int4* __restrict__ tiles, const int2* __restrict__ runs,
-                                            int ntiles, int G, int lane) {
-        if (j - j0 >= 32) {
-            j0 = j;
-            const int tl = blockIdx.x + (j0 + lane) * G;
-            if (tl < ntiles) {
-                m.d = __ldg(tiles + tl);
-                const int4* r4 = reinterpret_cast<const int4*>(runs + (size_t)tl * kRunMax);
-                m.r01 = __ldg(r4);
-                m.r23 = __ldg(r4 + 1);
-            }
-        }
-        const int src = j - j0;
-        return TileMeta{shfl_int4(m.d, src), shfl_int4(m.r01, src), shfl_int4(m.r23, src)};
-    }
-};
-static_assert(kRunMax == 4, "TileMeta holds four runs");
-
-__device__ __forceinline__ void tile_issue_r(const TileMeta& tm, TileStageR* st, uint64_t* bar,
-                                             const int32_t* rowptr, const uint16_t* lcol, const double* vals,
-                                             const double* x) {
-    const int4 d = tm.d;
-    const int a0 = d.z & ~1, c0 = d.z & ~7, r0 = d.x & ~3;
-    const uint32_t bv = d.w > d.z ? round16((uint32_t)(d.w - a0) * 8u) : 0u;
-    const uint32_t bc = d.w > d.z ? round16((uint32_t)(d.w - c0) * 2u) : 0u;
-    const uint32_t br = round16((uint32_t)(d.y + 1 - r0) * 4u);
-    const int2 rr[kRunMax] = {make_int2(tm.r01.x, tm.r01.y), make_int2(tm.r01.z, tm.r01.w),
-                              make_int2(tm.r23.x, tm.r23.y), make_int2(tm.r23.z, tm.r23.w)};
-    uint32_t bx = 0;
-#pragma unroll
-    for (int k = 0; k < kRunMax; ++k) bx += (uint32_t)rr[k].y * 8u;   // lengths are multiples of 4
-    mbar_expect_tx(bar, bv + bc + br + bx);
-    if (bv) bulk_g2s(st->vals, vals + a0, bv, bar);
-    if (bc) bulk_g2s(st->lcol, lcol + c0, bc, bar);
-    bulk_g2s(st->rp, rowptr + r0, br, bar);
-    int off = 0;
-#pragma unroll
-    for (int k = 0; k < kRunMax; ++k) {
-        if (rr[k].y > 0) bulk_g2s(st->xs + off, x + rr[k].x, (uint32_t)rr[k].y * 8u, bar);
-        off += rr[k].y;
-    }
-}
-
 // ------------------------------------------------------------------ run-staged, warp-specialised
 //
 // Run-staged tiles without a block-wide barrier per tile: one producer warp
@@ -706,8 +626,6 @@ __device__ __forceinline__ void tile_issue_r(const TileMeta& tm, TileStageR* st,
 // all eight warps have released it. Warps drift apart instead of waiting for the
 // slowest one, which spreads shared-memory and FP64 issue over time.
 
-constexpr int kRwConsumers = kTileRows / 32;
-constexpr int kRwThreads = (kRwConsumers + 1) * 32;
 
 
 template <int S> constexpr int rw_blocks_per_sm() { return S == 2 ? 4 : 3; }
@@ -744,7 +662,7 @@ spmv_tiled_rw(const int4* __restrict__ tiles, const int2* __restrict__ runs, int
         TilePrefetch pf;
         for (int j = 0;; ++j) {
             const int t = blockIdx.x + j * G;
-            if (t >= ntiles || failed) break;
+            if (t >= ntiles || __any_sync(0xffffffffu, failed != 0)) break;   // one decision per warp
             const TileMeta tm = pf.get(j, tiles, runs, ntiles, G, lane);
             if (lane == 0) {
                 const int k = j % S, u = j / S;
@@ -765,26 +683,17 @@ spmv_tiled_rw(const int4* __restrict__ tiles, const int2* __restrict__ runs, int
             const int t = blockIdx.x + j * G;
             if (t >= ntiles) break;
             const int k = j % S;
-            if (failed || !mbar_wait_bounded(&full[k], (uint32_t)((j / S) & 1))) {
-                failed = 1;
-                atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+            const bool ok = !failed && mbar_wait_bounded(&full[k], (uint32_t)((j / S) & 1));
+            if (!__all_sync(0xffffffffu, ok)) {   // the warp takes one path
+                if (lane == 0) {
+                    failed = 1;
+                    atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+                }
                 break;
             }
-            const TileStageR* Sg = st + k;
-            const int4 d = Sg->desc;
-            const int row = d.x + warp * 32 + lane;
-            const bool active = row < d.y;
-            int kb = 0, len = 0;
-            if (active) {
-                const int r0 = d.x & ~3;
-                kb = Sg->rp[row - r0];
-                len = Sg->rp[row + 1 - r0] - kb;
-            }
-            const int maxlen = __reduce_max_sync(0xffffffffu, len);
-            const int vb = kb - (d.z & ~1), cb = kb - (d.z & ~7);
-            double sum = 0.0;
-            for (int u = 0; u < maxlen; ++u)
-                if (u < len) sum = fma(Sg->vals[vb + u], Sg->xs[Sg->lcol[cb + u]], sum);
+            int row;
+            bool active;
+            const double sum = rw_row_dot(st + k, warp, lane, row, active);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[k]);   // this warp is done with stage k
             if (active) epilogue<EPI>(row, sum, y, e, s, a0, a1);
@@ -1148,43 +1057,6 @@ spmv32_tiled(const int4* __restrict__ tiles, const int2* __restrict__ xwin, int 
 // FP32 run-staged product, warp-specialised (the mixed-precision chain): the FP64
 // operand's tiles, runs and 16-bit slots with the FP32 copy of the values; runs start
 // and end on multiples of 4 entries, so the FP32 x runs move in 16-byte units too.
-struct __align__(16) TileStageR32 {
-    int4 desc;
-    float vals[kRunCap + 4];
-    uint16_t lcol[kRunCap + kPadLcol];
-    int32_t rp[kTileRows + 8];
-    float xs[kRunXs];
-};
-static_assert(offsetof(TileStageR32, vals) % 16 == 0 && offsetof(TileStageR32, lcol) % 16 == 0 &&
-              offsetof(TileStageR32, rp) % 16 == 0 && offsetof(TileStageR32, xs) % 16 == 0 &&
-              sizeof(TileStageR32) % 16 == 0, "bulk-copy destinations are 16-byte aligned");
-constexpr int kRw32Stages = 4, kRw32BlocksPerSM = 4;
-
-__device__ __forceinline__ void tile_issue_r32(const TileMeta& tm, TileStageR32* st, uint64_t* bar,
-                                               const int32_t* rowptr, const uint16_t* lcol, const float* vals,
-                                               const float* x) {
-    const int4 d = tm.d;
-    const int a0 = d.z & ~3, c0 = d.z & ~7, r0 = d.x & ~3;
-    const uint32_t bv = d.w > d.z ? round16((uint32_t)(d.w - a0) * 4u) : 0u;
-    const uint32_t bc = d.w > d.z ? round16((uint32_t)(d.w - c0) * 2u) : 0u;
-    const uint32_t br = round16((uint32_t)(d.y + 1 - r0) * 4u);
-    const int2 rr[kRunMax] = {make_int2(tm.r01.x, tm.r01.y), make_int2(tm.r01.z, tm.r01.w),
-                              make_int2(tm.r23.x, tm.r23.y), make_int2(tm.r23.z, tm.r23.w)};
-    uint32_t bx = 0;
-#pragma unroll
-    for (int k = 0; k < kRunMax; ++k) bx += (uint32_t)rr[k].y * 4u;   // lengths are multiples of 4
-    mbar_expect_tx(bar, bv + bc + br + bx);
-    if (bv) bulk_g2s(st->vals, vals + a0, bv, bar);
-    if (bc) bulk_g2s(st->lcol, lcol + c0, bc, bar);
-    bulk_g2s(st->rp, rowptr + r0, br, bar);
-    int off = 0;
-#pragma unroll
-    for (int k = 0; k < kRunMax; ++k) {
-        if (rr[k].y > 0) bulk_g2s(st->xs + off, x + rr[k].x, (uint32_t)rr[k].y * 4u, bar);
-        off += rr[k].y;
-    }
-}
-
 template <int EPI>
 __global__ void __launch_bounds__(kRwThreads, kRw32BlocksPerSM)
 spmv32_tiled_rw(const int4* __restrict__ tiles, const int2* __restrict__ runs, int ntiles,
@@ -1216,7 +1088,7 @@ spmv32_tiled_rw(const int4* __restrict__ tiles, const int2* __restrict__ runs, i
         TilePrefetch pf;
         for (int j = 0;; ++j) {
             const int t = blockIdx.x + j * G;
-            if (t >= ntiles || failed) break;
+            if (t >= ntiles || __any_sync(0xffffffffu, failed != 0)) break;   // one decision per warp
             const TileMeta tm = pf.get(j, tiles, runs, ntiles, G, lane);
             if (lane == 0) {
                 const int k = j % S, u = j / S;
@@ -1225,7 +1097,7 @@ spmv32_tiled_rw(const int4* __restrict__ tiles, const int2* __restrict__ runs, i
                     atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
                 } else {
                     st[k].desc = tm.d;
-                    tile_issue_r32(tm, st + k, &full[k], rowptr, lcol, vals, x);
+                    tile_issue_r<float>(tm, st + k, &full[k], rowptr, lcol, vals, x);
                     last_use[k] = u;
                 }
             }
@@ -1236,24 +1108,17 @@ spmv32_tiled_rw(const int4* __restrict__ tiles, const int2* __restrict__ runs, i
             const int t = blockIdx.x + j * G;
             if (t >= ntiles) break;
             const int k = j % S;
-            if (failed || !mbar_wait_bounded(&full[k], (uint32_t)((j / S) & 1))) {
-                failed = 1;
-                atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+            const bool ok = !failed && mbar_wait_bounded(&full[k], (uint32_t)((j / S) & 1));
+            if (!__all_sync(0xffffffffu, ok)) {   // the warp takes one path
+                if (lane == 0) {
+                    failed = 1;
+                    atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+                }
                 break;
             }
-            const TileStageR32* Sg = st + k;
-            const int4 d = Sg->desc;
-            const int row = d.x + warp * 32 + lane;
-            const bool active = row < d.y;
-            int kb = 0, len = 0;
-            if (active) {
-                const int r0 = d.x & ~3;
-                kb = Sg->rp[row - r0];
-                len = Sg->rp[row + 1 - r0] - kb;
-            }
-            const int vb = kb - (d.z & ~3), cb = kb - (d.z & ~7);
-            float sum = 0.0f;
-            for (int u = 0; u < len; ++u) sum = fmaf(Sg->vals[vb + u], Sg->xs[Sg->lcol[cb + u]], sum);
+            int row;
+            bool active;
+            float sum = rw_row_dot(st + k, warp, lane, row, active);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[k]);
             if (active) {
@@ -1598,7 +1463,22 @@ __device__ bool enhanced_stop(Ctl* c, int t) {
     return false;
 }
 
-__global__ void cta_aux_step(Ctl* c, int t) {
+__global__ void __launch_bounds__(384) cta_aux_step(Ctl* c, int t, const double* part, int G) {
+    if (part != nullptr) {
+        // fused chain: a warp sums the per-block partials of phi_{w+1} (lane-strided, then
+        // a shuffle tree: a fixed order), and the grid-wide counter starts over
+        const int lane = threadIdx.x & 31;
+        if (threadIdx.x == 0) c->chain_bar = 0;
+        if (c->status == 0) {
+            for (int w = threadIdx.x >> 5; w < 2 * t; w += blockDim.x >> 5) {
+                double s = 0.0;
+                for (int i = lane; i < G; i += 32) s += part[(size_t)w * G + i];
+                s = warp_sum(s);
+                if (lane == 0) c->phi[w + 1] = s;
+            }
+        }
+        __syncthreads();
+    }
     if (threadIdx.x != 0 || c->status != 0) return;
     for (int i = 1; i <= 2 * t; ++i)
         if (!finite(c->phi[i])) { c->status = TACTA_REASON_NONFINITE; return; }
@@ -1608,8 +1488,9 @@ __global__ void cta_aux_step(Ctl* c, int t) {
     if (c->rank == 0) c->status = TACTA_REASON_BREAKDOWN;
 }
 
-cudaError_t launch_cta_aux_step(const LaunchCtx& L, int t) {
-    cta_aux_step<<<1, 32, 0, L.stream>>>(L.ctl, t);
+cudaError_t launch_cta_aux_step(const LaunchCtx& L, int t, const double* part, int G) {
+    // 12 warps for the moment sums: the solve's registers (~134 per thread) allow 384 threads
+    cta_aux_step<<<1, part ? 384 : 32, 0, L.stream>>>(L.ctl, t, part, G);
     if (L.launches) ++*L.launches;
     return cudaGetLastError();
 }

@@ -88,8 +88,14 @@ struct Plan {
     int g_cta32_key = -1;
     int64_t g_cta32_launches = 0;
     int g_cta32_iters = 0;
+    // fused chain (A and Aᵀ both run-staged): blocks of the cooperative launch per
+    // precision (0: not available) and the per-block moment partials
+    int chain_grid = 0, chain_grid32 = 0;
+    double* chain_part = nullptr;    // 2 kTMax x max(chain_grid, chain_grid32)
+    bool fused = false;              // this call runs the fused chain
     // opt-in profiling of the iteration's products (events around each launch)
     bool profiling = false;
+    int prof_count = 0;
     std::vector<cudaEvent_t> pev;
     size_t pev_used = 0;
     double prof_bytes = 0.0;
@@ -119,6 +125,7 @@ static cudaError_t chain_spmv(Plan* p, const LaunchCtx& L, const DevOperand& A, 
     if ((err = cudaEventRecord(p->pev[p->pev_used + 1], L.stream)) != cudaSuccess) return err;
     p->pev_used += 2;
     p->prof_bytes += spmv_bytes(A);
+    p->prof_count += 1;
     return cudaSuccess;
 }
 
@@ -126,6 +133,7 @@ static void prof_begin(Plan* p, int profile) {
     p->profiling = profile != 0;
     p->pev_used = 0;
     p->prof_bytes = 0.0;
+    p->prof_count = 0;
 }
 
 static void prof_end(Plan* p, tacta_info* info) {
@@ -136,7 +144,7 @@ static void prof_end(Plan* p, tacta_info* info) {
         float t = 0.f;
         if (cudaEventElapsedTime(&t, p->pev[i], p->pev[i + 1]) == cudaSuccess) ms += t;
     }
-    info->spmv_count = (int32_t)(p->pev_used / 2);
+    info->spmv_count = p->prof_count;
     info->spmv_ms = ms;
     info->spmv_bytes = p->prof_bytes;
     p->profiling = false;
@@ -166,7 +174,7 @@ static void plan_free(Plan* p) {
     F(p->A.dense.vals);
     F(p->At.csr.rowptr); F(p->At.csr.colidx); F(p->At.csr.vals); F(p->At.csr.tiles); F(p->At.csr.xwin); F(p->At.csr.runs); F(p->At.csr.lcol);
     F(p->At.dense.vals);
-    F(p->ctl); F(p->partials); F(p->flag_dev);
+    F(p->ctl); F(p->partials); F(p->flag_dev); F(p->chain_part);
     F(p->b); F(p->x); F(p->r); F(p->tmp_m); F(p->tmp_n);
     for (int i = 0; i < kTMax; ++i) { F(p->z[i]); F(p->u[i]); }
     F(p->d); F(p->c); F(p->v); F(p->bt); F(p->xbest); F(p->wx); F(p->wd); F(p->hist);
@@ -416,6 +424,14 @@ static tacta_status plan_create(const tacta_matrix* M, const tacta_options* opt,
         PTRY(csr_transpose(s, a, p->At.csr));
         PTRY(setup_csr_kernel(a, s));
         PTRY(setup_csr_kernel(p->At.csr, s));
+        const DevCSR& at = p->At.csr;
+        if (a.cfg.kind == 3 && a.lcol && at.cfg.kind == 3 && at.lcol) {
+            const int tiles = std::max(a.ntiles, at.ntiles);
+            p->chain_grid = cta_chain_grid(p->sms, tiles, false);
+            p->chain_grid32 = cta_chain_grid(p->sms, tiles, true);
+            const int g = std::max(p->chain_grid, p->chain_grid32);
+            if (g > 0) PTRY(cudaMalloc(&p->chain_part, sizeof(double) * 2 * kTMax * g));
+        }
     } else {
         p->A.format = p->At.format = TACTA_DENSE;
         DevDense& a = p->A.dense;
@@ -531,6 +547,34 @@ static tacta_status ensure_mixed(Plan* p, int t_max, cudaStream_t s) {
     return TACTA_OK;
 }
 
+template <typename V>
+static ChainOps<V> chain_ops(const DevCSR& At, const DevCSR& A, const V* at_vals, const V* a_vals) {
+    ChainOps<V> o;
+    const DevCSR* op[2] = {&At, &A};
+    for (int i = 0; i < 2; ++i) {
+        o.tiles[i] = op[i]->tiles;
+        o.runs[i] = op[i]->runs;
+        o.rowptr[i] = op[i]->rowptr;
+        o.lcol[i] = op[i]->lcol;
+        o.ntiles[i] = op[i]->ntiles;
+    }
+    o.vals[0] = at_vals;
+    o.vals[1] = a_vals;
+    return o;
+}
+
+// events around the fused chain when profiling: it counts as its 2t products
+static cudaError_t prof_mark(Plan* p, const LaunchCtx& L) {
+    if (!p->profiling) return cudaSuccess;
+    while (p->pev.size() < p->pev_used + 1) {
+        cudaEvent_t ev;
+        cudaError_t err = cudaEventCreate(&ev);
+        if (err != cudaSuccess) return err;
+        p->pev.push_back(ev);
+    }
+    return cudaEventRecord(p->pev[p->pev_used++], L.stream);
+}
+
 // One F_t step, mixed precision: FP32 chain and update, then (gated on the device)
 // the refinement: fold the FP32 correction into the FP64 x and recompute the true
 // residual b - A x with the FP64 product, stored back into the FP32 residual.
@@ -548,6 +592,7 @@ static cudaError_t chain_spmv32(Plan* p, const LaunchCtx& L, const DevCSR32& A, 
     if ((err = launch_spmv32(L, A, x, y, p->chain_scale, EPI_NORM, f, GATE_ALWAYS)) != cudaSuccess) return err;
     if ((err = cudaEventRecord(p->pev[p->pev_used + 1], L.stream)) != cudaSuccess) return err;
     p->pev_used += 2;
+    p->prof_count += 1;
     const DevCSR& a = *A.base;
     p->prof_bytes += 8.0 * (double)a.nnz + 4.0 * (double)(a.rows + 1) + 4.0 * (double)a.cols + 4.0 * (double)a.rows;
     return cudaSuccess;
@@ -555,15 +600,32 @@ static cudaError_t chain_spmv32(Plan* p, const LaunchCtx& L, const DevCSR32& A, 
 
 static cudaError_t enqueue_cta32_iter(Plan* p, const LaunchCtx& L, int t) {
     cudaError_t e;
-    const float* uprev = p->r32;
-    for (int i = 0; i < t; ++i) {
-        if ((e = chain_spmv32(p, L, p->At32, uprev, p->z32[i], FinArgs{FIN_PHI, 2 * i + 1, nullptr})) != cudaSuccess)
-            return e;
-        if ((e = chain_spmv32(p, L, p->A32, p->z32[i], p->u32[i], FinArgs{FIN_PHI, 2 * i + 2, nullptr})) !=
-            cudaSuccess) return e;
-        uprev = p->u32[i];
+    if (p->fused) {
+        ChainVecs<float> v;
+        v.r = p->r32;
+        for (int i = 0; i < kTMax; ++i) { v.z[i] = p->z32[i]; v.u[i] = p->u32[i]; }
+        if ((e = prof_mark(p, L)) != cudaSuccess) return e;
+        if ((e = launch_cta_chain32(L, chain_ops<float>(p->At.csr, p->A.csr, p->At32.vals, p->A32.vals), v, t,
+                                    p->chain_scale, p->chain_part, p->chain_grid32)) != cudaSuccess) return e;
+        if ((e = prof_mark(p, L)) != cudaSuccess) return e;
+        if (p->profiling) {
+            for (const DevCSR* a : {&p->At.csr, &p->A.csr})
+                p->prof_bytes += t * (8.0 * (double)a->nnz + 4.0 * (double)(a->rows + 1) + 4.0 * (double)a->cols +
+                                      4.0 * (double)a->rows);
+            p->prof_count += 2 * t;
+        }
+        if ((e = launch_cta_aux_step(L, t, p->chain_part, p->chain_grid32)) != cudaSuccess) return e;
+    } else {
+        const float* uprev = p->r32;
+        for (int i = 0; i < t; ++i) {
+            if ((e = chain_spmv32(p, L, p->At32, uprev, p->z32[i], FinArgs{FIN_PHI, 2 * i + 1, nullptr})) !=
+                cudaSuccess) return e;
+            if ((e = chain_spmv32(p, L, p->A32, p->z32[i], p->u32[i], FinArgs{FIN_PHI, 2 * i + 2, nullptr})) !=
+                cudaSuccess) return e;
+            uprev = p->u32[i];
+        }
+        if ((e = launch_cta_aux_step(L, t)) != cudaSuccess) return e;
     }
-    if ((e = launch_cta_aux_step(L, t)) != cudaSuccess) return e;
     if ((e = launch_cta_update32(L, t, p->m, p->n, p->dx32, p->r32, p->z32, p->u32, p->chain_scale,
                                  FinArgs{FIN_CTA_UPDATE, 0, p->hist})) != cudaSuccess) return e;
     if ((e = launch_fold_correction(L, p->n, p->x, p->dx32, GATE_NEED_TRUE)) != cudaSuccess) return e;
@@ -608,6 +670,24 @@ static int schedule_period(int t_max, int cycle) {
 
 static cudaError_t enqueue_cta_iter(Plan* p, const LaunchCtx& L, int t) {
     cudaError_t e;
+    if (p->fused) {
+        ChainVecs<double> v;
+        v.r = p->r;
+        for (int i = 0; i < kTMax; ++i) { v.z[i] = p->z[i]; v.u[i] = p->u[i]; }
+        if ((e = prof_mark(p, L)) != cudaSuccess) return e;
+        if ((e = launch_cta_chain(L, chain_ops<double>(p->At.csr, p->A.csr, p->At.csr.vals, p->A.csr.vals), v, t,
+                                  p->chain_part, p->chain_grid)) != cudaSuccess) return e;
+        if ((e = prof_mark(p, L)) != cudaSuccess) return e;
+        if (p->profiling) {
+            p->prof_bytes += t * (spmv_bytes(p->At) + spmv_bytes(p->A));
+            p->prof_count += 2 * t;
+        }
+        if ((e = launch_cta_aux_step(L, t, p->chain_part, p->chain_grid)) != cudaSuccess) return e;
+        if ((e = launch_cta_update(L, t, p->m, p->n, p->x, p->r, p->z, p->u,
+                                   FinArgs{FIN_CTA_UPDATE, 0, p->hist})) != cudaSuccess) return e;
+        return launch_spmv(L, p->A, p->x, p->r, EPI_RESID, EpiArgs{p->b, nullptr, nullptr},
+                           FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE);
+    }
     const double* uprev = p->r;
     EpiArgs none{nullptr, nullptr, nullptr};
     for (int i = 0; i < t; ++i) {
@@ -846,7 +926,8 @@ static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t h
     }
     const int t_max = O.o.t_max, cycle = O.o.cycle;
     const int period = schedule_period(t_max, cycle);
-    const int key = t_max * 4 + cycle;
+    p->fused = O.o.fused_chain != 0 && (mixed ? p->chain_grid32 : p->chain_grid) > 0;
+    const int key = (t_max * 4 + cycle) * 2 + (p->fused ? 1 : 0);
     cudaGraphExec_t* g = mixed ? &p->g_cta32 : &p->g_cta;
     int* gkey = mixed ? &p->g_cta32_key : &p->g_cta_key;
     if (*g && *gkey != key) {
@@ -1127,6 +1208,7 @@ void tacta_default_options(tacta_options* o) {
     o->profile = 0;
     o->precision = TACTA_PRECISION_FP64;
     o->nonneg = 0;
+    o->fused_chain = 1;
     o->rho_max = 0.0;
     o->stream = nullptr;
 }

@@ -1,0 +1,136 @@
+"""The fused CTA chain (all 2t products of a step in one cooperative launch) against the
+oracle and against the one-launch-per-product path (needs a GB300).
+
+Both paths compute every row of every product with the same arithmetic; only the
+moments' partial sums are added in another fixed order. So fixed trajectories match
+the oracle as the per-product path does, the two paths agree closely with each other,
+and the fused path is deterministic (graph replay equals direct launches bit for bit).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tacta():
+    import torch
+    import paper_2304_12168_gb300 as t
+    t.load_library()
+    torch.cuda.set_device(0)
+    return t
+
+
+def from_scipy(S, seed):
+    S = sp.csr_matrix(S)
+    S.sort_indices()
+    rng = np.random.default_rng(seed)
+    b = S @ rng.standard_normal(S.shape[1])
+    return gen.Problem(name="s", m=S.shape[0], n=S.shape[1], fmt="csr",
+                       rowptr=S.indptr.astype(np.int32), colidx=S.indices.astype(np.int32),
+                       vals=S.data.astype(np.float64), b=b)
+
+
+def rect_banded():
+    """20000 x 22000, three diagonals at offsets 0, 700, 1500: A has 79 tiles, Aᵀ 86 (both
+    ragged), so the grid is 86 blocks and some blocks have no tile of A."""
+    rng = np.random.default_rng(11)
+    return from_scipy(sp.diags([rng.standard_normal(20000)] * 3, [0, 700, 1500], shape=(20000, 22000)), 12)
+
+
+CASES = {
+    "stencil_24": lambda: gen.convdiff_stencil(24),      # 576 rows: 3 tiles, 3 blocks
+    "stencil_300": lambda: gen.convdiff_stencil(300),    # 90000 rows: 352 tiles per product
+    "rect_banded": rect_banded,
+    "clement_5001": lambda: gen.clement(5001),
+}
+
+
+def dev(p):
+    import torch
+    import paper_2304_12168_gb300 as t
+    d = torch.device("cuda:0")
+    return (t.CSR(torch.from_numpy(p.rowptr).to(d), torch.from_numpy(p.colidx).to(d),
+                  torch.from_numpy(p.vals).to(d), (p.m, p.n)),
+            torch.from_numpy(np.ascontiguousarray(p.b)).to(d))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fused_trajectory_matches_oracle(tacta, name):
+    """40 F_t steps (ping-pong t = 1..5 and back) on the fused path: iterations, products,
+    x (1e-9) and the residual history (1e-8) against the oracle; the fused path launched
+    fewer kernels than the per-product path on the same run."""
+    p = CASES[name]()
+    A, b = dev(p)
+    opts = dict(tol=1e-30, tol_normal=0.0, max_iter=40)
+    x, hist, info = tacta.cta_solve(A, b, fused_chain=1, **opts)
+    _, _, info0 = tacta.cta_solve(A, b, fused_chain=0, **opts)
+    ref = oracle.cta_solve(oracle.make_operator(p), p.b, **opts)
+    assert info["iters"] == ref.iters == 40 and info["matvecs"] == ref.matvecs == info0["matvecs"]
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+    np.testing.assert_allclose(hist.cpu().numpy(), ref.hist, rtol=1e-8)
+    assert info["launches"] < info0["launches"]
+
+
+@pytest.mark.parametrize("name", ["stencil_300", "rect_banded"])
+def test_fused_equals_per_product_path(tacta, name):
+    """The two paths differ only in the order of the moments' partial sums (relative
+    differences ~1e-16), which the t x t centering solve amplifies by its condition
+    number: two steps (t = 1, 2) agree to 1e-13, four (t up to 4, condition ~1e5 on the
+    stencil) to 1e-10."""
+    p = CASES[name]()
+    A, b = dev(p)
+    for steps, tol in ((2, 1e-13), (4, 1e-10)):
+        opts = dict(tol=1e-30, tol_normal=0.0, max_iter=steps)
+        x1, h1, _ = tacta.cta_solve(A, b, fused_chain=1, **opts)
+        x0, h0, _ = tacta.cta_solve(A, b, fused_chain=0, **opts)
+        x1, x0 = x1.cpu().numpy(), x0.cpu().numpy()
+        assert np.linalg.norm(x1 - x0) <= tol * np.linalg.norm(x0), steps
+        np.testing.assert_allclose(h1.cpu().numpy(), h0.cpu().numpy(), rtol=tol)
+
+
+def test_fused_graph_replay_is_bitwise_deterministic(tacta):
+    """Graph replay and direct launches of the fused chain give identical bits."""
+    p = CASES["stencil_300"]()
+    A, b = dev(p)
+    opts = dict(tol=1e-30, tol_normal=0.0, max_iter=100)
+    xa, ha, _ = tacta.cta_solve(A, b, use_graph=1, **opts)
+    xb, hb, _ = tacta.cta_solve(A, b, use_graph=1, **opts)
+    xc, hc, _ = tacta.cta_solve(A, b, use_graph=0, **opts)
+    assert np.array_equal(xa.cpu().numpy(), xb.cpu().numpy())
+    assert np.array_equal(xa.cpu().numpy(), xc.cpu().numpy())
+    assert np.array_equal(ha.cpu().numpy(), hc.cpu().numpy())
+
+
+def test_fused_mixed_precision(tacta):
+    """Mixed precision on the fused FP32 chain: over the first steps its history follows
+    the per-product FP32 path (same FP32 products, moments summed in another order), and
+    the refined solve reaches 1e-12 with x within 1e-9 of the exact solution (x* = 1)."""
+    p = gen.convdiff_stencil(40)
+    A, b = dev(p)
+    _, h1, _ = tacta.cta_solve(A, b, tol=1e-30, tol_normal=0.0, max_iter=8,
+                               precision=tacta.PRECISION_MIXED, fused_chain=1)
+    _, h0, _ = tacta.cta_solve(A, b, tol=1e-30, tol_normal=0.0, max_iter=8,
+                               precision=tacta.PRECISION_MIXED, fused_chain=0)
+    np.testing.assert_allclose(h1.cpu().numpy(), h0.cpu().numpy(), rtol=1e-5)
+    x, _, info = tacta.cta_solve(A, b, tol=1e-12, tol_normal=0.0, max_iter=200000,
+                                 precision=tacta.PRECISION_MIXED, fused_chain=1)
+    assert info["reason_name"] == "RESIDUAL" and info["rel_res"] <= 1e-12
+    assert np.abs(x.cpu().numpy() - 1.0).max() <= 1e-9
+
+
+def test_fused_profile_counts_products(tacta):
+    """profile = 1 times the fused launch as its 2t products: counts and bytes match the
+    per-product path's."""
+    p = CASES["stencil_300"]()
+    A, b = dev(p)
+    opts = dict(tol=1e-30, tol_normal=0.0, max_iter=8, profile=1)
+    _, _, i1 = tacta.cta_solve(A, b, fused_chain=1, **opts)
+    _, _, i0 = tacta.cta_solve(A, b, fused_chain=0, **opts)
+    assert i1["spmv_count"] == i0["spmv_count"] == 2 * (1 + 2 + 3 + 4 + 5 + 4 + 3 + 2)
+    assert i1["spmv_bytes"] == pytest.approx(i0["spmv_bytes"], rel=1e-12)
+    assert i1["spmv_ms"] > 0
