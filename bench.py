@@ -13,9 +13,11 @@ value      : F_t iterations per second over the K timed steps (device events),
 e2e        : same metric through the one-shot C ABI call with host buffers
              (pinned): A and b copied in, plan built (device transpose), solve,
              x and the residual history copied out, all inside the timed region.
-roofline   : the iteration's products (CSR SpMV with A and Aᵀ), timed one by one
-             with CUDA events inside a profiled solve of the same workload;
-             algorithmic bytes per product = 12 nnz + 4 (rows+1) + 8 cols + 8 rows.
+roofline   : the fused chain kernel (the 2t CSR products with Aᵀ and A of each F_t
+             step in one cooperative launch), timed with CUDA events around every
+             launch inside a profiled solve of the same workload; reported per product
+             (a launch's bytes and time over its 2t products); algorithmic bytes per
+             product = 12 nnz + 4 (rows+1) + 8 cols + 8 rows.
 cpu_baseline: the FP64 numpy oracle on the same workload, a bounded sample of
              CPU_SAMPLE_ITERS iterations.
 
@@ -57,27 +59,28 @@ def peaks():
 
 
 def kernel_source_hash():
-    """sha256 of the dominant product's source: its stage layout, copy issue and kernel
-    (comment lines dropped) plus the mbarrier helpers it uses."""
+    """sha256 of the dominant kernel's source: the fused chain (chain.cu), the row-tile
+    stages and copy issue it uses (rowtiles.cuh) and the mbarrier helpers, comment lines
+    dropped."""
     csrc = os.path.join(ROOT, "paper_2304_12168_gb300", "csrc")
-    src = open(os.path.join(csrc, "kernels.cu")).read()
-    a = src.index("struct __align__(16) TileStageR {")
-    b = src.index("template <int S>\nsize_t spmv_tiled_rw_smem()")
-    code = "\n".join(l for l in src[a:b].splitlines() if not l.strip().startswith("//"))
-    code += open(os.path.join(csrc, "mbarrier.cuh")).read()
+    code = ""
+    for f in ("chain.cu", "rowtiles.cuh", "mbarrier.cuh"):
+        src = open(os.path.join(csrc, f)).read()
+        code += "\n".join(l for l in src.splitlines() if not l.strip().startswith("//"))
     return hashlib.sha256(code.encode()).hexdigest()
 
 
 def traffic_record():
-    """dram bytes per launch of the product from the committed ncu capture, if the
-    kernel's source is unchanged since it was taken (else None)."""
-    path = os.path.join(ROOT, "profiles", "spmv_traffic.json")
+    """dram bytes per product of the fused chain (a launch's bytes over its 2t products)
+    from the committed ncu capture, if the kernel's source is unchanged since it was
+    taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "chain_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
         if kernel_source_hash() != rec.get("kernel_source_sha256"):
             return None
-        return float(rec["dram_bytes_per_launch_full_size"])
+        return float(rec["dram_bytes_per_product_full_size"])
     except Exception:
         return None
 
@@ -193,6 +196,16 @@ def extra_workloads(tacta, dev, stream, plan_stencil, b_stencil, steps):
         torch.cuda.synchronize()
         ta_ms += e0.elapsed_time(e1)
         ta_its += info["iters"]
+    # the same FP64 CTA solve with one launch per product (fused_chain = 0), for comparison
+    kw0 = dict(tol=TOL, tol_normal=0.0, max_iter=ITERS_PER_STEP, fused_chain=0)
+    plan_stencil.cta(b_stencil, **kw0)
+    u_ms, u_its = 0.0, 0
+    for _ in range(steps):
+        t, _, info0 = timed_solve(plan_stencil, b_stencil, stream, **kw0)
+        u_ms += t
+        u_its += info0["iters"]
+    out["cta_fp64_per_product_launches"] = {"value": u_its / (u_ms * 1e-3), "unit": UNIT, "steps": steps,
+                                            "iters_per_step": ITERS_PER_STEP, "launches_per_step": info0["launches"]}
     out["ta_fp64_convdiff_1000x1000"] = {"value": ta_its / (ta_ms * 1e-3), "unit": "TA iterations/s",
                                          "steps": steps, "iters_per_step": ITERS_PER_STEP,
                                          "rel_res_after_step": info["rel_res"]}
@@ -467,10 +480,14 @@ def main():
     peak, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic_record(),
-                "kernel": "spmv_tiled_rw<3, EPI_NORM> (run-staged TMA row tiles, warp-specialised; A and Aᵀ products of the F_t chain)",
-                "launches_timed": prof["spmv_count"], "avg_launch_us": spmv_us,
-                "bytes_per_launch": spmv_bytes, "peak_kind": peak_kind,
-                "fp64_fma_per_launch": (p.nnz + p.m),
+                "kernel": "cta_chain_rw<double> (the F_t step's 2t products with Aᵀ and A in one "
+                          "cooperative launch: run-staged bulk-copy row tiles, warp-specialised, "
+                          "grid-wide barriers between products)",
+                "unit_of_work": "one product of the chain (2t per launch); achieved = bytes of the "
+                                "timed launches' products / their summed duration",
+                "products_timed": prof["spmv_count"], "avg_product_us": spmv_us,
+                "bytes_per_product": spmv_bytes, "peak_kind": peak_kind,
+                "fp64_fma_per_product": (p.nnz + p.m),
                 "fp64_fma_frac_of_nominal": (p.nnz + p.m) / (spmv_us * 1e-6) / 0.629e12}
 
     # ---------------- e2e: one-shot C ABI call with pinned host buffers
