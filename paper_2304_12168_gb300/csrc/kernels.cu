@@ -855,13 +855,13 @@ template <int T>
 __global__ void __launch_bounds__(kBlock)
 cta_update(int64_t m, int64_t n, double* __restrict__ x, double* __restrict__ r, VecPtrs z,
            VecPtrs u, Ctl* ctl, double* partials, FinArgs f) {
+    const int64_t len = m > n ? m : n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (ctl->status != 0) return;
     double al[T];
 #pragma unroll
     for (int j = 0; j < T; ++j) al[j] = ctl->alpha[j];
     double a0 = 0.0;
-    const int64_t len = m > n ? m : n;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
         if (i < n) {
             double v = x[i];
@@ -1259,6 +1259,8 @@ template <int T>
 __global__ void __launch_bounds__(kBlock)
 cta_update32(int64_t m, int64_t n, float* __restrict__ dx, float* __restrict__ r, F32Ptrs z, F32Ptrs u,
              float xscale, Ctl* ctl, double* partials, FinArgs f) {
+    const int64_t len = m > n ? m : n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (ctl->status != 0) return;
     // the chain vectors are scaled (z_i by s^(2i-1), u_i by s^(2i), s = xscale a power of
     // two), so the solve on the scaled moments gives beta with x += s sum beta_i z_i,
@@ -1270,8 +1272,6 @@ cta_update32(int64_t m, int64_t n, float* __restrict__ dx, float* __restrict__ r
         ax[j] = (float)(ctl->alpha[j] * (double)xscale);
     }
     float acc = 0.0f;
-    const int64_t len = m > n ? m : n;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
         if (i < n) {
             float v = dx[i];
@@ -1463,29 +1463,62 @@ __device__ bool enhanced_stop(Ctl* c, int t) {
     return false;
 }
 
+// The step decision and auxiliary solve (one thread, FP64), in its own kernel so that
+// the solve's registers stay out of the streaming kernels. The control block is staged
+// in shared memory by all threads at once, so the one-thread solve works on shared-
+// memory loads instead of a chain of dependent global loads.
 __global__ void __launch_bounds__(384) cta_aux_step(Ctl* c, int t, const double* part, int G) {
+    __shared__ Ctl sc;
+    static_assert(sizeof(Ctl) % 8 == 0, "the control block copies as 8-byte words");
+    {
+        const uint64_t* src = reinterpret_cast<const uint64_t*>(c);
+        uint64_t* dst = reinterpret_cast<uint64_t*>(&sc);
+        for (int i = threadIdx.x; i < (int)(sizeof(Ctl) / 8); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    if (part != nullptr && threadIdx.x == 0) c->chain_bar = 0;   // the fused chain's counter starts over
+    if (sc.status != 0) return;
     if (part != nullptr) {
-        // fused chain: a warp sums the per-block partials of phi_{w+1} (lane-strided, then
-        // a shuffle tree: a fixed order), and the grid-wide counter starts over
+        // fused chain: a warp sums the per-block partials of phi_{w+1} (lane-strided with
+        // two accumulators, then a shuffle tree: a fixed order)
         const int lane = threadIdx.x & 31;
-        if (threadIdx.x == 0) c->chain_bar = 0;
-        if (c->status == 0) {
-            for (int w = threadIdx.x >> 5; w < 2 * t; w += blockDim.x >> 5) {
-                double s = 0.0;
-                for (int i = lane; i < G; i += 32) s += part[(size_t)w * G + i];
-                s = warp_sum(s);
-                if (lane == 0) c->phi[w + 1] = s;
+        for (int w = threadIdx.x >> 5; w < 2 * t; w += blockDim.x >> 5) {
+            const double* pw = part + (size_t)w * G;
+            double s0 = 0.0, s1 = 0.0;
+            int i = lane;
+#pragma unroll 4
+            for (; i + 32 < G; i += 64) {
+                s0 += pw[i];
+                s1 += pw[i + 32];
+            }
+            if (i < G) s0 += pw[i];
+            const double s = warp_sum(s0 + s1);
+            if (lane == 0) {
+                sc.phi[w + 1] = s;
+                c->phi[w + 1] = s;
             }
         }
         __syncthreads();
     }
-    if (threadIdx.x != 0 || c->status != 0) return;
+    if (threadIdx.x != 0) return;
+    int status = 0;
     for (int i = 1; i <= 2 * t; ++i)
-        if (!finite(c->phi[i])) { c->status = TACTA_REASON_NONFINITE; return; }
-    if (c->phi[1] <= __dmul_rn(c->nrm_thr, c->cs2)) { c->status = TACTA_REASON_NORMAL; return; }
-    if (c->enhanced && t >= 2 && enhanced_stop(c, t)) return;
-    c->rank = hankel_solve_dev(c->phi, t, c->pivot_tol, c->alpha);
-    if (c->rank == 0) c->status = TACTA_REASON_BREAKDOWN;
+        if (!finite(sc.phi[i])) status = TACTA_REASON_NONFINITE;
+    if (status == 0 && sc.phi[1] <= __dmul_rn(sc.nrm_thr, sc.cs2)) status = TACTA_REASON_NORMAL;
+    if (status != 0) {
+        c->status = status;
+        return;
+    }
+    if (sc.enhanced && t >= 2 && enhanced_stop(&sc, t)) {
+        for (int k = 0; k < t; ++k) c->alpha[k] = sc.alpha[k];
+        c->rank = sc.rank;
+        c->enh_stop = 1;
+        return;
+    }
+    const int rank = hankel_solve_dev(sc.phi, t, sc.pivot_tol, sc.alpha);
+    for (int k = 0; k < t; ++k) c->alpha[k] = sc.alpha[k];
+    c->rank = rank;
+    if (rank == 0) c->status = TACTA_REASON_BREAKDOWN;
 }
 
 cudaError_t launch_cta_aux_step(const LaunchCtx& L, int t, const double* part, int G) {
