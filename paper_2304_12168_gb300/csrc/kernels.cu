@@ -211,17 +211,33 @@ __device__ void reduce_and_finish(double a0, double a1, Ctl* ctl, double* partia
     __syncthreads();
     if (!am_last) return;
     __threadfence();
+    // the finisher runs on one thread against a shared-memory copy of the control block,
+    // loaded and stored by the block's threads at once (its logic reads and writes a
+    // dozen fields; as dependent global accesses that chain took microseconds)
+    __shared__ Ctl sc;
+    constexpr int kWords = (int)(sizeof(Ctl) / 8);
+    static_assert(sizeof(Ctl) % 8 == 0 && kWords <= NT, "the control block copies as one word per thread");
+    uint64_t* cw = reinterpret_cast<uint64_t*>(ctl);
+    uint64_t* sw = reinterpret_cast<uint64_t*>(&sc);
+    const bool staged = f.kind != FIN_NONE;
+    if (staged && threadIdx.x < kWords) sw[threadIdx.x] = __ldcg(cw + threadIdx.x);
     double t0 = 0.0, t1 = 0.0;
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
         t0 += __ldcg(&partials[2 * i]);
         if (NRED > 1) t1 += __ldcg(&partials[2 * i + 1]);
     }
-    t0 = block_sum_warp0<NT>(t0, sh);
+    t0 = block_sum_warp0<NT>(t0, sh);   // its barriers also publish the staged copy
     if (NRED > 1) t1 = block_sum_warp0<NT>(t1, sh);
-    if (threadIdx.x == 0) {
-        ctl->counter = 0;
-        finish(ctl, f, t0, t1);
+    if (!staged) {
+        if (threadIdx.x == 0) ctl->counter = 0;
+        return;
     }
+    if (threadIdx.x == 0) {
+        sc.counter = 0;
+        finish(&sc, f, t0, t1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kWords) cw[threadIdx.x] = sw[threadIdx.x];
 }
 
 template <int EPI>
@@ -857,10 +873,11 @@ cta_update(int64_t m, int64_t n, double* __restrict__ x, double* __restrict__ r,
            VecPtrs u, Ctl* ctl, double* partials, FinArgs f) {
     const int64_t len = m > n ? m : n;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (ctl->status != 0) return;
+    const int32_t status = ctl->status;   // loaded together with alpha
     double al[T];
 #pragma unroll
     for (int j = 0; j < T; ++j) al[j] = ctl->alpha[j];
+    if (status != 0) return;
     double a0 = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
         if (i < n) {
