@@ -83,7 +83,7 @@ enum Epilogue : int {
     EPI_NONE = 0,      // y = A x
     EPI_NORM = 1,      // y = A x;          red0 += y²
     EPI_RESID = 2,     // y = b - A x;      red0 += y², red1 += y b
-    EPI_TAPIVOT = 3,   // y = s (A x) = v;  w = v - b + d (= v - b'); red0 += d w, red1 += w²
+    EPI_TAPIVOT = 3,   // v = s (A x); y = w = v - b + d (= v - b'); red0 += d w, red1 += w²
     EPI_RESID_F32 = 4, // FP64 product, v = b - A x; yf = (float) v; red0 += v², red1 += v b
     EPI_NORM_POS = 5   // y = max(A x, 0);  red0 += y²  (c_+ of TA for LP feasibility)
 };

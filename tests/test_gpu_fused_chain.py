@@ -134,3 +134,4 @@ def test_fused_profile_counts_products(tacta):
     assert i1["spmv_count"] == i0["spmv_count"] == 2 * (1 + 2 + 3 + 4 + 5 + 4 + 3 + 2)
     assert i1["spmv_bytes"] == pytest.approx(i0["spmv_bytes"], rel=1e-12)
     assert i1["spmv_ms"] > 0
+
