@@ -173,7 +173,10 @@ __device__ __forceinline__ double block_sum_warp0(double v, double* sh) {
 // Block-level reduction of NRED values (a0 and, if NRED = 2, a1), one partial
 // per block; the last block to finish (atomic ticket, no waiting) sums the
 // partials in block order and runs the finisher. Requires blockDim = NT.
-template <int NRED = 2, int NT = kBlock>
+// STAGED: the finisher runs against a shared-memory copy of the control block, loaded and
+// stored by the block's threads at once (for the vector kernels, whose finishers read and
+// write a dozen fields); otherwise it works on the control block in global memory.
+template <int NRED = 2, int NT = kBlock, bool STAGED = false>
 __device__ void reduce_and_finish(double a0, double a1, Ctl* ctl, double* partials,
                                   const FinArgs& f) {
     __shared__ double sh[NT];
@@ -190,33 +193,39 @@ __device__ void reduce_and_finish(double a0, double a1, Ctl* ctl, double* partia
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    // the finisher runs on one thread against a shared-memory copy of the control block,
-    // loaded and stored by the block's threads at once (its logic reads and writes a
-    // dozen fields; as dependent global accesses that chain took microseconds)
-    __shared__ Ctl sc;
-    constexpr int kWords = (int)(sizeof(Ctl) / 8);
-    static_assert(sizeof(Ctl) % 8 == 0 && kWords <= NT, "the control block copies as one word per thread");
-    uint64_t* cw = reinterpret_cast<uint64_t*>(ctl);
-    uint64_t* sw = reinterpret_cast<uint64_t*>(&sc);
-    const bool staged = f.kind != FIN_NONE;
-    if (staged && threadIdx.x < kWords) sw[threadIdx.x] = __ldcg(cw + threadIdx.x);
-    double t0 = 0.0, t1 = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-        t0 += __ldcg(&partials[2 * i]);
-        if (NRED > 1) t1 += __ldcg(&partials[2 * i + 1]);
+    if constexpr (STAGED) {
+        __shared__ Ctl sc;
+        constexpr int kWords = (int)(sizeof(Ctl) / 8);
+        static_assert(sizeof(Ctl) % 8 == 0 && kWords <= NT, "the control block copies as one word per thread");
+        uint64_t* cw = reinterpret_cast<uint64_t*>(ctl);
+        uint64_t* sw = reinterpret_cast<uint64_t*>(&sc);
+        if (threadIdx.x < kWords) sw[threadIdx.x] = __ldcg(cw + threadIdx.x);
+        double t0 = 0.0, t1 = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+            t0 += __ldcg(&partials[2 * i]);
+            if (NRED > 1) t1 += __ldcg(&partials[2 * i + 1]);
+        }
+        t0 = block_sum_warp0<NT>(t0, sh);   // its barriers also publish the staged copy
+        if (NRED > 1) t1 = block_sum_warp0<NT>(t1, sh);
+        if (threadIdx.x == 0) {
+            sc.counter = 0;
+            finish(&sc, f, t0, t1);
+        }
+        __syncthreads();
+        if (threadIdx.x < kWords) cw[threadIdx.x] = sw[threadIdx.x];
+    } else {
+        double t0 = 0.0, t1 = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+            t0 += __ldcg(&partials[2 * i]);
+            if (NRED > 1) t1 += __ldcg(&partials[2 * i + 1]);
+        }
+        t0 = block_sum_warp0<NT>(t0, sh);
+        if (NRED > 1) t1 = block_sum_warp0<NT>(t1, sh);
+        if (threadIdx.x == 0) {
+            ctl->counter = 0;
+            finish(ctl, f, t0, t1);
+        }
     }
-    t0 = block_sum_warp0<NT>(t0, sh);   // its barriers also publish the staged copy
-    if (NRED > 1) t1 = block_sum_warp0<NT>(t1, sh);
-    if (!staged) {
-        if (threadIdx.x == 0) ctl->counter = 0;
-        return;
-    }
-    if (threadIdx.x == 0) {
-        sc.counter = 0;
-        finish(&sc, f, t0, t1);
-    }
-    __syncthreads();
-    if (threadIdx.x < kWords) cw[threadIdx.x] = sw[threadIdx.x];
 }
 
 }  // namespace tacta

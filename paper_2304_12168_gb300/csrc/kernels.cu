@@ -687,7 +687,7 @@ cta_update(int64_t m, int64_t n, double* __restrict__ x, double* __restrict__ r,
             a0 = fma(v, v, a0);
         }
     }
-    reduce_and_finish<1>(a0, 0.0, ctl, partials, f);
+    reduce_and_finish<1, kBlock, true>(a0, 0.0, ctl, partials, f);
 }
 
 // TA update (Alg. 2.2): b'' = (1-alpha) b' + alpha v, i.e. with d = b - b' and the stored
@@ -719,7 +719,7 @@ ta_update(int64_t m, int64_t n, double* __restrict__ x, double* __restrict__ d,
         }
         if (i < n) x[i] = om * x[i] + as * __ldg(c + i);
     }
-    reduce_and_finish(a0, a1, ctl, partials, f);
+    reduce_and_finish<2, kBlock, true>(a0, a1, ctl, partials, f);
 }
 
 // sum a_i² and sum a_i b_i (b may be null) over one vector, with a finisher.
@@ -1099,7 +1099,7 @@ cta_update32(int64_t m, int64_t n, float* __restrict__ dx, float* __restrict__ r
             acc = fmaf(v, v, acc);
         }
     }
-    reduce_and_finish<1>((double)acc, 0.0, ctl, partials, f);
+    reduce_and_finish<1, kBlock, true>((double)acc, 0.0, ctl, partials, f);
 }
 
 // x += (double) dx, dx = 0: the FP32 correction folded into the FP64 iterate
