@@ -127,8 +127,11 @@ typedef struct {
                                 (banded and stencil matrices): 1 (default) = the 2t products
                                 z_i = Aᵀ u_{i-1}, u_i = A z_i of a step (Alg. 1.1) and their moments
                                 run as one cooperative launch, the products separated by grid-wide
-                                barriers; 0 = one launch per product. Same arithmetic per row; the
-                                moments' partial sums are added in a different fixed order      */
+                                barriers, on the diagonal form of A and Aᵀ when their nonzeros lie
+                                on at most 6 diagonals (col - row constant), else on the run-staged
+                                CSR; 2 = the same launch, always on the run-staged CSR; 0 = one
+                                launch per product. Same arithmetic per row; the moments' partial
+                                sums are added in a different fixed order                       */
     double rho_max;          /* ta_solve: stop (reason RHO_BOUND) once rho exceeds this; <= 0: none */
     void* stream;            /* cudaStream_t (NULL: legacy default stream)                      */
 } tacta_options;

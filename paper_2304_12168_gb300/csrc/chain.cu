@@ -19,6 +19,7 @@
 // Every wait is bounded (about a second); a block that gives up sets the TIMEOUT stop
 // reason, which every other waiting block polls, so the launch always ends.
 #include <algorithm>
+#include <cstddef>
 
 #include "internal.h"
 #include "mbarrier.cuh"
@@ -59,11 +60,124 @@ __device__ __forceinline__ double chain_warp_sum(double v) {
 __device__ __forceinline__ double sq_acc(double s, double a) { return fma(s, s, a); }
 __device__ __forceinline__ float sq_acc(float s, float a) { return fmaf(s, s, a); }
 
+// ------------------------------------------------------------------ tile formats
+//
+// A format supplies the stage layout, the per-tile metadata the producer warp prefetches,
+// the copy issue (matrix part, then x runs) and the row dot product of one consumer lane.
+
+// Run-staged CSR: values, 16-bit column slots and row offsets per tile (any banded CSR
+// whose tiles draw on at most four short runs of x).
 template <typename V>
-__global__ void __launch_bounds__(kRwThreads, ChainShape<V>::MINB)
-cta_chain_rw(ChainOps<V> ops, ChainVecs<V> vec, int t, float scale, Ctl* ctl, double* part) {
-    constexpr int S = ChainShape<V>::S;
+struct RunFmt {
     using Stage = TileStageRT<V>;
+    using Meta = TileMeta;
+    using Ops = ChainOps<V>;
+    struct Prefetch {
+        TilePrefetch pf;
+        __device__ __forceinline__ Meta get(int j, const Ops& ops, int o, int G, int lane) {
+            return pf.get(j, ops.tiles[o], ops.runs[o], ops.ntiles[o], G, lane);
+        }
+    };
+    static __device__ __forceinline__ void issue_mat(const Meta& m, Stage* st, uint64_t* bar, const Ops& ops, int o) {
+        st->desc = m.d;   // visible to the consumers through the stage's mbarrier
+        tile_issue_mat<V>(m, st, bar, ops.rowptr[o], ops.lcol[o], ops.vals[o]);
+    }
+    static __device__ __forceinline__ void issue_x(const Meta& m, Stage* st, uint64_t* bar, const V* x) {
+        tile_issue_x<V>(m, st, bar, x);
+    }
+    static __device__ __forceinline__ V row_dot(const Stage* sg, const Ops&, int warp, int lane, int& row,
+                                                bool& active) {
+        return rw_row_dot(sg, warp, lane, row, active);
+    }
+};
+
+// Diagonal form (DIA): every nonzero on one of k <= kDiaMax diagonals col - row = offset_k.
+// A tile's stage holds its k x 256 values laid out by diagonal then row, one byte per
+// row with bit k set where the row stores diagonal k, and its runs of x; lane r of the
+// tile reads x[row0 + r + offset_k] at slot sbase_k + r. Per nonzero only its value moves
+// (8 bytes FP64, 4 FP32), against 10 / 6 with the run-staged CSR's slots and offsets, and
+// the row's FMAs run in the CSR order (ascending column), so the products are the same.
+template <typename V>
+struct __align__(16) DiaStage {
+    int4 desc;                       // {row begin, row end, tile, 0}
+    int32_t sbase[8];                // slot of x[row begin + offset_k] in xs
+    uint8_t mask[kTileRows];
+    V vals[kDiaMax * kTileRows];
+    V xs[kRunXs];
+};
+static_assert(offsetof(DiaStage<double>, mask) % 16 == 0 && offsetof(DiaStage<double>, vals) % 16 == 0 &&
+              offsetof(DiaStage<double>, xs) % 16 == 0 && sizeof(DiaStage<double>) % 16 == 0 &&
+              offsetof(DiaStage<float>, vals) % 16 == 0 && offsetof(DiaStage<float>, xs) % 16 == 0 &&
+              sizeof(DiaStage<float>) % 16 == 0, "bulk-copy destinations are 16-byte aligned");
+static_assert(kDiaMax <= 8, "DiaStage holds eight slot bases");
+
+struct DiaMeta {
+    int4 d;          // {row begin, row end, tile, 0}
+    int4 r01, r23;   // runs 0..3 as {first, length} pairs
+    int4 s0, s1;     // slot bases of diagonals 0..7
+};
+
+template <typename V>
+struct DiaFmt {
+    using Stage = DiaStage<V>;
+    using Meta = DiaMeta;
+    using Ops = ChainOpsDia<V>;
+    struct Prefetch {   // lane i holds tile j0 + i's runs and slot bases, 32 tiles at a time
+        int4 r01{}, r23{}, s0{}, s1{};
+        int j0 = -32;
+        __device__ __forceinline__ Meta get(int j, const Ops& ops, int o, int G, int lane) {
+            if (j - j0 >= 32) {
+                j0 = j;
+                const int tl = blockIdx.x + (j0 + lane) * G;
+                if (tl < ops.ntiles[o]) {
+                    const int4* r4 = reinterpret_cast<const int4*>(ops.runs[o] + (size_t)tl * kRunMax);
+                    r01 = __ldg(r4);
+                    r23 = __ldg(r4 + 1);
+                    const int4* s4 = reinterpret_cast<const int4*>(ops.sbase[o] + (size_t)tl * 8);
+                    s0 = __ldg(s4);
+                    s1 = __ldg(s4 + 1);
+                }
+            }
+            const int src = j - j0;
+            const int tl = blockIdx.x + j * G;
+            const int r0 = tl * kTileRows;
+            const int r1 = r0 + kTileRows < ops.rows[o] ? r0 + kTileRows : ops.rows[o];
+            return Meta{make_int4(r0, r1, tl, 0), shfl_int4(r01, src), shfl_int4(r23, src), shfl_int4(s0, src),
+                        shfl_int4(s1, src)};
+        }
+    };
+    static __device__ __forceinline__ void issue_mat(const Meta& m, Stage* st, uint64_t* bar, const Ops& ops, int o) {
+        st->desc = m.d;
+        st->sbase[0] = m.s0.x; st->sbase[1] = m.s0.y; st->sbase[2] = m.s0.z; st->sbase[3] = m.s0.w;
+        st->sbase[4] = m.s1.x; st->sbase[5] = m.s1.y; st->sbase[6] = m.s1.z; st->sbase[7] = m.s1.w;
+        const uint32_t bv = (uint32_t)ops.k * kTileRows * (uint32_t)sizeof(V);
+        const uint32_t bx = (uint32_t)(m.r01.y + m.r01.w + m.r23.y + m.r23.w) * (uint32_t)sizeof(V);
+        mbar_expect_tx(bar, bv + kTileRows + bx);
+        bulk_g2s(st->vals, ops.vals[o] + (size_t)m.d.z * ops.k * kTileRows, bv, bar);
+        bulk_g2s(st->mask, ops.mask[o] + (size_t)m.d.z * kTileRows, kTileRows, bar);
+    }
+    static __device__ __forceinline__ void issue_x(const Meta& m, Stage* st, uint64_t* bar, const V* x) {
+        issue_runs<V>(m.r01, m.r23, st->xs, bar, x);
+    }
+    static __device__ __forceinline__ V row_dot(const Stage* sg, const Ops& ops, int warp, int lane, int& row,
+                                                bool& active) {
+        const int lr = warp * 32 + lane;
+        row = sg->desc.x + lr;
+        active = row < sg->desc.y;
+        const unsigned msk = active ? sg->mask[lr] : 0u;
+        V sum = V(0);
+        for (int k = 0; k < ops.k; ++k)
+            if ((msk >> k) & 1u) sum = fma(sg->vals[k * kTileRows + lr], sg->xs[sg->sbase[k] + lr], sum);
+        return sum;
+    }
+};
+
+template <typename V, class F>
+__global__ void __launch_bounds__(kRwThreads, ChainShape<V>::MINB)
+cta_chain(typename F::Ops ops, ChainVecs<V> vec, int t, float scale, Ctl* ctl, double* part) {
+    constexpr int S = ChainShape<V>::S;
+    using Stage = typename F::Stage;
+    using Meta = typename F::Meta;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Stage* st = reinterpret_cast<Stage*>(smem_raw);
     __shared__ __align__(8) uint64_t full[S], empty[S];
@@ -89,7 +203,7 @@ cta_chain_rw(ChainOps<V> ops, ChainVecs<V> vec, int t, float scale, Ctl* ctl, do
         // ---- producer: lane 0 issues, the lanes prefetch tile metadata
         int last_use[S];
         for (int k = 0; k < S; ++k) last_use[k] = -1;
-        TileMeta pend[S];
+        Meta pend[S];
         int pend_k[S];
         int q = 0;   // position of the next tile in this block's sequence over all products
         for (int p = 0; p < P && !__any_sync(0xffffffffu, failed != 0); ++p) {   // one decision per warp
@@ -98,25 +212,24 @@ cta_chain_rw(ChainOps<V> ops, ChainVecs<V> vec, int t, float scale, Ctl* ctl, do
             const int nt = ops.ntiles[o];
             bool gated = p > 0;    // x of product p exists once every block finished p - 1
             int np = 0;
-            TilePrefetch pf;
+            typename F::Prefetch pf;
             for (int j = 0;; ++j) {
                 if (blockIdx.x + j * G >= nt || __any_sync(0xffffffffu, failed != 0)) break;
-                const TileMeta tm = pf.get(j, ops.tiles[o], ops.runs[o], nt, G, lane);
+                const Meta tm = pf.get(j, ops, o, G, lane);
                 if (lane == 0) {
                     const int k = q % S, u = q / S;
                     if (u > 0 && !mbar_wait_bounded(&empty[k], (uint32_t)((u - 1) & 1))) {
                         failed = 1;
                         atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
                     } else {
-                        st[k].desc = tm.d;
-                        tile_issue_mat<V>(tm, st + k, &full[k], ops.rowptr[o], ops.lcol[o], ops.vals[o]);
+                        F::issue_mat(tm, st + k, &full[k], ops, o);
                         last_use[k] = u;
                         if (gated) {
                             pend[np] = tm;
                             pend_k[np] = k;
                             ++np;
                         } else {
-                            tile_issue_x<V>(tm, st + k, &full[k], x);
+                            F::issue_x(tm, st + k, &full[k], x);
                         }
                     }
                     if (gated && np == S) {   // every stage holds a tile waiting for its x runs
@@ -126,7 +239,7 @@ cta_chain_rw(ChainOps<V> ops, ChainVecs<V> vec, int t, float scale, Ctl* ctl, do
                         }
                         // issued even after a failure (in-bounds reads) so that every armed
                         // stage completes and the block can drain its copies
-                        for (int i = 0; i < np; ++i) tile_issue_x<V>(pend[i], st + pend_k[i], &full[pend_k[i]], x);
+                        for (int i = 0; i < np; ++i) F::issue_x(pend[i], st + pend_k[i], &full[pend_k[i]], x);
                         np = 0;
                         gated = false;
                     }
@@ -139,7 +252,7 @@ cta_chain_rw(ChainOps<V> ops, ChainVecs<V> vec, int t, float scale, Ctl* ctl, do
                     failed = 1;
                     atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
                 }
-                for (int i = 0; i < np; ++i) tile_issue_x<V>(pend[i], st + pend_k[i], &full[pend_k[i]], x);
+                for (int i = 0; i < np; ++i) F::issue_x(pend[i], st + pend_k[i], &full[pend_k[i]], x);
             }
             __syncwarp();
         }
@@ -169,7 +282,7 @@ cta_chain_rw(ChainOps<V> ops, ChainVecs<V> vec, int t, float scale, Ctl* ctl, do
                 }
                 int row;
                 bool active;
-                V sum = rw_row_dot(st + k, warp, lane, row, active);
+                V sum = F::row_dot(st + k, ops, warp, lane, row, active);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[k]);   // this warp is done with stage k
                 if (active) {
@@ -202,61 +315,75 @@ cta_chain_rw(ChainOps<V> ops, ChainVecs<V> vec, int t, float scale, Ctl* ctl, do
     }
 }
 
-template <typename V>
-static size_t chain_smem() { return (size_t)ChainShape<V>::S * sizeof(TileStageRT<V>); }
+template <typename V, class F>
+static size_t chain_smem() { return (size_t)ChainShape<V>::S * sizeof(typename F::Stage); }
 
-template <typename V>
+template <typename V, class F>
 static int chain_grid_t(int sms, int max_tiles) {
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(cta_chain_rw<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)chain_smem<V>()) != cudaSuccess)
+        if (cudaFuncSetAttribute(cta_chain<V, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)chain_smem<V, F>()) != cudaSuccess)
             return 0;
         attr = true;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cta_chain_rw<V>, kRwThreads, chain_smem<V>()) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cta_chain<V, F>, kRwThreads, chain_smem<V, F>()) !=
         cudaSuccess)
         return 0;
     return std::max(0, std::min(per_sm * sms, max_tiles));
 }
 
-int cta_chain_grid(int sms, int max_tiles, bool fp32) {
+int cta_chain_grid(int sms, int max_tiles, bool fp32, bool dia) {
     int dev = 0, coop = 0;
     int g = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop)
-        g = fp32 ? chain_grid_t<float>(sms, max_tiles) : chain_grid_t<double>(sms, max_tiles);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop) {
+        if (dia) g = fp32 ? chain_grid_t<float, DiaFmt<float>>(sms, max_tiles)
+                          : chain_grid_t<double, DiaFmt<double>>(sms, max_tiles);
+        else g = fp32 ? chain_grid_t<float, RunFmt<float>>(sms, max_tiles)
+                      : chain_grid_t<double, RunFmt<double>>(sms, max_tiles);
+    }
     (void)cudaGetLastError();   // a refused query leaves no error for the next launch to report
     return g;
 }
 
-template <typename V>
-static cudaError_t launch_chain_t(const LaunchCtx& L, const ChainOps<V>& ops, const ChainVecs<V>& v, int t,
+template <typename V, class F>
+static cudaError_t launch_chain_t(const LaunchCtx& L, const typename F::Ops& ops, const ChainVecs<V>& v, int t,
                                   float scale, double* part, int grid) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kRwThreads);
-    cfg.dynamicSmemBytes = chain_smem<V>();
+    cfg.dynamicSmemBytes = chain_smem<V, F>();
     cfg.stream = L.stream;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;   // all blocks resident: they wait on one another
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, cta_chain_rw<V>, ops, v, t, scale, L.ctl, part);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, cta_chain<V, F>, ops, v, t, scale, L.ctl, part);
     if (L.launches) ++*L.launches;
     return e;
 }
 
 cudaError_t launch_cta_chain(const LaunchCtx& L, const ChainOps<double>& ops, const ChainVecs<double>& v, int t,
                              double* part, int grid) {
-    return launch_chain_t<double>(L, ops, v, t, 1.0f, part, grid);
+    return launch_chain_t<double, RunFmt<double>>(L, ops, v, t, 1.0f, part, grid);
 }
 
 cudaError_t launch_cta_chain32(const LaunchCtx& L, const ChainOps<float>& ops, const ChainVecs<float>& v, int t,
                                float scale, double* part, int grid) {
-    return launch_chain_t<float>(L, ops, v, t, scale, part, grid);
+    return launch_chain_t<float, RunFmt<float>>(L, ops, v, t, scale, part, grid);
+}
+
+cudaError_t launch_cta_chain_dia(const LaunchCtx& L, const ChainOpsDia<double>& ops, const ChainVecs<double>& v,
+                                 int t, double* part, int grid) {
+    return launch_chain_t<double, DiaFmt<double>>(L, ops, v, t, 1.0f, part, grid);
+}
+
+cudaError_t launch_cta_chain_dia32(const LaunchCtx& L, const ChainOpsDia<float>& ops, const ChainVecs<float>& v,
+                                   int t, float scale, double* part, int grid) {
+    return launch_chain_t<float, DiaFmt<float>>(L, ops, v, t, scale, part, grid);
 }
 
 }  // namespace tacta

@@ -111,6 +111,24 @@ constexpr int kTileRows = 256;
 constexpr int kTileCapSmall = 2048;   // 4 blocks per SM
 constexpr int kTileCapLarge = 8192;   // 1 block per SM
 
+// Diagonal form of a banded operand whose nonzeros lie on at most kDiaMax diagonals
+// (col - row = offset_k), in fixed kTileRows-row tiles: the values by tile, diagonal and
+// row ([tile][k][kTileRows], zero where a row lacks diagonal k), one byte per row with bit
+// k set where the row stores diagonal k, the tile's runs of x and, per tile and diagonal,
+// the slot of x[first row + offset_k] in those runs laid end to end. Built on the device
+// at plan time (transpose.cu); used by the fused chain.
+constexpr int kDiaMax = 6;
+struct DevDIA {
+    int k = 0;                   // diagonals; 0 = not in diagonal form
+    int ntiles = 0;
+    int offsets[kDiaMax] = {};   // ascending (host copy)
+    double* vals = nullptr;      // ntiles * k * kTileRows
+    float* vals32 = nullptr;     // FP32 copy for the mixed-precision chain (made on first use)
+    uint8_t* mask = nullptr;     // ntiles * kTileRows
+    int2* runs = nullptr;        // ntiles * kRunMax {first column, length}
+    int32_t* sbase = nullptr;    // ntiles * 8
+};
+
 struct DevCSR {          // CSR operand in device memory (rows x cols)
     int64_t rows = 0, cols = 0, nnz = 0;
     int32_t* rowptr = nullptr;   // rows + 1 (+ 4 padding)
@@ -124,6 +142,7 @@ struct DevCSR {          // CSR operand in device memory (rows x cols)
     uint16_t* lcol = nullptr;    // per nonzero: its column's slot in the tile's staged runs (nnz + kPadLcol)
     int2* runs = nullptr;        // per tile kRunMax {first column, length} (multiples of 4; length 0 = unused)
     SpmvCfg cfg{};
+    DevDIA dia;                  // diagonal form, when the operand has one (fused chain)
 };
 
 // Banded operands (every tile's columns span at most kXSpan entries of x) also
@@ -218,8 +237,24 @@ struct ChainVecs {
     V* z[kTMax];         // z_i = Aᵀ u_{i-1}
     V* u[kTMax];         // u_i = A z_i
 };
+template <typename V>
+struct ChainOpsDia {             // the fused chain on operands in diagonal form; index 0 is Aᵀ, 1 is A
+    const V* vals[2];
+    const uint8_t* mask[2];
+    const int2* runs[2];
+    const int32_t* sbase[2];
+    int ntiles[2];
+    int rows[2];
+    int k;                       // diagonals (the same for A and Aᵀ)
+};
 // blocks of the cooperative chain launch (all resident), 0 if it cannot run here
-int cta_chain_grid(int sms, int max_tiles, bool fp32);
+int cta_chain_grid(int sms, int max_tiles, bool fp32, bool dia);
+cudaError_t launch_cta_chain_dia(const LaunchCtx& L, const ChainOpsDia<double>& ops, const ChainVecs<double>& v,
+                                 int t, double* part, int grid);
+cudaError_t launch_cta_chain_dia32(const LaunchCtx& L, const ChainOpsDia<float>& ops, const ChainVecs<float>& v,
+                                   int t, float scale, double* part, int grid);
+// diagonal form of a CSR operand (d.k = 0 when it has none); flag: 2 ints of device scratch
+cudaError_t dia_build(cudaStream_t s, const DevCSR& a, DevDIA& d, int* flag_dev, int* flag_host);
 cudaError_t launch_cta_chain(const LaunchCtx& L, const ChainOps<double>& ops, const ChainVecs<double>& v, int t,
                              double* part, int grid);
 cudaError_t launch_cta_chain32(const LaunchCtx& L, const ChainOps<float>& ops, const ChainVecs<float>& v, int t,

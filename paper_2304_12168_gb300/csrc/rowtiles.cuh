@@ -98,17 +98,23 @@ __device__ __forceinline__ void tile_issue_mat(const TileMeta& tm, TileStageRT<V
     bulk_g2s(st->rp, rowptr + r0, br, bar);
 }
 
-// The x runs of tile tm into stage st, laid end to end (one thread; after tile_issue_mat).
+// Up to kRunMax runs of x ({first, length} pairs r01, r23) into xs, laid end to end (one thread).
 template <typename V>
-__device__ __forceinline__ void tile_issue_x(const TileMeta& tm, TileStageRT<V>* st, uint64_t* bar, const V* x) {
-    const int2 rr[kRunMax] = {make_int2(tm.r01.x, tm.r01.y), make_int2(tm.r01.z, tm.r01.w),
-                              make_int2(tm.r23.x, tm.r23.y), make_int2(tm.r23.z, tm.r23.w)};
+__device__ __forceinline__ void issue_runs(const int4& r01, const int4& r23, V* xs, uint64_t* bar, const V* x) {
+    const int2 rr[kRunMax] = {make_int2(r01.x, r01.y), make_int2(r01.z, r01.w), make_int2(r23.x, r23.y),
+                              make_int2(r23.z, r23.w)};
     int off = 0;
 #pragma unroll
     for (int k = 0; k < kRunMax; ++k) {
-        if (rr[k].y > 0) bulk_g2s(st->xs + off, x + rr[k].x, (uint32_t)rr[k].y * (uint32_t)sizeof(V), bar);
+        if (rr[k].y > 0) bulk_g2s(xs + off, x + rr[k].x, (uint32_t)rr[k].y * (uint32_t)sizeof(V), bar);
         off += rr[k].y;
     }
+}
+
+// The x runs of tile tm into stage st (one thread; after tile_issue_mat).
+template <typename V>
+__device__ __forceinline__ void tile_issue_x(const TileMeta& tm, TileStageRT<V>* st, uint64_t* bar, const V* x) {
+    issue_runs<V>(tm.r01, tm.r23, st->xs, bar, x);
 }
 
 template <typename V>

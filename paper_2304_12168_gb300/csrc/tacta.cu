@@ -91,8 +91,10 @@ struct Plan {
     // fused chain (A and Aᵀ both run-staged): blocks of the cooperative launch per
     // precision (0: not available) and the per-block moment partials
     int chain_grid = 0, chain_grid32 = 0;
-    double* chain_part = nullptr;    // 2 kTMax x max(chain_grid, chain_grid32)
+    int dia_grid = 0, dia_grid32 = 0;   // the same on the diagonal form (0: A has none)
+    double* chain_part = nullptr;    // 2 kTMax x the largest of those grids
     bool fused = false;              // this call runs the fused chain
+    bool dia = false;                // ... on the diagonal form
     // opt-in profiling of the iteration's products (events around each launch)
     bool profiling = false;
     int prof_count = 0;
@@ -179,6 +181,7 @@ static void plan_free(Plan* p) {
     for (int i = 0; i < kTMax; ++i) { F(p->z[i]); F(p->u[i]); }
     F(p->d); F(p->c); F(p->v); F(p->bt); F(p->xbest); F(p->wx); F(p->wd); F(p->hist);
     F(p->A32.vals); F(p->At32.vals); F(p->r32); F(p->dx32);
+    for (DevDIA* d : {&p->A.csr.dia, &p->At.csr.dia}) { F(d->vals); F(d->vals32); F(d->mask); F(d->runs); F(d->sbase); }
     for (int i = 0; i < kTMax; ++i) { F(p->z32[i]); F(p->u32[i]); }
     if (p->stage) cudaFreeHost(p->stage);
     if (p->poll) cudaFreeHost(p->poll);
@@ -427,9 +430,17 @@ static tacta_status plan_create(const tacta_matrix* M, const tacta_options* opt,
         const DevCSR& at = p->At.csr;
         if (a.cfg.kind == 3 && a.lcol && at.cfg.kind == 3 && at.lcol) {
             const int tiles = std::max(a.ntiles, at.ntiles);
-            p->chain_grid = cta_chain_grid(p->sms, tiles, false);
-            p->chain_grid32 = cta_chain_grid(p->sms, tiles, true);
-            const int g = std::max(p->chain_grid, p->chain_grid32);
+            p->chain_grid = cta_chain_grid(p->sms, tiles, false, false);
+            p->chain_grid32 = cta_chain_grid(p->sms, tiles, true, false);
+            // the diagonal form, when both A and Aᵀ have one (banded with few diagonals)
+            PTRY(dia_build(s, a, a.dia, p->flag_dev, p->flag_host));
+            if (a.dia.k > 0) PTRY(dia_build(s, p->At.csr, p->At.csr.dia, p->flag_dev, p->flag_host));
+            if (a.dia.k > 0 && p->At.csr.dia.k == a.dia.k) {
+                const int dt = std::max(a.dia.ntiles, p->At.csr.dia.ntiles);
+                p->dia_grid = cta_chain_grid(p->sms, dt, false, true);
+                p->dia_grid32 = cta_chain_grid(p->sms, dt, true, true);
+            }
+            const int g = std::max(std::max(p->chain_grid, p->chain_grid32), std::max(p->dia_grid, p->dia_grid32));
             if (g > 0) PTRY(cudaMalloc(&p->chain_part, sizeof(double) * 2 * kTMax * g));
         }
     } else {
@@ -522,6 +533,12 @@ static tacta_status ensure_mixed(Plan* p, int t_max, cudaStream_t s) {
         }
         CUDA_TRY(f32(&p->r32, p->m));
         CUDA_TRY(f32(&p->dx32, p->n));
+        for (DevDIA* d : {&p->A.csr.dia, &p->At.csr.dia}) {
+            if (d->k == 0) continue;
+            const int64_t nv = (int64_t)d->ntiles * d->k * kTileRows;
+            CUDA_TRY(cudaMalloc(&d->vals32, sizeof(float) * nv));
+            CUDA_TRY(convert_to_f32(s, d->vals, d->vals32, nv));
+        }
         CUDA_TRY(spmv32_prepare());
         // chain scale: products are multiplied by 1/sigma so the FP32 chain vectors stay
         // within range (H^i r grows like ||A||^(2i)); sigma is a power of two (exact)
@@ -561,6 +578,30 @@ static ChainOps<V> chain_ops(const DevCSR& At, const DevCSR& A, const V* at_vals
     o.vals[0] = at_vals;
     o.vals[1] = a_vals;
     return o;
+}
+
+template <typename V>
+static ChainOpsDia<V> chain_ops_dia(const DevCSR& At, const DevCSR& A, const V* at_vals, const V* a_vals) {
+    ChainOpsDia<V> o;
+    const DevCSR* op[2] = {&At, &A};
+    for (int i = 0; i < 2; ++i) {
+        o.mask[i] = op[i]->dia.mask;
+        o.runs[i] = op[i]->dia.runs;
+        o.sbase[i] = op[i]->dia.sbase;
+        o.ntiles[i] = op[i]->dia.ntiles;
+        o.rows[i] = (int)op[i]->rows;
+    }
+    o.vals[0] = at_vals;
+    o.vals[1] = a_vals;
+    o.k = A.dia.k;
+    return o;
+}
+
+// algorithmic bytes of one product on the diagonal form: the tiles' values (k per row,
+// zeros where a row lacks a diagonal) and row masks, x read once, y written once
+static double dia_bytes(const DevCSR& a, double vsize) {
+    const double rows_t = (double)a.dia.ntiles * kTileRows;
+    return vsize * (double)a.dia.k * rows_t + rows_t + vsize * (double)a.cols + vsize * (double)a.rows;
 }
 
 // events around the fused chain when profiling: it counts as its 2t products
@@ -605,16 +646,25 @@ static cudaError_t enqueue_cta32_iter(Plan* p, const LaunchCtx& L, int t) {
         v.r = p->r32;
         for (int i = 0; i < kTMax; ++i) { v.z[i] = p->z32[i]; v.u[i] = p->u32[i]; }
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
-        if ((e = launch_cta_chain32(L, chain_ops<float>(p->At.csr, p->A.csr, p->At32.vals, p->A32.vals), v, t,
-                                    p->chain_scale, p->chain_part, p->chain_grid32)) != cudaSuccess) return e;
+        if (p->dia) {
+            e = launch_cta_chain_dia32(L, chain_ops_dia<float>(p->At.csr, p->A.csr, p->At.csr.dia.vals32,
+                                                               p->A.csr.dia.vals32),
+                                       v, t, p->chain_scale, p->chain_part, p->dia_grid32);
+        } else {
+            e = launch_cta_chain32(L, chain_ops<float>(p->At.csr, p->A.csr, p->At32.vals, p->A32.vals), v, t,
+                                   p->chain_scale, p->chain_part, p->chain_grid32);
+        }
+        if (e != cudaSuccess) return e;
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
         if (p->profiling) {
             for (const DevCSR* a : {&p->At.csr, &p->A.csr})
-                p->prof_bytes += t * (8.0 * (double)a->nnz + 4.0 * (double)(a->rows + 1) + 4.0 * (double)a->cols +
-                                      4.0 * (double)a->rows);
+                p->prof_bytes += t * (p->dia ? dia_bytes(*a, 4.0)
+                                             : 8.0 * (double)a->nnz + 4.0 * (double)(a->rows + 1) +
+                                                   4.0 * (double)a->cols + 4.0 * (double)a->rows);
             p->prof_count += 2 * t;
         }
-        if ((e = launch_cta_aux_step(L, t, p->chain_part, p->chain_grid32)) != cudaSuccess) return e;
+        if ((e = launch_cta_aux_step(L, t, p->chain_part, p->dia ? p->dia_grid32 : p->chain_grid32)) !=
+            cudaSuccess) return e;
     } else {
         const float* uprev = p->r32;
         for (int i = 0; i < t; ++i) {
@@ -675,14 +725,23 @@ static cudaError_t enqueue_cta_iter(Plan* p, const LaunchCtx& L, int t) {
         v.r = p->r;
         for (int i = 0; i < kTMax; ++i) { v.z[i] = p->z[i]; v.u[i] = p->u[i]; }
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
-        if ((e = launch_cta_chain(L, chain_ops<double>(p->At.csr, p->A.csr, p->At.csr.vals, p->A.csr.vals), v, t,
-                                  p->chain_part, p->chain_grid)) != cudaSuccess) return e;
+        if (p->dia) {
+            e = launch_cta_chain_dia(L, chain_ops_dia<double>(p->At.csr, p->A.csr, p->At.csr.dia.vals,
+                                                              p->A.csr.dia.vals),
+                                     v, t, p->chain_part, p->dia_grid);
+        } else {
+            e = launch_cta_chain(L, chain_ops<double>(p->At.csr, p->A.csr, p->At.csr.vals, p->A.csr.vals), v, t,
+                                 p->chain_part, p->chain_grid);
+        }
+        if (e != cudaSuccess) return e;
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
         if (p->profiling) {
-            p->prof_bytes += t * (spmv_bytes(p->At) + spmv_bytes(p->A));
+            p->prof_bytes += t * (p->dia ? dia_bytes(p->At.csr, 8.0) + dia_bytes(p->A.csr, 8.0)
+                                         : spmv_bytes(p->At) + spmv_bytes(p->A));
             p->prof_count += 2 * t;
         }
-        if ((e = launch_cta_aux_step(L, t, p->chain_part, p->chain_grid)) != cudaSuccess) return e;
+        if ((e = launch_cta_aux_step(L, t, p->chain_part, p->dia ? p->dia_grid : p->chain_grid)) != cudaSuccess)
+            return e;
         if ((e = launch_cta_update(L, t, p->m, p->n, p->x, p->r, p->z, p->u,
                                    FinArgs{FIN_CTA_UPDATE, 0, p->hist})) != cudaSuccess) return e;
         return launch_spmv(L, p->A, p->x, p->r, EPI_RESID, EpiArgs{p->b, nullptr, nullptr},
@@ -926,8 +985,9 @@ static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t h
     }
     const int t_max = O.o.t_max, cycle = O.o.cycle;
     const int period = schedule_period(t_max, cycle);
-    p->fused = O.o.fused_chain != 0 && (mixed ? p->chain_grid32 : p->chain_grid) > 0;
-    const int key = (t_max * 4 + cycle) * 2 + (p->fused ? 1 : 0);
+    p->dia = O.o.fused_chain == 1 && (mixed ? p->dia_grid32 : p->dia_grid) > 0;
+    p->fused = p->dia || (O.o.fused_chain != 0 && (mixed ? p->chain_grid32 : p->chain_grid) > 0);
+    const int key = (t_max * 4 + cycle) * 4 + (p->fused ? 1 : 0) + (p->dia ? 2 : 0);
     cudaGraphExec_t* g = mixed ? &p->g_cta32 : &p->g_cta;
     int* gkey = mixed ? &p->g_cta32_key : &p->g_cta_key;
     if (*g && *gkey != key) {

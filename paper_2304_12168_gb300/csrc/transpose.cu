@@ -10,6 +10,7 @@
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
+#include <algorithm>
 #include <climits>
 
 #include "internal.h"
@@ -187,6 +188,132 @@ run_tiles(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx
     }
 }
 
+
+// ------------------------------------------------------------------ diagonal form
+
+constexpr int kDiaEmpty = INT_MIN;   // no offset: col - row > INT_MIN for int32 indices
+
+struct DiaOffsets {
+    int k;
+    int off[kDiaMax];
+};
+
+// off into a set of kDiaMax slots (shared or global memory), first free slot in order,
+// so that concurrent inserts of one value land in one slot; *ovf set when the set is full
+__device__ void dia_insert(int* slots, int* ovf, int off) {
+    for (int j = 0; j < kDiaMax; ++j) {
+        int v = *(volatile int*)&slots[j];
+        if (v == off) return;
+        if (v == kDiaEmpty) {
+            v = atomicCAS(&slots[j], kDiaEmpty, off);
+            if (v == kDiaEmpty || v == off) return;
+        }
+    }
+    atomicOr(ovf, 1);
+}
+
+__global__ void dia_init(int* slots, int* ovf) {
+    if (threadIdx.x < kDiaMax) slots[threadIdx.x] = kDiaEmpty;
+    if (threadIdx.x == 0) *ovf = 0;
+}
+
+// the distinct diagonals col - row (a set per block in shared memory, merged at the end)
+__global__ void dia_offsets(const int32_t* rowptr, const int32_t* colidx, int64_t rows, int* slots, int* ovf) {
+    __shared__ int ls[kDiaMax];
+    __shared__ int lovf;
+    if (threadIdx.x < kDiaMax) ls[threadIdx.x] = kDiaEmpty;
+    if (threadIdx.x == 0) lovf = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
+        if (*(volatile int*)&lovf) break;
+        for (int32_t j = rowptr[r]; j < rowptr[r + 1]; ++j) dia_insert(ls, &lovf, colidx[j] - (int32_t)r);
+    }
+    __syncthreads();
+    if (threadIdx.x < kDiaMax && ls[threadIdx.x] != kDiaEmpty) dia_insert(slots, ovf, ls[threadIdx.x]);
+    if (threadIdx.x == 0 && lovf) atomicOr(ovf, 1);
+}
+
+// One thread per 256-row tile: the column range of each diagonal over the tile's rows
+// (clipped to [0, cols), aligned outwards to 4 entries) merged into runs (a gap of more
+// than kRunGap columns starts a new one), and each diagonal's slot base. fail: the tile
+// needs more than kRunMax runs or kRunXs staged entries.
+__global__ void dia_tiles(int ntiles, int64_t rows, int64_t cols, DiaOffsets d, int2* runs, int32_t* sbase,
+                          int* fail) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const int64_t r0 = (int64_t)t * kTileRows;
+    const int64_t r1 = r0 + kTileRows < rows ? r0 + kTileRows : rows;
+    int2 rr[kRunMax];
+    int rk[kDiaMax];
+    int nrun = 0, total = 0;
+    bool bad = false;
+    int64_t cs = -1, ce = -1;   // the run being merged, [cs, ce)
+    auto close = [&]() {
+        if (nrun == kRunMax) { bad = true; return; }
+        rr[nrun++] = make_int2((int)cs, (int)(ce - cs));
+        total += (int)(ce - cs);
+    };
+    for (int k = 0; k < d.k; ++k) {
+        rk[k] = -1;
+        int64_t s = r0 + d.off[k], e = r1 + d.off[k];
+        if (s < 0) s = 0;
+        if (e > cols) e = cols;
+        if (s >= e) continue;
+        s &= ~(int64_t)3;
+        e = (e + 3) & ~(int64_t)3;
+        if (cs >= 0 && s <= ce + kRunGap) {
+            if (e > ce) ce = e;
+        } else {
+            if (cs >= 0) close();
+            cs = s;
+            ce = e;
+        }
+        rk[k] = nrun;   // the index the run being merged gets when it closes
+    }
+    if (cs >= 0) close();
+    if (bad || total > kRunXs) {
+        atomicOr(fail, 1);
+        return;
+    }
+    int start[kRunMax];
+    for (int i = 0, o = 0; i < kRunMax; ++i) {
+        start[i] = o;
+        if (i < nrun) o += rr[i].y;
+    }
+    for (int i = 0; i < kRunMax; ++i) runs[(size_t)t * kRunMax + i] = i < nrun ? rr[i] : make_int2(0, 0);
+    for (int k = 0; k < 8; ++k) {
+        int sb = 0;
+        if (k < d.k && rk[k] >= 0) sb = start[rk[k]] + (int)(r0 + d.off[k] - rr[rk[k]].x);
+        sbase[(size_t)t * 8 + k] = sb;
+    }
+}
+
+// one thread per row: its values into the diagonal-major layout and its mask byte;
+// fail: an entry off the diagonals or two entries on one (a repeated column)
+__global__ void dia_fill(const int32_t* rowptr, const int32_t* colidx, const double* vals, int64_t rows, DiaOffsets d,
+                         double* dvals, uint8_t* mask, int* fail) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
+        const int64_t t = r / kTileRows;
+        const int lr = (int)(r % kTileRows);
+        unsigned m8 = 0;
+        for (int32_t j = rowptr[r]; j < rowptr[r + 1]; ++j) {
+            const int off = colidx[j] - (int32_t)r;
+            int k = -1;
+            for (int i = 0; i < d.k; ++i)
+                if (d.off[i] == off) k = i;
+            if (k < 0 || ((m8 >> k) & 1u)) {
+                atomicOr(fail, 1);
+                continue;
+            }
+            m8 |= 1u << k;
+            dvals[((size_t)t * d.k + k) * kTileRows + lr] = vals[j];
+        }
+        mask[r] = (uint8_t)m8;
+    }
+}
+
 }  // namespace
 
 cudaError_t run_tiles_build(cudaStream_t s, const DevCSR& a, int4* tiles, int2* xwin, int2* runs, uint16_t* lcol,
@@ -196,6 +323,58 @@ cudaError_t run_tiles_build(cudaStream_t s, const DevCSR& a, int4* tiles, int2* 
     if (e != cudaSuccess || ntiles == 0) return e;
     run_tiles<<<ntiles, kTileRows, 0, s>>>(a.rowptr, a.colidx, a.rows, tiles, xwin, runs, lcol, stats);
     return cudaGetLastError();
+}
+
+cudaError_t dia_build(cudaStream_t s, const DevCSR& a, DevDIA& d, int* flag_dev, int* flag_host) {
+    d = DevDIA{};
+    if (a.rows == 0 || a.nnz == 0) return cudaSuccess;
+    int* set = nullptr;
+    int h[kDiaMax + 1];
+    cudaError_t e = cudaMalloc(&set, sizeof(int) * (kDiaMax + 1));
+    if (e != cudaSuccess) return e;
+    auto drop = [&](cudaError_t err) {
+        cudaFree(set);
+        cudaFree(d.vals); cudaFree(d.mask); cudaFree(d.runs); cudaFree(d.sbase);
+        d = DevDIA{};
+        return err;
+    };
+    dia_init<<<1, 32, 0, s>>>(set, set + kDiaMax);
+    dia_offsets<<<blocks_for(a.rows), kBlock, 0, s>>>(a.rowptr, a.colidx, a.rows, set, set + kDiaMax);
+    if ((e = cudaGetLastError()) != cudaSuccess) return drop(e);
+    if ((e = cudaMemcpyAsync(h, set, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return drop(e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return drop(e);
+    if (h[kDiaMax] != 0) return drop(cudaSuccess);   // more than kDiaMax diagonals
+    DiaOffsets off{};
+    for (int i = 0; i < kDiaMax; ++i)
+        if (h[i] != kDiaEmpty) off.off[off.k++] = h[i];
+    std::sort(off.off, off.off + off.k);
+    const int ntiles = (int)((a.rows + kTileRows - 1) / kTileRows);
+    if ((e = cudaMalloc(&d.runs, sizeof(int2) * kRunMax * ntiles)) != cudaSuccess) return drop(e);
+    if ((e = cudaMalloc(&d.sbase, sizeof(int32_t) * 8 * ntiles)) != cudaSuccess) return drop(e);
+    if ((e = cudaMemsetAsync(flag_dev, 0, sizeof(int), s)) != cudaSuccess) return drop(e);
+    dia_tiles<<<(ntiles + kBlock - 1) / kBlock, kBlock, 0, s>>>(ntiles, a.rows, a.cols, off, d.runs, d.sbase,
+                                                                flag_dev);
+    if ((e = cudaGetLastError()) != cudaSuccess) return drop(e);
+    if ((e = cudaMemcpyAsync(flag_host, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return drop(e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return drop(e);
+    if (*flag_host) return drop(cudaSuccess);
+    const size_t nv = (size_t)ntiles * off.k * kTileRows;
+    if ((e = cudaMalloc(&d.vals, sizeof(double) * nv)) != cudaSuccess) return drop(e);
+    if ((e = cudaMalloc(&d.mask, (size_t)ntiles * kTileRows)) != cudaSuccess) return drop(e);
+    if ((e = cudaMemsetAsync(d.vals, 0, sizeof(double) * nv, s)) != cudaSuccess) return drop(e);
+    if ((e = cudaMemsetAsync(d.mask, 0, (size_t)ntiles * kTileRows, s)) != cudaSuccess) return drop(e);
+    dia_fill<<<blocks_for(a.rows), kBlock, 0, s>>>(a.rowptr, a.colidx, a.vals, a.rows, off, d.vals, d.mask, flag_dev);
+    if ((e = cudaGetLastError()) != cudaSuccess) return drop(e);
+    if ((e = cudaMemcpyAsync(flag_host, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return drop(e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return drop(e);
+    if (*flag_host) return drop(cudaSuccess);
+    cudaFree(set);
+    d.k = off.k;
+    d.ntiles = ntiles;
+    for (int i = 0; i < off.k; ++i) d.offsets[i] = off.off[i];
+    return cudaSuccess;
 }
 
 cudaError_t csr_validate(cudaStream_t s, const int32_t* rowptr, const int32_t* colidx, int64_t m,

@@ -124,14 +124,77 @@ def test_fused_mixed_precision(tacta):
 
 
 def test_fused_profile_counts_products(tacta):
-    """profile = 1 times the fused launch as its 2t products: counts and bytes match the
-    per-product path's."""
+    """profile = 1 times the fused launch as its 2t products: on the run-staged CSR
+    (fused_chain = 2) counts and bytes match the per-product path's."""
     p = CASES["stencil_300"]()
     A, b = dev(p)
     opts = dict(tol=1e-30, tol_normal=0.0, max_iter=8, profile=1)
-    _, _, i1 = tacta.cta_solve(A, b, fused_chain=1, **opts)
+    _, _, i1 = tacta.cta_solve(A, b, fused_chain=2, **opts)
     _, _, i0 = tacta.cta_solve(A, b, fused_chain=0, **opts)
     assert i1["spmv_count"] == i0["spmv_count"] == 2 * (1 + 2 + 3 + 4 + 5 + 4 + 3 + 2)
     assert i1["spmv_bytes"] == pytest.approx(i0["spmv_bytes"], rel=1e-12)
     assert i1["spmv_ms"] > 0
 
+
+
+# ------------------------------------------------------------------ diagonal form
+
+def dia_bytes(p, k, vsize=8.0):
+    """Algorithmic bytes of one product on the diagonal form: k values per row of every
+    256-row tile, one mask byte per row, x read once, y written once."""
+    rows_t = -(-p.m // 256) * 256
+    return vsize * k * rows_t + rows_t + vsize * p.n + vsize * p.m
+
+
+@pytest.mark.parametrize("name", ["stencil_300", "rect_banded", "clement_5001"])
+def test_diagonal_form_matches_run_staged_chain(tacta, name):
+    """fused_chain = 1 runs the chain on the diagonal form (the profiled bytes are the
+    diagonal form's), fused_chain = 2 on the run-staged CSR; every row's FMAs run in the
+    same order, so the two trajectories agree to rounding in the moments' partial sums
+    (bit for bit when both launches have the same grid)."""
+    p = CASES[name]()
+    A, b = dev(p)
+    opts = dict(tol=1e-30, tol_normal=0.0, max_iter=8, profile=1)
+    x1, h1, i1 = tacta.cta_solve(A, b, fused_chain=1, **opts)
+    x2, h2, i2 = tacta.cta_solve(A, b, fused_chain=2, **opts)
+    S = sp.csr_matrix((p.vals, p.colidx, p.rowptr), shape=(p.m, p.n))
+    rows = np.repeat(np.arange(p.m), np.diff(S.indptr))
+    k = len(np.unique(S.indices - rows))
+    St = S.T.tocsr()
+    pt = gen.Problem(name="t", m=p.n, n=p.m, fmt="csr", rowptr=St.indptr, colidx=St.indices, vals=St.data)
+    per_step = [1, 2, 3, 4, 5, 4, 3, 2]
+    want = sum(t * (dia_bytes(pt, k) + dia_bytes(p, k)) for t in per_step)
+    assert i1["spmv_bytes"] == pytest.approx(want, rel=1e-12)
+    assert i2["spmv_bytes"] != pytest.approx(want, rel=1e-6)
+    x1, x2 = x1.cpu().numpy(), x2.cpu().numpy()
+    assert np.linalg.norm(x1 - x2) <= 1e-12 * np.linalg.norm(x2)
+    np.testing.assert_allclose(h1.cpu().numpy(), h2.cpu().numpy(), rtol=1e-12)
+
+
+def test_diagonal_form_mixed_precision(tacta):
+    """The FP32 chain on the diagonal form: the refined solve reaches 1e-12 with x within
+    1e-9 of the exact solution (x* = 1), as on the run-staged CSR."""
+    p = gen.convdiff_stencil(40)
+    A, b = dev(p)
+    for fused in (1, 2):
+        x, _, info = tacta.cta_solve(A, b, tol=1e-12, tol_normal=0.0, max_iter=200000,
+                                     precision=tacta.PRECISION_MIXED, fused_chain=fused)
+        assert info["reason_name"] == "RESIDUAL" and info["rel_res"] <= 1e-12
+        assert np.abs(x.cpu().numpy() - 1.0).max() <= 1e-9
+
+
+def test_many_diagonals_stay_on_run_staged_csr(tacta):
+    """Eight diagonals (more than the diagonal form holds): fused_chain = 1 runs the
+    run-staged CSR chain (its profiled bytes are the CSR's) and matches the oracle."""
+    rng = np.random.default_rng(13)
+    offs = [0, 1, 2, 3, 40, 41, 42, 43]
+    S = sp.csr_matrix(sp.diags([rng.standard_normal(6000) for _ in offs], offs, shape=(6000, 6100)))
+    S.sort_indices()
+    p = from_scipy(S, 14)
+    A, b = dev(p)
+    opts = dict(tol=1e-30, tol_normal=0.0, max_iter=8, profile=1)
+    x, _, info = tacta.cta_solve(A, b, fused_chain=1, **opts)
+    _, _, info2 = tacta.cta_solve(A, b, fused_chain=2, **opts)
+    assert info["spmv_bytes"] == pytest.approx(info2["spmv_bytes"], rel=1e-12)
+    ref = oracle.cta_solve(oracle.make_operator(p), p.b, tol=1e-30, tol_normal=0.0, max_iter=8)
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
