@@ -128,7 +128,7 @@ typedef struct {
                                 z_i = Aᵀ u_{i-1}, u_i = A z_i of a step (Alg. 1.1) and their moments
                                 run as one cooperative launch, the products separated by grid-wide
                                 barriers, on the diagonal form of A and Aᵀ when their nonzeros lie
-                                on at most 6 diagonals (col - row constant), else on the run-staged
+                                on at most 5 diagonals (col - row constant), else on the run-staged
                                 CSR; 2 = the same launch, always on the run-staged CSR; 0 = one
                                 launch per product. Same arithmetic per row; the moments' partial
                                 sums are added in a different fixed order                       */

@@ -117,7 +117,7 @@ constexpr int kTileCapLarge = 8192;   // 1 block per SM
 // k set where the row stores diagonal k, the tile's runs of x and, per tile and diagonal,
 // the slot of x[first row + offset_k] in those runs laid end to end. Built on the device
 // at plan time (transpose.cu); used by the fused chain.
-constexpr int kDiaMax = 6;
+constexpr int kDiaMax = 5;
 struct DevDIA {
     int k = 0;                   // diagonals; 0 = not in diagonal form
     int ntiles = 0;
