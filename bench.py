@@ -70,11 +70,11 @@ FP64_TFLOPS_NOMINAL = 1.25
 
 def kernel_source_hash():
     """sha256 of the dominant kernel's source: the fused chain (chain.cu), the row-tile
-    stages and copy issue it uses (rowtiles.cuh) and the mbarrier helpers, comment lines
-    dropped."""
+    stages and copy issue it uses (rowtiles.cuh), the mbarrier helpers and the layout
+    constants (internal.h), comment lines dropped."""
     csrc = os.path.join(ROOT, "paper_2304_12168_gb300", "csrc")
     code = ""
-    for f in ("chain.cu", "rowtiles.cuh", "mbarrier.cuh"):
+    for f in ("chain.cu", "rowtiles.cuh", "mbarrier.cuh", "internal.h"):
         src = open(os.path.join(csrc, f)).read()
         code += "\n".join(l for l in src.splitlines() if not l.strip().startswith("//"))
     return hashlib.sha256(code.encode()).hexdigest()
