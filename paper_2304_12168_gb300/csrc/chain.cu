@@ -166,8 +166,9 @@ struct DiaFmt {
         active = row < sg->desc.y;
         const unsigned msk = active ? sg->mask[lr] : 0u;
         V sum = V(0);
-        for (int k = 0; k < ops.k; ++k)
-            if ((msk >> k) & 1u) sum = fma(sg->vals[k * kTileRows + lr], sg->xs[sg->sbase[k] + lr], sum);
+#pragma unroll
+        for (int k = 0; k < kDiaMax; ++k)
+            if (k < ops.k && ((msk >> k) & 1u)) sum = fma(sg->vals[k * kTileRows + lr], sg->xs[sg->sbase[k] + lr], sum);
         return sum;
     }
 };
