@@ -1,4 +1,5 @@
-// The CTA product chain of one F_t step as one persistent launch (run-staged operands).
+// The CTA product chain of one F_t step as one persistent launch (banded operands, on
+// their diagonal form or their run-staged CSR form: the two tile formats below).
 //
 // Alg. 1.1 with H = AAᵀ builds, from u_0 = r, the chain z_i = Aᵀ u_{i-1}, u_i = A z_i
 // (i = 1..t) and the moments phi_{2i-1} = ||z_i||², phi_{2i} = ||u_i||² (Eq. eqcoeff).
@@ -10,8 +11,8 @@
 //   * at the end of product p each block writes its partial of phi_{p+1} and arrives
 //     on a grid-wide counter; product p+1 reads p's output vector, so its x runs are
 //     copied only once all G blocks have arrived (p + 1) times;
-//   * the matrix part of the first tiles of product p+1 (values, slots, row offsets:
-//     8 of every 10 bytes per nonzero) does not depend on the counter: the producer
+//   * the matrix part of the first tiles of product p+1 (values and the format's
+//     indexing data) does not depend on the counter: the producer
 //     warp issues it into the free stages before waiting, so the copies of the next
 //     product are in flight while the slowest blocks finish the current one;
 //   * the moments are summed from the per-block partials by the step's auxiliary
