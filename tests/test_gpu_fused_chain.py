@@ -198,3 +198,27 @@ def test_many_diagonals_stay_on_run_staged_csr(tacta):
     assert info["spmv_bytes"] == pytest.approx(info2["spmv_bytes"], rel=1e-12)
     ref = oracle.cta_solve(oracle.make_operator(p), p.b, tol=1e-30, tol_normal=0.0, max_iter=8)
     assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+
+
+def test_repeated_column_stays_on_run_staged_csr(tacta):
+    """A row that stores one column twice (CSR allows it; the product adds both) cannot be
+    put in diagonal form: the plan keeps the run-staged CSR chain, and the trajectory
+    matches the oracle's, whose product adds the repeated entries too."""
+    S = sp.csr_matrix(sp.diags([np.full(3000, 4.0), np.full(3000, -1.0), np.full(3000, -1.5)], [0, 1, -1],
+                               shape=(3000, 3000)))
+    S.sort_indices()
+    rp, ci, va = S.indptr.copy(), list(S.indices), list(S.data)
+    k = rp[5] + 1                       # row 5 stores column 5 (its diagonal) a second time
+    ci.insert(k, 5)
+    va.insert(k, 0.25)
+    rp[6:] += 1
+    rng = np.random.default_rng(3)
+    p = gen.Problem(name="dup", m=3000, n=3000, fmt="csr", rowptr=rp.astype(np.int32),
+                    colidx=np.array(ci, dtype=np.int32), vals=np.array(va), b=rng.standard_normal(3000))
+    A, b = dev(p)
+    opts = dict(tol=1e-30, tol_normal=0.0, max_iter=8, profile=1)
+    x, _, info = tacta.cta_solve(A, b, fused_chain=1, **opts)
+    _, _, info2 = tacta.cta_solve(A, b, fused_chain=2, **opts)
+    assert info["spmv_bytes"] == pytest.approx(info2["spmv_bytes"], rel=1e-12)
+    ref = oracle.cta_solve(oracle.make_operator(p), p.b, tol=1e-30, tol_normal=0.0, max_iter=8)
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
