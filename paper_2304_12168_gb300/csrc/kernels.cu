@@ -521,6 +521,111 @@ spmv_tiled_rw(const int4* __restrict__ tiles, const int2* __restrict__ runs, int
 template <int S>
 size_t spmv_tiled_rw_smem() { return (size_t)S * sizeof(TileStageR); }
 
+// The same warp-specialised product on the diagonal form (operands whose nonzeros lie on
+// at most kDiaMax diagonals): only the values move, and every row runs its FMAs in the
+// CSR's column order, so the results are those of spmv_tiled_rw.
+template <int S, int EPI>
+__global__ void __launch_bounds__(kRwThreads, rw_blocks_per_sm<S>())
+spmv_dia(ChainOpsDia<double> ops, const double* __restrict__ x, double* __restrict__ y, EpiArgs e, Ctl* ctl,
+         double* partials, FinArgs f, int gate) {
+    using F = DiaFmt<double>;
+    if (gated_out(ctl, gate)) return;
+    if (gate != GATE_FORCE && blockIdx.x == 0 && threadIdx.x == 0) ctl->matvecs += 1;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    F::Stage* st = reinterpret_cast<F::Stage*>(smem_raw);
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ volatile int failed;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int G = gridDim.x, ntiles = ops.ntiles[0];
+    if (tid == 0) {
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kRwConsumers);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
+    }
+    __syncthreads();
+    double a0 = 0.0, a1 = 0.0;
+    int last_use[S];
+    for (int k = 0; k < S; ++k) last_use[k] = -1;
+    if (warp == kRwConsumers) {
+        F::Prefetch pf;
+        for (int j = 0;; ++j) {
+            const int t = blockIdx.x + j * G;
+            if (t >= ntiles || __any_sync(0xffffffffu, failed != 0)) break;   // one decision per warp
+            const F::Meta tm = pf.get(j, ops, 0, G, lane);
+            if (lane == 0) {
+                const int k = j % S, u = j / S;
+                if (u > 0 && !mbar_wait_bounded(&empty[k], (uint32_t)((u - 1) & 1))) {
+                    failed = 1;
+                    atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+                } else {
+                    F::issue_mat(tm, st + k, &full[k], ops, 0);
+                    F::issue_x(tm, st + k, &full[k], x);
+                    last_use[k] = u;
+                }
+            }
+            __syncwarp();
+        }
+    } else {
+        const double s = (EPI == EPI_TAPIVOT) ? ctl->s : 0.0;
+        for (int j = 0;; ++j) {
+            const int t = blockIdx.x + j * G;
+            if (t >= ntiles) break;
+            const int k = j % S;
+            const bool ok = !failed && mbar_wait_bounded(&full[k], (uint32_t)((j / S) & 1));
+            if (!__all_sync(0xffffffffu, ok)) {   // the warp takes one path
+                if (lane == 0) {
+                    failed = 1;
+                    atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+                }
+                break;
+            }
+            int row;
+            bool active;
+            const double sum = F::row_dot(st + k, ops, warp, lane, row, active);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[k]);
+            if (active) epilogue<EPI>(row, sum, y, e, s, a0, a1);
+        }
+    }
+    __syncthreads();
+    if (failed && warp == kRwConsumers && lane == 0) {
+        for (int k = 0; k < S; ++k)
+            if (last_use[k] >= 0) mbar_wait_bounded(&full[k], (uint32_t)(last_use[k] & 1));
+    }
+    if (EPI != EPI_NONE || f.kind != FIN_NONE)
+        reduce_and_finish<EpiRed<EPI>::value, kRwThreads>(a0, a1, ctl, partials, f);
+}
+
+template <int S, int EPI>
+static cudaError_t spmv_dia_launch(const LaunchCtx& L, const DevCSR& A, const double* x, double* y, EpiArgs e,
+                                   FinArgs f, int gate) {
+    static bool attr = false;
+    const size_t smem = (size_t)S * sizeof(DiaFmt<double>::Stage);
+    if (!attr) {
+        const cudaError_t e2 = cudaFuncSetAttribute(spmv_dia<S, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem);
+        if (e2 != cudaSuccess) return e2;
+        attr = true;
+    }
+    ChainOpsDia<double> ops{};
+    ops.vals[0] = A.dia.vals;
+    ops.mask[0] = A.dia.mask;
+    ops.runs[0] = A.dia.runs;
+    ops.sbase[0] = A.dia.sbase;
+    ops.ntiles[0] = A.dia.ntiles;
+    ops.rows[0] = (int)A.rows;
+    ops.k = A.dia.k;
+    const int sms = L.max_grid / 8;
+    const int grid = std::min(A.dia.ntiles, std::max(1, sms * rw_blocks_per_sm<S>()));
+    spmv_dia<S, EPI><<<grid, kRwThreads, smem, L.stream>>>(ops, x, y, e, L.ctl, L.partials, f, gate);
+    if (L.launches) ++*L.launches;
+    return cudaGetLastError();
+}
+
+
 template <int S, int EPI>
 static cudaError_t spmv_tiled_rw_launch(const LaunchCtx& L, const DevCSR& A, const double* x, double* y,
                                         EpiArgs e, FinArgs f, int gate) {
@@ -616,6 +721,16 @@ static cudaError_t spmv_dispatch(const LaunchCtx& L, int kind, const Acc& acc, c
 
 cudaError_t launch_spmv(const LaunchCtx& L, const DevOperand& A, const double* x, double* y,
                         int epi, EpiArgs e, FinArgs f, int gate) {
+    if (A.format == TACTA_CSR && A.csr.dia.k > 0) {
+        switch (epi) {
+        case EPI_NONE: return spmv_dia_launch<kRwStages, EPI_NONE>(L, A.csr, x, y, e, f, gate);
+        case EPI_NORM: return spmv_dia_launch<kRwStages, EPI_NORM>(L, A.csr, x, y, e, f, gate);
+        case EPI_RESID: return spmv_dia_launch<kRwStages, EPI_RESID>(L, A.csr, x, y, e, f, gate);
+        case EPI_RESID_F32: return spmv_dia_launch<kRwStages, EPI_RESID_F32>(L, A.csr, x, y, e, f, gate);
+        case EPI_NORM_POS: return spmv_dia_launch<kRwStages, EPI_NORM_POS>(L, A.csr, x, y, e, f, gate);
+        default: return spmv_dia_launch<kRwStages, EPI_TAPIVOT>(L, A.csr, x, y, e, f, gate);
+        }
+    }
     if (A.format == TACTA_CSR && A.csr.cfg.kind == 3 && A.csr.lcol) {
         switch (epi) {
         case EPI_NONE: return spmv_tiled_rw_launch<kRwStages, EPI_NONE>(L, A.csr, x, y, e, f, gate);

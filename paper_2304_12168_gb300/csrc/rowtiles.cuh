@@ -165,6 +165,119 @@ __device__ __forceinline__ float rw_row_dot(const TileStageR32* Sg, int warp, in
     return sum;
 }
 
+// ------------------------------------------------------------------ tile formats
+//
+// A format supplies the stage layout, the per-tile metadata the producer warp prefetches,
+// the copy issue (matrix part, then x runs) and the row dot product of one consumer lane.
+
+// Run-staged CSR: values, 16-bit column slots and row offsets per tile (any banded CSR
+// whose tiles draw on at most four short runs of x).
+template <typename V>
+struct RunFmt {
+    using Stage = TileStageRT<V>;
+    using Meta = TileMeta;
+    using Ops = ChainOps<V>;
+    struct Prefetch {
+        TilePrefetch pf;
+        __device__ __forceinline__ Meta get(int j, const Ops& ops, int o, int G, int lane) {
+            return pf.get(j, ops.tiles[o], ops.runs[o], ops.ntiles[o], G, lane);
+        }
+    };
+    static __device__ __forceinline__ void issue_mat(const Meta& m, Stage* st, uint64_t* bar, const Ops& ops, int o) {
+        st->desc = m.d;   // visible to the consumers through the stage's mbarrier
+        tile_issue_mat<V>(m, st, bar, ops.rowptr[o], ops.lcol[o], ops.vals[o]);
+    }
+    static __device__ __forceinline__ void issue_x(const Meta& m, Stage* st, uint64_t* bar, const V* x) {
+        tile_issue_x<V>(m, st, bar, x);
+    }
+    static __device__ __forceinline__ V row_dot(const Stage* sg, const Ops&, int warp, int lane, int& row,
+                                                bool& active) {
+        return rw_row_dot(sg, warp, lane, row, active);
+    }
+};
+
+// Diagonal form (DIA): every nonzero on one of k <= kDiaMax diagonals col - row = offset_k.
+// A tile's stage holds its k x 256 values laid out by diagonal then row, one byte per
+// row with bit k set where the row stores diagonal k, and its runs of x; lane r of the
+// tile reads x[row0 + r + offset_k] at slot sbase_k + r. Per nonzero only its value moves
+// (8 bytes FP64, 4 FP32), against 10 / 6 with the run-staged CSR's slots and offsets, and
+// the row's FMAs run in the CSR order (ascending column), so the products are the same.
+template <typename V>
+struct __align__(16) DiaStage {
+    int4 desc;                       // {row begin, row end, tile, 0}
+    int32_t sbase[8];                // slot of x[row begin + offset_k] in xs
+    uint8_t mask[kTileRows];
+    V vals[kDiaMax * kTileRows];
+    V xs[kRunXs];
+};
+static_assert(offsetof(DiaStage<double>, mask) % 16 == 0 && offsetof(DiaStage<double>, vals) % 16 == 0 &&
+              offsetof(DiaStage<double>, xs) % 16 == 0 && sizeof(DiaStage<double>) % 16 == 0 &&
+              offsetof(DiaStage<float>, vals) % 16 == 0 && offsetof(DiaStage<float>, xs) % 16 == 0 &&
+              sizeof(DiaStage<float>) % 16 == 0, "bulk-copy destinations are 16-byte aligned");
+static_assert(kDiaMax <= 8, "DiaStage holds eight slot bases");
+
+struct DiaMeta {
+    int4 d;          // {row begin, row end, tile, 0}
+    int4 r01, r23;   // runs 0..3 as {first, length} pairs
+    int4 s0, s1;     // slot bases of diagonals 0..7
+};
+
+template <typename V>
+struct DiaFmt {
+    using Stage = DiaStage<V>;
+    using Meta = DiaMeta;
+    using Ops = ChainOpsDia<V>;
+    struct Prefetch {   // lane i holds tile j0 + i's runs and slot bases, 32 tiles at a time
+        int4 r01{}, r23{}, s0{}, s1{};
+        int j0 = -32;
+        __device__ __forceinline__ Meta get(int j, const Ops& ops, int o, int G, int lane) {
+            if (j - j0 >= 32) {
+                j0 = j;
+                const int tl = blockIdx.x + (j0 + lane) * G;
+                if (tl < ops.ntiles[o]) {
+                    const int4* r4 = reinterpret_cast<const int4*>(ops.runs[o] + (size_t)tl * kRunMax);
+                    r01 = __ldg(r4);
+                    r23 = __ldg(r4 + 1);
+                    const int4* s4 = reinterpret_cast<const int4*>(ops.sbase[o] + (size_t)tl * 8);
+                    s0 = __ldg(s4);
+                    s1 = __ldg(s4 + 1);
+                }
+            }
+            const int src = j - j0;
+            const int tl = blockIdx.x + j * G;
+            const int r0 = tl * kTileRows;
+            const int r1 = r0 + kTileRows < ops.rows[o] ? r0 + kTileRows : ops.rows[o];
+            return Meta{make_int4(r0, r1, tl, 0), shfl_int4(r01, src), shfl_int4(r23, src), shfl_int4(s0, src),
+                        shfl_int4(s1, src)};
+        }
+    };
+    static __device__ __forceinline__ void issue_mat(const Meta& m, Stage* st, uint64_t* bar, const Ops& ops, int o) {
+        st->desc = m.d;
+        st->sbase[0] = m.s0.x; st->sbase[1] = m.s0.y; st->sbase[2] = m.s0.z; st->sbase[3] = m.s0.w;
+        st->sbase[4] = m.s1.x; st->sbase[5] = m.s1.y; st->sbase[6] = m.s1.z; st->sbase[7] = m.s1.w;
+        const uint32_t bv = (uint32_t)ops.k * kTileRows * (uint32_t)sizeof(V);
+        const uint32_t bx = (uint32_t)(m.r01.y + m.r01.w + m.r23.y + m.r23.w) * (uint32_t)sizeof(V);
+        mbar_expect_tx(bar, bv + kTileRows + bx);
+        bulk_g2s(st->vals, ops.vals[o] + (size_t)m.d.z * ops.k * kTileRows, bv, bar);
+        bulk_g2s(st->mask, ops.mask[o] + (size_t)m.d.z * kTileRows, kTileRows, bar);
+    }
+    static __device__ __forceinline__ void issue_x(const Meta& m, Stage* st, uint64_t* bar, const V* x) {
+        issue_runs<V>(m.r01, m.r23, st->xs, bar, x);
+    }
+    static __device__ __forceinline__ V row_dot(const Stage* sg, const Ops& ops, int warp, int lane, int& row,
+                                                bool& active) {
+        const int lr = warp * 32 + lane;
+        row = sg->desc.x + lr;
+        active = row < sg->desc.y;
+        const unsigned msk = active ? sg->mask[lr] : 0u;
+        V sum = V(0);
+#pragma unroll
+        for (int k = 0; k < kDiaMax; ++k)
+            if (k < ops.k && ((msk >> k) & 1u)) sum = fma(sg->vals[k * kTileRows + lr], sg->xs[sg->sbase[k] + lr], sum);
+        return sum;
+    }
+};
+
 // eight consumer warps (one per 32 rows of a tile) and one producer warp
 constexpr int kRwConsumers = kTileRows / 32;
 constexpr int kRwThreads = (kRwConsumers + 1) * 32;
