@@ -322,6 +322,19 @@ const char* tacta_batch_last_error(void);
    -1 when t is outside 1..8 or a pointer is NULL. Touches no GPU. */
 int32_t tacta_aux_solve(const double* phi, int32_t t, double pivot_tol, double* alpha);
 
+/* tacta_dia_tile_plan -- the per-tile plan of the diagonal form the fused chain and the
+   single products use for banded operands (rows x cols, k <= 5 diagonals col - row =
+   offsets[0..k-1], strictly ascending), computed on the host by the code the plan-time
+   kernel runs: tile `tile` (rows [256 tile, 256 tile + 256) clipped to rows) stages the
+   ranges x[row + offset_i] clipped to [0, cols), aligned outwards to 4 entries and merged
+   when closer than 16, laid end to end; row r of the tile reads x[r + offset_i] at slot
+   sbase[i] + (r - 256 tile). Writes runs (4 {first column, length} pairs, 8 int32, unused
+   pairs {0, 0}) and sbase (8 int32) and returns 1 when the tile fits (at most 4 runs of at
+   most 896 entries in total), 0 when it does not (outputs untouched), -1 on invalid
+   arguments. Touches no GPU. */
+int32_t tacta_dia_tile_plan(int64_t rows, int64_t cols, int32_t k, const int32_t* offsets, int32_t tile,
+                            int32_t* runs, int32_t* sbase);
+
 /* Description of the last error on the calling thread ("" if none). */
 const char* tacta_last_error(void);
 

@@ -69,7 +69,7 @@ EXPORTS = ["tacta_default_options", "cta_solve", "ta_solve", "ta_minnorm", "tact
            "tacta_residual_static", "tacta_last_error", "tacta_version",
            "tacta_batch_create", "tacta_batch_cta", "tacta_batch_destroy", "tacta_batch_tune",
            "tacta_batch_set_config", "tacta_batch_num_configs", "tacta_batch_config_shape",
-           "tacta_batch_last_error", "tacta_aux_solve"]
+           "tacta_batch_last_error", "tacta_aux_solve", "tacta_dia_tile_plan"]
 
 _lib_handle = None
 
@@ -130,6 +130,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tacta_batch_last_error.restype = ctypes.c_char_p
     lib.tacta_aux_solve.argtypes = [dp, ctypes.c_int32, ctypes.c_double, dp]
     lib.tacta_aux_solve.restype = ctypes.c_int32
+    lib.tacta_dia_tile_plan.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, i32p, ctypes.c_int32,
+                                        i32p, i32p]
+    lib.tacta_dia_tile_plan.restype = ctypes.c_int32
     _lib_handle = lib
     return lib
 
@@ -385,6 +388,18 @@ def aux_solve(phi, t, pivot_tol=1e-12):
     if rank < 0:
         raise ValueError("t must be in 1..8")
     return al[: int(t)], int(rank)
+
+
+def dia_tile_plan(rows, cols, offsets, tile):
+    """tacta_dia_tile_plan: (fits, runs as 4 (first, length) pairs, 8 slot bases) of one
+    256-row tile of the diagonal form; fits is None on invalid arguments."""
+    off = (ctypes.c_int32 * max(1, len(offsets)))(*[int(o) for o in offsets])
+    runs = (ctypes.c_int32 * 8)()
+    sb = (ctypes.c_int32 * 8)()
+    st = load_library().tacta_dia_tile_plan(int(rows), int(cols), len(offsets), off, int(tile), runs, sb)
+    if st < 0:
+        return None, None, None
+    return bool(st), [(runs[2 * i], runs[2 * i + 1]) for i in range(4)], list(sb)
 
 
 def _check_batch(st: int):

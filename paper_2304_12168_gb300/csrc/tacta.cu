@@ -17,6 +17,7 @@
 
 #include "internal.h"
 #include "hankel.cuh"
+#include "dia_plan.cuh"
 
 namespace tacta {
 
@@ -1426,6 +1427,29 @@ tacta_status ta_minnorm(const tacta_matrix* A, const double* b, const double* x0
 }
 
 }  // extern "C"
+
+extern "C" int32_t tacta_dia_tile_plan(int64_t rows, int64_t cols, int32_t k, const int32_t* offsets, int32_t tile,
+                                       int32_t* runs, int32_t* sbase) {
+    using namespace tacta;
+    if (!offsets || !runs || !sbase || k < 1 || k > kDiaMax || rows < 1 || cols < 1 || tile < 0 ||
+        (int64_t)tile * kTileRows >= rows)
+        return -1;
+    DiaOffsets d{};
+    d.k = k;
+    for (int i = 0; i < k; ++i) {
+        d.off[i] = offsets[i];
+        if (i > 0 && offsets[i] <= offsets[i - 1]) return -1;   // strictly ascending
+    }
+    int2 rr[kRunMax];
+    int32_t sb[8];
+    if (!dia_tile_plan(rows, cols, d, tile, rr, sb)) return 0;
+    for (int i = 0; i < kRunMax; ++i) {
+        runs[2 * i] = rr[i].x;
+        runs[2 * i + 1] = rr[i].y;
+    }
+    for (int i = 0; i < 8; ++i) sbase[i] = sb[i];
+    return 1;
+}
 
 extern "C" int32_t tacta_aux_solve(const double* phi, int32_t t, double pivot_tol, double* alpha) {
     if (!phi || !alpha || t < 1 || t > kTMax) return -1;

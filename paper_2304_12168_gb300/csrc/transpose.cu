@@ -14,6 +14,7 @@
 #include <climits>
 
 #include "internal.h"
+#include "dia_plan.cuh"
 
 namespace tacta {
 
@@ -193,11 +194,6 @@ run_tiles(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx
 
 constexpr int kDiaEmpty = INT_MIN;   // no offset: col - row > INT_MIN for int32 indices
 
-struct DiaOffsets {
-    int k;
-    int off[kDiaMax];
-};
-
 // off into a set of kDiaMax slots (shared or global memory), first free slot in order,
 // so that concurrent inserts of one value land in one slot; *ovf set when the set is full
 __device__ void dia_insert(int* slots, int* ovf, int off) {
@@ -234,59 +230,13 @@ __global__ void dia_offsets(const int32_t* rowptr, const int32_t* colidx, int64_
     if (threadIdx.x == 0 && lovf) atomicOr(ovf, 1);
 }
 
-// One thread per 256-row tile: the column range of each diagonal over the tile's rows
-// (clipped to [0, cols), aligned outwards to 4 entries) merged into runs (a gap of more
-// than kRunGap columns starts a new one), and each diagonal's slot base. fail: the tile
-// needs more than kRunMax runs or kRunXs staged entries.
+// one thread per 256-row tile: its runs of x and slot bases (dia_tile_plan); fail: a tile
+// needs more than kRunMax runs or kRunXs staged entries
 __global__ void dia_tiles(int ntiles, int64_t rows, int64_t cols, DiaOffsets d, int2* runs, int32_t* sbase,
                           int* fail) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
-    const int64_t r0 = (int64_t)t * kTileRows;
-    const int64_t r1 = r0 + kTileRows < rows ? r0 + kTileRows : rows;
-    int2 rr[kRunMax];
-    int rk[kDiaMax];
-    int nrun = 0, total = 0;
-    bool bad = false;
-    int64_t cs = -1, ce = -1;   // the run being merged, [cs, ce)
-    auto close = [&]() {
-        if (nrun == kRunMax) { bad = true; return; }
-        rr[nrun++] = make_int2((int)cs, (int)(ce - cs));
-        total += (int)(ce - cs);
-    };
-    for (int k = 0; k < d.k; ++k) {
-        rk[k] = -1;
-        int64_t s = r0 + d.off[k], e = r1 + d.off[k];
-        if (s < 0) s = 0;
-        if (e > cols) e = cols;
-        if (s >= e) continue;
-        s &= ~(int64_t)3;
-        e = (e + 3) & ~(int64_t)3;
-        if (cs >= 0 && s <= ce + kRunGap) {
-            if (e > ce) ce = e;
-        } else {
-            if (cs >= 0) close();
-            cs = s;
-            ce = e;
-        }
-        rk[k] = nrun;   // the index the run being merged gets when it closes
-    }
-    if (cs >= 0) close();
-    if (bad || total > kRunXs) {
-        atomicOr(fail, 1);
-        return;
-    }
-    int start[kRunMax];
-    for (int i = 0, o = 0; i < kRunMax; ++i) {
-        start[i] = o;
-        if (i < nrun) o += rr[i].y;
-    }
-    for (int i = 0; i < kRunMax; ++i) runs[(size_t)t * kRunMax + i] = i < nrun ? rr[i] : make_int2(0, 0);
-    for (int k = 0; k < 8; ++k) {
-        int sb = 0;
-        if (k < d.k && rk[k] >= 0) sb = start[rk[k]] + (int)(r0 + d.off[k] - rr[rk[k]].x);
-        sbase[(size_t)t * 8 + k] = sb;
-    }
+    if (!dia_tile_plan(rows, cols, d, t, runs + (size_t)t * kRunMax, sbase + (size_t)t * 8)) atomicOr(fail, 1);
 }
 
 // one thread per row: its values into the diagonal-major layout and its mask byte;
