@@ -17,13 +17,16 @@ roofline   : the fused chain kernel (the 2t products with Aᵀ and A of each F_t
              one cooperative launch, on the diagonal form of the stencil), timed with
              CUDA events around every launch inside a profiled solve of the same
              workload; reported per product (a launch's work and time over its 2t
-             products). Per product the kernel must move 8 k rows + rows + 8 cols +
-             8 rows bytes (k = 5 diagonals; 57 MB) and issue one FP64 FMA per nonzero
-             and per row (2 (nnz + rows) flops, 12 MFLOP); the larger of the two floors
-             (FP64 at the nominal 1.25 TFLOP/s: 9.6 us; HBM at the measured copy
-             bandwidth: 8.5 us) is the bound reported, the other is given beside it.
+             products) as HBM bandwidth on the CSR product's algorithmic bytes
+             12 nnz + 4 (rows + 1) + 8 cols + 8 rows (79.95 MB) against the measured
+             copy peak. Beside it: the whole F_t step's algorithmic bytes at the
+             measured rate ("step"), the DRAM bytes ncu counted ("dram"), the bytes
+             the diagonal form moves (8 k rows + rows + 8 cols + 8 rows, 57 MB,
+             "format") and the FP64 FMA rate against the nominal 1.25 TFLOP/s ("fp64":
+             one FMA per nonzero and per row, 12 MFLOP; the kernel's actual bound).
 cpu_baseline: the FP64 numpy oracle on the same workload, a bounded sample of
-             CPU_SAMPLE_ITERS iterations.
+             CPU_SAMPLE_ITERS iterations, on all host cores (numpy's BLAS pool) and
+             on one thread.
 
 --impl reference times the oracle itself (the CPU statement of the method) on
 the same config, each step a bounded sample of REF_ITERS_PER_STEP iterations.
@@ -382,6 +385,70 @@ def cpu_baseline(p, iters):
     return r.iters / dt, dt, r
 
 
+def host_cores():
+    """Cores this process may run on (the GPU machine's host cores)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+_ORACLE_CHILD = """
+import json, sys, time
+sys.path.insert(0, {root!r})
+import gen, oracle
+p = gen.convdiff_stencil({grid})
+A = oracle.make_operator(p)
+t0 = time.perf_counter()
+r = oracle.cta_solve(A, p.b, tol={tol!r}, tol_normal=0.0, max_iter={iters})
+dt = time.perf_counter() - t0
+print(json.dumps({{"iters": int(r.iters), "seconds": dt}}))
+"""
+
+
+def oracle_rate(threads, iters):
+    """The oracle as it stands on the same workload (first `iters` F_t steps of the solve) in
+    a fresh process whose BLAS / OpenMP pools have `threads` threads. numpy's vector
+    operations (dots, norms, axpys) use that pool; scipy's CSR products run on one thread
+    whatever the setting, so the all-core figure shows how far the oracle as written can
+    use the host. Returns (F_t per second, seconds) or None if the child failed."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = str(threads)
+    code = _ORACLE_CHILD.format(root=ROOT, grid=GRID, tol=TOL, iters=iters)
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=600, check=True).stdout
+        d = json.loads(out.strip().splitlines()[-1])
+        return d["iters"] / d["seconds"], d["seconds"]
+    except Exception:
+        return None
+
+
+def fpt_schedule(k, t_max=5):
+    """t of F_t step k under the ping-pong cycle 1, 2, .., t_max, .., 2, 1, 2, .."""
+    period = 2 * t_max - 2
+    j = k % period
+    return j + 1 if j < t_max else 2 * t_max - 1 - j
+
+
+def survey_bytes_per_product(m, n, nnz):
+    """Algorithmic bytes of one CSR product with A (m x n, FP64 values, int32 indices):
+    values and column indices 12 nnz, row offsets 4 (m + 1), x read once 8 n, y written
+    once 8 m."""
+    return 12.0 * nnz + 4.0 * (m + 1) + 8.0 * n + 8.0 * m
+
+
+def survey_bytes_per_fpt(m, n, nnz, t):
+    """Algorithmic bytes of one CTA F_t step of order t, unfused: t products with Aᵀ and t
+    with A (CSR), the chain's vectors read and written once per product, and the update
+    reading t z's, t u's and x, r and writing x, r: t (B_A + B_Aᵀ) + 8 t (m + 2 n + m) +
+    8 (t + 2)(n + m)."""
+    ba = 12.0 * nnz + 4.0 * (m + 1)
+    bat = 12.0 * nnz + 4.0 * (n + 1)
+    return t * (ba + bat) + 8.0 * t * (m + 2 * n + m) + 8.0 * (t + 2) * (n + m)
+
+
 def run_reference(args):
     """The oracle as it stands, on the host cores, on this workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -403,8 +470,9 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": f"{GRID}x{GRID}", "n": p.n, "nnz": p.nnz,
                        "iters_per_step": REF_ITERS_PER_STEP, "tol": TOL},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                             "sample": sample + " (numpy's BLAS pool at its default, all host cores; "
+                                                "scipy's CSR products on one thread)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -485,28 +553,40 @@ def main():
     # ---------------- roofline: the products of the iteration, each timed with events
     _, _, prof = plan.cta(b, profile=1, **opts)
     spmv_us = 1e3 * prof["spmv_ms"] / prof["spmv_count"]
-    spmv_bytes = prof["spmv_bytes"] / prof["spmv_count"]
+    fmt_bytes = prof["spmv_bytes"] / prof["spmv_count"]      # what the diagonal form moves per product
+    alg_bytes = survey_bytes_per_product(p.m, p.n, p.nnz)     # the CSR product's algorithmic bytes
     flops = 2.0 * (p.nnz + p.m)                       # one FP64 FMA per nonzero and per row (the norm)
     peak, peak_kind = peaks()
-    hbm = {"achieved": spmv_bytes / (spmv_us * 1e-6) / 1e9, "peak": peak, "unit": "GB/s", "peak_kind": peak_kind}
-    hbm["frac"] = hbm["achieved"] / peak
-    alu = {"achieved": flops / (spmv_us * 1e-6) / 1e12, "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
-           "peak_kind": "nominal FP64 (CUDA cores)"}
-    alu["frac"] = alu["achieved"] / FP64_TFLOPS_NOMINAL
-    fp64_bound = flops / (FP64_TFLOPS_NOMINAL * 1e12) > spmv_bytes / (peak * 1e9)
-    main, other = (alu, hbm) if fp64_bound else (hbm, alu)
-    roofline = {"bound": "alu" if fp64_bound else "hbm", "achieved": main["achieved"], "peak": main["peak"],
-                "unit": main["unit"], "frac": main["frac"], "traffic": traffic_record(),
-                "peak_kind": main["peak_kind"],
-                "other_bound": {"bound": "hbm" if fp64_bound else "alu", **other},
-                "kernel": "cta_chain<double, DiaFmt> (the F_t step's 2t products with A\u1d40 and A in one "
-                          "cooperative launch on the diagonal form: bulk-copy row tiles, warp-specialised, "
-                          "grid-wide barriers between products)",
-                "unit_of_work": "one product of the chain (2t per launch): bytes and flops of the timed "
-                                "launches' products over their summed duration",
-                "products_timed": prof["spmv_count"], "avg_product_us": spmv_us,
-                "bytes_per_product": spmv_bytes, "flops_per_product": flops,
-                "traffic_unit": "DRAM bytes per product (ncu)"}
+    achieved = alg_bytes / (spmv_us * 1e-6) / 1e9
+    traffic = traffic_record()
+    fpt_bytes = statistics.fmean(survey_bytes_per_fpt(p.m, p.n, p.nnz, fpt_schedule(k))
+                                 for k in range(iters_per_step))
+    step_gbs = fpt_bytes * value / 1e9
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        "traffic": traffic, "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)",
+        "kernel": "cta_chain<double, DiaFmt> (the F_t step's 2t products with A\u1d40 and A in one "
+                  "cooperative launch on the diagonal form: bulk-copy row tiles, warp-specialised, "
+                  "grid-wide barriers between products)",
+        "unit_of_work": "one product of the chain (2t per launch): the CSR product's algorithmic bytes "
+                        "12 nnz + 4 (rows + 1) + 8 cols + 8 rows over the timed launches' summed duration "
+                        "per product",
+        "products_timed": prof["spmv_count"], "avg_product_us": spmv_us, "bytes_per_product": alg_bytes,
+        "traffic_unit": "DRAM bytes per product (ncu)",
+        # the whole F_t step against the same peak: the unfused step's algorithmic bytes at the
+        # schedule's mean order, times the measured F_t rate
+        "step": {"bytes_per_fpt": fpt_bytes, "achieved": step_gbs, "unit": "GB/s", "frac": step_gbs / peak},
+        # what DRAM actually served (ncu's dram__bytes per product over the event-timed product)
+        "dram": ({"achieved": traffic / (spmv_us * 1e-6) / 1e9, "unit": "GB/s",
+                  "frac": traffic / (spmv_us * 1e-6) / 1e9 / peak} if traffic else None),
+        # the diagonal form moves fewer bytes than CSR, and the FP64 pipe bounds it
+        "format": {"bytes_per_product": fmt_bytes, "achieved": fmt_bytes / (spmv_us * 1e-6) / 1e9,
+                   "unit": "GB/s", "frac": fmt_bytes / (spmv_us * 1e-6) / 1e9 / peak},
+        "fp64": {"bound": "alu", "flops_per_product": flops, "achieved": flops / (spmv_us * 1e-6) / 1e12,
+                 "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+                 "frac": flops / (spmv_us * 1e-6) / 1e12 / FP64_TFLOPS_NOMINAL,
+                 "peak_kind": "nominal FP64 on CUDA cores: 152 SMs x 2 FMA/clk x 2.07 GHz x 2 flops "
+                              "(not measured by the driver)"}}
 
     # ---------------- e2e: one-shot C ABI call with pinned host buffers
     hA = tacta.CSR(torch.from_numpy(p.rowptr).pin_memory(), torch.from_numpy(p.colidx).pin_memory(),
@@ -538,10 +618,19 @@ def main():
     if rank == 0 and world == 1 and not args.no_extra:   # the other configurations: at N = 1 only
         line["extra"] = extra_workloads(tacta, dev, stream, plan, b, min(args.steps, 5))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, r = cpu_baseline(p, CPU_SAMPLE_ITERS)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {CPU_SAMPLE_ITERS} F_t steps of the same solve "
-                                          f"({dt:.1f} s, numpy FP64, single thread)"}
+        cores = host_cores()
+        one = oracle_rate(1, CPU_SAMPLE_ITERS)
+        allc = oracle_rate(cores, CPU_SAMPLE_ITERS) if cores > 1 else one
+        if one is None or allc is None:           # no child process: time it here
+            v, dt, _ = cpu_baseline(p, CPU_SAMPLE_ITERS)
+            one = allc = (v, dt)
+        line["cpu_baseline"] = {
+            "value": allc[0], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {CPU_SAMPLE_ITERS} F_t steps of the same solve ({allc[1]:.1f} s; numpy "
+                      f"FP64 with its BLAS pool at {cores} threads; scipy's CSR products, most of the "
+                      "work, run on one thread)",
+            "host_cores": cores,
+            "single_thread": {"value": one[0], "unit": UNIT, "cores": 1, "seconds": one[1]}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

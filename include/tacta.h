@@ -245,7 +245,10 @@ tacta_status tacta_plan_outer(tacta_plan plan, double alpha, const double* u, co
  *   counter that must start at zero is cleared at the start of each call; calls
  *   whose work overlaps on the GPU race on the array. The first call on each
  *   device looks up the array's address (cudaGetSymbolAddress) with that device
- *   current; make that first call before any stream capture.
+ *   current; make that first call before any stream capture. The address stays
+ *   cached for the process's life, so it is stale after a cudaDeviceReset of that
+ *   device: do not call this entry point on a device after resetting it. Device
+ *   indices >= 64 -> TACTA_ERR_INVALID.
  */
 tacta_status tacta_residual_static(const tacta_matrix* A, const double* x, const double* b,
                                    double* r_out, double* norms_out, void* stream);

@@ -281,12 +281,19 @@ def residual_static(A, x, b):
     M, on_dev, keep = _matrix(A)
     if not on_dev:
         raise ValueError("residual_static needs CUDA tensors")
-    px, _, kx = _ptr(x, np.float64)
-    pb, _, kb = _ptr(b, np.float64)
-    r = torch.empty(int(M.m), dtype=torch.float64, device=kb.device)
-    norms = np.zeros(2, dtype=np.float64)
-    st = lib.tacta_residual_static(ctypes.byref(M), px, pb, r.data_ptr(), norms.ctypes.data,
-                                   _stream_ptr(True))
+    px, dx, kx = _ptr(x, np.float64)
+    pb, db, kb = _ptr(b, np.float64)
+    if not (dx and db):
+        raise ValueError("residual_static needs CUDA tensors")
+    devs = {kx.device, kb.device} | {t.device for t in keep if isinstance(t, torch.Tensor)}
+    if len(devs) != 1:
+        raise ValueError(f"A, x and b must be on one CUDA device (got {sorted(map(str, devs))})")
+    # the library works on the current device: make it the tensors' device for the call
+    with torch.cuda.device(kb.device):
+        r = torch.empty(int(M.m), dtype=torch.float64, device=kb.device)
+        norms = np.zeros(2, dtype=np.float64)
+        st = lib.tacta_residual_static(ctypes.byref(M), px, pb, r.data_ptr(), norms.ctypes.data,
+                                       _stream_ptr(True))
     _check(st)
     del keep, kx, kb
     return r, float(norms[0]), float(norms[1])

@@ -883,13 +883,13 @@ void set_attrs(cudaError_t& attr) {
 }
 
 cudaError_t prepare_kernels() {
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    std::call_once(once, [] {
-        set_attrs<double>(attr);
-        set_attrs<float>(attr);
-        set_attrs<__nv_bfloat16>(attr);
-    });
+    static const char done_key = 0;   // the attributes are per device
+    if (done_on_device(&done_key)) return cudaSuccess;
+    cudaError_t attr = cudaSuccess;
+    set_attrs<double>(attr);
+    set_attrs<float>(attr);
+    set_attrs<__nv_bfloat16>(attr);
+    if (attr == cudaSuccess) mark_done_on_device(&done_key);
     return attr;
 }
 

@@ -209,12 +209,12 @@ static size_t chain_smem() { return (size_t)ChainShape<V>::S * sizeof(typename F
 
 template <typename V, class F>
 static int chain_grid_t(int sms, int max_tiles) {
-    static bool attr = false;
-    if (!attr) {
+    static const char attr_key = 0;
+    if (!done_on_device(&attr_key)) {
         if (cudaFuncSetAttribute(cta_chain<V, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)chain_smem<V, F>()) != cudaSuccess)
             return 0;
-        attr = true;
+        mark_done_on_device(&attr_key);
     }
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cta_chain<V, F>, kRwThreads, chain_smem<V, F>()) !=

@@ -285,6 +285,15 @@ cudaError_t dense_transpose(cudaStream_t s, const double* A, int64_t rows, int64
 cudaError_t run_tiles_build(cudaStream_t s, const DevCSR& a, int4* tiles, int2* xwin, int2* runs, uint16_t* lcol,
                             int32_t* stats);
 
+// ---------------------------------------------------------------- per-device one-time setup
+// Kernel attributes (the dynamic shared-memory opt-in above 48 KB) are per device, so a
+// process-wide "done" flag would leave a second device without them. done_on_device(key)
+// tells whether the setup identified by `key` (the address of a static of the caller) has
+// succeeded on the current device; mark_done_on_device records it. Thread-safe; two threads
+// racing through the same setup both run it, which is harmless for attribute setters.
+bool done_on_device(const void* key);
+void mark_done_on_device(const void* key);
+
 // ---------------------------------------------------------------- errors
 void set_error(const std::string& msg);
 const char* get_error();

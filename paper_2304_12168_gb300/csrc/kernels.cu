@@ -522,8 +522,9 @@ template <int S>
 size_t spmv_tiled_rw_smem() { return (size_t)S * sizeof(TileStageR); }
 
 // The same warp-specialised product on the diagonal form (operands whose nonzeros lie on
-// at most kDiaMax diagonals): only the values move, and every row runs its FMAs in the
-// CSR's column order, so the results are those of spmv_tiled_rw.
+// at most kDiaMax diagonals): only the values move, and every row runs its FMAs in
+// ascending column order, so the results are those of spmv_tiled_rw whenever the CSR rows
+// list their columns in ascending order.
 template <int S, int EPI>
 __global__ void __launch_bounds__(kRwThreads, rw_blocks_per_sm<S>())
 spmv_dia(ChainOpsDia<double> ops, const double* __restrict__ x, double* __restrict__ y, EpiArgs e, Ctl* ctl,
@@ -602,13 +603,13 @@ spmv_dia(ChainOpsDia<double> ops, const double* __restrict__ x, double* __restri
 template <int S, int EPI>
 static cudaError_t spmv_dia_launch(const LaunchCtx& L, const DevCSR& A, const double* x, double* y, EpiArgs e,
                                    FinArgs f, int gate) {
-    static bool attr = false;
+    static const char attr_key = 0;
     const size_t smem = (size_t)S * sizeof(DiaFmt<double>::Stage);
-    if (!attr) {
+    if (!done_on_device(&attr_key)) {
         const cudaError_t e2 = cudaFuncSetAttribute(spmv_dia<S, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                     (int)smem);
         if (e2 != cudaSuccess) return e2;
-        attr = true;
+        mark_done_on_device(&attr_key);
     }
     ChainOpsDia<double> ops{};
     ops.vals[0] = A.dia.vals;
@@ -638,8 +639,8 @@ static cudaError_t spmv_tiled_rw_launch(const LaunchCtx& L, const DevCSR& A, con
 }
 
 cudaError_t spmv_tiled_prepare() {
-    static bool done = false;
-    if (done) return cudaSuccess;
+    static const char done_key = 0;
+    if (done_on_device(&done_key)) return cudaSuccess;
     cudaError_t e = cudaSuccess;
 #define TACTA_TILED_ATTR(CAP, EPI)                                                                   \
     if (e == cudaSuccess)                                                                            \
@@ -673,7 +674,7 @@ cudaError_t spmv_tiled_prepare() {
 #undef TACTA_TILED_RW_ATTR
 
 #undef TACTA_TILED_X_ATTR
-    if (e == cudaSuccess) done = true;
+    if (e == cudaSuccess) mark_done_on_device(&done_key);
     return e;
 }
 
@@ -1108,13 +1109,13 @@ static cudaError_t spmv32_epi(const LaunchCtx& L, const DevCSR32& A, const float
                               FinArgs f, int gate) {
     const DevCSR& a = *A.base;
     if (a.cfg.kind == 3 && a.lcol) {
-        static bool attr_set = false;
+        static const char attr_key = 0;
         constexpr size_t sm = kRw32Stages * sizeof(TileStageR32);
-        if (!attr_set) {
+        if (!done_on_device(&attr_key)) {
             const cudaError_t e2 = cudaFuncSetAttribute(spmv32_tiled_rw<EPI>,
                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e2 != cudaSuccess) return e2;
-            attr_set = true;
+            mark_done_on_device(&attr_key);
         }
         const int grid = std::min(a.ntiles, std::max(1, (L.max_grid / 8) * kRw32BlocksPerSM));
         spmv32_tiled_rw<EPI><<<grid, kRwThreads, sm, L.stream>>>(a.tiles, a.runs, a.ntiles, a.rowptr, a.lcol, A.vals,
@@ -1165,8 +1166,8 @@ cudaError_t abs_row_sum_max(cudaStream_t s, const DevCSR& A, double* dev_out, do
 }
 
 cudaError_t spmv32_prepare() {
-    static bool done = false;
-    if (done) return cudaSuccess;
+    static const char done_key = 0;
+    if (done_on_device(&done_key)) return cudaSuccess;
     cudaError_t e = cudaSuccess;
 #define TACTA_S32_ATTR(CAP, XW, EPI)                                                                        \
     if (e == cudaSuccess)                                                                                   \
@@ -1176,7 +1177,7 @@ cudaError_t spmv32_prepare() {
     TACTA_S32_ATTR(kTileCapSmall, false, EPI_NORM) TACTA_S32_ATTR(kTileCapSmall, false, EPI_NONE)
     TACTA_S32_ATTR(kTileCapLarge, false, EPI_NORM) TACTA_S32_ATTR(kTileCapLarge, false, EPI_NONE)
 #undef TACTA_S32_ATTR
-    if (e == cudaSuccess) done = true;
+    if (e == cudaSuccess) mark_done_on_device(&done_key);
     return e;
 }
 

@@ -201,7 +201,10 @@ struct RunFmt {
 // row with bit k set where the row stores diagonal k, and its runs of x; lane r of the
 // tile reads x[row0 + r + offset_k] at slot sbase_k + r. Per nonzero only its value moves
 // (8 bytes FP64, 4 FP32), against 10 / 6 with the run-staged CSR's slots and offsets, and
-// the row's FMAs run in the CSR order (ascending column), so the products are the same.
+// the row's FMAs run in ascending diagonal order, i.e. ascending column: that is the CSR
+// order, and the products equal the CSR kernels' bit for bit, when each CSR row lists its
+// columns in ascending order (the transposes built here always do; a caller's A with
+// unsorted rows can differ in the last bits).
 template <typename V>
 struct __align__(16) DiaStage {
     int4 desc;                       // {row begin, row end, tile, 0}

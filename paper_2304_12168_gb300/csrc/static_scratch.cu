@@ -20,7 +20,9 @@
 //     of every call; two calls whose work overlaps on the GPU race on the array;
 //   * the first call on each device looks up the array's device address
 //     (cudaGetSymbolAddress) with that device current; make that first call
-//     outside any stream capture.
+//     outside any stream capture. The address is cached for the life of the
+//     process: after a cudaDeviceReset of that device it is stale, so a caller
+//     that resets a device must not call this entry point on it again.
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -167,9 +169,14 @@ extern "C" tacta_status tacta_residual_static(const tacta_matrix* A, const doubl
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (e != cudaSuccess) {
         set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
         return TACTA_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("device index " + std::to_string(dev) + " is beyond the " + std::to_string(kMaxDevices) +
+                  " devices whose scratch address tacta_residual_static caches");
+        return TACTA_ERR_INVALID;
     }
     unsigned char* scratch = nullptr;
     if ((e = scratch_address(dev, &scratch)) != cudaSuccess) {

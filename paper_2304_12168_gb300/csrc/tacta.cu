@@ -12,7 +12,10 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "internal.h"
@@ -25,6 +28,24 @@ namespace tacta {
 static thread_local std::string g_err;
 void set_error(const std::string& m) { g_err = m; }
 const char* get_error() { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ per-device one-time setup
+static std::mutex g_done_lock;
+static std::set<std::pair<const void*, int>> g_done;
+
+bool done_on_device(const void* key) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> guard(g_done_lock);
+    return g_done.count({key, dev}) != 0;
+}
+
+void mark_done_on_device(const void* key) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> guard(g_done_lock);
+    g_done.insert({key, dev});
+}
 
 #define CUDA_TRY(expr)                                                                      \
     do {                                                                                    \

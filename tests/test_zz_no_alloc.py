@@ -15,6 +15,7 @@ import gen
 pytestmark = pytest.mark.gpu
 
 RES_TOL = 1e-10      # final relative residuals agree within 1e-10 (as in test_gpu_parity)
+U = np.finfo(np.float64).eps / 2
 
 
 def _device(p):
@@ -28,6 +29,17 @@ def _device(p):
                  torch.from_numpy(p.vals).to(d), (p.m, p.n)), b
 
 
+def _host_residual(p, x):
+    """b - A x on the host in FP64, and the rounding bound of one side per row:
+    (k + 1) u (|b| + |A||x|) with k the row's stored entries."""
+    S = p.scipy()
+    r = p.b - S @ x
+    absS = abs(S)
+    k = np.diff(S.indptr) if p.fmt == "csr" else np.full(p.m, p.n)
+    bound = (k + 1) * U * (np.abs(p.b) + absS @ np.abs(x))
+    return r, bound
+
+
 @pytest.mark.parametrize("kind", ["csr", "dense"])
 def test_residual_static_matches_cta_solve_on_two_calls_in_a_row(kind):
     import torch
@@ -36,19 +48,27 @@ def test_residual_static_matches_cta_solve_on_two_calls_in_a_row(kind):
     torch.cuda.set_device(0)
     p = gen.convdiff_stencil(60) if kind == "csr" else gen.dense_gaussian(300, 200, seed=4)
     A, b = _device(p)
-    bnorm = float(torch.linalg.norm(b))
+    bnorm = float(np.linalg.norm(p.b))
     rng = np.random.default_rng(3)
     for call in range(2):
-        x = torch.from_numpy(rng.standard_normal(p.n)).to("cuda:0")
+        xh = rng.standard_normal(p.n)
+        x = torch.from_numpy(xh).to("cuda:0")
         # the existing entry point: cta_solve from x0 = x with no iterations reports the
         # true residual b - A x at exit
         _, hist, info = tacta.cta_solve(A, b, x, tol=1e-30, tol_normal=0.0, max_iter=0)
         r, rr, rb = tacta.residual_static(A, x, b)
         assert abs(np.sqrt(rr) / bnorm - info["rel_res"]) <= RES_TOL * max(1.0, info["rel_res"])
         assert abs(np.sqrt(rr) / bnorm - float(hist[0])) <= RES_TOL * max(1.0, float(hist[0]))
-        # r itself is b - A x, and rᵀb is its dot with b
-        assert float(torch.linalg.norm(r)) ** 2 == pytest.approx(rr, rel=1e-12)
-        assert float(torch.dot(r, b)) == pytest.approx(rb, rel=1e-10, abs=1e-10 * bnorm ** 2)
+        # r entry by entry against b - A x formed on the host: the two sides differ by at
+        # most the sum of their rounding bounds
+        rh, bound = _host_residual(p, xh)
+        rg = r.cpu().numpy()
+        assert np.all(np.abs(rg - rh) <= 2 * bound), float(np.max(np.abs(rg - rh) / (2 * bound)))
+        # the reductions against host sums of the host residual (error of a sum of m terms
+        # plus the propagated per-entry bound)
+        m = p.m
+        assert abs(rr - float(rh @ rh)) <= 2 * float(np.abs(rh) @ (2 * bound)) + 2 * m * U * float(rh @ rh)
+        assert abs(rb - float(rh @ p.b)) <= float(np.abs(p.b) @ (2 * bound)) + 2 * m * U * float(np.abs(rh) @ np.abs(p.b))
 
 
 def test_residual_static_rejects_host_arrays_and_oversized_m():
