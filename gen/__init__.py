@@ -30,7 +30,7 @@ import scipy.sparse as sp
 
 __all__ = [
     "Problem", "dense_gaussian", "dense_low_rank", "convdiff_stencil",
-    "clement", "lp_rect", "random_csr", "diag_matrix", "DenseBatch", "dense_batch",
+    "clement", "lp_rect", "random_csr", "diag_matrix", "DenseBatch", "dense_batch", "banded_rect",
 ]
 
 
@@ -182,6 +182,20 @@ def lp_rect(m: int = 10000, n: int = 1_000_000, per_col: int = 30, dup_rows: int
     x[nzx] = rng.standard_normal(nzx.size)
     return _from_scipy(f"lp_rect_{m}x{n}", A, x, {"seed": seed, "per_col": per_col,
                                                  "dup_rows": dup_rows})
+
+
+def banded_rect(m: int, n: int, offsets=(0, 1, 3), seed: int = 3) -> Problem:
+    """A well-conditioned banded m x n matrix (m <= n): the main diagonal U(1.5, 2.5), the
+    other diagonals col - row = offset U(-0.4, 0.4) (diagonally dominant rows, so full row
+    rank with singular values in ~[0.7, 3.3]); x_known ~ N(0,1), b = A x_known, which
+    has a component in the null space of A when m < n (x_known is not the minimum-norm
+    solution). Its minimum-norm problems make Algorithm 2.5's trips short."""
+    rng = np.random.default_rng(seed)
+    diags = [rng.uniform(1.5, 2.5, min(m, n - k)) if k == 0 else rng.uniform(-0.4, 0.4, min(m, n - k))
+             for k in offsets]
+    S = sp.diags(diags, list(offsets), shape=(m, n), format="csr")
+    x = np.random.default_rng(seed + 1).standard_normal(n)
+    return _from_scipy(f"banded_{m}x{n}", S, x, {"offsets": list(offsets)})
 
 
 def random_csr(m: int, n: int, density: float = 0.05, seed: int = 0, empty_rows: int = 0,

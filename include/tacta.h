@@ -208,6 +208,24 @@ tacta_status tacta_plan_minnorm(tacta_plan plan, const double* b, const double* 
                                 int32_t hist_cap, tacta_info* info);
 void tacta_plan_destroy(tacta_plan plan);
 
+/* tacta_plan_minnorm_bisect -- Algorithm 2.5 (Sec. 4.4) alone: bisection on rho from a given
+   approximate solution x_eps of M x = rhs, M = A and rhs = b (normal = 0) or M = AᵀA and
+   rhs = Aᵀb applied through products with A and Aᵀ (normal = 1).
+   rho_hi = ||x_eps||, rho_lo = 0; while rho_hi - rho_lo > tol ||x_eps||: Alg. 2.1 at the
+   midpoint rho, from the last witness (from x = 0 before the first); a trip that meets the
+   residual test sets rho_hi = rho and its x becomes the answer, a witness sets
+   rho_lo = (b - b')ᵀb / ||Mᵀ(b - b')|| (Cor. cor1), a normal-equation stop ends the call with
+   that x. max_iter bounds the TA iterations of all trips together.
+   b, x_eps, x_out follow the plan's on_device flag (m, n, n values). trip_log is a HOST
+   array of 6 * log_cap doubles (NULL with log_cap = 0: not written): trip i writes
+   {rho, the trip's stop reason (TACTA_REASON_*), rho_hi after the trip, rho_lo after the
+   trip, the trip's TA iterations, 0}. info->trips = trips run (log rows beyond log_cap are
+   dropped), info->rho = rho_hi, info->rho_lower = rho_lo, info->reason = GAP when the gap
+   closed. Errors as the other plan calls. */
+tacta_status tacta_plan_minnorm_bisect(tacta_plan plan, const double* b, const double* x_eps, int32_t normal,
+                                       const tacta_options* opt, double* x_out, double* trip_log,
+                                       int32_t log_cap, tacta_info* info);
+
 /* tacta_plan_transpose -- a new plan for Aᵀ built from the device copy held by `plan`
    (used by adjoint solves: the backward of a solve with A solves with Aᵀ). The new plan's
    vector pointers follow the same on_device flag. */

@@ -65,7 +65,7 @@ class tacta_info(ctypes.Structure):
 
 EXPORTS = ["tacta_default_options", "cta_solve", "ta_solve", "ta_minnorm", "tacta_plan_create",
            "tacta_plan_cta", "tacta_plan_ta", "tacta_plan_minnorm", "tacta_plan_destroy",
-           "tacta_plan_transpose", "tacta_plan_matvec", "tacta_plan_outer",
+           "tacta_plan_transpose", "tacta_plan_matvec", "tacta_plan_outer", "tacta_plan_minnorm_bisect",
            "tacta_residual_static", "tacta_last_error", "tacta_version",
            "tacta_batch_create", "tacta_batch_cta", "tacta_batch_destroy", "tacta_batch_tune",
            "tacta_batch_set_config", "tacta_batch_num_configs", "tacta_batch_config_shape",
@@ -104,6 +104,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tacta_version.restype = ctypes.c_int32
     lib.tacta_residual_static.argtypes = [P(tacta_matrix), dp, dp, dp, dp, vp]
     lib.tacta_residual_static.restype = ctypes.c_int32
+    lib.tacta_plan_minnorm_bisect.argtypes = [vp, dp, dp, ctypes.c_int32, P(tacta_options), dp, dp,
+                                              ctypes.c_int32, P(tacta_info)]
+    lib.tacta_plan_minnorm_bisect.restype = ctypes.c_int32
     lib.tacta_plan_transpose.argtypes = [vp, P(tacta_options), P(vp)]
     lib.tacta_plan_transpose.restype = ctypes.c_int32
     lib.tacta_plan_matvec.argtypes = [vp, ctypes.c_int32, dp, dp, P(tacta_options)]
@@ -339,6 +342,25 @@ class Plan:
 
     def minnorm(self, b, hist_cap=None, **opts):
         return self._call("tacta_plan_minnorm", b, None, hist_cap, opts)
+
+    def minnorm_bisect(self, b, x_eps, normal=False, log_cap=256, **opts):
+        """tacta_plan_minnorm_bisect: Algorithm 2.5 alone from x_eps ->
+        (x, trip log as a (trips, 6) array: rho, reason, rho_hi, rho_lo, iters, 0; info dict)."""
+        lib = load_library()
+        pb, db_, kb = _ptr(b, np.float64)
+        pe, de, ke = _ptr(x_eps, np.float64)
+        if db_ != bool(self.on_device) or de != bool(self.on_device):
+            raise ValueError("b and x_eps must be on the same side as the plan's matrix")
+        o = make_options(self.on_device, **opts)
+        x = _vec_out(self.n, self.on_device, kb)
+        log = np.zeros((max(int(log_cap), 1), 6), dtype=np.float64)
+        info = tacta_info()
+        st = lib.tacta_plan_minnorm_bisect(self._h, pb, pe, int(bool(normal)), ctypes.byref(o),
+                                           _ptr(x, np.float64)[0], log.ctypes.data, int(log_cap),
+                                           ctypes.byref(info))
+        _check(st)
+        del kb, ke
+        return x, log[: min(info.trips, int(log_cap))].copy(), _info_dict(st, info)
 
     def transpose(self, **opts):
         """tacta_plan_transpose: a plan for Aᵀ from this plan's device copy."""

@@ -1141,6 +1141,100 @@ static tacta_status plan_ta(Plan* p, const VecIO& io, const tacta_options* opt, 
 
 // ------------------------------------------------------------------ hybrid minimum norm (Sec. 5.2, Alg. 2.5)
 
+struct BisectOut {
+    double rho_hi = 0.0, rho_lo = 0.0;
+    int64_t used = 0;     // TA iterations over all trips
+    int trips = 0;
+    int reason = TACTA_REASON_GAP;
+};
+
+// Algorithm 2.5 (Sec. 4.4) on M x = rhs, M = A (normal = 0) or AᵀA with rhs = Aᵀb
+// (normal = 1), from the approximate solution x_eps held in p->x (b already loaded).
+// rho_hi = ||x_eps||, rho_lo = 0; while rho_hi - rho_lo > tol ||x_eps||: rho = the midpoint,
+// Alg. 2.1 at rho from the last witness (from 0 before the first), on success
+// rho_hi = rho and its x is the answer, on a witness rho_lo = (b - b')ᵀb / ||Mᵀ(b - b')||
+// (Cor. cor1). A normal-equation stop of a trip ends the call with that x. The answer is
+// left in p->xbest. With trip_log non-null, trip i writes 6 doubles at trip_log[6 i]:
+// rho, the trip's stop reason, rho_hi and rho_lo after the trip, its iterations, 0.
+static tacta_status minnorm_bisect(Plan* p, const Opts& O, int normal, double* trip_log, int log_cap,
+                                   int64_t* launches, BisectOut* out) {
+    tacta_status st;
+    LaunchCtx L{O.s, p->ctl, p->partials, p->grid, launches};
+    EpiArgs none{nullptr, nullptr, nullptr};
+    if (normal)
+        CUDA_TRY(launch_spmv(L, p->At, p->b, p->bt, EPI_NONE, none, FinArgs{FIN_NONE, 0, nullptr}, GATE_FORCE));
+    CUDA_TRY(cudaMemcpyAsync(p->xbest, p->x, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
+    Ctl h = base_ctl(O, 0);
+    if ((st = write_ctl(p, O.s, h)) != TACTA_OK) return st;
+    CUDA_TRY(launch_reduce_vec(L, p->n, p->x, nullptr, FinArgs{FIN_STORE, 0, nullptr}, GATE_ALWAYS));
+    if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
+    double rho_hi = std::sqrt(p->stage->red[0]);
+    double rho_lo = 0.0;
+    const double gap = O.o.tol * rho_hi;
+    // thresholds of the operator in use (||rhs||², ||Mᵀ rhs||²)
+    const double* rhs = normal ? p->bt : p->b;
+    const int64_t mm = normal ? p->n : p->m;
+    CUDA_TRY(launch_reduce_vec(L, mm, rhs, nullptr, FinArgs{FIN_SETUP_B, 0, nullptr}, GATE_ALWAYS));
+    CUDA_TRY(apply_Mt(p, L, normal, rhs, p->tmp_n, EPI_NORM, none, FinArgs{FIN_SETUP_MTB, 0, nullptr}, GATE_ALWAYS));
+    bool have_witness = false;
+    int64_t used = 0;
+    int trips = 0;
+    int final_reason = TACTA_REASON_GAP;
+    while (rho_hi - rho_lo > gap) {
+        if (used >= O.o.max_iter) { final_reason = TACTA_REASON_MAXITER; break; }
+        const double rho = 0.5 * (rho_hi + rho_lo);
+        ctl_set_trip<<<1, 1, 0, O.s>>>(p->ctl, rho, (int)(O.o.max_iter - used));
+        ++*launches;
+        CUDA_TRY(cudaGetLastError());
+        if (have_witness) {
+            CUDA_TRY(cudaMemcpyAsync(p->x, p->wx, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
+            CUDA_TRY(cudaMemcpyAsync(p->d, p->wd, sizeof(double) * mm, cudaMemcpyDeviceToDevice, O.s));
+        } else {
+            CUDA_TRY(cudaMemsetAsync(p->x, 0, sizeof(double) * p->n, O.s));
+            CUDA_TRY(cudaMemcpyAsync(p->d, rhs, sizeof(double) * mm, cudaMemcpyDeviceToDevice, O.s));
+        }
+        CUDA_TRY(launch_reduce_vec(L, mm, p->d, rhs, FinArgs{FIN_TRIP_START, 0, nullptr}, GATE_FORCE));
+        if ((st = ta_iterate(p, O, normal, O.o.max_iter - used, launches)) != TACTA_OK) return st;
+        if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
+        const Ctl c = *p->stage;
+        used += c.k;
+        bool stop = false;
+        if (c.status == TACTA_REASON_RESIDUAL) {
+            rho_hi = rho;
+            CUDA_TRY(cudaMemcpyAsync(p->xbest, p->x, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
+        } else if (c.status == TACTA_REASON_WITNESS) {
+            rho_lo = c.db / std::sqrt(c.cn2);
+            have_witness = true;
+            CUDA_TRY(cudaMemcpyAsync(p->wx, p->x, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
+            CUDA_TRY(cudaMemcpyAsync(p->wd, p->d, sizeof(double) * mm, cudaMemcpyDeviceToDevice, O.s));
+        } else if (c.status == TACTA_REASON_NORMAL) {
+            CUDA_TRY(cudaMemcpyAsync(p->xbest, p->x, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
+            final_reason = TACTA_REASON_NORMAL;
+            stop = true;
+        } else {
+            final_reason = c.status;
+            stop = true;
+        }
+        if (trip_log && trips < log_cap) {
+            double* row = trip_log + 6 * (size_t)trips;
+            row[0] = rho;
+            row[1] = (double)c.status;
+            row[2] = rho_hi;
+            row[3] = rho_lo;
+            row[4] = (double)c.k;
+            row[5] = 0.0;
+        }
+        ++trips;
+        if (stop) break;
+    }
+    out->rho_hi = rho_hi;
+    out->rho_lo = rho_lo;
+    out->used = used;
+    out->trips = trips;
+    out->reason = final_reason;
+    return TACTA_OK;
+}
+
 static tacta_status plan_minnorm(Plan* p, const VecIO& io, const tacta_options* opt, tacta_info* info) {
     Opts O = resolve(opt);
     tacta_status st;
@@ -1180,63 +1274,13 @@ static tacta_status plan_minnorm(Plan* p, const VecIO& io, const tacta_options* 
     }
     const double rel_res = std::sqrt(c1.red[0] / c1.bn2);
     const int normal = rel_res <= O.o.tol_cta ? 0 : 1;
-    // phase 2: Algorithm 2.5 on (A, b) or (AᵀA, Aᵀb)
-    EpiArgs none{nullptr, nullptr, nullptr};
-    if (normal)
-        CUDA_TRY(launch_spmv(L, p->At, p->b, p->bt, EPI_NONE, none, FinArgs{FIN_NONE, 0, nullptr}, GATE_FORCE));
-    CUDA_TRY(cudaMemcpyAsync(p->xbest, p->x, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
-    Ctl h = base_ctl(O, 0);
-    if ((st = write_ctl(p, O.s, h)) != TACTA_OK) return st;
-    CUDA_TRY(launch_reduce_vec(L, p->n, p->x, nullptr, FinArgs{FIN_STORE, 0, nullptr}, GATE_ALWAYS));
-    if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
-    double rho_hi = std::sqrt(p->stage->red[0]);
-    double rho_lo = 0.0;
-    const double gap = O.o.tol * rho_hi;
-    // thresholds of the operator in use (||rhs||², ||Mᵀ rhs||²)
-    const double* rhs = normal ? p->bt : p->b;
-    const int64_t mm = normal ? p->n : p->m;
-    CUDA_TRY(launch_reduce_vec(L, mm, rhs, nullptr, FinArgs{FIN_SETUP_B, 0, nullptr}, GATE_ALWAYS));
-    CUDA_TRY(apply_Mt(p, L, normal, rhs, p->tmp_n, EPI_NORM, none, FinArgs{FIN_SETUP_MTB, 0, nullptr}, GATE_ALWAYS));
-    bool have_witness = false;
-    int64_t used = 0;
-    int trips = 0;
-    int final_reason = TACTA_REASON_GAP;
-    while (rho_hi - rho_lo > gap) {
-        if (used >= O.o.max_iter) { final_reason = TACTA_REASON_MAXITER; break; }
-        const double rho = 0.5 * (rho_hi + rho_lo);
-        ctl_set_trip<<<1, 1, 0, O.s>>>(p->ctl, rho, (int)(O.o.max_iter - used));
-        ++launches;
-        CUDA_TRY(cudaGetLastError());
-        if (have_witness) {
-            CUDA_TRY(cudaMemcpyAsync(p->x, p->wx, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
-            CUDA_TRY(cudaMemcpyAsync(p->d, p->wd, sizeof(double) * mm, cudaMemcpyDeviceToDevice, O.s));
-        } else {
-            CUDA_TRY(cudaMemsetAsync(p->x, 0, sizeof(double) * p->n, O.s));
-            CUDA_TRY(cudaMemcpyAsync(p->d, rhs, sizeof(double) * mm, cudaMemcpyDeviceToDevice, O.s));
-        }
-        CUDA_TRY(launch_reduce_vec(L, mm, p->d, rhs, FinArgs{FIN_TRIP_START, 0, nullptr}, GATE_FORCE));
-        if ((st = ta_iterate(p, O, normal, O.o.max_iter - used, &launches)) != TACTA_OK) return st;
-        if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
-        const Ctl c = *p->stage;
-        used += c.k;
-        ++trips;
-        if (c.status == TACTA_REASON_RESIDUAL) {
-            rho_hi = rho;
-            CUDA_TRY(cudaMemcpyAsync(p->xbest, p->x, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
-        } else if (c.status == TACTA_REASON_WITNESS) {
-            rho_lo = c.db / std::sqrt(c.cn2);
-            have_witness = true;
-            CUDA_TRY(cudaMemcpyAsync(p->wx, p->x, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
-            CUDA_TRY(cudaMemcpyAsync(p->wd, p->d, sizeof(double) * mm, cudaMemcpyDeviceToDevice, O.s));
-        } else if (c.status == TACTA_REASON_NORMAL) {
-            CUDA_TRY(cudaMemcpyAsync(p->xbest, p->x, sizeof(double) * p->n, cudaMemcpyDeviceToDevice, O.s));
-            final_reason = TACTA_REASON_NORMAL;
-            break;
-        } else {
-            final_reason = c.status;
-            break;
-        }
-    }
+    // phase 2: Algorithm 2.5 on (A, b) or (AᵀA, Aᵀb) from CTA's x
+    BisectOut bo;
+    if ((st = minnorm_bisect(p, O, normal, nullptr, 0, &launches, &bo)) != TACTA_OK) return st;
+    const double rho_hi = bo.rho_hi, rho_lo = bo.rho_lo;
+    const int64_t used = bo.used;
+    const int trips = bo.trips;
+    const int final_reason = bo.reason;
     // residuals of the original system at x_best
     if ((st = exit_residuals(p, O, p->xbest, &launches)) != TACTA_OK) return st;
     if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
@@ -1259,6 +1303,62 @@ static tacta_status plan_minnorm(Plan* p, const VecIO& io, const tacta_options* 
     out_info.rho = rho_hi;
     out_info.rho_lower = rho_lo;
     out_info.trips = trips;
+    out_info.normal_system = normal;
+    out_info.launches = launches;
+    if (info) *info = out_info;
+    return out;
+}
+
+// Algorithm 2.5 alone from a caller's approximate solution x_eps of M x = rhs (see
+// minnorm_bisect), with the per-trip log on the host.
+static tacta_status plan_bisect(Plan* p, const double* b, const double* x_eps, int normal, const tacta_options* opt,
+                                double* x_out, double* trip_log, int log_cap, tacta_info* info) {
+    Opts O = resolve(opt);
+    tacta_status st;
+    if ((st = validate_opts(O.o)) != TACTA_OK) return st;
+    if (!x_eps) { set_error("x_eps is NULL"); return TACTA_ERR_INVALID; }
+    if (normal != 0 && normal != 1) { set_error("normal must be 0 or 1"); return TACTA_ERR_INVALID; }
+    if (log_cap < 0 || (log_cap > 0 && !trip_log)) { set_error("trip_log / log_cap"); return TACTA_ERR_INVALID; }
+    CUDA_TRY(cudaSetDevice(p->device));
+    VecIO io{b, x_eps, x_out, nullptr, 0};
+    if ((st = load_b(p, O, io)) != TACTA_OK) return st;
+    if ((st = ensure_hist(p, 1)) != TACTA_OK) return st;
+    int64_t launches = 0;
+    LaunchCtx L{O.s, p->ctl, p->partials, p->grid, &launches};
+    EpiArgs none{nullptr, nullptr, nullptr};
+    // ||b||² and ||Aᵀb||² of the original system, for the exit residuals
+    if ((st = write_ctl(p, O.s, base_ctl(O, 0))) != TACTA_OK) return st;
+    CUDA_TRY(launch_reduce_vec(L, p->m, p->b, nullptr, FinArgs{FIN_SETUP_B, 0, nullptr}, GATE_FORCE));
+    CUDA_TRY(launch_spmv(L, p->At, p->b, p->tmp_n, EPI_NORM, none, FinArgs{FIN_SETUP_MTB, 0, nullptr}, GATE_FORCE));
+    if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
+    const double bn2 = p->stage->bn2, atbn2 = p->stage->mtbn2;
+    tacta_info out_info;
+    std::memset(&out_info, 0, sizeof(out_info));
+    if (bn2 == 0.0) {
+        CUDA_TRY(cudaMemsetAsync(p->x, 0, sizeof(double) * p->n, O.s));
+        if ((st = store_out(p, O, io, p->x, 0)) != TACTA_OK) return st;
+        out_info.reason = TACTA_REASON_ZERO_RHS;
+        if (info) *info = out_info;
+        return TACTA_OK;
+    }
+    CUDA_TRY(cudaMemcpyAsync(p->x, x_eps, sizeof(double) * p->n, cudaMemcpyDefault, O.s));
+    BisectOut bo;
+    if ((st = minnorm_bisect(p, O, normal, trip_log, log_cap, &launches, &bo)) != TACTA_OK) return st;
+    if ((st = exit_residuals(p, O, p->xbest, &launches)) != TACTA_OK) return st;
+    if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
+    const Ctl c = *p->stage;
+    if ((st = store_out(p, O, io, p->xbest, 0)) != TACTA_OK) return st;
+    const tacta_status out = status_of(bo.reason);
+    if (out == TACTA_ERR_NONFINITE) set_error("non-finite value in a reduction");
+    if (out == TACTA_ERR_TIMEOUT) set_error("a bounded wait inside a kernel gave up");
+    out_info.status = out;
+    out_info.reason = bo.reason;
+    out_info.iters = (int32_t)bo.used;
+    out_info.rel_res = std::sqrt(c.red[0] / bn2);
+    out_info.rel_normal_res = atbn2 > 0 ? std::sqrt(c.red[2] / atbn2) : 0.0;
+    out_info.rho = bo.rho_hi;
+    out_info.rho_lower = bo.rho_lo;
+    out_info.trips = bo.trips;
     out_info.normal_system = normal;
     out_info.launches = launches;
     if (info) *info = out_info;
@@ -1339,6 +1439,14 @@ tacta_status tacta_plan_ta(tacta_plan plan, const double* b, const double* x0, c
 tacta_status tacta_plan_minnorm(tacta_plan plan, const double* b, const double* x0, const tacta_options* opt,
                                 double* x_out, double* hist, int32_t hist_cap, tacta_info* info) {
     return plan_call(2, plan, b, x0, opt, x_out, hist, hist_cap, info);
+}
+
+tacta_status tacta_plan_minnorm_bisect(tacta_plan plan, const double* b, const double* x_eps, int32_t normal,
+                                       const tacta_options* opt, double* x_out, double* trip_log, int32_t log_cap,
+                                       tacta_info* info) {
+    set_error("");
+    if (!plan || !plan->p) { set_error("plan is NULL"); return TACTA_ERR_INVALID; }
+    return plan_bisect(plan->p, b, x_eps, normal, opt, x_out, trip_log, log_cap, info);
 }
 
 tacta_status tacta_plan_transpose(tacta_plan plan, const tacta_options* opt, tacta_plan* out) {

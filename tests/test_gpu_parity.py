@@ -3,8 +3,9 @@
 Tolerances (FP64 path): relative solution error <= 1e-9 and final true
 relative residual equal within 1e-10. Fixed-length runs must take the same
 number of steps with the same residual history; runs to a tolerance must stop
-within the spread of stop indices the oracle itself shows under 1e-16
-perturbations of b (see oracle_iteration_spread).
+inside the window the oracle's own stop index spans under 1e-16 perturbations
+of b (tests/oracle_spread.py: 16 perturbed runs, Tukey's fences, +-1 step),
+which is the unperturbed index +-1 whenever the oracle's index does not move.
 """
 import numpy as np
 import pytest
@@ -12,6 +13,7 @@ import pytest
 import gen
 import oracle
 from oracle import Reason
+from tests.oracle_spread import stop_index_window
 
 pytestmark = pytest.mark.gpu
 
@@ -58,20 +60,10 @@ def relerr(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def oracle_iteration_spread(solve, p, x0, okw, n=3):
-    """Stop indices of the oracle on right-hand sides perturbed by 1e-16 relative
-    noise: the spread rounding alone produces in the method (seeded)."""
-    rng = np.random.default_rng(99)
-    its = []
-    for _ in range(n):
-        bp = p.b * (1.0 + 1e-16 * rng.standard_normal(p.m))
-        its.append(solve(oracle.make_operator(p), bp, x0, **okw).iters)
-    return min(its), max(its)
-
-
-def check_iters(got, ref_iters, spread):
-    lo, hi = min(spread[0], ref_iters), max(spread[1], ref_iters)
-    assert 0.75 * lo - 3 <= got <= 1.25 * hi + 3, (got, ref_iters, spread)
+def check_iters(got, solve_name, p, x0, okw):
+    """The GPU's stop index lies in the oracle's own rounding window (stop_index_window)."""
+    lo, hi, its = stop_index_window(solve_name, p, x0, okw)
+    assert lo <= got <= hi, (got, lo, hi, sorted(its.tolist()))
 
 
 def check_cta(tacta, p, x0=None, iter_slack=None, **kw):
@@ -84,7 +76,7 @@ def check_cta(tacta, p, x0=None, iter_slack=None, **kw):
     ref = oracle.cta_solve(oracle.make_operator(p), p.b, x0, **okw)
     xg = x.cpu().numpy()
     if iter_slack is None:       # run to tolerance: the stop index is rounding-sensitive
-        check_iters(info["iters"], ref.iters, oracle_iteration_spread(oracle.cta_solve, p, x0, okw))
+        check_iters(info["iters"], "cta_solve", p, x0, okw)
         assert info["reason_name"] == REASON[int(ref.reason)]
     else:
         assert abs(info["iters"] - ref.iters) <= iter_slack, (info, ref.iters, ref.reason)
@@ -273,7 +265,7 @@ def check_ta(tacta, p, x0=None, iter_slack=None, x_tol=X_TOL, **kw):
     ref = oracle.ta_solve(oracle.make_operator(p), p.b, x0, **okw)
     xg = x.cpu().numpy()
     if iter_slack is None:
-        check_iters(info["iters"], ref.iters, oracle_iteration_spread(oracle.ta_solve, p, x0, okw))
+        check_iters(info["iters"], "ta_solve", p, x0, okw)
     else:
         assert abs(info["iters"] - ref.iters) <= iter_slack, (info, ref.iters, ref.reason)
     assert relerr(xg, ref.x) <= x_tol, relerr(xg, ref.x)
