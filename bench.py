@@ -13,17 +13,16 @@ value      : F_t iterations per second over the K timed steps (device events),
 e2e        : same metric through the one-shot C ABI call with host buffers
              (pinned): A and b copied in, plan built (device transpose), solve,
              x and the residual history copied out, all inside the timed region.
-roofline   : the fused chain kernel (the 2t products with Aᵀ and A of each F_t step in
-             one cooperative launch, on the diagonal form of the stencil), timed with
-             CUDA events around every launch inside a profiled solve of the same
-             workload; reported per product (a launch's work and time over its 2t
-             products) as HBM bandwidth on the CSR product's algorithmic bytes
-             12 nnz + 4 (rows + 1) + 8 cols + 8 rows (79.95 MB) against the measured
-             copy peak. Beside it: the whole F_t step's algorithmic bytes at the
-             measured rate ("step"), the DRAM bytes ncu counted ("dram"), the bytes
-             the diagonal form moves (8 k rows + rows + 8 cols + 8 rows, 57 MB,
-             "format") and the FP64 FMA rate against the nominal 1.25 TFLOP/s ("fp64":
-             one FMA per nonzero and per row, 12 MFLOP; the kernel's actual bound).
+roofline   : the fused step kernel (one cooperative launch per F_t step: the 2t products
+             with Aᵀ and A on the diagonal form of the stencil, the moments, the
+             auxiliary solve and the x, r update), timed with CUDA events around every
+             launch inside a profiled solve of the same workload, as HBM bandwidth on the
+             survey's algorithmic bytes of an F_t step (CSR products, 559.7 MB at the
+             mean order t = 3) against the measured copy peak. Beside it: the whole solve
+             step at the measured F_t rate ("step", gated residual launch and launch gaps
+             included), the DRAM bytes ncu counted ("dram"), the bytes the diagonal form
+             needs ("format") and the FP64 FMA rate against the nominal 1.25 TFLOP/s
+             ("fp64").
 cpu_baseline: the FP64 numpy oracle on the same workload, a bounded sample of
              CPU_SAMPLE_ITERS iterations, on all host cores (numpy's BLAS pool) and
              on one thread.
@@ -550,41 +549,47 @@ def main():
     clocks = clk.summary()
     last = infos[-1]
 
-    # ---------------- roofline: the products of the iteration, each timed with events
+    # ---------------- roofline: the fused step kernel, every launch timed with events
     _, _, prof = plan.cta(b, profile=1, **opts)
-    spmv_us = 1e3 * prof["spmv_ms"] / prof["spmv_count"]
-    fmt_bytes = prof["spmv_bytes"] / prof["spmv_count"]      # what the diagonal form moves per product
-    alg_bytes = survey_bytes_per_product(p.m, p.n, p.nnz)     # the CSR product's algorithmic bytes
-    flops = 2.0 * (p.nnz + p.m)                       # one FP64 FMA per nonzero and per row (the norm)
+    launch_us = 1e3 * prof["spmv_ms"] / prof["spmv_count"]
+    alg_bytes = prof["spmv_bytes"] / prof["spmv_count"]      # the survey's bytes per F_t step
+    ts = [fpt_schedule(k) for k in range(prof["spmv_count"])]
+    t_mean = statistics.fmean(ts)
     peak, peak_kind = peaks()
-    achieved = alg_bytes / (spmv_us * 1e-6) / 1e9
+    achieved = alg_bytes / (launch_us * 1e-6) / 1e9
     traffic = traffic_record()
     fpt_bytes = statistics.fmean(survey_bytes_per_fpt(p.m, p.n, p.nnz, fpt_schedule(k))
                                  for k in range(iters_per_step))
     step_gbs = fpt_bytes * value / 1e9
+    rows_t = -(-p.m // 256) * 256
+    dia_product = 8.0 * 5 * rows_t + rows_t + 8.0 * p.n + 8.0 * p.m     # the diagonal form, k = 5
+    fmt_bytes = statistics.fmean(2 * t * dia_product + 8.0 * (t + 2) * (p.m + p.n) for t in ts)
+    fmas = statistics.fmean(2 * t * (p.nnz + p.m) + t * (p.n + p.m) + p.m for t in ts)
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
         "traffic": traffic, "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)",
-        "kernel": "cta_chain<double, DiaFmt> (the F_t step's 2t products with A\u1d40 and A in one "
-                  "cooperative launch on the diagonal form: bulk-copy row tiles, warp-specialised, "
-                  "grid-wide barriers between products)",
-        "unit_of_work": "one product of the chain (2t per launch): the CSR product's algorithmic bytes "
-                        "12 nnz + 4 (rows + 1) + 8 cols + 8 rows over the timed launches' summed duration "
-                        "per product",
-        "products_timed": prof["spmv_count"], "avg_product_us": spmv_us, "bytes_per_product": alg_bytes,
-        "traffic_unit": "DRAM bytes per product (ncu)",
-        # the whole F_t step against the same peak: the unfused step's algorithmic bytes at the
-        # schedule's mean order, times the measured F_t rate
+        "kernel": "cta_chain<double, DiaFmt, true>: one cooperative launch per F_t step -- the 2t "
+                  "products with A\u1d40 and A on the diagonal form (bulk-copy row tiles, "
+                  "warp-specialised, grid-wide barriers between products), then in every block the "
+                  "moments, the auxiliary solve and the block's slice of the x and r update",
+        "unit_of_work": "one F_t step (one launch): the survey's algorithmic bytes of an unfused F_t "
+                        "step of order t, t (B_A + B_At) + 8 t (2 m + 2 n) + 8 (t + 2)(m + n) with "
+                        "B_A = 12 nnz + 4 (m + 1), over the launch's event-timed duration",
+        "launches_timed": prof["spmv_count"], "avg_launch_us": launch_us, "mean_t": t_mean,
+        "bytes_per_launch": alg_bytes, "traffic_unit": "DRAM bytes per launch at t = 3 (ncu)",
+        # the whole solve step (the step kernel plus the gated true-residual launch and the
+        # gaps between launches) against the same peak
         "step": {"bytes_per_fpt": fpt_bytes, "achieved": step_gbs, "unit": "GB/s", "frac": step_gbs / peak},
-        # what DRAM actually served (ncu's dram__bytes per product over the event-timed product)
-        "dram": ({"achieved": traffic / (spmv_us * 1e-6) / 1e9, "unit": "GB/s",
-                  "frac": traffic / (spmv_us * 1e-6) / 1e9 / peak} if traffic else None),
-        # the diagonal form moves fewer bytes than CSR, and the FP64 pipe bounds it
-        "format": {"bytes_per_product": fmt_bytes, "achieved": fmt_bytes / (spmv_us * 1e-6) / 1e9,
-                   "unit": "GB/s", "frac": fmt_bytes / (spmv_us * 1e-6) / 1e9 / peak},
-        "fp64": {"bound": "alu", "flops_per_product": flops, "achieved": flops / (spmv_us * 1e-6) / 1e12,
+        # what DRAM actually served (ncu's dram__bytes per launch over the event-timed launch)
+        "dram": ({"achieved": traffic / (launch_us * 1e-6) / 1e9, "unit": "GB/s",
+                  "frac": traffic / (launch_us * 1e-6) / 1e9 / peak} if traffic else None),
+        # the diagonal form moves fewer bytes than CSR: values only, k = 5 per row
+        "format": {"bytes_per_launch": fmt_bytes, "achieved": fmt_bytes / (launch_us * 1e-6) / 1e9,
+                   "unit": "GB/s", "frac": fmt_bytes / (launch_us * 1e-6) / 1e9 / peak},
+        "fp64": {"bound": "alu", "flops_per_launch": 2.0 * fmas,
+                 "achieved": 2.0 * fmas / (launch_us * 1e-6) / 1e12,
                  "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
-                 "frac": flops / (spmv_us * 1e-6) / 1e12 / FP64_TFLOPS_NOMINAL,
+                 "frac": 2.0 * fmas / (launch_us * 1e-6) / 1e12 / FP64_TFLOPS_NOMINAL,
                  "peak_kind": "nominal FP64 on CUDA cores: 152 SMs x 2 FMA/clk x 2.07 GHz x 2 flops "
                               "(not measured by the driver)"}}
 

@@ -131,7 +131,17 @@ typedef struct {
                                 on at most 5 diagonals (col - row constant), else on the run-staged
                                 CSR; 2 = the same launch, always on the run-staged CSR; 0 = one
                                 launch per product. Same arithmetic per row; the moments' partial
-                                sums are added in a different fixed order                       */
+                                sums are added in a different fixed order. With 1 and 2 the
+                                launch is the whole F_t step: after the products every block
+                                solves the auxiliary equation from the same moment partials and
+                                updates its slice of x and r (one launch per step); 3 = the
+                                products of option 1 in one launch, the auxiliary solve and the
+                                update as two more launches                                       */
+    int32_t wait_limit_log2; /* the fused chain's grid-wide waits (a block waiting for every block
+                                to finish the previous product) give up after 2^this SM cycles
+                                and end the call with TACTA_ERR_TIMEOUT; 0 = 31 (about a second).
+                                Small values exist so that tests can make a wait run out; the
+                                waits on the block's own copies keep the ~1 s limit          */
     double rho_max;          /* ta_solve: stop (reason RHO_BOUND) once rho exceeds this; <= 0: none */
     void* stream;            /* cudaStream_t (NULL: legacy default stream)                      */
 } tacta_options;
@@ -152,16 +162,23 @@ typedef struct {
     int32_t normal_system;   /* minnorm: 1 when TA ran on (AᵀA, Aᵀb)                    */
     int32_t hist_len;        /* entries written to hist                                */
     int64_t launches;        /* GPU kernels launched by the call                        */
-    int32_t spmv_count;      /* profile = 1: products timed (iteration chain only)      */
+    int32_t spmv_count;      /* profile = 1: units timed. Fused step (fused_chain 1, 2): one
+                                unit per F_t step launch; otherwise one per product of the
+                                iteration chain                                          */
     int32_t spmv_pad;
-    double spmv_ms;          /* profile = 1: summed device time of those products       */
-    double spmv_bytes;       /* profile = 1: their algorithmic bytes (values, indices,
-                                row offsets, input vector once, output vector once)     */
+    double spmv_ms;          /* profile = 1: summed device time of those launches       */
+    double spmv_bytes;       /* profile = 1: their algorithmic bytes. Per product: values,
+                                indices, row offsets, input vector once, output vector
+                                once. Per fused F_t step of order t: t such products with
+                                A and t with Aᵀ in CSR, the chain's vectors and the update's
+                                8 (t + 2)(m + n) (4-byte values and vectors on the FP32
+                                chain)                                                   */
 } tacta_info;
 
 /* Fill *opt with the defaults: tol 1e-10, tol_normal -1, tol_cta 0, pivot_tol 1e-12,
    max_iter 1000, t_max 5, ping-pong cycle, R = 40, use_graph 1, poll_every 64, profile 0,
-   precision FP64, nonneg 0, enhanced 0, fused_chain 1, rho_max 0 (none), NULL stream. */
+   precision FP64, nonneg 0, enhanced 0, fused_chain 1, wait_limit_log2 0 (2^31 cycles),
+   rho_max 0 (none), NULL stream. */
 void tacta_default_options(tacta_options* opt);
 
 /*

@@ -49,7 +49,8 @@ class tacta_options(ctypes.Structure):
                 ("recompute_every", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("poll_every", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("nonneg", ctypes.c_int32), ("enhanced", ctypes.c_int32),
-                ("fused_chain", ctypes.c_int32), ("rho_max", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("fused_chain", ctypes.c_int32), ("wait_limit_log2", ctypes.c_int32),
+                ("rho_max", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
 
 class tacta_info(ctypes.Structure):

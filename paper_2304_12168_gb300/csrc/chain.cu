@@ -15,14 +15,24 @@
 //     indexing data) does not depend on the counter: the producer
 //     warp issues it into the free stages before waiting, so the copies of the next
 //     product are in flight while the slowest blocks finish the current one;
-//   * the moments are summed from the per-block partials by the step's auxiliary
-//     kernel (fixed order, deterministic), not by a last block.
+//   * the fused step (STEP = true) also finishes the F_t step in the same launch: after
+//     the last product every block waits for all G blocks, sums the moments from the
+//     per-block partials in one fixed order (so every block holds the same bits), takes
+//     the step decision and solves the auxiliary equation (Eq. eqcoeff) redundantly on
+//     one thread, and then updates its slice of x and r (Eqs. CTAGEN7, CTAGEN7A); the
+//     last block to finish (atomic ticket) adds the ||r||² partials and runs the stop
+//     tests. One launch per F_t step instead of three;
+//   * without STEP the moments are summed by the step's auxiliary kernel (fixed order,
+//     deterministic) and the update runs as its own launch.
 // Every wait is bounded (about a second); a block that gives up sets the TIMEOUT stop
 // reason, which every other waiting block polls, so the launch always ends.
 #include <algorithm>
 #include <cstddef>
+#include <type_traits>
 
 #include "internal.h"
+#include "aux_step.cuh"
+#include "finish.cuh"
 #include "mbarrier.cuh"
 #include "rowtiles.cuh"
 
@@ -39,17 +49,106 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
 }
 
 // One thread: wait until the grid-wide counter reaches `target` (all blocks arrived
-// after the previous product). Gives up when the solve stops (another block's timeout)
-// or after ~2^31 cycles. The proxy fence orders the bulk copies (async proxy) that
-// follow after the acquire of the other blocks' plain stores.
+// after the previous product). Gives up when another block timed out (the TIMEOUT
+// stop reason; no other reason is set while a block of the launch can still wait) or
+// after ctl->wait_cycles SM cycles (2^31, about a second, unless the caller asked for
+// less). The proxy fence orders the bulk copies (async proxy) that follow
+// after the acquire of the other blocks' plain stores.
 __device__ bool grid_wait(Ctl* ctl, uint32_t target) {
     const long long t0 = clock64();
+    const long long limit = ctl->wait_cycles > 0 ? ctl->wait_cycles : (1LL << 31);
     while (ld_acquire_gpu(&ctl->chain_bar) < target) {
-        if (*(volatile int32_t*)&ctl->status != 0) return false;
-        if (clock64() - t0 > (1LL << 31)) return false;
+        if (*(volatile int32_t*)&ctl->status == TACTA_REASON_TIMEOUT) return false;
+        if (clock64() - t0 > limit) return false;
     }
     asm volatile("fence.proxy.async.global;" ::: "memory");
     return true;
+}
+
+// The update of the fused step (Eqs. CTAGEN7, CTAGEN7A) over this thread's slice:
+// x += sum_j ax_j z_j, r -= sum_j al_j u_j, and the thread's sum of r_i² (FP64 chain:
+// al = ax = alpha; FP32 chain: al = alpha, ax = alpha * xscale on the correction dx).
+// Every thread of every block takes 16-byte chunks in a grid-wide stride; each entry's
+// FMAs run in j order (as the separate update kernels do). The chain vectors were written
+// by other blocks in this launch, so they are read through L2 (ld.global.cg), not the
+// read-only path.
+template <int T, typename V>
+__device__ __forceinline__ double step_update(const StepArgs<V>& sa, const ChainVecs<V>& vec, const double* alpha) {
+    constexpr int W = 16 / (int)sizeof(V);
+    using VW = typename std::conditional<sizeof(V) == 8, double2, float4>::type;
+    V al[T], ax[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+        al[j] = (V)alpha[j];
+        ax[j] = sizeof(V) == 8 ? (V)alpha[j] : (V)(alpha[j] * (double)sa.xscale);
+    }
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // x (n entries)
+    const int64_t nx = sa.n / W;
+    for (int64_t c = gt; c < nx; c += nth) {
+        VW zv[T];
+#pragma unroll
+        for (int j = 0; j < T; ++j) zv[j] = __ldcg(reinterpret_cast<const VW*>(vec.z[j]) + c);
+        VW xv = __ldcg(reinterpret_cast<const VW*>(sa.x) + c);
+        V* xe = reinterpret_cast<V*>(&xv);
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            V v = xe[e];
+#pragma unroll
+            for (int j = 0; j < T; ++j) v = fma(ax[j], reinterpret_cast<const V*>(&zv[j])[e], v);
+            xe[e] = v;
+        }
+        reinterpret_cast<VW*>(sa.x)[c] = xv;
+    }
+    for (int64_t i = nx * W + gt; i < sa.n; i += nth) {
+        V v = sa.x[i];
+#pragma unroll
+        for (int j = 0; j < T; ++j) v = fma(ax[j], __ldcg(vec.z[j] + i), v);
+        sa.x[i] = v;
+    }
+    // r (m entries) and its squared norm
+    V acc = V(0);
+    const int64_t nr = sa.m / W;
+    for (int64_t c = gt; c < nr; c += nth) {
+        VW uv[T];
+#pragma unroll
+        for (int j = 0; j < T; ++j) uv[j] = __ldcg(reinterpret_cast<const VW*>(vec.u[j]) + c);
+        VW rv = __ldcg(reinterpret_cast<const VW*>(sa.r) + c);
+        V* re = reinterpret_cast<V*>(&rv);
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+            V v = re[e];
+#pragma unroll
+            for (int j = 0; j < T; ++j) v = fma(-al[j], reinterpret_cast<const V*>(&uv[j])[e], v);
+            re[e] = v;
+            acc = fma(v, v, acc);
+        }
+        reinterpret_cast<VW*>(sa.r)[c] = rv;
+    }
+    for (int64_t i = nr * W + gt; i < sa.m; i += nth) {
+        V v = sa.r[i];
+#pragma unroll
+        for (int j = 0; j < T; ++j) v = fma(-al[j], __ldcg(vec.u[j] + i), v);
+        sa.r[i] = v;
+        acc = fma(v, v, acc);
+    }
+    return (double)acc;
+}
+
+template <typename V>
+__device__ __noinline__ double step_update_t(const StepArgs<V>& sa, const ChainVecs<V>& vec, const double* alpha,
+                                             int t) {
+    switch (t) {
+    case 1: return step_update<1, V>(sa, vec, alpha);
+    case 2: return step_update<2, V>(sa, vec, alpha);
+    case 3: return step_update<3, V>(sa, vec, alpha);
+    case 4: return step_update<4, V>(sa, vec, alpha);
+    case 5: return step_update<5, V>(sa, vec, alpha);
+    case 6: return step_update<6, V>(sa, vec, alpha);
+    case 7: return step_update<7, V>(sa, vec, alpha);
+    default: return step_update<8, V>(sa, vec, alpha);
+    }
 }
 
 __device__ __forceinline__ double chain_warp_sum(double v) {
@@ -61,9 +160,9 @@ __device__ __forceinline__ double chain_warp_sum(double v) {
 __device__ __forceinline__ double sq_acc(double s, double a) { return fma(s, s, a); }
 __device__ __forceinline__ float sq_acc(float s, float a) { return fmaf(s, s, a); }
 
-template <typename V, class F>
+template <typename V, class F, bool STEP>
 __global__ void __launch_bounds__(kRwThreads, ChainShape<V>::MINB)
-cta_chain(typename F::Ops ops, ChainVecs<V> vec, int t, float scale, Ctl* ctl, double* part) {
+cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t, float scale, Ctl* ctl, double* part) {
     constexpr int S = ChainShape<V>::S;
     using Stage = typename F::Stage;
     using Meta = typename F::Meta;
@@ -73,6 +172,7 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, int t, float scale, Ctl* ctl, d
     __shared__ double red[2][kTileRows];
     __shared__ volatile int failed;
     __shared__ int stopped;
+    __shared__ int last_block;   // fused step: this block arrived last after the last product
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int G = gridDim.x, P = 2 * t;
     if (tid == 0) {
@@ -82,6 +182,7 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, int t, float scale, Ctl* ctl, d
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         failed = 0;
+        last_block = 0;
         stopped = ctl->status != 0;
         if (!stopped && blockIdx.x == 0) ctl->matvecs += P;
     }
@@ -193,34 +294,118 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, int t, float scale, Ctl* ctl, d
                 s = chain_warp_sum(s);
                 if (lane == 0) {
                     part[(size_t)p * G + blockIdx.x] = s;
-                    if (p + 1 < P) {
+                    if (STEP || p + 1 < P) {   // the fused step also counts the last product
                         asm volatile("fence.proxy.async.global;" ::: "memory");
                         __threadfence();
-                        atomicAdd(&ctl->chain_bar, 1u);
+                        const uint32_t old = atomicAdd(&ctl->chain_bar, 1u);
+                        if (STEP && p + 1 == P && old + 1u == (uint32_t)P * (uint32_t)G) {
+                            __threadfence();   // every block's partials of this step are visible
+                            last_block = 1;
+                        }
                     }
                 }
             }
         }
+    }
+    if constexpr (STEP) {
+        // ---- the rest of the F_t step, all nine warps. Every copy of this block has
+        // landed (consumers waited on every armed stage; a producer that gave up drained).
+        // The block that arrived last after the last product sums the moments and takes
+        // the step decision (a warp solves the auxiliary equation); the others wait for
+        // its flag and read alpha. Then every block updates its slice of x and r.
+        __shared__ Ctl sc;
+        __shared__ int decision;
+        __syncthreads();
+        if (failed) return;
+        if (last_block) {
+            {
+                const uint64_t* src = reinterpret_cast<const uint64_t*>(ctl);
+                uint64_t* dst = reinterpret_cast<uint64_t*>(&sc);
+                for (int i = tid; i < (int)(sizeof(Ctl) / 8); i += kRwThreads) dst[i] = __ldcg(src + i);
+            }
+            __syncthreads();
+            sum_moment_partials(&sc, t, part, G, ctl);   // phi_1..phi_2t, also into ctl->phi
+            if (warp == 0) {
+                int st2 = 0;
+                for (int i = 1; i <= 2 * t; ++i)
+                    if (!finite(sc.phi[i])) st2 = TACTA_REASON_NONFINITE;
+                if (st2 == 0 && sc.phi[1] <= __dmul_rn(sc.nrm_thr, sc.cs2)) st2 = TACTA_REASON_NORMAL;
+                if (st2 == 0 && sc.enhanced && t >= 2) {
+                    if (lane == 0) enhanced_stop(&sc, t);   // sets sc.enh_stop, sc.alpha
+                    __syncwarp();
+                }
+                if (st2 == 0 && !sc.enh_stop) {
+                    sc.rank = hankel_solve_warp(sc.phi, t, sc.pivot_tol, sc.alpha);
+                    if (sc.rank == 0) st2 = TACTA_REASON_BREAKDOWN;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    decision = st2;
+                    if (st2 != 0) {
+                        ctl->status = st2;
+                    } else {
+                        for (int k = 0; k < t; ++k) ctl->alpha[k] = sc.alpha[k];
+                        ctl->rank = sc.rank;
+                        if (sc.enh_stop) ctl->enh_stop = 1;
+                    }
+                    __threadfence();
+                    atomicExch(&ctl->step_flag, 1u);
+                }
+            }
+            __syncthreads();
+        } else {
+            if (tid == 0) {
+                const long long t0 = clock64();
+                const long long limit = ctl->wait_cycles > 0 ? ctl->wait_cycles : (1LL << 31);
+                bool ok = true;
+                while (ld_acquire_gpu(&ctl->step_flag) == 0u) {
+                    if (*(volatile int32_t*)&ctl->status == TACTA_REASON_TIMEOUT || clock64() - t0 > limit) {
+                        ok = false;
+                        break;
+                    }
+                }
+                if (!ok) {
+                    failed = 1;
+                    atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+                } else {
+                    decision = __ldcg(&ctl->status);
+                    sc.enh_stop = __ldcg(&ctl->enh_stop);
+                }
+            }
+            __syncthreads();
+            if (failed) return;
+            if (tid < t) sc.alpha[tid] = __ldcg(&ctl->alpha[tid]);
+            __syncthreads();
+        }
+        if (decision != 0 && !sc.enh_stop) return;   // NORMAL, NONFINITE, BREAKDOWN or TIMEOUT: the solve ends
+        const double acc = step_update_t<V>(sa, vec, sc.alpha, t);
+        reduce_and_finish<1, kRwThreads, true>(acc, 0.0, ctl, sa.upart, FinArgs{FIN_CTA_UPDATE, 0, sa.hist, 1});
     }
 }
 
 template <typename V, class F>
 static size_t chain_smem() { return (size_t)ChainShape<V>::S * sizeof(typename F::Stage); }
 
+// blocks of the cooperative launch: all resident, for both the chain-only and the fused
+// step kernel (the smaller of their occupancies)
 template <typename V, class F>
 static int chain_grid_t(int sms, int max_tiles) {
     static const char attr_key = 0;
     if (!done_on_device(&attr_key)) {
-        if (cudaFuncSetAttribute(cta_chain<V, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(cta_chain<V, F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)chain_smem<V, F>()) != cudaSuccess ||
+            cudaFuncSetAttribute(cta_chain<V, F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)chain_smem<V, F>()) != cudaSuccess)
             return 0;
         mark_done_on_device(&attr_key);
     }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cta_chain<V, F>, kRwThreads, chain_smem<V, F>()) !=
-        cudaSuccess)
+    int per_sm = 0, per_sm2 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cta_chain<V, F, false>, kRwThreads,
+                                                      chain_smem<V, F>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, cta_chain<V, F, true>, kRwThreads,
+                                                      chain_smem<V, F>()) != cudaSuccess)
         return 0;
-    return std::max(0, std::min(per_sm * sms, max_tiles));
+    return std::max(0, std::min(std::min(per_sm, per_sm2) * sms, max_tiles));
 }
 
 int cta_chain_grid(int sms, int max_tiles, bool fp32, bool dia) {
@@ -237,9 +422,9 @@ int cta_chain_grid(int sms, int max_tiles, bool fp32, bool dia) {
     return g;
 }
 
-template <typename V, class F>
-static cudaError_t launch_chain_t(const LaunchCtx& L, const typename F::Ops& ops, const ChainVecs<V>& v, int t,
-                                  float scale, double* part, int grid) {
+template <typename V, class F, bool STEP>
+static cudaError_t launch_chain_t(const LaunchCtx& L, const typename F::Ops& ops, const ChainVecs<V>& v,
+                                  const StepArgs<V>& sa, int t, float scale, double* part, int grid) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kRwThreads);
@@ -250,29 +435,38 @@ static cudaError_t launch_chain_t(const LaunchCtx& L, const typename F::Ops& ops
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, cta_chain<V, F>, ops, v, t, scale, L.ctl, part);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, cta_chain<V, F, STEP>, ops, v, sa, t, scale, L.ctl, part);
     if (L.launches) ++*L.launches;
     return e;
 }
 
+// sa == nullptr: the chain alone (the auxiliary step and the update follow as their own
+// launches); else the fused step
+template <typename V, class F>
+static cudaError_t launch_chain_any(const LaunchCtx& L, const typename F::Ops& ops, const ChainVecs<V>& v,
+                                    const StepArgs<V>* sa, int t, float scale, double* part, int grid) {
+    if (sa) return launch_chain_t<V, F, true>(L, ops, v, *sa, t, scale, part, grid);
+    return launch_chain_t<V, F, false>(L, ops, v, StepArgs<V>{}, t, scale, part, grid);
+}
+
 cudaError_t launch_cta_chain(const LaunchCtx& L, const ChainOps<double>& ops, const ChainVecs<double>& v, int t,
-                             double* part, int grid) {
-    return launch_chain_t<double, RunFmt<double>>(L, ops, v, t, 1.0f, part, grid);
+                             double* part, int grid, const StepArgs<double>* sa) {
+    return launch_chain_any<double, RunFmt<double>>(L, ops, v, sa, t, 1.0f, part, grid);
 }
 
 cudaError_t launch_cta_chain32(const LaunchCtx& L, const ChainOps<float>& ops, const ChainVecs<float>& v, int t,
-                               float scale, double* part, int grid) {
-    return launch_chain_t<float, RunFmt<float>>(L, ops, v, t, scale, part, grid);
+                               float scale, double* part, int grid, const StepArgs<float>* sa) {
+    return launch_chain_any<float, RunFmt<float>>(L, ops, v, sa, t, scale, part, grid);
 }
 
 cudaError_t launch_cta_chain_dia(const LaunchCtx& L, const ChainOpsDia<double>& ops, const ChainVecs<double>& v,
-                                 int t, double* part, int grid) {
-    return launch_chain_t<double, DiaFmt<double>>(L, ops, v, t, 1.0f, part, grid);
+                                 int t, double* part, int grid, const StepArgs<double>* sa) {
+    return launch_chain_any<double, DiaFmt<double>>(L, ops, v, sa, t, 1.0f, part, grid);
 }
 
 cudaError_t launch_cta_chain_dia32(const LaunchCtx& L, const ChainOpsDia<float>& ops, const ChainVecs<float>& v,
-                                   int t, float scale, double* part, int grid) {
-    return launch_chain_t<float, DiaFmt<float>>(L, ops, v, t, scale, part, grid);
+                                   int t, float scale, double* part, int grid, const StepArgs<float>* sa) {
+    return launch_chain_any<float, DiaFmt<float>>(L, ops, v, sa, t, scale, part, grid);
 }
 
 }  // namespace tacta

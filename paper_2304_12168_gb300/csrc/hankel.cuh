@@ -105,3 +105,108 @@ static __host__ __device__ __noinline__ int hankel_solve_dev(const double* phi, 
 }
 
 }  // namespace tacta
+
+#ifdef __CUDACC__
+namespace tacta {
+
+// The same solve by one warp, lane i holding row i of L: every value is formed by the same
+// operations in the same order as hankel_solve_t<T> (so alpha is bit for bit the same),
+// but the rows of each Cholesky column are computed in parallel and each lane keeps only
+// its own row, which keeps the solve in registers inside kernels with a tight register
+// budget. Every lane of the warp must call it; lanes i < T write alpha[i]; returns the
+// rank (the same in every lane).
+template <int T>
+__device__ __forceinline__ int hankel_solve_warp_t(const double* phi, double pivot_tol, double* alpha) {
+    const int i = threadIdx.x & 31;
+    int tt = T;
+#pragma unroll
+    for (int k = T; k >= 1; --k)
+        if (!(phi[2 * k] > 0.0)) tt = k - 1;
+    const double si = i < tt ? TACTA_DIV(1.0, TACTA_SQRT(phi[2 * i + 2])) : 0.0;
+    double Lr[T], d[T];
+    double my_dinv = 0.0;
+#pragma unroll
+    for (int j = 0; j < T; ++j) { Lr[j] = 0.0; d[j] = 0.0; }
+    int rank = 0;
+    bool go = true;
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+        if (go && k < tt) {
+            const double sk = __shfl_sync(0xffffffffu, si, k);
+            double dk = TACTA_MUL(TACTA_MUL(sk, phi[2 * k + 2]), sk);
+#pragma unroll
+            for (int j = 0; j < k; ++j) {
+                const double lkj = __shfl_sync(0xffffffffu, Lr[j], k);
+                dk = TACTA_SUB(dk, TACTA_MUL(TACTA_MUL(lkj, lkj), d[j]));
+            }
+            if (dk > pivot_tol) {
+                d[k] = dk;
+                const double dinv = TACTA_DIV(1.0, dk);
+                if (i == k) my_dinv = dinv;
+                double v = TACTA_MUL(TACTA_MUL(si, phi[(i < T ? i : 0) + k + 2]), sk);
+#pragma unroll
+                for (int j = 0; j < k; ++j) {
+                    const double lkj = __shfl_sync(0xffffffffu, Lr[j], k);
+                    v = TACTA_SUB(v, TACTA_MUL(TACTA_MUL(Lr[j], lkj), d[j]));
+                }
+                if (i > k && i < T) Lr[k] = TACTA_MUL(v, dinv);
+                rank = k + 1;
+            } else {
+                go = false;
+            }
+        }
+    }
+    // L w = D phi_{1..}: lane i subtracts L[i][j] w_j as w_j becomes known (j ascending,
+    // the order of the row sum in hankel_solve_t)
+    double v = i < T ? TACTA_MUL(si, phi[i + 1]) : 0.0;
+    double wmine = 0.0;
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+        double wj = __shfl_sync(0xffffffffu, v, j);
+        wj = j < rank ? wj : 0.0;
+        if (i == j) wmine = wj;
+        if (i > j) v = TACTA_SUB(v, TACTA_MUL(Lr[j], wj));
+    }
+    const double yi = i < rank ? TACTA_MUL(wmine, my_dinv) : 0.0;
+    // column i of L into lane i (Lc[j] = L[j][i], j > i)
+    double Lc[T];
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+        Lc[j] = 0.0;
+#pragma unroll
+        for (int c = 0; c < j; ++c) {
+            const double ljc = __shfl_sync(0xffffffffu, Lr[c], j);
+            if (i == c) Lc[j] = ljc;
+        }
+    }
+    // Lᵀ beta = y, rows from the last: lane i's sum runs over j = i+1.. ascending
+    double beta_mine = 0.0;
+    double bj[T];
+#pragma unroll
+    for (int k = T - 1; k >= 0; --k) {
+        double b = yi;
+#pragma unroll
+        for (int j = k + 1; j < T; ++j)
+            if (j < rank) b = TACTA_SUB(b, TACTA_MUL(Lc[j], bj[j]));
+        bj[k] = __shfl_sync(0xffffffffu, b, k);
+        if (i == k) beta_mine = b;
+    }
+    if (i < T) alpha[i] = i < rank ? TACTA_MUL(si, beta_mine) : 0.0;
+    return rank;
+}
+
+static __device__ __noinline__ int hankel_solve_warp(const double* phi, int t, double pivot_tol, double* alpha) {
+    switch (t) {
+    case 1: return hankel_solve_warp_t<1>(phi, pivot_tol, alpha);
+    case 2: return hankel_solve_warp_t<2>(phi, pivot_tol, alpha);
+    case 3: return hankel_solve_warp_t<3>(phi, pivot_tol, alpha);
+    case 4: return hankel_solve_warp_t<4>(phi, pivot_tol, alpha);
+    case 5: return hankel_solve_warp_t<5>(phi, pivot_tol, alpha);
+    case 6: return hankel_solve_warp_t<6>(phi, pivot_tol, alpha);
+    case 7: return hankel_solve_warp_t<7>(phi, pivot_tol, alpha);
+    default: return hankel_solve_warp_t<8>(phi, pivot_tol, alpha);
+    }
+}
+
+}  // namespace tacta
+#endif

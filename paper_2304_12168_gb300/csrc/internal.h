@@ -35,6 +35,7 @@ struct Ctl {
     int32_t enhanced;      // CTA: the enhanced stop of Sec. 3.2 is on
     int32_t enh_stop;      // CTA: this step applies x^ and ends the solve (reason ENHANCED)
     uint32_t chain_bar;    // fused CTA chain: grid-wide arrivals (reset by the step's auxiliary kernel)
+    uint32_t step_flag;    // fused step: the step decision and alpha are in this block (reset with chain_bar)
     double bn2;            // ||b||²  (b = rhs of the operator in use)
     double inv_bn2;        // 1 / ||b||² (0 when b = 0): the history stores ||r||² / ||b||²
     double mtbn2;          // ||Mᵀ b||²
@@ -50,6 +51,7 @@ struct Ctl {
     double cs2;            // chain scale²: the chain's moments are cs2^k phi_k (1 on the FP64 path)
     double ref_eta2;       // mixed CTA: refine once ||r||² <= ref_eta2 * ||r||² at the last refinement (0: off)
     double ref_thr;        // that threshold, set by each true residual
+    int64_t wait_cycles;   // fused chain: a grid-wide wait gives up after this many SM cycles
     double phi[2 * kTMax + 2];
     double alpha[kTMax];
     double red[4];         // scratch results of setup reductions
@@ -76,6 +78,7 @@ struct FinArgs {
     int kind;
     int idx;              // FIN_PHI / FIN_STORE slot
     double* hist;         // device history buffer (capacity ctl->hist_cap)
+    int reset_bar = 0;    // the finisher also resets the fused step's grid-wide counter
 };
 
 // Epilogues of the matrix-vector kernels: y = A x, then per row
@@ -247,18 +250,32 @@ struct ChainOpsDia {             // the fused chain on operands in diagonal form
     int rows[2];
     int k;                       // diagonals (the same for A and Aᵀ)
 };
+// The rest of a fused F_t step (chain.cu): after the products every block solves the
+// auxiliary equation and updates its slice of x and r; the last block runs the update's
+// finisher (step count, history, stop tests).
+template <typename V>
+struct StepArgs {
+    V* x = nullptr;          // FP64 chain: x; FP32 chain: dx, the correction since the last refinement
+    V* r = nullptr;          // the residual, u_0 of the next step
+    int64_t m = 0, n = 0;
+    float xscale = 1.0f;     // FP32 chain: z_i carries a scale, x += xscale sum alpha_i z_i
+    double* hist = nullptr;  // history buffer of the finisher
+    double* upart = nullptr; // per-block partials of ||r||² (2 doubles per block)
+};
 // blocks of the cooperative chain launch (all resident), 0 if it cannot run here
 int cta_chain_grid(int sms, int max_tiles, bool fp32, bool dia);
+// sa == nullptr: the 2t products only (cta_aux_step and the update kernel follow);
+// else the whole F_t step in the one launch
 cudaError_t launch_cta_chain_dia(const LaunchCtx& L, const ChainOpsDia<double>& ops, const ChainVecs<double>& v,
-                                 int t, double* part, int grid);
+                                 int t, double* part, int grid, const StepArgs<double>* sa);
 cudaError_t launch_cta_chain_dia32(const LaunchCtx& L, const ChainOpsDia<float>& ops, const ChainVecs<float>& v,
-                                   int t, float scale, double* part, int grid);
+                                   int t, float scale, double* part, int grid, const StepArgs<float>* sa);
 // diagonal form of a CSR operand (d.k = 0 when it has none); flag: 2 ints of device scratch
 cudaError_t dia_build(cudaStream_t s, const DevCSR& a, DevDIA& d, int* flag_dev, int* flag_host);
 cudaError_t launch_cta_chain(const LaunchCtx& L, const ChainOps<double>& ops, const ChainVecs<double>& v, int t,
-                             double* part, int grid);
+                             double* part, int grid, const StepArgs<double>* sa);
 cudaError_t launch_cta_chain32(const LaunchCtx& L, const ChainOps<float>& ops, const ChainVecs<float>& v, int t,
-                               float scale, double* part, int grid);
+                               float scale, double* part, int grid, const StepArgs<float>* sa);
 
 // mixed precision (FP32 chain, FP64 refinement)
 cudaError_t launch_spmv32(const LaunchCtx& L, const DevCSR32& A, const float* x, float* y, float scale,

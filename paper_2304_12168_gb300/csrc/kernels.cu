@@ -30,6 +30,7 @@
 #include "mbarrier.cuh"
 #include "rowtiles.cuh"
 #include "finish.cuh"
+#include "aux_step.cuh"
 
 namespace tacta {
 
@@ -1355,42 +1356,6 @@ cudaError_t launch_copy_gated(const LaunchCtx& L, double* dst, const double* src
 // its own kernel so that the solve's registers (its arrays live in registers) do not
 // count against the occupancy of every product and update kernel, as they would if it
 // ran inside their shared finisher.
-// Enhanced stop (Sec. 3.2, Eq. widehatxB): the first-order iterates r_0 = r',
-// r_{i+1} = r_i - a_i H r_i with a_i = r_iᵀH r_i / r_iᵀH² r_i are polynomials in H
-// applied to r' (r_i = sum_k c_k H^k r'), so r_iᵀ H^s r_i = sum_{a,b} c_a c_b phi_{a+b+s}
-// comes from the step's moments. If r_jᵀ H r_j <= thr for the smallest j <= t-1, the
-// step's coefficients become those of x^ = x' + sum_{i<j} a_i Aᵀ r_i
-// = x' + sum_k beta_k z_{k+1} (and r^ = r' - sum_k beta_k u_{k+1} = r_j), so the update
-// kernel applies x^ unchanged. Returns true if it stops there.
-__device__ bool enhanced_stop(Ctl* c, int t) {
-    double cf[kTMax], beta[kTMax];
-    for (int k = 0; k < kTMax; ++k) { cf[k] = 0.0; beta[k] = 0.0; }
-    cf[0] = 1.0;
-    for (int i = 0; i + 1 < t; ++i) {              // from r_i (degree i) to r_{i+1}
-        double s1 = 0.0, s2 = 0.0;
-        for (int a = 0; a <= i; ++a)
-            for (int b = 0; b <= i; ++b) {
-                const double w = __dmul_rn(cf[a], cf[b]);
-                s1 = __fma_rn(w, c->phi[a + b + 1], s1);
-                s2 = __fma_rn(w, c->phi[a + b + 2], s2);
-            }
-        if (!(s2 > 0.0)) return false;
-        const double ai = __ddiv_rn(s1, s2);
-        for (int k = 0; k <= i; ++k) beta[k] = __fma_rn(ai, cf[k], beta[k]);
-        for (int k = i + 1; k >= 1; --k) cf[k] = __fma_rn(-ai, cf[k - 1], cf[k]);
-        double q = 0.0;                              // r_{i+1}ᵀ H r_{i+1}
-        for (int a = 0; a <= i + 1; ++a)
-            for (int b = 0; b <= i + 1; ++b) q = __fma_rn(__dmul_rn(cf[a], cf[b]), c->phi[a + b + 1], q);
-        if (q <= c->nrm_thr) {
-            for (int k = 0; k < t; ++k) c->alpha[k] = beta[k];
-            c->rank = i + 1;
-            c->enh_stop = 1;
-            return true;
-        }
-    }
-    return false;
-}
-
 // The step decision and auxiliary solve (one thread, FP64), in its own kernel so that
 // the solve's registers stay out of the streaming kernels. The control block is staged
 // in shared memory by all threads at once, so the one-thread solve works on shared-
@@ -1406,47 +1371,16 @@ __global__ void __launch_bounds__(384) cta_aux_step(Ctl* c, int t, const double*
     __syncthreads();
     if (part != nullptr && threadIdx.x == 0) c->chain_bar = 0;   // the fused chain's counter starts over
     if (sc.status != 0) return;
-    if (part != nullptr) {
-        // fused chain: a warp sums the per-block partials of phi_{w+1} (lane-strided with
-        // two accumulators, then a shuffle tree: a fixed order)
-        const int lane = threadIdx.x & 31;
-        for (int w = threadIdx.x >> 5; w < 2 * t; w += blockDim.x >> 5) {
-            const double* pw = part + (size_t)w * G;
-            double s0 = 0.0, s1 = 0.0;
-            int i = lane;
-#pragma unroll 4
-            for (; i + 32 < G; i += 64) {
-                s0 += pw[i];
-                s1 += pw[i + 32];
-            }
-            if (i < G) s0 += pw[i];
-            const double s = warp_sum(s0 + s1);
-            if (lane == 0) {
-                sc.phi[w + 1] = s;
-                c->phi[w + 1] = s;
-            }
-        }
-        __syncthreads();
-    }
+    if (part != nullptr) sum_moment_partials(&sc, t, part, G, c);   // fused chain: the moments' partials
     if (threadIdx.x != 0) return;
-    int status = 0;
-    for (int i = 1; i <= 2 * t; ++i)
-        if (!finite(sc.phi[i])) status = TACTA_REASON_NONFINITE;
-    if (status == 0 && sc.phi[1] <= __dmul_rn(sc.nrm_thr, sc.cs2)) status = TACTA_REASON_NORMAL;
-    if (status != 0) {
+    const int status = aux_decide(&sc, t);
+    if (status != 0 && !sc.enh_stop) {
         c->status = status;
         return;
     }
-    if (sc.enhanced && t >= 2 && enhanced_stop(&sc, t)) {
-        for (int k = 0; k < t; ++k) c->alpha[k] = sc.alpha[k];
-        c->rank = sc.rank;
-        c->enh_stop = 1;
-        return;
-    }
-    const int rank = hankel_solve_dev(sc.phi, t, sc.pivot_tol, sc.alpha);
     for (int k = 0; k < t; ++k) c->alpha[k] = sc.alpha[k];
-    c->rank = rank;
-    if (rank == 0) c->status = TACTA_REASON_BREAKDOWN;
+    c->rank = sc.rank;
+    if (sc.enh_stop) c->enh_stop = 1;
 }
 
 cudaError_t launch_cta_aux_step(const LaunchCtx& L, int t, const double* part, int G) {

@@ -114,9 +114,11 @@ struct Plan {
     // precision (0: not available) and the per-block moment partials
     int chain_grid = 0, chain_grid32 = 0;
     int dia_grid = 0, dia_grid32 = 0;   // the same on the diagonal form (0: A has none)
-    double* chain_part = nullptr;    // 2 kTMax x the largest of those grids
+    double* chain_part = nullptr;    // (2 kTMax + 2) x the largest of those grids
+    int chain_part_grid = 0;         // that grid
     bool fused = false;              // this call runs the fused chain
     bool dia = false;                // ... on the diagonal form
+    bool step = false;               // ... as the fused step (auxiliary solve and update in the launch)
     // opt-in profiling of the iteration's products (events around each launch)
     bool profiling = false;
     int prof_count = 0;
@@ -380,6 +382,11 @@ static tacta_status validate_opts(const tacta_options& o) {
     if (o.max_iter < 0) { set_error("max_iter must be >= 0"); return TACTA_ERR_INVALID; }
     if (o.recompute_every < 0) { set_error("recompute_every must be >= 0"); return TACTA_ERR_INVALID; }
     if (o.cycle < 0 || o.cycle > 2) { set_error("unknown cycle"); return TACTA_ERR_INVALID; }
+    if (o.fused_chain < 0 || o.fused_chain > 3) { set_error("fused_chain must be in 0..3"); return TACTA_ERR_INVALID; }
+    if (o.wait_limit_log2 < 0 || o.wait_limit_log2 > 40) {
+        set_error("wait_limit_log2 must be in 0..40");
+        return TACTA_ERR_INVALID;
+    }
     if (o.precision != TACTA_PRECISION_FP64 && o.precision != TACTA_PRECISION_MIXED) {
         set_error("unknown precision");
         return TACTA_ERR_INVALID;
@@ -463,7 +470,9 @@ static tacta_status plan_create(const tacta_matrix* M, const tacta_options* opt,
                 p->dia_grid32 = cta_chain_grid(p->sms, dt, true, true);
             }
             const int g = std::max(std::max(p->chain_grid, p->chain_grid32), std::max(p->dia_grid, p->dia_grid32));
-            if (g > 0) PTRY(cudaMalloc(&p->chain_part, sizeof(double) * 2 * kTMax * g));
+            // 2t products' partials, then the fused step's ||r||² partials (2 per block)
+            if (g > 0) PTRY(cudaMalloc(&p->chain_part, sizeof(double) * (2 * kTMax + 2) * g));
+            p->chain_part_grid = g;
         }
     } else {
         p->A.format = p->At.format = TACTA_DENSE;
@@ -661,29 +670,56 @@ static cudaError_t chain_spmv32(Plan* p, const LaunchCtx& L, const DevCSR32& A, 
     return cudaSuccess;
 }
 
+// algorithmic bytes of one CTA F_t step of order t on CSR operands, unfused: t products
+// with Aᵀ and t with A (values and column indices, row offsets), the chain's vectors read
+// and written once per product, and the update reading t z's, t u's and x, r and writing
+// x, r; vsize = 8 (FP64) or 4 (the FP32 chain: FP32 values and vectors)
+static double fpt_bytes(const Plan* p, int t, double vsize) {
+    const double m = (double)p->m, n = (double)p->n, nnz = (double)p->A.nnz();
+    const double ba = (vsize + 4.0) * nnz + 4.0 * (m + 1.0), bat = (vsize + 4.0) * nnz + 4.0 * (n + 1.0);
+    return t * (ba + bat) + vsize * t * (m + 2.0 * n + m) + vsize * (t + 2.0) * (n + m);
+}
+
 static cudaError_t enqueue_cta32_iter(Plan* p, const LaunchCtx& L, int t) {
     cudaError_t e;
     if (p->fused) {
         ChainVecs<float> v;
         v.r = p->r32;
         for (int i = 0; i < kTMax; ++i) { v.z[i] = p->z32[i]; v.u[i] = p->u32[i]; }
+        StepArgs<float> sa;
+        sa.x = p->dx32;
+        sa.r = p->r32;
+        sa.m = p->m;
+        sa.n = p->n;
+        sa.xscale = p->chain_scale;
+        sa.hist = p->hist;
+        sa.upart = p->chain_part + (size_t)2 * kTMax * p->chain_part_grid;
+        const StepArgs<float>* sp = p->step ? &sa : nullptr;
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
         if (p->dia) {
             e = launch_cta_chain_dia32(L, chain_ops_dia<float>(p->At.csr, p->A.csr, p->At.csr.dia.vals32,
                                                                p->A.csr.dia.vals32),
-                                       v, t, p->chain_scale, p->chain_part, p->dia_grid32);
+                                       v, t, p->chain_scale, p->chain_part, p->dia_grid32, sp);
         } else {
             e = launch_cta_chain32(L, chain_ops<float>(p->At.csr, p->A.csr, p->At32.vals, p->A32.vals), v, t,
-                                   p->chain_scale, p->chain_part, p->chain_grid32);
+                                   p->chain_scale, p->chain_part, p->chain_grid32, sp);
         }
         if (e != cudaSuccess) return e;
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
-        if (p->profiling) {
+        if (p->profiling && p->step) {
+            p->prof_bytes += fpt_bytes(p, t, 4.0);
+            p->prof_count += 1;
+        } else if (p->profiling) {
             for (const DevCSR* a : {&p->At.csr, &p->A.csr})
                 p->prof_bytes += t * (p->dia ? dia_bytes(*a, 4.0)
                                              : 8.0 * (double)a->nnz + 4.0 * (double)(a->rows + 1) +
                                                    4.0 * (double)a->cols + 4.0 * (double)a->rows);
             p->prof_count += 2 * t;
+        }
+        if (p->step) {
+            if ((e = launch_fold_correction(L, p->n, p->x, p->dx32, GATE_NEED_TRUE)) != cudaSuccess) return e;
+            return launch_spmv(L, p->A, p->x, p->tmp_m, EPI_RESID_F32, EpiArgs{p->b, nullptr, p->r32},
+                               FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE);
         }
         if ((e = launch_cta_aux_step(L, t, p->chain_part, p->dia ? p->dia_grid32 : p->chain_grid32)) !=
             cudaSuccess) return e;
@@ -746,17 +782,33 @@ static cudaError_t enqueue_cta_iter(Plan* p, const LaunchCtx& L, int t) {
         ChainVecs<double> v;
         v.r = p->r;
         for (int i = 0; i < kTMax; ++i) { v.z[i] = p->z[i]; v.u[i] = p->u[i]; }
+        StepArgs<double> sa;
+        sa.x = p->x;
+        sa.r = p->r;
+        sa.m = p->m;
+        sa.n = p->n;
+        sa.hist = p->hist;
+        sa.upart = p->chain_part + (size_t)2 * kTMax * p->chain_part_grid;
+        const StepArgs<double>* sp = p->step ? &sa : nullptr;
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
         if (p->dia) {
             e = launch_cta_chain_dia(L, chain_ops_dia<double>(p->At.csr, p->A.csr, p->At.csr.dia.vals,
                                                               p->A.csr.dia.vals),
-                                     v, t, p->chain_part, p->dia_grid);
+                                     v, t, p->chain_part, p->dia_grid, sp);
         } else {
             e = launch_cta_chain(L, chain_ops<double>(p->At.csr, p->A.csr, p->At.csr.vals, p->A.csr.vals), v, t,
-                                 p->chain_part, p->chain_grid);
+                                 p->chain_part, p->chain_grid, sp);
         }
         if (e != cudaSuccess) return e;
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
+        if (p->step) {
+            if (p->profiling) {
+                p->prof_bytes += fpt_bytes(p, t, 8.0);
+                p->prof_count += 1;
+            }
+            return launch_spmv(L, p->A, p->x, p->r, EPI_RESID, EpiArgs{p->b, nullptr, nullptr},
+                               FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE);
+        }
         if (p->profiling) {
             p->prof_bytes += t * (p->dia ? dia_bytes(p->At.csr, 8.0) + dia_bytes(p->A.csr, 8.0)
                                          : spmv_bytes(p->At) + spmv_bytes(p->A));
@@ -938,6 +990,7 @@ static Ctl base_ctl(const Opts& O, int64_t hist_cap) {
     h.rho_max = O.o.rho_max > 0.0 ? O.o.rho_max : INFINITY;
     h.tol_n2 = O.o.tol_normal * O.o.tol_normal;
     h.pivot_tol = O.o.pivot_tol;
+    h.wait_cycles = 1LL << (O.o.wait_limit_log2 > 0 ? O.o.wait_limit_log2 : 31);
     return h;
 }
 
@@ -1007,9 +1060,10 @@ static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t h
     }
     const int t_max = O.o.t_max, cycle = O.o.cycle;
     const int period = schedule_period(t_max, cycle);
-    p->dia = O.o.fused_chain == 1 && (mixed ? p->dia_grid32 : p->dia_grid) > 0;
+    p->dia = (O.o.fused_chain == 1 || O.o.fused_chain == 3) && (mixed ? p->dia_grid32 : p->dia_grid) > 0;
     p->fused = p->dia || (O.o.fused_chain != 0 && (mixed ? p->chain_grid32 : p->chain_grid) > 0);
-    const int key = (t_max * 4 + cycle) * 4 + (p->fused ? 1 : 0) + (p->dia ? 2 : 0);
+    p->step = p->fused && O.o.fused_chain != 3;
+    const int key = ((t_max * 4 + cycle) * 4 + (p->fused ? 1 : 0) + (p->dia ? 2 : 0)) * 2 + (p->step ? 1 : 0);
     cudaGraphExec_t* g = mixed ? &p->g_cta32 : &p->g_cta;
     int* gkey = mixed ? &p->g_cta32_key : &p->g_cta_key;
     if (*g && *gkey != key) {

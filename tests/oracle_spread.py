@@ -76,6 +76,25 @@ def stop_index_window(solve_name, p, x0, okw, n=SAMPLES):
     return lo, hi, its
 
 
+def _bisect_x(args):
+    p, rhs, normal, x_eps, okw, seed = args
+    import oracle
+    from oracle.ta import ta_minnorm_bisect
+    A = oracle.make_operator(p)
+    M = oracle.NormalOperator(A) if normal else A
+    b = rhs if seed is None else _perturbed(rhs, seed)
+    return ta_minnorm_bisect(M, b, x_eps, **okw).x
+
+
+def bisect_x_spread(p, rhs, normal, x_eps, okw, n=4):
+    """Largest relative distance between the oracle's Algorithm 2.5 answer on rhs and on n
+    perturbed right-hand sides (the rounding growth of its TA trips)."""
+    jobs = [(p, rhs, normal, x_eps, okw, None)] + [(p, rhs, normal, x_eps, okw, 3000 + i) for i in range(n)]
+    xs = _map(_bisect_x, jobs)
+    nx = np.linalg.norm(xs[0])
+    return max(np.linalg.norm(x - xs[0]) for x in xs[1:]) / (nx if nx > 0 else 1.0)
+
+
 def stable_trip_prefix(p, rhs, normal, x_eps, okw, n=8):
     """Number of leading trips of Algorithm 2.5 whose (stop reason, iterations) the oracle
     reproduces on every one of n perturbed right-hand sides, and the unperturbed log."""

@@ -49,6 +49,7 @@ def test_struct_layouts_match_header(lib):
     assert o.t_max == 5 and o.cycle == 0 and o.recompute_every == 40 and o.use_graph == 1
     assert o.poll_every == 64 and o.stream is None
     assert o.precision == 0 and o.nonneg == 0 and o.enhanced == 0 and o.fused_chain == 1
+    assert o.wait_limit_log2 == 0
     assert o.rho_max == 0.0 and o.profile == 0
     assert lib.tacta_version() == 10000
     assert lib.tacta_last_error() == b""
