@@ -11,23 +11,33 @@
 
 namespace tacta {
 
-// phi_{w+1} = sum over blocks of part[w * G + block], w = 0 .. 2t-1, into sc->phi (and
-// into c->phi when c is not null). A warp per moment: lanes stride over the G partials
-// with two accumulators, then a shuffle tree; the order depends on G only, so every block
-// (of any size) that runs it gets the same bits. Ends with __syncthreads().
-__device__ __forceinline__ void sum_moment_partials(Ctl* sc, int t, const double* part, int G, Ctl* c) {
+// Sum of G per-block partials by one warp: lanes stride over them with two accumulators,
+// then a shuffle tree; the order depends on G only, so every block (of any size) that
+// runs it gets the same bits. The result is valid in lane 0.
+__device__ __forceinline__ double warp_sum_partials(const double* pw, int G) {
     const int lane = threadIdx.x & 31;
-    for (int w = threadIdx.x >> 5; w < 2 * t; w += blockDim.x >> 5) {
-        const double* pw = part + (size_t)w * G;
-        double s0 = 0.0, s1 = 0.0;
-        int i = lane;
+    double s0 = 0.0, s1 = 0.0;
+    int i = lane;
 #pragma unroll 4
-        for (; i + 32 < G; i += 64) {
-            s0 += __ldcg(pw + i);
-            s1 += __ldcg(pw + i + 32);
-        }
-        if (i < G) s0 += __ldcg(pw + i);
-        const double s = warp_sum(s0 + s1);
+    for (; i + 32 < G; i += 64) {
+        s0 += __ldcg(pw + i);
+        s1 += __ldcg(pw + i + 32);
+    }
+    if (i < G) s0 += __ldcg(pw + i);
+    return warp_sum(s0 + s1);
+}
+
+// phi_{w+1} = sum over blocks of part[w * G + block], w = 0 .. 2t-1, into sc->phi (and
+// into c->phi when c is not null), a warp per moment. rot shifts which warp takes which
+// moment (an FP64 instruction holds its sub-partition's FP64 unit, so co-resident blocks
+// spread their moment sums over different sub-partitions); the bits do not depend on it.
+// Ends with __syncthreads().
+__device__ __forceinline__ void sum_moment_partials(Ctl* sc, int t, const double* part, int G, Ctl* c,
+                                                    int rot = 0) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int me = ((threadIdx.x >> 5) + nw - rot % nw) % nw;
+    for (int w = me; w < 2 * t; w += nw) {
+        const double s = warp_sum_partials(part + (size_t)w * G, G);
         if (lane == 0) {
             sc->phi[w + 1] = s;
             if (c) c->phi[w + 1] = s;

@@ -18,8 +18,8 @@
 //   * the fused step (STEP = true) also finishes the F_t step in the same launch: after
 //     the last product every block waits for all G blocks, sums the moments from the
 //     per-block partials in one fixed order (so every block holds the same bits), takes
-//     the step decision and solves the auxiliary equation (Eq. eqcoeff) redundantly on
-//     one thread, and then updates its slice of x and r (Eqs. CTAGEN7, CTAGEN7A); the
+//     the step decision and solves the auxiliary equation (Eq. eqcoeff) redundantly with
+//     one warp, and then updates its slice of x and r (Eqs. CTAGEN7, CTAGEN7A); the
 //     last block to finish (atomic ticket) adds the ||r||² partials and runs the stop
 //     tests. One launch per F_t step instead of three;
 //   * without STEP the moments are summed by the step's auxiliary kernel (fixed order,
@@ -82,8 +82,9 @@ __device__ __forceinline__ double step_update(const StepArgs<V>& sa, const Chain
         al[j] = (V)alpha[j];
         ax[j] = sizeof(V) == 8 ? (V)alpha[j] : (V)(alpha[j] * (double)sa.xscale);
     }
-    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // the eight consumer warps of every block (two per sub-partition: the update is FP64-bound)
+    const int64_t nth = (int64_t)gridDim.x * kTileRows;
+    const int64_t gt = (int64_t)blockIdx.x * kTileRows + threadIdx.x;
     // x (n entries)
     const int64_t nx = sa.n / W;
     for (int64_t c = gt; c < nx; c += nth) {
@@ -164,15 +165,17 @@ template <typename V, class F, bool STEP>
 __global__ void __launch_bounds__(kRwThreads, ChainShape<V>::MINB)
 cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t, float scale, Ctl* ctl, double* part) {
     constexpr int S = ChainShape<V>::S;
+    constexpr bool kFp64 = sizeof(V) == 8;
     using Stage = typename F::Stage;
     using Meta = typename F::Meta;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Stage* st = reinterpret_cast<Stage*>(smem_raw);
     __shared__ __align__(8) uint64_t full[S], empty[S];
-    __shared__ double red[2][kTileRows];
+    __shared__ double red[3][kTileRows];
     __shared__ volatile int failed;
     __shared__ int stopped;
-    __shared__ int last_block;   // fused step: this block arrived last after the last product
+    __shared__ int decision;     // fused step: the step decision (0: update)
+    __shared__ Ctl sc;           // fused step: a copy of the control block, staged at entry
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int G = gridDim.x, P = 2 * t;
     if (tid == 0) {
@@ -182,12 +185,19 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t, float sc
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         failed = 0;
-        last_block = 0;
         stopped = ctl->status != 0;
-        if (!stopped && blockIdx.x == 0) ctl->matvecs += P;
+        if (!STEP && !stopped && blockIdx.x == 0) ctl->matvecs += P;
+    }
+    if (STEP) {   // the step decision's inputs (thresholds, options, need_true) stay fixed during the step
+        const uint64_t* src = reinterpret_cast<const uint64_t*>(ctl);
+        uint64_t* dst = reinterpret_cast<uint64_t*>(&sc);
+        for (int i = tid; i < (int)(sizeof(Ctl) / 8); i += kRwThreads) dst[i] = __ldcg(src + i);
     }
     __syncthreads();
     if (stopped) return;   // every block reads the status left by the previous kernels
+    // FP64 fused step after a step that asked for the true residual: product p = -1 is
+    // r = b - A x (on A, from x), before the chain reads r
+    const int p0 = (STEP && kFp64 && sc.need_true) ? -1 : 0;
 
     if (warp == kRwConsumers) {
         // ---- producer: lane 0 issues, the lanes prefetch tile metadata
@@ -196,11 +206,12 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t, float sc
         Meta pend[S];
         int pend_k[S];
         int q = 0;   // position of the next tile in this block's sequence over all products
-        for (int p = 0; p < P && !__any_sync(0xffffffffu, failed != 0); ++p) {   // one decision per warp
-            const int o = p & 1;   // 0: Aᵀ (z_i = Aᵀ u_{i-1}), 1: A (u_i = A z_i)
-            const V* x = p == 0 ? vec.r : (o ? vec.z[p >> 1] : vec.u[(p >> 1) - 1]);
+        for (int p = p0; p < P && !__any_sync(0xffffffffu, failed != 0); ++p) {   // one decision per warp
+            const int o = p < 0 ? 1 : (p & 1);   // 0: Aᵀ (z_i = Aᵀ u_{i-1}), 1: A (u_i = A z_i; r = b - A x)
+            const V* x = p < 0 ? sa.x : (p == 0 ? vec.r : (o ? vec.z[p >> 1] : vec.u[(p >> 1) - 1]));
             const int nt = ops.ntiles[o];
-            bool gated = p > 0;    // x of product p exists once every block finished p - 1
+            bool gated = p > p0;    // x of product p exists once every block finished p - 1
+            const uint32_t target = (uint32_t)(p - p0) * (uint32_t)G;
             int np = 0;
             typename F::Prefetch pf;
             for (int j = 0;; ++j) {
@@ -223,7 +234,7 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t, float sc
                         }
                     }
                     if (gated && np == S) {   // every stage holds a tile waiting for its x runs
-                        if (!grid_wait(ctl, (uint32_t)p * (uint32_t)G) && !failed) {
+                        if (!grid_wait(ctl, target) && !failed) {
                             failed = 1;
                             atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
                         }
@@ -238,7 +249,7 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t, float sc
                 __syncwarp();
             }
             if (lane == 0 && np > 0) {   // fewer of this block's tiles than stages
-                if (!grid_wait(ctl, (uint32_t)p * (uint32_t)G) && !failed) {
+                if (!grid_wait(ctl, target) && !failed) {
                     failed = 1;
                     atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
                 }
@@ -254,11 +265,12 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t, float sc
     } else {
         // ---- eight consumer warps: warp w multiplies rows [32 w, 32 w + 32) of each tile
         int q = 0;
-        for (int p = 0; p < P; ++p) {
-            const int o = p & 1;
-            V* y = o ? vec.u[p >> 1] : vec.z[p >> 1];
+        for (int p = p0; p < P; ++p) {
+            const int o = p < 0 ? 1 : (p & 1);
+            V* y = p < 0 ? sa.r : (o ? vec.u[p >> 1] : vec.z[p >> 1]);
             const int nt = ops.ntiles[o];
             V acc = V(0);
+            double acc1 = 0.0;   // the true residual's rᵀb
             for (int j = 0; blockIdx.x + j * G < nt; ++j, ++q) {
                 const int k = q % S;
                 bool ok = !failed && mbar_wait_bounded(&full[k], (uint32_t)((q / S) & 1));
@@ -276,57 +288,88 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t, float sc
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[k]);   // this warp is done with stage k
                 if (active) {
-                    if (sizeof(V) == 4) sum *= (V)scale;   // FP32 chain scale: a power of two, exact
+                    if constexpr (kFp64) {
+                        if (p < 0) {   // r = b - A x, with ||r||² and rᵀb
+                            const double bv = __ldg(sa.b + row);
+                            sum = bv - sum;
+                            acc1 = fma(sum, bv, acc1);
+                        }
+                    } else {
+                        sum *= (V)scale;   // FP32 chain scale: a power of two, exact
+                    }
                     y[row] = sum;
                     acc = sq_acc(sum, acc);
                 }
             }
-            // product p is done in this block: its partial of phi_{p+1}, then (all but the
-            // last product) the block's arrival on the grid-wide counter, after every
-            // consumer's stores of y (named barrier of the 256 consumer threads)
-            double* sh = red[p & 1];
+            // product p is done in this block: its partials (phi_{p+1}; the true residual's
+            // ||r||² and rᵀb), then (all but the chain-only launch's last product) the block's
+            // arrival on the grid-wide counter, after every consumer's stores of y (named
+            // barrier of the 256 consumer threads)
+            double* sh = p < 0 ? red[2] : red[p & 1];
             sh[tid] = (double)acc;
+            if (p < 0) red[1][tid] = acc1;
             asm volatile("bar.sync 1, %0;" ::"n"(kTileRows) : "memory");
             if (warp == 0) {
                 double s = sh[lane];
 #pragma unroll
                 for (int i = 1; i < kRwConsumers; ++i) s += sh[lane + 32 * i];
                 s = chain_warp_sum(s);
+                double s1 = 0.0;
+                if (p < 0) {
+                    s1 = red[1][lane];
+#pragma unroll
+                    for (int i = 1; i < kRwConsumers; ++i) s1 += red[1][lane + 32 * i];
+                    s1 = chain_warp_sum(s1);
+                }
                 if (lane == 0) {
-                    part[(size_t)p * G + blockIdx.x] = s;
+                    if (p < 0) {
+                        sa.rpart[blockIdx.x] = s;
+                        sa.rpart[G + blockIdx.x] = s1;
+                    } else {
+                        part[(size_t)p * G + blockIdx.x] = s;
+                    }
                     if (STEP || p + 1 < P) {   // the fused step also counts the last product
                         asm volatile("fence.proxy.async.global;" ::: "memory");
                         __threadfence();
-                        const uint32_t old = atomicAdd(&ctl->chain_bar, 1u);
-                        if (STEP && p + 1 == P && old + 1u == (uint32_t)P * (uint32_t)G) {
-                            __threadfence();   // every block's partials of this step are visible
-                            last_block = 1;
-                        }
+                        atomicAdd(&ctl->chain_bar, 1u);
                     }
                 }
             }
         }
     }
     if constexpr (STEP) {
-        // ---- the rest of the F_t step, all nine warps. Every copy of this block has
-        // landed (consumers waited on every armed stage; a producer that gave up drained).
-        // The block that arrived last after the last product sums the moments and takes
-        // the step decision (a warp solves the auxiliary equation); the others wait for
-        // its flag and read alpha. Then every block updates its slice of x and r.
-        __shared__ Ctl sc;
-        __shared__ int decision;
+        // ---- the rest of the F_t step. Every copy of this block has landed (consumers
+        // waited on every armed stage; a producer that gave up drained). Every block sums
+        // the moments from all blocks' partials in one fixed order, so every block holds the
+        // same bits, and takes the step decision itself (a warp solves the auxiliary
+        // equation): no block waits on another's decision. Then the eight consumer warps
+        // update the block's slice of x and r.
+        // Co-resident blocks (G = blocks per SM x SMs, filled SM by SM) use different warps
+        // for the one-warp work, so their FP64 chains run on different sub-partitions.
+        const int rot = (int)(blockIdx.x / (unsigned)max(1, G / ChainShape<V>::MINB)) & 3;
+        __syncthreads();
+        if (tid == 0 && !failed && !grid_wait(ctl, (uint32_t)(P - p0) * (uint32_t)G)) {
+            failed = 1;
+            atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+        }
         __syncthreads();
         if (failed) return;
-        if (last_block) {
-            {
-                const uint64_t* src = reinterpret_cast<const uint64_t*>(ctl);
-                uint64_t* dst = reinterpret_cast<uint64_t*>(&sc);
-                for (int i = tid; i < (int)(sizeof(Ctl) / 8); i += kRwThreads) dst[i] = __ldcg(src + i);
+        if (p0 < 0 && warp < 2) {   // the true residual's ||r||² and rᵀb
+            const double s = warp_sum_partials(sa.rpart + (size_t)warp * G, G);
+            if (lane == 0) sc.red[warp] = s;
+        }
+        sum_moment_partials(&sc, t, part, G, blockIdx.x == 0 ? ctl : nullptr, 2 + rot);
+        if (warp == rot) {
+            int st2 = 0;
+            bool go_on = true;
+            if (p0 < 0) {   // the true residual first (as the finisher of a separate residual kernel)
+                if (lane == 0) finish(&sc, FinArgs{FIN_TRUE_RES, 0, blockIdx.x == 0 ? sa.hist : nullptr},
+                                      sc.red[0], sc.red[1]);
+                __syncwarp();
+                go_on = sc.status == 0;
+                st2 = sc.status;
             }
-            __syncthreads();
-            sum_moment_partials(&sc, t, part, G, ctl);   // phi_1..phi_2t, also into ctl->phi
-            if (warp == 0) {
-                int st2 = 0;
+            if (go_on) {
                 for (int i = 1; i <= 2 * t; ++i)
                     if (!finite(sc.phi[i])) st2 = TACTA_REASON_NONFINITE;
                 if (st2 == 0 && sc.phi[1] <= __dmul_rn(sc.nrm_thr, sc.cs2)) st2 = TACTA_REASON_NORMAL;
@@ -335,12 +378,24 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t, float sc
                     __syncwarp();
                 }
                 if (st2 == 0 && !sc.enh_stop) {
-                    sc.rank = hankel_solve_warp(sc.phi, t, sc.pivot_tol, sc.alpha);
-                    if (sc.rank == 0) st2 = TACTA_REASON_BREAKDOWN;
+                    const int rank = hankel_solve_warp(sc.phi, t, sc.pivot_tol, sc.alpha);
+                    if (rank == 0) st2 = TACTA_REASON_BREAKDOWN;
+                    if (lane == 0) sc.rank = rank;
                 }
-                __syncwarp();
-                if (lane == 0) {
-                    decision = st2;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                decision = st2;
+                if (blockIdx.x == 0) {
+                    ctl->matvecs += (p0 < 0 ? 1 : 0) + (go_on ? P : 0);
+                    if (p0 < 0) {   // what the true residual's finisher changed
+                        ctl->rn2 = sc.rn2;
+                        ctl->db = sc.db;
+                        ctl->is_true = sc.is_true;
+                        ctl->need_true = sc.need_true;
+                        ctl->ref_thr = sc.ref_thr;
+                        ctl->hist_len = sc.hist_len;
+                    }
                     if (st2 != 0) {
                         ctl->status = st2;
                     } else {
@@ -348,37 +403,12 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t, float sc
                         ctl->rank = sc.rank;
                         if (sc.enh_stop) ctl->enh_stop = 1;
                     }
-                    __threadfence();
-                    atomicExch(&ctl->step_flag, 1u);
                 }
             }
-            __syncthreads();
-        } else {
-            if (tid == 0) {
-                const long long t0 = clock64();
-                const long long limit = ctl->wait_cycles > 0 ? ctl->wait_cycles : (1LL << 31);
-                bool ok = true;
-                while (ld_acquire_gpu(&ctl->step_flag) == 0u) {
-                    if (*(volatile int32_t*)&ctl->status == TACTA_REASON_TIMEOUT || clock64() - t0 > limit) {
-                        ok = false;
-                        break;
-                    }
-                }
-                if (!ok) {
-                    failed = 1;
-                    atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
-                } else {
-                    decision = __ldcg(&ctl->status);
-                    sc.enh_stop = __ldcg(&ctl->enh_stop);
-                }
-            }
-            __syncthreads();
-            if (failed) return;
-            if (tid < t) sc.alpha[tid] = __ldcg(&ctl->alpha[tid]);
-            __syncthreads();
         }
-        if (decision != 0 && !sc.enh_stop) return;   // NORMAL, NONFINITE, BREAKDOWN or TIMEOUT: the solve ends
-        const double acc = step_update_t<V>(sa, vec, sc.alpha, t);
+        __syncthreads();
+        if (decision != 0) return;   // the solve ends with this step
+        const double acc = warp < kRwConsumers ? step_update_t<V>(sa, vec, sc.alpha, t) : 0.0;
         reduce_and_finish<1, kRwThreads, true>(acc, 0.0, ctl, sa.upart, FinArgs{FIN_CTA_UPDATE, 0, sa.hist, 1});
     }
 }

@@ -209,10 +209,7 @@ __device__ void reduce_and_finish(double a0, double a1, Ctl* ctl, double* partia
         if (NRED > 1) t1 = block_sum_warp0<NT>(t1, sh);
         if (threadIdx.x == 0) {
             sc.counter = 0;
-            if (f.reset_bar) {   // every block of a fused step is past its grid waits
-                sc.chain_bar = 0;
-                sc.step_flag = 0;
-            }
+            if (f.reset_bar) sc.chain_bar = 0;   // every block of a fused step is past its grid waits
             finish(&sc, f, t0, t1);
         }
         __syncthreads();
@@ -227,10 +224,7 @@ __device__ void reduce_and_finish(double a0, double a1, Ctl* ctl, double* partia
         if (NRED > 1) t1 = block_sum_warp0<NT>(t1, sh);
         if (threadIdx.x == 0) {
             ctl->counter = 0;
-            if (f.reset_bar) {
-                ctl->chain_bar = 0;
-                ctl->step_flag = 0;
-            }
+            if (f.reset_bar) ctl->chain_bar = 0;
             finish(ctl, f, t0, t1);
         }
     }

@@ -35,7 +35,6 @@ struct Ctl {
     int32_t enhanced;      // CTA: the enhanced stop of Sec. 3.2 is on
     int32_t enh_stop;      // CTA: this step applies x^ and ends the solve (reason ENHANCED)
     uint32_t chain_bar;    // fused CTA chain: grid-wide arrivals (reset by the step's auxiliary kernel)
-    uint32_t step_flag;    // fused step: the step decision and alpha are in this block (reset with chain_bar)
     double bn2;            // ||b||²  (b = rhs of the operator in use)
     double inv_bn2;        // 1 / ||b||² (0 when b = 0): the history stores ||r||² / ||b||²
     double mtbn2;          // ||Mᵀ b||²
@@ -261,6 +260,9 @@ struct StepArgs {
     float xscale = 1.0f;     // FP32 chain: z_i carries a scale, x += xscale sum alpha_i z_i
     double* hist = nullptr;  // history buffer of the finisher
     double* upart = nullptr; // per-block partials of ||r||² (2 doubles per block)
+    const double* b = nullptr; // FP64 chain: the right-hand side, for the true residual of
+                               // a step that starts with one (ctl->need_true)
+    double* rpart = nullptr;   // its per-block partials: ||r||² then rᵀb (G each)
 };
 // blocks of the cooperative chain launch (all resident), 0 if it cannot run here
 int cta_chain_grid(int sms, int max_tiles, bool fp32, bool dia);

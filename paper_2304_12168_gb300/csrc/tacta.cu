@@ -114,7 +114,7 @@ struct Plan {
     // precision (0: not available) and the per-block moment partials
     int chain_grid = 0, chain_grid32 = 0;
     int dia_grid = 0, dia_grid32 = 0;   // the same on the diagonal form (0: A has none)
-    double* chain_part = nullptr;    // (2 kTMax + 2) x the largest of those grids
+    double* chain_part = nullptr;    // (2 kTMax + 4) x the largest of those grids
     int chain_part_grid = 0;         // that grid
     bool fused = false;              // this call runs the fused chain
     bool dia = false;                // ... on the diagonal form
@@ -470,8 +470,9 @@ static tacta_status plan_create(const tacta_matrix* M, const tacta_options* opt,
                 p->dia_grid32 = cta_chain_grid(p->sms, dt, true, true);
             }
             const int g = std::max(std::max(p->chain_grid, p->chain_grid32), std::max(p->dia_grid, p->dia_grid32));
-            // 2t products' partials, then the fused step's ||r||² partials (2 per block)
-            if (g > 0) PTRY(cudaMalloc(&p->chain_part, sizeof(double) * (2 * kTMax + 2) * g));
+            // 2t products' partials, the fused step's true-residual partials (2 rows) and
+            // its ||r||² partials (2 per block)
+            if (g > 0) PTRY(cudaMalloc(&p->chain_part, sizeof(double) * (2 * kTMax + 4) * g));
             p->chain_part_grid = g;
         }
     } else {
@@ -693,7 +694,7 @@ static cudaError_t enqueue_cta32_iter(Plan* p, const LaunchCtx& L, int t) {
         sa.n = p->n;
         sa.xscale = p->chain_scale;
         sa.hist = p->hist;
-        sa.upart = p->chain_part + (size_t)2 * kTMax * p->chain_part_grid;
+        sa.upart = p->chain_part + (size_t)(2 * kTMax + 2) * p->chain_part_grid;
         const StepArgs<float>* sp = p->step ? &sa : nullptr;
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
         if (p->dia) {
@@ -788,7 +789,9 @@ static cudaError_t enqueue_cta_iter(Plan* p, const LaunchCtx& L, int t) {
         sa.m = p->m;
         sa.n = p->n;
         sa.hist = p->hist;
-        sa.upart = p->chain_part + (size_t)2 * kTMax * p->chain_part_grid;
+        sa.rpart = p->chain_part + (size_t)2 * kTMax * p->chain_part_grid;
+        sa.upart = p->chain_part + (size_t)(2 * kTMax + 2) * p->chain_part_grid;
+        sa.b = p->b;
         const StepArgs<double>* sp = p->step ? &sa : nullptr;
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
         if (p->dia) {
@@ -801,13 +804,12 @@ static cudaError_t enqueue_cta_iter(Plan* p, const LaunchCtx& L, int t) {
         }
         if (e != cudaSuccess) return e;
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
-        if (p->step) {
+        if (p->step) {   // the true residual, when a step needs one, runs at the start of the next
             if (p->profiling) {
                 p->prof_bytes += fpt_bytes(p, t, 8.0);
                 p->prof_count += 1;
             }
-            return launch_spmv(L, p->A, p->x, p->r, EPI_RESID, EpiArgs{p->b, nullptr, nullptr},
-                               FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE);
+            return cudaSuccess;
         }
         if (p->profiling) {
             p->prof_bytes += t * (p->dia ? dia_bytes(p->At.csr, 8.0) + dia_bytes(p->A.csr, 8.0)
@@ -1079,6 +1081,11 @@ static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t h
                   mixed ? &p->g_cta32_launches : &p->g_cta_launches,
                   mixed ? &p->g_cta32_iters : &p->g_cta_iters, body, launches);
     if (st != TACTA_OK) return st;
+    // the FP64 fused step runs a pending true residual at the start of the next step: after
+    // the last step it runs here (a no-op when none is pending or the solve has stopped)
+    if (!mixed && p->step)
+        CUDA_TRY(launch_spmv(L, p->A, p->x, p->r, EPI_RESID, EpiArgs{p->b, nullptr, nullptr},
+                             FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE));
     if (mixed) CUDA_TRY(launch_fold_correction(L, p->n, p->x, p->dx32, GATE_FORCE));
     CUDA_TRY(cudaGetLastError());
     return TACTA_OK;

@@ -152,15 +152,19 @@ def test_fused_step_equals_chain_with_separate_update(tacta, name):
     """The fused step (fused_chain = 1) and the chain with its auxiliary solve and update
     as separate launches (fused_chain = 3) sum the same partials in the same order and
     update every entry with the same FMAs: x is bit for bit the same; only ||r||² is
-    added in another order (the history agrees to 1e-14)."""
+    added in another order (the history agrees to 1e-14). With R = 7 the fused step
+    starts every eighth step with the true residual b - A x (its own product inside the
+    launch, instead of a separate gated launch), with the same per-row arithmetic."""
     p = CASES[name]()
     A, b = dev(p)
-    opts = dict(tol=1e-30, tol_normal=0.0, max_iter=40)
-    x1, h1, i1 = tacta.cta_solve(A, b, fused_chain=1, **opts)
-    x3, h3, i3 = tacta.cta_solve(A, b, fused_chain=3, **opts)
-    assert i1["iters"] == i3["iters"] == 40 and i1["launches"] < i3["launches"]
-    assert np.array_equal(x1.cpu().numpy(), x3.cpu().numpy())
-    np.testing.assert_allclose(h1.cpu().numpy(), h3.cpu().numpy(), rtol=1e-14)
+    for R in (40, 7):
+        opts = dict(tol=1e-30, tol_normal=0.0, max_iter=40, recompute_every=R)
+        x1, h1, i1 = tacta.cta_solve(A, b, fused_chain=1, **opts)
+        x3, h3, i3 = tacta.cta_solve(A, b, fused_chain=3, **opts)
+        assert i1["iters"] == i3["iters"] == 40 and i1["launches"] < i3["launches"]
+        assert i1["matvecs"] == i3["matvecs"]
+        assert np.array_equal(x1.cpu().numpy(), x3.cpu().numpy()), R
+        np.testing.assert_allclose(h1.cpu().numpy(), h3.cpu().numpy(), rtol=1e-14)
 
 
 def test_fused_step_timeout_is_reported_and_the_plan_recovers(tacta):
