@@ -161,9 +161,34 @@ __device__ __forceinline__ double chain_warp_sum(double v) {
 __device__ __forceinline__ double sq_acc(double s, double a) { return fma(s, s, a); }
 __device__ __forceinline__ float sq_acc(float s, float a) { return fmaf(s, s, a); }
 
+// t of F_t step k under the cycle (the host's schedule; Sec. 5.1: ping-pong 1..t_max..1)
+__device__ __forceinline__ int step_order(int64_t k, int t_max, int cycle) {
+    if (cycle == TACTA_CYCLE_FIXED || t_max == 1) return t_max;
+    if (cycle == TACTA_CYCLE_SAWTOOTH) return 1 + (int)(k % t_max);
+    const int period = 2 * t_max - 2;
+    const int j = (int)(k % period);
+    return j < t_max ? j + 1 : 2 * t_max - 1 - j;
+}
+
+// The fields a step's decisions change, from a block's copy of the control block to the
+// control block itself (block 0 only; the other blocks keep their copies in step).
+__device__ __forceinline__ void publish_step(Ctl* c, const Ctl& sc, int t) {
+    c->k = sc.k;
+    c->is_true = sc.is_true;
+    c->need_true = sc.need_true;
+    c->rn2 = sc.rn2;
+    c->db = sc.db;
+    c->ref_thr = sc.ref_thr;
+    c->hist_len = sc.hist_len;
+    c->rank = sc.rank;
+    c->enh_stop = sc.enh_stop;
+    for (int k = 0; k < t; ++k) c->alpha[k] = sc.alpha[k];
+    if (sc.status != 0) c->status = sc.status;
+}
+
 template <typename V, class F, bool STEP>
 __global__ void __launch_bounds__(kRwThreads, ChainShape<V>::MINB)
-cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t, float scale, Ctl* ctl, double* part) {
+cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t_arg, float scale, Ctl* ctl, double* part) {
     constexpr int S = ChainShape<V>::S;
     constexpr bool kFp64 = sizeof(V) == 8;
     using Stage = typename F::Stage;
@@ -175,9 +200,9 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t, float sc
     __shared__ volatile int failed;
     __shared__ int stopped;
     __shared__ int decision;     // fused step: the step decision (0: update)
-    __shared__ Ctl sc;           // fused step: a copy of the control block, staged at entry
+    __shared__ Ctl sc;           // fused step: this block's copy of the control block
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int G = gridDim.x, P = 2 * t;
+    const int G = gridDim.x;
     if (tid == 0) {
         for (int k = 0; k < S; ++k) {
             mbar_init(&full[k], 1);
@@ -186,230 +211,267 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t, float sc
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         failed = 0;
         stopped = ctl->status != 0;
-        if (!STEP && !stopped && blockIdx.x == 0) ctl->matvecs += P;
+        if (!STEP && !stopped && blockIdx.x == 0) ctl->matvecs += 2 * t_arg;
     }
-    if (STEP) {   // the step decision's inputs (thresholds, options, need_true) stay fixed during the step
+    if (STEP) {   // every block keeps a copy: the step decisions are taken in every block alike
         const uint64_t* src = reinterpret_cast<const uint64_t*>(ctl);
         uint64_t* dst = reinterpret_cast<uint64_t*>(&sc);
         for (int i = tid; i < (int)(sizeof(Ctl) / 8); i += kRwThreads) dst[i] = __ldcg(src + i);
     }
     __syncthreads();
     if (stopped) return;   // every block reads the status left by the previous kernels
-    // FP64 fused step after a step that asked for the true residual: product p = -1 is
-    // r = b - A x (on A, from x), before the chain reads r
-    const int p0 = (STEP && kFp64 && sc.need_true) ? -1 : 0;
-
-    if (warp == kRwConsumers) {
-        // ---- producer: lane 0 issues, the lanes prefetch tile metadata
-        int last_use[S];
-        for (int k = 0; k < S; ++k) last_use[k] = -1;
-        Meta pend[S];
-        int pend_k[S];
-        int q = 0;   // position of the next tile in this block's sequence over all products
-        for (int p = p0; p < P && !__any_sync(0xffffffffu, failed != 0); ++p) {   // one decision per warp
-            const int o = p < 0 ? 1 : (p & 1);   // 0: Aᵀ (z_i = Aᵀ u_{i-1}), 1: A (u_i = A z_i; r = b - A x)
-            const V* x = p < 0 ? sa.x : (p == 0 ? vec.r : (o ? vec.z[p >> 1] : vec.u[(p >> 1) - 1]));
-            const int nt = ops.ntiles[o];
-            bool gated = p > p0;    // x of product p exists once every block finished p - 1
-            const uint32_t target = (uint32_t)(p - p0) * (uint32_t)G;
-            int np = 0;
-            typename F::Prefetch pf;
-            for (int j = 0;; ++j) {
-                if (blockIdx.x + j * G >= nt || __any_sync(0xffffffffu, failed != 0)) break;
-                const Meta tm = pf.get(j, ops, o, G, lane);
-                if (lane == 0) {
-                    const int k = q % S, u = q / S;
-                    if (u > 0 && !mbar_wait_bounded(&empty[k], (uint32_t)((u - 1) & 1))) {
-                        failed = 1;
-                        atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
-                    } else {
-                        F::issue_mat(tm, st + k, &full[k], ops, o);
-                        last_use[k] = u;
-                        if (gated) {
-                            pend[np] = tm;
-                            pend_k[np] = k;
-                            ++np;
+    // Co-resident blocks (G = blocks per SM x SMs, filled SM by SM) use different warps for
+    // the one-warp work, so their FP64 chains run on different sub-partitions.
+    const int rot = (int)(blockIdx.x / (unsigned)max(1, G / ChainShape<V>::MINB)) & 3;
+    int q = 0;               // position of the next tile in this block's sequence of tiles
+    uint32_t base = 0;       // grid-wide arrivals before the current step
+    int last_use[S];         // producer: the last use of each stage
+    for (int k = 0; k < S; ++k) last_use[k] = -1;
+    const int nsteps = STEP ? sa.nsteps : 1;
+    for (int step = 0; step < nsteps; ++step) {
+        if (STEP && !kFp64 && sc.need_true) break;   // FP32 chain: the refinement runs first
+        const int t = STEP ? step_order(sc.k, sa.t_max, sa.cycle) : t_arg;
+        const int P = 2 * t;
+        // FP64 fused step after a step that asked for the true residual: product p = -1 is
+        // r = b - A x (on A, from x), before the chain reads r
+        const int p0 = (STEP && kFp64 && sc.need_true) ? -1 : 0;
+        if (warp == kRwConsumers) {
+            // ---- producer: lane 0 issues, the lanes prefetch tile metadata
+            Meta pend[S];
+            int pend_k[S];
+            for (int p = p0; p < P && !__any_sync(0xffffffffu, failed != 0); ++p) {   // one decision per warp
+                const int o = p < 0 ? 1 : (p & 1);   // 0: Aᵀ (z_i = Aᵀ u_{i-1}), 1: A (u_i = A z_i; r = b - A x)
+                const V* x = p < 0 ? sa.x : (p == 0 ? vec.r : (o ? vec.z[p >> 1] : vec.u[(p >> 1) - 1]));
+                const int nt = ops.ntiles[o];
+                // x of product p exists once every block finished p - 1 (and the previous
+                // step's update, for the first product of a later step)
+                bool gated = p > p0 || step > 0;
+                const uint32_t target = base + (uint32_t)(p - p0) * (uint32_t)G;
+                int np = 0;
+                typename F::Prefetch pf;
+                for (int j = 0;; ++j) {
+                    if (blockIdx.x + j * G >= nt || __any_sync(0xffffffffu, failed != 0)) break;
+                    const Meta tm = pf.get(j, ops, o, G, lane);
+                    if (lane == 0) {
+                        const int k = q % S, u = q / S;
+                        if (u > 0 && !mbar_wait_bounded(&empty[k], (uint32_t)((u - 1) & 1))) {
+                            failed = 1;
+                            atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
                         } else {
-                            F::issue_x(tm, st + k, &full[k], x);
+                            F::issue_mat(tm, st + k, &full[k], ops, o);
+                            last_use[k] = u;
+                            if (gated) {
+                                pend[np] = tm;
+                                pend_k[np] = k;
+                                ++np;
+                            } else {
+                                F::issue_x(tm, st + k, &full[k], x);
+                            }
+                        }
+                        if (gated && np == S) {   // every stage holds a tile waiting for its x runs
+                            if (!grid_wait(ctl, target) && !failed) {
+                                failed = 1;
+                                atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+                            }
+                            // issued even after a failure (in-bounds reads) so that every armed
+                            // stage completes and the block can drain its copies
+                            for (int i = 0; i < np; ++i) F::issue_x(pend[i], st + pend_k[i], &full[pend_k[i]], x);
+                            np = 0;
+                            gated = false;
                         }
                     }
-                    if (gated && np == S) {   // every stage holds a tile waiting for its x runs
-                        if (!grid_wait(ctl, target) && !failed) {
+                    ++q;
+                    __syncwarp();
+                }
+                if (lane == 0 && np > 0) {   // fewer of this block's tiles than stages
+                    if (!grid_wait(ctl, target) && !failed) {
+                        failed = 1;
+                        atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+                    }
+                    for (int i = 0; i < np; ++i) F::issue_x(pend[i], st + pend_k[i], &full[pend_k[i]], x);
+                }
+                __syncwarp();
+            }
+            if (failed && lane == 0) {
+                // a wait gave up: let every copy already issued land before the block exits
+                for (int k = 0; k < S; ++k)
+                    if (last_use[k] >= 0) mbar_wait_bounded(&full[k], (uint32_t)(last_use[k] & 1));
+            }
+        } else {
+            // ---- eight consumer warps: warp w multiplies rows [32 w, 32 w + 32) of each tile
+            for (int p = p0; p < P; ++p) {
+                const int o = p < 0 ? 1 : (p & 1);
+                V* y = p < 0 ? sa.r : (o ? vec.u[p >> 1] : vec.z[p >> 1]);
+                const int nt = ops.ntiles[o];
+                V acc = V(0);
+                double acc1 = 0.0;   // the true residual's rᵀb
+                for (int j = 0; blockIdx.x + j * G < nt; ++j, ++q) {
+                    const int k = q % S;
+                    bool ok = !failed && mbar_wait_bounded(&full[k], (uint32_t)((q / S) & 1));
+                    ok = __all_sync(0xffffffffu, ok);   // the warp takes one path
+                    if (!ok) {
+                        if (lane == 0 && !failed) {
                             failed = 1;
                             atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
                         }
-                        // issued even after a failure (in-bounds reads) so that every armed
-                        // stage completes and the block can drain its copies
-                        for (int i = 0; i < np; ++i) F::issue_x(pend[i], st + pend_k[i], &full[pend_k[i]], x);
-                        np = 0;
-                        gated = false;
+                        continue;
                     }
-                }
-                ++q;
-                __syncwarp();
-            }
-            if (lane == 0 && np > 0) {   // fewer of this block's tiles than stages
-                if (!grid_wait(ctl, target) && !failed) {
-                    failed = 1;
-                    atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
-                }
-                for (int i = 0; i < np; ++i) F::issue_x(pend[i], st + pend_k[i], &full[pend_k[i]], x);
-            }
-            __syncwarp();
-        }
-        if (failed && lane == 0) {
-            // a wait gave up: let every copy already issued land before the block exits
-            for (int k = 0; k < S; ++k)
-                if (last_use[k] >= 0) mbar_wait_bounded(&full[k], (uint32_t)(last_use[k] & 1));
-        }
-    } else {
-        // ---- eight consumer warps: warp w multiplies rows [32 w, 32 w + 32) of each tile
-        int q = 0;
-        for (int p = p0; p < P; ++p) {
-            const int o = p < 0 ? 1 : (p & 1);
-            V* y = p < 0 ? sa.r : (o ? vec.u[p >> 1] : vec.z[p >> 1]);
-            const int nt = ops.ntiles[o];
-            V acc = V(0);
-            double acc1 = 0.0;   // the true residual's rᵀb
-            for (int j = 0; blockIdx.x + j * G < nt; ++j, ++q) {
-                const int k = q % S;
-                bool ok = !failed && mbar_wait_bounded(&full[k], (uint32_t)((q / S) & 1));
-                ok = __all_sync(0xffffffffu, ok);   // the warp takes one path
-                if (!ok) {
-                    if (lane == 0 && !failed) {
-                        failed = 1;
-                        atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
-                    }
-                    continue;
-                }
-                int row;
-                bool active;
-                V sum = F::row_dot(st + k, ops, warp, lane, row, active);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[k]);   // this warp is done with stage k
-                if (active) {
-                    if constexpr (kFp64) {
-                        if (p < 0) {   // r = b - A x, with ||r||² and rᵀb
-                            const double bv = __ldg(sa.b + row);
-                            sum = bv - sum;
-                            acc1 = fma(sum, bv, acc1);
+                    int row;
+                    bool active;
+                    V sum = F::row_dot(st + k, ops, warp, lane, row, active);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[k]);   // this warp is done with stage k
+                    if (active) {
+                        if constexpr (kFp64) {
+                            if (p < 0) {   // r = b - A x, with ||r||² and rᵀb
+                                const double bv = __ldg(sa.b + row);
+                                sum = bv - sum;
+                                acc1 = fma(sum, bv, acc1);
+                            }
+                        } else {
+                            sum *= (V)scale;   // FP32 chain scale: a power of two, exact
                         }
-                    } else {
-                        sum *= (V)scale;   // FP32 chain scale: a power of two, exact
+                        y[row] = sum;
+                        acc = sq_acc(sum, acc);
                     }
-                    y[row] = sum;
-                    acc = sq_acc(sum, acc);
                 }
-            }
-            // product p is done in this block: its partials (phi_{p+1}; the true residual's
-            // ||r||² and rᵀb), then (all but the chain-only launch's last product) the block's
-            // arrival on the grid-wide counter, after every consumer's stores of y (named
-            // barrier of the 256 consumer threads)
-            double* sh = p < 0 ? red[2] : red[p & 1];
-            sh[tid] = (double)acc;
-            if (p < 0) red[1][tid] = acc1;
-            asm volatile("bar.sync 1, %0;" ::"n"(kTileRows) : "memory");
-            if (warp == 0) {
-                double s = sh[lane];
+                // product p is done in this block: its partials (phi_{p+1}; the true
+                // residual's ||r||² and rᵀb), then (all but the chain-only launch's last
+                // product) the block's arrival on the grid-wide counter, after every
+                // consumer's stores of y (named barrier of the 256 consumer threads)
+                double* sh = p < 0 ? red[2] : red[p & 1];
+                sh[tid] = (double)acc;
+                if (p < 0) red[1][tid] = acc1;
+                asm volatile("bar.sync 1, %0;" ::"n"(kTileRows) : "memory");
+                if (warp == 0) {
+                    double s = sh[lane];
 #pragma unroll
-                for (int i = 1; i < kRwConsumers; ++i) s += sh[lane + 32 * i];
-                s = chain_warp_sum(s);
-                double s1 = 0.0;
-                if (p < 0) {
-                    s1 = red[1][lane];
-#pragma unroll
-                    for (int i = 1; i < kRwConsumers; ++i) s1 += red[1][lane + 32 * i];
-                    s1 = chain_warp_sum(s1);
-                }
-                if (lane == 0) {
+                    for (int i = 1; i < kRwConsumers; ++i) s += sh[lane + 32 * i];
+                    s = chain_warp_sum(s);
+                    double s1 = 0.0;
                     if (p < 0) {
-                        sa.rpart[blockIdx.x] = s;
-                        sa.rpart[G + blockIdx.x] = s1;
-                    } else {
-                        part[(size_t)p * G + blockIdx.x] = s;
+                        s1 = red[1][lane];
+#pragma unroll
+                        for (int i = 1; i < kRwConsumers; ++i) s1 += red[1][lane + 32 * i];
+                        s1 = chain_warp_sum(s1);
                     }
-                    if (STEP || p + 1 < P) {   // the fused step also counts the last product
-                        asm volatile("fence.proxy.async.global;" ::: "memory");
-                        __threadfence();
-                        atomicAdd(&ctl->chain_bar, 1u);
+                    if (lane == 0) {
+                        if (p < 0) {
+                            sa.rpart[blockIdx.x] = s;
+                            sa.rpart[G + blockIdx.x] = s1;
+                        } else {
+                            part[(size_t)p * G + blockIdx.x] = s;
+                        }
+                        if (STEP || p + 1 < P) {   // the fused step also counts the last product
+                            asm volatile("fence.proxy.async.global;" ::: "memory");
+                            __threadfence();
+                            atomicAdd(&ctl->chain_bar, 1u);
+                        }
                     }
                 }
             }
+        }
+        if constexpr (!STEP) {
+            break;
+        } else {
+            // ---- the rest of the F_t step. Every copy of this block has landed (consumers
+            // waited on every armed stage; a producer that gave up drained). Every block
+            // sums the moments from all blocks' partials in one fixed order, so every block
+            // holds the same bits, and takes the step decision itself (a warp solves the
+            // auxiliary equation): no block waits on another's decision. Then the eight
+            // consumer warps update the block's slice of x and r, every block adds the
+            // ||r||² partials after a grid-wide wait and runs the stop tests, and the next
+            // step starts in the same launch.
+            base += (uint32_t)(P - p0) * (uint32_t)G;
+            __syncthreads();
+            if (tid == 0 && !failed && !grid_wait(ctl, base)) {
+                failed = 1;
+                atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+            }
+            __syncthreads();
+            if (failed) return;
+            if (p0 < 0 && warp < 2) {   // the true residual's ||r||² and rᵀb
+                const double s = warp_sum_partials(sa.rpart + (size_t)warp * G, G);
+                if (lane == 0) sc.red[warp] = s;
+            }
+            sum_moment_partials(&sc, t, part, G, blockIdx.x == 0 ? ctl : nullptr, 2 + rot);
+            if (warp == rot) {
+                int st2 = 0;
+                bool go_on = true;
+                if (p0 < 0) {   // the true residual first (as the finisher of a separate residual kernel)
+                    if (lane == 0) finish(&sc, FinArgs{FIN_TRUE_RES, 0, blockIdx.x == 0 ? sa.hist : nullptr},
+                                          sc.red[0], sc.red[1]);
+                    __syncwarp();
+                    go_on = sc.status == 0;
+                    st2 = sc.status;
+                }
+                if (go_on) {
+                    for (int i = 1; i <= 2 * t; ++i)
+                        if (!finite(sc.phi[i])) st2 = TACTA_REASON_NONFINITE;
+                    if (st2 == 0 && sc.phi[1] <= __dmul_rn(sc.nrm_thr, sc.cs2)) st2 = TACTA_REASON_NORMAL;
+                    if (st2 == 0 && sc.enhanced && t >= 2) {
+                        if (lane == 0) enhanced_stop(&sc, t);   // sets sc.enh_stop, sc.alpha
+                        __syncwarp();
+                    }
+                    if (st2 == 0 && !sc.enh_stop) {
+                        const int rank = hankel_solve_warp(sc.phi, t, sc.pivot_tol, sc.alpha);
+                        if (rank == 0) st2 = TACTA_REASON_BREAKDOWN;
+                        if (lane == 0) sc.rank = rank;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    decision = st2;
+                    sc.status = st2;
+                    if (blockIdx.x == 0) {
+                        ctl->matvecs += (p0 < 0 ? 1 : 0) + (go_on ? P : 0);
+                        publish_step(ctl, sc, t);
+                    }
+                }
+            }
+            __syncthreads();
+            if (decision != 0) break;   // the solve ends with this step
+            const double acc = warp < kRwConsumers ? step_update_t<V>(sa, vec, sc.alpha, t) : 0.0;
+            // ||r||²: block partial, grid-wide wait (every block's slice of r is also
+            // complete then, for the next step's first product), the same sum in every block
+            const double bs = block_sum_warp0<kRwThreads>(acc, &red[0][0]);
+            if (tid == 0) {
+                sa.upart[blockIdx.x] = bs;
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                __threadfence();
+                atomicAdd(&ctl->chain_bar, 1u);
+            }
+            base += (uint32_t)G;
+            if (tid == 0 && !grid_wait(ctl, base)) {
+                failed = 1;
+                atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+            }
+            __syncthreads();
+            if (failed) return;
+            if (warp == rot) {
+                const double rn2 = warp_sum_partials(sa.upart, G);
+                if (lane == 0) {
+                    finish(&sc, FinArgs{FIN_CTA_UPDATE, 0, blockIdx.x == 0 ? sa.hist : nullptr}, rn2, 0.0);
+                    if (blockIdx.x == 0) publish_step(ctl, sc, t);
+                }
+            }
+            __syncthreads();
+            // a stop, or (FP32 chain) a refinement due: the FP64 residual and the fold of
+            // the FP32 correction run as their own launches after this one
+            if (sc.status != 0 || (!kFp64 && sc.need_true)) break;
         }
     }
     if constexpr (STEP) {
-        // ---- the rest of the F_t step. Every copy of this block has landed (consumers
-        // waited on every armed stage; a producer that gave up drained). Every block sums
-        // the moments from all blocks' partials in one fixed order, so every block holds the
-        // same bits, and takes the step decision itself (a warp solves the auxiliary
-        // equation): no block waits on another's decision. Then the eight consumer warps
-        // update the block's slice of x and r.
-        // Co-resident blocks (G = blocks per SM x SMs, filled SM by SM) use different warps
-        // for the one-warp work, so their FP64 chains run on different sub-partitions.
-        const int rot = (int)(blockIdx.x / (unsigned)max(1, G / ChainShape<V>::MINB)) & 3;
+        // every block is past its last grid-wide wait once it takes its ticket: the last one
+        // resets the counters for the next launch
         __syncthreads();
-        if (tid == 0 && !failed && !grid_wait(ctl, (uint32_t)(P - p0) * (uint32_t)G)) {
-            failed = 1;
-            atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
-        }
-        __syncthreads();
-        if (failed) return;
-        if (p0 < 0 && warp < 2) {   // the true residual's ||r||² and rᵀb
-            const double s = warp_sum_partials(sa.rpart + (size_t)warp * G, G);
-            if (lane == 0) sc.red[warp] = s;
-        }
-        sum_moment_partials(&sc, t, part, G, blockIdx.x == 0 ? ctl : nullptr, 2 + rot);
-        if (warp == rot) {
-            int st2 = 0;
-            bool go_on = true;
-            if (p0 < 0) {   // the true residual first (as the finisher of a separate residual kernel)
-                if (lane == 0) finish(&sc, FinArgs{FIN_TRUE_RES, 0, blockIdx.x == 0 ? sa.hist : nullptr},
-                                      sc.red[0], sc.red[1]);
-                __syncwarp();
-                go_on = sc.status == 0;
-                st2 = sc.status;
-            }
-            if (go_on) {
-                for (int i = 1; i <= 2 * t; ++i)
-                    if (!finite(sc.phi[i])) st2 = TACTA_REASON_NONFINITE;
-                if (st2 == 0 && sc.phi[1] <= __dmul_rn(sc.nrm_thr, sc.cs2)) st2 = TACTA_REASON_NORMAL;
-                if (st2 == 0 && sc.enhanced && t >= 2) {
-                    if (lane == 0) enhanced_stop(&sc, t);   // sets sc.enh_stop, sc.alpha
-                    __syncwarp();
-                }
-                if (st2 == 0 && !sc.enh_stop) {
-                    const int rank = hankel_solve_warp(sc.phi, t, sc.pivot_tol, sc.alpha);
-                    if (rank == 0) st2 = TACTA_REASON_BREAKDOWN;
-                    if (lane == 0) sc.rank = rank;
-                }
-            }
-            __syncwarp();
-            if (lane == 0) {
-                decision = st2;
-                if (blockIdx.x == 0) {
-                    ctl->matvecs += (p0 < 0 ? 1 : 0) + (go_on ? P : 0);
-                    if (p0 < 0) {   // what the true residual's finisher changed
-                        ctl->rn2 = sc.rn2;
-                        ctl->db = sc.db;
-                        ctl->is_true = sc.is_true;
-                        ctl->need_true = sc.need_true;
-                        ctl->ref_thr = sc.ref_thr;
-                        ctl->hist_len = sc.hist_len;
-                    }
-                    if (st2 != 0) {
-                        ctl->status = st2;
-                    } else {
-                        for (int k = 0; k < t; ++k) ctl->alpha[k] = sc.alpha[k];
-                        ctl->rank = sc.rank;
-                        if (sc.enh_stop) ctl->enh_stop = 1;
-                    }
-                }
+        if (tid == 0) {
+            __threadfence();
+            if (atomicAdd(&ctl->counter, 1u) == (uint32_t)G - 1u) {
+                ctl->counter = 0;
+                ctl->chain_bar = 0;
             }
         }
-        __syncthreads();
-        if (decision != 0) return;   // the solve ends with this step
-        const double acc = warp < kRwConsumers ? step_update_t<V>(sa, vec, sc.alpha, t) : 0.0;
-        reduce_and_finish<1, kRwThreads, true>(acc, 0.0, ctl, sa.upart, FinArgs{FIN_CTA_UPDATE, 0, sa.hist, 1});
     }
 }
 

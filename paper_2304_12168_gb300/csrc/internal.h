@@ -263,6 +263,9 @@ struct StepArgs {
     const double* b = nullptr; // FP64 chain: the right-hand side, for the true residual of
                                // a step that starts with one (ctl->need_true)
     double* rpart = nullptr;   // its per-block partials: ||r||² then rᵀb (G each)
+    int nsteps = 1;            // F_t steps per launch (the launch stops early at a stop, and
+                               // on the FP32 chain when a refinement is due)
+    int t_max = 5, cycle = 0;  // the order of step k follows the cycle from the device's k
 };
 // blocks of the cooperative chain launch (all resident), 0 if it cannot run here
 int cta_chain_grid(int sms, int max_tiles, bool fp32, bool dia);

@@ -687,40 +687,23 @@ static cudaError_t enqueue_cta32_iter(Plan* p, const LaunchCtx& L, int t) {
         ChainVecs<float> v;
         v.r = p->r32;
         for (int i = 0; i < kTMax; ++i) { v.z[i] = p->z32[i]; v.u[i] = p->u32[i]; }
-        StepArgs<float> sa;
-        sa.x = p->dx32;
-        sa.r = p->r32;
-        sa.m = p->m;
-        sa.n = p->n;
-        sa.xscale = p->chain_scale;
-        sa.hist = p->hist;
-        sa.upart = p->chain_part + (size_t)(2 * kTMax + 2) * p->chain_part_grid;
-        const StepArgs<float>* sp = p->step ? &sa : nullptr;
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
         if (p->dia) {
             e = launch_cta_chain_dia32(L, chain_ops_dia<float>(p->At.csr, p->A.csr, p->At.csr.dia.vals32,
                                                                p->A.csr.dia.vals32),
-                                       v, t, p->chain_scale, p->chain_part, p->dia_grid32, sp);
+                                       v, t, p->chain_scale, p->chain_part, p->dia_grid32, nullptr);
         } else {
             e = launch_cta_chain32(L, chain_ops<float>(p->At.csr, p->A.csr, p->At32.vals, p->A32.vals), v, t,
-                                   p->chain_scale, p->chain_part, p->chain_grid32, sp);
+                                   p->chain_scale, p->chain_part, p->chain_grid32, nullptr);
         }
         if (e != cudaSuccess) return e;
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
-        if (p->profiling && p->step) {
-            p->prof_bytes += fpt_bytes(p, t, 4.0);
-            p->prof_count += 1;
-        } else if (p->profiling) {
+        if (p->profiling) {
             for (const DevCSR* a : {&p->At.csr, &p->A.csr})
                 p->prof_bytes += t * (p->dia ? dia_bytes(*a, 4.0)
                                              : 8.0 * (double)a->nnz + 4.0 * (double)(a->rows + 1) +
                                                    4.0 * (double)a->cols + 4.0 * (double)a->rows);
             p->prof_count += 2 * t;
-        }
-        if (p->step) {
-            if ((e = launch_fold_correction(L, p->n, p->x, p->dx32, GATE_NEED_TRUE)) != cudaSuccess) return e;
-            return launch_spmv(L, p->A, p->x, p->tmp_m, EPI_RESID_F32, EpiArgs{p->b, nullptr, p->r32},
-                               FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE);
         }
         if ((e = launch_cta_aux_step(L, t, p->chain_part, p->dia ? p->dia_grid32 : p->chain_grid32)) !=
             cudaSuccess) return e;
@@ -783,34 +766,17 @@ static cudaError_t enqueue_cta_iter(Plan* p, const LaunchCtx& L, int t) {
         ChainVecs<double> v;
         v.r = p->r;
         for (int i = 0; i < kTMax; ++i) { v.z[i] = p->z[i]; v.u[i] = p->u[i]; }
-        StepArgs<double> sa;
-        sa.x = p->x;
-        sa.r = p->r;
-        sa.m = p->m;
-        sa.n = p->n;
-        sa.hist = p->hist;
-        sa.rpart = p->chain_part + (size_t)2 * kTMax * p->chain_part_grid;
-        sa.upart = p->chain_part + (size_t)(2 * kTMax + 2) * p->chain_part_grid;
-        sa.b = p->b;
-        const StepArgs<double>* sp = p->step ? &sa : nullptr;
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
         if (p->dia) {
             e = launch_cta_chain_dia(L, chain_ops_dia<double>(p->At.csr, p->A.csr, p->At.csr.dia.vals,
                                                               p->A.csr.dia.vals),
-                                     v, t, p->chain_part, p->dia_grid, sp);
+                                     v, t, p->chain_part, p->dia_grid, nullptr);
         } else {
             e = launch_cta_chain(L, chain_ops<double>(p->At.csr, p->A.csr, p->At.csr.vals, p->A.csr.vals), v, t,
-                                 p->chain_part, p->chain_grid, sp);
+                                 p->chain_part, p->chain_grid, nullptr);
         }
         if (e != cudaSuccess) return e;
         if ((e = prof_mark(p, L)) != cudaSuccess) return e;
-        if (p->step) {   // the true residual, when a step needs one, runs at the start of the next
-            if (p->profiling) {
-                p->prof_bytes += fpt_bytes(p, t, 8.0);
-                p->prof_count += 1;
-            }
-            return cudaSuccess;
-        }
         if (p->profiling) {
             p->prof_bytes += t * (p->dia ? dia_bytes(p->At.csr, 8.0) + dia_bytes(p->A.csr, 8.0)
                                          : spmv_bytes(p->At) + spmv_bytes(p->A));
@@ -836,6 +802,68 @@ static cudaError_t enqueue_cta_iter(Plan* p, const LaunchCtx& L, int t) {
     if ((e = launch_cta_update(L, t, p->m, p->n, p->x, p->r, p->z, p->u,
                                FinArgs{FIN_CTA_UPDATE, 0, p->hist})) != cudaSuccess) return e;
     return launch_spmv(L, p->A, p->x, p->r, EPI_RESID, EpiArgs{p->b, nullptr, nullptr},
+                       FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE);
+}
+
+// Up to nsteps F_t steps in one persistent launch of the fused step (the order of each
+// step follows the cycle from the device's step count). FP64: a true residual a step asks
+// for runs as the first product of the next step. FP32 chain: the launch ends early when a
+// refinement is due, which the two gated launches after it carry out (fold the FP32
+// correction into the FP64 x, FP64 residual b - A x).
+static cudaError_t enqueue_cta_steps(Plan* p, const LaunchCtx& L, int nsteps, int t_max, int cycle, bool mixed) {
+    cudaError_t e;
+    if ((e = prof_mark(p, L)) != cudaSuccess) return e;
+    if (!mixed) {
+        ChainVecs<double> v;
+        v.r = p->r;
+        for (int i = 0; i < kTMax; ++i) { v.z[i] = p->z[i]; v.u[i] = p->u[i]; }
+        StepArgs<double> sa;
+        sa.x = p->x;
+        sa.r = p->r;
+        sa.m = p->m;
+        sa.n = p->n;
+        sa.hist = p->hist;
+        sa.rpart = p->chain_part + (size_t)2 * kTMax * p->chain_part_grid;
+        sa.upart = p->chain_part + (size_t)(2 * kTMax + 2) * p->chain_part_grid;
+        sa.b = p->b;
+        sa.nsteps = nsteps;
+        sa.t_max = t_max;
+        sa.cycle = cycle;
+        if (p->dia)
+            e = launch_cta_chain_dia(L, chain_ops_dia<double>(p->At.csr, p->A.csr, p->At.csr.dia.vals,
+                                                              p->A.csr.dia.vals),
+                                     v, 0, p->chain_part, p->dia_grid, &sa);
+        else
+            e = launch_cta_chain(L, chain_ops<double>(p->At.csr, p->A.csr, p->At.csr.vals, p->A.csr.vals), v, 0,
+                                 p->chain_part, p->chain_grid, &sa);
+        if (e != cudaSuccess) return e;
+        return prof_mark(p, L);
+    }
+    ChainVecs<float> v;
+    v.r = p->r32;
+    for (int i = 0; i < kTMax; ++i) { v.z[i] = p->z32[i]; v.u[i] = p->u32[i]; }
+    StepArgs<float> sa;
+    sa.x = p->dx32;
+    sa.r = p->r32;
+    sa.m = p->m;
+    sa.n = p->n;
+    sa.xscale = p->chain_scale;
+    sa.hist = p->hist;
+    sa.upart = p->chain_part + (size_t)(2 * kTMax + 2) * p->chain_part_grid;
+    sa.nsteps = nsteps;
+    sa.t_max = t_max;
+    sa.cycle = cycle;
+    if (p->dia)
+        e = launch_cta_chain_dia32(L, chain_ops_dia<float>(p->At.csr, p->A.csr, p->At.csr.dia.vals32,
+                                                           p->A.csr.dia.vals32),
+                                   v, 0, p->chain_scale, p->chain_part, p->dia_grid32, &sa);
+    else
+        e = launch_cta_chain32(L, chain_ops<float>(p->At.csr, p->A.csr, p->At32.vals, p->A32.vals), v, 0,
+                               p->chain_scale, p->chain_part, p->chain_grid32, &sa);
+    if (e != cudaSuccess) return e;
+    if ((e = prof_mark(p, L)) != cudaSuccess) return e;
+    if ((e = launch_fold_correction(L, p->n, p->x, p->dx32, GATE_NEED_TRUE)) != cudaSuccess) return e;
+    return launch_spmv(L, p->A, p->x, p->tmp_m, EPI_RESID_F32, EpiArgs{p->b, nullptr, p->r32},
                        FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE);
 }
 
@@ -1065,7 +1093,9 @@ static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t h
     p->dia = (O.o.fused_chain == 1 || O.o.fused_chain == 3) && (mixed ? p->dia_grid32 : p->dia_grid) > 0;
     p->fused = p->dia || (O.o.fused_chain != 0 && (mixed ? p->chain_grid32 : p->chain_grid) > 0);
     p->step = p->fused && O.o.fused_chain != 3;
-    const int key = ((t_max * 4 + cycle) * 4 + (p->fused ? 1 : 0) + (p->dia ? 2 : 0)) * 2 + (p->step ? 1 : 0);
+    const int nsteps = std::max(1, O.o.poll_every);   // F_t steps per launch of the fused step
+    const int key = (((t_max * 4 + cycle) * 4 + (p->fused ? 1 : 0) + (p->dia ? 2 : 0)) * 2 + (p->step ? 1 : 0)) *
+                        4096 + std::min(nsteps, 4095);
     cudaGraphExec_t* g = mixed ? &p->g_cta32 : &p->g_cta;
     int* gkey = mixed ? &p->g_cta32_key : &p->g_cta_key;
     if (*g && *gkey != key) {
@@ -1073,13 +1103,25 @@ static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t h
         *g = nullptr;
     }
     *gkey = key;
-    auto body = [&](const LaunchCtx& LL, int64_t k) {
-        const int t = schedule(k, t_max, cycle);
-        return mixed ? enqueue_cta32_iter(p, LL, t) : enqueue_cta_iter(p, LL, t);
-    };
-    st = run_loop(p, O, O.o.max_iter, period, O.o.use_graph != 0, g,
-                  mixed ? &p->g_cta32_launches : &p->g_cta_launches,
-                  mixed ? &p->g_cta32_iters : &p->g_cta_iters, body, launches);
+    if (p->step) {
+        // one body = one launch of up to nsteps steps; the device stops at max_iter. FP64
+        // launches run their nsteps unless the solve stops; an FP32-chain launch may end
+        // early for a refinement, so up to one launch per step may be needed
+        Opts O1 = O;
+        O1.o.poll_every = 1;
+        const int64_t calls = mixed ? (int64_t)O.o.max_iter + 1 : ((int64_t)O.o.max_iter + nsteps - 1) / nsteps;
+        auto body = [&](const LaunchCtx& LL, int64_t) { return enqueue_cta_steps(p, LL, nsteps, t_max, cycle, mixed); };
+        st = run_loop(p, O1, calls, 1, O.o.use_graph != 0, g, mixed ? &p->g_cta32_launches : &p->g_cta_launches,
+                      mixed ? &p->g_cta32_iters : &p->g_cta_iters, body, launches);
+    } else {
+        auto body = [&](const LaunchCtx& LL, int64_t k) {
+            const int t = schedule(k, t_max, cycle);
+            return mixed ? enqueue_cta32_iter(p, LL, t) : enqueue_cta_iter(p, LL, t);
+        };
+        st = run_loop(p, O, O.o.max_iter, period, O.o.use_graph != 0, g,
+                      mixed ? &p->g_cta32_launches : &p->g_cta_launches,
+                      mixed ? &p->g_cta32_iters : &p->g_cta_iters, body, launches);
+    }
     if (st != TACTA_OK) return st;
     // the FP64 fused step runs a pending true residual at the start of the next step: after
     // the last step it runs here (a no-op when none is pending or the solve has stopped)
@@ -1117,6 +1159,13 @@ static tacta_status plan_cta(Plan* p, const VecIO& io, const tacta_options* opt,
     prof_begin(p, O.o.profile);
     if ((st = cta_core(p, O, io.x0, hist_cap, &launches)) != TACTA_OK) { p->profiling = false; return st; }
     if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
+    if (p->profiling && p->step) {   // the timed unit is an F_t step: the launches ran stage->k of them
+        const bool mixed = O.o.precision == TACTA_PRECISION_MIXED;
+        p->prof_count = p->stage->k;
+        p->prof_bytes = 0.0;
+        for (int k = 0; k < p->stage->k; ++k)
+            p->prof_bytes += fpt_bytes(p, schedule(k, O.o.t_max, O.o.cycle), mixed ? 4.0 : 8.0);
+    }
     if (p->stage->status == TACTA_REASON_ZERO_RHS) CUDA_TRY(cudaMemsetAsync(p->x, 0, sizeof(double) * p->n, O.s));
     if ((st = exit_residuals(p, O, p->x, &launches)) != TACTA_OK) return st;
     if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
