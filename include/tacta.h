@@ -350,6 +350,24 @@ void tacta_batch_destroy(tacta_batch batch);
 /* message of the last failed tacta_batch_* call on the calling thread */
 const char* tacta_batch_last_error(void);
 
+/* tacta_column_partition -- the column shards of a CTA solve spread over G GPUs (one
+   process per GPU). With A = [A_1 ... A_G] split by columns, H = A Aᵀ = sum_g A_g A_gᵀ
+   (Sec. 3 with H = A Aᵀ, Sec. 5), so every GPU keeps its slice x_g of x and the replicated
+   m-vectors r and u_i: z_{i,g} = A_gᵀ u_{i-1} is local, and u_i = sum_g A_g z_{i,g} needs
+   one sum over the GPUs per H-apply. That all-reduce carries m + 2 doubles per GPU:
+   [0, m) the GPU's A_g z_{i,g}, [m] its ||z_{i,g}||² (the partial of phi_{2i-1}),
+   [m + 1] zero (keeps the buffer a multiple of 16 bytes); phi_{2i} = ||u_i||² is then
+   computed on every GPU from the replicated u_i, and the true residual b - sum_g A_g x_g
+   takes one more all-reduce of the same layout (with ||x_g||²). This call only computes
+   the split: the n columns of a CSR matrix (host arrays) into nparts contiguous ranges
+   holding nearly equal numbers of stored entries, each range at least one column.
+   col_begin: nparts + 1 values (col_begin[0] = 0, col_begin[nparts] = n); shard_nnz:
+   nparts values. TACTA_ERR_INVALID on sizes outside m, n >= 1, 1 <= nparts <= n, on
+   rowptr[0] != 0 or rowptr[m] != nnz, or a column index outside [0, n). Touches no GPU. */
+tacta_status tacta_column_partition(int64_t m, int64_t n, int64_t nnz, const int32_t* rowptr,
+                                    const int32_t* colidx, int32_t nparts, int64_t* col_begin,
+                                    int64_t* shard_nnz);
+
 /* tacta_aux_solve -- CTA's auxiliary equation of order t (Eq. eqcoeff),
      [phi_{i+j}]_{i,j=1..t} alpha = [phi_i]_{i=1..t},
    solved on the host by the code the kernels run on the device: Jacobi scaling by

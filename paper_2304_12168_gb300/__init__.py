@@ -70,7 +70,7 @@ EXPORTS = ["tacta_default_options", "cta_solve", "ta_solve", "ta_minnorm", "tact
            "tacta_residual_static", "tacta_last_error", "tacta_version",
            "tacta_batch_create", "tacta_batch_cta", "tacta_batch_destroy", "tacta_batch_tune",
            "tacta_batch_set_config", "tacta_batch_num_configs", "tacta_batch_config_shape",
-           "tacta_batch_last_error", "tacta_aux_solve", "tacta_dia_tile_plan"]
+           "tacta_batch_last_error", "tacta_aux_solve", "tacta_dia_tile_plan", "tacta_column_partition"]
 
 _lib_handle = None
 
@@ -132,6 +132,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tacta_batch_config_shape.restype = ctypes.c_int32
     lib.tacta_batch_last_error.argtypes = []
     lib.tacta_batch_last_error.restype = ctypes.c_char_p
+    lib.tacta_column_partition.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, dp, dp,
+                                           ctypes.c_int32, dp, dp]
+    lib.tacta_column_partition.restype = ctypes.c_int32
     lib.tacta_aux_solve.argtypes = [dp, ctypes.c_int32, ctypes.c_double, dp]
     lib.tacta_aux_solve.restype = ctypes.c_int32
     lib.tacta_dia_tile_plan.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, i32p, ctypes.c_int32,
@@ -406,6 +409,17 @@ class Plan:
 
 
 BATCH_FP64, BATCH_FP32, BATCH_BF16 = 0, 1, 2
+
+
+def column_partition(rowptr, colidx, m, n, nparts):
+    """tacta_column_partition: (col_begin (nparts + 1), shard_nnz (nparts)) for host CSR arrays."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(colidx, dtype=np.int32)
+    cb = np.zeros(nparts + 1, dtype=np.int64)
+    sn = np.zeros(nparts, dtype=np.int64)
+    _check(load_library().tacta_column_partition(int(m), int(n), int(ci.size), rp.ctypes.data, ci.ctypes.data,
+                                                 int(nparts), cb.ctypes.data, sn.ctypes.data))
+    return cb, sn
 
 
 def aux_solve(phi, t, pivot_tol=1e-12):

@@ -1690,6 +1690,45 @@ extern "C" int32_t tacta_dia_tile_plan(int64_t rows, int64_t cols, int32_t k, co
     return 1;
 }
 
+extern "C" tacta_status tacta_column_partition(int64_t m, int64_t n, int64_t nnz, const int32_t* rowptr,
+                                               const int32_t* colidx, int32_t nparts, int64_t* col_begin,
+                                               int64_t* shard_nnz) {
+    using namespace tacta;
+    set_error("");
+    if (!rowptr || (nnz > 0 && !colidx) || !col_begin || !shard_nnz) {
+        set_error("NULL argument");
+        return TACTA_ERR_INVALID;
+    }
+    if (m < 1 || n < 1 || nnz < 0 || nparts < 1 || nparts > n || rowptr[0] != 0 || rowptr[m] != nnz) {
+        set_error("tacta_column_partition: need m, n >= 1, 1 <= nparts <= n, rowptr[0] = 0, rowptr[m] = nnz");
+        return TACTA_ERR_INVALID;
+    }
+    // stored entries per column, then the prefix count of entries in columns < j
+    std::vector<int64_t> before((size_t)n + 1, 0);
+    for (int64_t k = 0; k < nnz; ++k) {
+        const int32_t c = colidx[k];
+        if (c < 0 || c >= n) {
+            set_error("tacta_column_partition: column index out of range");
+            return TACTA_ERR_INVALID;
+        }
+        ++before[(size_t)c + 1];
+    }
+    for (int64_t j = 0; j < n; ++j) before[(size_t)j + 1] += before[(size_t)j];
+    // shard g starts at the first column whose preceding entries reach g * nnz / nparts, and
+    // every shard keeps at least one column
+    col_begin[0] = 0;
+    for (int32_t g = 1; g < nparts; ++g) {
+        const int64_t want = (int64_t)((double)nnz * g / nparts);
+        int64_t j = std::lower_bound(before.begin(), before.end(), want) - before.begin();
+        j = std::max<int64_t>(j, col_begin[g - 1] + 1);
+        j = std::min<int64_t>(j, n - (nparts - g));
+        col_begin[g] = j;
+    }
+    col_begin[nparts] = n;
+    for (int32_t g = 0; g < nparts; ++g) shard_nnz[g] = before[(size_t)col_begin[g + 1]] - before[(size_t)col_begin[g]];
+    return TACTA_OK;
+}
+
 extern "C" int32_t tacta_aux_solve(const double* phi, int32_t t, double pivot_tol, double* alpha) {
     if (!phi || !alpha || t < 1 || t > kTMax) return -1;
     return hankel_solve_dev(phi, t, pivot_tol, alpha);
