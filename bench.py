@@ -71,28 +71,30 @@ FP64_TFLOPS_NOMINAL = 1.25
 
 
 def kernel_source_hash():
-    """sha256 of the dominant kernel's source: the fused chain (chain.cu), the row-tile
-    stages and copy issue it uses (rowtiles.cuh), the mbarrier helpers and the layout
+    """sha256 of the dominant kernel's source: the fused step (chain.cu), the row-tile
+    stages and copy issue it uses (rowtiles.cuh), the mbarrier helpers, the step decision,
+    finishers and solve it calls (aux_step.cuh, finish.cuh, hankel.cuh) and the layout
     constants (internal.h), comment lines dropped."""
     csrc = os.path.join(ROOT, "paper_2304_12168_gb300", "csrc")
     code = ""
-    for f in ("chain.cu", "rowtiles.cuh", "mbarrier.cuh", "internal.h"):
+    for f in ("chain.cu", "rowtiles.cuh", "mbarrier.cuh", "aux_step.cuh", "finish.cuh", "hankel.cuh",
+              "internal.h"):
         src = open(os.path.join(csrc, f)).read()
         code += "\n".join(l for l in src.splitlines() if not l.strip().startswith("//"))
     return hashlib.sha256(code.encode()).hexdigest()
 
 
 def traffic_record():
-    """dram bytes per product of the fused chain (a launch's bytes over its 2t products)
-    from the committed ncu capture, if the kernel's source is unchanged since it was
-    taken (else None)."""
-    path = os.path.join(ROOT, "profiles", "chain_traffic.json")
+    """DRAM bytes per F_t step of the fused step kernel (a captured launch's bytes over its
+    steps, at the cycle's mean order t = 3) from the committed ncu capture, if the kernel's
+    source is unchanged since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "step_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
         if kernel_source_hash() != rec.get("kernel_source_sha256"):
             return None
-        return float(rec["dram_bytes_per_product_full_size"])
+        return float(rec["dram_bytes_per_step"])
     except Exception:
         return None
 
@@ -551,12 +553,14 @@ def main():
 
     # ---------------- roofline: the fused step kernel, every launch timed with events
     _, _, prof = plan.cta(b, profile=1, **opts)
-    launch_us = 1e3 * prof["spmv_ms"] / prof["spmv_count"]
+    # every launch of the fused step kernel timed with events; the unit is an F_t step
+    # (a launch runs up to 64 of them): the launches' summed time over the steps they ran
+    step_us = 1e3 * prof["spmv_ms"] / prof["spmv_count"]
     alg_bytes = prof["spmv_bytes"] / prof["spmv_count"]      # the survey's bytes per F_t step
     ts = [fpt_schedule(k) for k in range(prof["spmv_count"])]
     t_mean = statistics.fmean(ts)
     peak, peak_kind = peaks()
-    achieved = alg_bytes / (launch_us * 1e-6) / 1e9
+    achieved = alg_bytes / (step_us * 1e-6) / 1e9
     traffic = traffic_record()
     fpt_bytes = statistics.fmean(survey_bytes_per_fpt(p.m, p.n, p.nnz, fpt_schedule(k))
                                  for k in range(iters_per_step))
@@ -568,28 +572,29 @@ def main():
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
         "traffic": traffic, "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)",
-        "kernel": "cta_chain<double, DiaFmt, true>: one cooperative launch per F_t step -- the 2t "
-                  "products with A\u1d40 and A on the diagonal form (bulk-copy row tiles, "
-                  "warp-specialised, grid-wide barriers between products), then in every block the "
-                  "moments, the auxiliary solve and the block's slice of the x and r update",
-        "unit_of_work": "one F_t step (one launch): the survey's algorithmic bytes of an unfused F_t "
-                        "step of order t, t (B_A + B_At) + 8 t (2 m + 2 n) + 8 (t + 2)(m + n) with "
-                        "B_A = 12 nnz + 4 (m + 1), over the launch's event-timed duration",
-        "launches_timed": prof["spmv_count"], "avg_launch_us": launch_us, "mean_t": t_mean,
-        "bytes_per_launch": alg_bytes, "traffic_unit": "DRAM bytes per launch at t = 3 (ncu)",
+        "kernel": "cta_chain<double, DiaFmt, true>: the fused step, a persistent cooperative launch "
+                  "of up to 64 F_t steps -- per step the 2t products with A\u1d40 and A on the "
+                  "diagonal form (bulk-copy row tiles, warp-specialised, grid-wide waits between "
+                  "products), then in every block the moments, the auxiliary solve, the stop tests "
+                  "and the block's slice of the x and r update",
+        "unit_of_work": "one F_t step: the survey's algorithmic bytes of an unfused F_t step of order t, "
+                        "t (B_A + B_At) + 8 t (2 m + 2 n) + 8 (t + 2)(m + n) with B_A = 12 nnz + "
+                        "4 (m + 1), over the event-timed launches' duration per step",
+        "steps_timed": prof["spmv_count"], "avg_step_us": step_us, "mean_t": t_mean,
+        "bytes_per_step": alg_bytes, "traffic_unit": "DRAM bytes per F_t step at the mean order t = 3 (ncu)",
         # the whole solve step (the step kernel plus the gated true-residual launch and the
         # gaps between launches) against the same peak
         "step": {"bytes_per_fpt": fpt_bytes, "achieved": step_gbs, "unit": "GB/s", "frac": step_gbs / peak},
         # what DRAM actually served (ncu's dram__bytes per launch over the event-timed launch)
-        "dram": ({"achieved": traffic / (launch_us * 1e-6) / 1e9, "unit": "GB/s",
-                  "frac": traffic / (launch_us * 1e-6) / 1e9 / peak} if traffic else None),
+        "dram": ({"achieved": traffic / (step_us * 1e-6) / 1e9, "unit": "GB/s",
+                  "frac": traffic / (step_us * 1e-6) / 1e9 / peak} if traffic else None),
         # the diagonal form moves fewer bytes than CSR: values only, k = 5 per row
-        "format": {"bytes_per_launch": fmt_bytes, "achieved": fmt_bytes / (launch_us * 1e-6) / 1e9,
-                   "unit": "GB/s", "frac": fmt_bytes / (launch_us * 1e-6) / 1e9 / peak},
-        "fp64": {"bound": "alu", "flops_per_launch": 2.0 * fmas,
-                 "achieved": 2.0 * fmas / (launch_us * 1e-6) / 1e12,
+        "format": {"bytes_per_step": fmt_bytes, "achieved": fmt_bytes / (step_us * 1e-6) / 1e9,
+                   "unit": "GB/s", "frac": fmt_bytes / (step_us * 1e-6) / 1e9 / peak},
+        "fp64": {"bound": "alu", "flops_per_step": 2.0 * fmas,
+                 "achieved": 2.0 * fmas / (step_us * 1e-6) / 1e12,
                  "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
-                 "frac": 2.0 * fmas / (launch_us * 1e-6) / 1e12 / FP64_TFLOPS_NOMINAL,
+                 "frac": 2.0 * fmas / (step_us * 1e-6) / 1e12 / FP64_TFLOPS_NOMINAL,
                  "peak_kind": "nominal FP64 on CUDA cores: 152 SMs x 2 FMA/clk x 2.07 GHz x 2 flops "
                               "(not measured by the driver)"}}
 

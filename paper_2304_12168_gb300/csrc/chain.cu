@@ -170,9 +170,10 @@ __device__ __forceinline__ int step_order(int64_t k, int t_max, int cycle) {
     return j < t_max ? j + 1 : 2 * t_max - 1 - j;
 }
 
-// The fields a step's decisions change, from a block's copy of the control block to the
-// control block itself (block 0 only; the other blocks keep their copies in step).
-__device__ __forceinline__ void publish_step(Ctl* c, const Ctl& sc, int t) {
+// The fields the steps of a launch change, from a block's copy of the control block to the
+// control block itself, once at the end of the launch (block 0 only; every block keeps an
+// identical copy, and nothing else reads these fields while the launch runs).
+__device__ __forceinline__ void publish_steps(Ctl* c, const Ctl& sc) {
     c->k = sc.k;
     c->is_true = sc.is_true;
     c->need_true = sc.need_true;
@@ -182,8 +183,31 @@ __device__ __forceinline__ void publish_step(Ctl* c, const Ctl& sc, int t) {
     c->hist_len = sc.hist_len;
     c->rank = sc.rank;
     c->enh_stop = sc.enh_stop;
-    for (int k = 0; k < t; ++k) c->alpha[k] = sc.alpha[k];
+    c->matvecs = sc.matvecs;
+    for (int k = 0; k < kTMax; ++k) c->alpha[k] = sc.alpha[k];
+    for (int k = 0; k < 2 * kTMax + 2; ++k) c->phi[k] = sc.phi[k];
     if (sc.status != 0) c->status = sc.status;
+}
+
+// The stop tests of the last step (the finisher of the separate update kernel: step
+// count, history, true-residual period, residual and cap tests): every block waits for
+// every block's update, adds the ||r||² partials in one fixed order and runs them on its
+// copy of the control block. All threads of the block call it; false if the wait gave up.
+template <typename V>
+__device__ bool resolve_pending(Ctl* ctl, Ctl& sc, const StepArgs<V>& sa, int G, uint32_t base, int warp, int lane,
+                                int rot, volatile int& failed) {
+    if (threadIdx.x == 0 && !grid_wait(ctl, base)) {
+        failed = 1;
+        atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+    }
+    __syncthreads();
+    if (failed) return false;
+    if (warp == rot) {
+        const double rn2 = warp_sum_partials(sa.upart + (size_t)(sc.k & 1) * G, G);
+        if (lane == 0) finish(&sc, FinArgs{FIN_CTA_UPDATE, 0, blockIdx.x == 0 ? sa.hist : nullptr}, rn2, 0.0);
+    }
+    __syncthreads();
+    return true;
 }
 
 template <typename V, class F, bool STEP>
@@ -228,9 +252,26 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t_arg, floa
     int last_use[S];         // producer: the last use of each stage
     for (int k = 0; k < S; ++k) last_use[k] = -1;
     const int nsteps = STEP ? sa.nsteps : 1;
-    for (int step = 0; step < nsteps; ++step) {
+    // FP64 fused step: the stop tests of a step (its ||r||², the iteration count, the
+    // true-residual period) are taken at the next step's grid-wide wait, so that the
+    // update needs no wait of its own. pending: the last step's tests are still to be
+    // taken; the next step runs its chain meanwhile and is dropped if they stop the solve
+    // or ask for the true residual first. Steps whose tests do not depend on ||r||² being
+    // small (the period, the cap, the enhanced stop) take them before their chain.
+    bool pending = false;
+    int step = 0;
+    while (step < nsteps) {
+        if (STEP && kFp64 && pending) {
+            const int kk = sc.k + 1;
+            if (sc.enh_stop || (sc.R > 0 && kk % sc.R == 0) || kk >= sc.max_iter) {
+                if (!resolve_pending(ctl, sc, sa, G, base, warp, lane, rot, failed)) return;
+                pending = false;
+                if (sc.status != 0) break;
+            }
+        }
         if (STEP && !kFp64 && sc.need_true) break;   // FP32 chain: the refinement runs first
-        const int t = STEP ? step_order(sc.k, sa.t_max, sa.cycle) : t_arg;
+        ++step;
+        const int t = STEP ? step_order(sc.k + (pending ? 1 : 0), sa.t_max, sa.cycle) : t_arg;
         const int P = 2 * t;
         // FP64 fused step after a step that asked for the true residual: product p = -1 is
         // r = b - A x (on A, from x), before the chain reads r
@@ -244,8 +285,8 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t_arg, floa
                 const V* x = p < 0 ? sa.x : (p == 0 ? vec.r : (o ? vec.z[p >> 1] : vec.u[(p >> 1) - 1]));
                 const int nt = ops.ntiles[o];
                 // x of product p exists once every block finished p - 1 (and the previous
-                // step's update, for the first product of a later step)
-                bool gated = p > p0 || step > 0;
+                // step's update, for the first product of a later pass)
+                bool gated = p > p0 || step > 1;
                 const uint32_t target = base + (uint32_t)(p - p0) * (uint32_t)G;
                 int np = 0;
                 typename F::Prefetch pf;
@@ -379,9 +420,8 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t_arg, floa
             // sums the moments from all blocks' partials in one fixed order, so every block
             // holds the same bits, and takes the step decision itself (a warp solves the
             // auxiliary equation): no block waits on another's decision. Then the eight
-            // consumer warps update the block's slice of x and r, every block adds the
-            // ||r||² partials after a grid-wide wait and runs the stop tests, and the next
-            // step starts in the same launch.
+            // consumer warps update the block's slice of x and r, and the next step starts
+            // in the same launch.
             base += (uint32_t)(P - p0) * (uint32_t)G;
             __syncthreads();
             if (tid == 0 && !failed && !grid_wait(ctl, base)) {
@@ -390,15 +430,32 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t_arg, floa
             }
             __syncthreads();
             if (failed) return;
+            const int pw = (rot + 1) & 3;   // the warp that adds the last step's ||r||² partials
             if (p0 < 0 && warp < 2) {   // the true residual's ||r||² and rᵀb
-                const double s = warp_sum_partials(sa.rpart + (size_t)warp * G, G);
-                if (lane == 0) sc.red[warp] = s;
+                const double s2 = warp_sum_partials(sa.rpart + (size_t)warp * G, G);
+                if (lane == 0) sc.red[warp] = s2;
             }
-            sum_moment_partials(&sc, t, part, G, blockIdx.x == 0 ? ctl : nullptr, 2 + rot);
+            if (pending && warp == pw) {
+                const double s2 = warp_sum_partials(sa.upart + (size_t)(sc.k & 1) * G, G);
+                if (lane == 0) sc.red[2] = s2;
+            }
+            sum_moment_partials(&sc, t, part, G, nullptr, 2 + rot);
             if (warp == rot) {
                 int st2 = 0;
                 bool go_on = true;
-                if (p0 < 0) {   // the true residual first (as the finisher of a separate residual kernel)
+                if (pending) {   // the last step's stop tests (the update kernel's finisher)
+                    if (lane == 0) finish(&sc, FinArgs{FIN_CTA_UPDATE, 0, blockIdx.x == 0 ? sa.hist : nullptr},
+                                          sc.red[2], 0.0);
+                    __syncwarp();
+                    if (sc.status != 0) {
+                        go_on = false;
+                        st2 = sc.status;
+                    } else if (sc.need_true) {   // this chain ran on the recursive residual: dropped
+                        go_on = false;
+                        st2 = -1;
+                    }
+                }
+                if (go_on && p0 < 0) {   // the true residual first (as the finisher of a separate residual kernel)
                     if (lane == 0) finish(&sc, FinArgs{FIN_TRUE_RES, 0, blockIdx.x == 0 ? sa.hist : nullptr},
                                           sc.red[0], sc.red[1]);
                     __syncwarp();
@@ -422,46 +479,37 @@ cta_chain(typename F::Ops ops, ChainVecs<V> vec, StepArgs<V> sa, int t_arg, floa
                 __syncwarp();
                 if (lane == 0) {
                     decision = st2;
-                    sc.status = st2;
-                    if (blockIdx.x == 0) {
-                        ctl->matvecs += (p0 < 0 ? 1 : 0) + (go_on ? P : 0);
-                        publish_step(ctl, sc, t);
-                    }
+                    if (st2 > 0) sc.status = st2;
+                    sc.matvecs += (p0 < 0 ? 1 : 0) + (st2 >= 0 && (st2 == 0 || go_on) ? P : 0);
                 }
             }
             __syncthreads();
-            if (decision != 0) break;   // the solve ends with this step
+            pending = false;
+            if (decision < 0) continue;  // the true residual goes first: the next pass starts with it
+            if (decision != 0) break;    // the solve ends with this step
             const double acc = warp < kRwConsumers ? step_update_t<V>(sa, vec, sc.alpha, t) : 0.0;
-            // ||r||²: block partial, grid-wide wait (every block's slice of r is also
-            // complete then, for the next step's first product), the same sum in every block
+            // ||r||²: the block's partial, and its arrival (the next step's first product
+            // waits for every block's update through it)
             const double bs = block_sum_warp0<kRwThreads>(acc, &red[0][0]);
             if (tid == 0) {
-                sa.upart[blockIdx.x] = bs;
+                sa.upart[(size_t)(sc.k & 1) * G + blockIdx.x] = bs;
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 __threadfence();
                 atomicAdd(&ctl->chain_bar, 1u);
             }
             base += (uint32_t)G;
-            if (tid == 0 && !grid_wait(ctl, base)) {
-                failed = 1;
-                atomicExch(&ctl->status, (int32_t)TACTA_REASON_TIMEOUT);
+            if constexpr (kFp64) {
+                pending = true;
+            } else {
+                // FP32 chain: the stop tests now (a refinement ends the launch)
+                if (!resolve_pending(ctl, sc, sa, G, base, warp, lane, rot, failed)) return;
+                if (sc.status != 0 || sc.need_true) break;
             }
-            __syncthreads();
-            if (failed) return;
-            if (warp == rot) {
-                const double rn2 = warp_sum_partials(sa.upart, G);
-                if (lane == 0) {
-                    finish(&sc, FinArgs{FIN_CTA_UPDATE, 0, blockIdx.x == 0 ? sa.hist : nullptr}, rn2, 0.0);
-                    if (blockIdx.x == 0) publish_step(ctl, sc, t);
-                }
-            }
-            __syncthreads();
-            // a stop, or (FP32 chain) a refinement due: the FP64 residual and the fold of
-            // the FP32 correction run as their own launches after this one
-            if (sc.status != 0 || (!kFp64 && sc.need_true)) break;
         }
     }
     if constexpr (STEP) {
+        if (pending && !resolve_pending(ctl, sc, sa, G, base, warp, lane, rot, failed)) return;
+        if (blockIdx.x == 0 && tid == 0) publish_steps(ctl, sc);
         // every block is past its last grid-wide wait once it takes its ticket: the last one
         // resets the counters for the next launch
         __syncthreads();

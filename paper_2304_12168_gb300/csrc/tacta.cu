@@ -1109,7 +1109,9 @@ static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t h
         // early for a refinement, so up to one launch per step may be needed
         Opts O1 = O;
         O1.o.poll_every = 1;
-        const int64_t calls = mixed ? (int64_t)O.o.max_iter + 1 : ((int64_t)O.o.max_iter + nsteps - 1) / nsteps;
+        // (a few spare launches: a pass whose chain is dropped for a true residual does
+        // not count as a step)
+        const int64_t calls = mixed ? (int64_t)O.o.max_iter + 1 : ((int64_t)O.o.max_iter + nsteps - 1) / nsteps + 8;
         auto body = [&](const LaunchCtx& LL, int64_t) { return enqueue_cta_steps(p, LL, nsteps, t_max, cycle, mixed); };
         st = run_loop(p, O1, calls, 1, O.o.use_graph != 0, g, mixed ? &p->g_cta32_launches : &p->g_cta_launches,
                       mixed ? &p->g_cta32_iters : &p->g_cta_iters, body, launches);
