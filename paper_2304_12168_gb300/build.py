@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtacta.so")
-SOURCES = ["kernels.cu", "transpose.cu", "tacta.cu", "static_scratch.cu", "batched.cu", "chain.cu"]
+SOURCES = ["kernels.cu", "transpose.cu", "tacta.cu", "static_scratch.cu", "batched.cu", "chain.cu",
+           "dense_cluster.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                 "-Xcompiler", "-ffp-contract=off",

@@ -307,6 +307,23 @@ cudaError_t dense_transpose(cudaStream_t s, const double* A, int64_t rows, int64
 cudaError_t run_tiles_build(cudaStream_t s, const DevCSR& a, int4* tiles, int2* xwin, int2* runs, uint16_t* lcol,
                             int32_t* stats);
 
+// ---------------------------------------------------------------- small dense A on chip
+// CTA on a dense A that fits the shared memory of one thread-block cluster (dense_cluster.cu):
+// whole F_t steps in one launch, A and Aᵀ split by rows over the cluster's blocks.
+struct DenseClusterArgs {
+    const double* A;         // m x n row-major (device)
+    const double* At;        // n x m row-major (device)
+    int64_t m, n;
+    double* x;               // n: read at entry, written at exit
+    double* r;               // m: the carried residual, read at entry, written at exit
+    const double* b;         // m
+    double* hist;            // history buffer
+    int nsteps, t_max, cycle;
+};
+// blocks of the cluster (16 or 8) that hold an m x n system, 0 if none does on this device
+int dense_cluster_size(int64_t m, int64_t n);
+cudaError_t launch_cta_dense_cluster(const LaunchCtx& L, const DenseClusterArgs& a, int C);
+
 // ---------------------------------------------------------------- per-device one-time setup
 // Kernel attributes (the dynamic shared-memory opt-in above 48 KB) are per device, so a
 // process-wide "done" flag would leave a second device without them. done_on_device(key)

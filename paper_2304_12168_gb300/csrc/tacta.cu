@@ -119,6 +119,8 @@ struct Plan {
     bool fused = false;              // this call runs the fused chain
     bool dia = false;                // ... on the diagonal form
     bool step = false;               // ... as the fused step (auxiliary solve and update in the launch)
+    int dc_size = 0;                 // dense A held on chip by a cluster of this many blocks (0: no)
+    bool dcl = false;                // this call runs the on-chip dense step
     // opt-in profiling of the iteration's products (events around each launch)
     bool profiling = false;
     int prof_count = 0;
@@ -486,6 +488,7 @@ static tacta_status plan_create(const tacta_matrix* M, const tacta_options* opt,
         PTRY(dense_transpose(s, a.vals, m, n, t.vals));
         a.cfg.kind = n >= 64 ? 1 : 0;
         t.cfg.kind = m >= 64 ? 1 : 0;
+        p->dc_size = dense_cluster_size(m, n);   // small enough to keep on chip in one cluster
     }
     const int64_t mn = std::max(m, n);
     PTRY(cudaMalloc(&p->ctl, sizeof(Ctl)));
@@ -1093,9 +1096,10 @@ static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t h
     p->dia = (O.o.fused_chain == 1 || O.o.fused_chain == 3) && (mixed ? p->dia_grid32 : p->dia_grid) > 0;
     p->fused = p->dia || (O.o.fused_chain != 0 && (mixed ? p->chain_grid32 : p->chain_grid) > 0);
     p->step = p->fused && O.o.fused_chain != 3;
+    p->dcl = !mixed && p->A.format == TACTA_DENSE && p->dc_size > 0 && O.o.fused_chain != 0;
     const int nsteps = std::max(1, O.o.poll_every);   // F_t steps per launch of the fused step
-    const int key = (((t_max * 4 + cycle) * 4 + (p->fused ? 1 : 0) + (p->dia ? 2 : 0)) * 2 + (p->step ? 1 : 0)) *
-                        4096 + std::min(nsteps, 4095);
+    const int key = ((((t_max * 4 + cycle) * 4 + (p->fused ? 1 : 0) + (p->dia ? 2 : 0)) * 2 + (p->step ? 1 : 0)) * 2 +
+                     (p->dcl ? 1 : 0)) * 4096 + std::min(nsteps, 4095);
     cudaGraphExec_t* g = mixed ? &p->g_cta32 : &p->g_cta;
     int* gkey = mixed ? &p->g_cta32_key : &p->g_cta_key;
     if (*g && *gkey != key) {
@@ -1103,7 +1107,21 @@ static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t h
         *g = nullptr;
     }
     *gkey = key;
-    if (p->step) {
+    if (p->dcl) {
+        // small dense A on chip: one cluster launch runs up to nsteps steps; the device stops at max_iter
+        Opts O1 = O;
+        O1.o.poll_every = 1;
+        const int64_t calls = ((int64_t)O.o.max_iter + nsteps - 1) / nsteps + 8;
+        auto body = [&](const LaunchCtx& LL, int64_t) {
+            cudaError_t e = prof_mark(p, LL);
+            if (e != cudaSuccess) return e;
+            DenseClusterArgs a{p->A.dense.vals, p->At.dense.vals, p->m, p->n, p->x, p->r, p->b, p->hist,
+                               nsteps, t_max, cycle};
+            if ((e = launch_cta_dense_cluster(LL, a, p->dc_size)) != cudaSuccess) return e;
+            return prof_mark(p, LL);
+        };
+        st = run_loop(p, O1, calls, 1, O.o.use_graph != 0, g, &p->g_cta_launches, &p->g_cta_iters, body, launches);
+    } else if (p->step) {
         // one body = one launch of up to nsteps steps; the device stops at max_iter. FP64
         // launches run their nsteps unless the solve stops; an FP32-chain launch may end
         // early for a refinement, so up to one launch per step may be needed
@@ -1127,7 +1145,7 @@ static tacta_status cta_core(Plan* p, const Opts& O, const double* x0, int64_t h
     if (st != TACTA_OK) return st;
     // the FP64 fused step runs a pending true residual at the start of the next step: after
     // the last step it runs here (a no-op when none is pending or the solve has stopped)
-    if (!mixed && p->step)
+    if (!mixed && (p->step || p->dcl))
         CUDA_TRY(launch_spmv(L, p->A, p->x, p->r, EPI_RESID, EpiArgs{p->b, nullptr, nullptr},
                              FinArgs{FIN_TRUE_RES, 0, p->hist}, GATE_NEED_TRUE));
     if (mixed) CUDA_TRY(launch_fold_correction(L, p->n, p->x, p->dx32, GATE_FORCE));
@@ -1161,7 +1179,7 @@ static tacta_status plan_cta(Plan* p, const VecIO& io, const tacta_options* opt,
     prof_begin(p, O.o.profile);
     if ((st = cta_core(p, O, io.x0, hist_cap, &launches)) != TACTA_OK) { p->profiling = false; return st; }
     if ((st = read_ctl(p, O.s)) != TACTA_OK) return st;
-    if (p->profiling && p->step) {   // the timed unit is an F_t step: the launches ran stage->k of them
+    if (p->profiling && (p->step || p->dcl)) {   // the timed unit is an F_t step: the launches ran stage->k of them
         const bool mixed = O.o.precision == TACTA_PRECISION_MIXED;
         p->prof_count = p->stage->k;
         p->prof_bytes = 0.0;
