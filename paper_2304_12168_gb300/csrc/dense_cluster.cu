@@ -118,28 +118,31 @@ __device__ void dc_rows(const double* M, int64_t rows, int64_t len, const double
             a0 = fma(v, v, a0);
         }
     }
-    // per-warp values are the same in every lane; warp 0 adds the eight in order
+    // per-warp values are the same in every lane; warp 0 adds the eight in a fixed tree
     if (lane == 0) {
         red[warp] = a0;
         red[8 + warp] = a1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s0 = 0.0, s1 = 0.0;
-        for (int w = 0; w < kDcThreads / 32; ++w) {
-            s0 += red[w];
-            s1 += red[8 + w];
+    if (threadIdx.x < 32) {
+        double s0 = lane < NW ? red[lane] : 0.0, s1 = lane < NW ? red[8 + lane] : 0.0;
+#pragma unroll
+        for (int o = NW / 2; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
         }
-        acc = s0;
-        acc1 = s1;
+        if (threadIdx.x == 0) {
+            acc = s0;
+            acc1 = s1;
+        }
     }
 }
 
-// The cluster-wide sums of `k` block partials published at part[0, k) of every block (after
-// the cluster barrier that follows their writes): thread 0, rank order, the same bits in
-// every block.
+// The cluster-wide sums of `k` <= 2 block partials published at part[0, k) of every block
+// (after the cluster barrier that follows their writes), into out on thread 0: the same
+// bits in every block.
 // The remote loads run in parallel (thread j of warp 0 fetches block j's partials), the
-// additions in rank order on lane 0.
+// additions in a fixed tree.
 __device__ __forceinline__ void dc_sum(cg::cluster_group& cl, const double* part, int k, double* out) {
     if (threadIdx.x < 32) {
         const unsigned j = threadIdx.x;
@@ -149,14 +152,16 @@ __device__ __forceinline__ void dc_sum(cg::cluster_group& cl, const double* part
             v0 = pp[0];
             if (k > 1) v1 = pp[1];
         }
-        double s0 = 0.0, s1 = 0.0;
-        for (unsigned i = 0; i < cl.num_blocks(); ++i) {
-            s0 += __shfl_sync(0xffffffffu, v0, i);
-            s1 += __shfl_sync(0xffffffffu, v1, i);
+        // a fixed butterfly (lanes beyond the cluster hold exact zeros): lane 0's sum has the
+        // same bits in every block
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+            v1 += __shfl_xor_sync(0xffffffffu, v1, o);
         }
         if (threadIdx.x == 0) {
-            out[0] = s0;
-            if (k > 1) out[1] = s1;
+            out[0] = v0;
+            if (k > 1) out[1] = v1;
         }
     }
 }
