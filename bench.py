@@ -342,10 +342,12 @@ def batched_workload(tacta, dev, stream):
         B.cta(b, **kw)                                       # warm (graph capture)
         t, (x, iters, rel, reason) = timed(lambda: B.cta(b, **kw), stream)
         conv = reason == 1
+        shape = tacta.Batch.configs()[cfg]
+        blocks = min(B0.count, torch.cuda.get_device_properties(dev).multi_processor_count * shape[1])
         res[name] = {"time_ms": t, "converged": int(conv.sum()), "maxiter": int((reason == 3).sum()),
                      "system_iters": int(iters.sum()), "system_iters_per_s": float(iters.sum() / (t * 1e-3)),
                      "max_rel_res_converged": float(rel[conv].max()) if conv.any() else None,
-                     "config": tacta.Batch.configs()[cfg]}
+                     "config": shape, "completion": completion_profile(*B.timeline(), blocks)}
         B.close()
     # single-system FP64 path on a sample, extrapolated to the batch
     idx = np.linspace(0, B0.count - 1, 24).astype(int)
@@ -364,6 +366,26 @@ def batched_workload(tacta, dev, stream):
         res[name]["speedup_over_plan_fp64"] = res["plan_fp64_per_system_sample"]["extrapolated_batch_ms"] / \
             res[name]["time_ms"]
     return res
+
+
+def completion_profile(tb, te, blocks):
+    """The batch's completion profile from the per-system device clocks of one solve: when
+    50/90/99/100 % of the systems were done (ms after the first was taken), the share of
+    the launch's block-time spent on systems, and the mean share of blocks still busy
+    after the 90 % mark (the tail)."""
+    import numpy as np
+    t0 = int(tb.min())
+    done = np.sort((te - t0) * 1e-6)
+    span = float(done[-1])
+    pct = {f"p{q}_ms": float(done[min(len(done) - 1, int(np.ceil(q / 100 * len(done))) - 1)])
+           for q in (50, 90, 99, 100)}
+    busy = float(np.sum(te - tb)) * 1e-6
+    t90 = pct["p90_ms"]
+    beg, end = (tb - t0) * 1e-6, (te - t0) * 1e-6
+    tail = float(np.sum(np.clip(end, t90, None) - np.clip(beg, t90, None)))
+    return dict(pct, blocks=int(blocks), busy_frac=busy / (blocks * span) if span > 0 else None,
+                tail_busy_frac=tail / (blocks * (span - t90)) if span > t90 else None,
+                longest_system_ms=float(((te - tb) * 1e-6).max()))
 
 
 def timed(fn, stream):

@@ -301,7 +301,8 @@ tacta_status tacta_residual_static(const tacta_matrix* A, const double* x, const
  *   Storage of the copy of A_s that the chain z_i = Aᵀ u_{i-1}, u_i = A z_i reads:
  *     TACTA_BATCH_FP64 -- FP64 chain; the iteration follows the FP64 path exactly.
  *     TACTA_BATCH_FP32 -- FP32 values and chain (FP32 accumulation).
- *     TACTA_BATCH_BF16 -- BF16 values widened to FP32 (FP32 accumulation).
+ *     TACTA_BATCH_BF16 -- BF16 values, FP32 chain and accumulation (widened on CUDA
+ *                         cores, or on the tensor cores: tacta_batch_config_tensor_cores).
  *   In every mode the moments, the auxiliary solve (Eq. eqcoeff) and the stop
  *   tests are FP64, and the residual b - A x is recomputed in FP64 from an FP64
  *   copy of A_s: every recompute_every steps, whenever the carried residual passes
@@ -340,12 +341,25 @@ tacta_status tacta_batch_cta(tacta_batch batch, const double* b, double* x, int3
 /* Launch configurations: threads per block and resident blocks per SM. The autotuner
    times every configuration that fits on (batch, b) with the given options, keeps the
    fastest for later solves and returns its index and time; set_config picks one
-   (-1: the default). */
+   (-1: the default). tacta_batch_config_tensor_cores(c) is 1 when configuration c runs
+   the chain's products on the tensor cores (BF16 tiles, mma.sync m16n8k16 with FP32
+   accumulation, the FP32 chain vectors carried exactly as three BF16 terms): it admits
+   BF16 storage with n_s <= 1024 only (other batches: TACTA_ERR_INVALID from
+   tacta_batch_cta, skipped by the autotuner). */
 int32_t tacta_batch_num_configs(void);
 tacta_status tacta_batch_config_shape(int32_t config, int32_t* threads, int32_t* blocks_per_sm);
+int32_t tacta_batch_config_tensor_cores(int32_t config);
 tacta_status tacta_batch_tune(tacta_batch batch, const double* b, const tacta_options* opt,
                               int32_t* best_config, double* best_ms);
 tacta_status tacta_batch_set_config(tacta_batch batch, int32_t config);
+/* tacta_batch_timeline -- when each system of the last completed tacta_batch_cta was
+   taken by a thread block and when that block finished it: count values each, device
+   clock (%globaltimer, nanoseconds; only differences are meaningful), host or device
+   pointers. Systems the last solve did not reach hold their previous values (0 before
+   the first solve). The batch's completion profile -- how many systems are done by a
+   given time, how many blocks are still busy in the launch's tail -- follows from them.
+   Synchronous. */
+tacta_status tacta_batch_timeline(tacta_batch batch, int64_t* t_begin_ns, int64_t* t_end_ns);
 void tacta_batch_destroy(tacta_batch batch);
 /* message of the last failed tacta_batch_* call on the calling thread */
 const char* tacta_batch_last_error(void);

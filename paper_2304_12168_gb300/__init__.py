@@ -70,7 +70,7 @@ EXPORTS = ["tacta_default_options", "cta_solve", "ta_solve", "ta_minnorm", "tact
            "tacta_residual_static", "tacta_last_error", "tacta_version",
            "tacta_batch_create", "tacta_batch_cta", "tacta_batch_destroy", "tacta_batch_tune",
            "tacta_batch_set_config", "tacta_batch_num_configs", "tacta_batch_config_shape",
-           "tacta_batch_last_error", "tacta_aux_solve", "tacta_dia_tile_plan", "tacta_column_partition"]
+           "tacta_batch_last_error", "tacta_batch_timeline", "tacta_batch_config_tensor_cores", "tacta_aux_solve", "tacta_dia_tile_plan", "tacta_column_partition"]
 
 _lib_handle = None
 
@@ -123,6 +123,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tacta_batch_destroy.argtypes = [vp]
     lib.tacta_batch_destroy.restype = None
     lib.tacta_batch_tune.argtypes = [vp, dp, P(tacta_options), i32p, P(ctypes.c_double)]
+    lib.tacta_batch_config_tensor_cores.argtypes = [ctypes.c_int32]
+    lib.tacta_batch_config_tensor_cores.restype = ctypes.c_int32
+    lib.tacta_batch_timeline.argtypes = [vp, vp, vp]
+    lib.tacta_batch_timeline.restype = ctypes.c_int32
     lib.tacta_batch_tune.restype = ctypes.c_int32
     lib.tacta_batch_set_config.argtypes = [vp, ctypes.c_int32]
     lib.tacta_batch_set_config.restype = ctypes.c_int32
@@ -510,6 +514,14 @@ class Batch:
     def set_config(self, config: int):
         _check_batch(load_library().tacta_batch_set_config(self._h, int(config)))
 
+    def timeline(self):
+        """(t_begin, t_end): int64 device-clock nanoseconds at which each system of the last
+        solve was taken by a block and finished (tacta_batch_timeline)."""
+        tb = np.zeros(self.count, dtype=np.int64)
+        te = np.zeros(self.count, dtype=np.int64)
+        _check_batch(load_library().tacta_batch_timeline(self._h, tb.ctypes.data, te.ctypes.data))
+        return tb, te
+
     @staticmethod
     def configs():
         """[(threads per block, blocks per SM)] of the launch configurations."""
@@ -520,6 +532,13 @@ class Batch:
             _check_batch(lib.tacta_batch_config_shape(c, ctypes.byref(t), ctypes.byref(p)))
             out.append((t.value, p.value))
         return out
+
+    @staticmethod
+    def tensor_core_configs():
+        """Indices of the launch configurations whose products run on the tensor cores
+        (BF16 storage only)."""
+        lib = load_library()
+        return [c for c in range(lib.tacta_batch_num_configs()) if lib.tacta_batch_config_tensor_cores(c)]
 
     def split(self, v, which="x"):
         """Per-system views of a packed vector."""

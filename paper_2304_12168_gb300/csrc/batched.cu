@@ -25,6 +25,7 @@
 #include <mutex>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "hankel.cuh"
@@ -61,7 +62,9 @@ __device__ __forceinline__ void load16(const __nv_bfloat16* p, float (&o)[8]) {
     }
 }
 
-__device__ __forceinline__ bool finite_d(double v) { return fabs(v) <= DBL_MAX; }
+__device__ __forceinline__ bool finite_d(double v) {
+    return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;   // exponent not all ones
+}
 
 template <class TA> __device__ __forceinline__ TA to_store(double v);
 template <> __device__ __forceinline__ double to_store<double>(double v) { return v; }
@@ -80,7 +83,7 @@ struct SysDesc {
 struct BatchParams {
     double tol2, tol_n2, pivot_tol, eta2;
     int32_t max_iter, R, t_max, cycle;
-    int32_t m_cap, n_cap;  // vector capacities (n_cap a multiple of 8)
+    int32_t m_cap, n_cap;  // vector capacities (multiples of 8: every vector starts 16-byte aligned)
     int64_t a_cap;         // elements of A a block can stage in shared memory
     int64_t area_bytes;    // streamed kernel: bytes of the A area (ring, or A when resident)
 };
@@ -89,7 +92,15 @@ struct BatchOut {
     int32_t* iters;
     int32_t* reason;
     double* rel_res;
+    int64_t* t_beg;        // per system: device clock (ns) when a block took it and when it finished
+    int64_t* t_end;
 };
+
+__device__ __forceinline__ int64_t clock_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (int64_t)t;
+}
 
 __device__ __forceinline__ int schedule_dev(int k, int t_max, int cycle) {
     if (cycle == TACTA_CYCLE_FIXED || t_max == 1) return t_max;
@@ -99,34 +110,112 @@ __device__ __forceinline__ int schedule_dev(int k, int t_max, int cycle) {
     return j < t_max ? j + 1 : 2 * t_max - 1 - j;
 }
 
+// Sums of squares of chain values. An FP64 chain sums in FP64. An FP32 chain sums in
+// FP32 pairs hi + lo: each square is split exactly (p = fl(v v), e = fma(v, v, -p)) and
+// added by Knuth's TwoSum, whose error term goes to lo, so the pair carries about
+// 2^-44 relative accuracy while every operation stays on the FP32 pipe (this GPU issues
+// FP64 at a small fraction of the FP32 rate). The _rn intrinsics keep the compiler from
+// contracting the split's multiply-add pairs.
+template <class TC> struct SqAcc;
+template <> struct SqAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s = fma(v, v, s); }
+    __device__ __forceinline__ void merge(const SqAcc& o) { s += o.s; }
+    __device__ __forceinline__ SqAcc shfl_xor(int o) const {
+        SqAcc r;
+        r.s = __shfl_xor_sync(0xffffffffu, s, o);
+        return r;
+    }
+    __device__ __forceinline__ void put(double* slot) const { *slot = s; }
+    __device__ __forceinline__ static SqAcc get(const double* slot) {
+        SqAcc r;
+        r.s = *slot;
+        return r;
+    }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct SqAcc<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add_pair(float p, float e) {
+        const float sm = __fadd_rn(hi, p);
+        const float bv = __fsub_rn(sm, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sm, bv)), __fsub_rn(p, bv));
+        hi = sm;
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ void add(float v) {
+        const float p = __fmul_rn(v, v);
+        add_pair(p, __fmaf_rn(v, v, -p));
+    }
+    __device__ __forceinline__ void merge(const SqAcc& o) { add_pair(o.hi, o.lo); }
+    __device__ __forceinline__ SqAcc shfl_xor(int o) const {
+        SqAcc r;
+        r.hi = __shfl_xor_sync(0xffffffffu, hi, o);
+        r.lo = __shfl_xor_sync(0xffffffffu, lo, o);
+        return r;
+    }
+    __device__ __forceinline__ void put(double* slot) const {
+        *reinterpret_cast<float2*>(slot) = make_float2(hi, lo);
+    }
+    __device__ __forceinline__ static SqAcc get(const double* slot) {
+        const float2 v = *reinterpret_cast<const float2*>(slot);
+        SqAcc r;
+        r.hi = v.x;
+        r.lo = v.y;
+        return r;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+template <class TC>
+__device__ __forceinline__ SqAcc<TC> warp_sum_sq(SqAcc<TC> a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a.merge(a.shfl_xor(o));
+    return a;
+}
+
+// block-wide sums of two accumulators (red: 2 NT/32 + 2 slots); thread 0 adds the warps'
+// sums in warp order and every thread gets the FP64 totals
+template <int NT, class TC>
+__device__ __forceinline__ double2 block_sum_sq(SqAcc<TC> a, SqAcc<TC> b, double* red) {
+    a = warp_sum_sq(a);
+    b = warp_sum_sq(b);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();                       // red is free (previous readers are done)
+    if (lane == 0) { a.put(red + 2 * w); b.put(red + 2 * w + 1); }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SqAcc<TC> ta = SqAcc<TC>::get(red), tb = SqAcc<TC>::get(red + 1);
+        for (int i = 1; i < NT / 32; ++i) {
+            ta.merge(SqAcc<TC>::get(red + 2 * i));
+            tb.merge(SqAcc<TC>::get(red + 2 * i + 1));
+        }
+        red[2 * (NT / 32)] = ta.value();
+        red[2 * (NT / 32) + 1] = tb.value();
+    }
+    __syncthreads();
+    return make_double2(red[2 * (NT / 32)], red[2 * (NT / 32) + 1]);
+}
+
 // block-wide sums of two FP64 values; every thread gets the result
 template <int NT>
 __device__ __forceinline__ double2 block_sum2(double a, double b, double* red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();                       // red is free (previous readers are done)
-    if (lane == 0) { red[2 * w] = a; red[2 * w + 1] = b; }
-    __syncthreads();
-    double2 r = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int i = 0; i < NT / 32; ++i) { r.x += red[2 * i]; r.y += red[2 * i + 1]; }
-    return r;
+    SqAcc<double> sa, sb;
+    sa.s = a;
+    sb.s = b;
+    return block_sum_sq<NT, double>(sa, sb, red);
 }
 
-// out = (Aᵀ u) * scale, out and the squares' sum in the chain type / FP64
+// out = (Aᵀ u) * scale, out and the sum of its squares
 template <class TA, int NT>
-__device__ double prod_t(const TA* A, int m, int n, int ld, const typename Elem<TA>::TC* u,
+__device__ SqAcc<typename Elem<TA>::TC> prod_t(const TA* A, int m, int n, int ld, const typename Elem<TA>::TC* u,
                          typename Elem<TA>::TC* out, typename Elem<TA>::TC* part, double scale) {
     using TC = typename Elem<TA>::TC;
     constexpr int V = Elem<TA>::V;
     const int CG = (n + V - 1) / V;
     const int RG = CG >= NT ? 1 : NT / CG;
     const TC sc = (TC)scale;
-    double sq = 0.0;
+    SqAcc<TC> sq;
     for (int w = threadIdx.x; w < CG * RG; w += NT) {
         const int cg = w % CG, rg = w / CG;
         TC acc[V];
@@ -164,7 +253,7 @@ __device__ double prod_t(const TA* A, int m, int n, int ld, const typename Elem<
                 if (c < n) {
                     const TC z = acc[v] * sc;
                     out[c] = z;
-                    sq = fma((double)z, (double)z, sq);
+                    sq.add(z);
                 }
             }
         } else {
@@ -179,7 +268,7 @@ __device__ double prod_t(const TA* A, int m, int n, int ld, const typename Elem<
             for (int rg = 0; rg < RG; ++rg) acc += part[rg * CG * V + c];
             const TC z = acc * sc;
             out[c] = z;
-            sq = fma((double)z, (double)z, sq);
+            sq.add(z);
         }
     }
     return sq;
@@ -187,7 +276,7 @@ __device__ double prod_t(const TA* A, int m, int n, int ld, const typename Elem<
 
 // out = (A z) * scale: LPR lanes per row (a power of two >= the row's vectors, <= 32)
 template <class TA, int NT>
-__device__ double prod_n(const TA* A, int m, int n, int ld, const typename Elem<TA>::TC* z,
+__device__ SqAcc<typename Elem<TA>::TC> prod_n(const TA* A, int m, int n, int ld, const typename Elem<TA>::TC* z,
                          typename Elem<TA>::TC* out, double scale) {
     using TC = typename Elem<TA>::TC;
     constexpr int V = Elem<TA>::V;
@@ -198,7 +287,7 @@ __device__ double prod_n(const TA* A, int m, int n, int ld, const typename Elem<
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane / lpr, sl = lane % lpr;
     const TC sc = (TC)scale;
-    double sq = 0.0;
+    SqAcc<TC> sq;
     for (int base = warp * rpw; base < m; base += (NT / 32) * rpw) {
         const int row = base + sub;
         TC acc = 0;
@@ -231,7 +320,7 @@ __device__ double prod_n(const TA* A, int m, int n, int ld, const typename Elem<
         if (row < m && sl == 0) {
             const TC y = acc * sc;
             out[row] = y;
-            sq = fma((double)y, (double)y, sq);
+            sq.add(y);
         }
     }
     return sq;
@@ -268,9 +357,10 @@ __device__ double2 residual64(const double* __restrict__ A64, int m, int n, cons
 }
 
 struct Shared {           // block-wide scalars (static shared memory)
-    double red[2 * 16];
+    double red[2 * 16 + 2];
     double phi[2 * kTMax + 2];
     double beta[kTMax];
+    double coef[2 * kTMax];   // the update's coefficients in the chain type (beta_j, beta_j / s)
     int32_t sys;
     int32_t rank;
     int32_t stop;
@@ -298,6 +388,7 @@ batch_cta(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, in
         __syncthreads();
         const int q = S.sys;
         if (q >= count) break;
+        if (tid == 0) out.t_beg[order[q]] = clock_ns();
         const SysDesc d = sys[order[q]];
         const int m = d.m, n = d.n, ld = d.ld;
         const double* b = bvec + d.b_off;
@@ -326,8 +417,8 @@ batch_cta(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, in
         const double bn2 = block_sum2<NT>(bb, 0.0, S.red).x;   // also orders the writes above
         double nrm_thr = 0.0;
         if (P.tol_n2 > 0.0 && bn2 > 0.0) {
-            const double mt = prod_t<TA, NT>(A, m, n, ld, r, z, part, 1.0);
-            nrm_thr = P.tol_n2 * block_sum2<NT>(mt, 0.0, S.red).x;
+            const SqAcc<TC> mt = prod_t<TA, NT>(A, m, n, ld, r, z, part, 1.0);
+            nrm_thr = P.tol_n2 * block_sum_sq<NT>(mt, SqAcc<TC>{}, S.red).x;
             for (int c = tid; c < n; c += NT) z[c] = 0;
         }
         double rn2 = bn2;
@@ -362,49 +453,56 @@ batch_cta(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, in
             for (int i = 1; i <= t; ++i) {
                 TC* zi = z + (int64_t)(i - 1) * P.n_cap;
                 TC* ui = u + (int64_t)(i - 1) * P.m_cap;
-                const double p1 = prod_t<TA, NT>(A, m, n, ld, uprev, zi, part, d.inv_s);
+                const SqAcc<TC> p1 = prod_t<TA, NT>(A, m, n, ld, uprev, zi, part, d.inv_s);
                 __syncthreads();   // zi complete before the product with A reads it
-                const double p2 = prod_n<TA, NT>(A, m, n, ld, zi, ui, d.inv_s);
-                const double2 ph = block_sum2<NT>(p1, p2, S.red);   // also completes ui
+                const SqAcc<TC> p2 = prod_n<TA, NT>(A, m, n, ld, zi, ui, d.inv_s);
+                const double2 ph = block_sum_sq<NT>(p1, p2, S.red);   // also completes ui
                 if (tid == 0) {
                     S.phi[2 * i - 1] = ph.x;
                     S.phi[2 * i] = ph.y;
                 }
                 uprev = ui;
             }
-            if (tid == 0) {
+            if (tid < 32) {   // the auxiliary solve by one warp (bit for bit the serial solve)
+                __syncwarp();
                 int st = 0;
                 for (int i = 1; i <= 2 * t; ++i)
                     if (!finite_d(S.phi[i])) st = TACTA_REASON_NONFINITE;
                 // normal-equation test on the unscaled phi_1 = s² phi~_1
                 if (st == 0 && S.phi[1] * d.s * d.s <= nrm_thr) st = TACTA_REASON_NORMAL;
                 if (st == 0) {
-                    S.rank = hankel_solve_dev(S.phi, t, P.pivot_tol, S.beta);
-                    if (S.rank == 0) st = TACTA_REASON_BREAKDOWN;
+                    const int rank = hankel_solve_warp(S.phi, t, P.pivot_tol, S.beta);
+                    if (rank == 0) st = TACTA_REASON_BREAKDOWN;
+                    __syncwarp();
+                    if (tid < t) {   // the update's coefficients, converted once
+                        TC* cf = reinterpret_cast<TC*>(S.coef);
+                        cf[tid] = (TC)S.beta[tid];
+                        cf[kTMax + tid] = (TC)(S.beta[tid] * d.inv_s);
+                    }
                 }
-                S.stop = st;
+                if (tid == 0) S.stop = st;
             }
             __syncthreads();
             if (S.stop) { reason = S.stop; break; }
             // dx += s^-1 sum beta_j z_j ; r -= sum beta_j u_j ; ||r||²
             TC bz[kTMax], bu[kTMax];
             for (int j = 0; j < t; ++j) {
-                bu[j] = (TC)S.beta[j];
-                bz[j] = (TC)(S.beta[j] * d.inv_s);
+                bu[j] = reinterpret_cast<const TC*>(S.coef)[j];
+                bz[j] = reinterpret_cast<const TC*>(S.coef)[kTMax + j];
             }
             for (int c = tid; c < n; c += NT) {
                 TC v = dx[c];
                 for (int j = 0; j < t; ++j) v = fma(bz[j], z[(int64_t)j * P.n_cap + c], v);
                 dx[c] = v;
             }
-            double sq = 0.0;
+            SqAcc<TC> sq;
             for (int i = tid; i < m; i += NT) {
                 TC v = r[i];
                 for (int j = 0; j < t; ++j) v = fma(-bu[j], u[(int64_t)j * P.m_cap + i], v);
                 r[i] = v;
-                sq = fma((double)v, (double)v, sq);
+                sq.add(v);
             }
-            rn2 = block_sum2<NT>(sq, 0.0, S.red).x;
+            rn2 = block_sum_sq<NT>(sq, SqAcc<TC>{}, S.red).x;
             ++k;
             is_true = false;
             if (P.R > 0 && k % P.R == 0) need_true = true;
@@ -425,6 +523,7 @@ batch_cta(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, in
             out.iters[order[q]] = k;
             out.reason[order[q]] = reason;
             out.rel_res[order[q]] = rel;
+            out.t_end[order[q]] = clock_ns();
         }
         __syncthreads();   // the next system may reuse every buffer
     }
@@ -455,17 +554,20 @@ __device__ __forceinline__ void consumers_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
 }
 
-// sum of one FP64 value over the NT consumer threads (all must call); every caller gets it
-template <int NT>
-__device__ __forceinline__ double consumer_sum(double v, double* red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+// sum of the consumer threads' accumulators (all NT must call), added in warp order by
+// consumer thread 0, the only thread that receives it
+template <int NT, class TC>
+__device__ __forceinline__ double consumer_sum(SqAcc<TC> a, double* red) {
+    a = warp_sum_sq(a);
     consumers_sync<NT>();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    if ((threadIdx.x & 31) == 0) a.put(red + (threadIdx.x >> 5));
     consumers_sync<NT>();
     double r = 0.0;
-#pragma unroll
-    for (int i = 0; i < NT / 32; ++i) r += red[i];
+    if (threadIdx.x == 0) {
+        SqAcc<TC> t = SqAcc<TC>::get(red);
+        for (int i = 1; i < NT / 32; ++i) t.merge(SqAcc<TC>::get(red + i));
+        r = t.value();
+    }
     return r;
 }
 
@@ -475,10 +577,31 @@ struct Ring {
     uint64_t* empty;
 };
 
+// chain-vector values at V consecutive columns (16-byte aligned shared memory)
+__device__ __forceinline__ void loadc(const double* p, double (&o)[2]) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x;
+    o[1] = v.y;
+}
+__device__ __forceinline__ void loadc(const float* p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void loadc(const float* p, float (&o)[8]) {
+    const float4 v = *reinterpret_cast<const float4*>(p), w = *reinterpret_cast<const float4*>(p + 4);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    o[4] = w.x; o[5] = w.y; o[6] = w.z; o[7] = w.w;
+}
+
 // One pass over A (consumer warps). DOT: uo = A zin * sc (returns ||uo||² in sq_u);
 // else the row weights come from uin. AXPY: zo = Aᵀ u * sc (returns ||zo||² in sq_z).
+// The sums of squares are valid in consumer thread 0 only.
 // resident: A_s is in shared memory at Ares; else chunk q of the sequence sits in ring
 // stage q % kRing. Returns false if a wait gave up.
+// Each lane keeps its columns of zin in registers for the whole pass, and each warp
+// takes two rows at a time (rows rr and rr + NW of the chunk), so that two dot products
+// and their shuffle reductions are in flight together; slices of the register row past
+// the row's end are skipped by warp-uniform branches.
 template <class TA, int NW, int JV, bool DOT, bool AXPY>
 __device__ bool fused_pass(const TA* Ares, bool resident, const Ring& ring, uint32_t& qseq, int m, int n, int ld,
                            int R, int nch, int n_cap, const typename Elem<TA>::TC* zin,
@@ -488,14 +611,23 @@ __device__ bool fused_pass(const TA* Ares, bool resident, const Ring& ring, uint
     using TC = typename Elem<TA>::TC;
     constexpr int V = Elem<TA>::V, NT = NW * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int CG = ld / V;
+    const int CG = ld / V, CGn = (n + V - 1) / V;   // vectors per stored row; per row of A
     const TC tsc = (TC)sc;
+    TC zr[JV][V];
     TC acc[JV][V];
 #pragma unroll
-    for (int j = 0; j < JV; ++j)
+    for (int j = 0; j < JV; ++j) {
+        const int cv = lane + 32 * j;
+        if (DOT && cv < CGn) {   // zin is zero from n up to its capacity, a multiple of 8
+            loadc(zin + cv * V, zr[j]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) zr[j][v] = 0;
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[j][v] = 0;
-    double su = 0.0;
+    }
+    SqAcc<TC> su;
     bool ok = true;
     for (int c = 0; c < nch; ++c) {
         const TA* chunk;
@@ -509,44 +641,73 @@ __device__ bool fused_pass(const TA* Ares, bool resident, const Ring& ring, uint
         }
         const int row0 = c * R, rows = min(R, m - row0);
         if (ok) {
-            for (int rr = warp; rr < rows; rr += NW) {
-                TC a[JV][V];
+            for (int rr = warp; rr < rows; rr += 2 * NW) {
+                const int r1 = rr + NW;
+                const bool two = r1 < rows;
+                TC a0[JV][V], a1[JV][V];
 #pragma unroll
                 for (int j = 0; j < JV; ++j) {
                     const int cv = lane + 32 * j;
+                    if (32 * j >= CG) {   // warp-uniform: this slice of the row is past its end
+#pragma unroll
+                        for (int v = 0; v < V; ++v) a0[j][v] = a1[j][v] = 0;
+                        continue;
+                    }
                     if (cv < CG) {
-                        load16(chunk + (int64_t)rr * ld + cv * V, a[j]);
+                        load16(chunk + (int64_t)rr * ld + cv * V, a0[j]);
                     } else {
 #pragma unroll
-                        for (int v = 0; v < V; ++v) a[j][v] = 0;
+                        for (int v = 0; v < V; ++v) a0[j][v] = 0;
+                    }
+                    if (two && cv < CG) {
+                        load16(chunk + (int64_t)r1 * ld + cv * V, a1[j]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) a1[j][v] = 0;
                     }
                 }
-                TC u;
+                TC u0, u1;
                 if (DOT) {
-                    TC dsum = 0;
+                    TC d0 = 0, d1 = 0, e0 = 0, e1 = 0;   // two partial sums per row
 #pragma unroll
                     for (int j = 0; j < JV; ++j) {
-                        const int cv = lane + 32 * j;
-                        if (cv < CG) {
+                        if (32 * j >= CG) break;   // warp-uniform
 #pragma unroll
-                            for (int v = 0; v < V; ++v) dsum = fma(a[j][v], zin[cv * V + v], dsum);
+                        for (int v = 0; v < V; v += 2) {
+                            d0 = fma(a0[j][v], zr[j][v], d0);
+                            e0 = fma(a0[j][v + 1], zr[j][v + 1], e0);
+                            d1 = fma(a1[j][v], zr[j][v], d1);
+                            e1 = fma(a1[j][v + 1], zr[j][v + 1], e1);
                         }
                     }
+                    d0 += e0;
+                    d1 += e1;
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-                    u = dsum * tsc;
+                    for (int o = 16; o > 0; o >>= 1) {
+                        d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+                        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+                    }
+                    u0 = d0 * tsc;
+                    u1 = two ? d1 * tsc : (TC)0;
                     if (lane == 0) {
-                        uo[row0 + rr] = u;
-                        su = fma((double)u, (double)u, su);
+                        uo[row0 + rr] = u0;
+                        su.add(u0);
+                        if (two) {
+                            uo[row0 + r1] = u1;
+                            su.add(u1);
+                        }
                     }
                 } else {
-                    u = uin[row0 + rr];
+                    u0 = uin[row0 + rr];
+                    u1 = two ? uin[row0 + r1] : (TC)0;
                 }
                 if (AXPY) {
 #pragma unroll
-                    for (int j = 0; j < JV; ++j)
+                    for (int j = 0; j < JV; ++j) {
+                        if (32 * j >= CG) break;   // warp-uniform
 #pragma unroll
-                        for (int v = 0; v < V; ++v) acc[j][v] = fma(a[j][v], u, acc[j][v]);
+                        for (int v = 0; v < V; ++v) acc[j][v] = fma(a1[j][v], u1, fma(a0[j][v], u0, acc[j][v]));
+                    }
                 }
             }
         }
@@ -556,13 +717,13 @@ __device__ bool fused_pass(const TA* Ares, bool resident, const Ring& ring, uint
             ++qseq;
         }
     }
-    double sz = 0.0;
+    SqAcc<TC> sz;
     if (AXPY) {
         // zo = (sum over warps of the accumulators) * sc, in warp order (deterministic)
 #pragma unroll
         for (int j = 0; j < JV; ++j) {
             const int cv = lane + 32 * j;
-            if (cv < CG) {
+            if (cv < CGn) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) part[(int64_t)warp * n_cap + cv * V + v] = acc[j][v];
             }
@@ -573,7 +734,7 @@ __device__ bool fused_pass(const TA* Ares, bool resident, const Ring& ring, uint
             for (int w = 0; w < NW; ++w) t += part[(int64_t)w * n_cap + col];
             t *= tsc;
             zo[col] = t;
-            sz = fma((double)t, (double)t, sz);
+            sz.add(t);
         }
     }
     sq_u = DOT ? consumer_sum<NT>(su, red) : 0.0;
@@ -581,7 +742,290 @@ __device__ bool fused_pass(const TA* Ares, bool resident, const Ring& ring, uint
     return ok;
 }
 
-template <class TA, int NW, int JV>
+// ------------------------------------------------------------------ BF16 tensor-core pass
+//
+// The same pass with the products on the tensor cores (mma.sync m16n8k16, BF16 operands,
+// FP32 accumulation). A 16 x 16 tile of A_s serves both products:
+//  * u = A z: the tile is the MMA's A operand (ldmatrix from the staged rows) and z the
+//    B operand, carried exactly as three BF16 terms z = z_hi + z_lo + z_lo2 in B's
+//    columns 0..2 (an FP32 value has 24 significant bits, a BF16 term 8), so the
+//    FP32 chain loses nothing to the BF16 operand;
+//  * z' = Aᵀ u: the tile transposed in registers (movmatrix) is the A operand of a
+//    second MMA whose B operand is u split the same way, accumulated over the rows.
+// Work split: the row's 16-column tiles are divided among WG column groups of warps
+// (WG a power of two, at most 8 tiles per group); the NW / WG warps of a group take
+// SB consecutive 16-row blocks each per round. A round: every warp loads its tiles and
+// forms its part of A z for its rows; the parts meet in shared memory (exch, double
+// buffered by round parity); after one consumer barrier every warp sums them in group
+// order and applies the transposed tiles it still holds in registers to the finished u.
+// The stored row length ld is 8 (mod 16) elements, so the eight rows an ldmatrix reads
+// fall in distinct bank groups.
+
+constexpr int kMmaStageBytes = 40 * 1024;
+
+struct MmaGeo {
+    int KT;      // 16-column tiles of a row
+    int WG;      // column groups of warps
+    int KG;      // tiles per group (<= the pass's template bound)
+    int KGT;     // template bound: 1, 2, 4 or 8
+    int NL;      // warps per group (row lanes)
+    int SB;      // row blocks per warp and round (8 / KGT)
+    int R;       // rows per chunk (multiple of 16)
+};
+
+__host__ __device__ inline MmaGeo mma_geo(int n, int ld, int NW) {
+    MmaGeo g{};
+    g.KT = (n + 15) / 16;
+    if (g.KT <= 8) {
+        g.WG = 1;
+        g.KGT = g.KT <= 1 ? 1 : g.KT <= 2 ? 2 : g.KT <= 4 ? 4 : 8;
+    } else {
+        g.WG = 2;
+        while (g.WG * 8 < g.KT) g.WG *= 2;
+        g.KGT = 8;
+    }
+    g.KG = (g.KT + g.WG - 1) / g.WG;
+    g.NL = NW / g.WG;
+    g.SB = 8 / g.KGT;
+    const int row_bytes = ld * 2;
+    const int round_rows = 16 * g.NL * g.SB;
+    if (round_rows * row_bytes <= kMmaStageBytes) {
+        g.R = (kMmaStageBytes / (round_rows * row_bytes)) * round_rows;
+    } else {
+        g.R = (kMmaStageBytes / (16 * row_bytes)) * 16;
+    }
+    return g;
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&a)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ uint32_t movmatrix_t(uint32_t a) {
+    uint32_t d;
+    asm("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(d) : "r"(a));
+    return d;
+}
+
+// term s (0, 1, 2) of the split v = hi + lo + lo2 into BF16 values, as raw bits; 0 for s > 2
+__device__ __forceinline__ uint32_t split_term(float v, int s) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const float r1 = __fsub_rn(v, __bfloat162float(h));            // exact
+    const __nv_bfloat16 l = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 l2 = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(l)));
+    const __nv_bfloat16 t = s == 0 ? h : s == 1 ? l : l2;
+    return s > 2 ? 0u : (uint32_t)__bfloat16_as_ushort(t);
+}
+
+__device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) { return lo | (hi << 16); }
+
+// Same contract as fused_pass, for BF16 storage; KGT = G.KGT.
+template <int NW, int KGT, bool DOT, bool AXPY>
+__device__ bool mma_pass(const __nv_bfloat16* Ares, bool resident, const Ring& ring, uint32_t& qseq, int m, int n,
+                         int ld, const MmaGeo& G, int nch, int n_cap, const float* zin, const float* uin, float* uo,
+                         float* zo, float* part, float* exch, double sc, double* red, double& sq_u, double& sq_z) {
+    constexpr int NT = NW * 32, SB = 8 / KGT;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = warp % G.WG, l = warp / G.WG;
+    const int sp = lane >> 2, q4 = lane & 3;      // B column (split term) / C row, and pair index
+    const int RR = 16 * G.NL * SB;                // rows of a round
+    const float tsc = (float)sc;
+    // B fragments of z for this warp's tiles: rows (columns of A) 2 q4 + {0, 1} and + 8
+    uint32_t bz[KGT][2];
+#pragma unroll
+    for (int kk = 0; kk < KGT; ++kk) {
+        const int c0 = (g * G.KG + kk) * 16 + 2 * q4;
+        const bool tile = DOT && kk < G.KG;
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int c = c0 + (e & 1) + (e >> 1) * 8;
+            v[e] = tile && c < n ? zin[c] : 0.0f;
+        }
+        bz[kk][0] = pack2(split_term(v[0], sp), split_term(v[1], sp));
+        bz[kk][1] = pack2(split_term(v[2], sp), split_term(v[3], sp));
+    }
+    float acc[KGT][4];
+#pragma unroll
+    for (int kk = 0; kk < KGT; ++kk)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[kk][e] = 0.0f;
+    SqAcc<float> su;
+    bool ok = true;
+    int buf = 0;
+    // this lane's ldmatrix row and column offsets within a 16 x 16 tile
+    const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8, lcol = (lane >> 4) * 8;
+    for (int c = 0; c < nch; ++c) {
+        const __nv_bfloat16* chunk;
+        int k = 0;
+        if (resident) {
+            chunk = Ares + (int64_t)c * G.R * ld;
+        } else {
+            k = (int)(qseq % kRing);
+            if (ok) ok = mbar_wait_bounded(&ring.full[k], (qseq / kRing) & 1u);
+            chunk = reinterpret_cast<const __nv_bfloat16*>(ring.area + (size_t)k * kMmaStageBytes);
+        }
+        const int row0 = c * G.R, rows = min(G.R, m - row0);
+        const int RBc = (rows + 15) / 16;
+        // every warp runs every round (the rounds hold consumer barriers), loading nothing
+        // once a wait has given up
+        const int rounds = (RBc + G.NL * SB - 1) / (G.NL * SB);
+        const uint32_t cbase = smem_addr(chunk);
+        for (int rd = 0; rd < rounds; ++rd) {
+            uint32_t af[SB][KGT][4];
+            float cd[SB][4];
+#pragma unroll
+            for (int sb = 0; sb < SB; ++sb) {
+                const int rb = (rd * G.NL + l) * SB + sb;
+                const bool lo_ok = rb * 16 + sp < rows, hi_ok = rb * 16 + sp + 8 < rows;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) cd[sb][e] = 0.0f;
+#pragma unroll
+                for (int kk = 0; kk < KGT; ++kk) {
+                    const int kt = g * G.KG + kk;
+                    if (ok && rb < RBc && kk < G.KG && kt < G.KT) {
+                        ldmatrix_x4(af[sb][kk],
+                                    cbase + (uint32_t)(((rb * 16 + lrow) * ld + kt * 16 + lcol) * 2));
+                        if (!lo_ok) { af[sb][kk][0] = 0u; af[sb][kk][2] = 0u; }   // rows past the chunk
+                        if (!hi_ok) { af[sb][kk][1] = 0u; af[sb][kk][3] = 0u; }
+                        if (DOT) mma_bf16(cd[sb], af[sb][kk], bz[kk][0], bz[kk][1]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) af[sb][kk][e] = 0u;
+                    }
+                }
+            }
+            if (!resident && rd == rounds - 1) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ring.empty[k]);   // the chunk's tiles are in registers
+            }
+            float* ex = exch + (size_t)buf * G.WG * RR;
+            if (DOT) {
+                // this group's part of A z for each row: (hi + lo) + lo2 columns of C
+#pragma unroll
+                for (int sb = 0; sb < SB; ++sb) {
+                    float v0 = cd[sb][0] + cd[sb][1], v1 = cd[sb][2] + cd[sb][3];
+                    v0 += __shfl_down_sync(0xffffffffu, v0, 1);
+                    v1 += __shfl_down_sync(0xffffffffu, v1, 1);
+                    if (q4 == 0) {
+                        ex[g * RR + (l * SB + sb) * 16 + sp] = v0;
+                        ex[g * RR + (l * SB + sb) * 16 + sp + 8] = v1;
+                    }
+                }
+                consumers_sync<NT>();
+            }
+#pragma unroll
+            for (int sb = 0; sb < SB; ++sb) {
+                const int rb = (rd * G.NL + l) * SB + sb;
+                if (rb >= RBc) continue;
+                // u at rows 2 q4 + {0, 1} and + 8 of the block (the B fragment's K rows)
+                float uv[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int kr = 2 * q4 + (e & 1) + (e >> 1) * 8;
+                    const int row = rb * 16 + kr;
+                    float u = 0.0f;
+                    if (row < rows) {
+                        if (DOT) {
+                            const int idx = (l * SB + sb) * 16 + kr;
+                            for (int gg = 0; gg < G.WG; ++gg) u += ex[gg * RR + idx];
+                            u *= tsc;
+                            if (g == 0 && sp == 0) {
+                                uo[row0 + row] = u;
+                                su.add(u);
+                            }
+                        } else {
+                            u = uin[row0 + row];
+                        }
+                    }
+                    uv[e] = u;
+                }
+                if (AXPY) {
+                    const uint32_t b0 = pack2(split_term(uv[0], sp), split_term(uv[1], sp));
+                    const uint32_t b1 = pack2(split_term(uv[2], sp), split_term(uv[3], sp));
+#pragma unroll
+                    for (int kk = 0; kk < KGT; ++kk) {
+                        const int kt = g * G.KG + kk;
+                        if (kk < G.KG && kt < G.KT) {
+                            const uint32_t at[4] = {movmatrix_t(af[sb][kk][0]), movmatrix_t(af[sb][kk][2]),
+                                                    movmatrix_t(af[sb][kk][1]), movmatrix_t(af[sb][kk][3])};
+                            mma_bf16(acc[kk], at, b0, b1);
+                        }
+                    }
+                }
+            }
+            buf ^= 1;
+        }
+        if (!resident) ++qseq;
+    }
+    SqAcc<float> sz;
+    if (AXPY) {
+        // this warp's columns: (hi + lo) + lo2 columns of the accumulators, per row lane
+#pragma unroll
+        for (int kk = 0; kk < KGT; ++kk) {
+            float v0 = acc[kk][0] + acc[kk][1], v1 = acc[kk][2] + acc[kk][3];
+            v0 += __shfl_down_sync(0xffffffffu, v0, 1);
+            v1 += __shfl_down_sync(0xffffffffu, v1, 1);
+            const int kt = g * G.KG + kk;
+            if (q4 == 0 && kk < G.KG && kt < G.KT) {
+                const int col = kt * 16 + sp;
+                if (col < n) part[(int64_t)l * n_cap + col] = v0;
+                if (col + 8 < n) part[(int64_t)l * n_cap + col + 8] = v1;
+            }
+        }
+        consumers_sync<NT>();
+        for (int col = threadIdx.x; col < n; col += NT) {
+            float t = 0.0f;
+            for (int w = 0; w < G.NL; ++w) t += part[(int64_t)w * n_cap + col];
+            t *= tsc;
+            zo[col] = t;
+            sz.add(t);
+        }
+    }
+    sq_u = DOT ? consumer_sum<NT>(su, red) : 0.0;
+    sq_z = AXPY ? consumer_sum<NT>(sz, red) : 0.0;
+    return ok;
+}
+
+// the three kinds of pass of a chain step, on CUDA cores or (BF16, MMA) on the tensor cores
+template <class TA, int NW, int JV, bool MMA, bool DOT, bool AXPY>
+__device__ __forceinline__ bool chain_pass(const TA* Ares, bool resident, const Ring& ring, uint32_t& qseq, int m,
+                                           int n, int ld, int R, const MmaGeo& G, int nch, int n_cap,
+                                           const typename Elem<TA>::TC* zin, const typename Elem<TA>::TC* uin,
+                                           typename Elem<TA>::TC* uo, typename Elem<TA>::TC* zo,
+                                           typename Elem<TA>::TC* part, float* exch, double sc, double* red,
+                                           double& sq_u, double& sq_z) {
+    if constexpr (MMA) {
+        switch (G.KGT) {
+        case 1:
+            return mma_pass<NW, 1, DOT, AXPY>(Ares, resident, ring, qseq, m, n, ld, G, nch, n_cap, zin, uin, uo, zo,
+                                              part, exch, sc, red, sq_u, sq_z);
+        case 2:
+            return mma_pass<NW, 2, DOT, AXPY>(Ares, resident, ring, qseq, m, n, ld, G, nch, n_cap, zin, uin, uo, zo,
+                                              part, exch, sc, red, sq_u, sq_z);
+        case 4:
+            return mma_pass<NW, 4, DOT, AXPY>(Ares, resident, ring, qseq, m, n, ld, G, nch, n_cap, zin, uin, uo, zo,
+                                              part, exch, sc, red, sq_u, sq_z);
+        default:
+            return mma_pass<NW, 8, DOT, AXPY>(Ares, resident, ring, qseq, m, n, ld, G, nch, n_cap, zin, uin, uo, zo,
+                                              part, exch, sc, red, sq_u, sq_z);
+        }
+    } else {
+        return fused_pass<TA, NW, JV, DOT, AXPY>(Ares, resident, ring, qseq, m, n, ld, R, nch, n_cap, zin, uin, uo,
+                                                 zo, part, sc, red, sq_u, sq_z);
+    }
+}
+
+template <class TA, int NW, int JV, bool MMA>
 __global__ void __launch_bounds__((NW + 1) * 32, 1)
 batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, int count,
             const TA* __restrict__ alo, const double* __restrict__ a64, const double* __restrict__ bvec,
@@ -600,6 +1044,8 @@ batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
     TC* z = u + (int64_t)P.t_max * P.m_cap;          // t_max x n_cap
     TC* dx = z + (int64_t)P.t_max * P.n_cap;         // n_cap
     TC* part = dx + P.n_cap;                         // NW x n_cap
+    float* exch = reinterpret_cast<float*>(part + (int64_t)NW * P.n_cap);   // MMA: 2 x 16 NW x 8
+    constexpr int kStage = MMA ? kMmaStageBytes : kChunkBytes;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool producer = warp == NW;
     const Ring ring{smem_raw, full, empty};
@@ -619,8 +1065,12 @@ batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
         __syncthreads();
         const int q = S.sys;
         if (q >= count) break;
+        if (tid == 0) out.t_beg[order[q]] = clock_ns();
         if (fail_s) {   // this block stops; the system it took is reported as timed out
-            if (tid == 0) out.reason[order[q]] = TACTA_REASON_TIMEOUT;
+            if (tid == 0) {
+                out.reason[order[q]] = TACTA_REASON_TIMEOUT;
+                out.t_end[order[q]] = clock_ns();
+            }
             break;
         }
         const SysDesc d = sys[order[q]];
@@ -630,9 +1080,11 @@ batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
         const double* A64 = a64 + d.a64;
         const TA* Ag = alo + d.a_lo;
         const int64_t row_bytes = (int64_t)ld * (int64_t)sizeof(TA);
-        const int R = (int)max((int64_t)1, (int64_t)kChunkBytes / row_bytes);
+        const MmaGeo G = MMA ? mma_geo(n, ld, NW) : MmaGeo{};
+        const int R = MMA ? G.R : (int)max((int64_t)1, (int64_t)kChunkBytes / row_bytes);
         const int nch = (m + R - 1) / R;
-        const bool resident = (int64_t)m * row_bytes <= P.area_bytes;
+        // (the tensor-core pass reads whole 16-row blocks)
+        const bool resident = (int64_t)(MMA ? (m + 15) / 16 * 16 : m) * row_bytes <= P.area_bytes;
         const TA* Ares = reinterpret_cast<const TA*>(smem_raw);
         if (resident) {   // one copy of A_s into the area
             if (tid == NT) {
@@ -657,8 +1109,8 @@ batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
         const double bn2 = block_sum2<NB>(bb, 0.0, S.red).x;
         double nrm_thr = 0.0;
         if (P.tol_n2 > 0.0 && bn2 > 0.0) {   // ||Aᵀb||² (from global memory, the slow path)
-            const double mt = prod_t<TA, NB>(Ag, m, n, ld, r, z, part, 1.0);
-            nrm_thr = P.tol_n2 * block_sum2<NB>(mt, 0.0, S.red).x;
+            const SqAcc<TC> mt = prod_t<TA, NB>(Ag, m, n, ld, r, z, part, 1.0);
+            nrm_thr = P.tol_n2 * block_sum_sq<NB>(mt, SqAcc<TC>{}, S.red).x;
             for (int c = tid; c < n; c += NB) z[c] = 0;
         }
         double rn2 = bn2;
@@ -704,7 +1156,7 @@ batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
                             const int row0 = c * R, rows = min(R, m - row0);
                             const uint32_t bytes = (uint32_t)((int64_t)rows * row_bytes);
                             mbar_expect_tx(&full[kk], bytes);
-                            bulk_g2s(smem_raw + (size_t)kk * kChunkBytes, Ag + (int64_t)row0 * ld, bytes, &full[kk]);
+                            bulk_g2s(smem_raw + (size_t)kk * kStage, Ag + (int64_t)row0 * ld, bytes, &full[kk]);
                             ++qseq;
                         }
                     }
@@ -713,36 +1165,44 @@ batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
             } else {
                 // z_1 = Aᵀ r / s ; then u_i = A z_i / s with z_{i+1} = Aᵀ u_i / s ; u_t alone
                 double pu = 0.0, pz = 0.0;
-                bool ok = fused_pass<TA, NW, JV, false, true>(Ares, resident, ring, qseq, m, n, ld, R, nch, P.n_cap,
-                                                             nullptr, r, nullptr, z, part, d.inv_s, cred, pu, pz);
+                bool ok = chain_pass<TA, NW, JV, MMA, false, true>(Ares, resident, ring, qseq, m, n, ld, R, G, nch,
+                                                                  P.n_cap, nullptr, r, nullptr, z, part, exch,
+                                                                  d.inv_s, cred, pu, pz);
                 if (tid == 0) S.phi[1] = pz;
                 for (int i = 1; i <= t && ok; ++i) {
                     TC* zi = z + (int64_t)(i - 1) * P.n_cap;
                     TC* ui = u + (int64_t)(i - 1) * P.m_cap;
                     consumers_sync<NT>();   // z_i complete
                     if (i < t) {
-                        ok = fused_pass<TA, NW, JV, true, true>(Ares, resident, ring, qseq, m, n, ld, R, nch, P.n_cap,
-                                                               zi, nullptr, ui, zi + P.n_cap, part, d.inv_s, cred, pu,
-                                                               pz);
+                        ok = chain_pass<TA, NW, JV, MMA, true, true>(Ares, resident, ring, qseq, m, n, ld, R, G, nch,
+                                                                    P.n_cap, zi, nullptr, ui, zi + P.n_cap, part,
+                                                                    exch, d.inv_s, cred, pu, pz);
                         if (tid == 0) { S.phi[2 * i] = pu; S.phi[2 * i + 1] = pz; }
                     } else {
-                        ok = fused_pass<TA, NW, JV, true, false>(Ares, resident, ring, qseq, m, n, ld, R, nch,
-                                                                P.n_cap, zi, nullptr, ui, nullptr, part, d.inv_s,
-                                                                cred, pu, pz);
+                        ok = chain_pass<TA, NW, JV, MMA, true, false>(Ares, resident, ring, qseq, m, n, ld, R, G,
+                                                                     nch, P.n_cap, zi, nullptr, ui, nullptr, part,
+                                                                     exch, d.inv_s, cred, pu, pz);
                         if (tid == 0) S.phi[2 * i] = pu;
                     }
                 }
                 if (!ok) fail_s = 1;
-                if (tid == 0) {
+                if (warp == 0) {   // the auxiliary solve by one warp (bit for bit the serial solve)
+                    __syncwarp();
                     int st = 0;
                     for (int i = 1; i <= 2 * t; ++i)
                         if (!finite_d(S.phi[i])) st = TACTA_REASON_NONFINITE;
                     if (st == 0 && S.phi[1] * d.s * d.s <= nrm_thr) st = TACTA_REASON_NORMAL;
                     if (st == 0) {
-                        S.rank = hankel_solve_dev(S.phi, t, P.pivot_tol, S.beta);
-                        if (S.rank == 0) st = TACTA_REASON_BREAKDOWN;
+                        const int rank = hankel_solve_warp(S.phi, t, P.pivot_tol, S.beta);
+                        if (rank == 0) st = TACTA_REASON_BREAKDOWN;
+                        __syncwarp();
+                        if (lane < t) {   // the update's coefficients, converted once
+                            TC* cf = reinterpret_cast<TC*>(S.coef);
+                            cf[lane] = (TC)S.beta[lane];
+                            cf[kTMax + lane] = (TC)(S.beta[lane] * d.inv_s);
+                        }
                     }
-                    S.stop = st;
+                    if (lane == 0) S.stop = st;
                 }
             }
             __syncthreads();
@@ -750,22 +1210,22 @@ batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
             if (S.stop) { reason = S.stop; break; }
             TC bz[kTMax], bu[kTMax];
             for (int j = 0; j < t; ++j) {
-                bu[j] = (TC)S.beta[j];
-                bz[j] = (TC)(S.beta[j] * d.inv_s);
+                bu[j] = reinterpret_cast<const TC*>(S.coef)[j];
+                bz[j] = reinterpret_cast<const TC*>(S.coef)[kTMax + j];
             }
             for (int c = tid; c < n; c += NB) {
                 TC v = dx[c];
                 for (int j = 0; j < t; ++j) v = fma(bz[j], z[(int64_t)j * P.n_cap + c], v);
                 dx[c] = v;
             }
-            double sq = 0.0;
+            SqAcc<TC> sq;
             for (int i = tid; i < m; i += NB) {
                 TC v = r[i];
                 for (int j = 0; j < t; ++j) v = fma(-bu[j], u[(int64_t)j * P.m_cap + i], v);
                 r[i] = v;
-                sq = fma((double)v, (double)v, sq);
+                sq.add(v);
             }
-            rn2 = block_sum2<NB>(sq, 0.0, S.red).x;
+            rn2 = block_sum_sq<NB>(sq, SqAcc<TC>{}, S.red).x;
             ++k;
             is_true = false;
             if (P.R > 0 && k % P.R == 0) need_true = true;
@@ -785,6 +1245,7 @@ batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
             out.iters[order[q]] = k;
             out.reason[order[q]] = reason;
             out.rel_res[order[q]] = rel;
+            out.t_end[order[q]] = clock_ns();
         }
         __syncthreads();
     }
@@ -851,11 +1312,16 @@ struct Config {
     int nt;            // threads per block (the streamed kernel: consumers, plus one producer warp)
     int per_sm;        // resident blocks per SM
     bool streamed;     // batch_cta_s (fused passes, bulk-copy ring) instead of batch_cta
+    bool mma;          // batch_cta_s with the BF16 tensor-core passes (BF16 storage only)
 };
-constexpr Config kConfigs[] = {{128, 2, false}, {128, 4, false}, {256, 1, false}, {256, 2, false}, {512, 1, false},
-                               {256, 1, true}};
+constexpr Config kConfigs[] = {{128, 2, false, false}, {128, 4, false, false}, {256, 1, false, false},
+                               {256, 2, false, false}, {512, 1, false, false}, {256, 1, true, false},
+                               {256, 1, true, true}};
 constexpr int kDefaultConfig = 3;
-constexpr int kStreamNW = 8, kStreamJV = 8;
+constexpr int kStreamNW = 8;
+// vectors of a row each lane holds in registers (FP64 2, FP32 4, BF16 8 values each):
+// rows of up to 512, 1024 and 1024 columns
+template <class TA> constexpr int stream_jv() { return std::is_same_v<TA, __nv_bfloat16> ? 4 : 8; }
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
 template <class TA>
@@ -874,7 +1340,9 @@ void set_attrs(cudaError_t& attr) {
         if (attr == cudaSuccess)
             attr = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmemMax);
     };
-    set((const void*)batch_cta_s<TA, kStreamNW, kStreamJV>);
+    set((const void*)batch_cta_s<TA, kStreamNW, stream_jv<TA>(), false>);
+    if constexpr (std::is_same_v<TA, __nv_bfloat16>)
+        set((const void*)batch_cta_s<TA, kStreamNW, stream_jv<TA>(), true>);
     set((const void*)batch_cta<TA, 128, 2>);
     set((const void*)batch_cta<TA, 128, 4>);
     set((const void*)batch_cta<TA, 256, 1>);
@@ -900,8 +1368,16 @@ cudaError_t launch_cfg(int cfg, cudaStream_t s, int grid, size_t smem, const Sys
     const TA* a = reinterpret_cast<const TA*>(alo);
     switch (cfg) {
     case 5:
-        batch_cta_s<TA, kStreamNW, kStreamJV><<<grid, kStreamNW * 32 + 32, smem, s>>>(sys, order, count, a, a64, b,
-                                                                                    x, o, queue, P, fail_flag);
+        batch_cta_s<TA, kStreamNW, stream_jv<TA>(), false><<<grid, kStreamNW * 32 + 32, smem, s>>>(
+            sys, order, count, a, a64, b, x, o, queue, P, fail_flag);
+        break;
+    case 6:
+        if constexpr (std::is_same_v<TA, __nv_bfloat16>) {
+            batch_cta_s<TA, kStreamNW, stream_jv<TA>(), true><<<grid, kStreamNW * 32 + 32, smem, s>>>(
+                sys, order, count, a, a64, b, x, o, queue, P, fail_flag);
+        } else {
+            return cudaErrorInvalidConfiguration;   // make_params admits it for BF16 storage only
+        }
         break;
     case 0: batch_cta<TA, 128, 2><<<grid, 128, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
     case 1: batch_cta<TA, 128, 4><<<grid, 128, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
@@ -935,6 +1411,7 @@ struct tacta_batch_s {
     int32_t* reason = nullptr;
     double* rel = nullptr;
     int32_t* queue = nullptr;
+    int64_t* stamps = nullptr;     // 2 x count: per-system begin and end clocks of the last solve
     int config = -1;               // index into kConfigs (-1: default)
     cudaGraphExec_t graph = nullptr;
     int graph_key = -1;
@@ -950,6 +1427,7 @@ void free_batch(tacta_batch_s* B) {
     if (B->graph) cudaGraphExecDestroy(B->graph);
     cudaFree(B->sys); cudaFree(B->order); cudaFree(B->a64); cudaFree(B->alo); cudaFree(B->b); cudaFree(B->x);
     cudaFree(B->iters); cudaFree(B->reason); cudaFree(B->rel); cudaFree(B->queue);
+    cudaFree(B->stamps);
     delete B;
 }
 
@@ -972,7 +1450,7 @@ bool make_params(const tacta_batch_s* B, const tacta_options& o, int cfg, BatchP
     P.R = o.recompute_every;
     P.t_max = o.t_max;
     P.cycle = o.cycle;
-    P.m_cap = B->m_max;
+    P.m_cap = (B->m_max + 7) & ~7;
     P.n_cap = (B->n_max + 7) & ~7;
     const int V = B->storage == TACTA_BATCH_FP64 ? 2 : B->storage == TACTA_BATCH_FP32 ? 4 : 8;
     const int tc = B->storage == TACTA_BATCH_FP64 ? 8 : 4;
@@ -987,11 +1465,16 @@ bool make_params(const tacta_batch_s* B, const tacta_options& o, int cfg, BatchP
         P.area_bytes = 0;
         *smem_out = (size_t)(((P.a_cap * (int64_t)elem_size(B->storage) + 15) & ~15) + vb);
     } else {
-        if (P.n_cap / V > 32 * kStreamJV) return false;          // row slices must fit the registers
+        if (C.mma && (B->storage != TACTA_BATCH_BF16 || B->n_max > 1024)) return false;
+        const int jv = B->storage == TACTA_BATCH_FP64 ? stream_jv<double>() : B->storage == TACTA_BATCH_FP32
+                                                                              ? stream_jv<float>()
+                                                                              : stream_jv<__nv_bfloat16>();
+        if (P.n_cap / V > 32 * jv) return false;                 // row slices must fit the registers
         const int64_t part = std::max<int64_t>((int64_t)kStreamNW * P.n_cap, (int64_t)(C.nt + 32) * V);
-        const int64_t vb = (chain + part) * tc;
+        const int64_t exch = C.mma ? 2 * 16 * kStreamNW * 8 : 0;
+        const int64_t vb = (chain + part + exch) * tc;
         const int64_t area = ((per_block - vb) / 16) * 16;
-        if (area < (int64_t)kRing * kChunkBytes) return false;
+        if (area < (int64_t)kRing * (C.mma ? kMmaStageBytes : kChunkBytes)) return false;
         P.area_bytes = area;
         P.a_cap = 0;
         *smem_out = (size_t)(area + vb);
@@ -1007,7 +1490,7 @@ cudaError_t launch_batch(tacta_batch_s* B, cudaStream_t s, const tacta_options& 
     BatchParams P{};
     if (!make_params(B, o, cfg, &P, &smem)) return cudaErrorInvalidConfiguration;
     const int grid = std::max(1, std::min(B->count, B->sms * C.per_sm));
-    BatchOut out{B->iters, B->reason, B->rel};
+    BatchOut out{B->iters, B->reason, B->rel, B->stamps, B->stamps + B->count};
     cudaError_t e = cudaMemsetAsync(B->queue, 0, 2 * sizeof(int32_t), s);   // queue head, timeout flag
     if (e != cudaSuccess) return e;
     switch (B->storage) {
@@ -1078,7 +1561,8 @@ extern "C" tacta_status tacta_batch_create(int32_t count, const int32_t* m, cons
         std::memset(&q, 0, sizeof(q));
         q.m = m[s];
         q.n = n[s];
-        q.ld = (n[s] + 7) & ~7;
+        // BF16 rows: 16-column tiles plus 8, so that ldmatrix's eight rows hit distinct banks
+        q.ld = storage == TACTA_BATCH_BF16 ? ((n[s] + 15) & ~15) + 8 : (n[s] + 7) & ~7;
         q.a64 = a64;
         q.a_lo = alo;
         q.b_off = bo;
@@ -1120,6 +1604,8 @@ extern "C" tacta_status tacta_batch_create(int32_t count, const int32_t* m, cons
     BCHK(cudaMalloc(&B->reason, sizeof(int32_t) * std::max<int32_t>(count, 1)));
     BCHK(cudaMalloc(&B->rel, sizeof(double) * std::max<int32_t>(count, 1)));
     BCHK(cudaMalloc(&B->queue, 2 * sizeof(int32_t)));
+    BCHK(cudaMalloc(&B->stamps, 2 * sizeof(int64_t) * std::max<int32_t>(count, 1)));
+    BCHK(cudaMemsetAsync(B->stamps, 0, 2 * sizeof(int64_t) * std::max<int32_t>(count, 1), s));
     if (count > 0) {
         // largest systems first: the queue's tail is then made of short jobs
         std::vector<int32_t> ord((size_t)count);
@@ -1161,6 +1647,20 @@ extern "C" tacta_status tacta_batch_set_config(tacta_batch B, int32_t config) {
 }
 
 extern "C" int32_t tacta_batch_num_configs(void) { return kNumConfigs; }
+
+extern "C" int32_t tacta_batch_config_tensor_cores(int32_t config) {
+    return config >= 0 && config < kNumConfigs && kConfigs[config].mma ? 1 : 0;
+}
+
+extern "C" tacta_status tacta_batch_timeline(tacta_batch B, int64_t* t_begin_ns, int64_t* t_end_ns) {
+    g_batch_err.clear();
+    if (!B || !t_begin_ns || !t_end_ns) { g_batch_err = "NULL argument"; return TACTA_ERR_INVALID; }
+    BTRY(cudaSetDevice(B->device));
+    if (B->count == 0) return TACTA_OK;
+    BTRY(cudaMemcpy(t_begin_ns, B->stamps, sizeof(int64_t) * B->count, cudaMemcpyDefault));
+    BTRY(cudaMemcpy(t_end_ns, B->stamps + B->count, sizeof(int64_t) * B->count, cudaMemcpyDefault));
+    return TACTA_OK;
+}
 
 extern "C" tacta_status tacta_batch_config_shape(int32_t config, int32_t* threads, int32_t* blocks_per_sm) {
     if (config < 0 || config >= kNumConfigs || !threads || !blocks_per_sm) return TACTA_ERR_INVALID;

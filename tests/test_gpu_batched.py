@@ -54,6 +54,7 @@ def problem(A, b):
 
 
 STREAMED = 5   # launch configuration of the fused-pass kernel with the bulk-copy ring
+TENSOR = 6     # the same kernel with the products on the tensor cores (BF16 storage)
 
 
 def run(tacta, mats, bs, storage, config=None, **opts):
@@ -82,7 +83,7 @@ def test_fp64_fixed_trajectories_match_oracle(tacta, config):
         assert tacta.REASON[int(reason[s])] == "MAXITER"
 
 
-@pytest.mark.parametrize("config", [None, STREAMED])
+@pytest.mark.parametrize("config", [None, STREAMED, TENSOR])
 @pytest.mark.parametrize("storage,tol,xtol", [("BATCH_FP64", 1e-10, 1e-8), ("BATCH_FP32", 1e-8, 1e-6),
                                               ("BATCH_BF16", 1e-8, 3e-2)])
 def test_to_tolerance_min_norm(tacta, storage, tol, xtol, config):
@@ -90,8 +91,10 @@ def test_to_tolerance_min_norm(tacta, storage, tol, xtol, config):
     the host-recomputed FP64 residual meets tol, the reported one equals it, and x is the
     minimum-norm solution within cond(A) times xtol: about 100 tol for FP64, and for the
     low-precision copies 10 times their unit roundoff (2^-24, 2^-9) plus the tolerance."""
+    if config == TENSOR and storage != "BATCH_BF16":
+        pytest.skip("the tensor-core passes read BF16 storage only")
     mats, bs, lr = small_batch(2, 48, aspect=(1.4, 2.0))
-    if config == STREAMED:   # add systems larger than the shared-memory area: they stream
+    if config in (STREAMED, TENSOR):   # add systems larger than the shared-memory area: they stream
         m2, b2, _ = small_batch(6, 12, m_range=(220, 300), aspect=(1.4, 1.8))
         mats, bs = mats + m2, bs + b2
     xs, iters, rel, reason = run(tacta, mats, bs, getattr(tacta, storage), config=config, tol=tol,
@@ -145,13 +148,66 @@ def test_graph_replay_and_configs_agree(tacta):
     x2, it2, r2, _ = B.cta(b, use_graph=1, **opts)
     x3, it3, r3, _ = B.cta(b, use_graph=0, **opts)
     assert np.array_equal(x1, x2) and np.array_equal(x1, x3) and np.array_equal(it1, it3)
+    tc = tacta.Batch.tensor_core_configs()
+    assert tc == [TENSOR]
     for c in range(len(tacta.Batch.configs())):
         B.set_config(c)
+        if c in tc:   # BF16 storage only: refused for this FP32 batch
+            with pytest.raises(tacta.TactaError):
+                B.cta(b, **opts)
+            continue
         _, _, rc, reason = B.cta(b, **opts)
         assert all(tacta.REASON[int(r)] == "RESIDUAL" for r in reason) and np.all(rc <= 1e-8 * (1 + 1e-6))
     best, ms = B.tune(b, **opts)
-    assert 0 <= best < len(tacta.Batch.configs()) and ms > 0
+    assert 0 <= best < len(tacta.Batch.configs()) and best not in tc and ms > 0
     B.close()
+
+
+def bf16_round(a):
+    """Round-to-nearest-even to BF16 (8 significant bits) of float64 values, as float64."""
+    m, e = np.frexp(a)
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+# shapes that reach every work split of the tensor-core pass: 16-column tiles per row
+# 1, 2, 3-4, 5-8 and 9-64 (one to eight column groups of warps), rows not a multiple of
+# 16, several row chunks, and systems that stream through the ring (above ~100 KB)
+TC_SHAPES = [(5, 9), (16, 16), (17, 30), (40, 33), (33, 64), (70, 100), (100, 128), (130, 150), (64, 250),
+             (200, 520), (600, 40), (300, 420), (257, 1024), (150, 600)]
+
+
+@pytest.mark.parametrize("config", [STREAMED, TENSOR])
+def test_bf16_two_steps_match_oracle_on_stored_matrix(tacta, config):
+    """Two steps (t = 1, 2: every kind of pass -- Aᵀr alone, A z_i with Aᵀu_i, A z_t alone)
+    with BF16 storage on CUDA cores and on the tensor cores, against the oracle run in FP64
+    on the BF16-rounded matrix. The FP32 chain differs from it by FP32 rounding (about
+    1e-7 relative per product, amplified by the 2 x 2 auxiliary solve), so x agrees to
+    1e-4; a lost operand term (z or u carried in one or two BF16 terms, 2^-9 / 2^-17) or a
+    misplaced fragment shows far above that."""
+    rng = np.random.default_rng(11)
+    mats = [rng.standard_normal(sh) for sh in TC_SHAPES]
+    bs = [A @ rng.standard_normal(A.shape[1]) for A in mats]
+    opts = dict(tol=1e-30, tol_normal=0.0, max_iter=2)
+    xs, iters, rel, reason = run(tacta, mats, bs, tacta.BATCH_BF16, config=config, **opts)
+    for s, (A, b) in enumerate(zip(mats, bs)):
+        ref = oracle.cta_solve(oracle.make_operator(problem(bf16_round(A), b)), b, pivot_tol=1e-6, **opts)
+        assert iters[s] == 2 and tacta.REASON[int(reason[s])] == "MAXITER", s
+        err = np.linalg.norm(xs[s] - ref.x) / np.linalg.norm(ref.x)
+        assert err <= 1e-4, (s, A.shape, err)
+
+
+def test_bf16_tensor_cores_one_step(tacta):
+    """One step (t = 1: x = (phi_1 / phi_2) Aᵀ b) on the tensor cores against the oracle on
+    the BF16-rounded matrix to 2e-5: the products' only error is FP32 accumulation."""
+    rng = np.random.default_rng(12)
+    mats = [rng.standard_normal(sh) for sh in TC_SHAPES]
+    bs = [A @ rng.standard_normal(A.shape[1]) for A in mats]
+    opts = dict(tol=1e-30, tol_normal=0.0, max_iter=1)
+    xs, iters, rel, reason = run(tacta, mats, bs, tacta.BATCH_BF16, config=TENSOR, **opts)
+    for s, (A, b) in enumerate(zip(mats, bs)):
+        ref = oracle.cta_solve(oracle.make_operator(problem(bf16_round(A), b)), b, pivot_tol=1e-6, **opts)
+        err = np.linalg.norm(xs[s] - ref.x) / np.linalg.norm(ref.x)
+        assert err <= 2e-5, (s, A.shape, err)
 
 
 def test_full_batch_4096_fp32(tacta):
