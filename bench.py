@@ -269,7 +269,47 @@ def extra_workloads(tacta, dev, stream, plan_stencil, b_stencil, steps):
     out["batched_dense_4096"] = batched_workload(tacta, dev, stream)
     out["dense_256"] = dense_workload(tacta, dev, stream)
     out["autograd_2000x8000"] = autograd_workload(tacta, dev, stream)
+    out["dense_2000x8000"] = dense_minnorm_workload(tacta, dev, stream)
     return out
+
+
+def dense_minnorm_workload(tacta, dev, stream):
+    """Dense full-row-rank 2000 x 8000 N(0,1) min-norm system (b = A x0): CTA time to 1e-8
+    in FP64 and in mixed precision (FP32 copies of A and Aᵀ), and one profiled solve per
+    precision for the dense products' bandwidth: algorithmic bytes per product (the values
+    once, x read and y written once) over the product's event-timed duration, against the
+    measured HBM peak."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(9)
+    D = rng.standard_normal((2000, 8000))
+    bh = D @ rng.standard_normal(8000)
+    A = torch.from_numpy(D).to(dev)
+    b = torch.from_numpy(bh).to(dev)
+    plan = tacta.Plan(A)
+    peak, peak_src = peaks()
+    res = {"workload": "dense 2000 x 8000 N(0,1), b = A x0, CTA to 1e-8", "tol": TOL,
+           "hbm_peak_gbs": peak, "hbm_peak_source": peak_src}
+    xs = {}
+    for name, prec in (("fp64", tacta.PRECISION_FP64), ("mixed", tacta.PRECISION_MIXED)):
+        kw = dict(tol=TOL, tol_normal=0.0, max_iter=20000, precision=prec)
+        plan.cta(b, **kw)
+        best = None
+        for _ in range(3):
+            t, x, info = timed_solve(plan, b, stream, **kw)
+            best = t if best is None else min(best, t)
+        xs[name] = x.double()
+        _, _, prof = plan.cta(b, profile=1, **kw)
+        gbs = prof["spmv_bytes"] / (prof["spmv_ms"] * 1e-3) / 1e9 if prof["spmv_ms"] > 0 else None
+        res[name] = {"time_to_tol_ms": best, "iters": info["iters"], "rel_res": info["rel_res"],
+                     "reason": info["reason_name"], "products_profiled": prof["spmv_count"],
+                     "us_per_product": 1e3 * prof["spmv_ms"] / max(prof["spmv_count"], 1),
+                     "product_gbs": gbs, "product_hbm_frac": gbs / peak if gbs else None}
+    res["mixed_vs_fp64_rel_x_diff"] = float(torch.linalg.norm(xs["mixed"] - xs["fp64"]) /
+                                            torch.linalg.norm(xs["fp64"]))
+    res["speedup_mixed_over_fp64"] = res["fp64"]["time_to_tol_ms"] / res["mixed"]["time_to_tol_ms"]
+    plan.close()
+    return res
 
 
 def dense_workload(tacta, dev, stream):
@@ -283,9 +323,9 @@ def dense_workload(tacta, dev, stream):
         A = torch.from_numpy(p.dense).to(dev)
         b = torch.from_numpy(p.b).to(dev)
         plan = tacta.Plan(A)
-        for alg in ("cta", "ta"):
-            kw = dict(tol=1e-10, tol_normal=0.0, max_iter=20000)
-            fn = getattr(plan, alg)
+        for alg, extra in (("cta", {}), ("ta", {}), ("cta_mixed", {"precision": tacta.PRECISION_MIXED})):
+            kw = dict(tol=1e-10, tol_normal=0.0, max_iter=20000, **extra)
+            fn = getattr(plan, alg.split("_")[0])
             fn(b, **kw)
             t, (x, _, info) = timed(lambda: fn(b, **kw), stream)
             res[f"{name}_{alg}"] = {"time_to_tol_ms": t, "iters": info["iters"],

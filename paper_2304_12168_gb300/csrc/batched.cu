@@ -882,13 +882,13 @@ __device__ bool mma_pass(const __nv_bfloat16* Ares, bool resident, const Ring& r
         const uint32_t cbase = smem_addr(chunk);
         for (int rd = 0; rd < rounds; ++rd) {
             uint32_t af[SB][KGT][4];
-            float cd[SB][4];
+            float cd[SB][4], ce[SB][4];   // A z over the even and the odd tiles (two MMA chains)
 #pragma unroll
             for (int sb = 0; sb < SB; ++sb) {
                 const int rb = (rd * G.NL + l) * SB + sb;
                 const bool lo_ok = rb * 16 + sp < rows, hi_ok = rb * 16 + sp + 8 < rows;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) cd[sb][e] = 0.0f;
+                for (int e = 0; e < 4; ++e) cd[sb][e] = ce[sb][e] = 0.0f;
 #pragma unroll
                 for (int kk = 0; kk < KGT; ++kk) {
                     const int kt = g * G.KG + kk;
@@ -897,7 +897,7 @@ __device__ bool mma_pass(const __nv_bfloat16* Ares, bool resident, const Ring& r
                                     cbase + (uint32_t)(((rb * 16 + lrow) * ld + kt * 16 + lcol) * 2));
                         if (!lo_ok) { af[sb][kk][0] = 0u; af[sb][kk][2] = 0u; }   // rows past the chunk
                         if (!hi_ok) { af[sb][kk][1] = 0u; af[sb][kk][3] = 0u; }
-                        if (DOT) mma_bf16(cd[sb], af[sb][kk], bz[kk][0], bz[kk][1]);
+                        if (DOT) mma_bf16((kk & 1) ? ce[sb] : cd[sb], af[sb][kk], bz[kk][0], bz[kk][1]);
                     } else {
 #pragma unroll
                         for (int e = 0; e < 4; ++e) af[sb][kk][e] = 0u;
@@ -913,7 +913,8 @@ __device__ bool mma_pass(const __nv_bfloat16* Ares, bool resident, const Ring& r
                 // this group's part of A z for each row: (hi + lo) + lo2 columns of C
 #pragma unroll
                 for (int sb = 0; sb < SB; ++sb) {
-                    float v0 = cd[sb][0] + cd[sb][1], v1 = cd[sb][2] + cd[sb][3];
+                    float v0 = (cd[sb][0] + ce[sb][0]) + (cd[sb][1] + ce[sb][1]);
+                    float v1 = (cd[sb][2] + ce[sb][2]) + (cd[sb][3] + ce[sb][3]);
                     v0 += __shfl_down_sync(0xffffffffu, v0, 1);
                     v1 += __shfl_down_sync(0xffffffffu, v1, 1);
                     if (q4 == 0) {
@@ -1081,7 +1082,10 @@ batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
         const TA* Ag = alo + d.a_lo;
         const int64_t row_bytes = (int64_t)ld * (int64_t)sizeof(TA);
         const MmaGeo G = MMA ? mma_geo(n, ld, NW) : MmaGeo{};
-        const int R = MMA ? G.R : (int)max((int64_t)1, (int64_t)kChunkBytes / row_bytes);
+        // CUDA-core chunks: a multiple of the 2 NW rows the consumer warps take per round
+        // when the stage holds that many, so that no warp takes an extra round per chunk
+        const int64_t fit = max((int64_t)1, (int64_t)kChunkBytes / row_bytes);
+        const int R = MMA ? G.R : (int)(fit >= 2 * NW ? fit / (2 * NW) * (2 * NW) : fit);
         const int nch = (m + R - 1) / R;
         // (the tensor-core pass reads whole 16-row blocks)
         const bool resident = (int64_t)(MMA ? (m + 15) / 16 * 16 : m) * row_bytes <= P.area_bytes;

@@ -51,6 +51,8 @@ struct Ctl {
     double ref_eta2;       // mixed CTA: refine once ||r||² <= ref_eta2 * ||r||² at the last refinement (0: off)
     double ref_thr;        // that threshold, set by each true residual
     int64_t wait_cycles;   // fused chain: a grid-wide wait gives up after this many SM cycles
+    int32_t loops;         // on-device loop: bodies run by the current graph launch
+    int32_t loop_limit;    // ... and its bound (the loop also ends once status != 0)
     double phi[2 * kTMax + 2];
     double alpha[kTMax];
     double red[4];         // scratch results of setup reductions
@@ -288,9 +290,20 @@ cudaError_t launch_spmv32(const LaunchCtx& L, const DevCSR32& A, const float* x,
 cudaError_t launch_cta_update32(const LaunchCtx& L, int t, int64_t m, int64_t n, float* dx, float* r,
                                 float* const* z, float* const* u, float xscale, FinArgs f);
 cudaError_t abs_row_sum_max(cudaStream_t s, const DevCSR& A, double* dev_out, double* host_out);
+// dense FP32 product of the mixed-precision chain (row-major A, rows x cols): y = (A x) *
+// scale, ||y||² to the finisher
+cudaError_t launch_dense32(const LaunchCtx& L, int64_t rows, int64_t cols, const float* A, const float* x,
+                           float* y, float scale, FinArgs f, int gate);
+cudaError_t dense_abs_row_sum_max(cudaStream_t s, int64_t rows, int64_t cols, const double* vals, double* dev_out,
+                                  double* host_out);
 cudaError_t launch_outer_on_pattern(cudaStream_t s, int grid, const DevOperand& A, double alpha, const double* u,
                                     const double* v, double* out);
 cudaError_t launch_fold_correction(const LaunchCtx& L, int64_t n, double* x, float* dx, int gate);
+// on-device iteration loop (a graph WHILE node): loop_begin resets the body count and sets
+// its bound before the graph launch; loop_continue, the body's last kernel, counts the
+// body and sets the node's condition to (status == 0 and count < bound)
+cudaError_t launch_loop_begin(cudaStream_t s, Ctl* ctl, int32_t limit);
+cudaError_t launch_loop_continue(cudaStream_t s, Ctl* ctl, cudaGraphConditionalHandle h);
 cudaError_t convert_to_f32(cudaStream_t s, const double* src, float* dst, int64_t len);
 cudaError_t spmv32_prepare();
 

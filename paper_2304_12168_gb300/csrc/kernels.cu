@@ -1166,6 +1166,124 @@ cudaError_t abs_row_sum_max(cudaStream_t s, const DevCSR& A, double* dev_out, do
     return cudaStreamSynchronize(s);
 }
 
+// Dense FP32 product of the mixed-precision chain: y = (A x) * scale for row-major A,
+// ||y||² (FP64, added per row) to the finisher. WPR warps share a row (the grid then has
+// enough warps in flight for HBM when rows are few and long): each sums an interleaved
+// share of the row's 16-byte vectors with four independent accumulators, and the WPR
+// partial sums meet in shared memory in warp order (deterministic).
+template <int WPR>
+__global__ void __launch_bounds__(kBlock)
+dense32_rows(int64_t rows, int64_t cols, const float* __restrict__ A, const float* __restrict__ x,
+             float* __restrict__ y, float scale, Ctl* ctl, double* partials, FinArgs f, int gate) {
+    if (gated_out(ctl, gate)) return;
+    if (gate != GATE_FORCE && blockIdx.x == 0 && threadIdx.x == 0) ctl->matvecs += 1;
+    constexpr int RPB = (kBlock / 32) / WPR;   // rows per block and pass
+    __shared__ float red[kBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rl = warp / WPR, part = warp % WPR;
+    const bool vec = (cols & 3) == 0;          // rows start 16-byte aligned
+    double a0 = 0.0;
+    const int64_t groups = (rows + RPB - 1) / RPB;
+    for (int64_t gidx = blockIdx.x; gidx < groups; gidx += gridDim.x) {
+        const int64_t row = gidx * RPB + rl;
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+        if (row < rows) {
+            const float* a = A + row * cols;
+            if (vec) {
+                const float4* a4 = reinterpret_cast<const float4*>(a);
+                const float4* x4 = reinterpret_cast<const float4*>(x);
+                const int64_t nv = cols >> 2, step = 32 * WPR;
+                int64_t c = part * 32 + lane;
+                for (; c + 3 * step < nv; c += 4 * step) {
+                    const float4 p0 = __ldg(a4 + c), p1 = __ldg(a4 + c + step), p2 = __ldg(a4 + c + 2 * step),
+                                 p3 = __ldg(a4 + c + 3 * step);
+                    const float4 q0 = __ldg(x4 + c), q1 = __ldg(x4 + c + step), q2 = __ldg(x4 + c + 2 * step),
+                                 q3 = __ldg(x4 + c + 3 * step);
+                    s0 = fmaf(p0.x, q0.x, s0); s0 = fmaf(p0.y, q0.y, s0); s0 = fmaf(p0.z, q0.z, s0); s0 = fmaf(p0.w, q0.w, s0);
+                    s1 = fmaf(p1.x, q1.x, s1); s1 = fmaf(p1.y, q1.y, s1); s1 = fmaf(p1.z, q1.z, s1); s1 = fmaf(p1.w, q1.w, s1);
+                    s2 = fmaf(p2.x, q2.x, s2); s2 = fmaf(p2.y, q2.y, s2); s2 = fmaf(p2.z, q2.z, s2); s2 = fmaf(p2.w, q2.w, s2);
+                    s3 = fmaf(p3.x, q3.x, s3); s3 = fmaf(p3.y, q3.y, s3); s3 = fmaf(p3.z, q3.z, s3); s3 = fmaf(p3.w, q3.w, s3);
+                }
+                for (; c < nv; c += step) {
+                    const float4 p0 = __ldg(a4 + c), q0 = __ldg(x4 + c);
+                    s0 = fmaf(p0.x, q0.x, s0); s0 = fmaf(p0.y, q0.y, s0); s0 = fmaf(p0.z, q0.z, s0); s0 = fmaf(p0.w, q0.w, s0);
+                }
+            } else {
+                for (int64_t c = part * 32 + lane; c < cols; c += 32 * WPR) s0 = fmaf(__ldg(a + c), __ldg(x + c), s0);
+            }
+        }
+        float sum = (s0 + s1) + (s2 + s3);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (WPR == 1) {
+            if (lane == 0 && row < rows) {
+                const float v = sum * scale;
+                y[row] = v;
+                a0 = fma((double)v, (double)v, a0);
+            }
+        } else {
+            if (lane == 0) red[warp] = sum;
+            __syncthreads();
+            if (part == 0 && lane == 0 && row < rows) {
+                float t = red[warp];
+                for (int q = 1; q < WPR; ++q) t += red[warp + q];
+                const float v = t * scale;
+                y[row] = v;
+                a0 = fma((double)v, (double)v, a0);
+            }
+            __syncthreads();
+        }
+    }
+    reduce_and_finish<1>(a0, 0.0, ctl, partials, f);
+}
+
+cudaError_t launch_dense32(const LaunchCtx& L, int64_t rows, int64_t cols, const float* A, const float* x,
+                           float* y, float scale, FinArgs f, int gate) {
+    // split rows among warps until the launch has about as many warps as the grid holds
+    // (the partials buffer bounds the grid at max_grid blocks)
+    const int64_t want = (int64_t)L.max_grid * (kBlock / 32);
+    int wpr = 1;
+    while (wpr < 8 && rows * wpr * 2 <= want && cols >= 256LL * wpr) wpr *= 2;
+    const int64_t rpb = (kBlock / 32) / wpr;
+    const int64_t groups = (rows + rpb - 1) / rpb;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)L.max_grid));
+    if (L.launches) ++*L.launches;
+    switch (wpr) {
+    case 1: dense32_rows<1><<<grid, kBlock, 0, L.stream>>>(rows, cols, A, x, y, scale, L.ctl, L.partials, f, gate); break;
+    case 2: dense32_rows<2><<<grid, kBlock, 0, L.stream>>>(rows, cols, A, x, y, scale, L.ctl, L.partials, f, gate); break;
+    case 4: dense32_rows<4><<<grid, kBlock, 0, L.stream>>>(rows, cols, A, x, y, scale, L.ctl, L.partials, f, gate); break;
+    default: dense32_rows<8><<<grid, kBlock, 0, L.stream>>>(rows, cols, A, x, y, scale, L.ctl, L.partials, f, gate); break;
+    }
+    return cudaGetLastError();
+}
+
+// max_i sum_k |A_ik| of a dense row-major matrix (the infinity norm)
+__global__ void dense_abs_row_sum_max_kernel(int64_t rows, int64_t cols, const double* __restrict__ vals,
+                                             unsigned long long* out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double best = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+        double sm = 0.0;
+        for (int64_t c = lane; c < cols; c += 32) sm += fabs(vals[r * cols + c]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+        best = fmax(best, sm);
+    }
+    if (lane == 0) atomicMax(out, (unsigned long long)__double_as_longlong(best));
+}
+
+cudaError_t dense_abs_row_sum_max(cudaStream_t s, int64_t rows, int64_t cols, const double* vals, double* dev_out,
+                                  double* host_out) {
+    cudaError_t e = cudaMemsetAsync(dev_out, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    dense_abs_row_sum_max_kernel<<<1024, kBlock, 0, s>>>(rows, cols, vals,
+                                                         reinterpret_cast<unsigned long long*>(dev_out));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(host_out, dev_out, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
 cudaError_t spmv32_prepare() {
     static const char done_key = 0;
     if (done_on_device(&done_key)) return cudaSuccess;
@@ -1217,6 +1335,26 @@ cta_update32(int64_t m, int64_t n, float* __restrict__ dx, float* __restrict__ r
         }
     }
     reduce_and_finish<1, kBlock, true>((double)acc, 0.0, ctl, partials, f);
+}
+
+__global__ void loop_begin_kernel(Ctl* ctl, int32_t limit) {
+    ctl->loops = 0;
+    ctl->loop_limit = limit;
+}
+
+__global__ void loop_continue_kernel(Ctl* ctl, cudaGraphConditionalHandle h) {
+    const int32_t n = ++ctl->loops;
+    cudaGraphSetConditional(h, (ctl->status == 0 && n < ctl->loop_limit) ? 1u : 0u);
+}
+
+cudaError_t launch_loop_begin(cudaStream_t s, Ctl* ctl, int32_t limit) {
+    loop_begin_kernel<<<1, 1, 0, s>>>(ctl, limit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loop_continue(cudaStream_t s, Ctl* ctl, cudaGraphConditionalHandle h) {
+    loop_continue_kernel<<<1, 1, 0, s>>>(ctl, h);
+    return cudaGetLastError();
 }
 
 // x += (double) dx, dx = 0: the FP32 correction folded into the FP64 iterate

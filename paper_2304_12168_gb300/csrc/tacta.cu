@@ -548,16 +548,37 @@ static tacta_status ensure_hist(Plan* p, int64_t cap) {
 
 // FP32 copies and vectors of the mixed-precision path (made on first use)
 static tacta_status ensure_mixed(Plan* p, int t_max, cudaStream_t s) {
-    if (p->A.format != TACTA_CSR) {
-        set_error("mixed precision needs A in CSR format");
-        return TACTA_ERR_INVALID;
-    }
     auto f32 = [&](float** ptr, int64_t len) {
         cudaError_t e = cudaMalloc(ptr, sizeof(float) * (len + kPadVec32));
         if (e == cudaSuccess) e = cudaMemsetAsync(*ptr, 0, sizeof(float) * (len + kPadVec32), s);
         return e;
     };
-    if (!p->A32.vals) {
+    // chain scale 1/sigma from the infinity norms of A and Aᵀ (see below)
+    auto set_scale = [&](double ninf, double n1) {
+        const double bound = std::sqrt(ninf * n1);
+        int e2 = 0;
+        if (bound > 0.0 && std::isfinite(bound)) e2 = (int)std::ceil(std::log2(bound));
+        e2 = std::max(-120, std::min(120, e2));
+        p->chain_scale = std::ldexp(1.0f, -e2);
+    };
+    if (p->A.format == TACTA_DENSE && !p->A32.vals) {
+        // dense A: FP32 copies of A and Aᵀ (row-major), read by the dense FP32 products
+        free_graphs(p);
+        const int64_t mn = p->m * p->n;
+        CUDA_TRY(cudaMalloc(&p->A32.vals, sizeof(float) * (mn + kPadVals32)));
+        CUDA_TRY(cudaMalloc(&p->At32.vals, sizeof(float) * (mn + kPadVals32)));
+        if (mn > 0) {
+            CUDA_TRY(convert_to_f32(s, p->A.dense.vals, p->A32.vals, mn));
+            CUDA_TRY(convert_to_f32(s, p->At.dense.vals, p->At32.vals, mn));
+        }
+        CUDA_TRY(f32(&p->r32, p->m));
+        CUDA_TRY(f32(&p->dx32, p->n));
+        CUDA_TRY(dense_abs_row_sum_max(s, p->m, p->n, p->A.dense.vals, p->partials, &p->stage->red[0]));
+        const double ninf = p->stage->red[0];
+        CUDA_TRY(dense_abs_row_sum_max(s, p->n, p->m, p->At.dense.vals, p->partials, &p->stage->red[0]));
+        set_scale(ninf, p->stage->red[0]);
+    }
+    if (p->A.format == TACTA_CSR && !p->A32.vals) {
         free_graphs(p);
         for (DevCSR32* a : {&p->A32, &p->At32}) {
             const DevCSR& base = (a == &p->A32) ? p->A.csr : p->At.csr;
@@ -582,11 +603,7 @@ static tacta_status ensure_mixed(Plan* p, int t_max, cudaStream_t s) {
         ninf = p->stage->red[0];
         CUDA_TRY(abs_row_sum_max(s, p->At.csr, p->partials, &p->stage->red[0]));
         n1 = p->stage->red[0];
-        const double bound = std::sqrt(ninf * n1);
-        int e2 = 0;
-        if (bound > 0.0 && std::isfinite(bound)) e2 = (int)std::ceil(std::log2(bound));
-        e2 = std::max(-120, std::min(120, e2));
-        p->chain_scale = std::ldexp(1.0f, -e2);
+        set_scale(ninf, n1);
     }
     for (int i = 0; i < t_max; ++i) {
         if (!p->z32[i]) {
@@ -656,7 +673,14 @@ static cudaError_t prof_mark(Plan* p, const LaunchCtx& L) {
 // residual b - A x with the FP64 product, stored back into the FP32 residual.
 static cudaError_t chain_spmv32(Plan* p, const LaunchCtx& L, const DevCSR32& A, const float* x, float* y,
                                 FinArgs f) {
-    if (!p->profiling) return launch_spmv32(L, A, x, y, p->chain_scale, EPI_NORM, f, GATE_ALWAYS);
+    const bool dense = p->A.format == TACTA_DENSE;
+    const bool tr = &A == &p->At32;                       // the product with Aᵀ (n x m)
+    auto launch = [&]() {
+        return dense ? launch_dense32(L, tr ? p->n : p->m, tr ? p->m : p->n, A.vals, x, y, p->chain_scale, f,
+                                      GATE_ALWAYS)
+                     : launch_spmv32(L, A, x, y, p->chain_scale, EPI_NORM, f, GATE_ALWAYS);
+    };
+    if (!p->profiling) return launch();
     while (p->pev.size() < p->pev_used + 2) {
         cudaEvent_t ev;
         cudaError_t err = cudaEventCreate(&ev);
@@ -665,12 +689,17 @@ static cudaError_t chain_spmv32(Plan* p, const LaunchCtx& L, const DevCSR32& A, 
     }
     cudaError_t err = cudaEventRecord(p->pev[p->pev_used], L.stream);
     if (err != cudaSuccess) return err;
-    if ((err = launch_spmv32(L, A, x, y, p->chain_scale, EPI_NORM, f, GATE_ALWAYS)) != cudaSuccess) return err;
+    if ((err = launch()) != cudaSuccess) return err;
     if ((err = cudaEventRecord(p->pev[p->pev_used + 1], L.stream)) != cudaSuccess) return err;
     p->pev_used += 2;
     p->prof_count += 1;
-    const DevCSR& a = *A.base;
-    p->prof_bytes += 8.0 * (double)a.nnz + 4.0 * (double)(a.rows + 1) + 4.0 * (double)a.cols + 4.0 * (double)a.rows;
+    if (dense) {   // the FP32 values once, x read and y written once
+        p->prof_bytes += 4.0 * (double)(p->m * p->n) + 4.0 * (double)(p->m + p->n);
+    } else {
+        const DevCSR& a = *A.base;
+        p->prof_bytes += 8.0 * (double)a.nnz + 4.0 * (double)(a.rows + 1) + 4.0 * (double)a.cols +
+                         4.0 * (double)a.rows;
+    }
     return cudaSuccess;
 }
 
@@ -918,6 +947,59 @@ static tacta_status run_loop(Plan* p, const Opts& O, int64_t max_iter, int perio
     LaunchCtx L{O.s, p->ctl, p->partials, p->grid, launches};
     if (max_iter <= 0) return TACTA_OK;
     const int64_t poll = std::max<int64_t>(O.o.poll_every, 1);
+    if (use_graph) {
+        // The iteration loop on the device: one graph whose WHILE node repeats a body of
+        // ceil(poll / period) schedule periods of iterations followed by loop_continue,
+        // which keeps the node running while the control block's status is 0 and the
+        // body count is below the bound that covers max_iter; no host polling, and no
+        // launches enqueued past the stop.
+        const int reps = (int)std::max<int64_t>(1, (poll + period - 1) / period);
+        const int iters = reps * period;
+        if (*graph == nullptr) {
+            int64_t cnt = 0;
+            LaunchCtx C{p->cap, p->ctl, p->partials, p->grid, &cnt};
+            cudaGraph_t g = nullptr;
+            cudaGraphConditionalHandle h = 0;
+            CUDA_TRY(cudaGraphCreate(&g, 0));
+            cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+            cudaGraphNodeParams np{};
+            cudaGraphNode_t node = nullptr;
+            if (e == cudaSuccess) {
+                np.type = cudaGraphNodeTypeConditional;
+                np.conditional.handle = h;
+                np.conditional.type = cudaGraphCondTypeWhile;
+                np.conditional.size = 1;
+                e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+            }
+            if (e == cudaSuccess)
+                e = cudaStreamBeginCaptureToGraph(p->cap, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                for (int k = 0; k < iters && e == cudaSuccess; ++k) e = body(C, (int64_t)k);
+                if (e == cudaSuccess) e = launch_loop_continue(p->cap, p->ctl, h);
+                cudaGraph_t captured = nullptr;
+                const cudaError_t e2 = cudaStreamEndCapture(p->cap, &captured);
+                if (e == cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                *graph = nullptr;
+                set_error(std::string("graph with the on-device loop: ") + cudaGetErrorString(e));
+                return TACTA_ERR_CUDA;
+            }
+            *graph_launches = cnt + 1;   // the body's kernels and loop_continue
+            *graph_iters = iters;
+        }
+        const int64_t limit = (max_iter + iters - 1) / iters;
+        CUDA_TRY(launch_loop_begin(O.s, p->ctl, (int32_t)std::min<int64_t>(limit, INT32_MAX)));
+        CUDA_TRY(cudaGraphLaunch(*graph, O.s));
+        // bodies run, for the launch count
+        CUDA_TRY(cudaMemcpyAsync(&p->poll[0], &p->ctl->loops, sizeof(int32_t), cudaMemcpyDeviceToHost, O.s));
+        CUDA_TRY(cudaStreamSynchronize(O.s));
+        *launches += 1 + (int64_t)p->poll[0] * *graph_launches;
+        return TACTA_OK;
+    }
     if (use_graph && *graph == nullptr) {
         // capture ceil(poll / period) periods of iterations on the private stream
         const int reps = (int)std::max<int64_t>(1, (poll + period - 1) / period);
