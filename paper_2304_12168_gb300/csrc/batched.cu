@@ -554,19 +554,25 @@ __device__ __forceinline__ void consumers_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
 }
 
-// sum of the consumer threads' accumulators (all NT must call), added in warp order by
-// consumer thread 0, the only thread that receives it
+// the sums of the consumer threads' two accumulators (all NT must call; red: 2 NT/32
+// slots), added in warp order by consumer thread 0, the only thread that receives them;
+// a_lane0: only lane 0 of each warp holds a nonzero a (no shuffles needed for it)
 template <int NT, class TC>
-__device__ __forceinline__ double consumer_sum(SqAcc<TC> a, double* red) {
-    a = warp_sum_sq(a);
+__device__ __forceinline__ double2 consumer_sum2(SqAcc<TC> a, bool a_lane0, SqAcc<TC> b, double* red) {
+    if (!a_lane0) a = warp_sum_sq(a);
+    b = warp_sum_sq(b);
+    const int w = threadIdx.x >> 5;
     consumers_sync<NT>();
-    if ((threadIdx.x & 31) == 0) a.put(red + (threadIdx.x >> 5));
+    if ((threadIdx.x & 31) == 0) { a.put(red + 2 * w); b.put(red + 2 * w + 1); }
     consumers_sync<NT>();
-    double r = 0.0;
+    double2 r = make_double2(0.0, 0.0);
     if (threadIdx.x == 0) {
-        SqAcc<TC> t = SqAcc<TC>::get(red);
-        for (int i = 1; i < NT / 32; ++i) t.merge(SqAcc<TC>::get(red + i));
-        r = t.value();
+        SqAcc<TC> ta = SqAcc<TC>::get(red), tb = SqAcc<TC>::get(red + 1);
+        for (int i = 1; i < NT / 32; ++i) {
+            ta.merge(SqAcc<TC>::get(red + 2 * i));
+            tb.merge(SqAcc<TC>::get(red + 2 * i + 1));
+        }
+        r = make_double2(ta.value(), tb.value());
     }
     return r;
 }
@@ -737,8 +743,10 @@ __device__ bool fused_pass(const TA* Ares, bool resident, const Ring& ring, uint
             sz.add(t);
         }
     }
-    sq_u = DOT ? consumer_sum<NT>(su, red) : 0.0;
-    sq_z = AXPY ? consumer_sum<NT>(sz, red) : 0.0;
+    // (the row sums of squares sit in lane 0 of each warp)
+    const double2 sq = consumer_sum2<NT>(su, true, sz, red);
+    sq_u = sq.x;
+    sq_z = sq.y;
     return ok;
 }
 
@@ -992,8 +1000,9 @@ __device__ bool mma_pass(const __nv_bfloat16* Ares, bool resident, const Ring& r
             sz.add(t);
         }
     }
-    sq_u = DOT ? consumer_sum<NT>(su, red) : 0.0;
-    sq_z = AXPY ? consumer_sum<NT>(sz, red) : 0.0;
+    const double2 sq = consumer_sum2<NT>(su, false, sz, red);
+    sq_u = sq.x;
+    sq_z = sq.y;
     return ok;
 }
 
@@ -1035,7 +1044,7 @@ batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
     constexpr int NT = NW * 32;              // consumer threads
     constexpr int NB = NT + 32;              // with the producer warp
     __shared__ Shared S;
-    __shared__ double cred[NW];
+    __shared__ double cred[2 * NW];
     __shared__ __align__(8) uint64_t full[kRing], empty[kRing], loaded;
     __shared__ int fail_s;
     extern __shared__ __align__(128) unsigned char smem_raw[];
