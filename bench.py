@@ -299,7 +299,10 @@ def dense_minnorm_workload(tacta, dev, stream):
             t, x, info = timed_solve(plan, b, stream, **kw)
             best = t if best is None else min(best, t)
         xs[name] = x.double()
-        _, _, prof = plan.cta(b, profile=1, poll_every=1, **kw)   # products that ran, one poll per step
+        # profiled to exactly the steps the solve took: no launch runs past the stop, and the
+        # products run back to back (launch latency hidden) as in the solve
+        kwp = dict(kw, max_iter=info["iters"])
+        _, _, prof = plan.cta(b, profile=1, **kwp)
         gbs = prof["spmv_bytes"] / (prof["spmv_ms"] * 1e-3) / 1e9 if prof["spmv_ms"] > 0 else None
         res[name] = {"time_to_tol_ms": best, "iters": info["iters"], "rel_res": info["rel_res"],
                      "reason": info["reason_name"], "products_profiled": prof["spmv_count"],
@@ -406,6 +409,28 @@ def batched_workload(tacta, dev, stream):
         res[name]["speedup_over_plan_fp64"] = res["plan_fp64_per_system_sample"]["extrapolated_batch_ms"] / \
             res[name]["time_ms"]
     return res
+
+
+def batch_sample():
+    """152 systems of the batched workload's distribution (seed 3), BF16 storage, each
+    solved for at most 300 steps (tol 1e-8) with the fused-pass kernel on CUDA cores and
+    then on the tensor cores, direct launches (the case profiled in profiles/)."""
+    import gen
+    import torch
+    import paper_2304_12168_gb300 as tacta
+    tacta.load_library()
+    torch.cuda.set_device(0)
+    B0 = gen.dense_batch(152, seed=3)
+    b = B0.packed_b()
+    cores = [c for c in range(len(tacta.Batch.configs())) if c not in tacta.Batch.tensor_core_configs()]
+    for cfg in (max(cores), tacta.Batch.tensor_core_configs()[0]):
+        B = tacta.Batch(B0.mats, storage=tacta.BATCH_BF16)
+        B.set_config(cfg)
+        x, it, rel, reason = B.cta(b, tol=TOL, tol_normal=0.0, max_iter=300, use_graph=0)
+        tb, te = B.timeline()
+        print(json.dumps({"config": cfg, "shape": tacta.Batch.configs()[cfg], "system_steps": int(it.sum()),
+                          "span_ms": float((te.max() - tb.min()) * 1e-6)}))
+        B.close()
 
 
 def completion_profile(tb, te, blocks):
@@ -551,11 +576,19 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
     ap.add_argument("--iters", type=int, default=ITERS_PER_STEP,
                     help="F_t iterations per step (default %(default)s; smaller for profiler runs)")
+    ap.add_argument("--batch-sample", action="store_true",
+                    help="only run a 152-system sample of the batched workload (BF16 storage, the CUDA-core and "
+                         "the tensor-core launch configurations, 300 steps each): the profiler's case")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="direct launches instead of the solve's graph (profilers cannot replay kernels of "
+                         "a graph with a conditional node)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch_sample:
+        return batch_sample()
 
     import numpy as np
     import torch
@@ -580,7 +613,7 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     iters_per_step = args.iters
-    opts = dict(tol=TOL, tol_normal=0.0, max_iter=iters_per_step)
+    opts = dict(tol=TOL, tol_normal=0.0, max_iter=iters_per_step, use_graph=0 if args.no_graph else 1)
 
     for _ in range(args.warmup):
         plan.cta(b, **opts)

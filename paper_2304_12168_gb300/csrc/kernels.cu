@@ -52,15 +52,6 @@ struct CsrAcc {
     __device__ __forceinline__ double val(int64_t k) const { return __ldg(vals + k); }
 };
 
-struct DenseAcc {
-    const double* __restrict__ vals;
-    int64_t rows, cols;
-    __device__ __forceinline__ int64_t begin(int64_t r) const { return r * cols; }
-    __device__ __forceinline__ int64_t end(int64_t r) const { return r * cols + cols; }
-    __device__ __forceinline__ int64_t col(int64_t k, int64_t b) const { return k - b; }
-    __device__ __forceinline__ double val(int64_t k) const { return __ldg(vals + k); }
-};
-
 template <int EPI>
 __device__ __forceinline__ void epilogue(int64_t row, double sum, double* __restrict__ y,
                                          const EpiArgs& e, double s, double& a0, double& a1) {
@@ -708,6 +699,96 @@ static cudaError_t spmv_dispatch_epi(const LaunchCtx& L, int kind, const Acc& ac
     return cudaGetLastError();
 }
 
+// Dense FP64 product, every epilogue: row-major A, WPR warps share a row (enough warps in
+// flight for HBM and the FP64 pipe when rows are few and long), each summing an
+// interleaved share of the row's 16-byte vectors with four independent FMA chains; the
+// WPR partial sums meet in shared memory in warp order (deterministic), and one lane runs
+// the row's epilogue.
+template <int WPR, int EPI>
+__global__ void __launch_bounds__(kBlock)
+dense_rows(int64_t rows, int64_t cols, const double* __restrict__ A, const double* __restrict__ x,
+           double* __restrict__ y, EpiArgs e, Ctl* ctl, double* partials, FinArgs f, int gate) {
+    if (gated_out(ctl, gate)) return;
+    if (gate != GATE_FORCE && blockIdx.x == 0 && threadIdx.x == 0) ctl->matvecs += 1;
+    const double sv = (EPI == EPI_TAPIVOT) ? ctl->s : 0.0;
+    constexpr int RPB = (kBlock / 32) / WPR;   // rows per block and pass
+    __shared__ double red[kBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rl = warp / WPR, part = warp % WPR;
+    const bool vec = (cols & 1) == 0;          // rows start 16-byte aligned
+    double a0 = 0.0, a1 = 0.0;
+    const int64_t groups = (rows + RPB - 1) / RPB;
+    for (int64_t gidx = blockIdx.x; gidx < groups; gidx += gridDim.x) {
+        const int64_t row = gidx * RPB + rl;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        if (row < rows) {
+            const double* a = A + row * cols;
+            if (vec) {
+                const double2* a2 = reinterpret_cast<const double2*>(a);
+                const double2* x2 = reinterpret_cast<const double2*>(x);
+                const int64_t nv = cols >> 1, step = 32 * WPR;
+                int64_t c = part * 32 + lane;
+                for (; c + step < nv; c += 2 * step) {
+                    const double2 p0 = __ldg(a2 + c), p1 = __ldg(a2 + c + step);
+                    const double2 q0 = __ldg(x2 + c), q1 = __ldg(x2 + c + step);
+                    s0 = fma(p0.x, q0.x, s0);
+                    s1 = fma(p0.y, q0.y, s1);
+                    s2 = fma(p1.x, q1.x, s2);
+                    s3 = fma(p1.y, q1.y, s3);
+                }
+                if (c < nv) {
+                    const double2 p0 = __ldg(a2 + c), q0 = __ldg(x2 + c);
+                    s0 = fma(p0.x, q0.x, s0);
+                    s1 = fma(p0.y, q0.y, s1);
+                }
+            } else {
+                for (int64_t c = part * 32 + lane; c < cols; c += 32 * WPR) s0 = fma(__ldg(a + c), __ldg(x + c), s0);
+            }
+        }
+        double sum = (s0 + s1) + (s2 + s3);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (WPR == 1) {
+            if (lane == 0 && row < rows) epilogue<EPI>(row, sum, y, e, sv, a0, a1);
+        } else {
+            if (lane == 0) red[warp] = sum;
+            __syncthreads();
+            if (part == 0 && lane == 0 && row < rows) {
+                double t = red[warp];
+                for (int q = 1; q < WPR; ++q) t += red[warp + q];
+                epilogue<EPI>(row, t, y, e, sv, a0, a1);
+            }
+            __syncthreads();
+        }
+    }
+    if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish<EpiRed<EPI>::value>(a0, a1, ctl, partials, f);
+}
+
+// warps per row of the dense products: split rows until the launch has about as many
+// warps as the grid holds (the partials buffer bounds the grid at max_grid blocks)
+static int dense_wpr(const LaunchCtx& L, int64_t rows, int64_t cols) {
+    const int64_t want = (int64_t)L.max_grid * (kBlock / 32);
+    int wpr = 1;
+    while (wpr < 8 && rows * wpr * 2 <= want && cols >= 256LL * wpr) wpr *= 2;
+    return wpr;
+}
+
+template <int EPI>
+static cudaError_t dense_launch(const LaunchCtx& L, const DevDense& A, const double* x, double* y, EpiArgs e,
+                                FinArgs f, int gate) {
+    const int wpr = dense_wpr(L, A.rows, A.cols);
+    const int64_t rpb = (kBlock / 32) / wpr;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((A.rows + rpb - 1) / rpb, (int64_t)L.max_grid));
+    if (L.launches) ++*L.launches;
+    switch (wpr) {
+    case 1: dense_rows<1, EPI><<<grid, kBlock, 0, L.stream>>>(A.rows, A.cols, A.vals, x, y, e, L.ctl, L.partials, f, gate); break;
+    case 2: dense_rows<2, EPI><<<grid, kBlock, 0, L.stream>>>(A.rows, A.cols, A.vals, x, y, e, L.ctl, L.partials, f, gate); break;
+    case 4: dense_rows<4, EPI><<<grid, kBlock, 0, L.stream>>>(A.rows, A.cols, A.vals, x, y, e, L.ctl, L.partials, f, gate); break;
+    default: dense_rows<8, EPI><<<grid, kBlock, 0, L.stream>>>(A.rows, A.cols, A.vals, x, y, e, L.ctl, L.partials, f, gate); break;
+    }
+    return cudaGetLastError();
+}
+
 template <class Acc>
 static cudaError_t spmv_dispatch(const LaunchCtx& L, int kind, const Acc& acc, const double* x,
                                  double* y, int epi, EpiArgs e, FinArgs f, int gate) {
@@ -767,8 +848,14 @@ cudaError_t launch_spmv(const LaunchCtx& L, const DevOperand& A, const double* x
         CsrAcc acc{A.csr.rowptr, A.csr.colidx, A.csr.vals, A.csr.rows};
         return spmv_dispatch(L, A.csr.cfg.kind, acc, x, y, epi, e, f, gate);
     }
-    DenseAcc acc{A.dense.vals, A.dense.rows, A.dense.cols};
-    return spmv_dispatch(L, A.dense.cfg.kind, acc, x, y, epi, e, f, gate);
+    switch (epi) {
+    case EPI_NONE: return dense_launch<EPI_NONE>(L, A.dense, x, y, e, f, gate);
+    case EPI_NORM: return dense_launch<EPI_NORM>(L, A.dense, x, y, e, f, gate);
+    case EPI_RESID: return dense_launch<EPI_RESID>(L, A.dense, x, y, e, f, gate);
+    case EPI_RESID_F32: return dense_launch<EPI_RESID_F32>(L, A.dense, x, y, e, f, gate);
+    case EPI_NORM_POS: return dense_launch<EPI_NORM_POS>(L, A.dense, x, y, e, f, gate);
+    default: return dense_launch<EPI_TAPIVOT>(L, A.dense, x, y, e, f, gate);
+    }
 }
 
 // ------------------------------------------------------------------ vector kernels
@@ -1239,11 +1326,7 @@ dense32_rows(int64_t rows, int64_t cols, const float* __restrict__ A, const floa
 
 cudaError_t launch_dense32(const LaunchCtx& L, int64_t rows, int64_t cols, const float* A, const float* x,
                            float* y, float scale, FinArgs f, int gate) {
-    // split rows among warps until the launch has about as many warps as the grid holds
-    // (the partials buffer bounds the grid at max_grid blocks)
-    const int64_t want = (int64_t)L.max_grid * (kBlock / 32);
-    int wpr = 1;
-    while (wpr < 8 && rows * wpr * 2 <= want && cols >= 256LL * wpr) wpr *= 2;
+    const int wpr = dense_wpr(L, rows, cols);
     const int64_t rpb = (kBlock / 32) / wpr;
     const int64_t groups = (rows + rpb - 1) / rpb;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)L.max_grid));
