@@ -294,6 +294,7 @@ cudaError_t abs_row_sum_max(cudaStream_t s, const DevCSR& A, double* dev_out, do
 // scale, ||y||² to the finisher
 cudaError_t launch_dense32(const LaunchCtx& L, int64_t rows, int64_t cols, const float* A, const float* x,
                            float* y, float scale, FinArgs f, int gate);
+cudaError_t dense32_prepare();   // kernel attributes of the dense FP32 product (before any capture)
 cudaError_t dense_abs_row_sum_max(cudaStream_t s, int64_t rows, int64_t cols, const double* vals, double* dev_out,
                                   double* host_out);
 cudaError_t launch_outer_on_pattern(cudaStream_t s, int grid, const DevOperand& A, double alpha, const double* u,

@@ -764,8 +764,10 @@ dense_rows(int64_t rows, int64_t cols, const double* __restrict__ A, const doubl
     if (EPI != EPI_NONE || f.kind != FIN_NONE) reduce_and_finish<EpiRed<EPI>::value>(a0, a1, ctl, partials, f);
 }
 
-// warps per row of the dense products: split rows until the launch has about as many
-// warps as the grid holds (the partials buffer bounds the grid at max_grid blocks)
+// Warps per row of the dense products: rows are split among warps until the launch has
+// about as many warps as the grid holds (rows few and long), keeping at least 256 columns
+// per warp; the grid is at most max_grid blocks (the partials buffer), one group of
+// 8 / wpr rows per block and pass.
 static int dense_wpr(const LaunchCtx& L, int64_t rows, int64_t cols) {
     const int64_t want = (int64_t)L.max_grid * (kBlock / 32);
     int wpr = 1;
@@ -773,12 +775,17 @@ static int dense_wpr(const LaunchCtx& L, int64_t rows, int64_t cols) {
     return wpr;
 }
 
+static int dense_grid(const LaunchCtx& L, int64_t rows, int wpr) {
+    const int64_t rpb = (kBlock / 32) / wpr;
+    const int64_t groups = (rows + rpb - 1) / rpb;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)L.max_grid));
+}
+
 template <int EPI>
 static cudaError_t dense_launch(const LaunchCtx& L, const DevDense& A, const double* x, double* y, EpiArgs e,
                                 FinArgs f, int gate) {
     const int wpr = dense_wpr(L, A.rows, A.cols);
-    const int64_t rpb = (kBlock / 32) / wpr;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((A.rows + rpb - 1) / rpb, (int64_t)L.max_grid));
+    const int grid = dense_grid(L, A.rows, wpr);
     if (L.launches) ++*L.launches;
     switch (wpr) {
     case 1: dense_rows<1, EPI><<<grid, kBlock, 0, L.stream>>>(A.rows, A.cols, A.vals, x, y, e, L.ctl, L.partials, f, gate); break;
@@ -1255,9 +1262,13 @@ cudaError_t abs_row_sum_max(cudaStream_t s, const DevCSR& A, double* dev_out, do
 
 // Dense FP32 product of the mixed-precision chain: y = (A x) * scale for row-major A,
 // ||y||² (FP64, added per row) to the finisher. WPR warps share a row (the grid then has
-// enough warps in flight for HBM when rows are few and long): each sums an interleaved
-// share of the row's 16-byte vectors with four independent accumulators, and the WPR
-// partial sums meet in shared memory in warp order (deterministic).
+// enough warps in flight for HBM when rows are few and long). When the rows are 16-byte
+// aligned, x is staged in shared memory once per block and each lane keeps eight 16-byte
+// loads of A in flight (registers hold A only), summing an interleaved share of the row's
+// vectors with four independent accumulators; the WPR partial sums meet in shared memory
+// in warp order (deterministic).
+constexpr int kDenseXSmem = 64 * 1024;   // x staged in shared memory up to 16,384 columns
+
 template <int WPR>
 __global__ void __launch_bounds__(kBlock)
 dense32_rows(int64_t rows, int64_t cols, const float* __restrict__ A, const float* __restrict__ x,
@@ -1265,39 +1276,53 @@ dense32_rows(int64_t rows, int64_t cols, const float* __restrict__ A, const floa
     if (gated_out(ctl, gate)) return;
     if (gate != GATE_FORCE && blockIdx.x == 0 && threadIdx.x == 0) ctl->matvecs += 1;
     constexpr int RPB = (kBlock / 32) / WPR;   // rows per block and pass
+    extern __shared__ float4 xs[];             // x (staged: cols / 4 vectors)
     __shared__ float red[kBlock / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rl = warp / WPR, part = warp % WPR;
     const bool vec = (cols & 3) == 0;          // rows start 16-byte aligned
-    double a0 = 0.0;
+    const int64_t nv = cols >> 2;
+    const bool staged = vec && cols * 4 <= kDenseXSmem;
+    const int64_t step = 32 * WPR;
     const int64_t groups = (rows + RPB - 1) / RPB;
+    // eight 16-byte loads of A per lane and chunk, predicated at the row's end so that a
+    // chunk always has all its loads in flight; the first chunk of the block's first row
+    // is issued before x is staged, so the staging overlaps the first loads
+    float4 p[8];
+    auto load_chunk = [&](int64_t row, int64_t c0) {
+        const float4* a4 = reinterpret_cast<const float4*>(A + row * cols);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t idx = c0 + k * step;
+            p[k] = (row < rows && idx < nv) ? __ldcs(a4 + idx) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    if (staged) {
+        if ((int64_t)blockIdx.x < groups) load_chunk(blockIdx.x * RPB + rl, part * 32 + lane);
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        for (int64_t i = threadIdx.x; i < nv; i += kBlock) xs[i] = __ldg(x4 + i);
+        __syncthreads();
+    }
+    double a0 = 0.0;
     for (int64_t gidx = blockIdx.x; gidx < groups; gidx += gridDim.x) {
         const int64_t row = gidx * RPB + rl;
         float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-        if (row < rows) {
-            const float* a = A + row * cols;
-            if (vec) {
-                const float4* a4 = reinterpret_cast<const float4*>(a);
-                const float4* x4 = reinterpret_cast<const float4*>(x);
-                const int64_t nv = cols >> 2, step = 32 * WPR;
-                int64_t c = part * 32 + lane;
-                for (; c + 3 * step < nv; c += 4 * step) {
-                    const float4 p0 = __ldg(a4 + c), p1 = __ldg(a4 + c + step), p2 = __ldg(a4 + c + 2 * step),
-                                 p3 = __ldg(a4 + c + 3 * step);
-                    const float4 q0 = __ldg(x4 + c), q1 = __ldg(x4 + c + step), q2 = __ldg(x4 + c + 2 * step),
-                                 q3 = __ldg(x4 + c + 3 * step);
-                    s0 = fmaf(p0.x, q0.x, s0); s0 = fmaf(p0.y, q0.y, s0); s0 = fmaf(p0.z, q0.z, s0); s0 = fmaf(p0.w, q0.w, s0);
-                    s1 = fmaf(p1.x, q1.x, s1); s1 = fmaf(p1.y, q1.y, s1); s1 = fmaf(p1.z, q1.z, s1); s1 = fmaf(p1.w, q1.w, s1);
-                    s2 = fmaf(p2.x, q2.x, s2); s2 = fmaf(p2.y, q2.y, s2); s2 = fmaf(p2.z, q2.z, s2); s2 = fmaf(p2.w, q2.w, s2);
-                    s3 = fmaf(p3.x, q3.x, s3); s3 = fmaf(p3.y, q3.y, s3); s3 = fmaf(p3.z, q3.z, s3); s3 = fmaf(p3.w, q3.w, s3);
+        if (staged) {
+            for (int64_t c0 = part * 32 + lane; c0 < nv; c0 += 8 * step) {
+                if (!(gidx == (int64_t)blockIdx.x && c0 == part * 32 + lane)) load_chunk(row, c0);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int64_t idx = c0 + k * step;
+                    if (idx < nv) {
+                        const float4 q = xs[idx];
+                        s0 = fmaf(p[k].x, q.x, s0); s1 = fmaf(p[k].y, q.y, s1);
+                        s2 = fmaf(p[k].z, q.z, s2); s3 = fmaf(p[k].w, q.w, s3);
+                    }
                 }
-                for (; c < nv; c += step) {
-                    const float4 p0 = __ldg(a4 + c), q0 = __ldg(x4 + c);
-                    s0 = fmaf(p0.x, q0.x, s0); s0 = fmaf(p0.y, q0.y, s0); s0 = fmaf(p0.z, q0.z, s0); s0 = fmaf(p0.w, q0.w, s0);
-                }
-            } else {
-                for (int64_t c = part * 32 + lane; c < cols; c += 32 * WPR) s0 = fmaf(__ldg(a + c), __ldg(x + c), s0);
             }
+        } else if (row < rows) {
+            const float* a = A + row * cols;
+            for (int64_t c = part * 32 + lane; c < cols; c += step) s0 = fmaf(__ldg(a + c), __ldg(x + c), s0);
         }
         float sum = (s0 + s1) + (s2 + s3);
 #pragma unroll
@@ -1324,18 +1349,44 @@ dense32_rows(int64_t rows, int64_t cols, const float* __restrict__ A, const floa
     reduce_and_finish<1>(a0, 0.0, ctl, partials, f);
 }
 
+cudaError_t dense32_prepare() {
+    static const char done_key = 0;
+    if (done_on_device(&done_key)) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    for (const void* k : {(const void*)dense32_rows<1>, (const void*)dense32_rows<2>, (const void*)dense32_rows<4>,
+                          (const void*)dense32_rows<8>})
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kDenseXSmem);
+    if (e == cudaSuccess) mark_done_on_device(&done_key);
+    return e;
+}
+
 cudaError_t launch_dense32(const LaunchCtx& L, int64_t rows, int64_t cols, const float* A, const float* x,
                            float* y, float scale, FinArgs f, int gate) {
-    const int wpr = dense_wpr(L, rows, cols);
+    cudaError_t e = dense32_prepare();
+    if (e != cudaSuccess) return e;
+    const size_t sm = ((cols & 3) == 0 && cols * 4 <= kDenseXSmem) ? (size_t)cols * 4 : 0;
+    // one wave of resident blocks looping over row groups of 8 / wpr rows; wpr is the split
+    // whose groups fill the wave most evenly (the busiest block takes ceil(groups / wave))
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense32_rows<4>, kBlock, sm) != cudaSuccess || per < 1)
+        per = 1;
+    const int wave = std::min(L.max_grid, per * (L.max_grid / 8));
+    int wpr = 1;
+    double best = -1.0;
+    for (int w = 1; w <= 8; w *= 2) {
+        if (w > 1 && cols < 512LL * w) break;
+        const double groups = (double)((rows * w + (kBlock / 32) - 1) / (kBlock / 32));
+        const double eff = groups < wave ? groups / wave : (groups / wave) / std::ceil(groups / wave);
+        if (eff > best + 1e-9) { best = eff; wpr = w; }
+    }
     const int64_t rpb = (kBlock / 32) / wpr;
-    const int64_t groups = (rows + rpb - 1) / rpb;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(groups, (int64_t)L.max_grid));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((rows + rpb - 1) / rpb, (int64_t)wave));
     if (L.launches) ++*L.launches;
     switch (wpr) {
-    case 1: dense32_rows<1><<<grid, kBlock, 0, L.stream>>>(rows, cols, A, x, y, scale, L.ctl, L.partials, f, gate); break;
-    case 2: dense32_rows<2><<<grid, kBlock, 0, L.stream>>>(rows, cols, A, x, y, scale, L.ctl, L.partials, f, gate); break;
-    case 4: dense32_rows<4><<<grid, kBlock, 0, L.stream>>>(rows, cols, A, x, y, scale, L.ctl, L.partials, f, gate); break;
-    default: dense32_rows<8><<<grid, kBlock, 0, L.stream>>>(rows, cols, A, x, y, scale, L.ctl, L.partials, f, gate); break;
+    case 1: dense32_rows<1><<<grid, kBlock, sm, L.stream>>>(rows, cols, A, x, y, scale, L.ctl, L.partials, f, gate); break;
+    case 2: dense32_rows<2><<<grid, kBlock, sm, L.stream>>>(rows, cols, A, x, y, scale, L.ctl, L.partials, f, gate); break;
+    case 4: dense32_rows<4><<<grid, kBlock, sm, L.stream>>>(rows, cols, A, x, y, scale, L.ctl, L.partials, f, gate); break;
+    default: dense32_rows<8><<<grid, kBlock, sm, L.stream>>>(rows, cols, A, x, y, scale, L.ctl, L.partials, f, gate); break;
     }
     return cudaGetLastError();
 }

@@ -573,6 +573,7 @@ static tacta_status ensure_mixed(Plan* p, int t_max, cudaStream_t s) {
         }
         CUDA_TRY(f32(&p->r32, p->m));
         CUDA_TRY(f32(&p->dx32, p->n));
+        CUDA_TRY(dense32_prepare());
         CUDA_TRY(dense_abs_row_sum_max(s, p->m, p->n, p->A.dense.vals, p->partials, &p->stage->red[0]));
         const double ninf = p->stage->red[0];
         CUDA_TRY(dense_abs_row_sum_max(s, p->n, p->m, p->At.dense.vals, p->partials, &p->stage->red[0]));
