@@ -253,6 +253,13 @@ tacta_status tacta_plan_transpose(tacta_plan plan, const tacta_options* opt, tac
 tacta_status tacta_plan_matvec(tacta_plan plan, int32_t transpose, const double* x, double* y,
                                const tacta_options* opt);
 
+/* tacta_plan_residual -- r = b - A x (transpose = 0) or r = b - Aᵀ x (transpose = 1), the
+   residual of Sec. 2 formed by the plan's product kernel (its residual epilogue, FP64);
+   x, b, r follow the plan's on_device flag (lengths n, m, m or m, n, n). r may not alias
+   x or b. */
+tacta_status tacta_plan_residual(tacta_plan plan, int32_t transpose, const double* x, const double* b, double* r,
+                                 const tacta_options* opt);
+
 /* tacta_plan_outer -- out[k] += alpha * u[row(k)] * v[col(k)] for every stored entry k of A
    (CSR: in the caller's nonzero order; dense: row-major m*n). With u = -lambda, v = x it
    forms the gradient dL/dA of x = A^{-1} b on A's pattern (Sec. 3 solves made

@@ -15,7 +15,7 @@ u_i = A z_i:  H^i r = u_i,  Aᵀ H^{i-1} r = z_i,  phi_{2i-1} = ||z_i||²,
 phi_{2i} = ||u_i||².
 
 Readings where the paper leaves a choice open (each one is shared by the CUDA
-solver and listed in the design notes):
+solver):
   * t-cycling (Sec. 5.1): "ping-pong" 1,2,3,4,5,4,3,2,1,2,... -- after F_5 the
     next step is F_4, as the paper's example says; one iteration = one F_t.
   * stopping (Alg. 1.1 while-clauses): relative forms ||r|| <= tol ||b|| and

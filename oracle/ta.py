@@ -18,7 +18,7 @@ One TA iteration at iterate b' = A x' (Thm. prop0TA, Prop. prop1TA):
     alpha = (b - b')ᵀ (v - b') / ||v - b'||²             (Eq. alph)
     b'' = (1 - alpha) b' + alpha v,  x'' = (1 - alpha) x' + alpha rho c / ||c||
 
-Readings (shared with the CUDA solver, listed in the design notes):
+Readings (shared with the CUDA solver):
   * stopping: ||b - b'|| <= tol ||b|| and ||c|| <= tol_normal ||Aᵀ b||
     (relative forms of the while-clauses). Alg. 2.5's inner clause
     ||Aᵀ(b - b')|| > 0 is read the same way.

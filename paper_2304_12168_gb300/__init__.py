@@ -66,7 +66,7 @@ class tacta_info(ctypes.Structure):
 
 EXPORTS = ["tacta_default_options", "cta_solve", "ta_solve", "ta_minnorm", "tacta_plan_create",
            "tacta_plan_cta", "tacta_plan_ta", "tacta_plan_minnorm", "tacta_plan_destroy",
-           "tacta_plan_transpose", "tacta_plan_matvec", "tacta_plan_outer", "tacta_plan_minnorm_bisect",
+           "tacta_plan_transpose", "tacta_plan_matvec", "tacta_plan_residual", "tacta_plan_outer", "tacta_plan_minnorm_bisect",
            "tacta_residual_static", "tacta_last_error", "tacta_version",
            "tacta_batch_create", "tacta_batch_cta", "tacta_batch_destroy", "tacta_batch_tune",
            "tacta_batch_set_config", "tacta_batch_num_configs", "tacta_batch_config_shape",
@@ -112,6 +112,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tacta_plan_transpose.restype = ctypes.c_int32
     lib.tacta_plan_matvec.argtypes = [vp, ctypes.c_int32, dp, dp, P(tacta_options)]
     lib.tacta_plan_matvec.restype = ctypes.c_int32
+    lib.tacta_plan_residual.argtypes = [vp, ctypes.c_int32, dp, dp, dp, P(tacta_options)]
+    lib.tacta_plan_residual.restype = ctypes.c_int32
     lib.tacta_plan_outer.argtypes = [vp, ctypes.c_double, dp, dp, dp, P(tacta_options)]
     lib.tacta_plan_outer.restype = ctypes.c_int32
     i32p = P(ctypes.c_int32)
@@ -389,6 +391,18 @@ class Plan:
         _check(lib.tacta_plan_matvec(self._h, int(bool(transpose)), px, _ptr(y, np.float64)[0],
                                      ctypes.byref(o)))
         return y
+
+    def residual(self, x, b, transpose=False, **opts):
+        """tacta_plan_residual: b - A x, or b - Aᵀ x with transpose=True."""
+        lib = load_library()
+        px, _, kx = _ptr(x, np.float64)
+        pb, _, kb = _ptr(b, np.float64)
+        r = _vec_out(self.n if transpose else self.m, self.on_device, kx)
+        o = make_options(self.on_device, **opts)
+        _check(lib.tacta_plan_residual(self._h, int(bool(transpose)), px, pb, _ptr(r, np.float64)[0],
+                                       ctypes.byref(o)))
+        del kb
+        return r
 
     def outer(self, alpha, u, v, out, **opts):
         """tacta_plan_outer: out[k] += alpha u[row(k)] v[col(k)] over A's stored entries."""

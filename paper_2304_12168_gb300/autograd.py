@@ -55,7 +55,7 @@ class CTASolveFn(torch.autograd.Function):
             plan.outer(-1.0, lam, x, grad)                          # -lambda xᵀ
             if m < n:
                 w, _, _ = pt.cta(x.contiguous(), **opts)           # (A Aᵀ)^{-1} b
-                resid = (g - plan.matvec(lam, transpose=True)).contiguous()   # g - Aᵀ lambda
+                resid = plan.residual(lam, g.contiguous(), transpose=True)   # g - Aᵀ lambda
                 plan.outer(1.0, w, resid, grad)
         finally:
             pt.close()

@@ -1715,6 +1715,30 @@ tacta_status tacta_plan_matvec(tacta_plan plan, int32_t transpose, const double*
     return TACTA_OK;
 }
 
+tacta_status tacta_plan_residual(tacta_plan plan, int32_t transpose, const double* x, const double* b, double* r,
+                                 const tacta_options* opt) {
+    set_error("");
+    if (!plan || !plan->p || !x || !b || !r) { set_error("NULL argument"); return TACTA_ERR_INVALID; }
+    Plan* p = plan->p;
+    Opts O = resolve(opt);
+    CUDA_TRY(cudaSetDevice(p->device));
+    const DevOperand& A = transpose ? p->At : p->A;
+    const int64_t in_len = A.cols(), out_len = A.rows();
+    // x through a padded plan buffer (the staged kernels read 16-byte-rounded windows), b
+    // through another (max(m, n) long)
+    double* xin = transpose ? p->tmp_m : p->tmp_n;
+    double* yout = transpose ? p->tmp_n : p->tmp_m;
+    CUDA_TRY(cudaMemcpyAsync(xin, x, sizeof(double) * in_len, cudaMemcpyDefault, O.s));
+    CUDA_TRY(cudaMemcpyAsync(p->v, b, sizeof(double) * out_len, cudaMemcpyDefault, O.s));
+    int64_t launches = 0;
+    LaunchCtx L{O.s, p->ctl, p->partials, p->grid, &launches};
+    CUDA_TRY(launch_spmv(L, A, xin, yout, EPI_RESID, EpiArgs{p->v, nullptr, nullptr},
+                         FinArgs{FIN_NONE, 0, nullptr}, GATE_FORCE));
+    CUDA_TRY(cudaMemcpyAsync(r, yout, sizeof(double) * out_len, cudaMemcpyDefault, O.s));
+    CUDA_TRY(cudaStreamSynchronize(O.s));
+    return TACTA_OK;
+}
+
 tacta_status tacta_plan_outer(tacta_plan plan, double alpha, const double* u, const double* v, double* out,
                               const tacta_options* opt) {
     set_error("");

@@ -120,3 +120,32 @@ def test_cta_trajectory_per_variant(tacta, name):
     assert info["iters"] == ref.iters and info["matvecs"] == ref.matvecs
     assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
     np.testing.assert_allclose(hist.cpu().numpy(), ref.hist, rtol=1e-8)
+
+
+@pytest.mark.parametrize("kind", ["csr", "dense"])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_plan_residual(kind, transpose):
+    """tacta_plan_residual: b - A x and b - Aᵀ x through the product kernels' residual
+    epilogue, entry by entry against the host's FP64 within k u (|b| + |A||x|)."""
+    import torch
+    import paper_2304_12168_gb300 as tacta
+    tacta.load_library()
+    rng = np.random.default_rng(21)
+    m, n = 300, 170
+    D = rng.standard_normal((m, n)) * (rng.random((m, n)) < (0.08 if kind == "csr" else 1.0))
+    S = sp.csr_matrix(D)
+    dev = torch.device("cuda:0")
+    if kind == "csr":
+        A = tacta.CSR(torch.from_numpy(S.indptr.astype(np.int32)).to(dev), torch.from_numpy(S.indices.astype(np.int32)).to(dev),
+                      torch.from_numpy(S.data).to(dev), (m, n))
+    else:
+        A = torch.from_numpy(D).to(dev)
+    plan = tacta.Plan(A)
+    M = D.T if transpose else D
+    x = rng.standard_normal(M.shape[1])
+    b = rng.standard_normal(M.shape[0])
+    r = plan.residual(torch.from_numpy(x).to(dev), torch.from_numpy(b).to(dev), transpose=transpose).cpu().numpy()
+    plan.close()
+    ref = b - M @ x
+    bound = (M.shape[1] + 1) * 2.0 ** -53 * (np.abs(b) + np.abs(M) @ np.abs(x))
+    assert np.all(np.abs(r - ref) <= bound)
