@@ -352,10 +352,14 @@ tacta_status tacta_batch_cta(tacta_batch batch, const double* b, double* x, int3
    the chain's products on the tensor cores (BF16 tiles, mma.sync m16n8k16 with FP32
    accumulation, the FP32 chain vectors carried exactly as three BF16 terms): it admits
    BF16 storage with n_s <= 1024 only (other batches: TACTA_ERR_INVALID from
-   tacta_batch_cta, skipped by the autotuner). */
+   tacta_batch_cta, skipped by the autotuner). tacta_batch_config_stage_bytes(c) is the
+   ring stage of the fused-pass configurations (the tile of rows of A_s that a pass takes
+   at a time: 16, 32 or 48 KB on CUDA cores, 40 or 48 KB on the tensor cores; 0 for the
+   others), so the autotuner searches tile sizes as well as launch shapes. */
 int32_t tacta_batch_num_configs(void);
 tacta_status tacta_batch_config_shape(int32_t config, int32_t* threads, int32_t* blocks_per_sm);
 int32_t tacta_batch_config_tensor_cores(int32_t config);
+int32_t tacta_batch_config_stage_bytes(int32_t config);
 tacta_status tacta_batch_tune(tacta_batch batch, const double* b, const tacta_options* opt,
                               int32_t* best_config, double* best_ms);
 tacta_status tacta_batch_set_config(tacta_batch batch, int32_t config);

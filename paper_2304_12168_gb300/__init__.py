@@ -70,7 +70,7 @@ EXPORTS = ["tacta_default_options", "cta_solve", "ta_solve", "ta_minnorm", "tact
            "tacta_residual_static", "tacta_last_error", "tacta_version",
            "tacta_batch_create", "tacta_batch_cta", "tacta_batch_destroy", "tacta_batch_tune",
            "tacta_batch_set_config", "tacta_batch_num_configs", "tacta_batch_config_shape",
-           "tacta_batch_last_error", "tacta_batch_timeline", "tacta_batch_config_tensor_cores", "tacta_aux_solve", "tacta_dia_tile_plan", "tacta_column_partition"]
+           "tacta_batch_last_error", "tacta_batch_timeline", "tacta_batch_config_tensor_cores", "tacta_batch_config_stage_bytes", "tacta_aux_solve", "tacta_dia_tile_plan", "tacta_column_partition"]
 
 _lib_handle = None
 
@@ -127,6 +127,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tacta_batch_tune.argtypes = [vp, dp, P(tacta_options), i32p, P(ctypes.c_double)]
     lib.tacta_batch_config_tensor_cores.argtypes = [ctypes.c_int32]
     lib.tacta_batch_config_tensor_cores.restype = ctypes.c_int32
+    lib.tacta_batch_config_stage_bytes.argtypes = [ctypes.c_int32]
+    lib.tacta_batch_config_stage_bytes.restype = ctypes.c_int32
     lib.tacta_batch_timeline.argtypes = [vp, vp, vp]
     lib.tacta_batch_timeline.restype = ctypes.c_int32
     lib.tacta_batch_tune.restype = ctypes.c_int32
@@ -538,13 +540,14 @@ class Batch:
 
     @staticmethod
     def configs():
-        """[(threads per block, blocks per SM)] of the launch configurations."""
+        """[(threads per block, blocks per SM, ring stage bytes)] of the launch configurations
+        (the stage is 0 for the configurations without the bulk-copy ring)."""
         lib = load_library()
         out = []
         for c in range(lib.tacta_batch_num_configs()):
             t, p = ctypes.c_int32(), ctypes.c_int32()
             _check_batch(lib.tacta_batch_config_shape(c, ctypes.byref(t), ctypes.byref(p)))
-            out.append((t.value, p.value))
+            out.append((t.value, p.value, int(lib.tacta_batch_config_stage_bytes(c))))
         return out
 
     @staticmethod

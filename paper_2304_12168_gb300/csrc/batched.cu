@@ -84,6 +84,8 @@ struct BatchParams {
     double tol2, tol_n2, pivot_tol, eta2;
     int32_t max_iter, R, t_max, cycle;
     int32_t m_cap, n_cap;  // vector capacities (multiples of 8: every vector starts 16-byte aligned)
+    int32_t stage_bytes;   // streamed kernel: bytes of a ring stage (the autotuner's tile size)
+    int32_t pad_;
     int64_t a_cap;         // elements of A a block can stage in shared memory
     int64_t area_bytes;    // streamed kernel: bytes of the A area (ring, or A when resident)
 };
@@ -546,7 +548,7 @@ batch_cta(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, in
 // only at iteration boundaries, after the producer has issued the iteration's chunks.
 // Requires ceil(n / V) <= 32 JV for every system (the accumulators live in registers).
 
-constexpr int kChunkBytes = 32 * 1024;
+constexpr int kChunkBytes = 32 * 1024;   // default ring stage of the CUDA-core passes
 constexpr int kRing = 3;
 
 template <int NT>
@@ -578,9 +580,10 @@ __device__ __forceinline__ double2 consumer_sum2(SqAcc<TC> a, bool a_lane0, SqAc
 }
 
 struct Ring {
-    unsigned char* area;   // kRing stages of kChunkBytes
+    unsigned char* area;   // kRing stages of `stage` bytes
     uint64_t* full;
     uint64_t* empty;
+    int stage;
 };
 
 // chain-vector values at V consecutive columns (16-byte aligned shared memory)
@@ -643,7 +646,7 @@ __device__ bool fused_pass(const TA* Ares, bool resident, const Ring& ring, uint
         } else {
             k = (int)(qseq % kRing);
             if (ok) ok = mbar_wait_bounded(&ring.full[k], (qseq / kRing) & 1u);
-            chunk = reinterpret_cast<const TA*>(ring.area + (size_t)k * kChunkBytes);
+            chunk = reinterpret_cast<const TA*>(ring.area + (size_t)k * ring.stage);
         }
         const int row0 = c * R, rows = min(R, m - row0);
         if (ok) {
@@ -769,7 +772,7 @@ __device__ bool fused_pass(const TA* Ares, bool resident, const Ring& ring, uint
 // The stored row length ld is 8 (mod 16) elements, so the eight rows an ldmatrix reads
 // fall in distinct bank groups.
 
-constexpr int kMmaStageBytes = 40 * 1024;
+constexpr int kMmaStageBytes = 40 * 1024;   // default ring stage of the tensor-core passes
 
 struct MmaGeo {
     int KT;      // 16-column tiles of a row
@@ -781,7 +784,7 @@ struct MmaGeo {
     int R;       // rows per chunk (multiple of 16)
 };
 
-__host__ __device__ inline MmaGeo mma_geo(int n, int ld, int NW) {
+__host__ __device__ inline MmaGeo mma_geo(int n, int ld, int NW, int stage) {
     MmaGeo g{};
     g.KT = (n + 15) / 16;
     if (g.KT <= 8) {
@@ -797,10 +800,10 @@ __host__ __device__ inline MmaGeo mma_geo(int n, int ld, int NW) {
     g.SB = 8 / g.KGT;
     const int row_bytes = ld * 2;
     const int round_rows = 16 * g.NL * g.SB;
-    if (round_rows * row_bytes <= kMmaStageBytes) {
-        g.R = (kMmaStageBytes / (round_rows * row_bytes)) * round_rows;
+    if (round_rows * row_bytes <= stage) {
+        g.R = (stage / (round_rows * row_bytes)) * round_rows;
     } else {
-        g.R = (kMmaStageBytes / (16 * row_bytes)) * 16;
+        g.R = (stage / (16 * row_bytes)) * 16;
     }
     return g;
 }
@@ -880,7 +883,7 @@ __device__ bool mma_pass(const __nv_bfloat16* Ares, bool resident, const Ring& r
         } else {
             k = (int)(qseq % kRing);
             if (ok) ok = mbar_wait_bounded(&ring.full[k], (qseq / kRing) & 1u);
-            chunk = reinterpret_cast<const __nv_bfloat16*>(ring.area + (size_t)k * kMmaStageBytes);
+            chunk = reinterpret_cast<const __nv_bfloat16*>(ring.area + (size_t)k * ring.stage);
         }
         const int row0 = c * G.R, rows = min(G.R, m - row0);
         const int RBc = (rows + 15) / 16;
@@ -1055,10 +1058,10 @@ batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
     TC* dx = z + (int64_t)P.t_max * P.n_cap;         // n_cap
     TC* part = dx + P.n_cap;                         // NW x n_cap
     float* exch = reinterpret_cast<float*>(part + (int64_t)NW * P.n_cap);   // MMA: 2 x 16 NW x 8
-    constexpr int kStage = MMA ? kMmaStageBytes : kChunkBytes;
+    const int kStage = P.stage_bytes;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool producer = warp == NW;
-    const Ring ring{smem_raw, full, empty};
+    const Ring ring{smem_raw, full, empty, P.stage_bytes};
     if (tid == 0) {
         for (int k = 0; k < kRing; ++k) {
             mbar_init(&full[k], 1);
@@ -1090,10 +1093,10 @@ batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
         const double* A64 = a64 + d.a64;
         const TA* Ag = alo + d.a_lo;
         const int64_t row_bytes = (int64_t)ld * (int64_t)sizeof(TA);
-        const MmaGeo G = MMA ? mma_geo(n, ld, NW) : MmaGeo{};
+        const MmaGeo G = MMA ? mma_geo(n, ld, NW, kStage) : MmaGeo{};
         // CUDA-core chunks: a multiple of the 2 NW rows the consumer warps take per round
         // when the stage holds that many, so that no warp takes an extra round per chunk
-        const int64_t fit = max((int64_t)1, (int64_t)kChunkBytes / row_bytes);
+        const int64_t fit = max((int64_t)1, (int64_t)kStage / row_bytes);
         const int R = MMA ? G.R : (int)(fit >= 2 * NW ? fit / (2 * NW) * (2 * NW) : fit);
         const int nch = (m + R - 1) / R;
         // (the tensor-core pass reads whole 16-row blocks)
@@ -1326,10 +1329,12 @@ struct Config {
     int per_sm;        // resident blocks per SM
     bool streamed;     // batch_cta_s (fused passes, bulk-copy ring) instead of batch_cta
     bool mma;          // batch_cta_s with the BF16 tensor-core passes (BF16 storage only)
+    int stage_kb;      // streamed: KB per ring stage (the tile of rows a pass takes at a time)
 };
-constexpr Config kConfigs[] = {{128, 2, false, false}, {128, 4, false, false}, {256, 1, false, false},
-                               {256, 2, false, false}, {512, 1, false, false}, {256, 1, true, false},
-                               {256, 1, true, true}};
+constexpr Config kConfigs[] = {{128, 2, false, false, 0}, {128, 4, false, false, 0}, {256, 1, false, false, 0},
+                               {256, 2, false, false, 0}, {512, 1, false, false, 0}, {256, 1, true, false, 32},
+                               {256, 1, true, true, 40},  {256, 1, true, false, 16}, {256, 1, true, false, 48},
+                               {256, 1, true, true, 48}};
 constexpr int kDefaultConfig = 3;
 constexpr int kStreamNW = 8;
 // vectors of a row each lane holds in registers (FP64 2, FP32 4, BF16 8 values each):
@@ -1381,10 +1386,13 @@ cudaError_t launch_cfg(int cfg, cudaStream_t s, int grid, size_t smem, const Sys
     const TA* a = reinterpret_cast<const TA*>(alo);
     switch (cfg) {
     case 5:
+    case 7:
+    case 8:
         batch_cta_s<TA, kStreamNW, stream_jv<TA>(), false><<<grid, kStreamNW * 32 + 32, smem, s>>>(
             sys, order, count, a, a64, b, x, o, queue, P, fail_flag);
         break;
     case 6:
+    case 9:
         if constexpr (std::is_same_v<TA, __nv_bfloat16>) {
             batch_cta_s<TA, kStreamNW, stream_jv<TA>(), true><<<grid, kStreamNW * 32 + 32, smem, s>>>(
                 sys, order, count, a, a64, b, x, o, queue, P, fail_flag);
@@ -1487,7 +1495,9 @@ bool make_params(const tacta_batch_s* B, const tacta_options& o, int cfg, BatchP
         const int64_t exch = C.mma ? 2 * 16 * kStreamNW * 8 : 0;
         const int64_t vb = (chain + part + exch) * tc;
         const int64_t area = ((per_block - vb) / 16) * 16;
-        if (area < (int64_t)kRing * (C.mma ? kMmaStageBytes : kChunkBytes)) return false;
+        const int64_t stage = (int64_t)C.stage_kb * 1024;
+        if (area < (int64_t)kRing * stage) return false;
+        P.stage_bytes = (int32_t)stage;
         P.area_bytes = area;
         P.a_cap = 0;
         *smem_out = (size_t)(area + vb);
@@ -1663,6 +1673,10 @@ extern "C" int32_t tacta_batch_num_configs(void) { return kNumConfigs; }
 
 extern "C" int32_t tacta_batch_config_tensor_cores(int32_t config) {
     return config >= 0 && config < kNumConfigs && kConfigs[config].mma ? 1 : 0;
+}
+
+extern "C" int32_t tacta_batch_config_stage_bytes(int32_t config) {
+    return config >= 0 && config < kNumConfigs ? kConfigs[config].stage_kb * 1024 : 0;
 }
 
 extern "C" tacta_status tacta_batch_timeline(tacta_batch B, int64_t* t_begin_ns, int64_t* t_end_ns) {
