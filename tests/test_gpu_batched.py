@@ -233,3 +233,26 @@ def test_full_batch_4096_fp32(tacta):
         well = (n >= 1.5 * rank) if B0.low_rank[s] else (n / m >= 1.25 or n / m <= 0.8)
         assert not well, (s, m, n, bool(B0.low_rank[s]), names[s], rel[s])
     assert names.count("RESIDUAL") >= 0.98 * len(names)
+
+
+def test_timeline_and_stage_configs(tacta):
+    """The batch timeline: every system of the last solve has a start and an end stamp on
+    the device clock with end >= start; the fused-pass configurations report their ring
+    stages (16/32/48 KB on CUDA cores, 40/48 KB on the tensor cores) and every
+    configuration meets the tolerance on a BF16 batch."""
+    mats, bs, _ = small_batch(8, 24, m_range=(40, 160), aspect=(1.4, 2.0))
+    b = np.concatenate(bs)
+    B = tacta.Batch(mats, storage=tacta.BATCH_BF16)
+    x, iters, rel, reason = B.cta(b, tol=1e-8, tol_normal=0.0, max_iter=5000)
+    tb, te = B.timeline()
+    assert tb.shape == te.shape == (len(mats),)
+    assert np.all(tb > 0) and np.all(te >= tb)
+    stages = [c[2] for c in tacta.Batch.configs()]
+    tc = tacta.Batch.tensor_core_configs()
+    assert sorted(s for i, s in enumerate(stages) if s and i not in tc) == [16384, 32768, 49152]
+    assert sorted(stages[i] for i in tc) == [40960, 49152]
+    for c in range(len(stages)):
+        B.set_config(c)
+        _, _, rc, rs = B.cta(b, tol=1e-8, tol_normal=0.0, max_iter=5000)
+        assert all(tacta.REASON[int(r)] == "RESIDUAL" for r in rs) and np.all(rc <= 1e-8 * (1 + 1e-6)), c
+    B.close()
