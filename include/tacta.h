@@ -302,7 +302,9 @@ tacta_status tacta_residual_static(const tacta_matrix* A, const double* x, const
  *   from x_s = 0, so that x_s stays in range(A_sᵀ) (Thm. thmone (4)) and a consistent
  *   rank-deficient system yields the minimum-norm solution. All systems run in one
  *   persistent kernel launch (replayed as a CUDA graph when opt->use_graph is set):
- *   each thread block takes the next unsolved system from a queue, largest first.
+ *   each thread block takes the next unsolved system from a queue, ordered longest
+ *   first by the previous solve's measured time per system (the first solve: largest
+ *   m_s n_s first), so the slowest systems start at once and short ones fill the tail.
  *   The paper treats one system at a time; batching is this library's extension.
  *
  *   Storage of the copy of A_s that the chain z_i = Aᵀ u_{i-1}, u_i = A z_i reads:

@@ -1,6 +1,7 @@
 // Batched dense CTA: many independent systems A_s x_s = b_s in one persistent launch.
 //
-// Each block takes the next unsolved system from a queue (largest first) and runs
+// Each block takes the next unsolved system from a queue (longest first by the previous
+// solve's measured time per system; largest first on the first solve) and runs
 // CTA (Alg. 1.1 with H = A_s A_sᵀ, Eqs. CTAGEN7/CTAGEN7A, auxiliary equation
 // Eq. eqcoeff) on it to its own stop, then takes the next one. The chain
 // z_i = Aᵀ u_{i-1}, u_i = A z_i runs in the storage precision's arithmetic (FP64,
@@ -1751,6 +1752,23 @@ extern "C" tacta_status tacta_batch_cta(tacta_batch B, const double* b, double* 
     if (timed_out) {
         g_batch_err = "a wait in the batched kernel gave up (systems reported with reason TIMEOUT)";
         return TACTA_ERR_TIMEOUT;
+    }
+    // The next solve takes the systems longest first by this solve's measured time per
+    // system (the timeline): the longest starts at once and the short ones fill the tail.
+    // (A system's result does not depend on the block or the moment that takes it.)
+    if (B->count > 1) {
+        std::vector<int64_t> st((size_t)2 * B->count);
+        BTRY(cudaMemcpyAsync(st.data(), B->stamps, sizeof(int64_t) * 2 * B->count, cudaMemcpyDeviceToHost, s));
+        BTRY(cudaStreamSynchronize(s));
+        std::vector<int32_t> ord((size_t)B->count);
+        std::iota(ord.begin(), ord.end(), 0);
+        const int64_t* tb = st.data();
+        const int64_t* te = st.data() + B->count;
+        std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t c) {
+            return te[a] - tb[a] > te[c] - tb[c];
+        });
+        BTRY(cudaMemcpyAsync(B->order, ord.data(), sizeof(int32_t) * B->count, cudaMemcpyHostToDevice, s));
+        BTRY(cudaStreamSynchronize(s));
     }
     return TACTA_OK;
 }
