@@ -348,9 +348,12 @@ tacta_status tacta_batch_cta(tacta_batch batch, const double* b, double* x, int3
                              double* rel_res, int32_t* reason, const tacta_options* opt);
 
 /* Launch configurations: threads per block and resident blocks per SM. The autotuner
-   times every configuration that fits on (batch, b) with the given options, keeps the
-   fastest for later solves and returns its index and time; set_config picks one
-   (-1: the default). tacta_batch_config_tensor_cores(c) is 1 when configuration c runs
+   times every configuration that fits on (batch, b) with the given options (max_iter caps
+   each system's steps), keeps the best for later solves and returns its index and score
+   (ms): before any full solve the capped run's time; after one, the time of a full solve
+   that the capped run predicts -- the largest over the systems of its time per step times
+   its step count in the last full solve (a batch takes its slowest system's time).
+   set_config picks one (-1: the default). tacta_batch_config_tensor_cores(c) is 1 when configuration c runs
    the chain's products on the tensor cores (BF16 tiles, mma.sync m16n8k16 with FP32
    accumulation, the FP32 chain vectors carried exactly as three BF16 terms): it admits
    BF16 storage with n_s <= 1024 only (other batches: TACTA_ERR_INVALID from

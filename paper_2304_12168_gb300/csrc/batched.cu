@@ -1434,6 +1434,7 @@ struct tacta_batch_s {
     double* rel = nullptr;
     int32_t* queue = nullptr;
     int64_t* stamps = nullptr;     // 2 x count: per-system begin and end clocks of the last solve
+    std::vector<int32_t> last_iters;   // host: every system's step count in the last full solve
     int config = -1;               // index into kConfigs (-1: default)
     cudaGraphExec_t graph = nullptr;
     int graph_key = -1;
@@ -1755,7 +1756,10 @@ extern "C" tacta_status tacta_batch_cta(tacta_batch B, const double* b, double* 
     }
     // The next solve takes the systems longest first by this solve's measured time per
     // system (the timeline): the longest starts at once and the short ones fill the tail.
-    // (A system's result does not depend on the block or the moment that takes it.)
+    // (A system's result does not depend on the block or the moment that takes it.) The
+    // step counts stay on the host for the autotuner's makespan estimate.
+    B->last_iters.resize((size_t)B->count);
+    BTRY(cudaMemcpy(B->last_iters.data(), B->iters, sizeof(int32_t) * B->count, cudaMemcpyDeviceToHost));
     if (B->count > 1) {
         std::vector<int64_t> st((size_t)2 * B->count);
         BTRY(cudaMemcpyAsync(st.data(), B->stamps, sizeof(int64_t) * 2 * B->count, cudaMemcpyDeviceToHost, s));
@@ -1774,7 +1778,12 @@ extern "C" tacta_status tacta_batch_cta(tacta_batch B, const double* b, double* 
 }
 
 // Autotuner: times every launch configuration on the batch (each solve capped at
-// max_iter of the given options, graphs off), keeps the fastest, and returns it.
+// max_iter of the given options, graphs off), keeps the best, and returns it. Before any
+// full solve the score is the capped run's time; after one, it is the makespan the capped
+// run predicts for a full solve in the learned queue order: the largest, over the systems,
+// of the system's time per step in the capped run times its step count in the last full
+// solve (the batch takes its slowest system's time, and how a system shares its SM with
+// other blocks depends on the launch shape).
 extern "C" tacta_status tacta_batch_tune(tacta_batch B, const double* b, const tacta_options* opt,
                                          int32_t* best_config, double* best_ms) {
     g_batch_err.clear();
@@ -1801,7 +1810,22 @@ extern "C" tacta_status tacta_batch_tune(tacta_batch B, const double* b, const t
                  cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
                  cudaEventElapsedTime(&tc, e0, e1) == cudaSuccess;
         }
-        if (ok && (best < 0 || tc < best_t)) { best = c; best_t = tc; }
+        float score = tc;
+        if (ok && B->last_iters.size() == (size_t)B->count) {
+            std::vector<int64_t> st((size_t)2 * B->count);
+            std::vector<int32_t> it((size_t)B->count);
+            ok = cudaMemcpy(st.data(), B->stamps, sizeof(int64_t) * 2 * B->count, cudaMemcpyDeviceToHost) ==
+                     cudaSuccess &&
+                 cudaMemcpy(it.data(), B->iters, sizeof(int32_t) * B->count, cudaMemcpyDeviceToHost) == cudaSuccess;
+            double worst = 0.0;
+            for (int32_t q = 0; ok && q < B->count; ++q) {
+                if (it[q] <= 0) continue;
+                const double per_step = (double)(st[(size_t)B->count + q] - st[q]) / it[q];
+                worst = std::max(worst, per_step * std::max<int32_t>(B->last_iters[q], it[q]));
+            }
+            if (ok && worst > 0.0) score = (float)(worst * 1e-6);
+        }
+        if (ok && (best < 0 || score < best_t)) { best = c; best_t = score; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
