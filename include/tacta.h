@@ -376,6 +376,42 @@ tacta_status tacta_batch_set_config(tacta_batch batch, int32_t config);
    given time, how many blocks are still busy in the launch's tail -- follows from them.
    Synchronous. */
 tacta_status tacta_batch_timeline(tacta_batch batch, int64_t* t_begin_ns, int64_t* t_end_ns);
+/* tacta_batch_set_wide -- thread-block clusters for the longest systems. A batch takes
+   its slowest system's time, and a system that needs the whole step budget keeps one
+   block busy long after the others have finished. A cluster of C blocks (one per SM)
+   solves such a system together: each block holds ceil(m_s / C) rows of A_s, the
+   partial products Aᵀu are added across the cluster through distributed shared memory,
+   the moments and norms are block partials added in rank order (every block takes the
+   same FP64 decisions). The clusters start first and the single-block kernel takes the
+   other systems on the remaining SMs and on each SM a cluster leaves.
+     systems -1 (default): planned before each solve from the measured times of the
+                earlier solves (none before the first): the share of least simulated
+                makespan (tacta_batch_wide_plan);
+     systems 0: off;
+     systems > 0: that many systems from the head of the queue order (longest first by
+                the last solve; largest m_s n_s first before any), on clusters of
+                `cluster` blocks (1..8; 0: the largest of 8, 4, 2, 1 whose vectors fit
+                a block's shared memory), `clusters` clusters (0: one per system, at most
+                as many as can be resident).
+   A system a cluster solves runs the same iteration with its sums in another order:
+   its bits may differ from a one-block solve, within the same tolerances. */
+tacta_status tacta_batch_set_wide(tacta_batch batch, int32_t systems, int32_t cluster, int32_t clusters);
+/* tacta_batch_wide_plan -- the clusters' share that the next tacta_batch_cta with these
+   options would use (systems 0: none) and its predicted makespan in ms (0 while no
+   solve has measured the systems' times). Any output may be NULL. */
+tacta_status tacta_batch_wide_plan(tacta_batch batch, const tacta_options* opt, int32_t* systems, int32_t* cluster,
+                                   int32_t* clusters, double* predicted_ms);
+/* tacta_batch_simulate_makespan -- the planner's schedule model, on the host (no device
+   needed): nw cluster jobs of times w take `clusters` clusters of `cluster` SMs, each job
+   the next cluster to be free (longest first); nd one-block jobs of times d take per_sm
+   blocks on every SM no cluster holds from time 0 and on a cluster's SMs from the time
+   it has finished, each job the next block to be free (longest first; past the 512
+   longest, the rest spread as a fluid over the blocks' free times). Returns the time
+   the last job ends, in the unit of w and d; -1 on invalid arguments (a negative count,
+   a negative or NaN time, clusters x cluster > sms, a NULL array with a nonzero count,
+   cluster jobs without clusters). */
+double tacta_batch_simulate_makespan(const double* w, int32_t nw, int32_t clusters, int32_t cluster, const double* d,
+                                     int32_t nd, int32_t sms, int32_t per_sm);
 void tacta_batch_destroy(tacta_batch batch);
 /* message of the last failed tacta_batch_* call on the calling thread */
 const char* tacta_batch_last_error(void);

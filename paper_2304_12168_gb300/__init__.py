@@ -70,7 +70,8 @@ EXPORTS = ["tacta_default_options", "cta_solve", "ta_solve", "ta_minnorm", "tact
            "tacta_residual_static", "tacta_last_error", "tacta_version",
            "tacta_batch_create", "tacta_batch_cta", "tacta_batch_destroy", "tacta_batch_tune",
            "tacta_batch_set_config", "tacta_batch_num_configs", "tacta_batch_config_shape",
-           "tacta_batch_last_error", "tacta_batch_timeline", "tacta_batch_config_tensor_cores", "tacta_batch_config_stage_bytes", "tacta_aux_solve", "tacta_dia_tile_plan", "tacta_column_partition"]
+           "tacta_batch_last_error", "tacta_batch_timeline", "tacta_batch_config_tensor_cores", "tacta_batch_config_stage_bytes", "tacta_batch_set_wide",
+           "tacta_batch_wide_plan", "tacta_batch_simulate_makespan", "tacta_aux_solve", "tacta_dia_tile_plan", "tacta_column_partition"]
 
 _lib_handle = None
 
@@ -134,6 +135,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tacta_batch_tune.restype = ctypes.c_int32
     lib.tacta_batch_set_config.argtypes = [vp, ctypes.c_int32]
     lib.tacta_batch_set_config.restype = ctypes.c_int32
+    lib.tacta_batch_set_wide.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    lib.tacta_batch_set_wide.restype = ctypes.c_int32
+    lib.tacta_batch_wide_plan.argtypes = [vp, P(tacta_options), i32p, i32p, i32p, P(ctypes.c_double)]
+    lib.tacta_batch_wide_plan.restype = ctypes.c_int32
+    lib.tacta_batch_simulate_makespan.argtypes = [dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, dp,
+                                                  ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    lib.tacta_batch_simulate_makespan.restype = ctypes.c_double
     lib.tacta_batch_num_configs.argtypes = []
     lib.tacta_batch_num_configs.restype = ctypes.c_int32
     lib.tacta_batch_config_shape.argtypes = [ctypes.c_int32, i32p, i32p]
@@ -530,9 +538,34 @@ class Batch:
     def set_config(self, config: int):
         _check_batch(load_library().tacta_batch_set_config(self._h, int(config)))
 
+    def set_wide(self, systems: int = -1, cluster: int = 0, clusters: int = 0):
+        """Thread-block clusters for the longest systems (tacta_batch_set_wide): systems -1
+        planned from the earlier solves' measured times, 0 off, > 0 that many systems from
+        the head of the queue order on `clusters` clusters of `cluster` blocks (0: chosen)."""
+        _check_batch(load_library().tacta_batch_set_wide(self._h, int(systems), int(cluster), int(clusters)))
+
+    def wide_plan(self, **opts):
+        """(systems, cluster, clusters, predicted_ms) the next solve with these options would
+        use (tacta_batch_wide_plan)."""
+        o = make_options(False, **opts)
+        v = [ctypes.c_int32() for _ in range(3)]
+        ms = ctypes.c_double()
+        _check_batch(load_library().tacta_batch_wide_plan(self._h, ctypes.byref(o), *[ctypes.byref(a) for a in v],
+                                                          ctypes.byref(ms)))
+        return v[0].value, v[1].value, v[2].value, float(ms.value)
+
+    @staticmethod
+    def simulate_makespan(w, clusters, cluster, d, sms, per_sm):
+        """The planner's schedule model (tacta_batch_simulate_makespan; host only)."""
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        return float(load_library().tacta_batch_simulate_makespan(
+            w.ctypes.data if w.size else None, int(w.size), int(clusters), int(cluster),
+            d.ctypes.data if d.size else None, int(d.size), int(sms), int(per_sm)))
+
     def timeline(self):
         """(t_begin, t_end): int64 device-clock nanoseconds at which each system of the last
-        solve was taken by a block and finished (tacta_batch_timeline)."""
+        solve was taken by a block (or cluster) and finished (tacta_batch_timeline)."""
         tb = np.zeros(self.count, dtype=np.int64)
         te = np.zeros(self.count, dtype=np.int64)
         _check_batch(load_library().tacta_batch_timeline(self._h, tb.ctypes.data, te.ctypes.data))

@@ -17,6 +17,7 @@
 // (exact in binary arithmetic).
 //
 // The paper solves one system at a time; batching is this library's extension.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -25,6 +26,7 @@
 #include <cstring>
 #include <mutex>
 #include <numeric>
+#include <queue>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -32,6 +34,8 @@
 #include "hankel.cuh"
 #include "internal.h"
 #include "mbarrier.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace tacta {
 namespace {
@@ -530,6 +534,10 @@ batch_cta(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, in
         }
         __syncthreads();   // the next system may reuse every buffer
     }
+    // launched after the cluster kernel (programmatic dependent launch): finish no
+    // earlier than it, so that the stream's next operation sees every system solved
+    // (returns at once when there is no such dependency)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ------------------------------------------------------------------ streamed, fused kernel
@@ -1273,6 +1281,263 @@ batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
         for (uint32_t qq = first; qq < qseq; ++qq) mbar_wait_bounded(&full[qq % kRing], (qq / kRing) & 1u);
         mbar_wait_bounded(&loaded, loaded_phase ^ 1u);
     }
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // as in batch_cta
+}
+
+// ------------------------------------------------------------------ cluster kernel for the longest systems
+//
+// A batch takes its slowest system's time: a system that needs the whole step budget
+// runs for seconds on one block long after every other block has finished. Here the
+// C blocks of a thread-block cluster (C = 2, 4 or 8, one block per SM) solve one such
+// system together, with the same iteration as batch_cta:
+//   * block c keeps rows [c mb, c mb + mb) of A_s (mb = ceil(m / C)), staged in its
+//     shared memory when they fit, and the same rows of r and of every u_i;
+//   * z_i = Aᵀ u_{i-1} / s: every block forms the partial product over its rows; a
+//     cluster barrier publishes the partials, and every block adds all C of them in
+//     rank order through distributed shared memory, so all blocks hold the same bits
+//     of the whole z_i (the partials are double-buffered: one barrier per product);
+//   * u_i = A z_i / s: each block its own rows, from its copy of z_i;
+//   * the moments, ||r||² and the FP64 residual's norm are block partials that the
+//     blocks publish and add in rank order, so every block holds the same FP64 values
+//     and takes the same auxiliary solve and stop tests: every branch that encloses a
+//     cluster barrier depends on those shared values only;
+//   * x is updated in column slices (block c: columns [c nc, c nc + nc)); the FP64
+//     residual b - A x reads the whole x from global memory after a fence and a
+//     cluster barrier.
+// Every block signals the dependent launch (the single-block kernel that takes the
+// other systems) as soon as it starts, so that the clusters are placed first and that
+// kernel's blocks fill the remaining SMs, and each SM a cluster leaves.
+constexpr int kWideNT = 512;
+constexpr int kWideMaxC = 8;
+
+struct WideShared {
+    double slot[2][2 * kTMax + 2];   // this block's published partial sums (two sets)
+    double sum[2 * kTMax + 2];       // the cluster's sums of the last published set
+    int32_t q;                       // the system the cluster took (rank 0 writes every block's copy)
+};
+
+template <class TA>
+__global__ void __launch_bounds__(kWideNT, 1)
+batch_cta_w(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, int count,
+            const TA* __restrict__ alo, const double* __restrict__ a64, const double* __restrict__ bvec,
+            double* __restrict__ xvec, BatchOut out, int32_t* queue, BatchParams P) {
+    using TC = typename Elem<TA>::TC;
+    constexpr int NT = kWideNT;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks(), cr = (int)cl.block_rank();
+    __shared__ Shared S;
+    __shared__ WideShared W;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TA* As = reinterpret_cast<TA*>(smem_raw);
+    TC* vec = reinterpret_cast<TC*>(smem_raw + ((P.a_cap * (int64_t)sizeof(TA) + 15) & ~(int64_t)15));
+    TC* r = vec;                                     // m_cap (the block's rows)
+    TC* u = r + P.m_cap;                             // t_max x m_cap
+    TC* z = u + (int64_t)P.t_max * P.m_cap;          // t_max x n_cap (whole vectors)
+    TC* zp = z + (int64_t)P.t_max * P.n_cap;         // 2 x n_cap: the published partial products
+    TC* dx = zp + 2 * (int64_t)P.n_cap;              // n_cap (the block's columns are used)
+    TC* part = dx + P.n_cap;                         // NT x V
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int par = 0;      // partial-product buffer of the next product
+    int spar = 0;     // slot set of the next cluster sum
+
+    // W.sum[0, k) = the cluster's sums of the k values every block published in its slot
+    // set spar: warp j adds value j over the blocks by a fixed butterfly (lanes beyond the
+    // cluster hold exact zeros), so every block gets the same bits
+    auto cluster_sums = [&](int k) {
+        cl.sync();
+        for (int j = warp; j < k; j += NT / 32) {
+            double v = 0.0;
+            if (lane < C) v = cl.map_shared_rank(&W.slot[spar][0], lane)[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) W.sum[j] = v;
+        }
+        __syncthreads();
+        spar ^= 1;
+    };
+    // one block total (thread 0's value) published and summed over the cluster
+    auto cluster_total = [&](double v) -> double {
+        if (tid == 0) W.slot[spar][0] = v;
+        cluster_sums(1);
+        return W.sum[0];
+    };
+    // dst = (Aᵀ v) * scale, whole, from the blocks' partial products over their rows;
+    // returns the sum of squares over this block's column slice [c0, c1)
+    auto full_t = [&](const TA* A, int mo, int n, int ld, const TC* v, TC* dst, double scale, int c0,
+                      int c1) -> SqAcc<TC> {
+        TC* mine = zp + (int64_t)par * P.n_cap;
+        prod_t<TA, NT>(A, mo, n, ld, v, mine, part, 1.0);
+        cl.sync();                                   // every block's partial is complete
+        const TC* peer[kWideMaxC];
+#pragma unroll
+        for (int j = 0; j < kWideMaxC; ++j) peer[j] = cl.map_shared_rank(mine, j < C ? j : 0);
+        const TC sc = (TC)scale;
+        SqAcc<TC> sq;
+        for (int c = tid; c < n; c += NT) {
+            TC pv[kWideMaxC];
+#pragma unroll
+            for (int j = 0; j < kWideMaxC; ++j) pv[j] = j < C ? peer[j][c] : (TC)0;
+            TC acc = pv[0];
+#pragma unroll
+            for (int j = 1; j < kWideMaxC; ++j)
+                if (j < C) acc += pv[j];
+            const TC zv = acc * sc;
+            dst[c] = zv;
+            if (c >= c0 && c < c1) sq.add(zv);
+        }
+        __syncthreads();                             // dst complete before it is read
+        par ^= 1;
+        return sq;
+    };
+
+    for (;;) {
+        if (cr == 0 && tid == 0) {
+            const int q = atomicAdd(queue, 1);
+            for (int j = 0; j < C; ++j) *cl.map_shared_rank(&W.q, j) = q;
+        }
+        cl.sync();
+        const int q = W.q;
+        if (q >= count) break;
+        const int s_id = order[q];
+        if (cr == 0 && tid == 0) out.t_beg[s_id] = clock_ns();
+        const SysDesc d = sys[s_id];
+        const int m = d.m, n = d.n, ld = d.ld;
+        const int mb = (m + C - 1) / C, r0 = min(m, cr * mb), mo = min(m, r0 + mb) - r0;
+        const int nc = (n + C - 1) / C, c0 = min(n, cr * nc), c1 = min(n, c0 + nc);
+        const double* b = bvec + d.b_off + r0;
+        double* x = xvec + d.x_off;
+        const double* A64 = a64 + d.a64 + (int64_t)r0 * n;
+        const TA* A = alo + d.a_lo + (int64_t)r0 * ld;
+        const int64_t a_elems = (int64_t)mo * ld;
+        if (a_elems <= P.a_cap) {   // this block's rows in shared memory (16-byte copies)
+            const int64_t nv = a_elems * (int64_t)sizeof(TA) / 16;
+            const uint4* src = reinterpret_cast<const uint4*>(A);
+            uint4* dst = reinterpret_cast<uint4*>(As);
+            for (int64_t i = tid; i < nv; i += NT) dst[i] = __ldg(src + i);
+            A = As;
+        }
+        for (int c = c0 + tid; c < c1; c += NT) __stcg(x + c, 0.0);
+        for (int c = tid; c < P.n_cap; c += NT) dx[c] = 0;
+        for (int i = 0; i < P.t_max; ++i)
+            for (int c = tid; c < P.n_cap; c += NT) z[(int64_t)i * P.n_cap + c] = 0;
+        double bb = 0.0;
+        for (int i = tid; i < mo; i += NT) {
+            r[i] = (TC)b[i];
+            bb = fma(b[i], b[i], bb);
+        }
+        __threadfence();            // x = 0 is in global memory before a block reads it
+        const double bn2 = cluster_total(block_sum2<NT>(bb, 0.0, S.red).x);
+        double nrm_thr = 0.0;
+        if (P.tol_n2 > 0.0 && bn2 > 0.0) {   // ||Aᵀ b||²
+            const SqAcc<TC> mt = full_t(A, mo, n, ld, r, z, 1.0, c0, c1);
+            nrm_thr = P.tol_n2 * cluster_total(block_sum_sq<NT>(mt, SqAcc<TC>{}, S.red).x);
+            for (int c = tid; c < n; c += NT) z[c] = 0;
+        }
+        // fold dx into the block's columns of x, then r = b - A x in FP64 over the block's
+        // rows (the whole x from global memory); returns the cluster's ||r||²
+        auto true_residual = [&]() -> double {
+            for (int c = c0 + tid; c < c1; c += NT) {
+                __stcg(x + c, __ldcg(x + c) + (double)dx[c]);
+                dx[c] = 0;
+            }
+            __threadfence();
+            cl.sync();
+            const double2 rr = residual64<TC, NT>(A64, mo, n, b, x, r);
+            return cluster_total(block_sum2<NT>(rr.x, 0.0, S.red).x);
+        };
+        double rn2 = bn2;
+        bool is_true = true, need_true = false;
+        int k = 0, reason = 0;
+        const double res_thr = P.tol2 * bn2;
+        double ref_thr = P.eta2 * bn2;
+        if (bn2 == 0.0) reason = TACTA_REASON_ZERO_RHS;
+        while (reason == 0) {
+            if (!finite_d(rn2)) { reason = TACTA_REASON_NONFINITE; break; }
+            if (rn2 <= res_thr) {
+                if (is_true) { reason = TACTA_REASON_RESIDUAL; break; }
+                need_true = true;
+            }
+            if (need_true) {
+                rn2 = true_residual();
+                is_true = true;
+                need_true = false;
+                ref_thr = P.eta2 * rn2;
+                continue;
+            }
+            if (k >= P.max_iter) { reason = TACTA_REASON_MAXITER; break; }
+            const int t = schedule_dev(k, P.t_max, P.cycle);
+            // the chain u_0 = r, z_i = Aᵀ u_{i-1} / s, u_i = A z_i / s
+            const TC* uprev = r;
+            for (int i = 1; i <= t; ++i) {
+                TC* zi = z + (int64_t)(i - 1) * P.n_cap;
+                TC* ui = u + (int64_t)(i - 1) * P.m_cap;
+                const SqAcc<TC> p1 = full_t(A, mo, n, ld, uprev, zi, d.inv_s, c0, c1);
+                const SqAcc<TC> p2 = prod_n<TA, NT>(A, mo, n, ld, zi, ui, d.inv_s);
+                const double2 ph = block_sum_sq<NT>(p1, p2, S.red);   // also completes ui
+                if (tid == 0) {
+                    W.slot[spar][2 * i - 2] = ph.x;
+                    W.slot[spar][2 * i - 1] = ph.y;
+                }
+                uprev = ui;
+            }
+            cluster_sums(2 * t);
+            if (tid < 32) {   // the auxiliary solve by one warp of every block (the same bits)
+                if (tid < 2 * t) S.phi[tid + 1] = W.sum[tid];
+                __syncwarp();
+                int st = 0;
+                for (int i = 1; i <= 2 * t; ++i)
+                    if (!finite_d(S.phi[i])) st = TACTA_REASON_NONFINITE;
+                if (st == 0 && S.phi[1] * d.s * d.s <= nrm_thr) st = TACTA_REASON_NORMAL;
+                if (st == 0) {
+                    const int rank = hankel_solve_warp(S.phi, t, P.pivot_tol, S.beta);
+                    if (rank == 0) st = TACTA_REASON_BREAKDOWN;
+                    __syncwarp();
+                    if (tid < t) {
+                        TC* cf = reinterpret_cast<TC*>(S.coef);
+                        cf[tid] = (TC)S.beta[tid];
+                        cf[kTMax + tid] = (TC)(S.beta[tid] * d.inv_s);
+                    }
+                }
+                if (tid == 0) S.stop = st;
+            }
+            __syncthreads();
+            if (S.stop) { reason = S.stop; break; }
+            // dx += s^-1 sum beta_j z_j on the block's columns; r -= sum beta_j u_j on its rows
+            TC bz[kTMax], bu[kTMax];
+            for (int j = 0; j < t; ++j) {
+                bu[j] = reinterpret_cast<const TC*>(S.coef)[j];
+                bz[j] = reinterpret_cast<const TC*>(S.coef)[kTMax + j];
+            }
+            for (int c = c0 + tid; c < c1; c += NT) {
+                TC v = dx[c];
+                for (int j = 0; j < t; ++j) v = fma(bz[j], z[(int64_t)j * P.n_cap + c], v);
+                dx[c] = v;
+            }
+            SqAcc<TC> sq;
+            for (int i = tid; i < mo; i += NT) {
+                TC v = r[i];
+                for (int j = 0; j < t; ++j) v = fma(-bu[j], u[(int64_t)j * P.m_cap + i], v);
+                r[i] = v;
+                sq.add(v);
+            }
+            rn2 = cluster_total(block_sum_sq<NT>(sq, SqAcc<TC>{}, S.red).x);
+            ++k;
+            is_true = false;
+            if (P.R > 0 && k % P.R == 0) need_true = true;
+            else if (P.eta2 > 0.0 && rn2 <= ref_thr) need_true = true;
+        }
+        double rel = 0.0;
+        if (reason != TACTA_REASON_ZERO_RHS) rel = sqrt(true_residual() / bn2);
+        if (cr == 0 && tid == 0) {
+            out.iters[s_id] = k;
+            out.reason[s_id] = reason;
+            out.rel_res[s_id] = rel;
+            out.t_end[s_id] = clock_ns();
+        }
+        __syncthreads();   // the next system may reuse every buffer
+    }
+    cl.sync();   // no block leaves while a peer may still read its shared memory
 }
 
 // ------------------------------------------------------------------ setup kernels
@@ -1343,6 +1608,16 @@ constexpr int kStreamNW = 8;
 template <class TA> constexpr int stream_jv() { return std::is_same_v<TA, __nv_bfloat16> ? 4 : 8; }
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
+// the cluster kernel's share of a solve
+struct WidePlan {
+    int32_t systems = 0;    // the first `systems` entries of the queue order
+    int32_t cluster = 0;    // blocks per cluster
+    int32_t clusters = 0;   // clusters launched
+    bool operator==(const WidePlan& o) const {
+        return systems == o.systems && cluster == o.cluster && clusters == o.clusters;
+    }
+};
+
 template <class TA>
 size_t vec_bytes(const BatchParams& P, int nt) {
     using TC = typename Elem<TA>::TC;
@@ -1367,6 +1642,7 @@ void set_attrs(cudaError_t& attr) {
     set((const void*)batch_cta<TA, 256, 1>);
     set((const void*)batch_cta<TA, 256, 2>);
     set((const void*)batch_cta<TA, 512, 1>);
+    set((const void*)batch_cta_w<TA>);
 }
 
 cudaError_t prepare_kernels() {
@@ -1380,34 +1656,95 @@ cudaError_t prepare_kernels() {
     return attr;
 }
 
+// a launch, optionally as a programmatic dependent of the previous kernel in the stream
+template <class... KArgs, class... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), int grid, int threads, size_t smem, cudaStream_t s, bool pdl,
+                     Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    if (pdl) {
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <class TA>
-cudaError_t launch_cfg(int cfg, cudaStream_t s, int grid, size_t smem, const SysDesc* sys, const int32_t* order,
-                       int count, const void* alo, const double* a64, const double* b, double* x, BatchOut o,
-                       int32_t* queue, const BatchParams& P, int32_t* fail_flag) {
+cudaError_t launch_cfg(int cfg, cudaStream_t s, int grid, size_t smem, bool pdl, const SysDesc* sys,
+                       const int32_t* order, int count, const void* alo, const double* a64, const double* b,
+                       double* x, BatchOut o, int32_t* queue, const BatchParams& P, int32_t* fail_flag) {
     const TA* a = reinterpret_cast<const TA*>(alo);
+    const int stream_threads = kStreamNW * 32 + 32;
     switch (cfg) {
     case 5:
     case 7:
     case 8:
-        batch_cta_s<TA, kStreamNW, stream_jv<TA>(), false><<<grid, kStreamNW * 32 + 32, smem, s>>>(
-            sys, order, count, a, a64, b, x, o, queue, P, fail_flag);
-        break;
+        return launch_k(batch_cta_s<TA, kStreamNW, stream_jv<TA>(), false>, grid, stream_threads, smem, s, pdl, sys,
+                        order, count, a, a64, b, x, o, queue, P, fail_flag);
     case 6:
     case 9:
         if constexpr (std::is_same_v<TA, __nv_bfloat16>) {
-            batch_cta_s<TA, kStreamNW, stream_jv<TA>(), true><<<grid, kStreamNW * 32 + 32, smem, s>>>(
-                sys, order, count, a, a64, b, x, o, queue, P, fail_flag);
+            return launch_k(batch_cta_s<TA, kStreamNW, stream_jv<TA>(), true>, grid, stream_threads, smem, s, pdl,
+                            sys, order, count, a, a64, b, x, o, queue, P, fail_flag);
         } else {
             return cudaErrorInvalidConfiguration;   // make_params admits it for BF16 storage only
         }
-        break;
-    case 0: batch_cta<TA, 128, 2><<<grid, 128, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
-    case 1: batch_cta<TA, 128, 4><<<grid, 128, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
-    case 2: batch_cta<TA, 256, 1><<<grid, 256, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
-    case 3: batch_cta<TA, 256, 2><<<grid, 256, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
-    default: batch_cta<TA, 512, 1><<<grid, 512, smem, s>>>(sys, order, count, a, a64, b, x, o, queue, P); break;
+    case 0: return launch_k(batch_cta<TA, 128, 2>, grid, 128, smem, s, pdl, sys, order, count, a, a64, b, x, o, queue, P);
+    case 1: return launch_k(batch_cta<TA, 128, 4>, grid, 128, smem, s, pdl, sys, order, count, a, a64, b, x, o, queue, P);
+    case 2: return launch_k(batch_cta<TA, 256, 1>, grid, 256, smem, s, pdl, sys, order, count, a, a64, b, x, o, queue, P);
+    case 3: return launch_k(batch_cta<TA, 256, 2>, grid, 256, smem, s, pdl, sys, order, count, a, a64, b, x, o, queue, P);
+    default:
+        return launch_k(batch_cta<TA, 512, 1>, grid, 512, smem, s, pdl, sys, order, count, a, a64, b, x, o, queue, P);
     }
-    return cudaGetLastError();
+}
+
+// the cluster kernel: `clusters` clusters of C blocks over the first `count` entries of order
+template <class TA>
+cudaError_t launch_wide(int C, int clusters, size_t smem, cudaStream_t s, const SysDesc* sys, const int32_t* order,
+                        int count, const void* alo, const double* a64, const double* b, double* x, BatchOut o,
+                        int32_t* queue, const BatchParams& P) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(C * clusters));
+    cfg.blockDim = dim3(kWideNT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_cta_w<TA>, sys, order, count, reinterpret_cast<const TA*>(alo), a64, b, x,
+                              o, queue, P);
+}
+
+// clusters of C blocks of the cluster kernel that can be resident at once (0: none)
+template <class TA>
+int wide_max_clusters(int C, size_t smem) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(kWideNT);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, batch_cta_w<TA>, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 }  // namespace
@@ -1435,6 +1772,15 @@ struct tacta_batch_s {
     int32_t* queue = nullptr;
     int64_t* stamps = nullptr;     // 2 x count: per-system begin and end clocks of the last solve
     std::vector<int32_t> last_iters;   // host: every system's step count in the last full solve
+    std::vector<int32_t> ord;          // host copy of the queue order
+    std::vector<int32_t> m_of;         // per system: rows
+    std::vector<double> dur;           // per system: predicted time (ns) on one block of the configuration
+    std::vector<char> dur_meas;        // per system: dur was measured on one block (not derived)
+    double eff[kWideMaxC + 1] = {};    // learned speed of a C-block cluster (see plan_batch)
+    int32_t wide_mode = -1;            // cluster kernel: -1 planned, 0 off, > 0 that many systems
+    int32_t wide_cluster = 0, wide_clusters = 0;   // asked for with wide_mode > 0 (0: chosen)
+    WidePlan plan;                     // the cluster kernel's share of the next solve
+    WidePlan graph_plan;
     int config = -1;               // index into kConfigs (-1: default)
     cudaGraphExec_t graph = nullptr;
     int graph_key = -1;
@@ -1462,8 +1808,8 @@ template <class TA>
 int chain_size() { return (int)sizeof(typename Elem<TA>::TC); }
 
 // launch parameters of configuration cfg; false when it cannot run this batch
-bool make_params(const tacta_batch_s* B, const tacta_options& o, int cfg, BatchParams* out, size_t* smem_out) {
-    const Config C = kConfigs[cfg];
+// the iteration's parameters, shared by every kernel
+BatchParams base_params(const tacta_batch_s* B, const tacta_options& o) {
     BatchParams P{};
     P.tol2 = o.tol * o.tol;
     P.tol_n2 = o.tol_normal > 0.0 ? o.tol_normal * o.tol_normal : 0.0;
@@ -1473,6 +1819,12 @@ bool make_params(const tacta_batch_s* B, const tacta_options& o, int cfg, BatchP
     P.R = o.recompute_every;
     P.t_max = o.t_max;
     P.cycle = o.cycle;
+    return P;
+}
+
+bool make_params(const tacta_batch_s* B, const tacta_options& o, int cfg, BatchParams* out, size_t* smem_out) {
+    const Config C = kConfigs[cfg];
+    BatchParams P = base_params(B, o);
     P.m_cap = (B->m_max + 7) & ~7;
     P.n_cap = (B->n_max + 7) & ~7;
     const int V = B->storage == TACTA_BATCH_FP64 ? 2 : B->storage == TACTA_BATCH_FP32 ? 4 : 8;
@@ -1509,26 +1861,230 @@ bool make_params(const tacta_batch_s* B, const tacta_options& o, int cfg, BatchP
     return true;
 }
 
-cudaError_t launch_batch(tacta_batch_s* B, cudaStream_t s, const tacta_options& o, int cfg) {
+// launch parameters of the cluster kernel with C-block clusters; false when the largest
+// system's vectors do not fit a block's shared memory
+bool wide_params(const tacta_batch_s* B, const tacta_options& o, int C, BatchParams* out, size_t* smem_out) {
+    if (C < 1 || C > kWideMaxC) return false;
+    BatchParams P = base_params(B, o);
+    P.m_cap = ((B->m_max + C - 1) / C + 7) & ~7;   // a block's rows
+    P.n_cap = (B->n_max + 7) & ~7;
+    const int V = B->storage == TACTA_BATCH_FP64 ? 2 : B->storage == TACTA_BATCH_FP32 ? 4 : 8;
+    const int tc = B->storage == TACTA_BATCH_FP64 ? 8 : 4;
+    const int64_t es = (int64_t)elem_size(B->storage);
+    const int64_t vb =
+        ((int64_t)P.m_cap * (1 + P.t_max) + (int64_t)P.n_cap * (P.t_max + 3) + (int64_t)kWideNT * V) * tc;
+    const int64_t a_bytes = kBatchSmemMax - vb - 16;
+    if (a_bytes < 0) return false;
+    P.a_cap = (a_bytes / 16) * 16 / es;
+    *smem_out = (size_t)(((P.a_cap * es + 15) & ~15) + vb);
+    if ((int64_t)*smem_out > kBatchSmemMax) return false;
+    *out = P;
+    return true;
+}
+
+int wide_max_clusters_for(const tacta_batch_s* B, int C, size_t smem) {
+    switch (B->storage) {
+    case TACTA_BATCH_FP64: return wide_max_clusters<double>(C, smem);
+    case TACTA_BATCH_FP32: return wide_max_clusters<float>(C, smem);
+    default: return wide_max_clusters<__nv_bfloat16>(C, smem);
+    }
+}
+
+// One solve: the queue reset, then (plan.systems > 0) the cluster kernel on the first
+// plan.systems entries of the queue order, and the single-block kernel of configuration
+// cfg on the rest -- a programmatic dependent launch, so that its blocks start once every
+// cluster is placed and take the remaining SMs, and each SM a cluster leaves.
+cudaError_t launch_batch(tacta_batch_s* B, cudaStream_t s, const tacta_options& o, int cfg, const WidePlan& plan) {
     const Config C = kConfigs[cfg];
     size_t smem = 0;
     BatchParams P{};
     if (!make_params(B, o, cfg, &P, &smem)) return cudaErrorInvalidConfiguration;
-    const int grid = std::max(1, std::min(B->count, B->sms * C.per_sm));
+    const int K = std::min(std::max(plan.systems, 0), B->count);
+    const int rest = B->count - K;
+    const int grid = std::max(1, std::min(rest, B->sms * C.per_sm));
     BatchOut out{B->iters, B->reason, B->rel, B->stamps, B->stamps + B->count};
-    cudaError_t e = cudaMemsetAsync(B->queue, 0, 2 * sizeof(int32_t), s);   // queue head, timeout flag
+    // queue heads of the two kernels and the timeout flag
+    cudaError_t e = cudaMemsetAsync(B->queue, 0, 4 * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
+    if (K > 0) {
+        BatchParams Pw{};
+        size_t smw = 0;
+        if (!wide_params(B, o, plan.cluster, &Pw, &smw) || plan.clusters < 1) return cudaErrorInvalidConfiguration;
+        switch (B->storage) {
+        case TACTA_BATCH_FP64:
+            e = launch_wide<double>(plan.cluster, plan.clusters, smw, s, B->sys, B->order, K, B->alo, B->a64, B->b,
+                                    B->x, out, B->queue + 2, Pw);
+            break;
+        case TACTA_BATCH_FP32:
+            e = launch_wide<float>(plan.cluster, plan.clusters, smw, s, B->sys, B->order, K, B->alo, B->a64, B->b,
+                                   B->x, out, B->queue + 2, Pw);
+            break;
+        default:
+            e = launch_wide<__nv_bfloat16>(plan.cluster, plan.clusters, smw, s, B->sys, B->order, K, B->alo, B->a64,
+                                           B->b, B->x, out, B->queue + 2, Pw);
+            break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    if (rest == 0) return cudaSuccess;
+    const bool pdl = K > 0;
     switch (B->storage) {
     case TACTA_BATCH_FP64:
-        return launch_cfg<double>(cfg, s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x, out,
-                                  B->queue, P, B->queue + 1);
+        return launch_cfg<double>(cfg, s, grid, smem, pdl, B->sys, B->order + K, rest, B->alo, B->a64, B->b, B->x,
+                                  out, B->queue, P, B->queue + 1);
     case TACTA_BATCH_FP32:
-        return launch_cfg<float>(cfg, s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x, out,
-                                 B->queue, P, B->queue + 1);
+        return launch_cfg<float>(cfg, s, grid, smem, pdl, B->sys, B->order + K, rest, B->alo, B->a64, B->b, B->x,
+                                 out, B->queue, P, B->queue + 1);
     default:
-        return launch_cfg<__nv_bfloat16>(cfg, s, grid, smem, B->sys, B->order, B->count, B->alo, B->a64, B->b, B->x,
-                                         out, B->queue, P, B->queue + 1);
+        return launch_cfg<__nv_bfloat16>(cfg, s, grid, smem, pdl, B->sys, B->order + K, rest, B->alo, B->a64, B->b,
+                                         B->x, out, B->queue, P, B->queue + 1);
     }
+}
+
+// Predicted makespan (ns) of a solve, by list scheduling: the clusters take the wide
+// systems (one-cluster times w, descending) each as soon as it is free; the single-block
+// kernel's blocks (per_sm per SM) start at once on the SMs no cluster holds, and on a
+// cluster's C SMs when it has finished, and take the other systems (one-block times d,
+// descending) each as soon as one is free. Past the first kExact of d the short systems
+// are spread as a fluid over the blocks' free times (water filling).
+double simulate_makespan(const std::vector<double>& w, int clusters, int C, const std::vector<double>& d, int sms,
+                         int per_sm) {
+    constexpr size_t kExact = 512;
+    std::priority_queue<double, std::vector<double>, std::greater<double>> cq, bq;
+    double end = 0.0;
+    if (!w.empty() && clusters < 1) return INFINITY;
+    for (int i = 0; i < clusters; ++i) cq.push(0.0);
+    for (double v : w) {
+        const double t = cq.top();
+        cq.pop();
+        cq.push(t + v);
+        end = std::max(end, t + v);
+    }
+    for (int i = 0; i < std::max(0, sms - clusters * C) * per_sm; ++i) bq.push(0.0);
+    while (!cq.empty()) {
+        for (int i = 0; i < C * per_sm; ++i) bq.push(cq.top());
+        cq.pop();
+    }
+    if (bq.empty()) return d.empty() ? end : INFINITY;
+    double fluid = 0.0;
+    for (size_t i = 0; i < d.size(); ++i) {
+        if (i >= kExact) { fluid += d[i]; continue; }
+        const double t = bq.top();
+        bq.pop();
+        bq.push(t + d[i]);
+        end = std::max(end, t + d[i]);
+    }
+    if (fluid > 0.0) {
+        std::vector<double> f;
+        while (!bq.empty()) { f.push_back(bq.top()); bq.pop(); }   // ascending
+        double level = f[0], below = 0.0;   // below: fluid needed to raise f[0..i) to f[i]
+        size_t i = 1;
+        for (; i < f.size(); ++i) {
+            const double need = below + (f[i] - f[i - 1]) * (double)i;
+            if (need >= fluid) break;
+            below = need;
+        }
+        level = f[i - 1] + (fluid - below) / (double)i;
+        end = std::max(end, level);
+    }
+    return end;
+}
+
+// The queue order and the cluster kernel's share of the next solve, from the predicted
+// one-block times dur (ns; all zero: unknown). The order is longest first. With the
+// planner on (wide_mode -1) and the times known, the plan is the one of least simulated
+// makespan among: no clusters, and, for C = 8, 4, 2 (where the vectors fit), the K = 1,
+// 2, ... longest systems with at least 4 C rows and at least half the balanced time
+// (sum dur / blocks), on min(K, resident clusters) clusters, a system's cluster time
+// taken as dur / (C per_sm eff_C) with eff_C learned from earlier solves (0.5 before
+// any). wide_mode > 0 forces that many systems from the head of the order onto clusters
+// (of wide_cluster blocks, or the largest C that fits; wide_clusters of them, or as many
+// as are resident). Returns the simulated makespan in ms (0 when the times are unknown).
+double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const std::vector<double>& dur,
+                  WidePlan* plan_out, std::vector<int32_t>* ord_out) {
+    const int count = B->count;
+    std::vector<int32_t> ord = B->ord;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t c) { return dur[a] > dur[c]; });
+    const bool known = count > 0 && std::all_of(dur.begin(), dur.end(), [](double v) { return v > 0.0; });
+    const int per_sm = kConfigs[cfg].per_sm;
+    *plan_out = WidePlan{};
+    *ord_out = ord;
+    if (B->wide_mode == 0 || count == 0) {
+        if (!known) return 0.0;
+        std::vector<double> d;
+        for (int32_t s_ : ord) d.push_back(dur[s_]);
+        return simulate_makespan({}, 0, 1, d, B->sms, per_sm) * 1e-6;
+    }
+    auto fits = [&](int C, int* maxc) {
+        BatchParams Pw{};
+        size_t smw = 0;
+        if (!wide_params(B, o, C, &Pw, &smw)) return false;
+        *maxc = wide_max_clusters_for(B, C, smw);
+        return *maxc > 0;
+    };
+    if (B->wide_mode > 0) {   // forced
+        WidePlan p{};
+        p.systems = std::min(B->wide_mode, count);
+        int maxc = 0;
+        for (int C : {8, 4, 2, 1}) {
+            if (B->wide_cluster > 0 && C != B->wide_cluster) continue;
+            if (fits(C, &maxc)) { p.cluster = C; break; }
+        }
+        if (p.cluster == 0) return known ? INFINITY : 0.0;   // launch_batch refuses it
+        p.clusters = std::min(p.systems, maxc);
+        if (B->wide_clusters > 0) p.clusters = std::min(p.clusters, B->wide_clusters);
+        *plan_out = p;
+        if (!known) return 0.0;
+        std::vector<double> w, d;
+        const double e = B->eff[p.cluster] > 0.0 ? B->eff[p.cluster] : 0.5;
+        for (int j = 0; j < count; ++j) {
+            if (j < p.systems) w.push_back(dur[ord[j]] / (p.cluster * per_sm * e));
+            else d.push_back(dur[ord[j]]);
+        }
+        return simulate_makespan(w, p.clusters, p.cluster, d, B->sms, per_sm) * 1e-6;
+    }
+    if (!known) return 0.0;
+    std::vector<double> all;
+    double total = 0.0;
+    for (int32_t s_ : ord) { all.push_back(dur[s_]); total += dur[s_]; }
+    double best = simulate_makespan({}, 0, 1, all, B->sms, per_sm);
+    std::vector<int32_t> best_wide;
+    const double balanced = total / ((double)B->sms * per_sm);
+    for (int C : {8, 4, 2}) {
+        int maxc = 0;
+        if (!fits(C, &maxc)) continue;
+        const double e = B->eff[C] > 0.0 ? B->eff[C] : 0.5;
+        std::vector<int32_t> elig;   // positions in ord
+        for (int j = 0; j < count && elig.size() < 32; ++j)
+            if (B->m_of[ord[j]] >= 4 * C && dur[ord[j]] >= 0.5 * balanced) elig.push_back(j);
+        std::vector<char> wide((size_t)count, 0);
+        for (size_t K = 1; K <= elig.size(); ++K) {
+            wide[elig[K - 1]] = 1;
+            std::vector<double> w, d;
+            for (int j = 0; j < count; ++j) {
+                if (wide[j]) w.push_back(dur[ord[j]] / (C * per_sm * e));
+                else d.push_back(dur[ord[j]]);
+            }
+            const int cl = std::min((int)K, maxc);
+            const double ms = simulate_makespan(w, cl, C, d, B->sms, per_sm);
+            if (ms < 0.98 * best) {
+                best = ms;
+                plan_out->systems = (int32_t)K;
+                plan_out->cluster = C;
+                plan_out->clusters = cl;
+                best_wide.assign(elig.begin(), elig.begin() + K);
+            }
+        }
+    }
+    if (plan_out->systems > 0) {   // the wide systems first, then the rest, each longest first
+        std::vector<char> wide((size_t)count, 0);
+        std::vector<int32_t> o2;
+        for (int32_t j : best_wide) { wide[j] = 1; o2.push_back(ord[j]); }
+        for (int j = 0; j < count; ++j)
+            if (!wide[j]) o2.push_back(ord[j]);
+        *ord_out = o2;
+    }
+    return best * 1e-6;
 }
 
 bool batch_opts_ok(const tacta_options& o) {
@@ -1628,7 +2184,7 @@ extern "C" tacta_status tacta_batch_create(int32_t count, const int32_t* m, cons
     BCHK(cudaMalloc(&B->iters, sizeof(int32_t) * std::max<int32_t>(count, 1)));
     BCHK(cudaMalloc(&B->reason, sizeof(int32_t) * std::max<int32_t>(count, 1)));
     BCHK(cudaMalloc(&B->rel, sizeof(double) * std::max<int32_t>(count, 1)));
-    BCHK(cudaMalloc(&B->queue, 2 * sizeof(int32_t)));
+    BCHK(cudaMalloc(&B->queue, 4 * sizeof(int32_t)));
     BCHK(cudaMalloc(&B->stamps, 2 * sizeof(int64_t) * std::max<int32_t>(count, 1)));
     BCHK(cudaMemsetAsync(B->stamps, 0, 2 * sizeof(int64_t) * std::max<int32_t>(count, 1), s));
     if (count > 0) {
@@ -1638,6 +2194,10 @@ extern "C" tacta_status tacta_batch_create(int32_t count, const int32_t* m, cons
         std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b2) {
             return (int64_t)d[a].m * d[a].n > (int64_t)d[b2].m * d[b2].n;
         });
+        B->ord = ord;
+        B->m_of.assign(m, m + count);
+        B->dur.assign((size_t)count, 0.0);
+        B->dur_meas.assign((size_t)count, 0);
         BCHK(cudaMemcpyAsync(B->sys, d.data(), sizeof(SysDesc) * count, cudaMemcpyHostToDevice, s));
         BCHK(cudaMemcpyAsync(B->order, ord.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, s));
         BCHK(cudaMemcpyAsync(B->a64, vals, sizeof(double) * a64, on_device ? cudaMemcpyDeviceToDevice
@@ -1718,17 +2278,31 @@ extern "C" tacta_status tacta_batch_cta(tacta_batch B, const double* b, double* 
             return TACTA_ERR_INVALID;
         }
     }
+    // the queue order and the clusters' share, from the times the last solves measured
+    WidePlan plan{};
+    std::vector<int32_t> ord;
+    plan_batch(B, o, cfg, B->dur, &plan, &ord);
+    if (B->wide_mode > 0 && plan.systems == 0) {
+        g_batch_err = "the cluster kernel cannot take this batch (its vectors do not fit a block's shared memory)";
+        return TACTA_ERR_INVALID;
+    }
+    if (ord != B->ord) {
+        B->ord = ord;
+        BTRY(cudaMemcpyAsync(B->order, B->ord.data(), sizeof(int32_t) * B->count, cudaMemcpyHostToDevice, s));
+    }
+    B->plan = plan;
     BTRY(cudaMemcpyAsync(B->b, b, sizeof(double) * B->b_len, cudaMemcpyDefault, s));
     if (o.use_graph) {
-        // the solve is a queue reset and one persistent launch: replay it as a graph
-        if (!B->graph || B->graph_key != cfg || std::memcmp(&P, &B->graph_params, sizeof(P)) != 0) {
+        // the solve is a queue reset and one or two persistent launches: replay it as a graph
+        if (!B->graph || B->graph_key != cfg || std::memcmp(&P, &B->graph_params, sizeof(P)) != 0 ||
+            !(B->graph_plan == plan)) {
             if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
             cudaStream_t cs;
             BTRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                const cudaError_t el = launch_batch(B, cs, o, cfg);
+                const cudaError_t el = launch_batch(B, cs, o, cfg, plan);
                 e = cudaStreamEndCapture(cs, &g);
                 if (el != cudaSuccess) e = el;
             }
@@ -1738,10 +2312,11 @@ extern "C" tacta_status tacta_batch_cta(tacta_batch B, const double* b, double* 
             BTRY(e);
             B->graph_key = cfg;
             B->graph_params = P;
+            B->graph_plan = plan;
         }
         BTRY(cudaGraphLaunch(B->graph, s));
     } else {
-        BTRY(launch_batch(B, s, o, cfg));
+        BTRY(launch_batch(B, s, o, cfg, plan));
     }
     BTRY(cudaMemcpyAsync(x, B->x, sizeof(double) * B->x_len, cudaMemcpyDefault, s));
     if (iters) BTRY(cudaMemcpyAsync(iters, B->iters, sizeof(int32_t) * B->count, cudaMemcpyDefault, s));
@@ -1754,36 +2329,97 @@ extern "C" tacta_status tacta_batch_cta(tacta_batch B, const double* b, double* 
         g_batch_err = "a wait in the batched kernel gave up (systems reported with reason TIMEOUT)";
         return TACTA_ERR_TIMEOUT;
     }
-    // The next solve takes the systems longest first by this solve's measured time per
-    // system (the timeline): the longest starts at once and the short ones fill the tail.
-    // (A system's result does not depend on the block or the moment that takes it.) The
-    // step counts stay on the host for the autotuner's makespan estimate.
+    // What the next solve plans with (a system's result does not depend on the block or
+    // the moment that takes it; on a cluster, its sums run in another order): each
+    // system's time on one block -- measured where one block solved it; for a system a
+    // cluster solved, the learned cluster speed eff_C = sum of the one-block times
+    // measured before / (C per_sm sum of the cluster times), and a system without an
+    // earlier one-block time is given cluster time x C per_sm eff_C. The step counts stay
+    // on the host for the autotuner's makespan estimate.
     B->last_iters.resize((size_t)B->count);
     BTRY(cudaMemcpy(B->last_iters.data(), B->iters, sizeof(int32_t) * B->count, cudaMemcpyDeviceToHost));
-    if (B->count > 1) {
-        std::vector<int64_t> st((size_t)2 * B->count);
-        BTRY(cudaMemcpyAsync(st.data(), B->stamps, sizeof(int64_t) * 2 * B->count, cudaMemcpyDeviceToHost, s));
-        BTRY(cudaStreamSynchronize(s));
-        std::vector<int32_t> ord((size_t)B->count);
-        std::iota(ord.begin(), ord.end(), 0);
-        const int64_t* tb = st.data();
-        const int64_t* te = st.data() + B->count;
-        std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t c) {
-            return te[a] - tb[a] > te[c] - tb[c];
-        });
-        BTRY(cudaMemcpyAsync(B->order, ord.data(), sizeof(int32_t) * B->count, cudaMemcpyHostToDevice, s));
-        BTRY(cudaStreamSynchronize(s));
+    std::vector<int64_t> st((size_t)2 * B->count);
+    BTRY(cudaMemcpy(st.data(), B->stamps, sizeof(int64_t) * 2 * B->count, cudaMemcpyDeviceToHost));
+    const int64_t* tb = st.data();
+    const int64_t* te = st.data() + B->count;
+    const int per_sm = kConfigs[cfg].per_sm;
+    const int K = std::min(plan.systems, B->count), C = plan.cluster;
+    double num = 0.0, den = 0.0;
+    for (int j = 0; j < B->count; ++j) {
+        const int32_t q = B->ord[j];
+        const double meas = std::max(1.0, (double)(te[q] - tb[q]));
+        if (j >= K) {
+            B->dur[q] = meas;
+            B->dur_meas[q] = 1;
+        } else if (B->dur_meas[q]) {
+            num += B->dur[q];
+            den += (double)C * per_sm * meas;
+        }
+    }
+    if (den > 0.0) B->eff[C] = std::min(1.0, std::max(0.05, num / den));
+    for (int j = 0; j < K; ++j) {
+        const int32_t q = B->ord[j];
+        if (!B->dur_meas[q]) {
+            const double e = B->eff[C] > 0.0 ? B->eff[C] : 0.5;
+            B->dur[q] = std::max(1.0, (double)(te[q] - tb[q])) * C * per_sm * e;
+        }
     }
     return TACTA_OK;
 }
 
+extern "C" double tacta_batch_simulate_makespan(const double* w, int32_t nw, int32_t clusters, int32_t cluster,
+                                                const double* d, int32_t nd, int32_t sms, int32_t per_sm) {
+    if (nw < 0 || nd < 0 || clusters < 0 || cluster < 1 || sms < 1 || per_sm < 1 ||
+        (int64_t)clusters * cluster > sms || (nw > 0 && (!w || clusters < 1)) || (nd > 0 && !d))
+        return -1.0;
+    std::vector<double> wv(w, w + nw), dv(d, d + nd);
+    for (double v : wv)
+        if (!(v >= 0.0)) return -1.0;
+    for (double v : dv)
+        if (!(v >= 0.0)) return -1.0;
+    std::sort(wv.begin(), wv.end(), std::greater<double>());
+    std::sort(dv.begin(), dv.end(), std::greater<double>());
+    return simulate_makespan(wv, clusters, cluster, dv, sms, per_sm);
+}
+
+extern "C" tacta_status tacta_batch_set_wide(tacta_batch B, int32_t systems, int32_t cluster, int32_t clusters) {
+    g_batch_err.clear();
+    if (!B) { g_batch_err = "NULL batch"; return TACTA_ERR_INVALID; }
+    if (systems < -1 || cluster < 0 || cluster > kWideMaxC || clusters < 0) {
+        g_batch_err = "systems must be >= -1, cluster in 0..8, clusters >= 0";
+        return TACTA_ERR_INVALID;
+    }
+    B->wide_mode = systems;
+    B->wide_cluster = cluster;
+    B->wide_clusters = clusters;
+    return TACTA_OK;
+}
+
+extern "C" tacta_status tacta_batch_wide_plan(tacta_batch B, const tacta_options* opt, int32_t* systems,
+                                              int32_t* cluster, int32_t* clusters, double* predicted_ms) {
+    g_batch_err.clear();
+    if (!B) { g_batch_err = "NULL batch"; return TACTA_ERR_INVALID; }
+    const tacta_options o = resolve_opts(opt);
+    if (!batch_opts_ok(o)) return TACTA_ERR_INVALID;
+    BTRY(cudaSetDevice(B->device));
+    WidePlan plan{};
+    std::vector<int32_t> ord;
+    const double ms = plan_batch(B, o, B->config >= 0 ? B->config : kDefaultConfig, B->dur, &plan, &ord);
+    if (systems) *systems = plan.systems;
+    if (cluster) *cluster = plan.cluster;
+    if (clusters) *clusters = plan.clusters;
+    if (predicted_ms) *predicted_ms = ms;
+    return TACTA_OK;
+}
+
 // Autotuner: times every launch configuration on the batch (each solve capped at
-// max_iter of the given options, graphs off), keeps the best, and returns it. Before any
-// full solve the score is the capped run's time; after one, it is the makespan the capped
-// run predicts for a full solve in the learned queue order: the largest, over the systems,
-// of the system's time per step in the capped run times its step count in the last full
-// solve (the batch takes its slowest system's time, and how a system shares its SM with
-// other blocks depends on the launch shape).
+// max_iter of the given options, graphs off, single-block kernel only), keeps the best,
+// and returns it. Before any full solve the score is the capped run's time; after one,
+// it is the makespan predicted for a full solve: every system's one-block time taken as
+// its time per step in the capped run times its step count in the last full solve (how
+// a system shares its SM with other blocks depends on the launch shape), then the
+// planner's simulated makespan with those times (the clusters' share included, see
+// plan_batch). The best configuration's predicted times become the planner's.
 extern "C" tacta_status tacta_batch_tune(tacta_batch B, const double* b, const tacta_options* opt,
                                          int32_t* best_config, double* best_ms) {
     g_batch_err.clear();
@@ -1798,7 +2434,8 @@ extern "C" tacta_status tacta_batch_tune(tacta_batch B, const double* b, const t
     BTRY(cudaEventCreate(&e0));
     BTRY(cudaEventCreate(&e1));
     int best = -1;
-    float best_t = 0.0f;
+    double best_t = 0.0;
+    std::vector<double> best_dur;
     for (int c = 0; c < kNumConfigs; ++c) {
         size_t smem = 0;
         BatchParams P{};
@@ -1806,32 +2443,43 @@ extern "C" tacta_status tacta_batch_tune(tacta_batch B, const double* b, const t
         float tc = 0.0f;
         bool ok = true;
         for (int rep = 0; rep < 2 && ok; ++rep) {      // the first run warms caches and loads the module
-            ok = cudaEventRecord(e0, s) == cudaSuccess && launch_batch(B, s, o, c) == cudaSuccess &&
+            ok = cudaEventRecord(e0, s) == cudaSuccess && launch_batch(B, s, o, c, WidePlan{}) == cudaSuccess &&
                  cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
                  cudaEventElapsedTime(&tc, e0, e1) == cudaSuccess;
         }
-        float score = tc;
+        double score = tc;
+        std::vector<double> dc;
         if (ok && B->last_iters.size() == (size_t)B->count) {
             std::vector<int64_t> st((size_t)2 * B->count);
             std::vector<int32_t> it((size_t)B->count);
             ok = cudaMemcpy(st.data(), B->stamps, sizeof(int64_t) * 2 * B->count, cudaMemcpyDeviceToHost) ==
                      cudaSuccess &&
                  cudaMemcpy(it.data(), B->iters, sizeof(int32_t) * B->count, cudaMemcpyDeviceToHost) == cudaSuccess;
-            double worst = 0.0;
+            dc.assign((size_t)B->count, 0.0);
             for (int32_t q = 0; ok && q < B->count; ++q) {
-                if (it[q] <= 0) continue;
-                const double per_step = (double)(st[(size_t)B->count + q] - st[q]) / it[q];
-                worst = std::max(worst, per_step * std::max<int32_t>(B->last_iters[q], it[q]));
+                const double meas = std::max(1.0, (double)(st[(size_t)B->count + q] - st[q]));
+                dc[q] = it[q] > 0 ? meas / it[q] * std::max<int32_t>(B->last_iters[q], it[q]) : meas;
             }
-            if (ok && worst > 0.0) score = (float)(worst * 1e-6);
+            WidePlan p{};
+            std::vector<int32_t> ord;
+            const double ms = ok ? plan_batch(B, o, c, dc, &p, &ord) : 0.0;
+            if (ms > 0.0) score = ms;
         }
-        if (ok && (best < 0 || score < best_t)) { best = c; best_t = score; }
+        if (ok && (best < 0 || score < best_t)) {
+            best = c;
+            best_t = score;
+            best_dur = dc;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     BTRY(cudaGetLastError());
     if (best < 0) { g_batch_err = "no launch configuration fits this batch"; return TACTA_ERR_CUDA; }
     B->config = best;
+    if (best_dur.size() == (size_t)B->count) {
+        B->dur = best_dur;
+        B->dur_meas.assign((size_t)B->count, 1);
+    }
     if (best_config) *best_config = best;
     if (best_ms) *best_ms = best_t;
     return TACTA_OK;

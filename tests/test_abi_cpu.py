@@ -23,7 +23,7 @@ def lib():
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:tacta_status|void|const char\*|int32_t)\s+(\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:tacta_status|void|const char\*|int32_t|double)\s+(\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
@@ -124,3 +124,5 @@ def test_batch_arguments_are_rejected_before_gpu_work(lib):
     assert lib.tacta_batch_num_configs() >= 1
     assert lib.tacta_batch_config_shape(0, ctypes.byref(t), ctypes.byref(p)) == 0 and t.value > 0 and p.value > 0
     assert lib.tacta_batch_config_shape(99, ctypes.byref(t), ctypes.byref(p)) == -1
+    assert lib.tacta_batch_set_wide(None, -1, 0, 0) == -1
+    assert lib.tacta_batch_wide_plan(None, None, None, None, None, None) == -1

@@ -143,6 +143,7 @@ def test_graph_replay_and_configs_agree(tacta):
     mats, bs, _ = small_batch(4, 30, m_range=(32, 200), aspect=(1.4, 2.0))
     b = np.concatenate(bs)
     B = tacta.Batch(mats, storage=tacta.BATCH_FP32)
+    B.set_wide(0)   # the planner would move the longest systems onto clusters (other sums)
     opts = dict(tol=1e-8, tol_normal=0.0, max_iter=5000)
     x1, it1, r1, _ = B.cta(b, use_graph=1, **opts)
     x2, it2, r2, _ = B.cta(b, use_graph=1, **opts)
@@ -255,4 +256,146 @@ def test_timeline_and_stage_configs(tacta):
         B.set_config(c)
         _, _, rc, rs = B.cta(b, tol=1e-8, tol_normal=0.0, max_iter=5000)
         assert all(tacta.REASON[int(r)] == "RESIDUAL" for r in rs) and np.all(rc <= 1e-8 * (1 + 1e-6)), c
+    B.close()
+
+
+# ------------------------------------------------------------ thread-block clusters
+
+def run_wide(tacta, mats, bs, storage, systems, cluster, clusters=0, **opts):
+    B = tacta.Batch(mats, storage=storage)
+    B.set_wide(systems, cluster, clusters)
+    x, iters, rel, reason = B.cta(np.concatenate(bs), **opts)
+    plan = B.wide_plan(**opts)
+    xs = B.split(x)
+    B.close()
+    return xs, iters, rel, reason, plan
+
+
+def wide_mix(seed):
+    """Small systems (blocks of a C = 8 cluster with no rows at m < 8 ... 57), and large ones
+    whose rows exceed a block's shared memory (read through L2)."""
+    mats, bs, _ = small_batch(seed, 24, m_range=(5, 120))
+    m2, b2, _ = small_batch(seed + 100, 6, m_range=(300, 512))
+    return mats + m2, bs + b2
+
+
+@pytest.mark.parametrize("cluster", [2, 4, 8])
+def test_wide_fp64_fixed_trajectories_match_oracle(tacta, cluster):
+    """Every system on a cluster (FP64 storage, four steps t = 1..4 each): x, the step
+    count and the recomputed residual against the oracle's run on that system alone, as
+    for one block; fewer clusters than systems, so clusters take several in turn."""
+    mats, bs = wide_mix(21)
+    opts = dict(tol=1e-30, tol_normal=0.0, max_iter=4)
+    xs, iters, rel, reason, plan = run_wide(tacta, mats, bs, tacta.BATCH_FP64, len(mats), cluster, 5, **opts)
+    assert plan[:3] == (len(mats), cluster, 5)
+    for s, (A, b) in enumerate(zip(mats, bs)):
+        ref = oracle.cta_solve(oracle.make_operator(problem(A, b)), b, **opts)
+        assert iters[s] == ref.iters, s
+        assert np.linalg.norm(xs[s] - ref.x) <= 1e-9 * np.linalg.norm(ref.x), (s, A.shape)
+        assert rel[s] == pytest.approx(ref.rel_res, rel=1e-9), s
+        assert tacta.REASON[int(reason[s])] == "MAXITER"
+
+
+@pytest.mark.parametrize("storage,tol,xtol", [("BATCH_FP64", 1e-10, 1e-8), ("BATCH_FP32", 1e-8, 1e-6),
+                                              ("BATCH_BF16", 1e-8, 3e-2)])
+@pytest.mark.parametrize("cluster,share", [(8, 1.0), (4, 0.5), (2, 0.25)])
+def test_wide_to_tolerance_min_norm(tacta, storage, tol, xtol, cluster, share):
+    """Clusters on all, half or a quarter of the systems (the rest on single blocks of the
+    dependent launch at the same time), each precision: the host-recomputed FP64 residual
+    meets tol, the reported one equals it, x is the minimum-norm solution within cond(A)
+    times xtol, and with every system on a cluster a second solve gives the same bits."""
+    mats, bs, _ = small_batch(2, 40, aspect=(1.4, 2.0))
+    m2, b2, _ = small_batch(6, 8, m_range=(220, 400), aspect=(1.4, 1.8))
+    mats, bs = m2 + mats, b2 + bs
+    k = max(1, int(share * len(mats)))
+    B = tacta.Batch(mats, storage=getattr(tacta, storage))
+    B.set_wide(k, cluster)
+    opts = dict(tol=tol, tol_normal=0.0, max_iter=20000)
+    x, iters, rel, reason = B.cta(np.concatenate(bs), **opts)
+    x2, iters2, _, _ = B.cta(np.concatenate(bs), **opts)
+    if k == len(mats):   # (with fewer, the learned order may move other systems to the head)
+        assert np.array_equal(x, x2) and np.array_equal(iters, iters2)
+    assert B.wide_plan(**opts)[:2] == (k, cluster)
+    xs = B.split(x)
+    B.close()
+    for s, (A, b) in enumerate(zip(mats, bs)):
+        assert tacta.REASON[int(reason[s])] == "RESIDUAL", (s, reason[s], rel[s])
+        r = np.linalg.norm(b - A @ xs[s]) / np.linalg.norm(b)
+        assert r <= tol * (1 + 1e-6), (s, r)
+        assert rel[s] == pytest.approx(r, rel=1e-6, abs=1e-14)
+        sv = np.linalg.svd(A, compute_uv=False)
+        sv = sv[sv > 1e-10 * sv[0]]
+        xmn = np.linalg.pinv(A, rcond=1e-10) @ b
+        err = np.linalg.norm(xs[s] - xmn) / np.linalg.norm(xmn)
+        assert err <= xtol * sv[0] / sv[-1], (s, err)
+
+
+def test_wide_edge_cases(tacta):
+    """On clusters of 8: 1 x 1, one row, one column (blocks without rows or columns), a zero
+    right-hand side, and max_iter = 0."""
+    rng = np.random.default_rng(3)
+    mats = [np.array([[2.0]]), rng.standard_normal((1, 7)), rng.standard_normal((9, 1)),
+            rng.standard_normal((30, 40))]
+    bs = [np.array([4.0]), rng.standard_normal(1), mats[2] @ np.array([1.5]), np.zeros(30)]
+    xs, iters, rel, reason, _ = run_wide(tacta, mats, bs, tacta.BATCH_FP64, 4, 8, tol=1e-12, tol_normal=0.0,
+                                         max_iter=1000)
+    assert xs[0][0] == pytest.approx(2.0, rel=1e-14)
+    np.testing.assert_allclose(xs[1], np.linalg.pinv(mats[1]) @ bs[1], rtol=1e-10, atol=1e-12)
+    assert xs[2][0] == pytest.approx(1.5, rel=1e-10)
+    assert tacta.REASON[int(reason[3])] == "ZERO_RHS" and np.all(xs[3] == 0.0) and iters[3] == 0
+    xs, iters, rel, reason, _ = run_wide(tacta, mats[:3], bs[:3], tacta.BATCH_FP32, 3, 8, tol=1e-8,
+                                         tol_normal=0.0, max_iter=0)
+    assert all(tacta.REASON[int(r)] == "MAXITER" for r in reason)
+    assert np.all(iters == 0) and np.allclose(rel, 1.0) and all(np.all(x == 0.0) for x in xs)
+
+
+def test_wide_normal_equation_stop(tacta):
+    """The normal-equation test (||Aᵀr|| <= tol_normal ||Aᵀb||) on a cluster: an
+    inconsistent overdetermined system stops with reason NORMAL at the least-squares
+    solution, as on one block."""
+    rng = np.random.default_rng(17)
+    A = rng.standard_normal((200, 60))
+    b = rng.standard_normal(200)
+    opts = dict(tol=1e-12, tol_normal=1e-9, max_iter=20000)
+    xs, iters, rel, reason, _ = run_wide(tacta, [A], [b], tacta.BATCH_FP64, 1, 4, **opts)
+    xs1, iters1, _, reason1 = run(tacta, [A], [b], tacta.BATCH_FP64, **opts)
+    xls = np.linalg.lstsq(A, b, rcond=None)[0]
+    assert tacta.REASON[int(reason[0])] == "NORMAL" == tacta.REASON[int(reason1[0])]
+    assert np.linalg.norm(xs[0] - xls) <= 1e-6 * np.linalg.norm(xls)
+    assert np.linalg.norm(xs1[0] - xls) <= 1e-6 * np.linalg.norm(xls)
+
+
+def test_wide_plan_automatic(tacta):
+    """The planner: no clusters before any solve; after one, on a batch whose few
+    near-square systems take far longer than the rest, it puts the longest on clusters
+    with a smaller predicted makespan than one block each, and the solves meet the
+    tolerance wherever the systems converge."""
+    rng = np.random.default_rng(5)
+    mats, bs = [], []
+    for s in range(600):
+        m = int(rng.integers(32, 96))
+        n = int(2 * m)
+        mats.append(rng.standard_normal((m, n)))
+    for s in range(4):   # near-square: thousands of steps
+        mats.append(rng.standard_normal((400, 400)))
+    bs = [A @ rng.standard_normal(A.shape[1]) for A in mats]
+    b = np.concatenate(bs)
+    B = tacta.Batch(mats, storage=tacta.BATCH_FP32)
+    opts = dict(tol=1e-8, tol_normal=0.0, max_iter=3000)
+    assert B.wide_plan(**opts) == (0, 0, 0, 0.0)
+    B.cta(b, **opts)
+    systems, cluster, clusters, ms = B.wide_plan(**opts)
+    B.set_wide(0)
+    ms_off = B.wide_plan(**opts)[3]
+    B.set_wide(-1)
+    assert systems >= 1 and cluster in (2, 4, 8) and 1 <= clusters <= systems
+    assert 0 < ms < ms_off
+    for _ in range(2):
+        x, iters, rel, reason = B.cta(b, **opts)
+        xs = B.split(x)
+        for s, (A, bb) in enumerate(zip(mats, bs)):
+            if tacta.REASON[int(reason[s])] == "RESIDUAL":
+                assert np.linalg.norm(bb - A @ xs[s]) / np.linalg.norm(bb) <= 1e-8 * (1 + 1e-6), s
+            else:
+                assert tacta.REASON[int(reason[s])] == "MAXITER" and A.shape == (400, 400), s
     B.close()
