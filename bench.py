@@ -367,10 +367,12 @@ def autograd_workload(tacta, dev, stream):
 
 
 def batched_workload(tacta, dev, stream):
-    """4096 uneven dense systems (m in [32, 512], n in [m/2, 2m], 10% rank m/2) to 1e-8:
-    one persistent launch per storage precision (launch shape and ring stage autotuned
-    after a first full solve, whose step counts and measured times set the tuner's makespan
-    estimate and the queue order), against the single-system FP64 path (Plan per system)
+    """4096 uneven dense systems (m in [32, 512], n in [m/2, 2m], 10% rank m/2) to 1e-8,
+    per storage precision: the longest systems on thread-block clusters and the rest on
+    single blocks of one persistent launch (launch shape and ring stage autotuned after a
+    first full solve, whose step counts and measured times set the tuner's makespan
+    model, the queue order and the clusters' share; two warm solves teach the planner the
+    clusters' speed), against the single-system FP64 path (Plan per system)
     timed on an evenly spaced sample."""
     import gen
     import numpy as np
@@ -385,7 +387,9 @@ def batched_workload(tacta, dev, stream):
         B = tacta.Batch(mats, storage=st)
         B.cta(b, **kw)                     # a first full solve: step counts and queue order
         cfg, _ = B.tune(b, tol=TOL, tol_normal=0.0, max_iter=100)
-        B.cta(b, **kw)                                       # warm (graph capture)
+        for _ in range(2):   # warm: the planner learns the clusters' speed; graph capture
+            B.cta(b, **kw)
+        plan = B.wide_plan(**kw)                             # the share the timed solve uses
         t, (x, iters, rel, reason) = timed(lambda: B.cta(b, **kw), stream)
         conv = reason == 1
         shape = tacta.Batch.configs()[cfg]
@@ -393,7 +397,10 @@ def batched_workload(tacta, dev, stream):
         res[name] = {"time_ms": t, "converged": int(conv.sum()), "maxiter": int((reason == 3).sum()),
                      "system_iters": int(iters.sum()), "system_iters_per_s": float(iters.sum() / (t * 1e-3)),
                      "max_rel_res_converged": float(rel[conv].max()) if conv.any() else None,
-                     "config": shape, "completion": completion_profile(*B.timeline(), blocks)}
+                     "config": shape,
+                     "clusters": {"systems": plan[0], "blocks_per_cluster": plan[1], "clusters": plan[2],
+                                  "predicted_ms": plan[3]},
+                     "completion": completion_profile(*B.timeline(), blocks, clustered=plan[0] > 0)}
         B.close()
     # single-system FP64 path on a sample, extrapolated to the batch
     idx = np.linspace(0, B0.count - 1, 24).astype(int)
@@ -435,11 +442,12 @@ def batch_sample():
         B.close()
 
 
-def completion_profile(tb, te, blocks):
+def completion_profile(tb, te, blocks, clustered=False):
     """The batch's completion profile from the per-system device clocks of one solve: when
-    50/90/99/100 % of the systems were done (ms after the first was taken), the share of
-    the launch's block-time spent on systems, and the mean share of blocks still busy
-    after the 90 % mark (the tail)."""
+    50/90/99/100 % of the systems were done (ms after the first was taken), the longest
+    system's time, and -- when single blocks took every system -- the share of the launch's
+    block-time spent on systems and the mean share of blocks still busy after the 90 % mark
+    (the tail). (A system on a cluster holds several SMs: those shares are then omitted.)"""
     import numpy as np
     t0 = int(tb.min())
     done = np.sort((te - t0) * 1e-6)
@@ -450,9 +458,11 @@ def completion_profile(tb, te, blocks):
     t90 = pct["p90_ms"]
     beg, end = (tb - t0) * 1e-6, (te - t0) * 1e-6
     tail = float(np.sum(np.clip(end, t90, None) - np.clip(beg, t90, None)))
-    return dict(pct, blocks=int(blocks), busy_frac=busy / (blocks * span) if span > 0 else None,
-                tail_busy_frac=tail / (blocks * (span - t90)) if span > t90 else None,
-                longest_system_ms=float(((te - tb) * 1e-6).max()))
+    out = dict(pct, longest_system_ms=float(((te - tb) * 1e-6).max()))
+    if not clustered:
+        out.update(blocks=int(blocks), busy_frac=busy / (blocks * span) if span > 0 else None,
+                   tail_busy_frac=tail / (blocks * (span - t90)) if span > t90 else None)
+    return out
 
 
 def timed(fn, stream):

@@ -90,7 +90,7 @@ struct BatchParams {
     int32_t max_iter, R, t_max, cycle;
     int32_t m_cap, n_cap;  // vector capacities (multiples of 8: every vector starts 16-byte aligned)
     int32_t stage_bytes;   // streamed kernel: bytes of a ring stage (the autotuner's tile size)
-    int32_t pad_;
+    int32_t nc_cap;        // cluster kernel: capacity of a block's column slice (multiple of 8)
     int64_t a_cap;         // elements of A a block can stage in shared memory
     int64_t area_bytes;    // streamed kernel: bytes of the A area (ring, or A when resident)
 };
@@ -1288,31 +1288,37 @@ batch_cta_s(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
 //
 // A batch takes its slowest system's time: a system that needs the whole step budget
 // runs for seconds on one block long after every other block has finished. Here the
-// C blocks of a thread-block cluster (C = 2, 4 or 8, one block per SM) solve one such
+// C blocks of a thread-block cluster (C = 2 .. 16, one block per SM) solve one such
 // system together, with the same iteration as batch_cta:
 //   * block c keeps rows [c mb, c mb + mb) of A_s (mb = ceil(m / C)), staged in its
 //     shared memory when they fit, and the same rows of r and of every u_i;
-//   * z_i = Aᵀ u_{i-1} / s: every block forms the partial product over its rows; a
-//     cluster barrier publishes the partials, and every block adds all C of them in
-//     rank order through distributed shared memory, so all blocks hold the same bits
-//     of the whole z_i (the partials are double-buffered: one barrier per product);
-//   * u_i = A z_i / s: each block its own rows, from its copy of z_i;
-//   * the moments, ||r||² and the FP64 residual's norm are block partials that the
-//     blocks publish and add in rank order, so every block holds the same FP64 values
-//     and takes the same auxiliary solve and stop tests: every branch that encloses a
-//     cluster barrier depends on those shared values only;
-//   * x is updated in column slices (block c: columns [c nc, c nc + nc)); the FP64
-//     residual b - A x reads the whole x from global memory after a fence and a
-//     cluster barrier.
+//   * z_i = Aᵀ u_{i-1} / s: every block forms the partial product over its rows and a
+//     cluster barrier publishes the partials. An FP32 chain: every block adds all C
+//     partials of every column in rank order through distributed shared memory (the
+//     same bits in all blocks; the partials are double-buffered, one barrier per
+//     product). An FP64 chain (where every FP64 addition costs the SM's slow FP64 pipe):
+//     block c adds the C partials of its columns [c nc, c nc + nc) only, in rank order,
+//     and writes the sums into every block's copy of z_i; a second barrier completes it;
+//   * u_i = A z_i / s: each block its own rows, from its copy of z_i (a block keeps the
+//     whole current z_i and its own columns of every z_j of the step, for the update:
+//     with the rest of the vectors this leaves most of the shared memory to its rows);
+//   * the moments, ||r||² and the FP64 residual's norm are block partials (warp sums,
+//     then the warps' sums in a fixed butterfly) that the blocks publish and add in rank
+//     order, so every block holds the same FP64 values and takes the same auxiliary solve
+//     and stop tests: every branch that encloses a cluster barrier depends on those
+//     shared values only;
+//   * x is updated in column slices; the FP64 residual b - A x reads the whole x from
+//     global memory after a fence and a cluster barrier.
 // Every block signals the dependent launch (the single-block kernel that takes the
 // other systems) as soon as it starts, so that the clusters are placed first and that
 // kernel's blocks fill the remaining SMs, and each SM a cluster leaves.
 constexpr int kWideNT = 512;
-constexpr int kWideMaxC = 8;
+constexpr int kWideMaxC = 16;
 
 struct WideShared {
     double slot[2][2 * kTMax + 2];   // this block's published partial sums (two sets)
     double sum[2 * kTMax + 2];       // the cluster's sums of the last published set
+    double wred[2 * kTMax][kWideNT / 32];   // per value: the warps' partial sums
     int32_t q;                       // the system the cluster took (rank 0 writes every block's copy)
 };
 
@@ -1323,6 +1329,8 @@ batch_cta_w(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
             double* __restrict__ xvec, BatchOut out, int32_t* queue, BatchParams P) {
     using TC = typename Elem<TA>::TC;
     constexpr int NT = kWideNT;
+    constexpr int NW = NT / 32;
+    constexpr bool kScatter = std::is_same_v<TC, double>;   // reduce-scatter, then all-gather
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks(), cr = (int)cl.block_rank();
@@ -1331,22 +1339,38 @@ batch_cta_w(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TA* As = reinterpret_cast<TA*>(smem_raw);
     TC* vec = reinterpret_cast<TC*>(smem_raw + ((P.a_cap * (int64_t)sizeof(TA) + 15) & ~(int64_t)15));
+    constexpr int kZpBufs = kScatter ? 1 : 2;
     TC* r = vec;                                     // m_cap (the block's rows)
     TC* u = r + P.m_cap;                             // t_max x m_cap
-    TC* z = u + (int64_t)P.t_max * P.m_cap;          // t_max x n_cap (whole vectors)
-    TC* zp = z + (int64_t)P.t_max * P.n_cap;         // 2 x n_cap: the published partial products
-    TC* dx = zp + 2 * (int64_t)P.n_cap;              // n_cap (the block's columns are used)
-    TC* part = dx + P.n_cap;                         // NT x V
+    TC* zf = u + (int64_t)P.t_max * P.m_cap;         // n_cap: the whole current z_i
+    TC* zs = zf + P.n_cap;                           // t_max x nc_cap: the block's columns of every z_j
+    TC* zp = zs + (int64_t)P.t_max * P.nc_cap;       // kZpBufs x n_cap: the published partial products
+    TC* dx = zp + kZpBufs * (int64_t)P.n_cap;        // nc_cap: the block's columns
+    TC* part = dx + P.nc_cap;                        // NT x V
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    int par = 0;      // partial-product buffer of the next product
+    int par = 0;      // partial-product buffer of the next product (FP32 chain: two)
     int spar = 0;     // slot set of the next cluster sum
 
+    // a block sum in two steps: the warp's sum at wred[j][warp] (no barrier) ...
+    auto warp_part = [&](SqAcc<TC> a, int j) {
+        a = warp_sum_sq(a);
+        if (lane == 0) a.put(&W.wred[j][warp]);
+    };
+    // ... and, after a block barrier, values 0 .. k-1 added over the warps by a fixed
+    // butterfly (warp j: value j) and published in this block's slot set spar
+    auto publish = [&](int k) {
+        for (int j = warp; j < k; j += NW) {
+            SqAcc<TC> a = lane < NW ? SqAcc<TC>::get(&W.wred[j][lane]) : SqAcc<TC>{};
+            a = warp_sum_sq(a);
+            if (lane == 0) W.slot[spar][j] = a.value();
+        }
+    };
     // W.sum[0, k) = the cluster's sums of the k values every block published in its slot
     // set spar: warp j adds value j over the blocks by a fixed butterfly (lanes beyond the
     // cluster hold exact zeros), so every block gets the same bits
     auto cluster_sums = [&](int k) {
         cl.sync();
-        for (int j = warp; j < k; j += NT / 32) {
+        for (int j = warp; j < k; j += NW) {
             double v = 0.0;
             if (lane < C) v = cl.map_shared_rank(&W.slot[spar][0], lane)[j];
 #pragma unroll
@@ -1362,32 +1386,43 @@ batch_cta_w(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
         cluster_sums(1);
         return W.sum[0];
     };
-    // dst = (Aᵀ v) * scale, whole, from the blocks' partial products over their rows;
-    // returns the sum of squares over this block's column slice [c0, c1)
-    auto full_t = [&](const TA* A, int mo, int n, int ld, const TC* v, TC* dst, double scale, int c0,
+    // zf = (Aᵀ v) * scale, whole, in every block, from the blocks' partial products over
+    // their rows, and the block's columns [c0, c1) also into slice (unless null); returns
+    // their sum of squares
+    auto full_t = [&](const TA* A, int mo, int n, int ld, const TC* v, TC* slice, double scale, int c0,
                       int c1) -> SqAcc<TC> {
         TC* mine = zp + (int64_t)par * P.n_cap;
         prod_t<TA, NT>(A, mo, n, ld, v, mine, part, 1.0);
         cl.sync();                                   // every block's partial is complete
-        const TC* peer[kWideMaxC];
-#pragma unroll
-        for (int j = 0; j < kWideMaxC; ++j) peer[j] = cl.map_shared_rank(mine, j < C ? j : 0);
         const TC sc = (TC)scale;
         SqAcc<TC> sq;
-        for (int c = tid; c < n; c += NT) {
-            TC pv[kWideMaxC];
-#pragma unroll
-            for (int j = 0; j < kWideMaxC; ++j) pv[j] = j < C ? peer[j][c] : (TC)0;
-            TC acc = pv[0];
-#pragma unroll
-            for (int j = 1; j < kWideMaxC; ++j)
-                if (j < C) acc += pv[j];
-            const TC zv = acc * sc;
-            dst[c] = zv;
-            if (c >= c0 && c < c1) sq.add(zv);
+        if constexpr (kScatter) {
+            for (int c = c0 + tid; c < c1; c += NT) {
+                TC acc = 0;
+#pragma unroll 4
+                for (int j = 0; j < C; ++j) acc += *cl.map_shared_rank(mine + c, j);
+                const TC zv = acc * sc;
+#pragma unroll 4
+                for (int j = 0; j < C; ++j) *cl.map_shared_rank(zf + c, j) = zv;
+                if (slice) slice[c - c0] = zv;
+                sq.add(zv);
+            }
+            cl.sync();                               // every block holds the whole zf
+        } else {
+            for (int c = tid; c < n; c += NT) {
+                TC acc = 0;
+#pragma unroll 4
+                for (int j = 0; j < C; ++j) acc += *cl.map_shared_rank(mine + c, j);
+                const TC zv = acc * sc;
+                zf[c] = zv;
+                if (c >= c0 && c < c1) {
+                    if (slice) slice[c - c0] = zv;
+                    sq.add(zv);
+                }
+            }
+            __syncthreads();                         // zf complete before it is read
         }
-        __syncthreads();                             // dst complete before it is read
-        par ^= 1;
+        if constexpr (!kScatter) par ^= 1;
         return sq;
     };
 
@@ -1418,9 +1453,8 @@ batch_cta_w(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
             A = As;
         }
         for (int c = c0 + tid; c < c1; c += NT) __stcg(x + c, 0.0);
-        for (int c = tid; c < P.n_cap; c += NT) dx[c] = 0;
-        for (int i = 0; i < P.t_max; ++i)
-            for (int c = tid; c < P.n_cap; c += NT) z[(int64_t)i * P.n_cap + c] = 0;
+        for (int c = tid; c < P.nc_cap; c += NT) dx[c] = 0;
+        for (int c = tid; c < P.n_cap; c += NT) zf[c] = 0;   // (prod_n reads the padding)
         double bb = 0.0;
         for (int i = tid; i < mo; i += NT) {
             r[i] = (TC)b[i];
@@ -1430,16 +1464,16 @@ batch_cta_w(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
         const double bn2 = cluster_total(block_sum2<NT>(bb, 0.0, S.red).x);
         double nrm_thr = 0.0;
         if (P.tol_n2 > 0.0 && bn2 > 0.0) {   // ||Aᵀ b||²
-            const SqAcc<TC> mt = full_t(A, mo, n, ld, r, z, 1.0, c0, c1);
+            const SqAcc<TC> mt = full_t(A, mo, n, ld, r, nullptr, 1.0, c0, c1);
             nrm_thr = P.tol_n2 * cluster_total(block_sum_sq<NT>(mt, SqAcc<TC>{}, S.red).x);
-            for (int c = tid; c < n; c += NT) z[c] = 0;
+            for (int c = tid; c < n; c += NT) zf[c] = 0;
         }
         // fold dx into the block's columns of x, then r = b - A x in FP64 over the block's
         // rows (the whole x from global memory); returns the cluster's ||r||²
         auto true_residual = [&]() -> double {
             for (int c = c0 + tid; c < c1; c += NT) {
-                __stcg(x + c, __ldcg(x + c) + (double)dx[c]);
-                dx[c] = 0;
+                __stcg(x + c, __ldcg(x + c) + (double)dx[c - c0]);
+                dx[c - c0] = 0;
             }
             __threadfence();
             cl.sync();
@@ -1470,17 +1504,13 @@ batch_cta_w(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
             // the chain u_0 = r, z_i = Aᵀ u_{i-1} / s, u_i = A z_i / s
             const TC* uprev = r;
             for (int i = 1; i <= t; ++i) {
-                TC* zi = z + (int64_t)(i - 1) * P.n_cap;
                 TC* ui = u + (int64_t)(i - 1) * P.m_cap;
-                const SqAcc<TC> p1 = full_t(A, mo, n, ld, uprev, zi, d.inv_s, c0, c1);
-                const SqAcc<TC> p2 = prod_n<TA, NT>(A, mo, n, ld, zi, ui, d.inv_s);
-                const double2 ph = block_sum_sq<NT>(p1, p2, S.red);   // also completes ui
-                if (tid == 0) {
-                    W.slot[spar][2 * i - 2] = ph.x;
-                    W.slot[spar][2 * i - 1] = ph.y;
-                }
+                warp_part(full_t(A, mo, n, ld, uprev, zs + (int64_t)(i - 1) * P.nc_cap, d.inv_s, c0, c1), 2 * i - 2);
+                warp_part(prod_n<TA, NT>(A, mo, n, ld, zf, ui, d.inv_s), 2 * i - 1);
+                __syncthreads();   // ui complete before the next product reads it
                 uprev = ui;
             }
+            publish(2 * t);
             cluster_sums(2 * t);
             if (tid < 32) {   // the auxiliary solve by one warp of every block (the same bits)
                 if (tid < 2 * t) S.phi[tid + 1] = W.sum[tid];
@@ -1509,9 +1539,9 @@ batch_cta_w(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
                 bu[j] = reinterpret_cast<const TC*>(S.coef)[j];
                 bz[j] = reinterpret_cast<const TC*>(S.coef)[kTMax + j];
             }
-            for (int c = c0 + tid; c < c1; c += NT) {
+            for (int c = tid; c < c1 - c0; c += NT) {
                 TC v = dx[c];
-                for (int j = 0; j < t; ++j) v = fma(bz[j], z[(int64_t)j * P.n_cap + c], v);
+                for (int j = 0; j < t; ++j) v = fma(bz[j], zs[(int64_t)j * P.nc_cap + c], v);
                 dx[c] = v;
             }
             SqAcc<TC> sq;
@@ -1521,7 +1551,11 @@ batch_cta_w(const SysDesc* __restrict__ sys, const int32_t* __restrict__ order, 
                 r[i] = v;
                 sq.add(v);
             }
-            rn2 = cluster_total(block_sum_sq<NT>(sq, SqAcc<TC>{}, S.red).x);
+            warp_part(sq, 0);
+            __syncthreads();
+            publish(1);
+            cluster_sums(1);
+            rn2 = W.sum[0];
             ++k;
             is_true = false;
             if (P.R > 0 && k % P.R == 0) need_true = true;
@@ -1627,6 +1661,9 @@ size_t vec_bytes(const BatchParams& P, int nt) {
 
 // dynamic shared memory a block may ask for (the static Shared block and slack aside)
 constexpr int64_t kBatchSmemMax = 232448 - 2048;
+// the same for the cluster kernel (its static block also holds the warps' partial sums)
+constexpr int64_t kWideSmemMax = 232448 - 4096;
+static_assert(sizeof(Shared) + sizeof(WideShared) + 256 <= 4096, "the cluster kernel's static shared memory");
 
 template <class TA>
 void set_attrs(cudaError_t& attr) {
@@ -1642,7 +1679,11 @@ void set_attrs(cudaError_t& attr) {
     set((const void*)batch_cta<TA, 256, 1>);
     set((const void*)batch_cta<TA, 256, 2>);
     set((const void*)batch_cta<TA, 512, 1>);
-    set((const void*)batch_cta_w<TA>);
+    if (attr == cudaSuccess)
+        attr = cudaFuncSetAttribute((const void*)batch_cta_w<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kWideSmemMax);
+    if (attr == cudaSuccess)   // clusters of 16 blocks
+        attr = cudaFuncSetAttribute((const void*)batch_cta_w<TA>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
 cudaError_t prepare_kernels() {
@@ -1868,16 +1909,18 @@ bool wide_params(const tacta_batch_s* B, const tacta_options& o, int C, BatchPar
     BatchParams P = base_params(B, o);
     P.m_cap = ((B->m_max + C - 1) / C + 7) & ~7;   // a block's rows
     P.n_cap = (B->n_max + 7) & ~7;
+    P.nc_cap = ((B->n_max + C - 1) / C + 7) & ~7;  // a block's columns
     const int V = B->storage == TACTA_BATCH_FP64 ? 2 : B->storage == TACTA_BATCH_FP32 ? 4 : 8;
     const int tc = B->storage == TACTA_BATCH_FP64 ? 8 : 4;
     const int64_t es = (int64_t)elem_size(B->storage);
-    const int64_t vb =
-        ((int64_t)P.m_cap * (1 + P.t_max) + (int64_t)P.n_cap * (P.t_max + 3) + (int64_t)kWideNT * V) * tc;
-    const int64_t a_bytes = kBatchSmemMax - vb - 16;
+    const int zp_bufs = B->storage == TACTA_BATCH_FP64 ? 1 : 2;   // the kernel's kZpBufs
+    const int64_t vb = ((int64_t)P.m_cap * (1 + P.t_max) + (int64_t)P.n_cap * (1 + zp_bufs) +
+                        (int64_t)P.nc_cap * (1 + P.t_max) + (int64_t)kWideNT * V) * tc;
+    const int64_t a_bytes = kWideSmemMax - vb - 16;
     if (a_bytes < 0) return false;
     P.a_cap = (a_bytes / 16) * 16 / es;
     *smem_out = (size_t)(((P.a_cap * es + 15) & ~15) + vb);
-    if ((int64_t)*smem_out > kBatchSmemMax) return false;
+    if ((int64_t)*smem_out > kWideSmemMax) return false;
     *out = P;
     return true;
 }
@@ -2026,7 +2069,7 @@ double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const
         WidePlan p{};
         p.systems = std::min(B->wide_mode, count);
         int maxc = 0;
-        for (int C : {8, 4, 2, 1}) {
+        for (int C : {16, 8, 4, 2, 1}) {
             if (B->wide_cluster > 0 && C != B->wide_cluster) continue;
             if (fits(C, &maxc)) { p.cluster = C; break; }
         }
@@ -2050,7 +2093,7 @@ double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const
     double best = simulate_makespan({}, 0, 1, all, B->sms, per_sm);
     std::vector<int32_t> best_wide;
     const double balanced = total / ((double)B->sms * per_sm);
-    for (int C : {8, 4, 2}) {
+    for (int C : {16, 8, 4, 2}) {
         int maxc = 0;
         if (!fits(C, &maxc)) continue;
         const double e = B->eff[C] > 0.0 ? B->eff[C] : 0.5;
@@ -2386,7 +2429,7 @@ extern "C" tacta_status tacta_batch_set_wide(tacta_batch B, int32_t systems, int
     g_batch_err.clear();
     if (!B) { g_batch_err = "NULL batch"; return TACTA_ERR_INVALID; }
     if (systems < -1 || cluster < 0 || cluster > kWideMaxC || clusters < 0) {
-        g_batch_err = "systems must be >= -1, cluster in 0..8, clusters >= 0";
+        g_batch_err = "systems must be >= -1, cluster in 0..16, clusters >= 0";
         return TACTA_ERR_INVALID;
     }
     B->wide_mode = systems;
