@@ -1642,6 +1642,18 @@ constexpr int kStreamNW = 8;
 template <class TA> constexpr int stream_jv() { return std::is_same_v<TA, __nv_bfloat16> ? 4 : 8; }
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
+// A system's time on a C-block cluster, modelled per step as the larger of its one-block
+// time / C and -- when a block's rows do not fit its shared memory -- the time to stream
+// them (2 t_mean passes at kWideRowBw per SM), plus h0 + h1 C: the per-step work that
+// does not shrink with C (the auxiliary solve, the cluster barriers and exchanges, the
+// update) and a part that grows with the blocks to exchange with. h0 is learned from
+// the clustered solves (this value before any); h1 and the bandwidth are fixed. (Fitted
+// on 4096-system batches: FP64 h(8) = 17, h(16) = 21 us per step, FP32 14 / 18, BF16
+// 17 / 20; FP32 rows streamed at ~40 GB/s per SM next to the single-block kernel.)
+constexpr double kWideH0 = 12000.0;   // ns per step
+constexpr double kWideH1 = 500.0;     // ns per step and block of the cluster
+constexpr double kWideRowBw = 40.0;   // bytes per ns and SM
+
 // the cluster kernel's share of a solve
 struct WidePlan {
     int32_t systems = 0;    // the first `systems` entries of the queue order
@@ -1814,10 +1826,10 @@ struct tacta_batch_s {
     int64_t* stamps = nullptr;     // 2 x count: per-system begin and end clocks of the last solve
     std::vector<int32_t> last_iters;   // host: every system's step count in the last full solve
     std::vector<int32_t> ord;          // host copy of the queue order
-    std::vector<int32_t> m_of;         // per system: rows
+    std::vector<int32_t> m_of, n_of;   // per system: rows, columns
     std::vector<double> dur;           // per system: predicted time (ns) on one block of the configuration
     std::vector<char> dur_meas;        // per system: dur was measured on one block (not derived)
-    double eff[kWideMaxC + 1] = {};    // learned speed of a C-block cluster (see plan_batch)
+    double wide_h0 = -1.0;            // learned per-step overhead of a cluster (ns; < 0: none yet)
     int32_t wide_mode = -1;            // cluster kernel: -1 planned, 0 off, > 0 that many systems
     int32_t wide_cluster = 0, wide_clusters = 0;   // asked for with wide_mode > 0 (0: chosen)
     WidePlan plan;                     // the cluster kernel's share of the next solve
@@ -2033,16 +2045,37 @@ double simulate_makespan(const std::vector<double>& w, int clusters, int C, cons
     return end;
 }
 
+// the mean order t of the step-order schedule (one period)
+double mean_order(int t_max, int cycle) {
+    if (cycle == TACTA_CYCLE_FIXED || t_max == 1) return t_max;
+    if (cycle == TACTA_CYCLE_SAWTOOTH) return 0.5 * (t_max + 1);
+    const int period = 2 * t_max - 2;
+    double sum = 0.0;
+    for (int j = 0; j < period; ++j) sum += j < t_max ? j + 1 : 2 * t_max - 1 - j;
+    return sum / period;
+}
+
+// the cluster-time model above for system q on C blocks (a_cap: the elements of A a block
+// stages; one-block time dur, steps, mean order tm, overhead h0)
+double cluster_time_model(const tacta_batch_s* B, int32_t q, int C, int64_t a_cap, double dur, double steps,
+                          double tm, double h0) {
+    const int64_t ld = B->storage == TACTA_BATCH_BF16 ? ((B->n_of[q] + 15) & ~15) + 8 : (B->n_of[q] + 7) & ~7;
+    const int64_t rows = (B->m_of[q] + C - 1) / C;
+    const double stream = rows * ld <= a_cap ? 0.0 : 2.0 * tm * rows * ld * elem_size(B->storage) / kWideRowBw;
+    return std::max(dur / C, steps * stream) + steps * (h0 + kWideH1 * C);
+}
+
 // The queue order and the cluster kernel's share of the next solve, from the predicted
-// one-block times dur (ns; all zero: unknown). The order is longest first. With the
-// planner on (wide_mode -1) and the times known, the plan is the one of least simulated
-// makespan among: no clusters, and, for C = 8, 4, 2 (where the vectors fit), the K = 1,
-// 2, ... longest systems with at least 4 C rows and at least half the balanced time
-// (sum dur / blocks), on min(K, resident clusters) clusters, a system's cluster time
-// taken as dur / (C per_sm eff_C) with eff_C learned from earlier solves (0.5 before
-// any). wide_mode > 0 forces that many systems from the head of the order onto clusters
-// (of wide_cluster blocks, or the largest C that fits; wide_clusters of them, or as many
-// as are resident). Returns the simulated makespan in ms (0 when the times are unknown).
+// one-block times dur (ns; all zero: unknown) and the step counts of the last full
+// solve. The order is longest first. With the planner on (wide_mode -1) and the times
+// known, the plan is the one of least simulated makespan among: no clusters, and, for
+// C = 16, 8, 4, 2 (where the vectors fit), the K = 1, 2, ... (at most 96) longest
+// systems with at least 4 C rows and at least a quarter of the balanced time (sum dur /
+// blocks), on min(K, resident clusters) clusters, a system's cluster time by the model
+// above (cluster_time_model). wide_mode > 0 forces that
+// many systems from the head of the order onto clusters (of wide_cluster blocks, or the
+// largest C that fits; wide_clusters of them, or as many as are resident). Returns the
+// simulated makespan in ms (0 when the times are unknown).
 double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const std::vector<double>& dur,
                   WidePlan* plan_out, std::vector<int32_t>* ord_out) {
     const int count = B->count;
@@ -2050,6 +2083,14 @@ double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const
     std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t c) { return dur[a] > dur[c]; });
     const bool known = count > 0 && std::all_of(dur.begin(), dur.end(), [](double v) { return v > 0.0; });
     const int per_sm = kConfigs[cfg].per_sm;
+    const bool have_iters = B->last_iters.size() == (size_t)count;
+    const double h0 = B->wide_h0 >= 0.0 ? B->wide_h0 : kWideH0;
+    const double tm = mean_order(o.t_max, o.cycle);
+    int64_t a_cap_c = 0;   // of the cluster size being scored
+    auto cluster_time = [&](int32_t q, int C) {
+        const double steps = have_iters ? (double)B->last_iters[q] : 0.0;
+        return cluster_time_model(B, q, C, a_cap_c, dur[q], steps, tm, h0);
+    };
     *plan_out = WidePlan{};
     *ord_out = ord;
     if (B->wide_mode == 0 || count == 0) {
@@ -2062,6 +2103,7 @@ double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const
         BatchParams Pw{};
         size_t smw = 0;
         if (!wide_params(B, o, C, &Pw, &smw)) return false;
+        a_cap_c = Pw.a_cap;
         *maxc = wide_max_clusters_for(B, C, smw);
         return *maxc > 0;
     };
@@ -2078,10 +2120,14 @@ double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const
         if (B->wide_clusters > 0) p.clusters = std::min(p.clusters, B->wide_clusters);
         *plan_out = p;
         if (!known) return 0.0;
+        // the clusters take their systems longest (in cluster time) first
+        std::stable_sort(ord.begin(), ord.begin() + p.systems, [&](int32_t a, int32_t c) {
+            return cluster_time(a, p.cluster) > cluster_time(c, p.cluster);
+        });
+        *ord_out = ord;
         std::vector<double> w, d;
-        const double e = B->eff[p.cluster] > 0.0 ? B->eff[p.cluster] : 0.5;
         for (int j = 0; j < count; ++j) {
-            if (j < p.systems) w.push_back(dur[ord[j]] / (p.cluster * per_sm * e));
+            if (j < p.systems) w.push_back(cluster_time(ord[j], p.cluster));
             else d.push_back(dur[ord[j]]);
         }
         return simulate_makespan(w, p.clusters, p.cluster, d, B->sms, per_sm) * 1e-6;
@@ -2092,22 +2138,23 @@ double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const
     for (int32_t s_ : ord) { all.push_back(dur[s_]); total += dur[s_]; }
     double best = simulate_makespan({}, 0, 1, all, B->sms, per_sm);
     std::vector<int32_t> best_wide;
+    int64_t best_a_cap = 0;
     const double balanced = total / ((double)B->sms * per_sm);
     for (int C : {16, 8, 4, 2}) {
         int maxc = 0;
         if (!fits(C, &maxc)) continue;
-        const double e = B->eff[C] > 0.0 ? B->eff[C] : 0.5;
         std::vector<int32_t> elig;   // positions in ord
-        for (int j = 0; j < count && elig.size() < 32; ++j)
-            if (B->m_of[ord[j]] >= 4 * C && dur[ord[j]] >= 0.5 * balanced) elig.push_back(j);
+        for (int j = 0; j < count && elig.size() < 96; ++j)
+            if (B->m_of[ord[j]] >= 4 * C && dur[ord[j]] >= 0.25 * balanced) elig.push_back(j);
         std::vector<char> wide((size_t)count, 0);
         for (size_t K = 1; K <= elig.size(); ++K) {
             wide[elig[K - 1]] = 1;
             std::vector<double> w, d;
             for (int j = 0; j < count; ++j) {
-                if (wide[j]) w.push_back(dur[ord[j]] / (C * per_sm * e));
+                if (wide[j]) w.push_back(cluster_time(ord[j], C));
                 else d.push_back(dur[ord[j]]);
             }
+            std::sort(w.begin(), w.end(), std::greater<double>());
             const int cl = std::min((int)K, maxc);
             const double ms = simulate_makespan(w, cl, C, d, B->sms, per_sm);
             if (ms < 0.98 * best) {
@@ -2116,6 +2163,7 @@ double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const
                 plan_out->cluster = C;
                 plan_out->clusters = cl;
                 best_wide.assign(elig.begin(), elig.begin() + K);
+                best_a_cap = a_cap_c;
             }
         }
     }
@@ -2123,6 +2171,11 @@ double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const
         std::vector<char> wide((size_t)count, 0);
         std::vector<int32_t> o2;
         for (int32_t j : best_wide) { wide[j] = 1; o2.push_back(ord[j]); }
+        const int Cb = plan_out->cluster;
+        a_cap_c = best_a_cap;
+        std::stable_sort(o2.begin(), o2.end(), [&](int32_t a, int32_t c) {
+            return cluster_time(a, Cb) > cluster_time(c, Cb);
+        });
         for (int j = 0; j < count; ++j)
             if (!wide[j]) o2.push_back(ord[j]);
         *ord_out = o2;
@@ -2239,6 +2292,7 @@ extern "C" tacta_status tacta_batch_create(int32_t count, const int32_t* m, cons
         });
         B->ord = ord;
         B->m_of.assign(m, m + count);
+        B->n_of.assign(n, n + count);
         B->dur.assign((size_t)count, 0.0);
         B->dur_meas.assign((size_t)count, 0);
         BCHK(cudaMemcpyAsync(B->sys, d.data(), sizeof(SysDesc) * count, cudaMemcpyHostToDevice, s));
@@ -2374,37 +2428,48 @@ extern "C" tacta_status tacta_batch_cta(tacta_batch B, const double* b, double* 
     }
     // What the next solve plans with (a system's result does not depend on the block or
     // the moment that takes it; on a cluster, its sums run in another order): each
-    // system's time on one block -- measured where one block solved it; for a system a
-    // cluster solved, the learned cluster speed eff_C = sum of the one-block times
-    // measured before / (C per_sm sum of the cluster times), and a system without an
-    // earlier one-block time is given cluster time x C per_sm eff_C. The step counts stay
-    // on the host for the autotuner's makespan estimate.
+    // system's time on one block -- measured where one block solved it -- and the step
+    // counts. From the systems a cluster solved that have an earlier one-block time, the
+    // per-step overhead h0 of the cluster-time model (cluster_time_model) is refitted: the
+    // step-weighted mean of what the measured cluster time leaves over the model with
+    // h0 = 0. A system without an earlier one-block time is given (cluster time - steps
+    // (h0 + h1 C)) C, at least its cluster time.
     B->last_iters.resize((size_t)B->count);
     BTRY(cudaMemcpy(B->last_iters.data(), B->iters, sizeof(int32_t) * B->count, cudaMemcpyDeviceToHost));
     std::vector<int64_t> st((size_t)2 * B->count);
     BTRY(cudaMemcpy(st.data(), B->stamps, sizeof(int64_t) * 2 * B->count, cudaMemcpyDeviceToHost));
     const int64_t* tb = st.data();
     const int64_t* te = st.data() + B->count;
-    const int per_sm = kConfigs[cfg].per_sm;
     const int K = std::min(plan.systems, B->count), C = plan.cluster;
-    double num = 0.0, den = 0.0;
+    int64_t a_cap_w = 0;
+    if (K > 0) {
+        BatchParams Pw{};
+        size_t smw = 0;
+        if (wide_params(B, o, C, &Pw, &smw)) a_cap_w = Pw.a_cap;
+    }
+    const double tm = mean_order(o.t_max, o.cycle);
+    double hnum = 0.0, hden = 0.0;
     for (int j = 0; j < B->count; ++j) {
         const int32_t q = B->ord[j];
         const double meas = std::max(1.0, (double)(te[q] - tb[q]));
         if (j >= K) {
             B->dur[q] = meas;
             B->dur_meas[q] = 1;
-        } else if (B->dur_meas[q]) {
-            num += B->dur[q];
-            den += (double)C * per_sm * meas;
+        } else if (B->dur_meas[q] && B->last_iters[q] > 0) {
+            // the model's time with h0 = 0, subtracted from the measured time
+            const double steps = (double)B->last_iters[q];
+            hnum += meas - cluster_time_model(B, q, C, a_cap_w, B->dur[q], steps, tm, 0.0);
+            hden += steps;
         }
     }
-    if (den > 0.0) B->eff[C] = std::min(1.0, std::max(0.05, num / den));
+    if (hden > 0.0) B->wide_h0 = std::min(2e5, std::max(0.0, hnum / hden));
     for (int j = 0; j < K; ++j) {
         const int32_t q = B->ord[j];
         if (!B->dur_meas[q]) {
-            const double e = B->eff[C] > 0.0 ? B->eff[C] : 0.5;
-            B->dur[q] = std::max(1.0, (double)(te[q] - tb[q])) * C * per_sm * e;
+            const double meas = std::max(1.0, (double)(te[q] - tb[q]));
+            const double h0 = B->wide_h0 >= 0.0 ? B->wide_h0 : kWideH0;
+            const double steps = (double)B->last_iters[q];
+            B->dur[q] = std::max(meas, (meas - steps * (h0 + kWideH1 * C)) * C);
         }
     }
     return TACTA_OK;
