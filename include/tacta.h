@@ -349,10 +349,11 @@ tacta_status tacta_batch_cta(tacta_batch batch, const double* b, double* x, int3
 
 /* Launch configurations: threads per block and resident blocks per SM. The autotuner
    times every configuration that fits on (batch, b) with the given options (max_iter caps
-   each system's steps), keeps the best for later solves and returns its index and score
-   (ms): before any full solve the capped run's time; after one, the time of a full solve
-   that the capped run predicts -- the largest over the systems of its time per step times
-   its step count in the last full solve (a batch takes its slowest system's time).
+   each system's steps; single blocks only), keeps the best for later solves and returns
+   its index and score (ms): before any full solve the capped run's time; after one, the
+   makespan of a full solve that the capped run predicts -- every system's one-block time
+   taken as its time per step in the capped run times its step count in the last full
+   solve, then the planner's simulated makespan with those times (tacta_batch_set_wide).
    set_config picks one (-1: the default). tacta_batch_config_tensor_cores(c) is 1 when configuration c runs
    the chain's products on the tensor cores (BF16 tiles, mma.sync m16n8k16 with FP32
    accumulation, the FP32 chain vectors carried exactly as three BF16 terms): it admits
@@ -386,7 +387,10 @@ tacta_status tacta_batch_timeline(tacta_batch batch, int64_t* t_begin_ns, int64_
    other systems on the remaining SMs and on each SM a cluster leaves.
      systems -1 (default): planned before each solve from the measured times of the
                 earlier solves (none before the first): the share of least simulated
-                makespan (tacta_batch_wide_plan);
+                makespan (tacta_batch_wide_plan). A system's time on a C-block cluster is
+                modelled per step as the larger of its one-block time / C and the time to
+                stream a block's rows when they exceed its shared memory, plus an overhead
+                h0 + h1 C refitted after every clustered solve;
      systems 0: off;
      systems > 0: that many systems from the head of the queue order (longest first by
                 the last solve; largest m_s n_s first before any), on clusters of
