@@ -300,12 +300,15 @@ tacta_status tacta_residual_static(const tacta_matrix* A, const double* x, const
  *   Many independent systems A_s x_s = b_s (s = 0 .. count-1), A_s dense m_s x n_s,
  *   each solved by CTA (Alg. 1.1 with H = A_s A_sᵀ and the t-cycling of Sec. 5.1)
  *   from x_s = 0, so that x_s stays in range(A_sᵀ) (Thm. thmone (4)) and a consistent
- *   rank-deficient system yields the minimum-norm solution. All systems run in one
- *   persistent kernel launch (replayed as a CUDA graph when opt->use_graph is set):
- *   each thread block takes the next unsolved system from a queue, ordered longest
- *   first by the previous solve's measured time per system (the first solve: largest
- *   m_s n_s first), so the slowest systems start at once and short ones fill the tail.
- *   The paper treats one system at a time; batching is this library's extension.
+ *   rank-deficient system yields the minimum-norm solution. The systems run in one
+ *   persistent launch of a single-block kernel (replayed as a CUDA graph when
+ *   opt->use_graph is set): each thread block takes the next unsolved system from a
+ *   queue, ordered longest first by the earlier solves' measured time per system (the
+ *   first solve: largest m_s n_s first), so the slowest systems start at once and short
+ *   ones fill the tail. From the second solve on, the longest systems can go to thread-
+ *   block clusters of a second persistent launch that starts first
+ *   (tacta_batch_set_wide). The paper treats one system at a time; batching is this
+ *   library's extension.
  *
  *   Storage of the copy of A_s that the chain z_i = Aᵀ u_{i-1}, u_i = A z_i reads:
  *     TACTA_BATCH_FP64 -- FP64 chain; the iteration follows the FP64 path exactly.

@@ -1,4 +1,6 @@
-// Batched dense CTA: many independent systems A_s x_s = b_s in one persistent launch.
+// Batched dense CTA: many independent systems A_s x_s = b_s in one persistent launch
+// (the longest systems, from the second solve on, in a cluster kernel launched first:
+// see batch_cta_w and plan_batch).
 //
 // Each block takes the next unsolved system from a queue (longest first by the previous
 // solve's measured time per system; largest first on the first solve) and runs
