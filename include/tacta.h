@@ -419,6 +419,37 @@ tacta_status tacta_batch_wide_plan(tacta_batch batch, const tacta_options* opt, 
    cluster jobs without clusters). */
 double tacta_batch_simulate_makespan(const double* w, int32_t nw, int32_t clusters, int32_t cluster, const double* d,
                                      int32_t nd, int32_t sms, int32_t per_sm);
+/* tacta_batch_plan_search -- the planner that tacta_batch_cta runs before each solve,
+   on the host (no device needed), given what the solve would take from the device.
+     dur[count]       each system's one-block time (ns); all > 0, else "unknown": no plan
+     steps[count]     its step count in the last full solve (NULL: 0)
+     m, n[count]      its shape (the rows a block of a cluster holds, the row length)
+     storage, t_max, cycle   as in tacta_batch_create / tacta_options
+     sms, per_sm      the device's SMs and the launch configuration's blocks per SM
+     max_clusters[5], a_cap[5]   for cluster sizes 16, 8, 4, 2, 1: how many clusters can
+                      be resident (0: the size's vectors do not fit a block) and how many
+                      elements of A a block stages in shared memory
+     wide_mode, wide_cluster, wide_clusters   as in tacta_batch_set_wide
+     h0               the cluster-time model's per-step overhead (ns; 12000 before any
+                      clustered solve)
+   A system's time on a C-block cluster is modelled per step as the larger of its
+   one-block time / C and, when a block's ceil(m/C) rows exceed a_cap, the time to stream
+   them (2 x the schedule's mean order passes at 40 GB/s), plus h0 + 500 ns x C. With the
+   planner on (wide_mode -1) the plan is the one of least simulated makespan
+   (tacta_batch_simulate_makespan) among: no clusters, and for C = 16, 8, 4, 2 the K = 1,
+   2, ... (at most 96) longest systems with at least 4C rows and at least a quarter of the
+   balanced time (sum dur / (sms per_sm)), on min(K, max_clusters) clusters; a plan must
+   beat the best so far by 2%. Out: plan[3] = systems, cluster size, clusters (0, 0, 0:
+   none) and order[count], the queue order (a permutation of 0 .. count-1): the
+   clusters' systems first, longest in cluster time first, then the rest longest first
+   (ties keep system order). Returns the simulated makespan in ms; 0 while the times are
+   unknown; infinity for a forced plan with no cluster size that fits; -1 on invalid
+   arguments. */
+double tacta_batch_plan_search(int32_t count, const double* dur, const int32_t* steps, const int32_t* m,
+                               const int32_t* n, int32_t storage, int32_t t_max, int32_t cycle, int32_t sms,
+                               int32_t per_sm, const int32_t* max_clusters, const int64_t* a_cap, int32_t wide_mode,
+                               int32_t wide_cluster, int32_t wide_clusters, double h0, int32_t* plan,
+                               int32_t* order);
 void tacta_batch_destroy(tacta_batch batch);
 /* message of the last failed tacta_batch_* call on the calling thread */
 const char* tacta_batch_last_error(void);

@@ -71,7 +71,7 @@ EXPORTS = ["tacta_default_options", "cta_solve", "ta_solve", "ta_minnorm", "tact
            "tacta_batch_create", "tacta_batch_cta", "tacta_batch_destroy", "tacta_batch_tune",
            "tacta_batch_set_config", "tacta_batch_num_configs", "tacta_batch_config_shape",
            "tacta_batch_last_error", "tacta_batch_timeline", "tacta_batch_config_tensor_cores", "tacta_batch_config_stage_bytes", "tacta_batch_set_wide",
-           "tacta_batch_wide_plan", "tacta_batch_simulate_makespan", "tacta_aux_solve", "tacta_dia_tile_plan", "tacta_column_partition"]
+           "tacta_batch_wide_plan", "tacta_batch_simulate_makespan", "tacta_batch_plan_search", "tacta_aux_solve", "tacta_dia_tile_plan", "tacta_column_partition"]
 
 _lib_handle = None
 
@@ -142,6 +142,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tacta_batch_simulate_makespan.argtypes = [dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, dp,
                                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
     lib.tacta_batch_simulate_makespan.restype = ctypes.c_double
+    lib.tacta_batch_plan_search.argtypes = [ctypes.c_int32, dp, vp, vp, vp, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_double, vp, vp]
+    lib.tacta_batch_plan_search.restype = ctypes.c_double
     lib.tacta_batch_num_configs.argtypes = []
     lib.tacta_batch_num_configs.restype = ctypes.c_int32
     lib.tacta_batch_config_shape.argtypes = [ctypes.c_int32, i32p, i32p]
@@ -562,6 +566,28 @@ class Batch:
         return float(load_library().tacta_batch_simulate_makespan(
             w.ctypes.data if w.size else None, int(w.size), int(clusters), int(cluster),
             d.ctypes.data if d.size else None, int(d.size), int(sms), int(per_sm)))
+
+    @staticmethod
+    def plan_search(dur, steps, m, n, storage, t_max, cycle, sms, per_sm, max_clusters, a_cap, wide_mode=-1,
+                    wide_cluster=0, wide_clusters=0, h0=12000.0):
+        """The planner (tacta_batch_plan_search; host only): (makespan ms, (systems,
+        cluster, clusters), queue order). max_clusters and a_cap: five entries each, for
+        cluster sizes 16, 8, 4, 2, 1."""
+        dur = np.ascontiguousarray(dur, dtype=np.float64)
+        count = dur.size
+        st = None if steps is None else np.ascontiguousarray(steps, dtype=np.int32)
+        m = np.ascontiguousarray(m, dtype=np.int32)
+        n = np.ascontiguousarray(n, dtype=np.int32)
+        mc = np.ascontiguousarray(max_clusters, dtype=np.int32)
+        ac = np.ascontiguousarray(a_cap, dtype=np.int64)
+        plan = np.zeros(3, dtype=np.int32)
+        order = np.zeros(max(count, 1), dtype=np.int32)
+        ms = load_library().tacta_batch_plan_search(
+            count, dur.ctypes.data if count else None, st.ctypes.data if st is not None else None,
+            m.ctypes.data if count else None, n.ctypes.data if count else None, int(storage), int(t_max),
+            int(cycle), int(sms), int(per_sm), mc.ctypes.data, ac.ctypes.data, int(wide_mode), int(wide_cluster),
+            int(wide_clusters), float(h0), plan.ctypes.data, order.ctypes.data)
+        return float(ms), tuple(int(v) for v in plan), order[:count]
 
     def timeline(self):
         """(t_begin, t_end): int64 device-clock nanoseconds at which each system of the last

@@ -2057,69 +2057,85 @@ double mean_order(int t_max, int cycle) {
     return sum / period;
 }
 
-// the cluster-time model above for system q on C blocks (a_cap: the elements of A a block
-// stages; one-block time dur, steps, mean order tm, overhead h0)
-double cluster_time_model(const tacta_batch_s* B, int32_t q, int C, int64_t a_cap, double dur, double steps,
+// the cluster-time model above for a system of m rows and n columns on C blocks (a_cap:
+// the elements of A a block stages; one-block time dur, steps, mean order tm, overhead h0)
+double cluster_time_model(int storage, int32_t m, int32_t n, int C, int64_t a_cap, double dur, double steps,
                           double tm, double h0) {
-    const int64_t ld = B->storage == TACTA_BATCH_BF16 ? ((B->n_of[q] + 15) & ~15) + 8 : (B->n_of[q] + 7) & ~7;
-    const int64_t rows = (B->m_of[q] + C - 1) / C;
-    const double stream = rows * ld <= a_cap ? 0.0 : 2.0 * tm * rows * ld * elem_size(B->storage) / kWideRowBw;
+    const int64_t ld = storage == TACTA_BATCH_BF16 ? ((n + 15) & ~15) + 8 : (n + 7) & ~7;
+    const int64_t rows = (m + C - 1) / C;
+    const double stream = rows * ld <= a_cap ? 0.0 : 2.0 * tm * rows * ld * elem_size(storage) / kWideRowBw;
     return std::max(dur / C, steps * stream) + steps * (h0 + kWideH1 * C);
 }
 
-// The queue order and the cluster kernel's share of the next solve, from the predicted
-// one-block times dur (ns; all zero: unknown) and the step counts of the last full
-// solve. The order is longest first. With the planner on (wide_mode -1) and the times
-// known, the plan is the one of least simulated makespan among: no clusters, and, for
-// C = 16, 8, 4, 2 (where the vectors fit), the K = 1, 2, ... (at most 96) longest
-// systems with at least 4 C rows and at least a quarter of the balanced time (sum dur /
-// blocks), on min(K, resident clusters) clusters, a system's cluster time by the model
-// above (cluster_time_model). wide_mode > 0 forces that
-// many systems from the head of the order onto clusters (of wide_cluster blocks, or the
-// largest C that fits; wide_clusters of them, or as many as are resident). Returns the
-// simulated makespan in ms (0 when the times are unknown).
-double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const std::vector<double>& dur,
-                  WidePlan* plan_out, std::vector<int32_t>* ord_out) {
-    const int count = B->count;
-    std::vector<int32_t> ord = B->ord;
+// cluster sizes the planner considers, largest first (1: forced plans only)
+constexpr int kPlanSizes[] = {16, 8, 4, 2, 1};
+constexpr int kNumPlanSizes = 5;
+
+// What plan_search needs to know; host data only.
+struct PlanInput {
+    int count = 0;
+    const double* dur = nullptr;      // one-block time per system (ns; all > 0, else unknown)
+    const int32_t* steps = nullptr;   // step count per system in the last full solve (or null)
+    const int32_t* m = nullptr;
+    const int32_t* n = nullptr;
+    const int32_t* ord = nullptr;     // the current queue order
+    int storage = TACTA_BATCH_FP32, t_max = 5, cycle = TACTA_CYCLE_PINGPONG;
+    int sms = 1, per_sm = 1;
+    int wide_mode = -1, wide_cluster = 0, wide_clusters = 0;
+    double h0 = kWideH0;
+    int32_t max_clusters[kNumPlanSizes] = {};   // per kPlanSizes: resident clusters (0: the vectors do not fit)
+    int64_t a_cap[kNumPlanSizes] = {};          // per kPlanSizes: elements of A a block stages
+};
+
+// The queue order and the cluster kernel's share of the next solve. The order is longest
+// first by dur. With the planner on (wide_mode -1) and the times known, the plan is the
+// one of least simulated makespan among: no clusters, and, for C = 16, 8, 4, 2 (where the
+// vectors fit), the K = 1, 2, ... (at most 96) longest systems with at least 4 C rows and
+// at least a quarter of the balanced time (sum dur / blocks), on min(K, resident
+// clusters) clusters, a system's cluster time by cluster_time_model; a plan must beat the
+// best so far by 2%. The clusters' systems come first in the order, longest in cluster
+// time first. wide_mode > 0 forces that many systems from the head of the order onto
+// clusters (of wide_cluster blocks, or the largest C that fits; wide_clusters of them, or
+// as many as are resident). Returns the simulated makespan in ms (0 when the times are
+// unknown; infinite when a forced plan has no cluster size that fits).
+double plan_search(const PlanInput& in, WidePlan* plan_out, std::vector<int32_t>* ord_out) {
+    const int count = in.count;
+    const double* dur = in.dur;
+    std::vector<int32_t> ord(in.ord, in.ord + count);
     std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t c) { return dur[a] > dur[c]; });
-    const bool known = count > 0 && std::all_of(dur.begin(), dur.end(), [](double v) { return v > 0.0; });
-    const int per_sm = kConfigs[cfg].per_sm;
-    const bool have_iters = B->last_iters.size() == (size_t)count;
-    const double h0 = B->wide_h0 >= 0.0 ? B->wide_h0 : kWideH0;
-    const double tm = mean_order(o.t_max, o.cycle);
+    const bool known = count > 0 && std::all_of(dur, dur + count, [](double v) { return v > 0.0; });
+    const int per_sm = in.per_sm;
+    const double tm = mean_order(in.t_max, in.cycle);
     int64_t a_cap_c = 0;   // of the cluster size being scored
     auto cluster_time = [&](int32_t q, int C) {
-        const double steps = have_iters ? (double)B->last_iters[q] : 0.0;
-        return cluster_time_model(B, q, C, a_cap_c, dur[q], steps, tm, h0);
+        const double steps = in.steps ? (double)in.steps[q] : 0.0;
+        return cluster_time_model(in.storage, in.m[q], in.n[q], C, a_cap_c, dur[q], steps, tm, in.h0);
     };
     *plan_out = WidePlan{};
     *ord_out = ord;
-    if (B->wide_mode == 0 || count == 0) {
+    if (in.wide_mode == 0 || count == 0) {
         if (!known) return 0.0;
         std::vector<double> d;
         for (int32_t s_ : ord) d.push_back(dur[s_]);
-        return simulate_makespan({}, 0, 1, d, B->sms, per_sm) * 1e-6;
+        return simulate_makespan({}, 0, 1, d, in.sms, per_sm) * 1e-6;
     }
-    auto fits = [&](int C, int* maxc) {
-        BatchParams Pw{};
-        size_t smw = 0;
-        if (!wide_params(B, o, C, &Pw, &smw)) return false;
-        a_cap_c = Pw.a_cap;
-        *maxc = wide_max_clusters_for(B, C, smw);
-        return *maxc > 0;
+    auto fits = [&](int i, int* maxc) {
+        if (in.max_clusters[i] <= 0) return false;
+        a_cap_c = in.a_cap[i];
+        *maxc = in.max_clusters[i];
+        return true;
     };
-    if (B->wide_mode > 0) {   // forced
+    if (in.wide_mode > 0) {   // forced
         WidePlan p{};
-        p.systems = std::min(B->wide_mode, count);
+        p.systems = std::min(in.wide_mode, count);
         int maxc = 0;
-        for (int C : {16, 8, 4, 2, 1}) {
-            if (B->wide_cluster > 0 && C != B->wide_cluster) continue;
-            if (fits(C, &maxc)) { p.cluster = C; break; }
+        for (int i = 0; i < kNumPlanSizes; ++i) {
+            if (in.wide_cluster > 0 && kPlanSizes[i] != in.wide_cluster) continue;
+            if (fits(i, &maxc)) { p.cluster = kPlanSizes[i]; break; }
         }
         if (p.cluster == 0) return known ? INFINITY : 0.0;   // launch_batch refuses it
         p.clusters = std::min(p.systems, maxc);
-        if (B->wide_clusters > 0) p.clusters = std::min(p.clusters, B->wide_clusters);
+        if (in.wide_clusters > 0) p.clusters = std::min(p.clusters, in.wide_clusters);
         *plan_out = p;
         if (!known) return 0.0;
         // the clusters take their systems longest (in cluster time) first
@@ -2132,22 +2148,23 @@ double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const
             if (j < p.systems) w.push_back(cluster_time(ord[j], p.cluster));
             else d.push_back(dur[ord[j]]);
         }
-        return simulate_makespan(w, p.clusters, p.cluster, d, B->sms, per_sm) * 1e-6;
+        return simulate_makespan(w, p.clusters, p.cluster, d, in.sms, per_sm) * 1e-6;
     }
     if (!known) return 0.0;
     std::vector<double> all;
     double total = 0.0;
     for (int32_t s_ : ord) { all.push_back(dur[s_]); total += dur[s_]; }
-    double best = simulate_makespan({}, 0, 1, all, B->sms, per_sm);
+    double best = simulate_makespan({}, 0, 1, all, in.sms, per_sm);
     std::vector<int32_t> best_wide;
     int64_t best_a_cap = 0;
-    const double balanced = total / ((double)B->sms * per_sm);
-    for (int C : {16, 8, 4, 2}) {
+    const double balanced = total / ((double)in.sms * per_sm);
+    for (int i = 0; i < kNumPlanSizes; ++i) {
+        const int C = kPlanSizes[i];
         int maxc = 0;
-        if (!fits(C, &maxc)) continue;
+        if (C == 1 || !fits(i, &maxc)) continue;
         std::vector<int32_t> elig;   // positions in ord
         for (int j = 0; j < count && elig.size() < 96; ++j)
-            if (B->m_of[ord[j]] >= 4 * C && dur[ord[j]] >= 0.25 * balanced) elig.push_back(j);
+            if (in.m[ord[j]] >= 4 * C && dur[ord[j]] >= 0.25 * balanced) elig.push_back(j);
         std::vector<char> wide((size_t)count, 0);
         for (size_t K = 1; K <= elig.size(); ++K) {
             wide[elig[K - 1]] = 1;
@@ -2158,7 +2175,7 @@ double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const
             }
             std::sort(w.begin(), w.end(), std::greater<double>());
             const int cl = std::min((int)K, maxc);
-            const double ms = simulate_makespan(w, cl, C, d, B->sms, per_sm);
+            const double ms = simulate_makespan(w, cl, C, d, in.sms, per_sm);
             if (ms < 0.98 * best) {
                 best = ms;
                 plan_out->systems = (int32_t)K;
@@ -2183,6 +2200,40 @@ double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const
         *ord_out = o2;
     }
     return best * 1e-6;
+}
+
+// plan_search on this batch: the device's facts (which cluster sizes' vectors fit a
+// block, how many such clusters can be resident, how much of A a block stages) gathered
+// here, the launch configuration's blocks per SM, the learned overhead h0
+double plan_batch(const tacta_batch_s* B, const tacta_options& o, int cfg, const std::vector<double>& dur,
+                  WidePlan* plan_out, std::vector<int32_t>* ord_out) {
+    PlanInput in;
+    in.count = B->count;
+    in.dur = dur.data();
+    in.steps = B->last_iters.size() == (size_t)B->count ? B->last_iters.data() : nullptr;
+    in.m = B->m_of.data();
+    in.n = B->n_of.data();
+    in.ord = B->ord.data();
+    in.storage = B->storage;
+    in.t_max = o.t_max;
+    in.cycle = o.cycle;
+    in.sms = B->sms;
+    in.per_sm = kConfigs[cfg].per_sm;
+    in.wide_mode = B->wide_mode;
+    in.wide_cluster = B->wide_cluster;
+    in.wide_clusters = B->wide_clusters;
+    in.h0 = B->wide_h0 >= 0.0 ? B->wide_h0 : kWideH0;
+    const bool known = B->count > 0 && std::all_of(dur.begin(), dur.end(), [](double v) { return v > 0.0; });
+    if (B->wide_mode != 0 && (known || B->wide_mode > 0)) {   // (the device queries only when used)
+        for (int i = 0; i < kNumPlanSizes; ++i) {
+            BatchParams Pw{};
+            size_t smw = 0;
+            if (!wide_params(B, o, kPlanSizes[i], &Pw, &smw)) continue;
+            in.a_cap[i] = Pw.a_cap;
+            in.max_clusters[i] = wide_max_clusters_for(B, kPlanSizes[i], smw);
+        }
+    }
+    return plan_search(in, plan_out, ord_out);
 }
 
 bool batch_opts_ok(const tacta_options& o) {
@@ -2460,7 +2511,8 @@ extern "C" tacta_status tacta_batch_cta(tacta_batch B, const double* b, double* 
         } else if (B->dur_meas[q] && B->last_iters[q] > 0) {
             // the model's time with h0 = 0, subtracted from the measured time
             const double steps = (double)B->last_iters[q];
-            hnum += meas - cluster_time_model(B, q, C, a_cap_w, B->dur[q], steps, tm, 0.0);
+            hnum += meas - cluster_time_model(B->storage, B->m_of[q], B->n_of[q], C, a_cap_w, B->dur[q], steps,
+                                              tm, 0.0);
             hden += steps;
         }
     }
@@ -2490,6 +2542,54 @@ extern "C" double tacta_batch_simulate_makespan(const double* w, int32_t nw, int
     std::sort(wv.begin(), wv.end(), std::greater<double>());
     std::sort(dv.begin(), dv.end(), std::greater<double>());
     return simulate_makespan(wv, clusters, cluster, dv, sms, per_sm);
+}
+
+extern "C" double tacta_batch_plan_search(int32_t count, const double* dur, const int32_t* steps, const int32_t* m,
+                                          const int32_t* n, int32_t storage, int32_t t_max, int32_t cycle,
+                                          int32_t sms, int32_t per_sm, const int32_t* max_clusters,
+                                          const int64_t* a_cap, int32_t wide_mode, int32_t wide_cluster,
+                                          int32_t wide_clusters, double h0, int32_t* plan, int32_t* order) {
+    if (count < 0 || (count > 0 && (!dur || !m || !n || !order)) || !plan || !max_clusters || !a_cap) return -1.0;
+    if (storage != TACTA_BATCH_FP64 && storage != TACTA_BATCH_FP32 && storage != TACTA_BATCH_BF16) return -1.0;
+    if (t_max < 1 || t_max > kTMax || cycle < 0 || cycle > 2 || sms < 1 || per_sm < 1) return -1.0;
+    if (wide_mode < -1 || wide_cluster < 0 || wide_cluster > kWideMaxC || wide_clusters < 0) return -1.0;
+    if (!(h0 >= 0.0) || !std::isfinite(h0)) return -1.0;
+    for (int i = 0; i < kNumPlanSizes; ++i)
+        if (max_clusters[i] < 0 || a_cap[i] < 0) return -1.0;
+    for (int32_t q = 0; q < count; ++q) {
+        if (!(dur[q] >= 0.0) || !std::isfinite(dur[q]) || m[q] < 1 || n[q] < 1) return -1.0;
+        if (steps && steps[q] < 0) return -1.0;
+    }
+    std::vector<int32_t> ord0((size_t)count);
+    std::iota(ord0.begin(), ord0.end(), 0);
+    PlanInput in;
+    in.count = count;
+    in.dur = dur;
+    in.steps = steps;
+    in.m = m;
+    in.n = n;
+    in.ord = ord0.data();
+    in.storage = storage;
+    in.t_max = t_max;
+    in.cycle = cycle;
+    in.sms = sms;
+    in.per_sm = per_sm;
+    in.wide_mode = wide_mode;
+    in.wide_cluster = wide_cluster;
+    in.wide_clusters = wide_clusters;
+    in.h0 = h0;
+    for (int i = 0; i < kNumPlanSizes; ++i) {
+        in.max_clusters[i] = max_clusters[i];
+        in.a_cap[i] = a_cap[i];
+    }
+    WidePlan p{};
+    std::vector<int32_t> ord;
+    const double ms = plan_search(in, &p, &ord);
+    plan[0] = p.systems;
+    plan[1] = p.cluster;
+    plan[2] = p.clusters;
+    std::copy(ord.begin(), ord.end(), order);
+    return ms;
 }
 
 extern "C" tacta_status tacta_batch_set_wide(tacta_batch B, int32_t systems, int32_t cluster, int32_t clusters) {
