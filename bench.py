@@ -371,8 +371,8 @@ def batched_workload(tacta, dev, stream):
     per storage precision: the longest systems on thread-block clusters and the rest on
     single blocks of one persistent launch (launch shape and ring stage autotuned after a
     first full solve, whose step counts and measured times set the tuner's makespan
-    model, the queue order and the clusters' share; two warm solves teach the planner the
-    clusters' speed), against the single-system FP64 path (Plan per system)
+    model, the queue order and the clusters' share; two warm solves refit the planner's
+    per-step cluster overhead), against the single-system FP64 path (Plan per system)
     timed on an evenly spaced sample."""
     import gen
     import numpy as np
@@ -387,7 +387,7 @@ def batched_workload(tacta, dev, stream):
         B = tacta.Batch(mats, storage=st)
         B.cta(b, **kw)                     # a first full solve: step counts and queue order
         cfg, _ = B.tune(b, tol=TOL, tol_normal=0.0, max_iter=100)
-        for _ in range(2):   # warm: the planner learns the clusters' speed; graph capture
+        for _ in range(2):   # warm: the planner refits its cluster overhead; graph capture
             B.cta(b, **kw)
         plan = B.wide_plan(**kw)                             # the share the timed solve uses
         t, (x, iters, rel, reason) = timed(lambda: B.cta(b, **kw), stream)
